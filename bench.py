@@ -1,0 +1,335 @@
+"""Benchmark: incremental max-flow updates/s on the R-MAT scale-20 workload.
+
+One step = one whole pass of the hot path over one batch: apply the batch and
+repair the preflow (Alg. 5 lines 1-16), then the backward-BFS / worklist /
+discharge / remove-invalid loop until no active vertex remains, then the
+value.  The graph is R-MAT scale 20 (2^20 vertices, 16 x 2^20 draws,
+a/b/c/d = 0.57/0.19/0.19/0.05, self-loops dropped, duplicates merged, caps
+U[1,1000]); batches are mixed (40% increase, 40% decrease, 10% insert, 10%
+delete) of --batch updates.  The residual state (~0.6 GB) is larger than the
+129 MB L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--impl ours|reference]
+
+With N > 1 (torchrun), every rank runs its own replica (the path does not
+shard) and rank 0 reports the aggregate.  --impl reference
+times the CPU oracle (Dinic recomputed from scratch after each batch) on
+rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "dynamic maxflow updates/s & p50/p99 batch latency vs static re-solve; HBM GB/s"
+UNIT = "updates/s"
+HBM_FALLBACK_GBS = 6800.0
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": HBM_FALLBACK_GBS}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(args):
+    from paper_2511_01235_gb300 import workloads as W
+    if args.workload == "rmat20":
+        g = W.rmat(20, 16, 0.57, 0.19, 0.19, seed=2, cap_lo=1, cap_hi=1000)
+        ins_hi = 1000
+    elif args.workload == "er_small":
+        g = W.er_small()
+        ins_hi = 100
+    else:
+        raise SystemExit(f"unknown workload {args.workload}")
+    es = W.EdgeSet(g.n, g.src, g.dst, g.cap)
+    rng = np.random.default_rng(1234)
+    return g, es, rng, ins_hi
+
+
+def gen_batches(es, rng, count, B, ins_hi):
+    from paper_2511_01235_gb300 import workloads as W
+    out = []
+    for _ in range(count):
+        b = W.mixed_batch(es, B, rng, ins_cap_hi=ins_hi)
+        es.apply(b.u, b.v, b.cap)
+        out.append(b)
+    return out
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    """The CPU oracle timed on this host: Dinic from scratch on the updated graph, per batch."""
+    import oracle
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    g, es, rng, ins_hi = make_workload(args)
+    batches = gen_batches(es.copy(), rng, args.warmup + args.steps, args.batch, ins_hi)
+    es2 = W_edgeset(g)
+    times = []
+    for i, b in enumerate(batches):
+        es2.apply(b.u, b.v, b.cap)
+        u, v, c = es2.coo()
+        t0 = time.perf_counter()
+        oracle.maxflow(g.n, u, v, c, g.s, g.t)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    val = args.batch * len(times) / tot
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": config_of(args, g),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{len(times)} batches of {args.batch}; Dinic recomputed from scratch per batch"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def W_edgeset(g):
+    from paper_2511_01235_gb300 import workloads as W
+    return W.EdgeSet(g.n, g.src, g.dst, g.cap)
+
+
+def config_of(args, g):
+    return {"workload": f"{args.workload}: R-MAT scale 20, edge factor 16, a/b/c=0.57/0.19/0.19, caps U[1,1000]"
+            if args.workload == "rmat20" else args.workload,
+            "n": int(g.n), "m_merged": int(g.m), "s": int(g.s), "t": int(g.t), "batch": args.batch,
+            "batch_mix": "40% increase U[1,50] / 40% decrease to U[0,cap] / 10% insert / 10% delete",
+            "l2": "inputs larger than L2 (residual state ~0.6 GB vs 129 MB L2)",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+def cpu_baseline_sample(g, batches, budget_s=20.0):
+    import oracle
+    es2 = W_edgeset(g)
+    times = []
+    t_start = time.perf_counter()
+    for b in batches:
+        es2.apply(b.u, b.v, b.cap)
+        u, v, c = es2.coo()
+        t0 = time.perf_counter()
+        oracle.maxflow(g.n, u, v, c, g.s, g.t)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_start > budget_s:
+            break
+    return times
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=10000)
+    ap.add_argument("--workload", default="rmat20")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--static-reps", type=int, default=3)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2511_01235_gb300 import native
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    native.load()
+
+    g, es, rng, ins_hi = make_workload(args)
+    nb = args.warmup + args.steps
+    batches = gen_batches(es, rng, nb, args.batch, ins_hi)
+    dev_batches = [(torch.from_numpy(b.u).cuda(), torch.from_numpy(b.v).cuda(), torch.from_numpy(b.cap).cuda())
+                   for b in batches]
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    S = native.Solver(g.n, g.src, g.dst, g.cap, g.s, g.t, stream=stream)
+    init_s = time.perf_counter() - t0
+    static_value = S.query()[0]
+
+    # ---- device-resident timed region ----
+    for i in range(args.warmup):
+        S.update(*dev_batches[i])
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = ClockSampler(dev)
+    clk.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    lat = []
+    kbytes, kms = [], []
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        a, b = evs[k]
+        a.record(stream)
+        S.update(*dev_batches[args.warmup + k])
+        b.record(stream)
+        st = S.stats()
+        kbytes.append(st["bytes_bfs"] + st["bytes_discharge"] + st["bytes_fix"] + st["bytes_worklist"] + st["bytes_apply"])
+        kms.append(st["ms_last"])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    clocks = clk.stop()
+    lat = np.array([a.elapsed_time(b) for a, b in evs])
+    tot_ms = float(lat.sum())
+    if ws > 1:
+        t = torch.tensor([tot_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = ws * args.batch * args.steps / (tot_ms / 1e3)
+    final_value = S.query()[0]
+    last_stats = S.stats()
+
+    # ---- end-to-end through the public API with host buffers ----
+    e2e_b = gen_batches(es, rng, min(args.steps, 10), args.batch, ins_hi)
+    pinned = []
+    for b in e2e_b:
+        tu = torch.from_numpy(b.u).pin_memory()
+        tv = torch.from_numpy(b.v).pin_memory()
+        tc = torch.from_numpy(b.cap).pin_memory()
+        pinned.append((tu, tv, tc))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for tu, tv, tc in pinned:
+        native.maxflow_update(S.h, tu.numpy(), tv.numpy(), tc.numpy())
+        native.maxflow_query(S.h, S.n)
+    e2e_s = time.perf_counter() - t0
+    e2e_val = ws * args.batch * len(pinned) / e2e_s
+
+    # ---- static re-solve comparator (same updated graph) ----
+    static_ms = []
+    for _ in range(args.static_reps):
+        S.resolve_static()
+        static_ms.append(S.stats()["ms_last"])
+    static_stats = S.stats()
+
+    if rank == 0:
+        peaks, peak_src = _peaks()
+        hbm = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
+        avg_bytes = float(np.mean(kbytes))
+        avg_ms = float(np.mean(kms))
+        achieved = avg_bytes / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0.0
+        cpu = None
+        if not args.no_cpu_baseline and ws == 1:
+            times = cpu_baseline_sample(g, batches[: 8])
+            cpu = {"value": args.batch * len(times) / sum(times), "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"{len(times)} batches of {args.batch} on {os.cpu_count()} host cores "
+                             f"(Dinic recomputed from scratch per batch, single thread)"}
+        p50 = float(np.percentile(lat, 50))
+        p99 = float(np.percentile(lat, 99))
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": config_of(args, g),
+            "latency_ms": {"p50": p50, "p99": p99, "mean": float(lat.mean())},
+            "static_resolve_ms": float(np.median(static_ms)),
+            "speedup_vs_static": float(np.median(static_ms)) / p50 if p50 > 0 else None,
+            "flow_value": {"static": int(static_value), "final": int(final_value)},
+            "init_s": init_s,
+            "gpu_launches": args.steps,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None,
+                         "kernel": "mf_solve_kernel", "peak_source": f"{peak_src} hbm_gbs (copy)",
+                         "algorithmic_bytes_per_launch": avg_bytes, "avg_launch_ms": avg_ms},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 12 * args.batch,
+                    "d2h_bytes_per_step": 2048 + 8},
+            "clocks": clocks,
+            "last_update_stats": {k: last_stats[k] for k in ("iterations", "bfs_levels", "pushes", "relabels",
+                                                             "steep_fixes", "active_first", "ms_bfs", "ms_discharge",
+                                                             "ms_fix", "ms_worklist", "ms_apply", "grid_blocks",
+                                                             "kernel_cycles")},
+            "static_stats": {k: static_stats[k] for k in ("iterations", "bfs_levels", "pushes", "relabels",
+                                                          "ms_bfs", "ms_discharge", "ms_fix", "ms_worklist")},
+            "wall_s_timed": wall,
+        }
+        print(json.dumps(line), flush=True)
+    S.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * maxflow.h -- C ABI of the GB300 dynamic max-flow library.
+ *
+ * The library computes the maximum s-t flow of a directed graph with int32
+ * capacities and keeps it up to date under batches of capacity updates,
+ * following "Scalable Maxflow Processing for Dynamic Graphs" (Kannappan,
+ * Kumar, Nasre):
+ *   - the problem statement: Sec. 2.1 (flow network, capacity and
+ *     conservation constraints) and Sec. 4.1 (a batch is a set of edges with
+ *     new capacities, higher or lower than before);
+ *   - the residual graph: the Bi-CSR of Sec. 5.1 (every pair (u,v) with an
+ *     edge in either direction has a slot at u and a slot at v, plus the
+ *     index of the reverse slot);
+ *   - the static solve: Alg. 1 (initialisation, source saturation, loop of
+ *     backward BFS Alg. 4, push-relabel Alg. 2, remove-invalid-edges Alg. 3);
+ *   - the incremental re-solve: Alg. 5 (apply the batch, send back flow that
+ *     no longer fits, recompute excess, saturate the source edges again, loop
+ *     of backward BFS Alg. 6 rooted at t and every deficient vertex,
+ *     Alg. 2, Alg. 3) and its value formula;
+ *   - the certificate: the cut A = {h = n}, B = {h < n} (Sec. 3.1 Theorem 3.4
+ *     and the note after Theorem 3.6; Sec. 4.3).
+ *
+ * Every entry point returns an int status (MAXFLOW_OK = 0 or an error code
+ * below); maxflow_strerror() names it.  No entry point throws, aborts or
+ * faults the GPU on bad input: arguments are checked first and an error is
+ * returned with the state unchanged.
+ *
+ * Memory: the library copies every input it is given and owns its device
+ * state; output buffers belong to the caller.  Device memory comes from the
+ * allocator callbacks in maxflow_opts (e.g. PyTorch's caching allocator) or,
+ * when those are NULL, from cudaMalloc.  All GPU work of a context is issued
+ * on the context's stream.  Host pointers may be pageable or pinned; pinned
+ * memory makes the copies asynchronous with the host.
+ *
+ * Threads: a context must not be used from two host threads at once.
+ * Different contexts are independent.
+ */
+#ifndef MAXFLOW_GB300_H
+#define MAXFLOW_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define MAXFLOW_OK                0
+#define MAXFLOW_ERR_INVALID       1  /* bad argument: s == t, id out of range, negative capacity, n < 2, NULL */
+#define MAXFLOW_ERR_OOM           2  /* device or host allocation failed */
+#define MAXFLOW_ERR_CUDA          3  /* a CUDA runtime call failed (no usable GPU, launch error, ...) */
+#define MAXFLOW_ERR_NOT_CONVERGED 4  /* the iteration or time cap was hit; the state stays a valid preflow */
+#define MAXFLOW_ERR_STATE         5  /* call out of order (e.g. query before a solve) */
+#define MAXFLOW_ERR_INTERNAL      6  /* a self-check failed (certificate, device wait gave up) */
+#define MAXFLOW_ERR_TOO_LARGE     7  /* more slots than int32 indexing allows, or a capacity sum overflows int32 */
+
+typedef struct maxflow_ctx maxflow_ctx;   /* opaque, library-owned */
+
+/* A graph as host COO arrays (caller-owned; copied by maxflow_init).
+ * Self-loops are dropped and parallel edges are summed (their total must fit
+ * in int32).  Capacities must be >= 0. */
+typedef struct {
+    int32_t n;              /* vertices 0 .. n-1, n >= 2 */
+    int64_t m;              /* number of COO entries */
+    const int32_t *src;
+    const int32_t *dst;
+    const int32_t *cap;
+} maxflow_graph;
+
+/* A batch of capacity updates (Sec. 4.1): each (u, v, new_cap) SETS
+ * cap(u, v) = new_cap.  new_cap = 0 deletes the edge (its slots remain, with
+ * capacity 0).  If no slot exists for the pair {u, v} the update inserts one
+ * (into the per-vertex slack; a full row triggers a rebuild inside the call).
+ * Within one batch the last update of a directed pair wins; u == v is
+ * ignored.  The batch is validated whole before any state changes. */
+typedef struct {
+    int64_t count;
+    const int32_t *u;
+    const int32_t *v;
+    const int32_t *new_cap;
+    int32_t on_device;      /* 0: host arrays; 1: device arrays on the context's GPU */
+} maxflow_batch;
+
+typedef void *(*maxflow_alloc_fn)(size_t bytes, void *user, void *stream);
+typedef void (*maxflow_free_fn)(void *ptr, size_t bytes, void *user, void *stream);
+
+typedef struct {
+    int32_t kernel_cycles;      /* push/relabel cycles per vertex per discharge (Alg. 2's KERNEL_CYCLES);
+                                   0 = max(1, ceil(m / n)), the paper's average-degree heuristic (Sec. 6.1) */
+    int32_t data_driven;        /* 1: worklist of active vertices (Sec. 5.2.1 O1); 0: topology-driven */
+    int32_t fix_steep;          /* 1: run remove-invalid-edges (Alg. 3) after each discharge */
+    int32_t grid_blocks;        /* cooperative grid size; 0 = sized from the graph and the GPU */
+    int64_t max_iters;          /* outer-iteration cap per solve; 0 = 4n + 1000 */
+    double  time_limit_s;       /* device wall-clock cap per solve; 0 = 120 s */
+    double  wait_limit_s;       /* cap on any single device-side wait (grid barrier); 0 = 2 s */
+    float   slack_factor;       /* spare slots per vertex for insertions: max(slack_min, ceil(deg * factor)) */
+    int32_t slack_min;
+    int32_t device;             /* CUDA device ordinal; -1 = the current device */
+    void   *stream;             /* cudaStream_t for all work of the context; NULL = legacy default stream */
+    maxflow_alloc_fn alloc;     /* optional device allocator (NULL: cudaMalloc) */
+    maxflow_free_fn  free;
+    void   *alloc_user;
+} maxflow_opts;
+
+typedef struct {
+    int64_t n, m_edges;             /* vertices; directed edges with a slot (merged, incl. zero capacity) */
+    int64_t slots, slot_capacity;   /* used and reserved Bi-CSR slots */
+    int32_t kernel_cycles, grid_blocks, block_threads, blocks_per_sm;
+    int64_t solves, updates, rebuilds;
+    /* last solve (static, incremental or extraction run) */
+    int64_t iterations, bfs_levels, pushes, relabels, steep_fixes;
+    int64_t active_first, active_total;     /* active vertices in the first / all iterations */
+    int64_t bytes_bfs, bytes_discharge, bytes_fix, bytes_worklist, bytes_apply;  /* algorithmic bytes, per solve */
+    double  ms_last;                /* device time of the last solve kernel (CUDA events) */
+    double  ms_bfs, ms_discharge, ms_fix, ms_worklist, ms_apply;  /* device wall time per phase (globaltimer) */
+    int64_t value;                  /* value of the last solve */
+} maxflow_stats_t;
+
+/* Fill o with the defaults documented above. */
+void maxflow_default_opts(maxflow_opts *o);
+
+/* Build the residual Bi-CSR of g (Sec. 5.1) on the GPU and run the static
+ * solve (Alg. 1 with Alg. 4/6 heights, Alg. 2, Alg. 3).  s != t, both in
+ * [0, n).  opt may be NULL (defaults).  On success *out is a new context;
+ * on error *out is NULL. */
+int maxflow_init(maxflow_ctx **out, const maxflow_graph *g, int32_t s, int32_t t, const maxflow_opts *opt);
+
+/* Apply a batch and re-solve incrementally (Alg. 5 and Alg. 6): apply the
+ * capacity changes to the residual capacities, send back flow that exceeds
+ * a new capacity, update the excess, saturate the source edges, then resume
+ * push-relabel from the current heights and excesses.  Returns when the
+ * re-solve is done (the value is then available to maxflow_query). */
+int maxflow_update(maxflow_ctx *c, const maxflow_batch *b);
+
+/* The current maximum-flow value (value formula of Alg. 5: the sum of e(v)
+ * over v != s with h(v) < n, which equals e(t) plus the deficits).
+ * side (NULL or n host bytes): 1 for the source side A = {h = n} of the
+ * minimum cut (Sec. 3.1 note), 0 otherwise.  cut_cap (NULL ok): total capacity
+ * of edges from A to V \ A, equal to the value.  Synchronises the stream. */
+int maxflow_query(maxflow_ctx *c, int64_t *value, uint8_t *side, int64_t *cut_cap);
+
+/* The comparator of Sec. 6.2: re-solve the current graph from zero flow
+ * (Alg. 1) instead of incrementally. */
+int maxflow_resolve_static(maxflow_ctx *c);
+
+/* A feasible maximum flow (Sec. 3.1 Theorem 3.3, Lemma 3.5, Sec. 4.3 Claim):
+ * the excess left in A is returned to s and the deficits in B are filled
+ * from t, on a copy of the state (the solver state is not changed).
+ * On input *count is the capacity of the output arrays; on output it is the
+ * number of directed edges with capacity > 0.  If the capacity is too small
+ * (or the arrays are NULL) nothing is written and MAXFLOW_OK is returned with
+ * the needed count.  Outputs are host arrays: edge (u[i], v[i]) with
+ * capacity cap[i] carries flow[i], 0 <= flow[i] <= cap[i]. */
+int maxflow_get_flow(maxflow_ctx *c, int64_t *count, int32_t *u, int32_t *v, int32_t *cap, int32_t *flow);
+
+/* Counters and timings of the context and of its last solve. */
+int maxflow_stats(maxflow_ctx *c, maxflow_stats_t *out);
+
+/* Release every resource of the context (NULL is a no-op). */
+void maxflow_destroy(maxflow_ctx *c);
+
+/* A static string naming a status code. */
+const char *maxflow_strerror(int code);
+
+/* ---- step-level entry points (each runs one step of the path) ------------ */
+
+/* Replace the state by the flow assignment f(u[i], v[i]) = f[i] on the listed
+ * directed edges (all others 0): c_f(u,v) = c(u,v) - f(u,v) + f(v,u) and
+ * e(x) = inflow - outflow.  Each (u, v) must be an edge with 0 <= f <= cap.
+ * Host arrays.  Heights are left as they are. */
+int maxflow_set_flow(maxflow_ctx *c, int64_t count, const int32_t *u, const int32_t *v, const int32_t *f);
+
+/* Alg. 5 lines 1-16 only (apply, clamp, excess, source saturation); no re-solve. */
+int maxflow_apply(maxflow_ctx *c, const maxflow_batch *b);
+
+/* Alg. 6 only: heights = residual distance to {t} and every deficient vertex,
+ * h(s) = n, unreached vertices n.  Leaves flows and excesses unchanged. */
+int maxflow_global_relabel(maxflow_ctx *c);
+
+/* Resume the push-relabel loop (Alg. 5 lines 17-24) on the current state,
+ * without applying anything or saturating the source. */
+int maxflow_resolve(maxflow_ctx *c);
+
+/* Residual slots, row by row: (u, v, cap(u,v), c_f(u,v)).  *count in/out as
+ * in maxflow_get_flow (the number of used slots).  Host arrays. */
+int maxflow_get_residual(maxflow_ctx *c, int64_t *count, int32_t *u, int32_t *v, int32_t *cap, int32_t *cf);
+
+/* Heights and excesses (n entries each; either may be NULL).  Host arrays. */
+int maxflow_get_vertex_state(maxflow_ctx *c, int32_t *h, int64_t *e);
+
+/* Self-check of the state on the device.  Writes, for the current state:
+ * out[0] slots that break c_f(u,v) + c_f(v,u) = c(u,v) + c(v,u) or c_f >= 0
+ * (Sec. 3.1 Theorem 3.3); out[1] vertices whose tracked excess differs from
+ * the sum of its slots' c_f - c; out[2] residual slots from A = {h = n} into
+ * B (Theorem 3.4); out[3] active vertices (e > 0, h < n, not s or t);
+ * out[4] the cut capacity C(A, B); out[5] the value formula.  Six entries. */
+int maxflow_check(maxflow_ctx *c, int64_t *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MAXFLOW_GB300_H */

@@ -1,0 +1,770 @@
+// C ABI of the GB300 dynamic max-flow library (see include/maxflow.h).
+//
+// A context owns one residual Bi-CSR in device memory and runs every solve
+// as one cooperative launch of the persistent kernel in solver.cu.  The host
+// side only validates arguments, moves inputs and outputs, sizes scratch
+// buffers and, when an insertion finds a row without spare slots, rebuilds
+// the layout (keeping flows and excesses) and repeats the update.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "../../include/maxflow.h"
+#include "mf_internal.h"
+
+struct maxflow_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    maxflow_opts opt{};
+    int32_t n = 0, s = 0, t = 0;
+    int32_t kernel_cycles = 1;
+    int grid = 1, per_sm = 1, sms = 1;
+    MfGraph g{};
+    MfScratch sc{};
+    MfCtrl *ctrl = nullptr;
+    MfCtrl *hctrl = nullptr;      // pinned
+    long long *dbuf = nullptr;    // device scratch for aux outputs (16 entries)
+    long long *hbuf = nullptr;    // pinned mirror
+    int32_t *x_cf = nullptr, *x_cf2 = nullptr, *x_h = nullptr;
+    long long *x_e = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::vector<std::pair<void *, size_t>> allocs;
+    bool solved = false;
+    int64_t value = 0;
+    maxflow_stats_t st{};
+};
+
+namespace {
+
+struct DeviceGuard {
+    int old = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&old) != cudaSuccess) old = -1;
+        if (dev >= 0 && dev != old) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (old >= 0) cudaSetDevice(old);
+    }
+};
+
+void *dalloc(maxflow_ctx *c, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    void *p = nullptr;
+    if (c->opt.alloc) {
+        p = c->opt.alloc(bytes, c->opt.alloc_user, (void *)c->stream);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        p = nullptr;
+    }
+    if (p) c->allocs.emplace_back(p, bytes);
+    return p;
+}
+
+void dfree(maxflow_ctx *c, void *p)
+{
+    if (!p) return;
+    for (size_t i = 0; i < c->allocs.size(); ++i) {
+        if (c->allocs[i].first == p) {
+            size_t b = c->allocs[i].second;
+            if (c->opt.free) c->opt.free(p, b, c->opt.alloc_user, (void *)c->stream);
+            else cudaFree(p);
+            c->allocs.erase(c->allocs.begin() + (long)i);
+            return;
+        }
+    }
+}
+
+template <class T>
+T *dalloc_n(maxflow_ctx *c, int64_t count)
+{
+    return (T *)dalloc(c, sizeof(T) * (size_t)(count > 0 ? count : 1));
+}
+
+int rc_cuda(cudaError_t e) { return e == cudaSuccess ? MAXFLOW_OK : MAXFLOW_ERR_CUDA; }
+
+#define MF_TRY(expr)                          \
+    do {                                      \
+        int _rc = (expr);                     \
+        if (_rc != MAXFLOW_OK) return _rc;    \
+    } while (0)
+
+MfParams base_params(maxflow_ctx *c)
+{
+    MfParams p{};
+    p.g = c->g;
+    p.sc = c->sc;
+    p.ctrl = c->ctrl;
+    p.cf = c->g.cf;
+    p.h = c->g.h;
+    p.e = c->g.e;
+    p.sink = c->t;
+    p.source = c->s;
+    p.kernel_cycles = c->kernel_cycles;
+    p.fix_steep = c->opt.fix_steep ? 1 : 0;
+    p.data_driven = c->opt.data_driven ? 1 : 0;
+    p.max_iters = c->opt.max_iters > 0 ? c->opt.max_iters : 4LL * c->n + 1000;
+    double tl = c->opt.time_limit_s > 0 ? c->opt.time_limit_s : 120.0;
+    double wl = c->opt.wait_limit_s > 0 ? c->opt.wait_limit_s : 1.0;
+    p.time_limit_ns = (unsigned long long)(tl * 1e9);
+    p.wait_limit_ns = (unsigned long long)(wl * 1e9);
+    return p;
+}
+
+// Size the batch scratch for at least `count` updates.
+int ensure_batch(maxflow_ctx *c, int64_t count)
+{
+    if (count <= c->sc.batch_cap && c->sc.hkey) return MAXFLOW_OK;
+    int64_t cap = std::max<int64_t>(1024, c->sc.batch_cap);
+    while (cap < count) cap *= 2;
+    if (cap > (1LL << 29)) return MAXFLOW_ERR_TOO_LARGE;
+    int bits = 1;
+    while ((1LL << bits) < 2 * cap) ++bits;
+    MF_TRY(rc_cuda(cudaStreamSynchronize(c->stream)));
+    void *olds[] = {c->sc.hkey, c->sc.hval, c->sc.pkey, c->sc.pval, c->sc.bslot, c->sc.ins_list,
+                    c->sc.hused, c->sc.clamp, c->sc.bu, c->sc.bv, c->sc.bc};
+    for (void *p : olds) dfree(c, p);
+    int64_t hs = 1LL << bits;
+    c->sc.hkey = dalloc_n<unsigned long long>(c, hs);
+    c->sc.hval = dalloc_n<int32_t>(c, hs);
+    c->sc.pkey = dalloc_n<unsigned long long>(c, hs);
+    c->sc.pval = dalloc_n<int32_t>(c, hs);
+    c->sc.bslot = dalloc_n<int32_t>(c, cap);
+    c->sc.ins_list = dalloc_n<int32_t>(c, cap);
+    c->sc.hused = dalloc_n<int32_t>(c, cap);
+    c->sc.clamp = dalloc_n<int32_t>(c, cap);
+    c->sc.bu = dalloc_n<int32_t>(c, cap);
+    c->sc.bv = dalloc_n<int32_t>(c, cap);
+    c->sc.bc = dalloc_n<int32_t>(c, cap);
+    if (!c->sc.hkey || !c->sc.hval || !c->sc.pkey || !c->sc.pval || !c->sc.bslot || !c->sc.ins_list ||
+        !c->sc.hused || !c->sc.clamp || !c->sc.bu || !c->sc.bv || !c->sc.bc)
+        return MAXFLOW_ERR_OOM;
+    MF_TRY(rc_cuda(cudaMemsetAsync(c->sc.hkey, 0xff, sizeof(unsigned long long) * hs, c->stream)));
+    MF_TRY(rc_cuda(cudaMemsetAsync(c->sc.hval, 0xff, sizeof(int32_t) * hs, c->stream)));
+    MF_TRY(rc_cuda(cudaMemsetAsync(c->sc.pkey, 0xff, sizeof(unsigned long long) * hs, c->stream)));
+    MF_TRY(rc_cuda(cudaMemsetAsync(c->sc.pval, 0xff, sizeof(int32_t) * hs, c->stream)));
+    c->sc.batch_cap = cap;
+    c->sc.hash_bits = bits;
+    return MAXFLOW_OK;
+}
+
+void free_graph(maxflow_ctx *c)
+{
+    void *ps[] = {c->g.off, c->g.deg, c->g.bdeg, c->g.dst, c->g.cf, c->g.cap, c->g.rev, c->g.pcap};
+    for (void *p : ps) dfree(c, p);
+    c->g.off = c->g.deg = c->g.bdeg = c->g.dst = c->g.cf = c->g.cap = c->g.rev = c->g.pcap = nullptr;
+    dfree(c, c->x_cf);
+    dfree(c, c->x_cf2);
+    c->x_cf = c->x_cf2 = nullptr;
+}
+
+// Upload a host layout into freshly allocated slot arrays (vertex arrays kept).
+int upload_graph(maxflow_ctx *c, const MfHostGraph &hg)
+{
+    free_graph(c);
+    int64_t S = hg.slot_cap;
+    int32_t n = hg.n;
+    c->g.n = n;
+    c->g.slot_cap = S;
+    c->g.off = dalloc_n<int32_t>(c, n + 1);
+    c->g.deg = dalloc_n<int32_t>(c, n);
+    c->g.bdeg = dalloc_n<int32_t>(c, n);
+    c->g.dst = dalloc_n<int32_t>(c, S);
+    c->g.cf = dalloc_n<int32_t>(c, S);
+    c->g.cap = dalloc_n<int32_t>(c, S);
+    c->g.rev = dalloc_n<int32_t>(c, S);
+    c->g.pcap = dalloc_n<int32_t>(c, S);
+    if (!c->g.off || !c->g.deg || !c->g.bdeg || !c->g.dst || !c->g.cf || !c->g.cap || !c->g.rev || !c->g.pcap)
+        return MAXFLOW_ERR_OOM;
+    cudaStream_t st = c->stream;
+    MF_TRY(rc_cuda(cudaMemcpyAsync(c->g.off, hg.off, sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, st)));
+    MF_TRY(rc_cuda(cudaMemcpyAsync(c->g.deg, hg.deg, sizeof(int32_t) * n, cudaMemcpyHostToDevice, st)));
+    MF_TRY(rc_cuda(cudaMemcpyAsync(c->g.bdeg, hg.bdeg, sizeof(int32_t) * n, cudaMemcpyHostToDevice, st)));
+    MF_TRY(rc_cuda(cudaMemcpyAsync(c->g.dst, hg.dst, sizeof(int32_t) * S, cudaMemcpyHostToDevice, st)));
+    MF_TRY(rc_cuda(cudaMemcpyAsync(c->g.cf, hg.cf, sizeof(int32_t) * S, cudaMemcpyHostToDevice, st)));
+    MF_TRY(rc_cuda(cudaMemcpyAsync(c->g.cap, hg.cap, sizeof(int32_t) * S, cudaMemcpyHostToDevice, st)));
+    MF_TRY(rc_cuda(cudaMemcpyAsync(c->g.rev, hg.rev, sizeof(int32_t) * S, cudaMemcpyHostToDevice, st)));
+    MF_TRY(rc_cuda(cudaMemcpyAsync(c->g.pcap, hg.pcap, sizeof(int32_t) * S, cudaMemcpyHostToDevice, st)));
+    // the host arrays must stay valid until the copies complete
+    MF_TRY(rc_cuda(cudaStreamSynchronize(st)));
+    c->st.slot_capacity = S;
+    c->st.slots = hg.slots;
+    c->st.m_edges = hg.m_merged;
+    return MAXFLOW_OK;
+}
+
+void choose_grid(maxflow_ctx *c)
+{
+    int maxg = c->per_sm * c->sms;
+    int g = c->opt.grid_blocks;
+    if (g <= 0) {
+        double want = std::ceil((double)c->g.slot_cap / 8192.0);
+        g = (int)std::min<double>(maxg, std::max(2.0, want));
+    }
+    c->grid = std::max(1, std::min(g, maxg));
+    c->st.grid_blocks = c->grid;
+    c->st.block_threads = MF_BLOCK;
+    c->st.blocks_per_sm = c->per_sm;
+}
+
+void fill_stats(maxflow_ctx *c, const MfCtrl &h, float ms)
+{
+    maxflow_stats_t &s = c->st;
+    s.iterations = h.iters;
+    s.bfs_levels = h.bfs_levels;
+    s.pushes = h.pushes;
+    s.relabels = h.relabels;
+    s.steep_fixes = h.steep;
+    s.active_first = h.active_first;
+    s.active_total = h.active_total;
+    // algorithmic bytes of the paper's Bi-CSR (int32 per slot field, int64 excess):
+    //   BFS: per scanned slot dst + cf + pcap + h[dst] = 16 B; per vertex off + deg + h write + append = 16 B
+    //   discharge: per scanned slot in a cycle dst + cf + h[dst] = 12 B; per cycle off + deg + h + e = 20 B
+    //   remove-invalid: per slot 12 B; per vertex 20 B; worklist: h + e + deg + append per vertex = 20 B
+    s.bytes_bfs = 16 * h.slots_bfs + 16 * h.verts_bfs;
+    s.bytes_discharge = 12 * h.slots_dis + 20 * h.cycles_dis;
+    s.bytes_fix = 12 * h.slots_fix + 20 * h.verts_fix;
+    s.bytes_worklist = 16LL * c->n * (h.iters + 1);
+    s.bytes_apply = 100 * h.n_apply;
+    s.ms_last = ms;
+    s.ms_bfs = h.ns_bfs * 1e-6;
+    s.ms_discharge = h.ns_dis * 1e-6;
+    s.ms_fix = h.ns_fix * 1e-6;
+    s.ms_worklist = h.ns_wl * 1e-6;
+    s.ms_apply = h.ns_apply * 1e-6;
+    s.kernel_cycles = c->kernel_cycles;
+}
+
+// Launch one solve-kernel run and wait for it.  Returns the kernel's error
+// (MF_E_*) in *kerr and its status in *kstatus.
+int run_kernel(maxflow_ctx *c, const MfParams &p, int *kerr, int *kstatus)
+{
+    MF_TRY(rc_cuda(cudaEventRecord(c->ev0, c->stream)));
+    MF_TRY(mf_launch(p, c->grid, (void *)c->stream));
+    MF_TRY(rc_cuda(cudaEventRecord(c->ev1, c->stream)));
+    MF_TRY(rc_cuda(cudaMemcpyAsync(c->hctrl, c->ctrl, sizeof(MfCtrl), cudaMemcpyDeviceToHost, c->stream)));
+    MF_TRY(rc_cuda(cudaStreamSynchronize(c->stream)));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    *kerr = (int)c->hctrl->err.w[0];
+    *kstatus = c->hctrl->status;
+    fill_stats(c, *c->hctrl, ms);
+    if (*kerr != MF_E_NONE) {
+        // a barrier may have been left half-way: reset it for the next launch
+        MF_TRY(rc_cuda(cudaMemsetAsync(c->ctrl, 0, 2 * sizeof(MfLine), c->stream)));
+        MF_TRY(rc_cuda(cudaStreamSynchronize(c->stream)));
+    }
+    return MAXFLOW_OK;
+}
+
+int status_to_rc(int kerr, int kstatus)
+{
+    if (kerr == MF_E_INVALID) return MAXFLOW_ERR_INVALID;
+    if (kerr == MF_E_WAIT || kerr == MF_E_INTERNAL) return MAXFLOW_ERR_INTERNAL;
+    if (kerr != MF_E_NONE) return MAXFLOW_ERR_INTERNAL;
+    if (kstatus == MF_ST_CAP) return MAXFLOW_ERR_NOT_CONVERGED;
+    return MAXFLOW_OK;
+}
+
+// Run a solve that ends with the value phase; record the value.
+int run_solve(maxflow_ctx *c, MfParams p)
+{
+    int kerr = 0, kst = 0;
+    MF_TRY(run_kernel(c, p, &kerr, &kst));
+    int rc = status_to_rc(kerr, kst);
+    c->st.solves++;
+    if (rc == MAXFLOW_OK || rc == MAXFLOW_ERR_NOT_CONVERGED) {
+        c->value = c->hctrl->value;
+        c->st.value = c->value;
+        c->solved = (rc == MAXFLOW_OK);
+    }
+    return rc;
+}
+
+// Download the used slots as (u, v, cap, cf).
+int dump_slots(maxflow_ctx *c, std::vector<int32_t> &su, std::vector<int32_t> &sv, std::vector<int32_t> &scap,
+               std::vector<int32_t> &scf, const int32_t *cf_dev)
+{
+    int64_t S = c->g.slot_cap;
+    int32_t *rowid = dalloc_n<int32_t>(c, S);
+    if (!rowid) return MAXFLOW_ERR_OOM;
+    MfParams p = base_params(c);
+    int rc = mf_launch_aux(MF_AUX_DUMP, p, (void *)c->stream, nullptr, rowid);
+    std::vector<int32_t> hr((size_t)S), hd((size_t)S), hc((size_t)S), hf((size_t)S);
+    if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMemcpyAsync(hr.data(), rowid, sizeof(int32_t) * S, cudaMemcpyDeviceToHost, c->stream));
+    if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMemcpyAsync(hd.data(), c->g.dst, sizeof(int32_t) * S, cudaMemcpyDeviceToHost, c->stream));
+    if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMemcpyAsync(hc.data(), c->g.cap, sizeof(int32_t) * S, cudaMemcpyDeviceToHost, c->stream));
+    if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMemcpyAsync(hf.data(), cf_dev, sizeof(int32_t) * S, cudaMemcpyDeviceToHost, c->stream));
+    if (rc == MAXFLOW_OK) rc = rc_cuda(cudaStreamSynchronize(c->stream));
+    dfree(c, rowid);
+    if (rc != MAXFLOW_OK) return rc;
+    su.clear(); sv.clear(); scap.clear(); scf.clear();
+    for (int64_t x = 0; x < S; ++x) {
+        if (hr[(size_t)x] < 0) continue;
+        su.push_back(hr[(size_t)x]);
+        sv.push_back(hd[(size_t)x]);
+        scap.push_back(hc[(size_t)x]);
+        scf.push_back(hf[(size_t)x]);
+    }
+    return MAXFLOW_OK;
+}
+
+// Rebuild the layout with room for every pair named in the batch.
+int rebuild_for_batch(maxflow_ctx *c, const int32_t *hu, const int32_t *hv, int64_t count)
+{
+    std::vector<int32_t> su, sv, scap, scf;
+    MF_TRY(dump_slots(c, su, sv, scap, scf, c->g.cf));
+    MfHostGraph hg;
+    int rc = mf_rebuild_host(c->n, (int64_t)su.size(), su.data(), sv.data(), scap.data(), scf.data(), count, hu, hv,
+                             c->opt.slack_factor, c->opt.slack_min, hg);
+    if (rc == MAXFLOW_OK) rc = upload_graph(c, hg);
+    hg.release();
+    if (rc == MAXFLOW_OK) {
+        c->st.rebuilds++;
+        choose_grid(c);
+    }
+    return rc;
+}
+
+int check_host_batch(maxflow_ctx *c, const maxflow_batch *b)
+{
+    for (int64_t i = 0; i < b->count; ++i) {
+        int32_t u = b->u[i], v = b->v[i], w = b->new_cap[i];
+        if (u < 0 || u >= c->n || v < 0 || v >= c->n || w < 0) return MAXFLOW_ERR_INVALID;
+    }
+    return MAXFLOW_OK;
+}
+
+// Apply (and optionally solve) a batch.
+int do_batch(maxflow_ctx *c, const maxflow_batch *b, int mode)
+{
+    if (!b || b->count < 0) return MAXFLOW_ERR_INVALID;
+    if (b->count > 0 && (!b->u || !b->v || !b->new_cap)) return MAXFLOW_ERR_INVALID;
+    if (!b->on_device) MF_TRY(check_host_batch(c, b));
+    MF_TRY(ensure_batch(c, b->count));
+    MfParams p = base_params(c);
+    p.mode = mode;
+    p.bcount = b->count;
+    if (b->count > 0) {
+        if (b->on_device) {
+            p.bu = b->u;
+            p.bv = b->v;
+            p.bc = b->new_cap;
+        } else {
+            size_t bytes = sizeof(int32_t) * (size_t)b->count;
+            MF_TRY(rc_cuda(cudaMemcpyAsync(c->sc.bu, b->u, bytes, cudaMemcpyHostToDevice, c->stream)));
+            MF_TRY(rc_cuda(cudaMemcpyAsync(c->sc.bv, b->v, bytes, cudaMemcpyHostToDevice, c->stream)));
+            MF_TRY(rc_cuda(cudaMemcpyAsync(c->sc.bc, b->new_cap, bytes, cudaMemcpyHostToDevice, c->stream)));
+            p.bu = c->sc.bu;
+            p.bv = c->sc.bv;
+            p.bc = c->sc.bc;
+        }
+    }
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        int kerr = 0, kst = 0;
+        MF_TRY(run_kernel(c, p, &kerr, &kst));
+        if (kerr == MF_E_OVERFLOW) {
+            if (attempt == 1) return MAXFLOW_ERR_INTERNAL;
+            // names of the pairs, on the host
+            std::vector<int32_t> hu((size_t)b->count), hv((size_t)b->count);
+            if (b->on_device) {
+                MF_TRY(rc_cuda(cudaMemcpyAsync(hu.data(), b->u, sizeof(int32_t) * b->count, cudaMemcpyDeviceToHost, c->stream)));
+                MF_TRY(rc_cuda(cudaMemcpyAsync(hv.data(), b->v, sizeof(int32_t) * b->count, cudaMemcpyDeviceToHost, c->stream)));
+                MF_TRY(rc_cuda(cudaStreamSynchronize(c->stream)));
+            } else {
+                std::memcpy(hu.data(), b->u, sizeof(int32_t) * b->count);
+                std::memcpy(hv.data(), b->v, sizeof(int32_t) * b->count);
+            }
+            MF_TRY(rebuild_for_batch(c, hu.data(), hv.data(), b->count));
+            p.g = c->g;
+            p.cf = c->g.cf;
+            continue;
+        }
+        int rc = status_to_rc(kerr, kst);
+        if (mode & MF_M_SOLVE) {
+            c->st.solves++;
+            if (rc == MAXFLOW_OK || rc == MAXFLOW_ERR_NOT_CONVERGED) {
+                c->value = c->hctrl->value;
+                c->st.value = c->value;
+                c->solved = (rc == MAXFLOW_OK);
+            }
+        } else if (rc == MAXFLOW_OK) {
+            c->solved = false;
+        }
+        if (rc == MAXFLOW_OK || rc == MAXFLOW_ERR_NOT_CONVERGED) c->st.updates++;
+        return rc;
+    }
+    return MAXFLOW_ERR_INTERNAL;
+}
+
+int count_slots(maxflow_ctx *c, int64_t *used, int64_t *capped)
+{
+    std::vector<int32_t> su, sv, scap, scf;
+    MF_TRY(dump_slots(c, su, sv, scap, scf, c->g.cf));
+    *used = (int64_t)su.size();
+    int64_t k = 0;
+    for (int32_t x : scap) k += x > 0;
+    *capped = k;
+    return MAXFLOW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void maxflow_default_opts(maxflow_opts *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->kernel_cycles = 0;
+    o->data_driven = 1;
+    o->fix_steep = 1;
+    o->grid_blocks = 0;
+    o->max_iters = 0;
+    o->time_limit_s = 0;
+    o->wait_limit_s = 0;
+    o->slack_factor = 0.25f;
+    o->slack_min = 4;
+    o->device = -1;
+    o->stream = nullptr;
+}
+
+const char *maxflow_strerror(int code)
+{
+    switch (code) {
+    case MAXFLOW_OK: return "ok";
+    case MAXFLOW_ERR_INVALID: return "invalid argument";
+    case MAXFLOW_ERR_OOM: return "out of memory";
+    case MAXFLOW_ERR_CUDA: return "CUDA runtime error (no usable GPU or launch failure)";
+    case MAXFLOW_ERR_NOT_CONVERGED: return "iteration or time cap reached before convergence";
+    case MAXFLOW_ERR_STATE: return "call out of order";
+    case MAXFLOW_ERR_INTERNAL: return "internal self-check failed";
+    case MAXFLOW_ERR_TOO_LARGE: return "graph too large for int32 slot indexing or capacity sums";
+    default: return "unknown status";
+    }
+}
+
+void maxflow_destroy(maxflow_ctx *c)
+{
+    if (!c) return;
+    {
+        DeviceGuard dg(c->device);
+        if (c->stream) cudaStreamSynchronize(c->stream);
+        while (!c->allocs.empty()) dfree(c, c->allocs.back().first);
+        if (c->hctrl) cudaFreeHost(c->hctrl);
+        if (c->hbuf) cudaFreeHost(c->hbuf);
+        if (c->ev0) cudaEventDestroy(c->ev0);
+        if (c->ev1) cudaEventDestroy(c->ev1);
+    }
+    delete c;
+}
+
+int maxflow_init(maxflow_ctx **out, const maxflow_graph *g, int32_t s, int32_t t, const maxflow_opts *opt)
+{
+    if (!out) return MAXFLOW_ERR_INVALID;
+    *out = nullptr;
+    if (!g || g->n < 2 || g->m < 0 || s < 0 || t < 0 || s >= g->n || t >= g->n || s == t) return MAXFLOW_ERR_INVALID;
+    if (g->m > 0 && (!g->src || !g->dst || !g->cap)) return MAXFLOW_ERR_INVALID;
+    maxflow_opts o;
+    maxflow_default_opts(&o);
+    if (opt) o = *opt;
+    if (o.slack_factor < 0 || o.slack_min < 0 || o.kernel_cycles < 0) return MAXFLOW_ERR_INVALID;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return MAXFLOW_ERR_CUDA;
+    int dev = o.device;
+    if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return MAXFLOW_ERR_CUDA;
+    if (dev >= ndev) return MAXFLOW_ERR_INVALID;
+
+    MfHostGraph hg;
+    int rc = mf_build_host(g->n, g->m, g->src, g->dst, g->cap, o.slack_factor, o.slack_min, hg);
+    if (rc != MAXFLOW_OK) return rc;
+
+    maxflow_ctx *c = new (std::nothrow) maxflow_ctx();
+    if (!c) {
+        hg.release();
+        return MAXFLOW_ERR_OOM;
+    }
+    c->opt = o;
+    c->device = dev;
+    c->stream = (cudaStream_t)o.stream;
+    c->n = g->n;
+    c->s = s;
+    c->t = t;
+    c->st.n = g->n;
+    DeviceGuard dg(dev);
+    rc = dg.ok ? MAXFLOW_OK : MAXFLOW_ERR_CUDA;
+    if (rc == MAXFLOW_OK) rc = mf_max_coresident_blocks(dev, &c->per_sm, &c->sms);
+    if (rc == MAXFLOW_OK) rc = rc_cuda(cudaEventCreate(&c->ev0));
+    if (rc == MAXFLOW_OK) rc = rc_cuda(cudaEventCreate(&c->ev1));
+    if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMallocHost((void **)&c->hctrl, sizeof(MfCtrl)));
+    if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMallocHost((void **)&c->hbuf, 16 * sizeof(long long)));
+    if (rc == MAXFLOW_OK) rc = upload_graph(c, hg);
+    hg.release();
+    if (rc == MAXFLOW_OK) {
+        int32_t n = c->n;
+        c->g.h = dalloc_n<int32_t>(c, n);
+        c->g.e = dalloc_n<long long>(c, n);
+        c->sc.border = dalloc_n<int32_t>(c, n);
+        c->sc.bhub = dalloc_n<int32_t>(c, n);
+        for (int b = 0; b < 3; ++b) c->sc.wl[b] = dalloc_n<int32_t>(c, n);
+        c->sc.ins_need = dalloc_n<int32_t>(c, n);
+        c->ctrl = (MfCtrl *)dalloc(c, sizeof(MfCtrl));
+        c->dbuf = dalloc_n<long long>(c, 16);
+        if (!c->g.h || !c->g.e || !c->sc.border || !c->sc.bhub || !c->sc.wl[0] || !c->sc.wl[1] || !c->sc.wl[2] ||
+            !c->sc.ins_need || !c->ctrl || !c->dbuf)
+            rc = MAXFLOW_ERR_OOM;
+    }
+    if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMemsetAsync(c->sc.ins_need, 0, sizeof(int32_t) * c->n, c->stream));
+    if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMemsetAsync(c->ctrl, 0, sizeof(MfCtrl), c->stream));
+    if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMemsetAsync(c->g.h, 0, sizeof(int32_t) * c->n, c->stream));
+    if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMemsetAsync(c->g.e, 0, sizeof(long long) * c->n, c->stream));
+    if (rc == MAXFLOW_OK) rc = ensure_batch(c, 1024);
+    if (rc == MAXFLOW_OK) {
+        int64_t m = c->st.m_edges;
+        c->kernel_cycles = o.kernel_cycles > 0 ? o.kernel_cycles : (int32_t)std::max<int64_t>(1, (m + c->n - 1) / c->n);
+        choose_grid(c);
+        MfParams p = base_params(c);
+        p.mode = MF_M_STATIC_INIT | MF_M_SOLVE;
+        rc = run_solve(c, p);
+    }
+    if (rc != MAXFLOW_OK) {
+        maxflow_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return MAXFLOW_OK;
+}
+
+int maxflow_update(maxflow_ctx *c, const maxflow_batch *b)
+{
+    if (!c) return MAXFLOW_ERR_STATE;
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return MAXFLOW_ERR_CUDA;
+    return do_batch(c, b, MF_M_APPLY | MF_M_SOLVE);
+}
+
+int maxflow_apply(maxflow_ctx *c, const maxflow_batch *b)
+{
+    if (!c) return MAXFLOW_ERR_STATE;
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return MAXFLOW_ERR_CUDA;
+    return do_batch(c, b, MF_M_APPLY);
+}
+
+int maxflow_resolve_static(maxflow_ctx *c)
+{
+    if (!c) return MAXFLOW_ERR_STATE;
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return MAXFLOW_ERR_CUDA;
+    MfParams p = base_params(c);
+    p.mode = MF_M_STATIC_INIT | MF_M_SOLVE;
+    return run_solve(c, p);
+}
+
+int maxflow_resolve(maxflow_ctx *c)
+{
+    if (!c) return MAXFLOW_ERR_STATE;
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return MAXFLOW_ERR_CUDA;
+    MfParams p = base_params(c);
+    p.mode = MF_M_SOLVE;
+    return run_solve(c, p);
+}
+
+int maxflow_global_relabel(maxflow_ctx *c)
+{
+    if (!c) return MAXFLOW_ERR_STATE;
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return MAXFLOW_ERR_CUDA;
+    MfParams p = base_params(c);
+    p.mode = MF_M_BFS_ONLY;
+    int kerr = 0, kst = 0;
+    MF_TRY(run_kernel(c, p, &kerr, &kst));
+    return kerr == MF_E_NONE ? MAXFLOW_OK : MAXFLOW_ERR_INTERNAL;
+}
+
+int maxflow_query(maxflow_ctx *c, int64_t *value, uint8_t *side, int64_t *cut_cap)
+{
+    if (!c) return MAXFLOW_ERR_STATE;
+    if (!c->solved) return MAXFLOW_ERR_STATE;
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return MAXFLOW_ERR_CUDA;
+    MfParams p = base_params(c);
+    if (side) {
+        uint8_t *ds = (uint8_t *)dalloc(c, (size_t)c->n);
+        if (!ds) return MAXFLOW_ERR_OOM;
+        int rc = mf_launch_aux(MF_AUX_SIDE, p, (void *)c->stream, nullptr, ds);
+        if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMemcpyAsync(side, ds, (size_t)c->n, cudaMemcpyDeviceToHost, c->stream));
+        if (rc == MAXFLOW_OK) rc = rc_cuda(cudaStreamSynchronize(c->stream));
+        dfree(c, ds);
+        MF_TRY(rc);
+    }
+    if (cut_cap) {
+        MF_TRY(rc_cuda(cudaMemsetAsync(c->dbuf, 0, sizeof(long long), c->stream)));
+        MF_TRY(mf_launch_aux(MF_AUX_CUT, p, (void *)c->stream, c->dbuf, nullptr));
+        MF_TRY(rc_cuda(cudaMemcpyAsync(c->hbuf, c->dbuf, sizeof(long long), cudaMemcpyDeviceToHost, c->stream)));
+        MF_TRY(rc_cuda(cudaStreamSynchronize(c->stream)));
+        *cut_cap = c->hbuf[0];
+    }
+    if (value) *value = c->value;
+    return MAXFLOW_OK;
+}
+
+int maxflow_stats(maxflow_ctx *c, maxflow_stats_t *out)
+{
+    if (!c || !out) return MAXFLOW_ERR_INVALID;
+    *out = c->st;
+    return MAXFLOW_OK;
+}
+
+int maxflow_set_flow(maxflow_ctx *c, int64_t count, const int32_t *u, const int32_t *v, const int32_t *f)
+{
+    if (!c || count < 0) return MAXFLOW_ERR_INVALID;
+    if (count > 0 && (!u || !v || !f)) return MAXFLOW_ERR_INVALID;
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return MAXFLOW_ERR_CUDA;
+    int32_t *du = dalloc_n<int32_t>(c, count), *dv = dalloc_n<int32_t>(c, count), *df = dalloc_n<int32_t>(c, count);
+    int rc = (du && dv && df) ? MAXFLOW_OK : MAXFLOW_ERR_OOM;
+    size_t bytes = sizeof(int32_t) * (size_t)count;
+    if (rc == MAXFLOW_OK && count > 0) {
+        rc = rc_cuda(cudaMemcpyAsync(du, u, bytes, cudaMemcpyHostToDevice, c->stream));
+        if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMemcpyAsync(dv, v, bytes, cudaMemcpyHostToDevice, c->stream));
+        if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMemcpyAsync(df, f, bytes, cudaMemcpyHostToDevice, c->stream));
+    }
+    MfParams p = base_params(c);
+    if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMemsetAsync(c->dbuf, 0, sizeof(long long), c->stream));
+    if (rc == MAXFLOW_OK && count > 0) rc = mf_set_flow_items(p, (void *)c->stream, c->dbuf, count, du, dv, df, 0);
+    if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMemcpyAsync(c->hbuf, c->dbuf, sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+    if (rc == MAXFLOW_OK) rc = rc_cuda(cudaStreamSynchronize(c->stream));
+    if (rc == MAXFLOW_OK && c->hbuf[0] != 0) rc = MAXFLOW_ERR_INVALID;
+    if (rc == MAXFLOW_OK) rc = mf_launch_aux(MF_AUX_SET_CF_RESET, p, (void *)c->stream, nullptr, nullptr);
+    if (rc == MAXFLOW_OK && count > 0) rc = mf_set_flow_items(p, (void *)c->stream, c->dbuf, count, du, dv, df, 1);
+    if (rc == MAXFLOW_OK) rc = mf_launch_aux(MF_AUX_EXCESS, p, (void *)c->stream, nullptr, nullptr);
+    if (rc == MAXFLOW_OK) rc = rc_cuda(cudaStreamSynchronize(c->stream));
+    dfree(c, du);
+    dfree(c, dv);
+    dfree(c, df);
+    if (rc == MAXFLOW_OK) c->solved = false;
+    return rc;
+}
+
+int maxflow_get_residual(maxflow_ctx *c, int64_t *count, int32_t *u, int32_t *v, int32_t *cap, int32_t *cf)
+{
+    if (!c || !count) return MAXFLOW_ERR_INVALID;
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return MAXFLOW_ERR_CUDA;
+    std::vector<int32_t> su, sv, scap, scf;
+    MF_TRY(dump_slots(c, su, sv, scap, scf, c->g.cf));
+    int64_t k = (int64_t)su.size();
+    if (!u || !v || !cap || !cf || *count < k) {
+        *count = k;
+        return MAXFLOW_OK;
+    }
+    std::memcpy(u, su.data(), sizeof(int32_t) * k);
+    std::memcpy(v, sv.data(), sizeof(int32_t) * k);
+    std::memcpy(cap, scap.data(), sizeof(int32_t) * k);
+    std::memcpy(cf, scf.data(), sizeof(int32_t) * k);
+    *count = k;
+    return MAXFLOW_OK;
+}
+
+int maxflow_get_vertex_state(maxflow_ctx *c, int32_t *h, int64_t *e)
+{
+    if (!c) return MAXFLOW_ERR_INVALID;
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return MAXFLOW_ERR_CUDA;
+    if (h) MF_TRY(rc_cuda(cudaMemcpyAsync(h, c->g.h, sizeof(int32_t) * c->n, cudaMemcpyDeviceToHost, c->stream)));
+    if (e) MF_TRY(rc_cuda(cudaMemcpyAsync(e, c->g.e, sizeof(long long) * c->n, cudaMemcpyDeviceToHost, c->stream)));
+    return rc_cuda(cudaStreamSynchronize(c->stream));
+}
+
+int maxflow_check(maxflow_ctx *c, int64_t *out)
+{
+    if (!c || !out) return MAXFLOW_ERR_INVALID;
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return MAXFLOW_ERR_CUDA;
+    MfParams p = base_params(c);
+    MF_TRY(rc_cuda(cudaMemsetAsync(c->dbuf, 0, 8 * sizeof(long long), c->stream)));
+    MF_TRY(mf_launch_aux(MF_AUX_CHECK, p, (void *)c->stream, c->dbuf, nullptr));
+    MF_TRY(rc_cuda(cudaMemcpyAsync(c->hbuf, c->dbuf, 6 * sizeof(long long), cudaMemcpyDeviceToHost, c->stream)));
+    MF_TRY(rc_cuda(cudaStreamSynchronize(c->stream)));
+    for (int i = 0; i < 6; ++i) out[i] = c->hbuf[i];
+    return MAXFLOW_OK;
+}
+
+int maxflow_get_flow(maxflow_ctx *c, int64_t *count, int32_t *u, int32_t *v, int32_t *cap, int32_t *flow)
+{
+    if (!c || !count) return MAXFLOW_ERR_INVALID;
+    if (!c->solved) return MAXFLOW_ERR_STATE;
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return MAXFLOW_ERR_CUDA;
+    int64_t used = 0, capped = 0;
+    MF_TRY(count_slots(c, &used, &capped));
+    if (!u || !v || !cap || !flow || *count < capped) {
+        *count = capped;
+        return MAXFLOW_OK;
+    }
+    int64_t S = c->g.slot_cap;
+    if (!c->x_cf) c->x_cf = dalloc_n<int32_t>(c, S);
+    if (!c->x_cf2) c->x_cf2 = dalloc_n<int32_t>(c, S);
+    if (!c->x_h) c->x_h = dalloc_n<int32_t>(c, c->n);
+    if (!c->x_e) c->x_e = dalloc_n<long long>(c, c->n);
+    if (!c->x_cf || !c->x_cf2 || !c->x_h || !c->x_e) return MAXFLOW_ERR_OOM;
+    MF_TRY(rc_cuda(cudaMemcpyAsync(c->x_cf, c->g.cf, sizeof(int32_t) * S, cudaMemcpyDeviceToDevice, c->stream)));
+    MF_TRY(rc_cuda(cudaMemcpyAsync(c->x_e, c->g.e, sizeof(long long) * c->n, cudaMemcpyDeviceToDevice, c->stream)));
+    maxflow_stats_t keep = c->st;
+    // (a) return the excess left on the source side to s (Lemma 3.5): a
+    //     push-relabel run whose sink is s, with t excluded.
+    MfParams p = base_params(c);
+    p.cf = c->x_cf;
+    p.h = c->x_h;
+    p.e = c->x_e;
+    p.sink = c->s;
+    p.source = c->t;
+    p.mode = MF_M_SOLVE | MF_M_NO_DEFICIT_ROOTS;
+    int kerr = 0, kst = 0;
+    MF_TRY(run_kernel(c, p, &kerr, &kst));
+    int rc = status_to_rc(kerr, kst);
+    // (b) fill the deficits on the sink side from t (Sec. 4.3 Claim): the
+    //     same run on the reversed residual graph with negated excess.
+    const int32_t *io1[2] = {c->x_cf, c->x_cf2};
+    if (rc == MAXFLOW_OK) rc = mf_launch_aux(MF_AUX_REVERSE_CF, p, (void *)c->stream, nullptr, io1);
+    if (rc == MAXFLOW_OK) rc = mf_launch_aux(MF_AUX_NEGATE_E, p, (void *)c->stream, nullptr, nullptr);
+    if (rc == MAXFLOW_OK) {
+        MfParams q = p;
+        q.cf = c->x_cf2;
+        q.sink = c->t;
+        q.source = c->s;
+        MF_TRY(run_kernel(c, q, &kerr, &kst));
+        rc = status_to_rc(kerr, kst);
+    }
+    const int32_t *io2[2] = {c->x_cf2, c->x_cf};
+    if (rc == MAXFLOW_OK) rc = mf_launch_aux(MF_AUX_REVERSE_CF, p, (void *)c->stream, nullptr, io2);
+    if (rc == MAXFLOW_OK) rc = mf_launch_aux(MF_AUX_NEGATE_E, p, (void *)c->stream, nullptr, nullptr);
+    c->st = keep;
+    MF_TRY(rc);
+    std::vector<int32_t> su, sv, scap, scf;
+    MF_TRY(dump_slots(c, su, sv, scap, scf, c->x_cf));
+    int64_t k = 0;
+    for (size_t i = 0; i < su.size(); ++i) {
+        if (scap[i] <= 0) continue;
+        u[k] = su[i];
+        v[k] = sv[i];
+        cap[k] = scap[i];
+        int64_t f = (int64_t)scap[i] - scf[i];
+        flow[k] = (int32_t)(f > 0 ? f : 0);
+        ++k;
+    }
+    *count = k;
+    return MAXFLOW_OK;
+}
+
+}  // extern "C"

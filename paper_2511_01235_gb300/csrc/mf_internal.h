@@ -1,0 +1,167 @@
+// Internal structures of the GB300 max-flow library (not part of the ABI).
+//
+// Device layout of one residual graph (Sec. 5.1 Bi-CSR), structure of arrays:
+//   off[n+1]   reserved start of each row (rows are never moved in place)
+//   deg[n]     used slots of the row: base slots (sorted by dst) then inserted slots
+//   bdeg[n]    number of sorted base slots (binary search range)
+//   dst[S]     head v of slot (u, v)
+//   cf[S]      residual capacity c_f(u, v)
+//   cap[S]     capacity c(u, v) (0 for a reverse-only slot)
+//   rev[S]     index of the slot (v, u)
+//   pcap[S]    c(u, v) + c(v, u): with the pair-sum invariant (Sec. 3.1
+//              Theorem 3.3) c_f(v, u) = pcap - c_f(u, v), so the backward BFS
+//              reads the reverse residual without a gather through rev.
+//   h[n]       heights (int32), e[n] excesses (int64)
+#pragma once
+#include <stdint.h>
+
+#define MF_BLOCK 512          // threads per CTA of the persistent kernel
+#define MF_WARPS (MF_BLOCK / 32)
+#define MF_SMALL_DEG 16       // discharge: rows up to this many slots get one thread
+#define MF_HUB_DEG 4096       // rows above this many slots get a whole CTA (discharge) or the grid (BFS)
+#define MF_ACTIVE_HIST 64
+
+// Solve-kernel status (ctrl->status)
+#define MF_ST_RUNNING 0
+#define MF_ST_CONVERGED 1
+#define MF_ST_CAP 2           // iteration or time cap
+#define MF_ST_ERROR 3         // ctrl->err holds the error
+
+// ctrl->err values
+#define MF_E_NONE 0
+#define MF_E_INVALID 1        // batch entry out of range / negative capacity
+#define MF_E_OVERFLOW 2       // insertion needs more slack than a row has
+#define MF_E_WAIT 3           // a grid barrier wait gave up
+#define MF_E_INTERNAL 4
+
+// Kernel modes (bit mask)
+#define MF_M_STATIC_INIT 1    // c_f = cap, e = 0, h = 0, saturate the source (Alg. 1 lines 1-14)
+#define MF_M_APPLY 2          // Alg. 5 lines 1-16
+#define MF_M_SOLVE 4          // the push-relabel loop
+#define MF_M_BFS_ONLY 8       // one backward BFS, then stop
+#define MF_M_NO_DEFICIT_ROOTS 16  // BFS roots: the sink only (flow extraction runs)
+#define MF_M_SKIP_SOURCE_SAT 32   // apply without saturating the source again
+
+struct alignas(128) MfLine {
+    unsigned int w[32];
+};
+
+// Control block in device memory.  Fields that many CTAs update with atomics
+// sit on their own 128-byte lines.  Fields marked (hook) are written only by
+// the single thread that completes a grid barrier, while every other CTA
+// waits, and are read by all CTAs after it: every CTA sees the same value.
+struct MfCtrl {
+    MfLine bar_count;     // w[0]: arrivals at the current barrier
+    MfLine bar_gen;       // w[0]: barrier generation
+    MfLine err;           // w[0]: sticky error (MF_E_*)
+    MfLine bfs_tail;      // w[0]: regular frontier append position
+    MfLine hub_tail;      // w[0]: hub frontier append position
+    MfLine head0;         // w[0]: dynamic work head
+    MfLine head1;
+    MfLine head2;
+    MfLine wl_tail;       // w[0..2]: worklist append positions per bin
+    MfLine misc;          // w[0]: insert list tail, w[1]: touched tail, w[2]: overflow flag
+    // ---- (hook) snapshots ----
+    int status;
+    int level;
+    int lvl_lo, lvl_hi;
+    int hub_lo, hub_hi;
+    int wl_n[3];
+    int ins_n, touch_n;
+    int bfs_done;
+    long long iters;
+    unsigned long long t_start, t_phase;
+    // ---- results and statistics (atomics, flushed once per CTA per phase) ----
+    long long value;
+    long long pushes, relabels, steep, bfs_levels, active_total, active_first;
+    long long slots_bfs, verts_bfs, slots_dis, cycles_dis, slots_fix, verts_fix, verts_wl, n_apply;
+    unsigned long long ns_bfs, ns_dis, ns_fix, ns_wl, ns_apply;
+    int active_hist[MF_ACTIVE_HIST];
+};
+
+struct MfGraph {
+    int32_t n;
+    int64_t slot_cap;
+    int32_t *off, *deg, *bdeg;
+    int32_t *dst, *cf, *cap, *rev, *pcap;
+    int32_t *h;
+    long long *e;
+};
+
+struct MfScratch {
+    int32_t *border;          // [n] BFS order (level segments)
+    int32_t *bhub;            // [n] hub frontier
+    int32_t *wl[3];           // [n] worklists: small, mid, hub
+    // batch apply
+    int64_t batch_cap;
+    int32_t hash_bits;
+    unsigned long long *hkey; // [1 << hash_bits] directed-pair dedup
+    int32_t *hval;
+    unsigned long long *pkey; // [1 << hash_bits] new-pair dedup
+    int32_t *pval;
+    int32_t *bslot;           // [batch_cap] slot of each update (-2: superseded or ignored)
+    int32_t *ins_list;        // [batch_cap] new-pair table positions
+    int32_t *hused;           // [batch_cap] dedup table positions in use
+    int32_t *clamp;           // [batch_cap] updates that lowered a capacity
+    int32_t *ins_need;        // [n]
+    int32_t *bu, *bv, *bc;    // [batch_cap] staging of a host batch
+};
+
+struct MfParams {
+    MfGraph g;
+    MfScratch sc;
+    MfCtrl *ctrl;
+    int32_t *cf;              // residual array of this run (g.cf, or a copy for extraction)
+    int32_t *h;
+    long long *e;
+    int32_t sink, source;
+    int32_t mode;
+    int32_t kernel_cycles;
+    int32_t fix_steep;
+    int32_t data_driven;
+    long long max_iters;
+    unsigned long long time_limit_ns;
+    unsigned long long wait_limit_ns;
+    // batch
+    int64_t bcount;
+    const int32_t *bu, *bv, *bc;
+};
+
+// Host-built Bi-CSR (graph_build.cpp)
+struct MfHostGraph {
+    int32_t n = 0;
+    int64_t m_merged = 0;     // directed edges with capacity > 0 or explicitly given (merged)
+    int64_t slot_cap = 0, slots = 0;
+    int32_t *off = nullptr, *deg = nullptr, *bdeg = nullptr;
+    int32_t *dst = nullptr, *cap = nullptr, *rev = nullptr, *pcap = nullptr, *cf = nullptr;
+    void release();
+};
+
+// Build from COO.  Returns MAXFLOW_* status.
+int mf_build_host(int32_t n, int64_t m, const int32_t *src, const int32_t *dst, const int32_t *cap,
+                  float slack_factor, int32_t slack_min, MfHostGraph &out);
+
+// Rebuild from a slot dump (u, v, cap, cf per used slot, any order; both
+// directions of every pair present) plus extra zero-capacity pairs.
+int mf_rebuild_host(int32_t n, int64_t nslots, const int32_t *su, const int32_t *sv, const int32_t *scap,
+                    const int32_t *scf, int64_t nextra, const int32_t *xu, const int32_t *xv,
+                    float slack_factor, int32_t slack_min, MfHostGraph &out);
+
+// solver.cu
+int mf_launch(const MfParams &p, int grid, void *stream);
+int mf_max_coresident_blocks(int device, int *per_sm, int *num_sms);
+int mf_launch_aux(int which, const MfParams &p, void *stream, long long *dev_out, const void *extra);
+
+#define MF_AUX_SET_CF_RESET 1     // cf = cap on all used slots
+#define MF_AUX_SET_FLOW 2         // extra = {count, u, v, f} device arrays; validate into dev_out[0] or apply
+#define MF_AUX_EXCESS 3           // e = sum(cf - cap) per row
+#define MF_AUX_CHECK 4            // dev_out[0..5]
+#define MF_AUX_SIDE 5             // extra = uint8_t* side (device)
+#define MF_AUX_CUT 6              // dev_out[0] = cut capacity
+#define MF_AUX_REVERSE_CF 7       // extra = int32_t* out: out[x] = cf[rev[x]]
+#define MF_AUX_CLEAR_SCRATCH 8    // reset hash tables and ins_need
+#define MF_AUX_DUMP 9             // extra = int32_t* rowid per slot (u of each slot index)
+#define MF_AUX_NEGATE_E 10        // e = -e
+
+int mf_set_flow_items(const MfParams &p, void *stream, long long *dev_bad, long long count, const int32_t *du,
+                      const int32_t *dv, const int32_t *df, int apply);

@@ -1,0 +1,1295 @@
+// Device code of the GB300 dynamic max-flow library (sm_103a).
+//
+// One cooperative, persistent kernel runs a whole solve: the optional static
+// initialisation (Alg. 1 lines 1-14) or batch repair (Alg. 5 lines 1-16),
+// then the loop { backward BFS (Alg. 4 / Alg. 6) ; active-vertex worklist
+// (Sec. 5.2.1 O1) ; stop if empty ; push-relabel discharge (Alg. 2) ;
+// remove-invalid-edges (Alg. 3) }, then the value formula of Alg. 5.  Phases
+// are separated by a grid barrier instead of kernel launches, so the
+// termination test never leaves the device and a small update costs one
+// launch.  Every barrier wait is bounded in time: on expiry the CTA records
+// MF_E_WAIT and returns, and the host reports MAXFLOW_ERR_INTERNAL.
+//
+// Readings of the paper used here (the same as the CPU oracle's):
+//   - BFS roots are the sink and every vertex other than s, t with e < 0
+//     (Alg. 6), in the static solve too, and h(s) = n always;
+//   - termination is tested right after a complete BFS;
+//   - a relabel with no residual neighbour, or above n, sets h = n;
+//   - ties between equal-height neighbours go to the lowest slot index;
+//   - the value is the sum of e(v) over v != s with h(v) < n.
+// Excess of the sink and the source is accumulated per CTA in shared memory
+// and added once per phase (every vertex may push into the sink, and one
+// global atomic per push would serialise on that word).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/maxflow.h"
+#include "mf_internal.h"
+
+namespace {
+
+constexpr unsigned long long kEmpty = ~0ull;
+
+__device__ __forceinline__ int ldg_cg(const int *p) { return __ldcg(p); }
+__device__ __forceinline__ long long ldg_cg(const long long *p) { return __ldcg(p); }
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long gtimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ long long atomic_add_ll(long long *p, long long v)
+{
+    return (long long)atomicAdd((unsigned long long *)p, (unsigned long long)v);
+}
+
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w < v ? w : v;
+    }
+    return v;
+}
+
+__device__ __forceinline__ long long warp_sum_ll(long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ unsigned hash_slot(unsigned long long key, int bits)
+{
+    return (unsigned)((key * 0x9E3779B97F4A7C15ull) >> (64 - bits));
+}
+
+// Per-CTA accumulators, flushed to global memory once per phase.
+struct Sh {
+    long long sink_e, src_e;
+    long long pushes, relabels, steep, slots, verts, cycles;
+    unsigned long long red[MF_WARPS];
+    int bcast_i;
+    int bcast_h;
+    long long bcast_e;
+    int ok;
+};
+
+enum Hook {
+    H_START = 0,
+    H_NONE,
+    H_APPLY_VALID,
+    H_APPLY_LOCATED,
+    H_APPLY_CHECKED,
+    H_APPLY_DELTA,
+    H_ITER,
+    H_BFS_START,
+    H_BFS_NEXT,
+    H_WL,
+    H_DIS,
+    H_FINAL,
+};
+
+// Executed by the one thread that completes a grid barrier, while every
+// other CTA waits for it.
+__device__ __noinline__ void run_hook(const MfParams &P, int hook)
+{
+    MfCtrl *c = P.ctrl;
+    unsigned long long now = gtimer();
+    unsigned long long dt = now - c->t_phase;
+    c->t_phase = now;
+    switch (hook) {
+    case H_START:
+        c->err.w[0] = 0;
+        c->status = MF_ST_RUNNING;
+        c->iters = 0;
+        c->value = 0;
+        c->pushes = c->relabels = c->steep = c->bfs_levels = c->active_total = c->active_first = 0;
+        c->slots_bfs = c->verts_bfs = c->slots_dis = c->cycles_dis = c->slots_fix = c->verts_fix = 0;
+        c->verts_wl = c->n_apply = 0;
+        c->ns_bfs = c->ns_dis = c->ns_fix = c->ns_wl = c->ns_apply = 0;
+        c->bfs_tail.w[0] = 0;
+        c->hub_tail.w[0] = 0;
+        c->head0.w[0] = c->head1.w[0] = c->head2.w[0] = 0;
+        for (int i = 0; i < 4; ++i) c->wl_tail.w[i] = 0;
+        for (int i = 0; i < 8; ++i) c->misc.w[i] = 0;
+        for (int i = 0; i < MF_ACTIVE_HIST; ++i) c->active_hist[i] = 0;
+        c->t_start = now;
+        c->t_phase = now;
+        break;
+    case H_APPLY_VALID:
+    case H_APPLY_CHECKED:
+        c->ns_apply += dt;
+        if (hook == H_APPLY_CHECKED && c->misc.w[2] != 0 && c->err.w[0] == 0) c->err.w[0] = MF_E_OVERFLOW;
+        break;
+    case H_APPLY_LOCATED:
+        c->ns_apply += dt;
+        c->ins_n = (int)c->misc.w[0];
+        break;
+    case H_APPLY_DELTA:
+        c->ns_apply += dt;
+        c->touch_n = (int)c->misc.w[1];
+        break;
+    case H_NONE:
+        c->ns_apply += dt;
+        break;
+    case H_ITER:
+        c->ns_fix += dt;
+        c->bfs_tail.w[0] = 0;
+        c->hub_tail.w[0] = 0;
+        for (int i = 0; i < 4; ++i) c->wl_tail.w[i] = 0;
+        c->head0.w[0] = c->head1.w[0] = c->head2.w[0] = 0;
+        break;
+    case H_BFS_START:
+        c->ns_bfs += dt;
+        c->level = 0;
+        c->lvl_lo = 0;
+        c->lvl_hi = (int)c->bfs_tail.w[0];
+        c->hub_lo = 0;
+        c->hub_hi = (int)c->hub_tail.w[0];
+        c->head0.w[0] = 0;
+        c->bfs_done = (c->lvl_hi == 0 && c->hub_hi == 0);
+        break;
+    case H_BFS_NEXT:
+        c->ns_bfs += dt;
+        c->bfs_levels += 1;
+        c->level += 1;
+        c->lvl_lo = c->lvl_hi;
+        c->lvl_hi = (int)c->bfs_tail.w[0];
+        c->hub_lo = c->hub_hi;
+        c->hub_hi = (int)c->hub_tail.w[0];
+        c->head0.w[0] = 0;
+        c->bfs_done = (c->lvl_lo == c->lvl_hi && c->hub_lo == c->hub_hi);
+        break;
+    case H_WL: {
+        c->ns_wl += dt;
+        int active = (int)c->wl_tail.w[3];
+        for (int b = 0; b < 3; ++b) c->wl_n[b] = (int)c->wl_tail.w[b];
+        c->head0.w[0] = c->head1.w[0] = c->head2.w[0] = 0;
+        if (c->iters < MF_ACTIVE_HIST) c->active_hist[c->iters] = active;
+        if (c->iters == 0) c->active_first = active;
+        c->active_total += active;
+        if (active == 0) {
+            c->status = MF_ST_CONVERGED;
+        } else if (c->iters >= P.max_iters || now - c->t_start > P.time_limit_ns) {
+            c->status = MF_ST_CAP;
+        } else {
+            c->iters += 1;
+        }
+        break;
+    }
+    case H_DIS:
+        c->ns_dis += dt;
+        c->head0.w[0] = c->head1.w[0] = c->head2.w[0] = 0;
+        break;
+    case H_FINAL:
+        break;
+    }
+    if (c->err.w[0] != 0) c->status = MF_ST_ERROR;
+}
+
+// Grid-wide barrier with a hook.  Returns false if this CTA gave up waiting
+// (the caller must return from the kernel at once).
+__device__ bool grid_sync(const MfParams &P, int hook, Sh &sh)
+{
+    MfCtrl *c = P.ctrl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        unsigned gen = ld_acquire(&c->bar_gen.w[0]);
+        __threadfence();
+        unsigned arrived = atomicAdd(&c->bar_count.w[0], 1u) + 1u;
+        if (arrived == gridDim.x) {
+            atomicExch(&c->bar_count.w[0], 0u);
+            run_hook(P, hook);
+            __threadfence();
+            st_release(&c->bar_gen.w[0], gen + 1u);
+        } else {
+            unsigned long long t0 = 0;
+            unsigned spins = 0;
+            while (ld_acquire(&c->bar_gen.w[0]) == gen) {
+                ++spins;
+                if (spins > 16) __nanosleep(spins > 4096 ? 200 : 20);
+                if ((spins & 31u) == 0) {
+                    unsigned long long now = gtimer();
+                    if (t0 == 0) {
+                        t0 = now;
+                    } else if (now - t0 > P.wait_limit_ns) {
+                        atomicCAS(&c->err.w[0], 0u, (unsigned)MF_E_WAIT);
+                        ok = 0;
+                        break;
+                    }
+                }
+            }
+        }
+        __threadfence();
+        sh.ok = ok;
+    }
+    __syncthreads();
+    return sh.ok != 0;
+}
+
+// Hook-written control fields are read through L2 (never a stale L1 line).
+__device__ __forceinline__ int vrd(const int *p) { return *(volatile const int *)p; }
+__device__ __forceinline__ int status_of(const MfParams &P) { return vrd(&P.ctrl->status); }
+
+// Flush per-CTA accumulators (excess of sink/source and counters).
+__device__ void flush_acc(const MfParams &P, Sh &sh, int phase)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        MfCtrl *c = P.ctrl;
+        if (sh.sink_e) atomic_add_ll(P.e + P.sink, sh.sink_e);
+        if (sh.src_e) atomic_add_ll(P.e + P.source, sh.src_e);
+        if (sh.pushes) atomic_add_ll(&c->pushes, sh.pushes);
+        if (sh.relabels) atomic_add_ll(&c->relabels, sh.relabels);
+        if (sh.steep) atomic_add_ll(&c->steep, sh.steep);
+        if (sh.slots || sh.verts || sh.cycles) {
+            if (phase == 0) {
+                atomic_add_ll(&c->slots_bfs, sh.slots);
+                atomic_add_ll(&c->verts_bfs, sh.verts);
+            } else if (phase == 1) {
+                atomic_add_ll(&c->slots_dis, sh.slots);
+                atomic_add_ll(&c->cycles_dis, sh.cycles);
+            } else if (phase == 2) {
+                atomic_add_ll(&c->slots_fix, sh.slots);
+                atomic_add_ll(&c->verts_fix, sh.verts);
+            } else if (phase == 3) {
+                atomic_add_ll(&c->verts_wl, sh.verts);
+            } else {
+                atomic_add_ll(&c->n_apply, sh.verts);
+            }
+        }
+        sh.sink_e = sh.src_e = 0;
+        sh.pushes = sh.relabels = sh.steep = sh.slots = sh.verts = sh.cycles = 0;
+    }
+    __syncthreads();
+}
+
+// Add d to the excess of z (sink and source go to the CTA accumulators).
+__device__ __forceinline__ void add_excess(const MfParams &P, Sh &sh, int z, long long d)
+{
+    if (z == P.sink)
+        atomicAdd((unsigned long long *)&sh.sink_e, (unsigned long long)d);
+    else if (z == P.source)
+        atomicAdd((unsigned long long *)&sh.src_e, (unsigned long long)d);
+    else
+        atomic_add_ll(P.e + z, d);
+}
+
+// ---------------------------------------------------------------------------
+// Static initialisation (Alg. 1 lines 1-14)
+// ---------------------------------------------------------------------------
+
+__device__ __noinline__ void phase_static_reset(const MfParams &P)
+{
+    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long gs = (long long)gridDim.x * blockDim.x;
+    for (long long x = gt; x < P.g.slot_cap; x += gs) P.cf[x] = __ldcg(P.g.cap + x);
+    for (long long v = gt; v < P.g.n; v += gs) {
+        P.e[v] = 0;
+        P.h[v] = 0;
+    }
+}
+
+__device__ __noinline__ void phase_saturate_source(const MfParams &P, Sh &sh)
+{
+    const int s = P.source;
+    const int r0 = P.g.off[s];
+    const int d = ldg_cg(P.g.deg + s);
+    long long acc = 0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d; j += gridDim.x * blockDim.x) {
+        int x = r0 + j;
+        int c = ldg_cg(P.g.cap + x);
+        int y = ldg_cg(P.g.rev + x);
+        P.cf[x] = 0;
+        P.cf[y] = ldg_cg(P.g.pcap + x);
+        int z = ldg_cg(P.g.dst + x);
+        if (z == P.sink)
+            atomicAdd((unsigned long long *)&sh.sink_e, (unsigned long long)(long long)c);
+        else
+            P.e[z] = c;
+        acc -= c;
+    }
+    if (acc) atomicAdd((unsigned long long *)&sh.src_e, (unsigned long long)acc);
+}
+
+// ---------------------------------------------------------------------------
+// Batch apply and repair (Alg. 5 lines 1-16)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ bool batch_entry(const MfParams &P, long long i, int &u, int &v, int &c)
+{
+    u = __ldcg(P.bu + i);
+    v = __ldcg(P.bv + i);
+    c = __ldcg(P.bc + i);
+    return u >= 0 && u < P.g.n && v >= 0 && v < P.g.n && c >= 0;
+}
+
+// Validate every entry; insert the directed key into the dedup table, where
+// the largest batch index (the last update of the pair) wins.
+__device__ __noinline__ void phase_apply_validate(const MfParams &P)
+{
+    MfCtrl *ctl = P.ctrl;
+    const int bits = P.sc.hash_bits;
+    const unsigned mask = (1u << bits) - 1u;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P.bcount;
+         i += (long long)gridDim.x * blockDim.x) {
+        int u, v, c;
+        if (!batch_entry(P, i, u, v, c)) {
+            atomicCAS(&ctl->err.w[0], 0u, (unsigned)MF_E_INVALID);
+            continue;
+        }
+        if (u == v) continue;
+        unsigned long long key = ((unsigned long long)(unsigned)u << 32) | (unsigned)v;
+        unsigned pos = hash_slot(key, bits);
+        for (unsigned probe = 0; probe <= mask; ++probe) {
+            unsigned long long prev = atomicCAS(P.sc.hkey + pos, kEmpty, key);
+            if (prev == kEmpty || prev == key) {
+                if (prev == kEmpty) {
+                    unsigned k = atomicAdd(&ctl->misc.w[3], 1u);
+                    P.sc.hused[k] = (int)pos;       // positions to clear afterwards
+                }
+                atomicMax(P.sc.hval + pos, (int)i);
+                break;
+            }
+            pos = (pos + 1u) & mask;
+        }
+    }
+}
+
+__device__ __forceinline__ int find_slot(const MfParams &P, int u, int v)
+{
+    const int r0 = P.g.off[u];
+    int lo = r0, hi = r0 + ldg_cg(P.g.bdeg + u);
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (ldg_cg(P.g.dst + mid) < v) lo = mid + 1;
+        else hi = mid;
+    }
+    if (lo < r0 + ldg_cg(P.g.bdeg + u) && ldg_cg(P.g.dst + lo) == v) return lo;
+    const int end = r0 + ldg_cg(P.g.deg + u);
+    for (int x = r0 + ldg_cg(P.g.bdeg + u); x < end; ++x)
+        if (ldg_cg(P.g.dst + x) == v) return x;
+    return -1;
+}
+
+__device__ __forceinline__ unsigned hash_find(const unsigned long long *keys, int bits, unsigned long long key)
+{
+    const unsigned mask = (1u << bits) - 1u;
+    unsigned pos = hash_slot(key, bits);
+    for (unsigned probe = 0; probe <= mask; ++probe) {
+        unsigned long long k = __ldcg(keys + pos);
+        if (k == key) return pos;
+        if (k == kEmpty) return 0xffffffffu;
+        pos = (pos + 1u) & mask;
+    }
+    return 0xffffffffu;
+}
+
+// Locate the slot of every surviving update; a missing pair is entered once
+// into the new-pair table and counted against both rows' spare slots.
+__device__ __noinline__ void phase_apply_locate(const MfParams &P)
+{
+    MfCtrl *ctl = P.ctrl;
+    const int bits = P.sc.hash_bits;
+    const unsigned mask = (1u << bits) - 1u;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P.bcount;
+         i += (long long)gridDim.x * blockDim.x) {
+        int u, v, c;
+        batch_entry(P, i, u, v, c);
+        if (u == v) {
+            P.sc.bslot[i] = -2;
+            continue;
+        }
+        unsigned long long key = ((unsigned long long)(unsigned)u << 32) | (unsigned)v;
+        unsigned pos = hash_find(P.sc.hkey, bits, key);
+        if (pos == 0xffffffffu || __ldcg(P.sc.hval + pos) != (int)i) {
+            P.sc.bslot[i] = -2;     // a later update of the same pair wins
+            continue;
+        }
+        int x = find_slot(P, u, v);
+        P.sc.bslot[i] = x;
+        if (x >= 0) continue;
+        int a = min(u, v), b = max(u, v);
+        unsigned long long pk = ((unsigned long long)(unsigned)a << 32) | (unsigned)b;
+        unsigned pp = hash_slot(pk, bits);
+        for (unsigned probe = 0; probe <= mask; ++probe) {
+            unsigned long long prev = atomicCAS(P.sc.pkey + pp, kEmpty, pk);
+            if (prev == kEmpty) {
+                unsigned k = atomicAdd(&ctl->misc.w[0], 1u);
+                P.sc.ins_list[k] = (int)pp;
+                atomicAdd(P.sc.ins_need + a, 1);
+                atomicAdd(P.sc.ins_need + b, 1);
+                break;
+            }
+            if (prev == pk) break;
+            pp = (pp + 1u) & mask;
+        }
+    }
+}
+
+__device__ __noinline__ void phase_apply_check(const MfParams &P)
+{
+    MfCtrl *ctl = P.ctrl;
+    const int nins = vrd(&ctl->ins_n);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nins; k += gridDim.x * blockDim.x) {
+        unsigned long long pk = __ldcg(P.sc.pkey + __ldcg(P.sc.ins_list + k));
+        int a = (int)(pk >> 32), b = (int)(pk & 0xffffffffu);
+        int room_a = P.g.off[a + 1] - P.g.off[a] - ldg_cg(P.g.deg + a);
+        int room_b = P.g.off[b + 1] - P.g.off[b] - ldg_cg(P.g.deg + b);
+        if (ldg_cg(P.sc.ins_need + a) > room_a || ldg_cg(P.sc.ins_need + b) > room_b) atomicExch(&ctl->misc.w[2], 1u);
+    }
+}
+
+__device__ __noinline__ void phase_apply_insert(const MfParams &P)
+{
+    MfCtrl *ctl = P.ctrl;
+    const int nins = vrd(&ctl->ins_n);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nins; k += gridDim.x * blockDim.x) {
+        int pp = __ldcg(P.sc.ins_list + k);
+        unsigned long long pk = __ldcg(P.sc.pkey + pp);
+        int a = (int)(pk >> 32), b = (int)(pk & 0xffffffffu);
+        int xa = P.g.off[a] + atomicAdd(P.g.deg + a, 1);
+        int xb = P.g.off[b] + atomicAdd(P.g.deg + b, 1);
+        P.g.dst[xa] = b;
+        P.g.dst[xb] = a;
+        P.g.rev[xa] = xb;
+        P.g.rev[xb] = xa;
+        P.g.cap[xa] = P.g.cap[xb] = 0;
+        P.g.pcap[xa] = P.g.pcap[xb] = 0;
+        P.cf[xa] = P.cf[xb] = 0;
+        P.sc.pval[pp] = xa;
+        P.sc.ins_need[a] = 0;
+        P.sc.ins_need[b] = 0;
+    }
+}
+
+// Alg. 5 line 2: c_f(u,v) += c' - c; cap(u,v) = c'.
+__device__ __noinline__ void phase_apply_delta(const MfParams &P, Sh &sh)
+{
+    MfCtrl *ctl = P.ctrl;
+    const int bits = P.sc.hash_bits;
+    long long applied = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P.bcount;
+         i += (long long)gridDim.x * blockDim.x) {
+        int x = __ldcg(P.sc.bslot + i);
+        if (x == -2) continue;
+        int u, v, c;
+        batch_entry(P, i, u, v, c);
+        if (x == -1) {
+            int a = min(u, v), b = max(u, v);
+            unsigned long long pk = ((unsigned long long)(unsigned)a << 32) | (unsigned)b;
+            unsigned pp = hash_find(P.sc.pkey, bits, pk);
+            if (pp == 0xffffffffu) {
+                atomicCAS(&ctl->err.w[0], 0u, (unsigned)MF_E_INTERNAL);
+                continue;
+            }
+            int xa = __ldcg(P.sc.pval + pp);
+            x = (u == a) ? xa : ldg_cg(P.g.rev + xa);
+            P.sc.bslot[i] = x;
+        }
+        int old = ldg_cg(P.g.cap + x);
+        int delta = c - old;
+        ++applied;
+        if (delta == 0) continue;
+        P.g.cap[x] = c;
+        atomicAdd(P.cf + x, delta);
+        atomicAdd(P.g.pcap + x, delta);
+        atomicAdd(P.g.pcap + ldg_cg(P.g.rev + x), delta);
+        if (delta < 0) {
+            unsigned k = atomicAdd(&ctl->misc.w[1], 1u);
+            P.sc.clamp[k] = (int)i;
+        }
+    }
+    if (applied) atomicAdd((unsigned long long *)&sh.verts, (unsigned long long)applied);
+}
+
+// Alg. 5 lines 4-9 on the slots whose capacity went down, with the excess
+// change of the flow sent back; then clear the hash tables for the next batch.
+__device__ __noinline__ void phase_apply_clamp(const MfParams &P, Sh &sh)
+{
+    MfCtrl *ctl = P.ctrl;
+    const int nt = vrd(&ctl->touch_n);
+    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long gs = (long long)gridDim.x * blockDim.x;
+    for (long long k = gt; k < nt; k += gs) {
+        long long i = __ldcg(P.sc.clamp + k);
+        int x = __ldcg(P.sc.bslot + i);
+        int cfx = ldg_cg(P.cf + x);
+        if (cfx < 0) {
+            int u = __ldcg(P.bu + i), v = __ldcg(P.bv + i);
+            int d = -cfx;
+            atomicAdd(P.cf + x, d);
+            atomicAdd(P.cf + ldg_cg(P.g.rev + x), -d);
+            add_excess(P, sh, u, (long long)d);
+            add_excess(P, sh, v, -(long long)d);
+        }
+    }
+}
+
+__device__ __noinline__ void phase_apply_cleanup(const MfParams &P)
+{
+    MfCtrl *ctl = P.ctrl;
+    const int nused = (int)*(volatile unsigned *)&ctl->misc.w[3];
+    const int nins = (int)*(volatile unsigned *)&ctl->misc.w[0];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nused; k += gridDim.x * blockDim.x) {
+        int pos = __ldcg(P.sc.hused + k);
+        P.sc.hkey[pos] = kEmpty;
+        P.sc.hval[pos] = -1;
+    }
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nins; k += gridDim.x * blockDim.x) {
+        int pp = __ldcg(P.sc.ins_list + k);
+        unsigned long long pk = __ldcg(P.sc.pkey + pp);
+        if (pk != kEmpty) {
+            int a = (int)(pk >> 32), b = (int)(pk & 0xffffffffu);
+            P.sc.ins_need[a] = 0;
+            P.sc.ins_need[b] = 0;
+        }
+        P.sc.pkey[pp] = kEmpty;
+        P.sc.pval[pp] = -1;
+    }
+}
+
+// Alg. 5 lines 11-16 (reading: push the remaining residual of every edge out
+// of the source and add it to the head's excess).
+__device__ __noinline__ void phase_resaturate(const MfParams &P, Sh &sh)
+{
+    const int s = P.source;
+    const int r0 = P.g.off[s];
+    const int d = ldg_cg(P.g.deg + s);
+    long long acc = 0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d; j += gridDim.x * blockDim.x) {
+        int x = r0 + j;
+        int c = ldg_cg(P.cf + x);
+        if (c > 0) {
+            P.cf[x] = 0;
+            atomicAdd(P.cf + ldg_cg(P.g.rev + x), c);
+            add_excess(P, sh, ldg_cg(P.g.dst + x), (long long)c);
+            acc -= c;
+        }
+    }
+    if (acc) atomicAdd((unsigned long long *)&sh.src_e, (unsigned long long)acc);
+}
+
+// ---------------------------------------------------------------------------
+// Backward BFS (Alg. 4 / Alg. 6)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void warp_append(unsigned *tail, int *arr, bool take, int val)
+{
+    const unsigned m = __ballot_sync(0xffffffffu, take);
+    if (m == 0) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(tail, (unsigned)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (take) arr[base + __popc(m & ((1u << lane) - 1u))] = val;
+}
+
+__device__ __noinline__ void phase_bfs_init(const MfParams &P, Sh &sh)
+{
+    MfCtrl *ctl = P.ctrl;
+    const int n = P.g.n;
+    const bool deficit_roots = (P.mode & MF_M_NO_DEFICIT_ROOTS) == 0;
+    const int lane = threadIdx.x & 31;
+    const long long gs = (long long)gridDim.x * blockDim.x;
+    for (long long base = (long long)blockIdx.x * blockDim.x + threadIdx.x - lane; base < n; base += gs) {
+        int v = (int)base + lane;
+        bool root = false;
+        if (v < n) {
+            root = (v == P.sink) || (deficit_roots && v != P.source && ldg_cg(P.e + v) < 0);
+            P.h[v] = root ? 0 : n;
+        }
+        bool hub = root && ldg_cg(P.g.deg + v) > MF_HUB_DEG;
+        if (hub) P.sc.bhub[atomicAdd(&ctl->hub_tail.w[0], 1u)] = v;
+        warp_append(&ctl->bfs_tail.w[0], P.sc.border, root && !hub, v);
+    }
+}
+
+// Visit slot x = (u, z) at level L: z gets height L+1 if it is unlabelled,
+// is not the source, and has a residual edge (z, u): c_f(z,u) = pcap - c_f(u,z).
+__device__ __forceinline__ void bfs_visit(const MfParams &P, bool valid, int x, int L)
+{
+    MfCtrl *ctl = P.ctrl;
+    const int n = P.g.n;
+    bool claim = false;
+    int z = 0;
+    if (valid) {
+        z = ldg_cg(P.g.dst + x);
+        if (z != P.source && ldg_cg(P.h + z) == n) {
+            int rc = ldg_cg(P.g.pcap + x) - ldg_cg(P.cf + x);
+            if (rc > 0) claim = atomicCAS(P.h + z, n, L + 1) == n;
+        }
+    }
+    bool hub = claim && ldg_cg(P.g.deg + z) > MF_HUB_DEG;
+    if (hub) P.sc.bhub[atomicAdd(&ctl->hub_tail.w[0], 1u)] = z;
+    warp_append(&ctl->bfs_tail.w[0], P.sc.border, claim && !hub, z);
+}
+
+__device__ __noinline__ void phase_bfs_level(const MfParams &P, Sh &sh)
+{
+    MfCtrl *ctl = P.ctrl;
+    const int L = vrd(&ctl->level);
+    const int lane = threadIdx.x & 31;
+    const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    long long slots = 0;
+    // hubs of this level: every warp of the grid takes a share of each hub's slots
+    const int hlo = vrd(&ctl->hub_lo), hhi = vrd(&ctl->hub_hi);
+    for (int j = hlo; j < hhi; ++j) {
+        int u = __ldcg(P.sc.bhub + j);
+        int r0 = P.g.off[u];
+        int d = ldg_cg(P.g.deg + u);
+        for (int base = gwarp * 32; base < d; base += nwarps * 32) {
+            int k = base + lane;
+            bfs_visit(P, k < d, r0 + k, L);
+        }
+        if (gwarp == 0 && lane == 0) slots += d;
+    }
+    // regular frontier: warps take 32 vertices at a time and expand their
+    // rows together (each lane finds the vertex that owns its slot)
+    const int lo = vrd(&ctl->lvl_lo), cnt = vrd(&ctl->lvl_hi) - lo;
+    for (;;) {
+        int b = 0;
+        if (lane == 0) b = (int)atomicAdd(&ctl->head0.w[0], 32u);
+        b = __shfl_sync(0xffffffffu, b, 0);
+        if (b >= cnt) break;
+        int idx = b + lane;
+        int u = idx < cnt ? __ldcg(P.sc.border + lo + idx) : -1;
+        int d = u >= 0 ? ldg_cg(P.g.deg + u) : 0;
+        int r0 = u >= 0 ? P.g.off[u] : 0;
+        int incl = d;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int excl = incl - d;
+        const int T = __shfl_sync(0xffffffffu, incl, 31);
+        if (lane == 0) slots += T;
+        for (int kb = 0; kb < T; kb += 32) {
+            const int k = kb + lane;
+            int owner = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                int cand = owner + step;
+                int ec = __shfl_sync(0xffffffffu, excl, cand & 31);
+                if (cand < 32 && ec <= k) owner = cand;
+            }
+            int rb = __shfl_sync(0xffffffffu, r0, owner);
+            int eb = __shfl_sync(0xffffffffu, excl, owner);
+            bfs_visit(P, k < T, rb + (k - eb), L);
+        }
+    }
+    if (slots) atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)slots);
+}
+
+// ---------------------------------------------------------------------------
+// Worklist of active vertices (Sec. 5.2.1 O1) with the termination count
+// ---------------------------------------------------------------------------
+
+__device__ __noinline__ void phase_worklist(const MfParams &P, Sh &sh)
+{
+    MfCtrl *ctl = P.ctrl;
+    const int n = P.g.n;
+    const int lane = threadIdx.x & 31;
+    const long long gs = (long long)gridDim.x * blockDim.x;
+    for (long long base = (long long)blockIdx.x * blockDim.x + threadIdx.x - lane; base < n; base += gs) {
+        int v = (int)base + lane;
+        bool cand = v < n && v != P.sink && v != P.source;
+        bool act = cand && ldg_cg(P.h + v) < n && ldg_cg(P.e + v) > 0;
+        bool listed = P.data_driven ? act : cand;
+        int bin = 0;
+        if (listed) {
+            int d = ldg_cg(P.g.deg + v);
+            bin = d <= MF_SMALL_DEG ? 0 : (d <= MF_HUB_DEG ? 1 : 2);
+        }
+        unsigned am = __ballot_sync(0xffffffffu, act);
+        if (lane == 0 && am) atomicAdd(&ctl->wl_tail.w[3], (unsigned)__popc(am));
+        warp_append(&ctl->wl_tail.w[0], P.sc.wl[0], listed && bin == 0, v);
+        warp_append(&ctl->wl_tail.w[1], P.sc.wl[1], listed && bin == 1, v);
+        warp_append(&ctl->wl_tail.w[2], P.sc.wl[2], listed && bin == 2, v);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Discharge (Alg. 2)
+// ---------------------------------------------------------------------------
+
+// Push d = min(e', c_f(u, v^)) along slot x of u (Alg. 2 lines 11-15).
+__device__ __forceinline__ void do_push(const MfParams &P, Sh &sh, int u, int x, long long eu)
+{
+    int c = ldg_cg(P.cf + x);
+    long long d = eu < (long long)c ? eu : (long long)c;
+    if (d <= 0) return;
+    atomicSub(P.cf + x, (int)d);
+    atomicAdd(P.cf + ldg_cg(P.g.rev + x), (int)d);
+    atomic_add_ll(P.e + u, -d);
+    add_excess(P, sh, ldg_cg(P.g.dst + x), d);
+    atomicAdd((unsigned long long *)&sh.pushes, 1ull);
+}
+
+// One thread per vertex (rows of at most MF_SMALL_DEG slots).
+__device__ void discharge_thread(const MfParams &P, Sh &sh, int u)
+{
+    const int n = P.g.n;
+    const int r0 = P.g.off[u];
+    const int d = ldg_cg(P.g.deg + u);
+    int hu = ldg_cg(P.h + u);
+    long long cyc_done = 0;
+    for (int cyc = 0; cyc < P.kernel_cycles; ++cyc) {
+        long long eu = ldg_cg(P.e + u);
+        if (!(hu < n && eu > 0)) break;
+        ++cyc_done;
+        int best_h = 0x7fffffff, best_x = -1;
+        for (int j = 0; j < d; ++j) {
+            int x = r0 + j;
+            if (ldg_cg(P.cf + x) > 0) {
+                int hz = ldg_cg(P.h + ldg_cg(P.g.dst + x));
+                if (hz < best_h) {
+                    best_h = hz;
+                    best_x = x;
+                }
+            }
+        }
+        if (best_x >= 0 && hu > best_h) {
+            do_push(P, sh, u, best_x, eu);
+        } else {
+            hu = (best_x < 0 || best_h >= n - 1) ? n : best_h + 1;
+            P.h[u] = hu;
+            atomicAdd((unsigned long long *)&sh.relabels, 1ull);
+        }
+    }
+    if (cyc_done) {
+        atomicAdd((unsigned long long *)&sh.cycles, (unsigned long long)cyc_done);
+        atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)(cyc_done * d));
+    }
+}
+
+// One warp per vertex.
+__device__ void discharge_warp(const MfParams &P, Sh &sh, int u)
+{
+    const int n = P.g.n;
+    const int lane = threadIdx.x & 31;
+    const int r0 = P.g.off[u];
+    const int d = ldg_cg(P.g.deg + u);
+    int hu = ldg_cg(P.h + u);
+    long long cyc_done = 0;
+    for (int cyc = 0; cyc < P.kernel_cycles; ++cyc) {
+        long long eu = ldg_cg(P.e + u);
+        if (!(hu < n && eu > 0)) break;
+        ++cyc_done;
+        unsigned long long best = kEmpty;
+        for (int j = lane; j < d; j += 32) {
+            int x = r0 + j;
+            if (ldg_cg(P.cf + x) > 0) {
+                int hz = ldg_cg(P.h + ldg_cg(P.g.dst + x));
+                unsigned long long key = ((unsigned long long)(unsigned)hz << 32) | (unsigned)j;
+                best = key < best ? key : best;
+            }
+        }
+        best = warp_min_u64(best);
+        int best_h = best == kEmpty ? 0x7fffffff : (int)(best >> 32);
+        if (best != kEmpty && hu > best_h) {
+            if (lane == 0) do_push(P, sh, u, r0 + (int)(best & 0xffffffffu), eu);
+        } else {
+            hu = (best == kEmpty || best_h >= n - 1) ? n : best_h + 1;
+            if (lane == 0) {
+                P.h[u] = hu;
+                atomicAdd((unsigned long long *)&sh.relabels, 1ull);
+            }
+        }
+        __syncwarp();
+    }
+    if (lane == 0 && cyc_done) {
+        atomicAdd((unsigned long long *)&sh.cycles, (unsigned long long)cyc_done);
+        atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)(cyc_done * d));
+    }
+}
+
+// One CTA per vertex (hubs).  All threads of the CTA call this together.
+__device__ void discharge_cta(const MfParams &P, Sh &sh, int u)
+{
+    const int n = P.g.n;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int r0 = P.g.off[u];
+    const int d = ldg_cg(P.g.deg + u);
+    for (int cyc = 0; cyc < P.kernel_cycles; ++cyc) {
+        if (threadIdx.x == 0) {
+            sh.bcast_e = ldg_cg(P.e + u);
+            sh.bcast_h = ldg_cg(P.h + u);
+        }
+        __syncthreads();
+        long long eu = sh.bcast_e;
+        int hu = sh.bcast_h;
+        if (!(hu < n && eu > 0)) {
+            __syncthreads();
+            break;
+        }
+        unsigned long long best = kEmpty;
+        for (int j = threadIdx.x; j < d; j += blockDim.x) {
+            int x = r0 + j;
+            if (ldg_cg(P.cf + x) > 0) {
+                int hz = ldg_cg(P.h + ldg_cg(P.g.dst + x));
+                unsigned long long key = ((unsigned long long)(unsigned)hz << 32) | (unsigned)j;
+                best = key < best ? key : best;
+            }
+        }
+        best = warp_min_u64(best);
+        if (lane == 0) sh.red[wid] = best;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long b = kEmpty;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = sh.red[w] < b ? sh.red[w] : b;
+            int best_h = b == kEmpty ? 0x7fffffff : (int)(b >> 32);
+            if (b != kEmpty && hu > best_h) {
+                do_push(P, sh, u, r0 + (int)(b & 0xffffffffu), eu);
+            } else {
+                P.h[u] = (b == kEmpty || best_h >= n - 1) ? n : best_h + 1;
+                atomicAdd((unsigned long long *)&sh.relabels, 1ull);
+            }
+            atomicAdd((unsigned long long *)&sh.cycles, 1ull);
+            atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)d);
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __noinline__ void phase_discharge(const MfParams &P, Sh &sh)
+{
+    MfCtrl *ctl = P.ctrl;
+    const int lane = threadIdx.x & 31;
+    // hubs: one CTA each
+    const int nh = vrd(&ctl->wl_n[2]);
+    for (;;) {
+        if (threadIdx.x == 0) sh.bcast_i = (int)atomicAdd(&ctl->head2.w[0], 1u);
+        __syncthreads();
+        int i = sh.bcast_i;
+        __syncthreads();
+        if (i >= nh) break;
+        discharge_cta(P, sh, __ldcg(P.sc.wl[2] + i));
+    }
+    // mid-degree rows: one warp each
+    const int nm = vrd(&ctl->wl_n[1]);
+    for (;;) {
+        int i = 0;
+        if (lane == 0) i = (int)atomicAdd(&ctl->head1.w[0], 1u);
+        i = __shfl_sync(0xffffffffu, i, 0);
+        if (i >= nm) break;
+        discharge_warp(P, sh, __ldcg(P.sc.wl[1] + i));
+    }
+    // small rows: one thread each, 32 per grab
+    const int ns = vrd(&ctl->wl_n[0]);
+    for (;;) {
+        int b = 0;
+        if (lane == 0) b = (int)atomicAdd(&ctl->head0.w[0], 32u);
+        b = __shfl_sync(0xffffffffu, b, 0);
+        if (b >= ns) break;
+        if (b + lane < ns) discharge_thread(P, sh, __ldcg(P.sc.wl[0] + b + lane));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Remove invalid edges (Alg. 3)
+// ---------------------------------------------------------------------------
+
+// Push the whole residual of every steep slot of u (h(u) > h(v) + 1).
+__device__ __forceinline__ long long fix_slot(const MfParams &P, Sh &sh, int hu, int x)
+{
+    int c = ldg_cg(P.cf + x);
+    if (c <= 0) return 0;
+    int z = ldg_cg(P.g.dst + x);
+    if (!(hu > ldg_cg(P.h + z) + 1)) return 0;
+    int old = atomicExch(P.cf + x, 0);
+    if (old <= 0) return 0;
+    atomicAdd(P.cf + ldg_cg(P.g.rev + x), old);
+    add_excess(P, sh, z, (long long)old);
+    atomicAdd((unsigned long long *)&sh.steep, 1ull);
+    return old;
+}
+
+__device__ __noinline__ void phase_fix(const MfParams &P, Sh &sh)
+{
+    MfCtrl *ctl = P.ctrl;
+    const int lane = threadIdx.x & 31;
+    const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    long long slots = 0, verts = 0;
+    // hubs: the warps of the grid share each hub's row
+    const int nh = vrd(&ctl->wl_n[2]);
+    for (int i = 0; i < nh; ++i) {
+        int u = __ldcg(P.sc.wl[2] + i);
+        int hu = ldg_cg(P.h + u);
+        int r0 = P.g.off[u], d = ldg_cg(P.g.deg + u);
+        long long out = 0;
+        for (int j = gwarp * 32 + lane; j < d; j += nwarps * 32) out += fix_slot(P, sh, hu, r0 + j);
+        if (out) atomic_add_ll(P.e + u, -out);
+        if (gwarp == 0 && lane == 0) { slots += d; ++verts; }
+    }
+    // mid rows: warp per vertex
+    const int nm = vrd(&ctl->wl_n[1]);
+    for (;;) {
+        int i = 0;
+        if (lane == 0) i = (int)atomicAdd(&ctl->head1.w[0], 1u);
+        i = __shfl_sync(0xffffffffu, i, 0);
+        if (i >= nm) break;
+        int u = __ldcg(P.sc.wl[1] + i);
+        int hu = ldg_cg(P.h + u);
+        int r0 = P.g.off[u], d = ldg_cg(P.g.deg + u);
+        long long out = 0;
+        for (int j = lane; j < d; j += 32) out += fix_slot(P, sh, hu, r0 + j);
+        out = warp_sum_ll(out);
+        if (lane == 0) {
+            if (out) atomic_add_ll(P.e + u, -out);
+            slots += d;
+            ++verts;
+        }
+    }
+    // small rows: thread per vertex
+    const int ns = vrd(&ctl->wl_n[0]);
+    for (;;) {
+        int b = 0;
+        if (lane == 0) b = (int)atomicAdd(&ctl->head0.w[0], 32u);
+        b = __shfl_sync(0xffffffffu, b, 0);
+        if (b >= ns) break;
+        if (b + lane < ns) {
+            int u = __ldcg(P.sc.wl[0] + b + lane);
+            int hu = ldg_cg(P.h + u);
+            int r0 = P.g.off[u], d = ldg_cg(P.g.deg + u);
+            long long out = 0;
+            for (int j = 0; j < d; ++j) out += fix_slot(P, sh, hu, r0 + j);
+            if (out) atomic_add_ll(P.e + u, -out);
+            slots += d;
+            ++verts;
+        }
+    }
+    if (slots) atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)slots);
+    if (verts) atomicAdd((unsigned long long *)&sh.verts, (unsigned long long)verts);
+}
+
+// ---------------------------------------------------------------------------
+// Value (Alg. 5 last lines, reading R3)
+// ---------------------------------------------------------------------------
+
+__device__ __noinline__ void phase_value(const MfParams &P)
+{
+    const int n = P.g.n;
+    long long acc = 0;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x)
+        if ((int)v != P.source && ldg_cg(P.h + v) < n) acc += ldg_cg(P.e + v);
+    acc = warp_sum_ll(acc);
+    if ((threadIdx.x & 31) == 0 && acc) atomic_add_ll(&P.ctrl->value, acc);
+}
+
+__global__ void __launch_bounds__(MF_BLOCK, 1) mf_solve_kernel(MfParams P)
+{
+    __shared__ Sh sh;
+    if (threadIdx.x == 0) {
+        sh.sink_e = sh.src_e = 0;
+        sh.pushes = sh.relabels = sh.steep = sh.slots = sh.verts = sh.cycles = 0;
+    }
+    if (!grid_sync(P, H_START, sh)) return;
+
+    if (P.mode & MF_M_STATIC_INIT) {
+        phase_static_reset(P);
+        if (!grid_sync(P, H_NONE, sh)) return;
+        phase_saturate_source(P, sh);
+        flush_acc(P, sh, 4);
+        if (!grid_sync(P, H_NONE, sh)) return;
+    }
+    if (P.mode & MF_M_APPLY) {
+        phase_apply_validate(P);
+        if (!grid_sync(P, H_APPLY_VALID, sh)) return;
+        if (status_of(P) != MF_ST_RUNNING) {
+            phase_apply_cleanup(P);
+            grid_sync(P, H_FINAL, sh);
+            return;
+        }
+        phase_apply_locate(P);
+        if (!grid_sync(P, H_APPLY_LOCATED, sh)) return;
+        phase_apply_check(P);
+        if (!grid_sync(P, H_APPLY_CHECKED, sh)) return;
+        if (status_of(P) != MF_ST_RUNNING) {
+            phase_apply_cleanup(P);
+            grid_sync(P, H_FINAL, sh);
+            return;
+        }
+        phase_apply_insert(P);
+        if (!grid_sync(P, H_NONE, sh)) return;
+        phase_apply_delta(P, sh);
+        flush_acc(P, sh, 4);
+        if (!grid_sync(P, H_APPLY_DELTA, sh)) return;
+        phase_apply_clamp(P, sh);
+        phase_apply_cleanup(P);
+        flush_acc(P, sh, 4);
+        if (!grid_sync(P, H_NONE, sh)) return;
+        if (!(P.mode & MF_M_SKIP_SOURCE_SAT)) {
+            phase_resaturate(P, sh);
+            flush_acc(P, sh, 4);
+            if (!grid_sync(P, H_NONE, sh)) return;
+        }
+        if (status_of(P) != MF_ST_RUNNING) return;
+    }
+    if (!(P.mode & (MF_M_SOLVE | MF_M_BFS_ONLY))) return;
+
+    if (!grid_sync(P, H_ITER, sh)) return;
+    for (;;) {
+        // backward BFS
+        phase_bfs_init(P, sh);
+        if (!grid_sync(P, H_BFS_START, sh)) return;
+        while (!vrd(&P.ctrl->bfs_done)) {
+            phase_bfs_level(P, sh);
+            flush_acc(P, sh, 0);
+            if (!grid_sync(P, H_BFS_NEXT, sh)) return;
+        }
+        if (P.mode & MF_M_BFS_ONLY) return;
+        // worklist and termination test
+        phase_worklist(P, sh);
+        if (!grid_sync(P, H_WL, sh)) return;
+        if (status_of(P) != MF_ST_RUNNING) break;
+        // discharge and remove-invalid-edges
+        phase_discharge(P, sh);
+        flush_acc(P, sh, 1);
+        if (!grid_sync(P, H_DIS, sh)) return;
+        if (P.fix_steep) {
+            phase_fix(P, sh);
+            flush_acc(P, sh, 2);
+        }
+        if (!grid_sync(P, H_ITER, sh)) return;
+    }
+    if (status_of(P) == MF_ST_ERROR) return;
+    phase_value(P);
+    grid_sync(P, H_FINAL, sh);
+}
+
+// ---------------------------------------------------------------------------
+// Auxiliary kernels (state load/readback, checks, queries)
+// ---------------------------------------------------------------------------
+
+__global__ void k_cf_reset(MfParams P)
+{
+    for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < P.g.slot_cap;
+         x += (long long)gridDim.x * blockDim.x)
+        P.cf[x] = P.g.cap[x];
+}
+
+struct FlowItems {
+    long long count;
+    const int32_t *u, *v, *f;
+    int apply;
+};
+
+__global__ void k_set_flow(MfParams P, FlowItems F, long long *bad)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < F.count;
+         i += (long long)gridDim.x * blockDim.x) {
+        int u = F.u[i], v = F.v[i], f = F.f[i];
+        if (u < 0 || u >= P.g.n || v < 0 || v >= P.g.n || u == v) {
+            atomicAdd((unsigned long long *)bad, 1ull);
+            continue;
+        }
+        int x = find_slot(P, u, v);
+        if (x < 0 || f < 0 || f > P.g.cap[x]) {
+            atomicAdd((unsigned long long *)bad, 1ull);
+            continue;
+        }
+        if (F.apply && f > 0) {
+            atomicSub(P.cf + x, f);
+            atomicAdd(P.cf + P.g.rev[x], f);
+        }
+    }
+}
+
+// K8: e(v) = sum over v's slots of c_f - c.
+__global__ void k_excess(MfParams P, long long *mismatch)
+{
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < P.g.n;
+         v += (long long)gridDim.x * blockDim.x) {
+        int r0 = P.g.off[v], d = P.g.deg[v];
+        long long s = 0;
+        for (int j = 0; j < d; ++j) s += (long long)P.cf[r0 + j] - (long long)P.g.cap[r0 + j];
+        if (mismatch) {
+            if (s != P.e[v]) atomicAdd((unsigned long long *)mismatch, 1ull);
+        } else {
+            P.e[v] = s;
+        }
+    }
+}
+
+__global__ void k_check(MfParams P, long long *out)
+{
+    const int n = P.g.n;
+    long long pair_bad = 0, cross = 0, act = 0, cut = 0, val = 0;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+        int r0 = P.g.off[v], d = P.g.deg[v];
+        int hv = P.h[v];
+        for (int j = 0; j < d; ++j) {
+            int x = r0 + j, y = P.g.rev[x];
+            long long lhs = (long long)P.cf[x] + P.cf[y];
+            long long rhs = (long long)P.g.cap[x] + P.g.cap[y];
+            if (P.cf[x] < 0 || lhs != rhs || P.g.pcap[x] != rhs || P.g.dst[y] != (int)v || P.g.rev[y] != x) ++pair_bad;
+            if (hv == n && P.h[P.g.dst[x]] < n) {
+                cut += P.g.cap[x];
+                if (P.cf[x] > 0) ++cross;
+            }
+        }
+        if ((int)v != P.sink && (int)v != P.source && P.e[v] > 0 && hv < n) ++act;
+        if ((int)v != P.source && hv < n) val += P.e[v];
+    }
+    atomicAdd((unsigned long long *)&out[0], (unsigned long long)pair_bad);
+    atomicAdd((unsigned long long *)&out[2], (unsigned long long)cross);
+    atomicAdd((unsigned long long *)&out[3], (unsigned long long)act);
+    atomicAdd((unsigned long long *)&out[4], (unsigned long long)cut);
+    atomicAdd((unsigned long long *)&out[5], (unsigned long long)val);
+}
+
+__global__ void k_side(MfParams P, uint8_t *side)
+{
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < P.g.n;
+         v += (long long)gridDim.x * blockDim.x)
+        side[v] = (P.h[v] == P.g.n) ? 1 : 0;
+}
+
+__global__ void k_cut(MfParams P, long long *out)
+{
+    const int n = P.g.n;
+    const int lane = threadIdx.x & 31;
+    long long cut = 0;
+    for (long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n;
+         w += ((long long)gridDim.x * blockDim.x) >> 5) {
+        if (P.h[w] != n) continue;
+        int r0 = P.g.off[w], d = P.g.deg[w];
+        for (int j = lane; j < d; j += 32)
+            if (P.h[P.g.dst[r0 + j]] < n) cut += P.g.cap[r0 + j];
+    }
+    cut = warp_sum_ll(cut);
+    if (lane == 0 && cut) atomicAdd((unsigned long long *)out, (unsigned long long)cut);
+}
+
+__global__ void k_reverse_cf(MfParams P, const int32_t *in, int32_t *out)
+{
+    for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < P.g.slot_cap;
+         x += (long long)gridDim.x * blockDim.x)
+        out[x] = in[P.g.rev[x]];
+}
+
+__global__ void k_rowid(MfParams P, int32_t *rowid)
+{
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < P.g.n;
+         v += (long long)gridDim.x * blockDim.x) {
+        int r0 = P.g.off[v], d = P.g.deg[v], end = P.g.off[v + 1];
+        for (int x = r0; x < end; ++x) rowid[x] = x < r0 + d ? (int)v : -1;
+    }
+}
+
+__global__ void k_negate(long long *e, int n)
+{
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x)
+        e[v] = -e[v];
+}
+
+inline int cuda_rc(cudaError_t e) { return e == cudaSuccess ? MAXFLOW_OK : MAXFLOW_ERR_CUDA; }
+
+}  // namespace
+
+int mf_max_coresident_blocks(int device, int *per_sm, int *num_sms)
+{
+    int k = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, mf_solve_kernel, MF_BLOCK, 0) != cudaSuccess)
+        return MAXFLOW_ERR_CUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return MAXFLOW_ERR_CUDA;
+    *per_sm = k;
+    *num_sms = sms;
+    return k > 0 ? MAXFLOW_OK : MAXFLOW_ERR_CUDA;
+}
+
+int mf_launch(const MfParams &p, int grid, void *stream)
+{
+    MfParams q = p;
+    void *args[] = {&q};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)mf_solve_kernel, dim3(grid), dim3(MF_BLOCK), args, 0,
+                                                (cudaStream_t)stream);
+    return cuda_rc(e);
+}
+
+int mf_launch_aux(int which, const MfParams &p, void *stream, long long *dev_out, const void *extra)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    const int B = 256;
+    long long nv = p.g.n, ns = p.g.slot_cap;
+    int gv = (int)((nv + B - 1) / B);
+    int gs = (int)((ns + B - 1) / B);
+    if (gv > 65535) gv = 65535;
+    if (gs > 65535) gs = 65535;
+    if (gv < 1) gv = 1;
+    if (gs < 1) gs = 1;
+    switch (which) {
+    case MF_AUX_SET_CF_RESET:
+        k_cf_reset<<<gs, B, 0, st>>>(p);
+        break;
+    case MF_AUX_SET_FLOW: {
+        const FlowItems *f = (const FlowItems *)extra;
+        int g = (int)((f->count + B - 1) / B);
+        if (g < 1) g = 1;
+        if (g > 65535) g = 65535;
+        k_set_flow<<<g, B, 0, st>>>(p, *f, dev_out);
+        break;
+    }
+    case MF_AUX_EXCESS:
+        k_excess<<<gv, B, 0, st>>>(p, dev_out);
+        break;
+    case MF_AUX_CHECK:
+        k_check<<<gv, B, 0, st>>>(p, dev_out);
+        if (cudaGetLastError() != cudaSuccess) return MAXFLOW_ERR_CUDA;
+        k_excess<<<gv, B, 0, st>>>(p, dev_out + 1);
+        break;
+    case MF_AUX_SIDE:
+        k_side<<<gv, B, 0, st>>>(p, (uint8_t *)extra);
+        break;
+    case MF_AUX_CUT: {
+        int g = (int)((nv * 32 + B - 1) / B);
+        if (g > 65535) g = 65535;
+        if (g < 1) g = 1;
+        k_cut<<<g, B, 0, st>>>(p, dev_out);
+        break;
+    }
+    case MF_AUX_REVERSE_CF: {
+        const int32_t *const *io = (const int32_t *const *)extra;
+        k_reverse_cf<<<gs, B, 0, st>>>(p, io[0], (int32_t *)io[1]);
+        break;
+    }
+    case MF_AUX_DUMP:
+        k_rowid<<<gv, B, 0, st>>>(p, (int32_t *)extra);
+        break;
+    case MF_AUX_NEGATE_E:
+        k_negate<<<gv, B, 0, st>>>(p.e, p.g.n);
+        break;
+    default:
+        return MAXFLOW_ERR_INVALID;
+    }
+    return cuda_rc(cudaGetLastError());
+}
+
+int mf_set_flow_items(const MfParams &p, void *stream, long long *dev_bad, long long count,
+                                  const int32_t *du, const int32_t *dv, const int32_t *df, int apply)
+{
+    FlowItems f{count, du, dv, df, apply};
+    return mf_launch_aux(MF_AUX_SET_FLOW, p, stream, dev_bad, &f);
+}

@@ -1,0 +1,376 @@
+"""ctypes binding of the C ABI in include/maxflow.h.
+
+Argument marshalling only: every step of the solver runs in the CUDA library
+(paper_2511_01235_gb300/_build/libmaxflow_gb300.so).  If that library is
+missing, importing the solver raises at once -- there is no CPU fallback.
+
+The module-level functions carry the C names (maxflow_init, maxflow_update,
+maxflow_query, ...); `Solver` is a small object wrapper over them.  Device
+memory comes from PyTorch's caching allocator through the allocator
+callbacks of maxflow_opts, and work is issued on a torch CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build_ext
+
+OK = 0
+ERR_INVALID = 1
+ERR_OOM = 2
+ERR_CUDA = 3
+ERR_NOT_CONVERGED = 4
+ERR_STATE = 5
+ERR_INTERNAL = 6
+ERR_TOO_LARGE = 7
+
+
+class MaxflowError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} (status {code})")
+
+
+class Graph(C.Structure):
+    _fields_ = [("n", C.c_int32), ("m", C.c_int64), ("src", C.c_void_p), ("dst", C.c_void_p),
+                ("cap", C.c_void_p)]
+
+
+class Batch(C.Structure):
+    _fields_ = [("count", C.c_int64), ("u", C.c_void_p), ("v", C.c_void_p), ("new_cap", C.c_void_p),
+                ("on_device", C.c_int32)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class Opts(C.Structure):
+    _fields_ = [("kernel_cycles", C.c_int32), ("data_driven", C.c_int32), ("fix_steep", C.c_int32),
+                ("grid_blocks", C.c_int32), ("max_iters", C.c_int64), ("time_limit_s", C.c_double),
+                ("wait_limit_s", C.c_double), ("slack_factor", C.c_float), ("slack_min", C.c_int32),
+                ("device", C.c_int32), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("alloc_user", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n", C.c_int64), ("m_edges", C.c_int64), ("slots", C.c_int64), ("slot_capacity", C.c_int64),
+                ("kernel_cycles", C.c_int32), ("grid_blocks", C.c_int32), ("block_threads", C.c_int32),
+                ("blocks_per_sm", C.c_int32),
+                ("solves", C.c_int64), ("updates", C.c_int64), ("rebuilds", C.c_int64),
+                ("iterations", C.c_int64), ("bfs_levels", C.c_int64), ("pushes", C.c_int64),
+                ("relabels", C.c_int64), ("steep_fixes", C.c_int64),
+                ("active_first", C.c_int64), ("active_total", C.c_int64),
+                ("bytes_bfs", C.c_int64), ("bytes_discharge", C.c_int64), ("bytes_fix", C.c_int64),
+                ("bytes_worklist", C.c_int64), ("bytes_apply", C.c_int64),
+                ("ms_last", C.c_double), ("ms_bfs", C.c_double), ("ms_discharge", C.c_double),
+                ("ms_fix", C.c_double), ("ms_worklist", C.c_double), ("ms_apply", C.c_double),
+                ("value", C.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTS = ["maxflow_default_opts", "maxflow_init", "maxflow_update", "maxflow_query", "maxflow_resolve_static",
+           "maxflow_get_flow", "maxflow_stats", "maxflow_destroy", "maxflow_strerror", "maxflow_set_flow",
+           "maxflow_apply", "maxflow_global_relabel", "maxflow_resolve", "maxflow_get_residual",
+           "maxflow_get_vertex_state", "maxflow_check"]
+
+_lib = None
+
+
+def lib_path() -> str:
+    return build_ext.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = build_ext.LIB
+    if not os.path.exists(path):
+        if build_if_missing:
+            build_ext.build()
+        else:
+            raise ImportError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    L = C.CDLL(path)
+    vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+    P = C.POINTER
+    L.maxflow_default_opts.argtypes = [P(Opts)]
+    L.maxflow_default_opts.restype = None
+    L.maxflow_init.argtypes = [P(vp), P(Graph), i32, i32, P(Opts)]
+    L.maxflow_update.argtypes = [vp, P(Batch)]
+    L.maxflow_apply.argtypes = [vp, P(Batch)]
+    L.maxflow_query.argtypes = [vp, P(i64), vp, P(i64)]
+    L.maxflow_resolve_static.argtypes = [vp]
+    L.maxflow_resolve.argtypes = [vp]
+    L.maxflow_global_relabel.argtypes = [vp]
+    L.maxflow_get_flow.argtypes = [vp, P(i64), vp, vp, vp, vp]
+    L.maxflow_get_residual.argtypes = [vp, P(i64), vp, vp, vp, vp]
+    L.maxflow_get_vertex_state.argtypes = [vp, vp, vp]
+    L.maxflow_set_flow.argtypes = [vp, i64, vp, vp, vp]
+    L.maxflow_stats.argtypes = [vp, P(Stats)]
+    L.maxflow_check.argtypes = [vp, vp]
+    L.maxflow_destroy.argtypes = [vp]
+    L.maxflow_destroy.restype = None
+    L.maxflow_strerror.argtypes = [C.c_int]
+    L.maxflow_strerror.restype = C.c_char_p
+    for name in EXPORTS:
+        if name not in ("maxflow_default_opts", "maxflow_destroy", "maxflow_strerror"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def strerror(code: int) -> str:
+    try:
+        return load().maxflow_strerror(int(code)).decode()
+    except ImportError:
+        return f"status {code}"
+
+
+def _check(rc: int, where: str):
+    if rc != OK:
+        raise MaxflowError(rc, where)
+
+
+def _i32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+
+
+def _p(a):
+    return C.c_void_p(a.ctypes.data) if a is not None and a.size else None
+
+
+# ---- torch plumbing -----------------------------------------------------------
+
+class _TorchAllocator:
+    """Device memory from torch's caching allocator, handed to the library through callbacks."""
+
+    def __init__(self, device: int):
+        import torch
+        self.torch = torch
+        self.device = device
+
+        def _alloc(nbytes, user, stream):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(nbytes), device=self.device, stream=int(stream or 0)))
+            except Exception:
+                return None
+
+        def _free(ptr, nbytes, user, stream):
+            try:
+                torch.cuda.caching_allocator_delete(int(ptr))
+            except Exception:
+                pass
+
+        self.alloc = ALLOC_FN(_alloc)
+        self.free = FREE_FN(_free)
+
+
+# ---- the C names ---------------------------------------------------------------
+
+def maxflow_default_opts() -> Opts:
+    o = Opts()
+    load().maxflow_default_opts(C.byref(o))
+    return o
+
+
+def maxflow_init(n, src, dst, cap, s, t, opts: Opts | None = None):
+    src, dst, cap = _i32(src), _i32(dst), _i32(cap)
+    g = Graph(int(n), int(src.size), _p(src), _p(dst), _p(cap))
+    h = C.c_void_p()
+    rc = load().maxflow_init(C.byref(h), C.byref(g), int(s), int(t), C.byref(opts) if opts is not None else None)
+    _check(rc, "maxflow_init")
+    return h
+
+
+def _batch(u, v, c):
+    """A Batch from numpy (host) or torch CUDA tensors (device); returns (batch, keepalive)."""
+    if hasattr(u, "is_cuda") and u.is_cuda:
+        import torch
+        u = u.to(torch.int32).contiguous()
+        v = v.to(torch.int32).contiguous()
+        c = c.to(torch.int32).contiguous()
+        return Batch(int(u.numel()), u.data_ptr(), v.data_ptr(), c.data_ptr(), 1), (u, v, c)
+    if hasattr(u, "numpy"):
+        u, v, c = u.numpy(), v.numpy(), c.numpy()
+    u, v, c = _i32(u), _i32(v), _i32(c)
+    return Batch(int(u.size), _p(u), _p(v), _p(c), 0), (u, v, c)
+
+
+def maxflow_update(h, u, v, c):
+    b, keep = _batch(u, v, c)
+    _check(load().maxflow_update(h, C.byref(b)), "maxflow_update")
+
+
+def maxflow_apply(h, u, v, c):
+    b, keep = _batch(u, v, c)
+    _check(load().maxflow_apply(h, C.byref(b)), "maxflow_apply")
+
+
+def maxflow_query(h, n: int, side: bool = False, cut: bool = False):
+    val = C.c_int64()
+    cc = C.c_int64()
+    sd = np.zeros(n, np.uint8) if side else None
+    rc = load().maxflow_query(h, C.byref(val), _p(sd) if side else None, C.byref(cc) if cut else None)
+    _check(rc, "maxflow_query")
+    return int(val.value), (sd.astype(bool) if side else None), (int(cc.value) if cut else None)
+
+
+def maxflow_resolve_static(h):
+    _check(load().maxflow_resolve_static(h), "maxflow_resolve_static")
+
+
+def maxflow_resolve(h):
+    _check(load().maxflow_resolve(h), "maxflow_resolve")
+
+
+def maxflow_global_relabel(h):
+    _check(load().maxflow_global_relabel(h), "maxflow_global_relabel")
+
+
+def maxflow_get_flow(h):
+    L = load()
+    cnt = C.c_int64(0)
+    _check(L.maxflow_get_flow(h, C.byref(cnt), None, None, None, None), "maxflow_get_flow")
+    k = int(cnt.value)
+    u, v, cap, f = (np.zeros(max(k, 1), np.int32) for _ in range(4))
+    cnt = C.c_int64(k)
+    _check(L.maxflow_get_flow(h, C.byref(cnt), _p(u), _p(v), _p(cap), _p(f)), "maxflow_get_flow")
+    k = int(cnt.value)
+    return u[:k], v[:k], cap[:k], f[:k]
+
+
+def maxflow_get_residual(h):
+    L = load()
+    cnt = C.c_int64(0)
+    _check(L.maxflow_get_residual(h, C.byref(cnt), None, None, None, None), "maxflow_get_residual")
+    k = int(cnt.value)
+    u, v, cap, cf = (np.zeros(max(k, 1), np.int32) for _ in range(4))
+    cnt = C.c_int64(k)
+    _check(L.maxflow_get_residual(h, C.byref(cnt), _p(u), _p(v), _p(cap), _p(cf)), "maxflow_get_residual")
+    k = int(cnt.value)
+    return u[:k], v[:k], cap[:k], cf[:k]
+
+
+def maxflow_get_vertex_state(h, n: int):
+    hh = np.zeros(n, np.int32)
+    e = np.zeros(n, np.int64)
+    _check(load().maxflow_get_vertex_state(h, _p(hh), _p(e)), "maxflow_get_vertex_state")
+    return hh, e
+
+
+def maxflow_set_flow(h, u, v, f):
+    u, v, f = _i32(u), _i32(v), _i32(f)
+    _check(load().maxflow_set_flow(h, int(u.size), _p(u), _p(v), _p(f)), "maxflow_set_flow")
+
+
+def maxflow_stats(h) -> dict:
+    s = Stats()
+    _check(load().maxflow_stats(h, C.byref(s)), "maxflow_stats")
+    return s.as_dict()
+
+
+def maxflow_check(h) -> dict:
+    out = np.zeros(6, np.int64)
+    _check(load().maxflow_check(h, _p(out)), "maxflow_check")
+    keys = ["pair_violations", "excess_mismatch", "residual_cross_edges", "active", "cut_cap", "value"]
+    return {k: int(x) for k, x in zip(keys, out)}
+
+
+def maxflow_destroy(h):
+    if h:
+        load().maxflow_destroy(h)
+
+
+# ---- object wrapper --------------------------------------------------------------
+
+class Solver:
+    """One dynamic max-flow instance on one GPU (thin wrapper over the C calls)."""
+
+    def __init__(self, n, src, dst, cap, s, t, *, kernel_cycles=0, data_driven=True, fix_steep=True,
+                 grid_blocks=0, max_iters=0, time_limit_s=0.0, wait_limit_s=0.0, slack_factor=0.25,
+                 slack_min=4, device=None, stream=None, torch_alloc=True):
+        import torch
+        load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the solver runs on the GPU only")
+        self.n = int(n)
+        self.s, self.t = int(s), int(t)
+        dev = torch.cuda.current_device() if device is None else int(device)
+        self.device = dev
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        o = maxflow_default_opts()
+        o.kernel_cycles = int(kernel_cycles)
+        o.data_driven = int(bool(data_driven))
+        o.fix_steep = int(bool(fix_steep))
+        o.grid_blocks = int(grid_blocks)
+        o.max_iters = int(max_iters)
+        o.time_limit_s = float(time_limit_s)
+        o.wait_limit_s = float(wait_limit_s)
+        o.slack_factor = float(slack_factor)
+        o.slack_min = int(slack_min)
+        o.device = dev
+        o.stream = int(self.stream.cuda_stream)
+        self._alloc = _TorchAllocator(dev) if torch_alloc else None
+        if self._alloc is not None:
+            o.alloc = self._alloc.alloc
+            o.free = self._alloc.free
+        self._opts = o
+        self.h = maxflow_init(n, src, dst, cap, s, t, o)
+
+    def close(self):
+        if getattr(self, "h", None):
+            maxflow_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def update(self, u, v, c):
+        maxflow_update(self.h, u, v, c)
+
+    def apply(self, u, v, c):
+        maxflow_apply(self.h, u, v, c)
+
+    def query(self, side=False, cut=False):
+        return maxflow_query(self.h, self.n, side=side, cut=cut)
+
+    @property
+    def value(self) -> int:
+        return self.query()[0]
+
+    def resolve_static(self):
+        maxflow_resolve_static(self.h)
+
+    def resolve(self):
+        maxflow_resolve(self.h)
+
+    def global_relabel(self):
+        maxflow_global_relabel(self.h)
+
+    def get_flow(self):
+        return maxflow_get_flow(self.h)
+
+    def residual(self):
+        return maxflow_get_residual(self.h)
+
+    def vertex_state(self):
+        return maxflow_get_vertex_state(self.h, self.n)
+
+    def set_flow(self, u, v, f):
+        maxflow_set_flow(self.h, u, v, f)
+
+    def stats(self) -> dict:
+        return maxflow_stats(self.h)
+
+    def check(self) -> dict:
+        return maxflow_check(self.h)

@@ -276,8 +276,8 @@ def rmat_edges(scale: int, edge_factor: int, a: float, b: float, c: float, seed:
     """Raw R-MAT draws (with self-loops and duplicates), no noise."""
     rng = np.random.default_rng(seed)
     M = edge_factor << scale
-    u = np.zeros(M, dtype=np.int64)
-    v = np.zeros(M, dtype=np.int64)
+    u = np.zeros(M, dtype=np.uint32)
+    v = np.zeros(M, dtype=np.uint32)
     ab = a + b
     a_in_ab = a / ab
     c_in_cd = c / (1.0 - ab)
@@ -285,11 +285,22 @@ def rmat_edges(scale: int, edge_factor: int, a: float, b: float, c: float, seed:
         r1 = rng.random(M, dtype=np.float32)
         r2 = rng.random(M, dtype=np.float32)
         lower = r1 >= ab                        # quadrant c or d: u bit set
-        right = np.where(lower, r2 >= c_in_cd, r2 >= a_in_ab)   # quadrant b or d: v bit set
-        u |= lower.astype(np.int64) << bit
-        v |= right.astype(np.int64) << bit
-        del r1, r2, lower, right
-    return u, v
+        thr = np.where(lower, np.float32(c_in_cd), np.float32(a_in_ab))
+        right = r2 >= thr                       # quadrant b or d: v bit set
+        u[lower] |= np.uint32(1 << bit)
+        v[right] |= np.uint32(1 << bit)
+        del r1, r2, lower, right, thr
+    return u.astype(np.int64), v.astype(np.int64)
+
+
+def _sorted_unique(keys: np.ndarray) -> np.ndarray:
+    keys = np.sort(keys)
+    if keys.size == 0:
+        return keys
+    keep = np.empty(keys.size, dtype=bool)
+    keep[0] = True
+    np.not_equal(keys[1:], keys[:-1], out=keep[1:])
+    return keys[keep]
 
 
 def _csr_sym(n, src, dst):
@@ -311,7 +322,7 @@ def rmat(scale: int = 20, edge_factor: int = 16, a: float = 0.57, b: float = 0.1
     n = 1 << scale
     u, v = rmat_edges(scale, edge_factor, a, b, c, seed)
     keep = u != v
-    keys = np.unique(u[keep] * n + v[keep])
+    keys = _sorted_unique(u[keep] * n + v[keep])
     del u, v, keep
     src, dst = keys // n, keys % n
     rng = np.random.default_rng(seed + 7919)

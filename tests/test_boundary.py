@@ -1,0 +1,108 @@
+"""The C ABI without a GPU: the library loads, exports every function the
+header declares, the Python binding's struct layouts match the header, and
+argument errors are reported without touching a device."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2511_01235_gb300 import build_ext, native
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "maxflow.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build_ext.build()
+    return native.load()
+
+
+def declared_functions():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(maxflow_[a-z_]+)\s*\(", txt)) - {"maxflow_alloc_fn", "maxflow_free_fn"})
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    out = subprocess.run(["nm", "-D", "--defined-only", build_ext.LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (maxflow_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        getattr(lib, n)
+    assert sorted(native.EXPORTS) == names
+
+
+def test_struct_layout_matches_header(tmp_path, lib):
+    probe = tmp_path / "probe.c"
+    probe.write_text(r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "maxflow.h"
+#define F(T, f) printf(#T "." #f " %zu\n", offsetof(T, f))
+int main(void) {
+  printf("graph %zu\nbatch %zu\nopts %zu\nstats %zu\n", sizeof(maxflow_graph), sizeof(maxflow_batch),
+         sizeof(maxflow_opts), sizeof(maxflow_stats_t));
+  F(maxflow_opts, max_iters); F(maxflow_opts, time_limit_s); F(maxflow_opts, slack_factor);
+  F(maxflow_opts, stream); F(maxflow_opts, alloc); F(maxflow_opts, alloc_user);
+  F(maxflow_stats_t, iterations); F(maxflow_stats_t, ms_last); F(maxflow_stats_t, value);
+  F(maxflow_batch, on_device);
+  return 0;
+}
+''')
+    exe = tmp_path / "probe"
+    subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(probe), "-o", str(exe)])
+    got = dict(line.rsplit(" ", 1) for line in subprocess.check_output([str(exe)], text=True).splitlines())
+    got = {k: int(v) for k, v in got.items()}
+    assert got["graph"] == C.sizeof(native.Graph)
+    assert got["batch"] == C.sizeof(native.Batch)
+    assert got["opts"] == C.sizeof(native.Opts)
+    assert got["stats"] == C.sizeof(native.Stats)
+    for k, v in got.items():
+        if "." in k:
+            T, f = k.split(".")
+            cls = {"maxflow_opts": native.Opts, "maxflow_stats_t": native.Stats, "maxflow_batch": native.Batch}[T]
+            assert getattr(cls, f).offset == v, k
+
+
+def test_default_opts_and_strerror(lib):
+    o = native.maxflow_default_opts()
+    assert (o.data_driven, o.fix_steep, o.kernel_cycles, o.slack_min) == (1, 1, 0, 4)
+    assert abs(o.slack_factor - 0.25) < 1e-6
+    for code in range(8):
+        assert native.strerror(code)
+    assert native.strerror(native.ERR_INVALID) == "invalid argument"
+
+
+def test_init_argument_errors_without_gpu(lib):
+    g = native.Graph(3, 1, None, None, None)
+    h = C.c_void_p()
+    assert lib.maxflow_init(C.byref(h), C.byref(g), 0, 2, None) == native.ERR_INVALID   # NULL arrays
+    src = np.array([0], np.int32)
+    dst = np.array([1], np.int32)
+    cap = np.array([1], np.int32)
+    g = native.Graph(3, 1, src.ctypes.data, dst.ctypes.data, cap.ctypes.data)
+    assert lib.maxflow_init(C.byref(h), C.byref(g), 1, 1, None) == native.ERR_INVALID   # s == t
+    assert lib.maxflow_init(C.byref(h), C.byref(g), 0, 3, None) == native.ERR_INVALID   # t out of range
+    assert lib.maxflow_init(None, C.byref(g), 0, 2, None) == native.ERR_INVALID
+    assert not h.value
+
+
+def test_calls_on_null_context(lib):
+    v = C.c_int64()
+    assert lib.maxflow_query(None, C.byref(v), None, None) == native.ERR_STATE
+    assert lib.maxflow_update(None, None) == native.ERR_STATE
+    lib.maxflow_destroy(None)
+
+
+def test_no_cpu_fallback_when_library_missing(monkeypatch, tmp_path):
+    monkeypatch.setattr(native, "_lib", None)
+    monkeypatch.setattr(build_ext, "LIB", str(tmp_path / "missing.so"))
+    with pytest.raises(ImportError):
+        native.load()
