@@ -197,6 +197,35 @@ int maxflow_get_vertex_state(maxflow_ctx *c, int32_t *h, int64_t *e);
  * out[4] the cut capacity C(A, B); out[5] the value formula.  Six entries. */
 int maxflow_check(maxflow_ctx *c, int64_t *out);
 
+/* ---- for callers that cannot allocate device memory ---------------------- */
+
+/* The paper has no counterpart to this call; it exists for callers that may
+ * not allocate device memory once they are running -- a serving process that
+ * reserves its whole device memory pool at start-up, or a plugin inside a host
+ * application that owns the GPU allocator -- because an allocation can fail
+ * under their fixed budget, block, or synchronise the device.
+ *
+ * It computes the same heights as maxflow_global_relabel (Alg. 6 when
+ * deficit_roots != 0, Alg. 4 otherwise) on a residual graph the caller holds
+ * in device memory, and allocates nothing: the step's scratch (frontier lists
+ * and control block) is a file-scope device array sized for
+ * MAXFLOW_NOALLOC_MAX_N vertices (about 8 MB, held on every GPU that loads the
+ * library until the process exits).
+ *   rows:  slots of vertex u are off[u] .. off[u] + deg[u] - 1 (off: n+1 ints, deg: n ints)
+ *   slots: dst[x] = head v of slot (u, v); cf[x] = c_f(u, v); pcap[x] = c(u,v) + c(v,u),
+ *          so that c_f(v, u) = pcap[x] - cf[x]
+ *   e:     n excesses (int64); h: n heights (output)
+ * All pointers are device pointers on the current device; nothing is copied.
+ * The first call on a device looks up the array's device address and should
+ * come before any stream capture.  Calls share the array: two calls that overlap
+ * on the GPU race.  The call returns when the heights are written.
+ * Errors: MAXFLOW_ERR_TOO_LARGE if n > MAXFLOW_NOALLOC_MAX_N; MAXFLOW_ERR_INVALID
+ * for n < 2, s or t out of range, s == t, or a NULL pointer. */
+#define MAXFLOW_NOALLOC_MAX_N (1 << 20)
+int maxflow_global_relabel_noalloc(int32_t n, int32_t s, int32_t t, const int32_t *off, const int32_t *deg,
+                                   const int32_t *dst, const int32_t *cf, const int32_t *pcap, const int64_t *e,
+                                   int32_t *h, int32_t deficit_roots, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

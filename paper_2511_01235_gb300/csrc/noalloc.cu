@@ -1,0 +1,119 @@
+// Backward-BFS heights on caller-owned device arrays, without allocating.
+//
+// Some callers cannot allocate device memory on their request path: a serving
+// process that reserves its whole device memory pool at start-up, or a plugin
+// living inside a host application that owns the GPU allocator, must not call
+// cudaMalloc later, because an allocation can fail under their fixed budget,
+// can block, or can synchronise the device behind their back.  This entry
+// point serves them: the caller passes the residual graph, the excesses and the
+// output heights; the only scratch the step needs (the BFS frontier lists and
+// the kernel's control block) lives in the file-scope device array below.
+//
+// The array has a fixed maximum size (MAXFLOW_NOALLOC_MAX_N vertices), so every GPU
+// that loads this library holds about 8 MB for it until the process exits.
+// Every call uses the same array and it keeps the contents of the last call:
+// the barrier words of the control block are cleared before each launch, and
+// the kernel resets the rest itself.  Two calls whose work overlaps on the GPU
+// (different streams, or different host threads) race on the array.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <mutex>
+
+#include "../../include/maxflow.h"
+#include "mf_internal.h"
+
+namespace {
+
+// frontier list (MAXFLOW_NOALLOC_MAX_N ints) + hub list (MAXFLOW_NOALLOC_MAX_N ints) + control block
+constexpr size_t kCtrlBytes = (sizeof(MfCtrl) + 255) & ~(size_t)255;
+constexpr size_t kListBytes = sizeof(int32_t) * (size_t)MAXFLOW_NOALLOC_MAX_N;
+constexpr size_t kScratchBytes = kCtrlBytes + 2 * kListBytes;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+struct DeviceSetup {
+    bool ready = false;
+    unsigned char *base = nullptr;  // device address of g_noalloc_scratch on this device
+    int per_sm = 0, sms = 0;
+};
+
+constexpr int kMaxDevices = 64;
+DeviceSetup g_setup[kMaxDevices];
+std::mutex g_setup_mu;
+
+// Once per device, with that device current: the device address of the
+// scratch array (host code cannot use the symbol itself as a device pointer).
+int setup_device(int dev, DeviceSetup **out)
+{
+    if (dev < 0 || dev >= kMaxDevices) return MAXFLOW_ERR_INVALID;
+    std::lock_guard<std::mutex> lock(g_setup_mu);
+    DeviceSetup &d = g_setup[dev];
+    if (!d.ready) {
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || ptr == nullptr) return MAXFLOW_ERR_CUDA;
+        int rc = mf_max_coresident_blocks(dev, &d.per_sm, &d.sms);
+        if (rc != MAXFLOW_OK) return rc;
+        d.base = (unsigned char *)ptr;
+        d.ready = true;
+    }
+    *out = &d;
+    return MAXFLOW_OK;
+}
+
+}  // namespace
+
+extern "C" int maxflow_global_relabel_noalloc(int32_t n, int32_t s, int32_t t, const int32_t *off,
+                                              const int32_t *deg, const int32_t *dst, const int32_t *cf,
+                                              const int32_t *pcap, const int64_t *e, int32_t *h,
+                                              int32_t deficit_roots, void *stream)
+{
+    if (n < 2 || s < 0 || t < 0 || s >= n || t >= n || s == t) return MAXFLOW_ERR_INVALID;
+    if (n > MAXFLOW_NOALLOC_MAX_N) return MAXFLOW_ERR_TOO_LARGE;
+    if (!off || !deg || !dst || !cf || !pcap || !e || !h) return MAXFLOW_ERR_INVALID;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return MAXFLOW_ERR_CUDA;
+    DeviceSetup *ds = nullptr;
+    int rc = setup_device(dev, &ds);
+    if (rc != MAXFLOW_OK) return rc;
+
+    MfCtrl *ctrl = (MfCtrl *)ds->base;
+    MfParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.g.n = n;
+    p.g.off = const_cast<int32_t *>(off);
+    p.g.deg = const_cast<int32_t *>(deg);
+    p.g.dst = const_cast<int32_t *>(dst);
+    p.g.pcap = const_cast<int32_t *>(pcap);
+    p.g.cf = const_cast<int32_t *>(cf);
+    p.g.h = h;
+    p.g.e = (long long *)const_cast<int64_t *>(e);
+    p.sc.border = (int32_t *)(ds->base + kCtrlBytes);
+    p.sc.bhub = (int32_t *)(ds->base + kCtrlBytes + kListBytes);
+    p.ctrl = ctrl;
+    p.cf = p.g.cf;
+    p.h = h;
+    p.e = p.g.e;
+    p.sink = t;
+    p.source = s;
+    p.mode = MF_M_BFS_ONLY | (deficit_roots ? 0 : MF_M_NO_DEFICIT_ROOTS);
+    p.kernel_cycles = 1;
+    p.max_iters = 1;
+    p.time_limit_ns = 60ull * 1000000000ull;
+    p.wait_limit_ns = 1000000000ull;
+
+    cudaStream_t st = (cudaStream_t)stream;
+    // barrier words must start at zero (a previous call may have ended early)
+    if (cudaMemsetAsync(ctrl, 0, 2 * sizeof(MfLine), st) != cudaSuccess) return MAXFLOW_ERR_CUDA;
+    int maxg = ds->per_sm * ds->sms;
+    int grid = (int)((n + 2047) / 2048);
+    if (grid < 2) grid = 2;
+    if (grid > maxg) grid = maxg;
+    rc = mf_launch(p, grid, stream);
+    if (rc != MAXFLOW_OK) return rc;
+    unsigned err = 0;
+    if (cudaMemcpyAsync(&err, &ctrl->err.w[0], sizeof(err), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return MAXFLOW_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return MAXFLOW_ERR_CUDA;
+    return err == MF_E_NONE ? MAXFLOW_OK : MAXFLOW_ERR_INTERNAL;
+}

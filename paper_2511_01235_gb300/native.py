@@ -77,7 +77,7 @@ class Stats(C.Structure):
 EXPORTS = ["maxflow_default_opts", "maxflow_init", "maxflow_update", "maxflow_query", "maxflow_resolve_static",
            "maxflow_get_flow", "maxflow_stats", "maxflow_destroy", "maxflow_strerror", "maxflow_set_flow",
            "maxflow_apply", "maxflow_global_relabel", "maxflow_resolve", "maxflow_get_residual",
-           "maxflow_get_vertex_state", "maxflow_check"]
+           "maxflow_get_vertex_state", "maxflow_check", "maxflow_global_relabel_noalloc"]
 
 _lib = None
 
@@ -115,6 +115,7 @@ def load(build_if_missing: bool = False):
     L.maxflow_set_flow.argtypes = [vp, i64, vp, vp, vp]
     L.maxflow_stats.argtypes = [vp, P(Stats)]
     L.maxflow_check.argtypes = [vp, vp]
+    L.maxflow_global_relabel_noalloc.argtypes = [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, i32, vp]
     L.maxflow_destroy.argtypes = [vp]
     L.maxflow_destroy.restype = None
     L.maxflow_strerror.argtypes = [C.c_int]
@@ -281,6 +282,12 @@ def maxflow_check(h) -> dict:
     _check(load().maxflow_check(h, _p(out)), "maxflow_check")
     keys = ["pair_violations", "excess_mismatch", "residual_cross_edges", "active", "cut_cap", "value"]
     return {k: int(x) for k, x in zip(keys, out)}
+
+
+def maxflow_global_relabel_noalloc(n, s, t, off, deg, dst, cf, pcap, e, h, deficit_roots=True, stream=None):
+    """Device pointers (ints) in, heights written to h; allocates nothing on the device."""
+    return int(load().maxflow_global_relabel_noalloc(int(n), int(s), int(t), off, deg, dst, cf, pcap, e, h,
+                                                      int(bool(deficit_roots)), stream))
 
 
 def maxflow_destroy(h):
