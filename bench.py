@@ -97,29 +97,53 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_workload(args):
-    from paper_2511_01235_gb300 import workloads as W
-    if args.workload == "rmat20":
-        g = W.rmat(20, 16, 0.57, 0.19, 0.19, seed=2, cap_lo=1, cap_hi=1000)
-        ins_hi = 1000
-    elif args.workload == "er_small":
-        g = W.er_small()
-        ins_hi = 100
-    else:
-        raise SystemExit(f"unknown workload {args.workload}")
-    es = W.EdgeSet(g.n, g.src, g.dst, g.cap)
-    rng = np.random.default_rng(1234)
-    return g, es, rng, ins_hi
+class Workload:
+    """A graph plus a deterministic stream of update batches."""
 
+    def __init__(self, args):
+        from paper_2511_01235_gb300 import workloads as W
+        self.kind = args.workload
+        self.grid = None
+        if self.kind.startswith("rmat"):
+            scale = int(self.kind[4:] or 20)
+            self.g = W.rmat(scale, 16, 0.57, 0.19, 0.19, seed=2 if scale == 20 else 10 + scale, cap_lo=1,
+                            cap_hi=1000)
+            self.ins_hi = 1000
+        elif self.kind == "er_small":
+            self.g = W.er_small()
+            self.ins_hi = 100
+        elif self.kind.startswith("grid"):
+            side = int(self.kind[4:] or 2048)
+            self.grid = W.GridSegmentation(side=side, seed=3)
+            self.g = self.grid.graph()
+            self.ins_hi = 1000
+        else:
+            raise SystemExit(f"unknown workload {self.kind}")
+        self.es = W.EdgeSet(self.g.n, self.g.src, self.g.dst, self.g.cap)
+        self.rng = np.random.default_rng(1234)
+        self.k = 0
 
-def gen_batches(es, rng, count, B, ins_hi):
-    from paper_2511_01235_gb300 import workloads as W
-    out = []
-    for _ in range(count):
-        b = W.mixed_batch(es, B, rng, ins_cap_hi=ins_hi)
-        es.apply(b.u, b.v, b.cap)
-        out.append(b)
-    return out
+    def batches(self, count, B):
+        from paper_2511_01235_gb300 import workloads as W
+        out = []
+        for _ in range(count):
+            if self.grid is not None:
+                b = self.grid.window_batch(self.k % 30)
+            else:
+                b = W.mixed_batch(self.es, B, self.rng, ins_cap_hi=self.ins_hi)
+            self.es.apply(b.u, b.v, b.cap)
+            self.k += 1
+            out.append(b)
+        return out
+
+    def describe(self):
+        if self.kind.startswith("rmat"):
+            return (f"{self.kind}: R-MAT scale {self.kind[4:] or 20}, edge factor 16, a/b/c=0.57/0.19/0.19, "
+                    f"caps U[1,1000], mixed batches 40/40/10/10")
+        if self.kind == "er_small":
+            return "er_small: Erdos-Renyi n=4096 m=32768 caps U[1,100], mixed batches 40/40/10/10"
+        return (f"{self.kind}: {self.grid.side}x{self.grid.side} 4-connected segmentation grid, "
+                f"t-links re-drawn in a 256x256 window shifting 8 px per batch")
 
 
 def dist_env():
@@ -135,8 +159,10 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    g, es, rng, ins_hi = make_workload(args)
-    batches = gen_batches(es.copy(), rng, args.warmup + args.steps, args.batch, ins_hi)
+    wl = Workload(args)
+    g = wl.g
+    batches = wl.batches(args.warmup + args.steps, args.batch)
+    args.batch = batches[0].size
     es2 = W_edgeset(g)
     times = []
     for i, b in enumerate(batches):
@@ -152,7 +178,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-            "data": "synthetic", "config": config_of(args, g),
+            "data": "synthetic", "config": config_of(args, g, wl),
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{len(times)} batches of {args.batch}; Dinic recomputed from scratch per batch"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -164,12 +190,10 @@ def W_edgeset(g):
     return W.EdgeSet(g.n, g.src, g.dst, g.cap)
 
 
-def config_of(args, g):
-    return {"workload": f"{args.workload}: R-MAT scale 20, edge factor 16, a/b/c=0.57/0.19/0.19, caps U[1,1000]"
-            if args.workload == "rmat20" else args.workload,
+def config_of(args, g, wl):
+    return {"workload": wl.describe(),
             "n": int(g.n), "m_merged": int(g.m), "s": int(g.s), "t": int(g.t), "batch": args.batch,
-            "batch_mix": "40% increase U[1,50] / 40% decrease to U[0,cap] / 10% insert / 10% delete",
-            "l2": "inputs larger than L2 (residual state ~0.6 GB vs 129 MB L2)",
+            "l2": "inputs larger than L2 (residual state of R-MAT 20 / grid 2048 ~0.6 GB vs 129 MB L2)",
             "parallelism": f"replicas x{args.gpus}"}
 
 
@@ -199,6 +223,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--static-reps", type=int, default=3)
+    ap.add_argument("--quick", action="store_true", help="timed steps only (for profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -216,9 +241,11 @@ def main():
     dev = torch.cuda.current_device()
     native.load()
 
-    g, es, rng, ins_hi = make_workload(args)
+    wl = Workload(args)
+    g = wl.g
     nb = args.warmup + args.steps
-    batches = gen_batches(es, rng, nb, args.batch, ins_hi)
+    batches = wl.batches(nb, args.batch)
+    args.batch = batches[0].size
     dev_batches = [(torch.from_numpy(b.u).cuda(), torch.from_numpy(b.v).cuda(), torch.from_numpy(b.cap).cuda())
                    for b in batches]
     stream = torch.cuda.current_stream()
@@ -261,8 +288,11 @@ def main():
     final_value = S.query()[0]
     last_stats = S.stats()
 
+    if args.quick:
+        args.no_cpu_baseline = True
+        args.static_reps = 0
     # ---- end-to-end through the public API with host buffers ----
-    e2e_b = gen_batches(es, rng, min(args.steps, 10), args.batch, ins_hi)
+    e2e_b = wl.batches(0 if args.quick else min(args.steps, 10), args.batch)
     pinned = []
     for b in e2e_b:
         tu = torch.from_numpy(b.u).pin_memory()
@@ -275,7 +305,7 @@ def main():
         native.maxflow_update(S.h, tu.numpy(), tv.numpy(), tc.numpy())
         native.maxflow_query(S.h, S.n)
     e2e_s = time.perf_counter() - t0
-    e2e_val = ws * args.batch * len(pinned) / e2e_s
+    e2e_val = ws * args.batch * len(pinned) / e2e_s if pinned else None
 
     # ---- static re-solve comparator (same updated graph) ----
     static_ms = []
@@ -302,10 +332,10 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": config_of(args, g),
+            "config": config_of(args, g, wl),
             "latency_ms": {"p50": p50, "p99": p99, "mean": float(lat.mean())},
-            "static_resolve_ms": float(np.median(static_ms)),
-            "speedup_vs_static": float(np.median(static_ms)) / p50 if p50 > 0 else None,
+            "static_resolve_ms": float(np.median(static_ms)) if static_ms else None,
+            "speedup_vs_static": float(np.median(static_ms)) / p50 if static_ms and p50 > 0 else None,
             "flow_value": {"static": int(static_value), "final": int(final_value)},
             "init_s": init_s,
             "gpu_launches": args.steps,

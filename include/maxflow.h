@@ -93,7 +93,7 @@ typedef struct {
     int32_t grid_blocks;        /* cooperative grid size; 0 = sized from the graph and the GPU */
     int64_t max_iters;          /* outer-iteration cap per solve; 0 = 4n + 1000 */
     double  time_limit_s;       /* device wall-clock cap per solve; 0 = 120 s */
-    double  wait_limit_s;       /* cap on any single device-side wait (grid barrier); 0 = 2 s */
+    double  wait_limit_s;       /* cap on any single device-side wait (grid barrier); 0 = 1 s */
     float   slack_factor;       /* spare slots per vertex for insertions: max(slack_min, ceil(deg * factor)) */
     int32_t slack_min;
     int32_t device;             /* CUDA device ordinal; -1 = the current device */
@@ -207,10 +207,10 @@ int maxflow_check(maxflow_ctx *c, int64_t *out);
  *
  * It computes the same heights as maxflow_global_relabel (Alg. 6 when
  * deficit_roots != 0, Alg. 4 otherwise) on a residual graph the caller holds
- * in device memory, and allocates nothing: the step's scratch (frontier lists
- * and control block) is a file-scope device array sized for
- * MAXFLOW_NOALLOC_MAX_N vertices (about 8 MB, held on every GPU that loads the
- * library until the process exits).
+ * in device memory, and allocates nothing: the step's scratch (frontier lists and
+ * control block) is a file-scope device array sized for MAXFLOW_NOALLOC_MAX_N
+ * vertices and MAXFLOW_NOALLOC_MAX_SLOTS slots (about 14 MB, held on every GPU
+ * that loads the library until the process exits).
  *   rows:  slots of vertex u are off[u] .. off[u] + deg[u] - 1 (off: n+1 ints, deg: n ints)
  *   slots: dst[x] = head v of slot (u, v); cf[x] = c_f(u, v); pcap[x] = c(u,v) + c(v,u),
  *          so that c_f(v, u) = pcap[x] - cf[x]
@@ -219,9 +219,11 @@ int maxflow_check(maxflow_ctx *c, int64_t *out);
  * The first call on a device looks up the array's device address and should
  * come before any stream capture.  Calls share the array: two calls that overlap
  * on the GPU race.  The call returns when the heights are written.
- * Errors: MAXFLOW_ERR_TOO_LARGE if n > MAXFLOW_NOALLOC_MAX_N; MAXFLOW_ERR_INVALID
+ * Errors: MAXFLOW_ERR_TOO_LARGE if n > MAXFLOW_NOALLOC_MAX_N or off[n] >
+ * MAXFLOW_NOALLOC_MAX_SLOTS (off[n] is read back first); MAXFLOW_ERR_INVALID
  * for n < 2, s or t out of range, s == t, or a NULL pointer. */
 #define MAXFLOW_NOALLOC_MAX_N (1 << 20)
+#define MAXFLOW_NOALLOC_MAX_SLOTS (1 << 25)
 int maxflow_global_relabel_noalloc(int32_t n, int32_t s, int32_t t, const int32_t *off, const int32_t *deg,
                                    const int32_t *dst, const int32_t *cf, const int32_t *pcap, const int64_t *e,
                                    int32_t *h, int32_t deficit_roots, void *stream);

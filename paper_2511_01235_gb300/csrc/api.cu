@@ -195,6 +195,9 @@ int upload_graph(maxflow_ctx *c, const MfHostGraph &hg)
     MF_TRY(rc_cuda(cudaMemcpyAsync(c->g.pcap, hg.pcap, sizeof(int32_t) * S, cudaMemcpyHostToDevice, st)));
     // the host arrays must stay valid until the copies complete
     MF_TRY(rc_cuda(cudaStreamSynchronize(st)));
+    dfree(c, c->sc.bitem);
+    c->sc.bitem = dalloc_n<int2>(c, (int64_t)n + S / MF_BFS_CHUNK + 64);
+    if (!c->sc.bitem) return MAXFLOW_ERR_OOM;
     c->st.slot_capacity = S;
     c->st.slots = hg.slots;
     c->st.m_edges = hg.m_merged;
@@ -513,12 +516,11 @@ int maxflow_init(maxflow_ctx **out, const maxflow_graph *g, int32_t s, int32_t t
         c->g.h = dalloc_n<int32_t>(c, n);
         c->g.e = dalloc_n<long long>(c, n);
         c->sc.border = dalloc_n<int32_t>(c, n);
-        c->sc.bhub = dalloc_n<int32_t>(c, n);
         for (int b = 0; b < 3; ++b) c->sc.wl[b] = dalloc_n<int32_t>(c, n);
         c->sc.ins_need = dalloc_n<int32_t>(c, n);
         c->ctrl = (MfCtrl *)dalloc(c, sizeof(MfCtrl));
         c->dbuf = dalloc_n<long long>(c, 16);
-        if (!c->g.h || !c->g.e || !c->sc.border || !c->sc.bhub || !c->sc.wl[0] || !c->sc.wl[1] || !c->sc.wl[2] ||
+        if (!c->g.h || !c->g.e || !c->sc.border || !c->sc.bitem || !c->sc.wl[0] || !c->sc.wl[1] || !c->sc.wl[2] ||
             !c->sc.ins_need || !c->ctrl || !c->dbuf)
             rc = MAXFLOW_ERR_OOM;
     }

@@ -14,11 +14,14 @@
 //   h[n]       heights (int32), e[n] excesses (int64)
 #pragma once
 #include <stdint.h>
+#include <cuda_runtime.h>
 
 #define MF_BLOCK 512          // threads per CTA of the persistent kernel
 #define MF_WARPS (MF_BLOCK / 32)
 #define MF_SMALL_DEG 16       // discharge: rows up to this many slots get one thread
-#define MF_HUB_DEG 4096       // rows above this many slots get a whole CTA (discharge) or the grid (BFS)
+#define MF_HUB_DEG 4096       // discharge: rows above this many slots get a whole CTA
+#define MF_BFS_HUB 256        // BFS: rows above this many slots enter the frontier as work items
+#define MF_BFS_CHUNK 256      // BFS: slots per work item
 #define MF_ACTIVE_HIST 64
 
 // Solve-kernel status (ctrl->status)
@@ -55,7 +58,7 @@ struct MfCtrl {
     MfLine bar_gen;       // w[0]: barrier generation
     MfLine err;           // w[0]: sticky error (MF_E_*)
     MfLine bfs_tail;      // w[0]: regular frontier append position
-    MfLine hub_tail;      // w[0]: hub frontier append position
+    MfLine hub_tail;      // w[0]: frontier work-item append position
     MfLine head0;         // w[0]: dynamic work head
     MfLine head1;
     MfLine head2;
@@ -90,7 +93,7 @@ struct MfGraph {
 
 struct MfScratch {
     int32_t *border;          // [n] BFS order (level segments)
-    int32_t *bhub;            // [n] hub frontier
+    int2 *bitem;              // [n + slot_cap / MF_BFS_CHUNK + 64] frontier work items (first slot, length)
     int32_t *wl[3];           // [n] worklists: small, mid, hub
     // batch apply
     int64_t batch_cap;

@@ -9,8 +9,9 @@
 // output heights; the only scratch the step needs (the BFS frontier lists and
 // the kernel's control block) lives in the file-scope device array below.
 //
-// The array has a fixed maximum size (MAXFLOW_NOALLOC_MAX_N vertices), so every GPU
-// that loads this library holds about 8 MB for it until the process exits.
+// The array has a fixed maximum size (MAXFLOW_NOALLOC_MAX_N vertices and
+// MAXFLOW_NOALLOC_MAX_SLOTS slots), so every GPU that loads this library holds
+// about 14 MB for it until the process exits.
 // Every call uses the same array and it keeps the contents of the last call:
 // the barrier words of the control block are cleared before each launch, and
 // the kernel resets the rest itself.  Two calls whose work overlaps on the GPU
@@ -25,10 +26,13 @@
 
 namespace {
 
-// frontier list (MAXFLOW_NOALLOC_MAX_N ints) + hub list (MAXFLOW_NOALLOC_MAX_N ints) + control block
+// control block + frontier list (one int per vertex) + work items of long rows
+// (at most one per vertex plus one per MF_BFS_CHUNK slots)
 constexpr size_t kCtrlBytes = (sizeof(MfCtrl) + 255) & ~(size_t)255;
-constexpr size_t kListBytes = sizeof(int32_t) * (size_t)MAXFLOW_NOALLOC_MAX_N;
-constexpr size_t kScratchBytes = kCtrlBytes + 2 * kListBytes;
+constexpr size_t kListBytes = (sizeof(int32_t) * (size_t)MAXFLOW_NOALLOC_MAX_N + 255) & ~(size_t)255;
+constexpr size_t kItemBytes =
+    sizeof(int2) * ((size_t)MAXFLOW_NOALLOC_MAX_N + (size_t)MAXFLOW_NOALLOC_MAX_SLOTS / MF_BFS_CHUNK + 64);
+constexpr size_t kScratchBytes = kCtrlBytes + kListBytes + kItemBytes;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -89,7 +93,7 @@ extern "C" int maxflow_global_relabel_noalloc(int32_t n, int32_t s, int32_t t, c
     p.g.h = h;
     p.g.e = (long long *)const_cast<int64_t *>(e);
     p.sc.border = (int32_t *)(ds->base + kCtrlBytes);
-    p.sc.bhub = (int32_t *)(ds->base + kCtrlBytes + kListBytes);
+    p.sc.bitem = (int2 *)(ds->base + kCtrlBytes + kListBytes);
     p.ctrl = ctrl;
     p.cf = p.g.cf;
     p.h = h;
@@ -103,6 +107,12 @@ extern "C" int maxflow_global_relabel_noalloc(int32_t n, int32_t s, int32_t t, c
     p.wait_limit_ns = 1000000000ull;
 
     cudaStream_t st = (cudaStream_t)stream;
+    int32_t nslots = 0;
+    if (cudaMemcpyAsync(&nslots, off + n, sizeof(nslots), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return MAXFLOW_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return MAXFLOW_ERR_CUDA;
+    if (nslots < 0) return MAXFLOW_ERR_INVALID;
+    if (nslots > MAXFLOW_NOALLOC_MAX_SLOTS) return MAXFLOW_ERR_TOO_LARGE;
     // barrier words must start at zero (a previous call may have ended early)
     if (cudaMemsetAsync(ctrl, 0, 2 * sizeof(MfLine), st) != cudaSuccess) return MAXFLOW_ERR_CUDA;
     int maxg = ds->per_sm * ds->sms;

@@ -162,7 +162,7 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
         c->lvl_hi = (int)c->bfs_tail.w[0];
         c->hub_lo = 0;
         c->hub_hi = (int)c->hub_tail.w[0];
-        c->head0.w[0] = 0;
+        c->head0.w[0] = c->head1.w[0] = 0;
         c->bfs_done = (c->lvl_hi == 0 && c->hub_hi == 0);
         break;
     case H_BFS_NEXT:
@@ -173,7 +173,7 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
         c->lvl_hi = (int)c->bfs_tail.w[0];
         c->hub_lo = c->hub_hi;
         c->hub_hi = (int)c->hub_tail.w[0];
-        c->head0.w[0] = 0;
+        c->head0.w[0] = c->head1.w[0] = 0;
         c->bfs_done = (c->lvl_lo == c->lvl_hi && c->hub_lo == c->hub_hi);
         break;
     case H_WL: {
@@ -603,9 +603,33 @@ __device__ __forceinline__ void warp_append(unsigned *tail, int *arr, bool take,
     if (take) arr[base + __popc(m & ((1u << lane) - 1u))] = val;
 }
 
-__device__ __noinline__ void phase_bfs_init(const MfParams &P, Sh &sh)
+// A labelled vertex enters the next frontier either as one entry of the
+// regular list (rows of at most MF_BFS_HUB slots, expanded warp-cooperatively)
+// or, for longer rows, as ceil(deg / MF_BFS_CHUNK) work items (first slot,
+// length) that any warp can take: no row is ever walked by one warp alone.
+__device__ __forceinline__ void frontier_push(const MfParams &P, bool take, int z)
 {
     MfCtrl *ctl = P.ctrl;
+    int d = 0;
+    bool big = false;
+    if (take) {
+        d = ldg_cg(P.g.deg + z);
+        big = d > MF_BFS_HUB;
+    }
+    if (big) {
+        const int nch = (d + MF_BFS_CHUNK - 1) / MF_BFS_CHUNK;
+        const int x0 = P.g.off[z];
+        unsigned at = atomicAdd(&ctl->hub_tail.w[0], (unsigned)nch);
+        for (int c = 0; c < nch; ++c) {
+            int len = d - c * MF_BFS_CHUNK;
+            P.sc.bitem[at + c] = make_int2(x0 + c * MF_BFS_CHUNK, len < MF_BFS_CHUNK ? len : MF_BFS_CHUNK);
+        }
+    }
+    warp_append(&ctl->bfs_tail.w[0], P.sc.border, take && !big, z);
+}
+
+__device__ __noinline__ void phase_bfs_init(const MfParams &P, Sh &sh)
+{
     const int n = P.g.n;
     const bool deficit_roots = (P.mode & MF_M_NO_DEFICIT_ROOTS) == 0;
     const int lane = threadIdx.x & 31;
@@ -617,51 +641,61 @@ __device__ __noinline__ void phase_bfs_init(const MfParams &P, Sh &sh)
             root = (v == P.sink) || (deficit_roots && v != P.source && ldg_cg(P.e + v) < 0);
             P.h[v] = root ? 0 : n;
         }
-        bool hub = root && ldg_cg(P.g.deg + v) > MF_HUB_DEG;
-        if (hub) P.sc.bhub[atomicAdd(&ctl->hub_tail.w[0], 1u)] = v;
-        warp_append(&ctl->bfs_tail.w[0], P.sc.border, root && !hub, v);
+        frontier_push(P, root, v);
     }
 }
 
-// Visit slot x = (u, z) at level L: z gets height L+1 if it is unlabelled,
-// is not the source, and has a residual edge (z, u): c_f(z,u) = pcap - c_f(u,z).
-__device__ __forceinline__ void bfs_visit(const MfParams &P, bool valid, int x, int L)
+// Visit BR slots per lane at level L.  Slot x = (u, z): z gets height L+1 if
+// it is unlabelled, is not the source, and has a residual edge (z, u), i.e.
+// c_f(z, u) = pcap - c_f(u, z) > 0.  The loads of the BR slots are issued
+// together so each lane keeps BR independent gathers in flight.
+template <int BR>
+__device__ __forceinline__ void bfs_visit(const MfParams &P, const int (&x)[BR], const bool (&valid)[BR], int L)
 {
-    MfCtrl *ctl = P.ctrl;
     const int n = P.g.n;
-    bool claim = false;
-    int z = 0;
-    if (valid) {
-        z = ldg_cg(P.g.dst + x);
-        if (z != P.source && ldg_cg(P.h + z) == n) {
-            int rc = ldg_cg(P.g.pcap + x) - ldg_cg(P.cf + x);
-            if (rc > 0) claim = atomicCAS(P.h + z, n, L + 1) == n;
-        }
+    int z[BR], rc[BR], hz[BR];
+#pragma unroll
+    for (int r = 0; r < BR; ++r) {
+        z[r] = valid[r] ? ldg_cg(P.g.dst + x[r]) : P.source;
+        rc[r] = valid[r] ? ldg_cg(P.g.pcap + x[r]) - ldg_cg(P.cf + x[r]) : 0;
     }
-    bool hub = claim && ldg_cg(P.g.deg + z) > MF_HUB_DEG;
-    if (hub) P.sc.bhub[atomicAdd(&ctl->hub_tail.w[0], 1u)] = z;
-    warp_append(&ctl->bfs_tail.w[0], P.sc.border, claim && !hub, z);
+#pragma unroll
+    for (int r = 0; r < BR; ++r) hz[r] = (rc[r] > 0 && z[r] != P.source) ? ldg_cg(P.h + z[r]) : 0;
+#pragma unroll
+    for (int r = 0; r < BR; ++r) {
+        bool claim = hz[r] == n && atomicCAS(P.h + z[r], n, L + 1) == n;
+        frontier_push(P, claim, z[r]);
+    }
 }
+
+constexpr int kBR = 4;
 
 __device__ __noinline__ void phase_bfs_level(const MfParams &P, Sh &sh)
 {
     MfCtrl *ctl = P.ctrl;
     const int L = vrd(&ctl->level);
     const int lane = threadIdx.x & 31;
-    const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
     long long slots = 0;
-    // hubs of this level: every warp of the grid takes a share of each hub's slots
-    const int hlo = vrd(&ctl->hub_lo), hhi = vrd(&ctl->hub_hi);
-    for (int j = hlo; j < hhi; ++j) {
-        int u = __ldcg(P.sc.bhub + j);
-        int r0 = P.g.off[u];
-        int d = ldg_cg(P.g.deg + u);
-        for (int base = gwarp * 32; base < d; base += nwarps * 32) {
-            int k = base + lane;
-            bfs_visit(P, k < d, r0 + k, L);
+    // chunks of long rows: one warp per item (at most MF_BFS_CHUNK slots)
+    const int ilo = vrd(&ctl->hub_lo), icnt = vrd(&ctl->hub_hi) - ilo;
+    for (;;) {
+        int i = 0;
+        if (lane == 0) i = (int)atomicAdd(&ctl->head1.w[0], 1u);
+        i = __shfl_sync(0xffffffffu, i, 0);
+        if (i >= icnt) break;
+        const int2 it = __ldcg(P.sc.bitem + ilo + i);
+        if (lane == 0) slots += it.y;
+        for (int kb = 0; kb < it.y; kb += 32 * kBR) {
+            int xs[kBR];
+            bool vs[kBR];
+#pragma unroll
+            for (int r = 0; r < kBR; ++r) {
+                int k = kb + r * 32 + lane;
+                vs[r] = k < it.y;
+                xs[r] = it.x + k;
+            }
+            bfs_visit<kBR>(P, xs, vs, L);
         }
-        if (gwarp == 0 && lane == 0) slots += d;
     }
     // regular frontier: warps take 32 vertices at a time and expand their
     // rows together (each lane finds the vertex that owns its slot)
@@ -684,18 +718,25 @@ __device__ __noinline__ void phase_bfs_level(const MfParams &P, Sh &sh)
         const int excl = incl - d;
         const int T = __shfl_sync(0xffffffffu, incl, 31);
         if (lane == 0) slots += T;
-        for (int kb = 0; kb < T; kb += 32) {
-            const int k = kb + lane;
-            int owner = 0;
+        for (int kb = 0; kb < T; kb += 32 * kBR) {
+            int xs[kBR];
+            bool vs[kBR];
 #pragma unroll
-            for (int step = 16; step >= 1; step >>= 1) {
-                int cand = owner + step;
-                int ec = __shfl_sync(0xffffffffu, excl, cand & 31);
-                if (cand < 32 && ec <= k) owner = cand;
+            for (int r = 0; r < kBR; ++r) {
+                const int k = kb + r * 32 + lane;
+                int owner = 0;
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1) {
+                    int cand = owner + step;
+                    int ec = __shfl_sync(0xffffffffu, excl, cand & 31);
+                    if (cand < 32 && ec <= k) owner = cand;
+                }
+                int rb = __shfl_sync(0xffffffffu, r0, owner);
+                int eb = __shfl_sync(0xffffffffu, excl, owner);
+                vs[r] = k < T;
+                xs[r] = rb + (k - eb);
             }
-            int rb = __shfl_sync(0xffffffffu, r0, owner);
-            int eb = __shfl_sync(0xffffffffu, excl, owner);
-            bfs_visit(P, k < T, rb + (k - eb), L);
+            bfs_visit<kBR>(P, xs, vs, L);
         }
     }
     if (slots) atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)slots);
@@ -746,6 +787,36 @@ __device__ __forceinline__ void do_push(const MfParams &P, Sh &sh, int u, int x,
     atomicAdd((unsigned long long *)&sh.pushes, 1ull);
 }
 
+// Lowest residual neighbour over slots j = j0, j0 + step, ... (j < d) of the
+// row at r0, as a key (h(v) << 32 | j) so the minimum also breaks ties by the
+// lowest slot index.  Slots are read kU at a time with their loads issued
+// together.
+constexpr int kU = 4;
+
+__device__ __forceinline__ unsigned long long scan_lowest(const MfParams &P, int r0, int d, int j0, int step)
+{
+    unsigned long long best = kEmpty;
+    for (int jb = j0; jb < d; jb += step * kU) {
+        int c[kU], z[kU], hz[kU];
+#pragma unroll
+        for (int r = 0; r < kU; ++r) {
+            int j = jb + r * step;
+            c[r] = j < d ? ldg_cg(P.cf + r0 + j) : 0;
+            z[r] = j < d ? ldg_cg(P.g.dst + r0 + j) : 0;
+        }
+#pragma unroll
+        for (int r = 0; r < kU; ++r) hz[r] = c[r] > 0 ? ldg_cg(P.h + z[r]) : 0;
+#pragma unroll
+        for (int r = 0; r < kU; ++r) {
+            if (c[r] > 0) {
+                unsigned long long key = ((unsigned long long)(unsigned)hz[r] << 32) | (unsigned)(jb + r * step);
+                best = key < best ? key : best;
+            }
+        }
+    }
+    return best;
+}
+
 // One thread per vertex (rows of at most MF_SMALL_DEG slots).
 __device__ void discharge_thread(const MfParams &P, Sh &sh, int u)
 {
@@ -758,21 +829,12 @@ __device__ void discharge_thread(const MfParams &P, Sh &sh, int u)
         long long eu = ldg_cg(P.e + u);
         if (!(hu < n && eu > 0)) break;
         ++cyc_done;
-        int best_h = 0x7fffffff, best_x = -1;
-        for (int j = 0; j < d; ++j) {
-            int x = r0 + j;
-            if (ldg_cg(P.cf + x) > 0) {
-                int hz = ldg_cg(P.h + ldg_cg(P.g.dst + x));
-                if (hz < best_h) {
-                    best_h = hz;
-                    best_x = x;
-                }
-            }
-        }
-        if (best_x >= 0 && hu > best_h) {
-            do_push(P, sh, u, best_x, eu);
+        unsigned long long best = scan_lowest(P, r0, d, 0, 1);
+        int best_h = best == kEmpty ? 0x7fffffff : (int)(best >> 32);
+        if (best != kEmpty && hu > best_h) {
+            do_push(P, sh, u, r0 + (int)(best & 0xffffffffu), eu);
         } else {
-            hu = (best_x < 0 || best_h >= n - 1) ? n : best_h + 1;
+            hu = (best == kEmpty || best_h >= n - 1) ? n : best_h + 1;
             P.h[u] = hu;
             atomicAdd((unsigned long long *)&sh.relabels, 1ull);
         }
@@ -796,16 +858,7 @@ __device__ void discharge_warp(const MfParams &P, Sh &sh, int u)
         long long eu = ldg_cg(P.e + u);
         if (!(hu < n && eu > 0)) break;
         ++cyc_done;
-        unsigned long long best = kEmpty;
-        for (int j = lane; j < d; j += 32) {
-            int x = r0 + j;
-            if (ldg_cg(P.cf + x) > 0) {
-                int hz = ldg_cg(P.h + ldg_cg(P.g.dst + x));
-                unsigned long long key = ((unsigned long long)(unsigned)hz << 32) | (unsigned)j;
-                best = key < best ? key : best;
-            }
-        }
-        best = warp_min_u64(best);
+        unsigned long long best = warp_min_u64(scan_lowest(P, r0, d, lane, 32));
         int best_h = best == kEmpty ? 0x7fffffff : (int)(best >> 32);
         if (best != kEmpty && hu > best_h) {
             if (lane == 0) do_push(P, sh, u, r0 + (int)(best & 0xffffffffu), eu);
@@ -843,16 +896,7 @@ __device__ void discharge_cta(const MfParams &P, Sh &sh, int u)
             __syncthreads();
             break;
         }
-        unsigned long long best = kEmpty;
-        for (int j = threadIdx.x; j < d; j += blockDim.x) {
-            int x = r0 + j;
-            if (ldg_cg(P.cf + x) > 0) {
-                int hz = ldg_cg(P.h + ldg_cg(P.g.dst + x));
-                unsigned long long key = ((unsigned long long)(unsigned)hz << 32) | (unsigned)j;
-                best = key < best ? key : best;
-            }
-        }
-        best = warp_min_u64(best);
+        unsigned long long best = warp_min_u64(scan_lowest(P, r0, d, threadIdx.x, blockDim.x));
         if (lane == 0) sh.red[wid] = best;
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -929,19 +973,22 @@ __device__ __noinline__ void phase_fix(const MfParams &P, Sh &sh)
 {
     MfCtrl *ctl = P.ctrl;
     const int lane = threadIdx.x & 31;
-    const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
     long long slots = 0, verts = 0;
-    // hubs: the warps of the grid share each hub's row
+    // hubs: one CTA each
     const int nh = vrd(&ctl->wl_n[2]);
-    for (int i = 0; i < nh; ++i) {
+    for (;;) {
+        if (threadIdx.x == 0) sh.bcast_i = (int)atomicAdd(&ctl->head2.w[0], 1u);
+        __syncthreads();
+        int i = sh.bcast_i;
+        __syncthreads();
+        if (i >= nh) break;
         int u = __ldcg(P.sc.wl[2] + i);
         int hu = ldg_cg(P.h + u);
         int r0 = P.g.off[u], d = ldg_cg(P.g.deg + u);
         long long out = 0;
-        for (int j = gwarp * 32 + lane; j < d; j += nwarps * 32) out += fix_slot(P, sh, hu, r0 + j);
+        for (int j = threadIdx.x; j < d; j += blockDim.x) out += fix_slot(P, sh, hu, r0 + j);
         if (out) atomic_add_ll(P.e + u, -out);
-        if (gwarp == 0 && lane == 0) { slots += d; ++verts; }
+        if (threadIdx.x == 0) { slots += d; ++verts; }
     }
     // mid rows: warp per vertex
     const int nm = vrd(&ctl->wl_n[1]);
