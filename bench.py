@@ -264,7 +264,7 @@ def main():
     clk.start()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     lat = []
-    kbytes, kms = [], []
+    kbytes, kms, detail = [], [], []
     torch.cuda.synchronize()
     t_wall = time.perf_counter()
     for k in range(args.steps):
@@ -275,6 +275,7 @@ def main():
         st = S.stats()
         kbytes.append(st["bytes_bfs"] + st["bytes_discharge"] + st["bytes_fix"] + st["bytes_worklist"] + st["bytes_apply"])
         kms.append(st["ms_last"])
+        detail.append([round(st["ms_last"], 3), st["iterations"], st["bfs_levels"], st["pushes"], st["relabels"]])
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall
     clocks = clk.stop()
@@ -354,6 +355,8 @@ def main():
             "static_stats": {k: static_stats[k] for k in ("iterations", "bfs_levels", "pushes", "relabels",
                                                           "ms_bfs", "ms_discharge", "ms_fix", "ms_worklist")},
             "wall_s_timed": wall,
+            "steps_detail": {"cols": ["kernel_ms", "iterations", "bfs_levels", "pushes", "relabels"],
+                             "rows": detail},
         }
         print(json.dumps(line), flush=True)
     S.close()

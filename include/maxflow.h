@@ -115,6 +115,8 @@ typedef struct {
     double  ms_last;                /* device time of the last solve kernel (CUDA events) */
     double  ms_bfs, ms_discharge, ms_fix, ms_worklist, ms_apply;  /* device wall time per phase (globaltimer) */
     int64_t value;                  /* value of the last solve */
+    double  ms_kernel;              /* device clock from kernel entry to its last grid barrier */
+    int64_t barriers;               /* grid barriers the last solve kernel passed */
 } maxflow_stats_t;
 
 /* Fill o with the defaults documented above. */
@@ -156,6 +158,14 @@ int maxflow_get_flow(maxflow_ctx *c, int64_t *count, int32_t *u, int32_t *v, int
 
 /* Counters and timings of the context and of its last solve. */
 int maxflow_stats(maxflow_ctx *c, maxflow_stats_t *out);
+
+/* Timeline of the last solve kernel: for each grid barrier (at most `cap`),
+ * the phase boundary it closed and its time in microseconds after kernel
+ * entry.  Boundary ids: 0 start, 1 prologue step, 2 batch validated,
+ * 3 batch located, 4 room checked, 5 capacities changed, 6 iteration start,
+ * 7 BFS roots set, 8 BFS level done, 9 worklist built, 10 discharge done,
+ * 11 end.  *count receives the number of entries written.  Host arrays. */
+int maxflow_trace(maxflow_ctx *c, int32_t *boundary, double *t_us, int32_t cap, int32_t *count);
 
 /* Release every resource of the context (NULL is a no-op). */
 void maxflow_destroy(maxflow_ctx *c);

@@ -243,6 +243,8 @@ void fill_stats(maxflow_ctx *c, const MfCtrl &h, float ms)
     s.ms_fix = h.ns_fix * 1e-6;
     s.ms_worklist = h.ns_wl * 1e-6;
     s.ms_apply = h.ns_apply * 1e-6;
+    s.ms_kernel = (h.t_exit - h.t_entry) * 1e-6;
+    s.barriers = h.barriers;
     s.kernel_cycles = c->kernel_cycles;
 }
 
@@ -320,21 +322,60 @@ int dump_slots(maxflow_ctx *c, std::vector<int32_t> &su, std::vector<int32_t> &s
     return MAXFLOW_OK;
 }
 
-// Rebuild the layout with room for every pair named in the batch.
-int rebuild_for_batch(maxflow_ctx *c, const int32_t *hu, const int32_t *hv, int64_t count)
+// Grow the rows on the device so that every row has room for its pending
+// insertions (ins_need[], left by the kernel that reported the overflow) plus
+// fresh slack; flows, capacities and excesses keep their values and the slot
+// order inside each row is kept.
+int rebuild_device(maxflow_ctx *c)
 {
-    std::vector<int32_t> su, sv, scap, scf;
-    MF_TRY(dump_slots(c, su, sv, scap, scf, c->g.cf));
-    MfHostGraph hg;
-    int rc = mf_rebuild_host(c->n, (int64_t)su.size(), su.data(), sv.data(), scap.data(), scf.data(), count, hu, hv,
-                             c->opt.slack_factor, c->opt.slack_min, hg);
-    if (rc == MAXFLOW_OK) rc = upload_graph(c, hg);
-    hg.release();
+    const int32_t n = c->n;
+    MfParams p = base_params(c);
+    long long *noff = dalloc_n<long long>(c, (int64_t)n + 1);
+    if (!noff) return MAXFLOW_ERR_OOM;
+    int rc = mf_rebuild_capacity(p, (void *)c->stream, c->opt.slack_factor, c->opt.slack_min, noff);
+    long long total = 0;
+    if (rc == MAXFLOW_OK)
+        rc = rc_cuda(cudaMemcpyAsync(&total, noff + n, sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+    if (rc == MAXFLOW_OK) rc = rc_cuda(cudaStreamSynchronize(c->stream));
+    if (rc == MAXFLOW_OK && total >= (long long)INT32_MAX - 1) rc = MAXFLOW_ERR_TOO_LARGE;
+    int32_t *off = nullptr, *dst = nullptr, *cf = nullptr, *cap = nullptr, *rev = nullptr, *pcap = nullptr;
     if (rc == MAXFLOW_OK) {
-        c->st.rebuilds++;
-        choose_grid(c);
+        off = dalloc_n<int32_t>(c, (int64_t)n + 1);
+        dst = dalloc_n<int32_t>(c, total);
+        cf = dalloc_n<int32_t>(c, total);
+        cap = dalloc_n<int32_t>(c, total);
+        rev = dalloc_n<int32_t>(c, total);
+        pcap = dalloc_n<int32_t>(c, total);
+        if (!off || !dst || !cf || !cap || !rev || !pcap) rc = MAXFLOW_ERR_OOM;
     }
-    return rc;
+    if (rc == MAXFLOW_OK) rc = mf_rebuild_move(p, (void *)c->stream, noff, off, dst, cf, cap, rev, pcap, total);
+    if (rc == MAXFLOW_OK) rc = rc_cuda(cudaStreamSynchronize(c->stream));
+    if (rc != MAXFLOW_OK) {
+        int32_t *tmp[] = {off, dst, cf, cap, rev, pcap};
+        for (int32_t *q : tmp) dfree(c, q);
+        dfree(c, noff);
+        return rc;
+    }
+    int32_t *old[] = {c->g.off, c->g.dst, c->g.cf, c->g.cap, c->g.rev, c->g.pcap};
+    for (int32_t *q : old) dfree(c, q);
+    dfree(c, noff);
+    c->g.off = off;
+    c->g.dst = dst;
+    c->g.cf = cf;
+    c->g.cap = cap;
+    c->g.rev = rev;
+    c->g.pcap = pcap;
+    c->g.slot_cap = total;
+    dfree(c, c->x_cf);
+    dfree(c, c->x_cf2);
+    c->x_cf = c->x_cf2 = nullptr;
+    dfree(c, c->sc.bitem);
+    c->sc.bitem = dalloc_n<int2>(c, (int64_t)n + total / MF_BFS_CHUNK + 64);
+    if (!c->sc.bitem) return MAXFLOW_ERR_OOM;
+    c->st.slot_capacity = total;
+    c->st.rebuilds++;
+    choose_grid(c);
+    return MAXFLOW_OK;
 }
 
 int check_host_batch(maxflow_ctx *c, const maxflow_batch *b)
@@ -376,18 +417,9 @@ int do_batch(maxflow_ctx *c, const maxflow_batch *b, int mode)
         MF_TRY(run_kernel(c, p, &kerr, &kst));
         if (kerr == MF_E_OVERFLOW) {
             if (attempt == 1) return MAXFLOW_ERR_INTERNAL;
-            // names of the pairs, on the host
-            std::vector<int32_t> hu((size_t)b->count), hv((size_t)b->count);
-            if (b->on_device) {
-                MF_TRY(rc_cuda(cudaMemcpyAsync(hu.data(), b->u, sizeof(int32_t) * b->count, cudaMemcpyDeviceToHost, c->stream)));
-                MF_TRY(rc_cuda(cudaMemcpyAsync(hv.data(), b->v, sizeof(int32_t) * b->count, cudaMemcpyDeviceToHost, c->stream)));
-                MF_TRY(rc_cuda(cudaStreamSynchronize(c->stream)));
-            } else {
-                std::memcpy(hu.data(), b->u, sizeof(int32_t) * b->count);
-                std::memcpy(hv.data(), b->v, sizeof(int32_t) * b->count);
-            }
-            MF_TRY(rebuild_for_batch(c, hu.data(), hv.data(), b->count));
+            MF_TRY(rebuild_device(c));
             p.g = c->g;
+            p.sc = c->sc;
             p.cf = c->g.cf;
             continue;
         }
@@ -617,6 +649,19 @@ int maxflow_query(maxflow_ctx *c, int64_t *value, uint8_t *side, int64_t *cut_ca
         *cut_cap = c->hbuf[0];
     }
     if (value) *value = c->value;
+    return MAXFLOW_OK;
+}
+
+int maxflow_trace(maxflow_ctx *c, int32_t *boundary, double *t_us, int32_t cap, int32_t *count)
+{
+    if (!c || !count || cap < 0) return MAXFLOW_ERR_INVALID;
+    const MfCtrl &h = *c->hctrl;
+    int k = std::min<int>(h.trace_n, std::min<int>(cap, MF_TRACE));
+    for (int i = 0; i < k; ++i) {
+        if (boundary) boundary[i] = h.trace_hook[i];
+        if (t_us) t_us[i] = (double)(h.trace_t[i] - h.t_entry) * 1e-3;
+    }
+    *count = k;
     return MAXFLOW_OK;
 }
 

@@ -237,29 +237,3 @@ int mf_build_host(int32_t n, int64_t m, const int32_t *src, const int32_t *dst, 
     std::vector<SlotRec>().swap(rr);
     return layout(n, rstart, slots, slack_factor, slack_min, out);
 }
-
-int mf_rebuild_host(int32_t n, int64_t nslots, const int32_t *su, const int32_t *sv, const int32_t *scap,
-                    const int32_t *scf, int64_t nextra, const int32_t *xu, const int32_t *xv,
-                    float slack_factor, int32_t slack_min, MfHostGraph &out)
-{
-    std::vector<int32_t> ru;
-    std::vector<SlotRec> rr;
-    ru.reserve((size_t)(nslots + 2 * nextra));
-    rr.reserve((size_t)(nslots + 2 * nextra));
-    for (int64_t i = 0; i < nslots; ++i) {
-        ru.push_back(su[i]);
-        rr.push_back(SlotRec{sv[i], scap[i], scf[i]});
-    }
-    for (int64_t i = 0; i < nextra; ++i) {
-        if (xu[i] == xv[i]) continue;
-        ru.push_back(xu[i]);
-        rr.push_back(SlotRec{xv[i], -1, 0});
-        ru.push_back(xv[i]);
-        rr.push_back(SlotRec{xu[i], -1, 0});
-    }
-    std::vector<int64_t> rstart;
-    std::vector<SlotRec> slots;
-    int rc = group_rows(n, ru, rr, rstart, slots);
-    if (rc != MAXFLOW_OK) return rc;
-    return layout(n, rstart, slots, slack_factor, slack_min, out);
-}

@@ -18,11 +18,12 @@
 
 #define MF_BLOCK 512          // threads per CTA of the persistent kernel
 #define MF_WARPS (MF_BLOCK / 32)
-#define MF_SMALL_DEG 16       // discharge: rows up to this many slots get one thread
-#define MF_HUB_DEG 4096       // discharge: rows above this many slots get a whole CTA
+#define MF_SMALL_DEG 8        // discharge: rows up to this many slots get one thread
+#define MF_HUB_DEG 512        // discharge: rows above this many slots get a whole CTA
 #define MF_BFS_HUB 256        // BFS: rows above this many slots enter the frontier as work items
 #define MF_BFS_CHUNK 256      // BFS: slots per work item
 #define MF_ACTIVE_HIST 64
+#define MF_TRACE 256          // hook timeline entries kept per launch
 
 // Solve-kernel status (ctrl->status)
 #define MF_ST_RUNNING 0
@@ -80,6 +81,12 @@ struct MfCtrl {
     long long slots_bfs, verts_bfs, slots_dis, cycles_dis, slots_fix, verts_fix, verts_wl, n_apply;
     unsigned long long ns_bfs, ns_dis, ns_fix, ns_wl, ns_apply;
     int active_hist[MF_ACTIVE_HIST];
+    // ---- tracing: kernel entry (block 0, before the first barrier), last hook, hook timeline ----
+    unsigned long long t_entry, t_exit;
+    long long barriers;
+    int trace_n;
+    int trace_hook[MF_TRACE];
+    unsigned long long trace_t[MF_TRACE];
 };
 
 struct MfGraph {
@@ -144,12 +151,6 @@ struct MfHostGraph {
 int mf_build_host(int32_t n, int64_t m, const int32_t *src, const int32_t *dst, const int32_t *cap,
                   float slack_factor, int32_t slack_min, MfHostGraph &out);
 
-// Rebuild from a slot dump (u, v, cap, cf per used slot, any order; both
-// directions of every pair present) plus extra zero-capacity pairs.
-int mf_rebuild_host(int32_t n, int64_t nslots, const int32_t *su, const int32_t *sv, const int32_t *scap,
-                    const int32_t *scf, int64_t nextra, const int32_t *xu, const int32_t *xv,
-                    float slack_factor, int32_t slack_min, MfHostGraph &out);
-
 // solver.cu
 int mf_launch(const MfParams &p, int grid, void *stream);
 int mf_max_coresident_blocks(int device, int *per_sm, int *num_sms);
@@ -165,6 +166,11 @@ int mf_launch_aux(int which, const MfParams &p, void *stream, long long *dev_out
 #define MF_AUX_CLEAR_SCRATCH 8    // reset hash tables and ins_need
 #define MF_AUX_DUMP 9             // extra = int32_t* rowid per slot (u of each slot index)
 #define MF_AUX_NEGATE_E 10        // e = -e
+
+// device-side rebuild (rows grow, flows and excesses stay in place)
+int mf_rebuild_capacity(const MfParams &p, void *stream, float slack_factor, int slack_min, long long *noff);
+int mf_rebuild_move(const MfParams &p, void *stream, const long long *noff, int32_t *off, int32_t *dst, int32_t *cf,
+                    int32_t *cap, int32_t *rev, int32_t *pcap, long long slot_cap);
 
 int mf_set_flow_items(const MfParams &p, void *stream, long long *dev_bad, long long count, const int32_t *du,
                       const int32_t *dv, const int32_t *df, int apply);

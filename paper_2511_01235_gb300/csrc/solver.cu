@@ -79,6 +79,19 @@ __device__ __forceinline__ unsigned hash_slot(unsigned long long key, int bits)
     return (unsigned)((key * 0x9E3779B97F4A7C15ull) >> (64 - bits));
 }
 
+// Claim k work items from a shared head; returns the first index (>= cnt when
+// the work is exhausted).  The head is read first so that idle warps do not
+// queue atomics on it once the work is gone.  Call with the whole warp.
+__device__ __forceinline__ int warp_grab(unsigned *head, int cnt, unsigned k)
+{
+    int b = 0;
+    if ((threadIdx.x & 31) == 0) {
+        unsigned cur = *(volatile unsigned *)head;
+        b = (int)(cur >= (unsigned)cnt ? cur : atomicAdd(head, k));
+    }
+    return __shfl_sync(0xffffffffu, b, 0);
+}
+
 // Per-CTA accumulators, flushed to global memory once per phase.
 struct Sh {
     long long sink_e, src_e;
@@ -88,6 +101,7 @@ struct Sh {
     int bcast_h;
     long long bcast_e;
     int ok;
+    unsigned gen;
 };
 
 enum Hook {
@@ -105,16 +119,66 @@ enum Hook {
     H_FINAL,
 };
 
+__device__ __forceinline__ int rd(const int &x) { return __ldcg(&x); }
+__device__ __forceinline__ unsigned rd(const unsigned &x) { return __ldcg(&x); }
+__device__ __forceinline__ long long rd(const long long &x) { return __ldcg(&x); }
+__device__ __forceinline__ unsigned long long rd(const unsigned long long &x) { return __ldcg(&x); }
+
+// The termination test of the loop (Alg. 1 / Alg. 5: stop when no active
+// vertex remains), taken right after a complete backward BFS.
+__device__ __forceinline__ void decide_iteration(const MfParams &P, MfCtrl *c, unsigned long long now,
+                                                 const unsigned (&wl)[4], long long iters,
+                                                 unsigned long long t_start)
+{
+    const int active = (int)wl[3];
+    for (int b = 0; b < 3; ++b) c->wl_n[b] = (int)wl[b];
+    c->head0.w[0] = c->head1.w[0] = c->head2.w[0] = 0;
+    if (iters < MF_ACTIVE_HIST) c->active_hist[iters] = active;
+    if (iters == 0) c->active_first = active;
+    c->active_total = rd(c->active_total) + active;
+    if (active == 0) {
+        c->status = MF_ST_CONVERGED;
+    } else if (iters >= P.max_iters || now - t_start > P.time_limit_ns) {
+        c->status = MF_ST_CAP;
+    } else {
+        c->iters = iters + 1;
+    }
+}
+
 // Executed by the one thread that completes a grid barrier, while every
-// other CTA waits for it.
+// other CTA waits for it.  All fields it needs are loaded first (through L2)
+// so the barrier's critical path holds one memory round trip.
 __device__ __noinline__ void run_hook(const MfParams &P, int hook)
 {
     MfCtrl *c = P.ctrl;
-    unsigned long long now = gtimer();
-    unsigned long long dt = now - c->t_phase;
+    const unsigned long long now = gtimer();
+    const unsigned long long t_phase = rd(c->t_phase);
+    const int trace_n = hook == H_START ? 0 : rd(c->trace_n);
+    const long long barriers = hook == H_START ? 0 : rd(c->barriers);
+    const unsigned bfs_tail = rd(c->bfs_tail.w[0]), item_tail = rd(c->hub_tail.w[0]);
+    const int lvl_hi = rd(c->lvl_hi), hub_hi = rd(c->hub_hi), level = rd(c->level);
+    const long long iters = rd(c->iters), bfs_levels = rd(c->bfs_levels);
+    const unsigned long long t_start = rd(c->t_start);
+    unsigned wl[4], misc[4];
+    for (int i = 0; i < 4; ++i) {
+        wl[i] = rd(c->wl_tail.w[i]);
+        misc[i] = rd(c->misc.w[i]);
+    }
+    unsigned err = rd(c->err.w[0]);
+    const unsigned long long dt = now - t_phase;
+    const bool want_wl = P.data_driven && !(P.mode & MF_M_BFS_ONLY);
+
     c->t_phase = now;
+    c->barriers = barriers + 1;
+    c->t_exit = now;
+    if (trace_n < MF_TRACE) {
+        c->trace_hook[trace_n] = hook;
+        c->trace_t[trace_n] = now;
+    }
+    c->trace_n = trace_n + 1;
     switch (hook) {
     case H_START:
+        err = 0;
         c->err.w[0] = 0;
         c->status = MF_ST_RUNNING;
         c->iters = 0;
@@ -130,88 +194,74 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
         for (int i = 0; i < 8; ++i) c->misc.w[i] = 0;
         for (int i = 0; i < MF_ACTIVE_HIST; ++i) c->active_hist[i] = 0;
         c->t_start = now;
-        c->t_phase = now;
         break;
     case H_APPLY_VALID:
     case H_APPLY_CHECKED:
-        c->ns_apply += dt;
-        if (hook == H_APPLY_CHECKED && c->misc.w[2] != 0 && c->err.w[0] == 0) c->err.w[0] = MF_E_OVERFLOW;
+        c->ns_apply = rd(c->ns_apply) + dt;
+        if (hook == H_APPLY_CHECKED && misc[2] != 0 && err == 0) {
+            err = MF_E_OVERFLOW;
+            c->err.w[0] = err;
+        }
         break;
     case H_APPLY_LOCATED:
-        c->ns_apply += dt;
-        c->ins_n = (int)c->misc.w[0];
+        c->ns_apply = rd(c->ns_apply) + dt;
+        c->ins_n = (int)misc[0];
         break;
     case H_APPLY_DELTA:
-        c->ns_apply += dt;
-        c->touch_n = (int)c->misc.w[1];
+        c->ns_apply = rd(c->ns_apply) + dt;
+        c->touch_n = (int)misc[1];
         break;
     case H_NONE:
-        c->ns_apply += dt;
+        c->ns_apply = rd(c->ns_apply) + dt;
         break;
     case H_ITER:
-        c->ns_fix += dt;
+        c->ns_fix = rd(c->ns_fix) + dt;
         c->bfs_tail.w[0] = 0;
         c->hub_tail.w[0] = 0;
         for (int i = 0; i < 4; ++i) c->wl_tail.w[i] = 0;
         c->head0.w[0] = c->head1.w[0] = c->head2.w[0] = 0;
         break;
     case H_BFS_START:
-        c->ns_bfs += dt;
-        c->level = 0;
-        c->lvl_lo = 0;
-        c->lvl_hi = (int)c->bfs_tail.w[0];
-        c->hub_lo = 0;
-        c->hub_hi = (int)c->hub_tail.w[0];
+    case H_BFS_NEXT: {
+        c->ns_bfs = rd(c->ns_bfs) + dt;
+        const bool first = hook == H_BFS_START;
+        const int lo = first ? 0 : lvl_hi, hlo = first ? 0 : hub_hi;
+        const bool done = lo == (int)bfs_tail && hlo == (int)item_tail;
+        if (!first && !done) c->bfs_levels = bfs_levels + 1;
+        c->level = first ? 0 : level + 1;
+        c->lvl_lo = lo;
+        c->lvl_hi = (int)bfs_tail;
+        c->hub_lo = hlo;
+        c->hub_hi = (int)item_tail;
         c->head0.w[0] = c->head1.w[0] = 0;
-        c->bfs_done = (c->lvl_hi == 0 && c->hub_hi == 0);
-        break;
-    case H_BFS_NEXT:
-        c->ns_bfs += dt;
-        c->bfs_levels += 1;
-        c->level += 1;
-        c->lvl_lo = c->lvl_hi;
-        c->lvl_hi = (int)c->bfs_tail.w[0];
-        c->hub_lo = c->hub_hi;
-        c->hub_hi = (int)c->hub_tail.w[0];
-        c->head0.w[0] = c->head1.w[0] = 0;
-        c->bfs_done = (c->lvl_lo == c->lvl_hi && c->hub_lo == c->hub_hi);
-        break;
-    case H_WL: {
-        c->ns_wl += dt;
-        int active = (int)c->wl_tail.w[3];
-        for (int b = 0; b < 3; ++b) c->wl_n[b] = (int)c->wl_tail.w[b];
-        c->head0.w[0] = c->head1.w[0] = c->head2.w[0] = 0;
-        if (c->iters < MF_ACTIVE_HIST) c->active_hist[c->iters] = active;
-        if (c->iters == 0) c->active_first = active;
-        c->active_total += active;
-        if (active == 0) {
-            c->status = MF_ST_CONVERGED;
-        } else if (c->iters >= P.max_iters || now - c->t_start > P.time_limit_ns) {
-            c->status = MF_ST_CAP;
-        } else {
-            c->iters += 1;
-        }
+        c->bfs_done = done;
+        if (done && want_wl) decide_iteration(P, c, now, wl, iters, t_start);
         break;
     }
+    case H_WL:
+        c->ns_wl = rd(c->ns_wl) + dt;
+        decide_iteration(P, c, now, wl, iters, t_start);
+        break;
     case H_DIS:
-        c->ns_dis += dt;
+        c->ns_dis = rd(c->ns_dis) + dt;
         c->head0.w[0] = c->head1.w[0] = c->head2.w[0] = 0;
         break;
     case H_FINAL:
         break;
     }
-    if (c->err.w[0] != 0) c->status = MF_ST_ERROR;
+    if (err != 0) c->status = MF_ST_ERROR;
 }
 
 // Grid-wide barrier with a hook.  Returns false if this CTA gave up waiting
-// (the caller must return from the kernel at once).
+// (the caller must return from the kernel at once).  Each CTA counts the
+// barrier generations it has passed (sh.gen), so arriving needs no read.
 __device__ bool grid_sync(const MfParams &P, int hook, Sh &sh)
 {
     MfCtrl *c = P.ctrl;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        unsigned gen = ld_acquire(&c->bar_gen.w[0]);
+        const unsigned gen = sh.gen;
         __threadfence();
         unsigned arrived = atomicAdd(&c->bar_count.w[0], 1u) + 1u;
         if (arrived == gridDim.x) {
@@ -224,7 +274,7 @@ __device__ bool grid_sync(const MfParams &P, int hook, Sh &sh)
             unsigned spins = 0;
             while (ld_acquire(&c->bar_gen.w[0]) == gen) {
                 ++spins;
-                if (spins > 16) __nanosleep(spins > 4096 ? 200 : 20);
+                if (spins > 64) __nanosleep(spins > 4096 ? 200 : 32);
                 if ((spins & 31u) == 0) {
                     unsigned long long now = gtimer();
                     if (t0 == 0) {
@@ -238,6 +288,7 @@ __device__ bool grid_sync(const MfParams &P, int hook, Sh &sh)
             }
         }
         __threadfence();
+        sh.gen = gen + 1u;
         sh.ok = ok;
     }
     __syncthreads();
@@ -543,7 +594,9 @@ __device__ __noinline__ void phase_apply_clamp(const MfParams &P, Sh &sh)
     }
 }
 
-__device__ __noinline__ void phase_apply_cleanup(const MfParams &P)
+// keep_need: leave ins_need[] as it is (the rows' demand of spare slots after
+// an overflow; the rebuild that follows reads and clears it).
+__device__ __noinline__ void phase_apply_cleanup(const MfParams &P, bool keep_need)
 {
     MfCtrl *ctl = P.ctrl;
     const int nused = (int)*(volatile unsigned *)&ctl->misc.w[3];
@@ -556,7 +609,7 @@ __device__ __noinline__ void phase_apply_cleanup(const MfParams &P)
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nins; k += gridDim.x * blockDim.x) {
         int pp = __ldcg(P.sc.ins_list + k);
         unsigned long long pk = __ldcg(P.sc.pkey + pp);
-        if (pk != kEmpty) {
+        if (pk != kEmpty && !keep_need) {
             int a = (int)(pk >> 32), b = (int)(pk & 0xffffffffu);
             P.sc.ins_need[a] = 0;
             P.sc.ins_need[b] = 0;
@@ -603,29 +656,94 @@ __device__ __forceinline__ void warp_append(unsigned *tail, int *arr, bool take,
     if (take) arr[base + __popc(m & ((1u << lane) - 1u))] = val;
 }
 
-// A labelled vertex enters the next frontier either as one entry of the
+// Labelled vertices enter the next frontier either as one entry of the
 // regular list (rows of at most MF_BFS_HUB slots, expanded warp-cooperatively)
 // or, for longer rows, as ceil(deg / MF_BFS_CHUNK) work items (first slot,
 // length) that any warp can take: no row is ever walked by one warp alone.
-__device__ __forceinline__ void frontier_push(const MfParams &P, bool take, int z)
+// With with_wl, a labelled vertex that has excess (and is neither the sink
+// nor the source) also joins the worklist of the coming discharge (Sec. 5.2.1
+// O1): it is active exactly when this BFS labels it, so no separate pass over
+// all vertices is needed.
+//
+// Each lane brings R candidates; the four lists (regular frontier, three
+// worklist bins) are reserved with one packed warp scan and one round of
+// atomics, so a warp pays one append round trip per R slots.  Called by the
+// whole warp.
+template <int R>
+__device__ __forceinline__ void frontier_push(const MfParams &P, const bool (&take)[R], const int (&z)[R],
+                                              const int (&d)[R], const long long (&ev)[R], bool with_wl)
 {
     MfCtrl *ctl = P.ctrl;
-    int d = 0;
-    bool big = false;
-    if (take) {
-        d = ldg_cg(P.g.deg + z);
-        big = d > MF_BFS_HUB;
-    }
-    if (big) {
-        const int nch = (d + MF_BFS_CHUNK - 1) / MF_BFS_CHUNK;
-        const int x0 = P.g.off[z];
-        unsigned at = atomicAdd(&ctl->hub_tail.w[0], (unsigned)nch);
-        for (int c = 0; c < nch; ++c) {
-            int len = d - c * MF_BFS_CHUNK;
-            P.sc.bitem[at + c] = make_int2(x0 + c * MF_BFS_CHUNK, len < MF_BFS_CHUNK ? len : MF_BFS_CHUNK);
+    const int lane = threadIdx.x & 31;
+    // per-lane counts packed 8 bits each: [0] regular, [1..3] worklist bins
+    unsigned packed = 0;
+    bool anybig = false;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (!take[r]) continue;
+        const bool big = d[r] > MF_BFS_HUB;
+        anybig |= big;
+        if (!big) packed += 1u;
+        if (with_wl && ev[r] > 0) {
+            const int bin = d[r] <= MF_SMALL_DEG ? 0 : (d[r] <= MF_HUB_DEG ? 1 : 2);
+            packed += 1u << (8 * (bin + 1));
         }
     }
-    warp_append(&ctl->bfs_tail.w[0], P.sc.border, take && !big, z);
+    unsigned incl = packed;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+    const unsigned excl = incl - packed;
+    if (total != 0) {
+        unsigned base[4] = {0, 0, 0, 0};
+        if (lane == 0) {
+            if (total & 0xffu) base[0] = atomicAdd(&ctl->bfs_tail.w[0], total & 0xffu);
+            for (int b = 0; b < 3; ++b) {
+                unsigned k = (total >> (8 * (b + 1))) & 0xffu;
+                if (k) base[b + 1] = atomicAdd(&ctl->wl_tail.w[b], k);
+            }
+            unsigned act = ((total >> 8) & 0xffu) + ((total >> 16) & 0xffu) + ((total >> 24) & 0xffu);
+            if (act) atomicAdd(&ctl->wl_tail.w[3], act);
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b) base[b] = __shfl_sync(0xffffffffu, base[b], 0);
+        unsigned pos[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) pos[b] = base[b] + ((excl >> (8 * b)) & 0xffu);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (!take[r]) continue;
+            if (d[r] <= MF_BFS_HUB) P.sc.border[pos[0]++] = z[r];
+            if (with_wl && ev[r] > 0) {
+                const int bin = d[r] <= MF_SMALL_DEG ? 0 : (d[r] <= MF_HUB_DEG ? 1 : 2);
+                P.sc.wl[bin][pos[bin + 1]++] = z[r];
+            }
+        }
+    }
+    // long rows: the whole warp writes each row's work items
+    unsigned bm = __ballot_sync(0xffffffffu, anybig);
+    while (bm) {
+        const int src = __ffs(bm) - 1;
+        bm &= bm - 1u;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int zz = __shfl_sync(0xffffffffu, z[r], src);
+            const int dd = __shfl_sync(0xffffffffu, take[r] ? d[r] : 0, src);
+            if (dd <= MF_BFS_HUB) continue;
+            const int nch = (dd + MF_BFS_CHUNK - 1) / MF_BFS_CHUNK;
+            unsigned at = 0;
+            if (lane == 0) at = atomicAdd(&ctl->hub_tail.w[0], (unsigned)nch);
+            at = __shfl_sync(0xffffffffu, at, 0);
+            const int x0 = P.g.off[zz];
+            for (int c = lane; c < nch; c += 32) {
+                const int len = dd - c * MF_BFS_CHUNK;
+                P.sc.bitem[at + c] = make_int2(x0 + c * MF_BFS_CHUNK, len < MF_BFS_CHUNK ? len : MF_BFS_CHUNK);
+            }
+        }
+    }
 }
 
 __device__ __noinline__ void phase_bfs_init(const MfParams &P, Sh &sh)
@@ -635,25 +753,32 @@ __device__ __noinline__ void phase_bfs_init(const MfParams &P, Sh &sh)
     const int lane = threadIdx.x & 31;
     const long long gs = (long long)gridDim.x * blockDim.x;
     for (long long base = (long long)blockIdx.x * blockDim.x + threadIdx.x - lane; base < n; base += gs) {
-        int v = (int)base + lane;
-        bool root = false;
+        const int v = (int)base + lane;
+        bool root[1] = {false};
+        int zv[1] = {v}, dv[1] = {0};
+        long long ev[1] = {0};
         if (v < n) {
-            root = (v == P.sink) || (deficit_roots && v != P.source && ldg_cg(P.e + v) < 0);
-            P.h[v] = root ? 0 : n;
+            root[0] = (v == P.sink) || (deficit_roots && v != P.source && ldg_cg(P.e + v) < 0);
+            P.h[v] = root[0] ? 0 : n;
+            if (root[0]) dv[0] = ldg_cg(P.g.deg + v);
         }
-        frontier_push(P, root, v);
+        frontier_push<1>(P, root, zv, dv, ev, false);
     }
 }
 
 // Visit BR slots per lane at level L.  Slot x = (u, z): z gets height L+1 if
 // it is unlabelled, is not the source, and has a residual edge (z, u), i.e.
-// c_f(z, u) = pcap - c_f(u, z) > 0.  The loads of the BR slots are issued
-// together so each lane keeps BR independent gathers in flight.
+// c_f(z, u) = pcap - c_f(u, z) > 0.  Each stage (slot loads, height gathers,
+// claims, degree/excess loads) is issued for all BR slots together, so each
+// lane keeps BR independent requests in flight.
 template <int BR>
 __device__ __forceinline__ void bfs_visit(const MfParams &P, const int (&x)[BR], const bool (&valid)[BR], int L)
 {
+    const bool with_wl = P.data_driven && !(P.mode & MF_M_BFS_ONLY);
     const int n = P.g.n;
-    int z[BR], rc[BR], hz[BR];
+    int z[BR], rc[BR], hz[BR], d[BR];
+    bool claim[BR];
+    long long ev[BR];
 #pragma unroll
     for (int r = 0; r < BR; ++r) {
         z[r] = valid[r] ? ldg_cg(P.g.dst + x[r]) : P.source;
@@ -662,10 +787,13 @@ __device__ __forceinline__ void bfs_visit(const MfParams &P, const int (&x)[BR],
 #pragma unroll
     for (int r = 0; r < BR; ++r) hz[r] = (rc[r] > 0 && z[r] != P.source) ? ldg_cg(P.h + z[r]) : 0;
 #pragma unroll
+    for (int r = 0; r < BR; ++r) claim[r] = hz[r] == n && atomicCAS(P.h + z[r], n, L + 1) == n;
+#pragma unroll
     for (int r = 0; r < BR; ++r) {
-        bool claim = hz[r] == n && atomicCAS(P.h + z[r], n, L + 1) == n;
-        frontier_push(P, claim, z[r]);
+        d[r] = claim[r] ? ldg_cg(P.g.deg + z[r]) : 0;
+        ev[r] = (with_wl && claim[r] && z[r] != P.sink) ? ldg_cg(P.e + z[r]) : 0;
     }
+    frontier_push<BR>(P, claim, z, d, ev, with_wl);
 }
 
 constexpr int kBR = 4;
@@ -679,9 +807,7 @@ __device__ __noinline__ void phase_bfs_level(const MfParams &P, Sh &sh)
     // chunks of long rows: one warp per item (at most MF_BFS_CHUNK slots)
     const int ilo = vrd(&ctl->hub_lo), icnt = vrd(&ctl->hub_hi) - ilo;
     for (;;) {
-        int i = 0;
-        if (lane == 0) i = (int)atomicAdd(&ctl->head1.w[0], 1u);
-        i = __shfl_sync(0xffffffffu, i, 0);
+        const int i = warp_grab(&ctl->head1.w[0], icnt, 1u);
         if (i >= icnt) break;
         const int2 it = __ldcg(P.sc.bitem + ilo + i);
         if (lane == 0) slots += it.y;
@@ -701,9 +827,7 @@ __device__ __noinline__ void phase_bfs_level(const MfParams &P, Sh &sh)
     // rows together (each lane finds the vertex that owns its slot)
     const int lo = vrd(&ctl->lvl_lo), cnt = vrd(&ctl->lvl_hi) - lo;
     for (;;) {
-        int b = 0;
-        if (lane == 0) b = (int)atomicAdd(&ctl->head0.w[0], 32u);
-        b = __shfl_sync(0xffffffffu, b, 0);
+        const int b = warp_grab(&ctl->head0.w[0], cnt, 32u);
         if (b >= cnt) break;
         int idx = b + lane;
         int u = idx < cnt ? __ldcg(P.sc.border + lo + idx) : -1;
@@ -791,8 +915,7 @@ __device__ __forceinline__ void do_push(const MfParams &P, Sh &sh, int u, int x,
 // row at r0, as a key (h(v) << 32 | j) so the minimum also breaks ties by the
 // lowest slot index.  Slots are read kU at a time with their loads issued
 // together.
-constexpr int kU = 4;
-
+template <int kU>
 __device__ __forceinline__ unsigned long long scan_lowest(const MfParams &P, int r0, int d, int j0, int step)
 {
     unsigned long long best = kEmpty;
@@ -817,9 +940,11 @@ __device__ __forceinline__ unsigned long long scan_lowest(const MfParams &P, int
     return best;
 }
 
-// One thread per vertex (rows of at most MF_SMALL_DEG slots).
-__device__ void discharge_thread(const MfParams &P, Sh &sh, int u)
+// One thread per vertex (rows of at most MF_SMALL_DEG slots).  Returns true
+// if u was relabelled (only then can it have steep residual edges, Alg. 3).
+__device__ bool discharge_thread(const MfParams &P, Sh &sh, int u)
 {
+    bool lifted = false;
     const int n = P.g.n;
     const int r0 = P.g.off[u];
     const int d = ldg_cg(P.g.deg + u);
@@ -829,13 +954,14 @@ __device__ void discharge_thread(const MfParams &P, Sh &sh, int u)
         long long eu = ldg_cg(P.e + u);
         if (!(hu < n && eu > 0)) break;
         ++cyc_done;
-        unsigned long long best = scan_lowest(P, r0, d, 0, 1);
+        unsigned long long best = scan_lowest<4>(P, r0, d, 0, 1);
         int best_h = best == kEmpty ? 0x7fffffff : (int)(best >> 32);
         if (best != kEmpty && hu > best_h) {
             do_push(P, sh, u, r0 + (int)(best & 0xffffffffu), eu);
         } else {
             hu = (best == kEmpty || best_h >= n - 1) ? n : best_h + 1;
             P.h[u] = hu;
+            lifted = true;
             atomicAdd((unsigned long long *)&sh.relabels, 1ull);
         }
     }
@@ -843,11 +969,13 @@ __device__ void discharge_thread(const MfParams &P, Sh &sh, int u)
         atomicAdd((unsigned long long *)&sh.cycles, (unsigned long long)cyc_done);
         atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)(cyc_done * d));
     }
+    return lifted;
 }
 
-// One warp per vertex.
-__device__ void discharge_warp(const MfParams &P, Sh &sh, int u)
+// One warp per vertex (returns the same value in every lane).
+__device__ bool discharge_warp(const MfParams &P, Sh &sh, int u)
 {
+    bool lifted = false;
     const int n = P.g.n;
     const int lane = threadIdx.x & 31;
     const int r0 = P.g.off[u];
@@ -858,12 +986,13 @@ __device__ void discharge_warp(const MfParams &P, Sh &sh, int u)
         long long eu = ldg_cg(P.e + u);
         if (!(hu < n && eu > 0)) break;
         ++cyc_done;
-        unsigned long long best = warp_min_u64(scan_lowest(P, r0, d, lane, 32));
+        unsigned long long best = warp_min_u64(scan_lowest<8>(P, r0, d, lane, 32));
         int best_h = best == kEmpty ? 0x7fffffff : (int)(best >> 32);
         if (best != kEmpty && hu > best_h) {
             if (lane == 0) do_push(P, sh, u, r0 + (int)(best & 0xffffffffu), eu);
         } else {
             hu = (best == kEmpty || best_h >= n - 1) ? n : best_h + 1;
+            lifted = true;
             if (lane == 0) {
                 P.h[u] = hu;
                 atomicAdd((unsigned long long *)&sh.relabels, 1ull);
@@ -875,11 +1004,14 @@ __device__ void discharge_warp(const MfParams &P, Sh &sh, int u)
         atomicAdd((unsigned long long *)&sh.cycles, (unsigned long long)cyc_done);
         atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)(cyc_done * d));
     }
+    return lifted;
 }
 
-// One CTA per vertex (hubs).  All threads of the CTA call this together.
-__device__ void discharge_cta(const MfParams &P, Sh &sh, int u)
+// One CTA per vertex (hubs).  All threads of the CTA call this together;
+// the return value is meaningful in thread 0.
+__device__ bool discharge_cta(const MfParams &P, Sh &sh, int u)
 {
+    bool lifted = false;
     const int n = P.g.n;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int r0 = P.g.off[u];
@@ -896,7 +1028,7 @@ __device__ void discharge_cta(const MfParams &P, Sh &sh, int u)
             __syncthreads();
             break;
         }
-        unsigned long long best = warp_min_u64(scan_lowest(P, r0, d, threadIdx.x, blockDim.x));
+        unsigned long long best = warp_min_u64(scan_lowest<8>(P, r0, d, threadIdx.x, blockDim.x));
         if (lane == 0) sh.red[wid] = best;
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -907,6 +1039,7 @@ __device__ void discharge_cta(const MfParams &P, Sh &sh, int u)
                 do_push(P, sh, u, r0 + (int)(b & 0xffffffffu), eu);
             } else {
                 P.h[u] = (b == kEmpty || best_h >= n - 1) ? n : best_h + 1;
+                lifted = true;
                 atomicAdd((unsigned long long *)&sh.relabels, 1ull);
             }
             atomicAdd((unsigned long long *)&sh.cycles, 1ull);
@@ -914,6 +1047,7 @@ __device__ void discharge_cta(const MfParams &P, Sh &sh, int u)
         }
         __syncthreads();
     }
+    return lifted;
 }
 
 __device__ __noinline__ void phase_discharge(const MfParams &P, Sh &sh)
@@ -923,30 +1057,34 @@ __device__ __noinline__ void phase_discharge(const MfParams &P, Sh &sh)
     // hubs: one CTA each
     const int nh = vrd(&ctl->wl_n[2]);
     for (;;) {
-        if (threadIdx.x == 0) sh.bcast_i = (int)atomicAdd(&ctl->head2.w[0], 1u);
+        if (threadIdx.x == 0) {
+            unsigned cur = *(volatile unsigned *)&ctl->head2.w[0];
+            sh.bcast_i = (int)(cur >= (unsigned)nh ? cur : atomicAdd(&ctl->head2.w[0], 1u));
+        }
         __syncthreads();
         int i = sh.bcast_i;
         __syncthreads();
         if (i >= nh) break;
-        discharge_cta(P, sh, __ldcg(P.sc.wl[2] + i));
+        const int u = __ldcg(P.sc.wl[2] + i);
+        if (discharge_cta(P, sh, u) && threadIdx.x == 0) P.sc.wl[2][i] = ~u;
     }
     // mid-degree rows: one warp each
     const int nm = vrd(&ctl->wl_n[1]);
     for (;;) {
-        int i = 0;
-        if (lane == 0) i = (int)atomicAdd(&ctl->head1.w[0], 1u);
-        i = __shfl_sync(0xffffffffu, i, 0);
+        const int i = warp_grab(&ctl->head1.w[0], nm, 1u);
         if (i >= nm) break;
-        discharge_warp(P, sh, __ldcg(P.sc.wl[1] + i));
+        const int u = __ldcg(P.sc.wl[1] + i);
+        if (discharge_warp(P, sh, u) && lane == 0) P.sc.wl[1][i] = ~u;
     }
     // small rows: one thread each, 32 per grab
     const int ns = vrd(&ctl->wl_n[0]);
     for (;;) {
-        int b = 0;
-        if (lane == 0) b = (int)atomicAdd(&ctl->head0.w[0], 32u);
-        b = __shfl_sync(0xffffffffu, b, 0);
+        const int b = warp_grab(&ctl->head0.w[0], ns, 32u);
         if (b >= ns) break;
-        if (b + lane < ns) discharge_thread(P, sh, __ldcg(P.sc.wl[0] + b + lane));
+        if (b + lane < ns) {
+            const int u = __ldcg(P.sc.wl[0] + b + lane);
+            if (discharge_thread(P, sh, u)) P.sc.wl[0][b + lane] = ~u;
+        }
     }
 }
 
@@ -954,19 +1092,39 @@ __device__ __noinline__ void phase_discharge(const MfParams &P, Sh &sh)
 // Remove invalid edges (Alg. 3)
 // ---------------------------------------------------------------------------
 
-// Push the whole residual of every steep slot of u (h(u) > h(v) + 1).
-__device__ __forceinline__ long long fix_slot(const MfParams &P, Sh &sh, int hu, int x)
+// Alg. 3 on slots j = j0, j0 + step, ... of u's row: push the whole residual
+// of every steep slot (h(u) > h(v) + 1).  Returns the flow sent out of u.
+// Only vertices relabelled in the discharge can have steep slots (heights are
+// exact after the BFS and neighbours only rise), so only those are scanned.
+__device__ __forceinline__ long long fix_scan(const MfParams &P, Sh &sh, int hu, int r0, int d, int j0, int step)
 {
-    int c = ldg_cg(P.cf + x);
-    if (c <= 0) return 0;
-    int z = ldg_cg(P.g.dst + x);
-    if (!(hu > ldg_cg(P.h + z) + 1)) return 0;
-    int old = atomicExch(P.cf + x, 0);
-    if (old <= 0) return 0;
-    atomicAdd(P.cf + ldg_cg(P.g.rev + x), old);
-    add_excess(P, sh, z, (long long)old);
-    atomicAdd((unsigned long long *)&sh.steep, 1ull);
-    return old;
+    constexpr int kF = 4;
+    long long out = 0;
+    for (int jb = j0; jb < d; jb += step * kF) {
+        int c[kF], z[kF], hz[kF];
+#pragma unroll
+        for (int r = 0; r < kF; ++r) {
+            const int j = jb + r * step;
+            c[r] = j < d ? ldg_cg(P.cf + r0 + j) : 0;
+            z[r] = j < d ? ldg_cg(P.g.dst + r0 + j) : 0;
+        }
+#pragma unroll
+        for (int r = 0; r < kF; ++r) hz[r] = c[r] > 0 ? ldg_cg(P.h + z[r]) : 0x7fffffff;
+#pragma unroll
+        for (int r = 0; r < kF; ++r) {
+            if (c[r] > 0 && hu > hz[r] + 1) {
+                const int x = r0 + jb + r * step;
+                const int old = atomicExch(P.cf + x, 0);
+                if (old > 0) {
+                    atomicAdd(P.cf + ldg_cg(P.g.rev + x), old);
+                    add_excess(P, sh, z[r], (long long)old);
+                    atomicAdd((unsigned long long *)&sh.steep, 1ull);
+                    out += old;
+                }
+            }
+        }
+    }
+    return out;
 }
 
 __device__ __noinline__ void phase_fix(const MfParams &P, Sh &sh)
@@ -977,32 +1135,34 @@ __device__ __noinline__ void phase_fix(const MfParams &P, Sh &sh)
     // hubs: one CTA each
     const int nh = vrd(&ctl->wl_n[2]);
     for (;;) {
-        if (threadIdx.x == 0) sh.bcast_i = (int)atomicAdd(&ctl->head2.w[0], 1u);
+        if (threadIdx.x == 0) {
+            unsigned cur = *(volatile unsigned *)&ctl->head2.w[0];
+            sh.bcast_i = (int)(cur >= (unsigned)nh ? cur : atomicAdd(&ctl->head2.w[0], 1u));
+        }
         __syncthreads();
         int i = sh.bcast_i;
         __syncthreads();
         if (i >= nh) break;
-        int u = __ldcg(P.sc.wl[2] + i);
-        int hu = ldg_cg(P.h + u);
-        int r0 = P.g.off[u], d = ldg_cg(P.g.deg + u);
-        long long out = 0;
-        for (int j = threadIdx.x; j < d; j += blockDim.x) out += fix_slot(P, sh, hu, r0 + j);
+        const int ent = __ldcg(P.sc.wl[2] + i);
+        if (ent >= 0) continue;
+        const int u = ~ent;
+        const int hu = ldg_cg(P.h + u);
+        const int r0 = P.g.off[u], d = ldg_cg(P.g.deg + u);
+        long long out = fix_scan(P, sh, hu, r0, d, threadIdx.x, blockDim.x);
         if (out) atomic_add_ll(P.e + u, -out);
         if (threadIdx.x == 0) { slots += d; ++verts; }
     }
     // mid rows: warp per vertex
     const int nm = vrd(&ctl->wl_n[1]);
     for (;;) {
-        int i = 0;
-        if (lane == 0) i = (int)atomicAdd(&ctl->head1.w[0], 1u);
-        i = __shfl_sync(0xffffffffu, i, 0);
+        const int i = warp_grab(&ctl->head1.w[0], nm, 1u);
         if (i >= nm) break;
-        int u = __ldcg(P.sc.wl[1] + i);
-        int hu = ldg_cg(P.h + u);
-        int r0 = P.g.off[u], d = ldg_cg(P.g.deg + u);
-        long long out = 0;
-        for (int j = lane; j < d; j += 32) out += fix_slot(P, sh, hu, r0 + j);
-        out = warp_sum_ll(out);
+        const int ent = __ldcg(P.sc.wl[1] + i);
+        if (ent >= 0) continue;
+        const int u = ~ent;
+        const int hu = ldg_cg(P.h + u);
+        const int r0 = P.g.off[u], d = ldg_cg(P.g.deg + u);
+        long long out = warp_sum_ll(fix_scan(P, sh, hu, r0, d, lane, 32));
         if (lane == 0) {
             if (out) atomic_add_ll(P.e + u, -out);
             slots += d;
@@ -1012,19 +1172,19 @@ __device__ __noinline__ void phase_fix(const MfParams &P, Sh &sh)
     // small rows: thread per vertex
     const int ns = vrd(&ctl->wl_n[0]);
     for (;;) {
-        int b = 0;
-        if (lane == 0) b = (int)atomicAdd(&ctl->head0.w[0], 32u);
-        b = __shfl_sync(0xffffffffu, b, 0);
+        const int b = warp_grab(&ctl->head0.w[0], ns, 32u);
         if (b >= ns) break;
         if (b + lane < ns) {
-            int u = __ldcg(P.sc.wl[0] + b + lane);
-            int hu = ldg_cg(P.h + u);
-            int r0 = P.g.off[u], d = ldg_cg(P.g.deg + u);
-            long long out = 0;
-            for (int j = 0; j < d; ++j) out += fix_slot(P, sh, hu, r0 + j);
-            if (out) atomic_add_ll(P.e + u, -out);
-            slots += d;
-            ++verts;
+            const int ent = __ldcg(P.sc.wl[0] + b + lane);
+            if (ent < 0) {
+                const int u = ~ent;
+                const int hu = ldg_cg(P.h + u);
+                const int r0 = P.g.off[u], d = ldg_cg(P.g.deg + u);
+                long long out = fix_scan(P, sh, hu, r0, d, 0, 1);
+                if (out) atomic_add_ll(P.e + u, -out);
+                slots += d;
+                ++verts;
+            }
         }
     }
     if (slots) atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)slots);
@@ -1048,7 +1208,9 @@ __device__ __noinline__ void phase_value(const MfParams &P)
 __global__ void __launch_bounds__(MF_BLOCK, 1) mf_solve_kernel(MfParams P)
 {
     __shared__ Sh sh;
+    if (blockIdx.x == 0 && threadIdx.x == 0) P.ctrl->t_entry = gtimer();
     if (threadIdx.x == 0) {
+        sh.gen = ld_acquire(&P.ctrl->bar_gen.w[0]);   // nobody can pass the first barrier before all have read it
         sh.sink_e = sh.src_e = 0;
         sh.pushes = sh.relabels = sh.steep = sh.slots = sh.verts = sh.cycles = 0;
     }
@@ -1065,7 +1227,7 @@ __global__ void __launch_bounds__(MF_BLOCK, 1) mf_solve_kernel(MfParams P)
         phase_apply_validate(P);
         if (!grid_sync(P, H_APPLY_VALID, sh)) return;
         if (status_of(P) != MF_ST_RUNNING) {
-            phase_apply_cleanup(P);
+            phase_apply_cleanup(P, false);
             grid_sync(P, H_FINAL, sh);
             return;
         }
@@ -1074,7 +1236,7 @@ __global__ void __launch_bounds__(MF_BLOCK, 1) mf_solve_kernel(MfParams P)
         phase_apply_check(P);
         if (!grid_sync(P, H_APPLY_CHECKED, sh)) return;
         if (status_of(P) != MF_ST_RUNNING) {
-            phase_apply_cleanup(P);
+            phase_apply_cleanup(P, true);
             grid_sync(P, H_FINAL, sh);
             return;
         }
@@ -1084,7 +1246,7 @@ __global__ void __launch_bounds__(MF_BLOCK, 1) mf_solve_kernel(MfParams P)
         flush_acc(P, sh, 4);
         if (!grid_sync(P, H_APPLY_DELTA, sh)) return;
         phase_apply_clamp(P, sh);
-        phase_apply_cleanup(P);
+        phase_apply_cleanup(P, false);
         flush_acc(P, sh, 4);
         if (!grid_sync(P, H_NONE, sh)) return;
         if (!(P.mode & MF_M_SKIP_SOURCE_SAT)) {
@@ -1107,9 +1269,11 @@ __global__ void __launch_bounds__(MF_BLOCK, 1) mf_solve_kernel(MfParams P)
             if (!grid_sync(P, H_BFS_NEXT, sh)) return;
         }
         if (P.mode & MF_M_BFS_ONLY) return;
-        // worklist and termination test
-        phase_worklist(P, sh);
-        if (!grid_sync(P, H_WL, sh)) return;
+        // worklist and termination test (built during the BFS when data-driven)
+        if (!P.data_driven) {
+            phase_worklist(P, sh);
+            if (!grid_sync(P, H_WL, sh)) return;
+        }
         if (status_of(P) != MF_ST_RUNNING) break;
         // discharge and remove-invalid-edges
         phase_discharge(P, sh);
@@ -1252,6 +1416,96 @@ __global__ void k_negate(long long *e, int n)
         e[v] = -e[v];
 }
 
+// ---- device-side rebuild of the layout (rows grow; nothing moves to the host) ----
+
+// New reserved size of every row: used slots + pending insertions + slack.
+__global__ void k_row_capacity(MfParams P, float slack_factor, int slack_min, long long *cap_out)
+{
+    for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < P.g.n; u += (long long)gridDim.x * blockDim.x) {
+        long long need = (long long)P.g.deg[u] + P.sc.ins_need[u];
+        double want = (double)need * (double)slack_factor;
+        long long sl = (long long)want;
+        if ((double)sl < want) ++sl;
+        if (sl < slack_min) sl = slack_min;
+        if (sl > (1 << 24)) sl = 1 << 24;
+        cap_out[u] = need + sl;
+    }
+}
+
+// Exclusive scan of n int64 values in place, by one CTA of 1024 threads
+// (rows are few enough that a single pass over them is a few microseconds
+// per million vertices); writes the total to out[n].
+__global__ void __launch_bounds__(1024) k_scan_single(long long *a, long long n)
+{
+    __shared__ long long part[1024];
+    const long long per = (n + blockDim.x - 1) / blockDim.x;
+    const long long lo = threadIdx.x * per, hi = lo + per < n ? lo + per : n;
+    long long sum = 0;
+    for (long long i = lo; i < hi; ++i) sum += a[i];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long run = 0;
+        for (int k = 0; k < (int)blockDim.x; ++k) {
+            long long v = part[k];
+            part[k] = run;
+            run += v;
+        }
+        a[n] = run;
+    }
+    __syncthreads();
+    long long run = part[threadIdx.x];
+    for (long long i = lo; i < hi; ++i) {
+        long long v = a[i];
+        a[i] = run;
+        run += v;
+    }
+}
+
+struct MoveOut {
+    const long long *noff;   // new row starts (int64, n + 1)
+    int32_t *off, *dst, *cf, *cap, *rev, *pcap;   // new arrays
+    long long slot_cap;
+};
+
+// Copy every row to its new place; the reverse index of slot (u, v) moves with
+// row v: new_rev = new_off[v] + (rev - old_off[v]).
+__global__ void k_move_rows(MfParams P, MoveOut M)
+{
+    const int lane = threadIdx.x & 31;
+    for (long long u = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < P.g.n;
+         u += ((long long)gridDim.x * blockDim.x) >> 5) {
+        const int o0 = P.g.off[u], d = P.g.deg[u];
+        const int n0 = (int)M.noff[u], n1 = (int)M.noff[u + 1];
+        if (lane == 0) M.off[u] = n0;
+        for (int j = lane; j < n1 - n0; j += 32) {
+            const int y = n0 + j;
+            if (j < d) {
+                const int x = o0 + j;
+                const int v = P.g.dst[x];
+                M.dst[y] = v;
+                M.cf[y] = P.g.cf[x];
+                M.cap[y] = P.g.cap[x];
+                M.pcap[y] = P.g.pcap[x];
+                M.rev[y] = (int)M.noff[v] + (P.g.rev[x] - P.g.off[v]);
+            } else {
+                M.dst[y] = (int)u;
+                M.cf[y] = 0;
+                M.cap[y] = 0;
+                M.pcap[y] = 0;
+                M.rev[y] = y;
+            }
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) M.off[P.g.n] = (int)M.noff[P.g.n];
+}
+
+__global__ void k_clear_need(MfParams P)
+{
+    for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < P.g.n; u += (long long)gridDim.x * blockDim.x)
+        P.sc.ins_need[u] = 0;
+}
+
 inline int cuda_rc(cudaError_t e) { return e == cudaSuccess ? MAXFLOW_OK : MAXFLOW_ERR_CUDA; }
 
 }  // namespace
@@ -1339,4 +1593,34 @@ int mf_set_flow_items(const MfParams &p, void *stream, long long *dev_bad, long 
 {
     FlowItems f{count, du, dv, df, apply};
     return mf_launch_aux(MF_AUX_SET_FLOW, p, stream, dev_bad, &f);
+}
+
+int mf_rebuild_capacity(const MfParams &p, void *stream, float slack_factor, int slack_min, long long *noff)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    int g = (int)((p.g.n + 255) / 256);
+    if (g > 65535) g = 65535;
+    if (g < 1) g = 1;
+    k_row_capacity<<<g, 256, 0, st>>>(p, slack_factor, slack_min, noff);
+    if (cudaGetLastError() != cudaSuccess) return MAXFLOW_ERR_CUDA;
+    k_scan_single<<<1, 1024, 0, st>>>(noff, p.g.n);
+    return cuda_rc(cudaGetLastError());
+}
+
+int mf_rebuild_move(const MfParams &p, void *stream, const long long *noff, int32_t *off, int32_t *dst, int32_t *cf,
+                    int32_t *cap, int32_t *rev, int32_t *pcap, long long slot_cap)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    MoveOut M{noff, off, dst, cf, cap, rev, pcap, slot_cap};
+    long long thr = (long long)p.g.n * 32;
+    int g = (int)((thr + 255) / 256);
+    if (g > 65535) g = 65535;
+    if (g < 1) g = 1;
+    k_move_rows<<<g, 256, 0, st>>>(p, M);
+    if (cudaGetLastError() != cudaSuccess) return MAXFLOW_ERR_CUDA;
+    int gv = (int)((p.g.n + 255) / 256);
+    if (gv > 65535) gv = 65535;
+    if (gv < 1) gv = 1;
+    k_clear_need<<<gv, 256, 0, st>>>(p);
+    return cuda_rc(cudaGetLastError());
 }

@@ -68,7 +68,7 @@ class Stats(C.Structure):
                 ("bytes_worklist", C.c_int64), ("bytes_apply", C.c_int64),
                 ("ms_last", C.c_double), ("ms_bfs", C.c_double), ("ms_discharge", C.c_double),
                 ("ms_fix", C.c_double), ("ms_worklist", C.c_double), ("ms_apply", C.c_double),
-                ("value", C.c_int64)]
+                ("value", C.c_int64), ("ms_kernel", C.c_double), ("barriers", C.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -77,7 +77,10 @@ class Stats(C.Structure):
 EXPORTS = ["maxflow_default_opts", "maxflow_init", "maxflow_update", "maxflow_query", "maxflow_resolve_static",
            "maxflow_get_flow", "maxflow_stats", "maxflow_destroy", "maxflow_strerror", "maxflow_set_flow",
            "maxflow_apply", "maxflow_global_relabel", "maxflow_resolve", "maxflow_get_residual",
-           "maxflow_get_vertex_state", "maxflow_check", "maxflow_global_relabel_noalloc"]
+           "maxflow_get_vertex_state", "maxflow_check", "maxflow_global_relabel_noalloc", "maxflow_trace"]
+
+TRACE_NAMES = ["start", "prologue", "batch_validated", "batch_located", "room_checked", "capacities_changed",
+               "iteration_start", "bfs_roots", "bfs_level", "worklist", "discharge", "end"]
 
 _lib = None
 
@@ -115,6 +118,7 @@ def load(build_if_missing: bool = False):
     L.maxflow_set_flow.argtypes = [vp, i64, vp, vp, vp]
     L.maxflow_stats.argtypes = [vp, P(Stats)]
     L.maxflow_check.argtypes = [vp, vp]
+    L.maxflow_trace.argtypes = [vp, vp, vp, i32, P(i32)]
     L.maxflow_global_relabel_noalloc.argtypes = [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, i32, vp]
     L.maxflow_destroy.argtypes = [vp]
     L.maxflow_destroy.restype = None
@@ -290,6 +294,16 @@ def maxflow_global_relabel_noalloc(n, s, t, off, deg, dst, cf, pcap, e, h, defic
                                                       int(bool(deficit_roots)), stream))
 
 
+def maxflow_trace(h, cap: int = 256):
+    """(boundary names, microseconds after kernel entry) of the last solve kernel's grid barriers."""
+    b = np.zeros(cap, np.int32)
+    t = np.zeros(cap, np.float64)
+    k = C.c_int32(0)
+    _check(load().maxflow_trace(h, _p(b), _p(t), cap, C.byref(k)), "maxflow_trace")
+    k = int(k.value)
+    return [TRACE_NAMES[i] if 0 <= i < len(TRACE_NAMES) else str(i) for i in b[:k]], t[:k]
+
+
 def maxflow_destroy(h):
     if h:
         load().maxflow_destroy(h)
@@ -381,3 +395,6 @@ class Solver:
 
     def check(self) -> dict:
         return maxflow_check(self.h)
+
+    def trace(self):
+        return maxflow_trace(self.h)
