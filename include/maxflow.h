@@ -156,6 +156,18 @@ int maxflow_resolve_static(maxflow_ctx *c);
  * capacity cap[i] carries flow[i], 0 <= flow[i] <= cap[i]. */
 int maxflow_get_flow(maxflow_ctx *c, int64_t *count, int32_t *u, int32_t *v, int32_t *cap, int32_t *flow);
 
+/* Set KERNEL_CYCLES (Alg. 2) for the following solves: k >= 1, or 0 for the
+ * average-degree heuristic of Sec. 6.1.  The global-relabel frequency of the
+ * paper follows from it (Sec. 6.1: too low means many BFS, too high sends flow
+ * the wrong way). */
+int maxflow_set_kernel_cycles(maxflow_ctx *c, int32_t k);
+
+/* A deep copy of the context's state (graph, residual capacities, heights,
+ * excesses, value) on the same device and stream, as a new context; used to
+ * try several schedules from one state and to checkpoint a dynamic graph
+ * (the dynamic algorithm resumes from any saved state, Sec. 4.2). */
+int maxflow_clone(maxflow_ctx *c, maxflow_ctx **out);
+
 /* Counters and timings of the context and of its last solve. */
 int maxflow_stats(maxflow_ctx *c, maxflow_stats_t *out);
 

@@ -665,6 +665,93 @@ int maxflow_trace(maxflow_ctx *c, int32_t *boundary, double *t_us, int32_t cap, 
     return MAXFLOW_OK;
 }
 
+int maxflow_set_kernel_cycles(maxflow_ctx *c, int32_t k)
+{
+    if (!c || k < 0) return MAXFLOW_ERR_INVALID;
+    int64_t m = c->st.m_edges;
+    c->kernel_cycles = k > 0 ? k : (int32_t)std::max<int64_t>(1, (m + c->n - 1) / c->n);
+    c->st.kernel_cycles = c->kernel_cycles;
+    return MAXFLOW_OK;
+}
+
+int maxflow_clone(maxflow_ctx *src, maxflow_ctx **out)
+{
+    if (!src || !out) return MAXFLOW_ERR_INVALID;
+    *out = nullptr;
+    DeviceGuard dg(src->device);
+    if (!dg.ok) return MAXFLOW_ERR_CUDA;
+    maxflow_ctx *c = new (std::nothrow) maxflow_ctx();
+    if (!c) return MAXFLOW_ERR_OOM;
+    c->opt = src->opt;
+    c->device = src->device;
+    c->stream = src->stream;
+    c->n = src->n;
+    c->s = src->s;
+    c->t = src->t;
+    c->kernel_cycles = src->kernel_cycles;
+    c->per_sm = src->per_sm;
+    c->sms = src->sms;
+    c->st = src->st;
+    c->solved = src->solved;
+    c->value = src->value;
+    const int32_t n = c->n;
+    const int64_t S = src->g.slot_cap;
+    int rc = rc_cuda(cudaEventCreate(&c->ev0));
+    if (rc == MAXFLOW_OK) rc = rc_cuda(cudaEventCreate(&c->ev1));
+    if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMallocHost((void **)&c->hctrl, sizeof(MfCtrl)));
+    if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMallocHost((void **)&c->hbuf, 16 * sizeof(long long)));
+    if (rc == MAXFLOW_OK) {
+        c->g.n = n;
+        c->g.slot_cap = S;
+        c->g.off = dalloc_n<int32_t>(c, n + 1);
+        c->g.deg = dalloc_n<int32_t>(c, n);
+        c->g.bdeg = dalloc_n<int32_t>(c, n);
+        c->g.dst = dalloc_n<int32_t>(c, S);
+        c->g.cf = dalloc_n<int32_t>(c, S);
+        c->g.cap = dalloc_n<int32_t>(c, S);
+        c->g.rev = dalloc_n<int32_t>(c, S);
+        c->g.pcap = dalloc_n<int32_t>(c, S);
+        c->g.h = dalloc_n<int32_t>(c, n);
+        c->g.e = dalloc_n<long long>(c, n);
+        c->sc.border = dalloc_n<int32_t>(c, n);
+        c->sc.bitem = dalloc_n<int2>(c, (int64_t)n + S / MF_BFS_CHUNK + 64);
+        for (int b = 0; b < 3; ++b) c->sc.wl[b] = dalloc_n<int32_t>(c, n);
+        c->sc.ins_need = dalloc_n<int32_t>(c, n);
+        c->ctrl = (MfCtrl *)dalloc(c, sizeof(MfCtrl));
+        c->dbuf = dalloc_n<long long>(c, 16);
+        if (!c->g.off || !c->g.deg || !c->g.bdeg || !c->g.dst || !c->g.cf || !c->g.cap || !c->g.rev || !c->g.pcap ||
+            !c->g.h || !c->g.e || !c->sc.border || !c->sc.bitem || !c->sc.wl[0] || !c->sc.wl[1] || !c->sc.wl[2] ||
+            !c->sc.ins_need || !c->ctrl || !c->dbuf)
+            rc = MAXFLOW_ERR_OOM;
+    }
+    struct Cp { void *d; const void *s; size_t b; };
+    if (rc == MAXFLOW_OK) {
+        const Cp cps[] = {{c->g.off, src->g.off, sizeof(int32_t) * (size_t)(n + 1)},
+                          {c->g.deg, src->g.deg, sizeof(int32_t) * (size_t)n},
+                          {c->g.bdeg, src->g.bdeg, sizeof(int32_t) * (size_t)n},
+                          {c->g.dst, src->g.dst, sizeof(int32_t) * (size_t)S},
+                          {c->g.cf, src->g.cf, sizeof(int32_t) * (size_t)S},
+                          {c->g.cap, src->g.cap, sizeof(int32_t) * (size_t)S},
+                          {c->g.rev, src->g.rev, sizeof(int32_t) * (size_t)S},
+                          {c->g.pcap, src->g.pcap, sizeof(int32_t) * (size_t)S},
+                          {c->g.h, src->g.h, sizeof(int32_t) * (size_t)n},
+                          {c->g.e, src->g.e, sizeof(long long) * (size_t)n}};
+        for (const Cp &cp : cps)
+            if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMemcpyAsync(cp.d, cp.s, cp.b, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMemsetAsync(c->sc.ins_need, 0, sizeof(int32_t) * n, c->stream));
+    if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMemsetAsync(c->ctrl, 0, sizeof(MfCtrl), c->stream));
+    if (rc == MAXFLOW_OK) rc = ensure_batch(c, std::max<int64_t>(1024, src->sc.batch_cap));
+    if (rc == MAXFLOW_OK) rc = rc_cuda(cudaStreamSynchronize(c->stream));
+    if (rc != MAXFLOW_OK) {
+        maxflow_destroy(c);
+        return rc;
+    }
+    c->grid = src->grid;
+    *out = c;
+    return MAXFLOW_OK;
+}
+
 int maxflow_stats(maxflow_ctx *c, maxflow_stats_t *out)
 {
     if (!c || !out) return MAXFLOW_ERR_INVALID;

@@ -77,7 +77,8 @@ class Stats(C.Structure):
 EXPORTS = ["maxflow_default_opts", "maxflow_init", "maxflow_update", "maxflow_query", "maxflow_resolve_static",
            "maxflow_get_flow", "maxflow_stats", "maxflow_destroy", "maxflow_strerror", "maxflow_set_flow",
            "maxflow_apply", "maxflow_global_relabel", "maxflow_resolve", "maxflow_get_residual",
-           "maxflow_get_vertex_state", "maxflow_check", "maxflow_global_relabel_noalloc", "maxflow_trace"]
+           "maxflow_get_vertex_state", "maxflow_check", "maxflow_global_relabel_noalloc", "maxflow_trace",
+           "maxflow_set_kernel_cycles", "maxflow_clone"]
 
 TRACE_NAMES = ["start", "prologue", "batch_validated", "batch_located", "room_checked", "capacities_changed",
                "iteration_start", "bfs_roots", "bfs_level", "worklist", "discharge", "end"]
@@ -119,6 +120,8 @@ def load(build_if_missing: bool = False):
     L.maxflow_stats.argtypes = [vp, P(Stats)]
     L.maxflow_check.argtypes = [vp, vp]
     L.maxflow_trace.argtypes = [vp, vp, vp, i32, P(i32)]
+    L.maxflow_set_kernel_cycles.argtypes = [vp, i32]
+    L.maxflow_clone.argtypes = [vp, P(vp)]
     L.maxflow_global_relabel_noalloc.argtypes = [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, i32, vp]
     L.maxflow_destroy.argtypes = [vp]
     L.maxflow_destroy.restype = None
@@ -304,6 +307,16 @@ def maxflow_trace(h, cap: int = 256):
     return [TRACE_NAMES[i] if 0 <= i < len(TRACE_NAMES) else str(i) for i in b[:k]], t[:k]
 
 
+def maxflow_set_kernel_cycles(h, k: int):
+    _check(load().maxflow_set_kernel_cycles(h, int(k)), "maxflow_set_kernel_cycles")
+
+
+def maxflow_clone(h):
+    out = C.c_void_p()
+    _check(load().maxflow_clone(h, C.byref(out)), "maxflow_clone")
+    return out
+
+
 def maxflow_destroy(h):
     if h:
         load().maxflow_destroy(h)
@@ -398,3 +411,15 @@ class Solver:
 
     def trace(self):
         return maxflow_trace(self.h)
+
+    def set_kernel_cycles(self, k: int):
+        maxflow_set_kernel_cycles(self.h, k)
+
+    def clone(self) -> "Solver":
+        """A deep copy of this instance's device state (same device, stream and allocator)."""
+        other = Solver.__new__(Solver)
+        other.n, other.s, other.t = self.n, self.s, self.t
+        other.device, other.stream = self.device, self.stream
+        other._alloc, other._opts = self._alloc, self._opts
+        other.h = maxflow_clone(self.h)
+        return other

@@ -416,3 +416,38 @@ def test_init_rejects_bad_arguments():
         with pytest.raises(native.MaxflowError) as ei:
             native.Solver(*args)
         assert ei.value.code == native.ERR_INVALID
+
+
+def test_clone_is_independent_deep_copy():
+    g = W.erdos_renyi(2000, 14000, seed=131, cap_hi=100)
+    rng = np.random.default_rng(132)
+    S, es = run_dynamic(g, lambda es, k: W.mixed_batch(es, 300, rng, ins_cap_hi=100), 2)
+    C = S.clone()
+    assert slot_dict(*C.residual()) == slot_dict(*S.residual())
+    assert C.query()[0] == S.query()[0]
+    b = W.mixed_batch(es, 400, rng, ins_cap_hi=100, frac=(0.2, 0.2, 0.4))
+    es.apply(b.u, b.v, b.cap)
+    C.update(b.u, b.v, b.cap)
+    u2, v2, c2 = es.coo()
+    check_against_oracle(C, g.n, u2, v2, c2, g.s, g.t)
+    S.update(b.u, b.v, b.cap)
+    assert S.query()[0] == C.query()[0]
+    C.close()
+    S.close()
+
+
+@pytest.mark.parametrize("k", [1, 3, 64])
+def test_kernel_cycles_do_not_change_the_value(k):
+    g = W.erdos_renyi(2500, 16000, seed=141, cap_hi=100)
+    rng = np.random.default_rng(142)
+    S = native.Solver(g.n, g.src, g.dst, g.cap, g.s, g.t)
+    S.set_kernel_cycles(k)
+    assert S.stats()["kernel_cycles"] == k
+    es = W.EdgeSet(g.n, g.src, g.dst, g.cap)
+    for _ in range(3):
+        b = W.mixed_batch(es, 300, rng, ins_cap_hi=100)
+        es.apply(b.u, b.v, b.cap)
+        S.update(b.u, b.v, b.cap)
+        u2, v2, c2 = es.coo()
+        check_against_oracle(S, g.n, u2, v2, c2, g.s, g.t)
+    S.close()
