@@ -117,6 +117,9 @@ typedef struct {
     int64_t value;                  /* value of the last solve */
     double  ms_kernel;              /* device clock from kernel entry to its last grid barrier */
     int64_t barriers;               /* grid barriers the last solve kernel passed */
+    int64_t discharge_rounds;       /* discharge rounds the last solve ran (all iterations) */
+    int32_t rounds;                 /* current setting of maxflow_set_rounds */
+    int32_t reserved0;
 } maxflow_stats_t;
 
 /* Fill o with the defaults documented above. */
@@ -161,6 +164,14 @@ int maxflow_get_flow(maxflow_ctx *c, int64_t *count, int32_t *u, int32_t *v, int
  * paper follows from it (Sec. 6.1: too low means many BFS, too high sends flow
  * the wrong way). */
 int maxflow_set_kernel_cycles(maxflow_ctx *c, int32_t k);
+
+/* Discharge rounds per global relabel (>= 1).  1 is the paper's data-driven
+ * kernel (Sec. 5.2.1 O1): the vertices active right after the backward BFS get
+ * KERNEL_CYCLES cycles each.  With r > 1, vertices that become active while a
+ * round runs (they receive flow) are discharged in the next round, up to r
+ * rounds, before the next BFS -- as in the paper's kernel, where every vertex
+ * checks e(u) > 0 on each of its cycles. */
+int maxflow_set_rounds(maxflow_ctx *c, int32_t rounds);
 
 /* A deep copy of the context's state (graph, residual capacities, heights,
  * excesses, value) on the same device and stream, as a new context; used to

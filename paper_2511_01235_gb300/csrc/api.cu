@@ -23,6 +23,7 @@ struct maxflow_ctx {
     maxflow_opts opt{};
     int32_t n = 0, s = 0, t = 0;
     int32_t kernel_cycles = 1;
+    int32_t rounds = 1;
     int grid = 1, per_sm = 1, sms = 1;
     MfGraph g{};
     MfScratch sc{};
@@ -109,6 +110,7 @@ MfParams base_params(maxflow_ctx *c)
     p.sink = c->t;
     p.source = c->s;
     p.kernel_cycles = c->kernel_cycles;
+    p.rounds = c->rounds;
     p.fix_steep = c->opt.fix_steep ? 1 : 0;
     p.data_driven = c->opt.data_driven ? 1 : 0;
     p.max_iters = c->opt.max_iters > 0 ? c->opt.max_iters : 4LL * c->n + 1000;
@@ -204,6 +206,28 @@ int upload_graph(maxflow_ctx *c, const MfHostGraph &hg)
     return MAXFLOW_OK;
 }
 
+// Vertex-sized scratch of the solve kernel (frontier, worklists, stamps, lists).
+int alloc_vertex_scratch(maxflow_ctx *c)
+{
+    const int32_t n = c->n;
+    c->sc.border = dalloc_n<int32_t>(c, n);
+    for (int q = 0; q < 2; ++q)
+        for (int b = 0; b < 3; ++b) c->sc.wl[q][b] = dalloc_n<int32_t>(c, n);
+    c->sc.vmark = dalloc_n<int32_t>(c, n);
+    c->sc.fixmark = dalloc_n<int32_t>(c, n);
+    c->sc.fixl[0] = dalloc_n<int32_t>(c, n);
+    c->sc.fixl[1] = dalloc_n<int32_t>(c, n);
+    c->sc.ins_need = dalloc_n<int32_t>(c, n);
+    if (!c->sc.border || !c->sc.vmark || !c->sc.fixmark || !c->sc.fixl[0] || !c->sc.fixl[1] || !c->sc.ins_need)
+        return MAXFLOW_ERR_OOM;
+    for (int q = 0; q < 2; ++q)
+        for (int b = 0; b < 3; ++b)
+            if (!c->sc.wl[q][b]) return MAXFLOW_ERR_OOM;
+    MF_TRY(rc_cuda(cudaMemsetAsync(c->sc.vmark, 0xff, sizeof(int32_t) * n, c->stream)));
+    MF_TRY(rc_cuda(cudaMemsetAsync(c->sc.fixmark, 0xff, sizeof(int32_t) * n, c->stream)));
+    return rc_cuda(cudaMemsetAsync(c->sc.ins_need, 0, sizeof(int32_t) * n, c->stream));
+}
+
 void choose_grid(maxflow_ctx *c)
 {
     int maxg = c->per_sm * c->sms;
@@ -244,6 +268,7 @@ void fill_stats(maxflow_ctx *c, const MfCtrl &h, float ms)
     s.ms_worklist = h.ns_wl * 1e-6;
     s.ms_apply = h.ns_apply * 1e-6;
     s.ms_kernel = (h.t_exit - h.t_entry) * 1e-6;
+    s.discharge_rounds = h.rounds_total;
     s.barriers = h.barriers;
     s.kernel_cycles = c->kernel_cycles;
 }
@@ -547,16 +572,11 @@ int maxflow_init(maxflow_ctx **out, const maxflow_graph *g, int32_t s, int32_t t
         int32_t n = c->n;
         c->g.h = dalloc_n<int32_t>(c, n);
         c->g.e = dalloc_n<long long>(c, n);
-        c->sc.border = dalloc_n<int32_t>(c, n);
-        for (int b = 0; b < 3; ++b) c->sc.wl[b] = dalloc_n<int32_t>(c, n);
-        c->sc.ins_need = dalloc_n<int32_t>(c, n);
         c->ctrl = (MfCtrl *)dalloc(c, sizeof(MfCtrl));
         c->dbuf = dalloc_n<long long>(c, 16);
-        if (!c->g.h || !c->g.e || !c->sc.border || !c->sc.bitem || !c->sc.wl[0] || !c->sc.wl[1] || !c->sc.wl[2] ||
-            !c->sc.ins_need || !c->ctrl || !c->dbuf)
-            rc = MAXFLOW_ERR_OOM;
+        if (!c->g.h || !c->g.e || !c->sc.bitem || !c->ctrl || !c->dbuf) rc = MAXFLOW_ERR_OOM;
     }
-    if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMemsetAsync(c->sc.ins_need, 0, sizeof(int32_t) * c->n, c->stream));
+    if (rc == MAXFLOW_OK) rc = alloc_vertex_scratch(c);
     if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMemsetAsync(c->ctrl, 0, sizeof(MfCtrl), c->stream));
     if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMemsetAsync(c->g.h, 0, sizeof(int32_t) * c->n, c->stream));
     if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMemsetAsync(c->g.e, 0, sizeof(long long) * c->n, c->stream));
@@ -564,6 +584,8 @@ int maxflow_init(maxflow_ctx **out, const maxflow_graph *g, int32_t s, int32_t t
     if (rc == MAXFLOW_OK) {
         int64_t m = c->st.m_edges;
         c->kernel_cycles = o.kernel_cycles > 0 ? o.kernel_cycles : (int32_t)std::max<int64_t>(1, (m + c->n - 1) / c->n);
+        c->rounds = MF_DEFAULT_ROUNDS;
+        c->st.rounds = c->rounds;
         choose_grid(c);
         MfParams p = base_params(c);
         p.mode = MF_M_STATIC_INIT | MF_M_SOLVE;
@@ -674,6 +696,14 @@ int maxflow_set_kernel_cycles(maxflow_ctx *c, int32_t k)
     return MAXFLOW_OK;
 }
 
+int maxflow_set_rounds(maxflow_ctx *c, int32_t rounds)
+{
+    if (!c || rounds < 1 || rounds > (1 << 20)) return MAXFLOW_ERR_INVALID;
+    c->rounds = rounds;
+    c->st.rounds = rounds;
+    return MAXFLOW_OK;
+}
+
 int maxflow_clone(maxflow_ctx *src, maxflow_ctx **out)
 {
     if (!src || !out) return MAXFLOW_ERR_INVALID;
@@ -689,6 +719,7 @@ int maxflow_clone(maxflow_ctx *src, maxflow_ctx **out)
     c->s = src->s;
     c->t = src->t;
     c->kernel_cycles = src->kernel_cycles;
+    c->rounds = src->rounds;
     c->per_sm = src->per_sm;
     c->sms = src->sms;
     c->st = src->st;
@@ -713,17 +744,14 @@ int maxflow_clone(maxflow_ctx *src, maxflow_ctx **out)
         c->g.pcap = dalloc_n<int32_t>(c, S);
         c->g.h = dalloc_n<int32_t>(c, n);
         c->g.e = dalloc_n<long long>(c, n);
-        c->sc.border = dalloc_n<int32_t>(c, n);
         c->sc.bitem = dalloc_n<int2>(c, (int64_t)n + S / MF_BFS_CHUNK + 64);
-        for (int b = 0; b < 3; ++b) c->sc.wl[b] = dalloc_n<int32_t>(c, n);
-        c->sc.ins_need = dalloc_n<int32_t>(c, n);
         c->ctrl = (MfCtrl *)dalloc(c, sizeof(MfCtrl));
         c->dbuf = dalloc_n<long long>(c, 16);
         if (!c->g.off || !c->g.deg || !c->g.bdeg || !c->g.dst || !c->g.cf || !c->g.cap || !c->g.rev || !c->g.pcap ||
-            !c->g.h || !c->g.e || !c->sc.border || !c->sc.bitem || !c->sc.wl[0] || !c->sc.wl[1] || !c->sc.wl[2] ||
-            !c->sc.ins_need || !c->ctrl || !c->dbuf)
+            !c->g.h || !c->g.e || !c->sc.bitem || !c->ctrl || !c->dbuf)
             rc = MAXFLOW_ERR_OOM;
     }
+    if (rc == MAXFLOW_OK) rc = alloc_vertex_scratch(c);
     struct Cp { void *d; const void *s; size_t b; };
     if (rc == MAXFLOW_OK) {
         const Cp cps[] = {{c->g.off, src->g.off, sizeof(int32_t) * (size_t)(n + 1)},
@@ -739,7 +767,6 @@ int maxflow_clone(maxflow_ctx *src, maxflow_ctx **out)
         for (const Cp &cp : cps)
             if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMemcpyAsync(cp.d, cp.s, cp.b, cudaMemcpyDeviceToDevice, c->stream));
     }
-    if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMemsetAsync(c->sc.ins_need, 0, sizeof(int32_t) * n, c->stream));
     if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMemsetAsync(c->ctrl, 0, sizeof(MfCtrl), c->stream));
     if (rc == MAXFLOW_OK) rc = ensure_batch(c, std::max<int64_t>(1024, src->sc.batch_cap));
     if (rc == MAXFLOW_OK) rc = rc_cuda(cudaStreamSynchronize(c->stream));

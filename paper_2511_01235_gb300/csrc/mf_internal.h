@@ -23,6 +23,7 @@
 #define MF_BFS_HUB 256        // BFS: rows above this many slots enter the frontier as work items
 #define MF_BFS_CHUNK 256      // BFS: slots per work item
 #define MF_ACTIVE_HIST 64
+#define MF_DEFAULT_ROUNDS 4   // discharge rounds between global relabels unless set
 #define MF_TRACE 256          // hook timeline entries kept per launch
 
 // Solve-kernel status (ctrl->status)
@@ -65,6 +66,7 @@ struct MfCtrl {
     MfLine head2;
     MfLine wl_tail;       // w[0..2]: worklist append positions per bin
     MfLine misc;          // w[0]: insert list tail, w[1]: touched tail, w[2]: overflow flag
+    MfLine aux_tail;      // w[0..2]: next-round worklist tails, w[3]/w[4]: remove-invalid lists (warp / CTA)
     // ---- (hook) snapshots ----
     int status;
     int level;
@@ -73,6 +75,11 @@ struct MfCtrl {
     int wl_n[3];
     int ins_n, touch_n;
     int bfs_done;
+    int wl_sel;           // which worklist buffer the current round reads
+    int round;            // discharge round within the iteration
+    int dis_more;         // another discharge round follows
+    int fix_n[2];         // vertices for remove-invalid-edges (warp list, CTA list)
+    int qstamp, fstamp;   // dedupe stamps (never reset: they only grow across launches)
     long long iters;
     unsigned long long t_start, t_phase;
     // ---- results and statistics (atomics, flushed once per CTA per phase) ----
@@ -81,6 +88,7 @@ struct MfCtrl {
     long long slots_bfs, verts_bfs, slots_dis, cycles_dis, slots_fix, verts_fix, verts_wl, n_apply;
     unsigned long long ns_bfs, ns_dis, ns_fix, ns_wl, ns_apply;
     int active_hist[MF_ACTIVE_HIST];
+    long long rounds_total;
     // ---- tracing: kernel entry (block 0, before the first barrier), last hook, hook timeline ----
     unsigned long long t_entry, t_exit;
     long long barriers;
@@ -101,7 +109,10 @@ struct MfGraph {
 struct MfScratch {
     int32_t *border;          // [n] BFS order (level segments)
     int2 *bitem;              // [n + slot_cap / MF_BFS_CHUNK + 64] frontier work items (first slot, length)
-    int32_t *wl[3];           // [n] worklists: small, mid, hub
+    int32_t *wl[2][3];        // [n] worklists (two buffers for discharge rounds): small, mid, hub rows
+    int32_t *vmark;           // [n] round stamp of the last time a vertex was queued
+    int32_t *fixmark;         // [n] iteration stamp of the last time a vertex was listed for Alg. 3
+    int32_t *fixl[2];         // [n] vertices relabelled this iteration: rows <= MF_HUB_DEG, rows above
     // batch apply
     int64_t batch_cap;
     int32_t hash_bits;
@@ -127,6 +138,7 @@ struct MfParams {
     int32_t sink, source;
     int32_t mode;
     int32_t kernel_cycles;
+    int32_t rounds;           // discharge rounds between two global relabels (1 = the paper's O1 worklist)
     int32_t fix_steep;
     int32_t data_driven;
     long long max_iters;

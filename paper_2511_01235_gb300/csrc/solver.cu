@@ -128,8 +128,12 @@ __device__ __forceinline__ unsigned long long rd(const unsigned long long &x) { 
 // vertex remains), taken right after a complete backward BFS.
 __device__ __forceinline__ void decide_iteration(const MfParams &P, MfCtrl *c, unsigned long long now,
                                                  const unsigned (&wl)[4], long long iters,
-                                                 unsigned long long t_start)
+                                                 unsigned long long t_start, int qstamp, int fstamp)
 {
+    c->round = 0;
+    for (int i = 0; i < 8; ++i) c->aux_tail.w[i] = 0;
+    c->qstamp = qstamp + 1;
+    c->fstamp = fstamp + 1;
     const int active = (int)wl[3];
     for (int b = 0; b < 3; ++b) c->wl_n[b] = (int)wl[b];
     c->head0.w[0] = c->head1.w[0] = c->head2.w[0] = 0;
@@ -164,6 +168,10 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
         wl[i] = rd(c->wl_tail.w[i]);
         misc[i] = rd(c->misc.w[i]);
     }
+    unsigned aux[5];
+    for (int i = 0; i < 5; ++i) aux[i] = rd(c->aux_tail.w[i]);
+    const int sel = rd(c->wl_sel), round = rd(c->round), qstamp = rd(c->qstamp), fstamp = rd(c->fstamp);
+    const long long rounds_total = rd(c->rounds_total);
     unsigned err = rd(c->err.w[0]);
     const unsigned long long dt = now - t_phase;
     const bool want_wl = P.data_driven && !(P.mode & MF_M_BFS_ONLY);
@@ -193,6 +201,10 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
         for (int i = 0; i < 4; ++i) c->wl_tail.w[i] = 0;
         for (int i = 0; i < 8; ++i) c->misc.w[i] = 0;
         for (int i = 0; i < MF_ACTIVE_HIST; ++i) c->active_hist[i] = 0;
+        for (int i = 0; i < 8; ++i) c->aux_tail.w[i] = 0;
+        c->round = 0;
+        c->dis_more = 0;
+        c->rounds_total = 0;
         c->t_start = now;
         break;
     case H_APPLY_VALID:
@@ -235,17 +247,36 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
         c->hub_hi = (int)item_tail;
         c->head0.w[0] = c->head1.w[0] = 0;
         c->bfs_done = done;
-        if (done && want_wl) decide_iteration(P, c, now, wl, iters, t_start);
+        if (done && want_wl) decide_iteration(P, c, now, wl, iters, t_start, qstamp, fstamp);
         break;
     }
     case H_WL:
         c->ns_wl = rd(c->ns_wl) + dt;
-        decide_iteration(P, c, now, wl, iters, t_start);
+        decide_iteration(P, c, now, wl, iters, t_start, qstamp, fstamp);
         break;
-    case H_DIS:
+    case H_DIS: {
+        // after a discharge round: run another one over the vertices that
+        // became active during it, or end the discharge of this iteration
         c->ns_dis = rd(c->ns_dis) + dt;
         c->head0.w[0] = c->head1.w[0] = c->head2.w[0] = 0;
+        c->rounds_total = rounds_total + 1;
+        const unsigned nxt = aux[0] + aux[1] + aux[2];
+        if (round + 1 < P.rounds && nxt > 0 && err == 0) {
+            c->wl_sel = sel ^ 1;
+            for (int b = 0; b < 3; ++b) {
+                c->wl_n[b] = (int)aux[b];
+                c->aux_tail.w[b] = 0;
+            }
+            c->round = round + 1;
+            c->qstamp = qstamp + 1;
+            c->dis_more = 1;
+        } else {
+            c->dis_more = 0;
+            c->fix_n[0] = (int)aux[3];
+            c->fix_n[1] = (int)aux[4];
+        }
         break;
+    }
     case H_FINAL:
         break;
     }
@@ -671,7 +702,7 @@ __device__ __forceinline__ void warp_append(unsigned *tail, int *arr, bool take,
 // whole warp.
 template <int R>
 __device__ __forceinline__ void frontier_push(const MfParams &P, const bool (&take)[R], const int (&z)[R],
-                                              const int (&d)[R], const long long (&ev)[R], bool with_wl)
+                                              const int (&d)[R], const long long (&ev)[R], bool with_wl, int sel)
 {
     MfCtrl *ctl = P.ctrl;
     const int lane = threadIdx.x & 31;
@@ -719,7 +750,7 @@ __device__ __forceinline__ void frontier_push(const MfParams &P, const bool (&ta
             if (d[r] <= MF_BFS_HUB) P.sc.border[pos[0]++] = z[r];
             if (with_wl && ev[r] > 0) {
                 const int bin = d[r] <= MF_SMALL_DEG ? 0 : (d[r] <= MF_HUB_DEG ? 1 : 2);
-                P.sc.wl[bin][pos[bin + 1]++] = z[r];
+                P.sc.wl[sel][bin][pos[bin + 1]++] = z[r];
             }
         }
     }
@@ -762,7 +793,7 @@ __device__ __noinline__ void phase_bfs_init(const MfParams &P, Sh &sh)
             P.h[v] = root[0] ? 0 : n;
             if (root[0]) dv[0] = ldg_cg(P.g.deg + v);
         }
-        frontier_push<1>(P, root, zv, dv, ev, false);
+        frontier_push<1>(P, root, zv, dv, ev, false, 0);
     }
 }
 
@@ -772,7 +803,8 @@ __device__ __noinline__ void phase_bfs_init(const MfParams &P, Sh &sh)
 // claims, degree/excess loads) is issued for all BR slots together, so each
 // lane keeps BR independent requests in flight.
 template <int BR>
-__device__ __forceinline__ void bfs_visit(const MfParams &P, const int (&x)[BR], const bool (&valid)[BR], int L)
+__device__ __forceinline__ void bfs_visit(const MfParams &P, const int (&x)[BR], const bool (&valid)[BR], int L,
+                                          int sel)
 {
     const bool with_wl = P.data_driven && !(P.mode & MF_M_BFS_ONLY);
     const int n = P.g.n;
@@ -793,7 +825,7 @@ __device__ __forceinline__ void bfs_visit(const MfParams &P, const int (&x)[BR],
         d[r] = claim[r] ? ldg_cg(P.g.deg + z[r]) : 0;
         ev[r] = (with_wl && claim[r] && z[r] != P.sink) ? ldg_cg(P.e + z[r]) : 0;
     }
-    frontier_push<BR>(P, claim, z, d, ev, with_wl);
+    frontier_push<BR>(P, claim, z, d, ev, with_wl, sel);
 }
 
 constexpr int kBR = 4;
@@ -802,6 +834,7 @@ __device__ __noinline__ void phase_bfs_level(const MfParams &P, Sh &sh)
 {
     MfCtrl *ctl = P.ctrl;
     const int L = vrd(&ctl->level);
+    const int sel = vrd(&ctl->wl_sel);
     const int lane = threadIdx.x & 31;
     long long slots = 0;
     // chunks of long rows: one warp per item (at most MF_BFS_CHUNK slots)
@@ -820,7 +853,7 @@ __device__ __noinline__ void phase_bfs_level(const MfParams &P, Sh &sh)
                 vs[r] = k < it.y;
                 xs[r] = it.x + k;
             }
-            bfs_visit<kBR>(P, xs, vs, L);
+            bfs_visit<kBR>(P, xs, vs, L, sel);
         }
     }
     // regular frontier: warps take 32 vertices at a time and expand their
@@ -860,7 +893,7 @@ __device__ __noinline__ void phase_bfs_level(const MfParams &P, Sh &sh)
                 vs[r] = k < T;
                 xs[r] = rb + (k - eb);
             }
-            bfs_visit<kBR>(P, xs, vs, L);
+            bfs_visit<kBR>(P, xs, vs, L, sel);
         }
     }
     if (slots) atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)slots);
@@ -873,6 +906,7 @@ __device__ __noinline__ void phase_bfs_level(const MfParams &P, Sh &sh)
 __device__ __noinline__ void phase_worklist(const MfParams &P, Sh &sh)
 {
     MfCtrl *ctl = P.ctrl;
+    const int sel = vrd(&ctl->wl_sel);
     const int n = P.g.n;
     const int lane = threadIdx.x & 31;
     const long long gs = (long long)gridDim.x * blockDim.x;
@@ -888,9 +922,9 @@ __device__ __noinline__ void phase_worklist(const MfParams &P, Sh &sh)
         }
         unsigned am = __ballot_sync(0xffffffffu, act);
         if (lane == 0 && am) atomicAdd(&ctl->wl_tail.w[3], (unsigned)__popc(am));
-        warp_append(&ctl->wl_tail.w[0], P.sc.wl[0], listed && bin == 0, v);
-        warp_append(&ctl->wl_tail.w[1], P.sc.wl[1], listed && bin == 1, v);
-        warp_append(&ctl->wl_tail.w[2], P.sc.wl[2], listed && bin == 2, v);
+        warp_append(&ctl->wl_tail.w[0], P.sc.wl[sel][0], listed && bin == 0, v);
+        warp_append(&ctl->wl_tail.w[1], P.sc.wl[sel][1], listed && bin == 1, v);
+        warp_append(&ctl->wl_tail.w[2], P.sc.wl[sel][2], listed && bin == 2, v);
     }
 }
 
@@ -898,8 +932,42 @@ __device__ __noinline__ void phase_worklist(const MfParams &P, Sh &sh)
 // Discharge (Alg. 2)
 // ---------------------------------------------------------------------------
 
+// What a discharge round needs besides the graph: where vertices that become
+// active are queued for the next round, and the stamps that keep each vertex
+// at most once per round in that queue and once per iteration in the lists
+// of remove-invalid-edges.
+struct DisCtx {
+    int nsel;        // worklist buffer of the next round
+    int qstamp;      // stamp of this round's queue
+    int fstamp;      // stamp of this iteration's remove-invalid lists
+    bool queue;      // a next round follows, so queue newly active vertices
+};
+
+// z just became active (its excess went from <= 0 to > 0 during this round):
+// give it to the next round (Alg. 2's kernel checks e(u) > 0 on every cycle,
+// so a vertex that receives flow while the kernel runs is discharged too).
+__device__ __forceinline__ void enqueue_active(const MfParams &P, int z, const DisCtx &dc)
+{
+    if (atomicExch(P.sc.vmark + z, dc.qstamp) == dc.qstamp) return;
+    const int d = ldg_cg(P.g.deg + z);
+    const int bin = d <= MF_SMALL_DEG ? 0 : (d <= MF_HUB_DEG ? 1 : 2);
+    const unsigned pos = atomicAdd(&P.ctrl->aux_tail.w[bin], 1u);
+    P.sc.wl[dc.nsel][bin][pos] = z;
+}
+
+// u was relabelled: list it (once per iteration) for remove-invalid-edges;
+// only relabelled vertices can have steep residual edges.
+__device__ __forceinline__ void note_relabel(const MfParams &P, int u, const DisCtx &dc)
+{
+    if (atomicExch(P.sc.fixmark + u, dc.fstamp) == dc.fstamp) return;
+    const int d = ldg_cg(P.g.deg + u);
+    const int li = d > MF_HUB_DEG ? 1 : 0;
+    const unsigned pos = atomicAdd(&P.ctrl->aux_tail.w[3 + li], 1u);
+    P.sc.fixl[li][pos] = u;
+}
+
 // Push d = min(e', c_f(u, v^)) along slot x of u (Alg. 2 lines 11-15).
-__device__ __forceinline__ void do_push(const MfParams &P, Sh &sh, int u, int x, long long eu)
+__device__ __forceinline__ void do_push(const MfParams &P, Sh &sh, int u, int x, long long eu, const DisCtx &dc)
 {
     int c = ldg_cg(P.cf + x);
     long long d = eu < (long long)c ? eu : (long long)c;
@@ -907,7 +975,15 @@ __device__ __forceinline__ void do_push(const MfParams &P, Sh &sh, int u, int x,
     atomicSub(P.cf + x, (int)d);
     atomicAdd(P.cf + ldg_cg(P.g.rev + x), (int)d);
     atomic_add_ll(P.e + u, -d);
-    add_excess(P, sh, ldg_cg(P.g.dst + x), d);
+    const int z = ldg_cg(P.g.dst + x);
+    if (z == P.sink) {
+        atomicAdd((unsigned long long *)&sh.sink_e, (unsigned long long)d);
+    } else if (z == P.source) {
+        atomicAdd((unsigned long long *)&sh.src_e, (unsigned long long)d);
+    } else {
+        const long long old = atomic_add_ll(P.e + z, d);
+        if (dc.queue && old <= 0 && old + d > 0) enqueue_active(P, z, dc);
+    }
     atomicAdd((unsigned long long *)&sh.pushes, 1ull);
 }
 
@@ -942,7 +1018,7 @@ __device__ __forceinline__ unsigned long long scan_lowest(const MfParams &P, int
 
 // One thread per vertex (rows of at most MF_SMALL_DEG slots).  Returns true
 // if u was relabelled (only then can it have steep residual edges, Alg. 3).
-__device__ bool discharge_thread(const MfParams &P, Sh &sh, int u)
+__device__ bool discharge_thread(const MfParams &P, Sh &sh, int u, const DisCtx &dc)
 {
     bool lifted = false;
     const int n = P.g.n;
@@ -957,7 +1033,7 @@ __device__ bool discharge_thread(const MfParams &P, Sh &sh, int u)
         unsigned long long best = scan_lowest<4>(P, r0, d, 0, 1);
         int best_h = best == kEmpty ? 0x7fffffff : (int)(best >> 32);
         if (best != kEmpty && hu > best_h) {
-            do_push(P, sh, u, r0 + (int)(best & 0xffffffffu), eu);
+            do_push(P, sh, u, r0 + (int)(best & 0xffffffffu), eu, dc);
         } else {
             hu = (best == kEmpty || best_h >= n - 1) ? n : best_h + 1;
             P.h[u] = hu;
@@ -973,7 +1049,7 @@ __device__ bool discharge_thread(const MfParams &P, Sh &sh, int u)
 }
 
 // One warp per vertex (returns the same value in every lane).
-__device__ bool discharge_warp(const MfParams &P, Sh &sh, int u)
+__device__ bool discharge_warp(const MfParams &P, Sh &sh, int u, const DisCtx &dc)
 {
     bool lifted = false;
     const int n = P.g.n;
@@ -989,7 +1065,7 @@ __device__ bool discharge_warp(const MfParams &P, Sh &sh, int u)
         unsigned long long best = warp_min_u64(scan_lowest<8>(P, r0, d, lane, 32));
         int best_h = best == kEmpty ? 0x7fffffff : (int)(best >> 32);
         if (best != kEmpty && hu > best_h) {
-            if (lane == 0) do_push(P, sh, u, r0 + (int)(best & 0xffffffffu), eu);
+            if (lane == 0) do_push(P, sh, u, r0 + (int)(best & 0xffffffffu), eu, dc);
         } else {
             hu = (best == kEmpty || best_h >= n - 1) ? n : best_h + 1;
             lifted = true;
@@ -1009,7 +1085,7 @@ __device__ bool discharge_warp(const MfParams &P, Sh &sh, int u)
 
 // One CTA per vertex (hubs).  All threads of the CTA call this together;
 // the return value is meaningful in thread 0.
-__device__ bool discharge_cta(const MfParams &P, Sh &sh, int u)
+__device__ bool discharge_cta(const MfParams &P, Sh &sh, int u, const DisCtx &dc)
 {
     bool lifted = false;
     const int n = P.g.n;
@@ -1036,7 +1112,7 @@ __device__ bool discharge_cta(const MfParams &P, Sh &sh, int u)
             for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = sh.red[w] < b ? sh.red[w] : b;
             int best_h = b == kEmpty ? 0x7fffffff : (int)(b >> 32);
             if (b != kEmpty && hu > best_h) {
-                do_push(P, sh, u, r0 + (int)(b & 0xffffffffu), eu);
+                do_push(P, sh, u, r0 + (int)(b & 0xffffffffu), eu, dc);
             } else {
                 P.h[u] = (b == kEmpty || best_h >= n - 1) ? n : best_h + 1;
                 lifted = true;
@@ -1054,6 +1130,13 @@ __device__ __noinline__ void phase_discharge(const MfParams &P, Sh &sh)
 {
     MfCtrl *ctl = P.ctrl;
     const int lane = threadIdx.x & 31;
+    const int sel = vrd(&ctl->wl_sel);
+    DisCtx dc;
+    dc.nsel = sel ^ 1;
+    dc.qstamp = vrd(&ctl->qstamp);
+    dc.fstamp = vrd(&ctl->fstamp);
+    dc.queue = vrd(&ctl->round) + 1 < P.rounds;
+    const int *wl0 = P.sc.wl[sel][0], *wl1 = P.sc.wl[sel][1], *wl2 = P.sc.wl[sel][2];
     // hubs: one CTA each
     const int nh = vrd(&ctl->wl_n[2]);
     for (;;) {
@@ -1065,16 +1148,16 @@ __device__ __noinline__ void phase_discharge(const MfParams &P, Sh &sh)
         int i = sh.bcast_i;
         __syncthreads();
         if (i >= nh) break;
-        const int u = __ldcg(P.sc.wl[2] + i);
-        if (discharge_cta(P, sh, u) && threadIdx.x == 0) P.sc.wl[2][i] = ~u;
+        const int u = __ldcg(wl2 + i);
+        if (discharge_cta(P, sh, u, dc) && threadIdx.x == 0) note_relabel(P, u, dc);
     }
     // mid-degree rows: one warp each
     const int nm = vrd(&ctl->wl_n[1]);
     for (;;) {
         const int i = warp_grab(&ctl->head1.w[0], nm, 1u);
         if (i >= nm) break;
-        const int u = __ldcg(P.sc.wl[1] + i);
-        if (discharge_warp(P, sh, u) && lane == 0) P.sc.wl[1][i] = ~u;
+        const int u = __ldcg(wl1 + i);
+        if (discharge_warp(P, sh, u, dc) && lane == 0) note_relabel(P, u, dc);
     }
     // small rows: one thread each, 32 per grab
     const int ns = vrd(&ctl->wl_n[0]);
@@ -1082,8 +1165,8 @@ __device__ __noinline__ void phase_discharge(const MfParams &P, Sh &sh)
         const int b = warp_grab(&ctl->head0.w[0], ns, 32u);
         if (b >= ns) break;
         if (b + lane < ns) {
-            const int u = __ldcg(P.sc.wl[0] + b + lane);
-            if (discharge_thread(P, sh, u)) P.sc.wl[0][b + lane] = ~u;
+            const int u = __ldcg(wl0 + b + lane);
+            if (discharge_thread(P, sh, u, dc)) note_relabel(P, u, dc);
         }
     }
 }
@@ -1132,8 +1215,8 @@ __device__ __noinline__ void phase_fix(const MfParams &P, Sh &sh)
     MfCtrl *ctl = P.ctrl;
     const int lane = threadIdx.x & 31;
     long long slots = 0, verts = 0;
-    // hubs: one CTA each
-    const int nh = vrd(&ctl->wl_n[2]);
+    // rows above MF_HUB_DEG: one CTA each
+    const int nh = vrd(&ctl->fix_n[1]);
     for (;;) {
         if (threadIdx.x == 0) {
             unsigned cur = *(volatile unsigned *)&ctl->head2.w[0];
@@ -1143,23 +1226,19 @@ __device__ __noinline__ void phase_fix(const MfParams &P, Sh &sh)
         int i = sh.bcast_i;
         __syncthreads();
         if (i >= nh) break;
-        const int ent = __ldcg(P.sc.wl[2] + i);
-        if (ent >= 0) continue;
-        const int u = ~ent;
+        const int u = __ldcg(P.sc.fixl[1] + i);
         const int hu = ldg_cg(P.h + u);
         const int r0 = P.g.off[u], d = ldg_cg(P.g.deg + u);
         long long out = fix_scan(P, sh, hu, r0, d, threadIdx.x, blockDim.x);
         if (out) atomic_add_ll(P.e + u, -out);
         if (threadIdx.x == 0) { slots += d; ++verts; }
     }
-    // mid rows: warp per vertex
-    const int nm = vrd(&ctl->wl_n[1]);
+    // the others: one warp each
+    const int nw = vrd(&ctl->fix_n[0]);
     for (;;) {
-        const int i = warp_grab(&ctl->head1.w[0], nm, 1u);
-        if (i >= nm) break;
-        const int ent = __ldcg(P.sc.wl[1] + i);
-        if (ent >= 0) continue;
-        const int u = ~ent;
+        const int i = warp_grab(&ctl->head1.w[0], nw, 1u);
+        if (i >= nw) break;
+        const int u = __ldcg(P.sc.fixl[0] + i);
         const int hu = ldg_cg(P.h + u);
         const int r0 = P.g.off[u], d = ldg_cg(P.g.deg + u);
         long long out = warp_sum_ll(fix_scan(P, sh, hu, r0, d, lane, 32));
@@ -1167,24 +1246,6 @@ __device__ __noinline__ void phase_fix(const MfParams &P, Sh &sh)
             if (out) atomic_add_ll(P.e + u, -out);
             slots += d;
             ++verts;
-        }
-    }
-    // small rows: thread per vertex
-    const int ns = vrd(&ctl->wl_n[0]);
-    for (;;) {
-        const int b = warp_grab(&ctl->head0.w[0], ns, 32u);
-        if (b >= ns) break;
-        if (b + lane < ns) {
-            const int ent = __ldcg(P.sc.wl[0] + b + lane);
-            if (ent < 0) {
-                const int u = ~ent;
-                const int hu = ldg_cg(P.h + u);
-                const int r0 = P.g.off[u], d = ldg_cg(P.g.deg + u);
-                long long out = fix_scan(P, sh, hu, r0, d, 0, 1);
-                if (out) atomic_add_ll(P.e + u, -out);
-                slots += d;
-                ++verts;
-            }
         }
     }
     if (slots) atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)slots);
@@ -1275,10 +1336,12 @@ __global__ void __launch_bounds__(MF_BLOCK, 1) mf_solve_kernel(MfParams P)
             if (!grid_sync(P, H_WL, sh)) return;
         }
         if (status_of(P) != MF_ST_RUNNING) break;
-        // discharge and remove-invalid-edges
-        phase_discharge(P, sh);
-        flush_acc(P, sh, 1);
-        if (!grid_sync(P, H_DIS, sh)) return;
+        // discharge rounds, then remove-invalid-edges
+        do {
+            phase_discharge(P, sh);
+            flush_acc(P, sh, 1);
+            if (!grid_sync(P, H_DIS, sh)) return;
+        } while (vrd(&P.ctrl->dis_more));
         if (P.fix_steep) {
             phase_fix(P, sh);
             flush_acc(P, sh, 2);

@@ -68,7 +68,8 @@ class Stats(C.Structure):
                 ("bytes_worklist", C.c_int64), ("bytes_apply", C.c_int64),
                 ("ms_last", C.c_double), ("ms_bfs", C.c_double), ("ms_discharge", C.c_double),
                 ("ms_fix", C.c_double), ("ms_worklist", C.c_double), ("ms_apply", C.c_double),
-                ("value", C.c_int64), ("ms_kernel", C.c_double), ("barriers", C.c_int64)]
+                ("value", C.c_int64), ("ms_kernel", C.c_double), ("barriers", C.c_int64),
+                ("discharge_rounds", C.c_int64), ("rounds", C.c_int32), ("reserved0", C.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -78,7 +79,7 @@ EXPORTS = ["maxflow_default_opts", "maxflow_init", "maxflow_update", "maxflow_qu
            "maxflow_get_flow", "maxflow_stats", "maxflow_destroy", "maxflow_strerror", "maxflow_set_flow",
            "maxflow_apply", "maxflow_global_relabel", "maxflow_resolve", "maxflow_get_residual",
            "maxflow_get_vertex_state", "maxflow_check", "maxflow_global_relabel_noalloc", "maxflow_trace",
-           "maxflow_set_kernel_cycles", "maxflow_clone"]
+           "maxflow_set_kernel_cycles", "maxflow_clone", "maxflow_set_rounds"]
 
 TRACE_NAMES = ["start", "prologue", "batch_validated", "batch_located", "room_checked", "capacities_changed",
                "iteration_start", "bfs_roots", "bfs_level", "worklist", "discharge", "end"]
@@ -121,6 +122,7 @@ def load(build_if_missing: bool = False):
     L.maxflow_check.argtypes = [vp, vp]
     L.maxflow_trace.argtypes = [vp, vp, vp, i32, P(i32)]
     L.maxflow_set_kernel_cycles.argtypes = [vp, i32]
+    L.maxflow_set_rounds.argtypes = [vp, i32]
     L.maxflow_clone.argtypes = [vp, P(vp)]
     L.maxflow_global_relabel_noalloc.argtypes = [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, i32, vp]
     L.maxflow_destroy.argtypes = [vp]
@@ -311,6 +313,10 @@ def maxflow_set_kernel_cycles(h, k: int):
     _check(load().maxflow_set_kernel_cycles(h, int(k)), "maxflow_set_kernel_cycles")
 
 
+def maxflow_set_rounds(h, r: int):
+    _check(load().maxflow_set_rounds(h, int(r)), "maxflow_set_rounds")
+
+
 def maxflow_clone(h):
     out = C.c_void_p()
     _check(load().maxflow_clone(h, C.byref(out)), "maxflow_clone")
@@ -414,6 +420,9 @@ class Solver:
 
     def set_kernel_cycles(self, k: int):
         maxflow_set_kernel_cycles(self.h, k)
+
+    def set_rounds(self, r: int):
+        maxflow_set_rounds(self.h, r)
 
     def clone(self) -> "Solver":
         """A deep copy of this instance's device state (same device, stream and allocator)."""

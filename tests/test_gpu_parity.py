@@ -451,3 +451,23 @@ def test_kernel_cycles_do_not_change_the_value(k):
         u2, v2, c2 = es.coo()
         check_against_oracle(S, g.n, u2, v2, c2, g.s, g.t)
     S.close()
+
+
+@pytest.mark.parametrize("rounds,k", [(4, 1), (32, 4), (256, 16)])
+def test_discharge_rounds_do_not_change_the_value(rounds, k):
+    g = W.erdos_renyi(3000, 18000, seed=151, cap_hi=100)
+    rng = np.random.default_rng(152)
+    S = native.Solver(g.n, g.src, g.dst, g.cap, g.s, g.t)
+    S.set_rounds(rounds)
+    S.set_kernel_cycles(k)
+    S.resolve_static()
+    check_against_oracle(S, g.n, g.src, g.dst, g.cap, g.s, g.t)
+    es = W.EdgeSet(g.n, g.src, g.dst, g.cap)
+    for _ in range(3):
+        b = W.mixed_batch(es, 400, rng, ins_cap_hi=100, st_bias=(g.s, g.t, 0.3))
+        es.apply(b.u, b.v, b.cap)
+        S.update(b.u, b.v, b.cap)
+        u2, v2, c2 = es.coo()
+        check_against_oracle(S, g.n, u2, v2, c2, g.s, g.t)
+    assert S.stats()["rounds"] == rounds
+    S.close()
