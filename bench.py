@@ -265,6 +265,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--static-reps", type=int, default=3)
     ap.add_argument("--quick", action="store_true", help="timed steps only (for profiling runs)")
+    ap.add_argument("--sched-steps", type=int, default=6, help="batches for the learned-vs-fixed schedule comparison")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -345,6 +346,31 @@ def main():
     e2e_s = time.perf_counter() - t0
     e2e_val = ws * args.batch * len(pinned) / e2e_s if pinned else None
 
+    # ---- learned schedule vs the fixed ones on the same batch stream (clones of one state) ----
+    sched = None
+    if not args.quick and args.sched_steps > 0:
+        from paper_2511_01235_gb300 import scheduler as SCH
+        if os.path.exists(SCH.DEFAULT_WEIGHTS):
+            mlp = SCH.load()
+            sb = wl.batches(args.sched_steps, args.batch)
+            sched = {}
+            for key in ("learned", "paper", "default"):
+                C = S.clone()
+                ts = []
+                for b in sb:
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    if key == "learned":
+                        C.update_scheduled(b.u, b.v, b.cap, mlp)
+                    else:
+                        C.run_action(b.u, b.v, b.cap, SCH.ACTION_PAPER if key == "paper" else SCH.ACTION_DEFAULT)
+                    ts.append((time.perf_counter() - t0) * 1e3)
+                sched[key + "_ms_mean"] = float(np.mean(ts))
+                sched[key + "_value"] = int(C.query()[0])
+                C.close()
+            sched["batches"] = len(sb)
+            sched["note"] = "wall ms per update through the C ABI, host batches; paper = 1 round, K = avg degree"
+
     # ---- static re-solve comparator (same updated graph) ----
     static_ms = []
     for _ in range(args.static_reps):
@@ -389,6 +415,7 @@ def main():
                                                              "steep_fixes", "active_first", "ms_bfs", "ms_discharge",
                                                              "ms_fix", "ms_worklist", "ms_apply", "grid_blocks",
                                                              "kernel_cycles")},
+            "scheduler": sched,
             "static_stats": {k: static_stats[k] for k in ("iterations", "bfs_levels", "pushes", "relabels",
                                                           "ms_bfs", "ms_discharge", "ms_fix", "ms_worklist")},
             "wall_s_timed": wall,

@@ -120,6 +120,7 @@ typedef struct {
     int64_t discharge_rounds;       /* discharge rounds the last solve ran (all iterations) */
     int32_t rounds;                 /* current setting of maxflow_set_rounds */
     int32_t reserved0;
+    double  ms_update;              /* device time of every launch of the last update or solve call */
 } maxflow_stats_t;
 
 /* Fill o with the defaults documented above. */
@@ -172,6 +173,53 @@ int maxflow_set_kernel_cycles(maxflow_ctx *c, int32_t k);
  * rounds, before the next BFS -- as in the paper's kernel, where every vertex
  * checks e(u) > 0 on each of its cycles. */
 int maxflow_set_rounds(maxflow_ctx *c, int32_t rounds);
+
+/* ---- learned schedule (an addition to the paper's fixed KERNEL_CYCLES) ----
+ *
+ * A schedule (action) is a mode -- 0: incremental re-solve (Alg. 5), 1: apply
+ * the batch then re-solve from zero flow (Alg. 1) -- with a number of
+ * discharge rounds and of KERNEL_CYCLES (0: the average-degree heuristic).
+ * The action table is fixed; maxflow_sched_actions returns it (pass NULL
+ * arrays to get only the count).  A schedule never changes the result, only
+ * the work. */
+int maxflow_sched_actions(int32_t *mode, int32_t *rounds, int32_t *cycles, int32_t cap, int32_t *count);
+
+/* The 16 scheduler features of a batch for this context (host array of 16
+ * floats): batch size and fraction of the graph, graph size and degree, the
+ * fractions of updates touching s, touching t and deleting, the mean new
+ * capacity over the graph's mean, the last solve's iterations, time, first
+ * active count and BFS levels, the initial static solve's iterations and time,
+ * and a constant 1. */
+int maxflow_features(maxflow_ctx *c, const maxflow_batch *b, float *out);
+
+/* Apply the batch and re-solve with the given action (index into the table). */
+int maxflow_run_action(maxflow_ctx *c, const maxflow_batch *b, int32_t action);
+
+/* A fully connected network x (n_in) -> ReLU(H) -> ReLU(H) -> y (n_out) in
+ * fp32 on the device, trained with Adam on masked squared error; used to
+ * predict the log device time of each action from the features. */
+typedef struct maxflow_mlp maxflow_mlp;
+int maxflow_mlp_create(maxflow_mlp **out, int32_t n_in, int32_t n_hidden, int32_t n_out, uint64_t seed, void *stream);
+void maxflow_mlp_destroy(maxflow_mlp *m);
+int maxflow_mlp_shape(maxflow_mlp *m, int32_t *n_in, int32_t *n_hidden, int32_t *n_out, int64_t *n_params);
+/* Flat parameters [W1 (H x n_in) | b1 | W2 (H x H) | b2 | W3 (n_out x H) | b3], host arrays. */
+int maxflow_mlp_get_params(maxflow_mlp *m, float *host, int64_t count);
+int maxflow_mlp_set_params(maxflow_mlp *m, const float *host, int64_t count);
+/* y (rows x n_out) from x (rows x n_in); host arrays. */
+int maxflow_mlp_forward(maxflow_mlp *m, const float *x, int32_t rows, float *y);
+/* Gradient of L = sum(mask * (y - target)^2) / sum(mask) with respect to the
+ * flat parameters, and L; host arrays (grad has n_params entries). */
+int maxflow_mlp_grad(maxflow_mlp *m, const float *x, const float *target, const float *mask, int32_t rows,
+                     float *grad, float *loss);
+/* `steps` full-batch Adam steps (beta 0.9 / 0.999, eps 1e-8) at learning rate lr. */
+int maxflow_mlp_train(maxflow_mlp *m, const float *x, const float *target, const float *mask, int32_t rows,
+                      int32_t steps, float lr, float *loss_last);
+
+/* Compute the batch's features, let the network predict each action's log
+ * time, and run the action with the smallest prediction (written to
+ * *action_out, may be NULL).  The network must have 16 inputs and one output
+ * per action. */
+int maxflow_update_scheduled(maxflow_ctx *c, const maxflow_batch *b, maxflow_mlp *m, int32_t *action_out);
 
 /* A deep copy of the context's state (graph, residual capacities, heights,
  * excesses, value) on the same device and stream, as a new context; used to

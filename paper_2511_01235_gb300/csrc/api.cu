@@ -38,7 +38,20 @@ struct maxflow_ctx {
     bool solved = false;
     int64_t value = 0;
     maxflow_stats_t st{};
+    double acc_ms = 0;            // device time of all launches of the current update
+    float mean_cap = 0.f;         // mean capacity of the initial edges (scheduler feature)
+    double init_ms = 0;           // static solve at init (scheduler feature)
+    int64_t init_iters = 0;
+    float *feat = nullptr;        // [MF_FEATURES] device
+    float *sched_y = nullptr;     // [64] device
 };
+
+// exported by mlp.cu (C linkage)
+extern "C" {
+int mlp_forward_device(maxflow_mlp *m, const float *x_dev, int32_t rows, float *y_dev, cudaStream_t st);
+int mlp_n_out(const maxflow_mlp *m);
+int mlp_n_in(const maxflow_mlp *m);
+}
 
 namespace {
 
@@ -268,6 +281,7 @@ void fill_stats(maxflow_ctx *c, const MfCtrl &h, float ms)
     s.ms_worklist = h.ns_wl * 1e-6;
     s.ms_apply = h.ns_apply * 1e-6;
     s.ms_kernel = (h.t_exit - h.t_entry) * 1e-6;
+    s.ms_update = c->acc_ms;   // run_kernel has added this launch already
     s.discharge_rounds = h.rounds_total;
     s.barriers = h.barriers;
     s.kernel_cycles = c->kernel_cycles;
@@ -284,6 +298,7 @@ int run_kernel(maxflow_ctx *c, const MfParams &p, int *kerr, int *kstatus)
     MF_TRY(rc_cuda(cudaStreamSynchronize(c->stream)));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    c->acc_ms += ms;
     *kerr = (int)c->hctrl->err.w[0];
     *kstatus = c->hctrl->status;
     fill_stats(c, *c->hctrl, ms);
@@ -307,6 +322,7 @@ int status_to_rc(int kerr, int kstatus)
 // Run a solve that ends with the value phase; record the value.
 int run_solve(maxflow_ctx *c, MfParams p)
 {
+    c->acc_ms = 0;
     int kerr = 0, kst = 0;
     MF_TRY(run_kernel(c, p, &kerr, &kst));
     int rc = status_to_rc(kerr, kst);
@@ -415,6 +431,7 @@ int check_host_batch(maxflow_ctx *c, const maxflow_batch *b)
 // Apply (and optionally solve) a batch.
 int do_batch(maxflow_ctx *c, const maxflow_batch *b, int mode)
 {
+    c->acc_ms = 0;
     if (!b || b->count < 0) return MAXFLOW_ERR_INVALID;
     if (b->count > 0 && (!b->u || !b->v || !b->new_cap)) return MAXFLOW_ERR_INVALID;
     if (!b->on_device) MF_TRY(check_host_batch(c, b));
@@ -559,6 +576,11 @@ int maxflow_init(maxflow_ctx **out, const maxflow_graph *g, int32_t s, int32_t t
     c->s = s;
     c->t = t;
     c->st.n = g->n;
+    {
+        double sum = 0;
+        for (int64_t i = 0; i < g->m; ++i) sum += g->cap[i];
+        c->mean_cap = g->m > 0 ? (float)(sum / (double)g->m) : 0.f;
+    }
     DeviceGuard dg(dev);
     rc = dg.ok ? MAXFLOW_OK : MAXFLOW_ERR_CUDA;
     if (rc == MAXFLOW_OK) rc = mf_max_coresident_blocks(dev, &c->per_sm, &c->sms);
@@ -590,6 +612,13 @@ int maxflow_init(maxflow_ctx **out, const maxflow_graph *g, int32_t s, int32_t t
         MfParams p = base_params(c);
         p.mode = MF_M_STATIC_INIT | MF_M_SOLVE;
         rc = run_solve(c, p);
+        c->init_ms = c->st.ms_last;
+        c->init_iters = c->st.iterations;
+    }
+    if (rc == MAXFLOW_OK) {
+        c->feat = dalloc_n<float>(c, MF_FEATURES);
+        c->sched_y = dalloc_n<float>(c, 64);
+        if (!c->feat || !c->sched_y) rc = MAXFLOW_ERR_OOM;
     }
     if (rc != MAXFLOW_OK) {
         maxflow_destroy(c);
@@ -696,6 +725,146 @@ int maxflow_set_kernel_cycles(maxflow_ctx *c, int32_t k)
     return MAXFLOW_OK;
 }
 
+// ---- schedules chosen per update -----------------------------------------------
+
+namespace {
+
+struct SchedAction {
+    int32_t mode;      // 0: incremental (Alg. 5), 1: apply the batch, then re-solve from zero flow (Alg. 1)
+    int32_t rounds;
+    int32_t cycles;    // 0: the average-degree heuristic of Sec. 6.1
+};
+
+// Index 16 is the paper's fixed schedule (one round, KERNEL_CYCLES = average
+// degree) and 17 the library's default (MF_DEFAULT_ROUNDS rounds).
+const SchedAction kActions[] = {
+    {0, 1, 1}, {0, 1, 4}, {0, 1, 16}, {0, 1, 64},
+    {0, 4, 1}, {0, 4, 4}, {0, 4, 16}, {0, 4, 64},
+    {0, 16, 1}, {0, 16, 4}, {0, 16, 16}, {0, 16, 64},
+    {0, 64, 1}, {0, 64, 4}, {0, 64, 16}, {0, 64, 64},
+    {0, 1, 0}, {0, MF_DEFAULT_ROUNDS, 0},
+    {1, 4, 4}, {1, 16, 16}, {1, 64, 16}, {1, 1, 0},
+};
+constexpr int kNumActions = (int)(sizeof(kActions) / sizeof(kActions[0]));
+
+float lg(double x) { return (float)std::log2(1.0 + (x > 0 ? x : 0)); }
+
+// Stage the batch on the device (copying a host batch) and compute its features.
+int stage_and_features(maxflow_ctx *c, const maxflow_batch *b, maxflow_batch *dev_view)
+{
+    if (!b || b->count < 0) return MAXFLOW_ERR_INVALID;
+    if (b->count > 0 && (!b->u || !b->v || !b->new_cap)) return MAXFLOW_ERR_INVALID;
+    if (!b->on_device) MF_TRY(check_host_batch(c, b));
+    MF_TRY(ensure_batch(c, b->count));
+    *dev_view = *b;
+    if (!b->on_device && b->count > 0) {
+        size_t bytes = sizeof(int32_t) * (size_t)b->count;
+        MF_TRY(rc_cuda(cudaMemcpyAsync(c->sc.bu, b->u, bytes, cudaMemcpyHostToDevice, c->stream)));
+        MF_TRY(rc_cuda(cudaMemcpyAsync(c->sc.bv, b->v, bytes, cudaMemcpyHostToDevice, c->stream)));
+        MF_TRY(rc_cuda(cudaMemcpyAsync(c->sc.bc, b->new_cap, bytes, cudaMemcpyHostToDevice, c->stream)));
+        dev_view->u = c->sc.bu;
+        dev_view->v = c->sc.bv;
+        dev_view->new_cap = c->sc.bc;
+        dev_view->on_device = 1;
+    }
+    MfFeatIn f{};
+    f.bu = dev_view->u;
+    f.bv = dev_view->v;
+    f.bc = dev_view->new_cap;
+    f.count = b->count;
+    f.n = c->n;
+    f.s = c->s;
+    f.t = c->t;
+    f.m = c->st.m_edges;
+    f.mean_cap = c->mean_cap;
+    f.host[0] = lg((double)c->st.iterations) / 8.f;
+    f.host[1] = lg(c->st.ms_last * 1000.0) / 16.f;
+    f.host[2] = lg((double)c->st.active_first) / 20.f;
+    f.host[3] = lg((double)c->init_iters) / 8.f;
+    f.host[4] = lg(c->init_ms * 1000.0) / 16.f;
+    f.host[5] = lg((double)c->st.bfs_levels) / 12.f;
+    return mf_features(f, c->feat, (void *)c->stream);
+}
+
+int run_action(maxflow_ctx *c, const maxflow_batch *dev_batch, int a)
+{
+    const SchedAction &A = kActions[a];
+    const int32_t keep_k = c->kernel_cycles, keep_r = c->rounds;
+    int64_t m = c->st.m_edges;
+    c->kernel_cycles = A.cycles > 0 ? A.cycles : (int32_t)std::max<int64_t>(1, (m + c->n - 1) / c->n);
+    c->rounds = A.rounds;
+    int rc;
+    if (A.mode == 0) {
+        rc = do_batch(c, dev_batch, MF_M_APPLY | MF_M_SOLVE);
+    } else {
+        rc = do_batch(c, dev_batch, MF_M_APPLY | MF_M_SKIP_SOURCE_SAT);
+        double ms = c->acc_ms;
+        if (rc == MAXFLOW_OK) {
+            MfParams p = base_params(c);
+            p.mode = MF_M_STATIC_INIT | MF_M_SOLVE;
+            rc = run_solve(c, p);
+            c->acc_ms += ms;
+            c->st.ms_update = c->acc_ms;
+        }
+    }
+    c->kernel_cycles = keep_k;
+    c->rounds = keep_r;
+    return rc;
+}
+
+}  // namespace
+
+int maxflow_sched_actions(int32_t *mode, int32_t *rounds, int32_t *cycles, int32_t cap, int32_t *count)
+{
+    if (!count || cap < 0) return MAXFLOW_ERR_INVALID;
+    int k = std::min(cap, kNumActions);
+    for (int i = 0; i < k; ++i) {
+        if (mode) mode[i] = kActions[i].mode;
+        if (rounds) rounds[i] = kActions[i].rounds;
+        if (cycles) cycles[i] = kActions[i].cycles;
+    }
+    *count = (mode || rounds || cycles) ? k : kNumActions;
+    return MAXFLOW_OK;
+}
+
+int maxflow_features(maxflow_ctx *c, const maxflow_batch *b, float *out)
+{
+    if (!c || !out) return MAXFLOW_ERR_INVALID;
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return MAXFLOW_ERR_CUDA;
+    maxflow_batch view;
+    MF_TRY(stage_and_features(c, b, &view));
+    MF_TRY(rc_cuda(cudaMemcpyAsync(out, c->feat, sizeof(float) * MF_FEATURES, cudaMemcpyDeviceToHost, c->stream)));
+    return rc_cuda(cudaStreamSynchronize(c->stream));
+}
+
+int maxflow_run_action(maxflow_ctx *c, const maxflow_batch *b, int32_t action)
+{
+    if (!c || action < 0 || action >= kNumActions) return MAXFLOW_ERR_INVALID;
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return MAXFLOW_ERR_CUDA;
+    return run_action(c, b, action);
+}
+
+int maxflow_update_scheduled(maxflow_ctx *c, const maxflow_batch *b, maxflow_mlp *m, int32_t *action_out)
+{
+    if (!c || !m) return MAXFLOW_ERR_INVALID;
+    if (mlp_n_in(m) != MF_FEATURES || mlp_n_out(m) != kNumActions) return MAXFLOW_ERR_INVALID;
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return MAXFLOW_ERR_CUDA;
+    maxflow_batch view;
+    MF_TRY(stage_and_features(c, b, &view));
+    MF_TRY(mlp_forward_device(m, c->feat, 1, c->sched_y, c->stream));
+    float y[64];
+    MF_TRY(rc_cuda(cudaMemcpyAsync(y, c->sched_y, sizeof(float) * kNumActions, cudaMemcpyDeviceToHost, c->stream)));
+    MF_TRY(rc_cuda(cudaStreamSynchronize(c->stream)));
+    int best = 0;
+    for (int i = 1; i < kNumActions; ++i)
+        if (y[i] < y[best]) best = i;
+    if (action_out) *action_out = best;
+    return run_action(c, &view, best);
+}
+
 int maxflow_set_rounds(maxflow_ctx *c, int32_t rounds)
 {
     if (!c || rounds < 1 || rounds > (1 << 20)) return MAXFLOW_ERR_INVALID;
@@ -725,6 +894,9 @@ int maxflow_clone(maxflow_ctx *src, maxflow_ctx **out)
     c->st = src->st;
     c->solved = src->solved;
     c->value = src->value;
+    c->mean_cap = src->mean_cap;
+    c->init_ms = src->init_ms;
+    c->init_iters = src->init_iters;
     const int32_t n = c->n;
     const int64_t S = src->g.slot_cap;
     int rc = rc_cuda(cudaEventCreate(&c->ev0));
@@ -747,8 +919,10 @@ int maxflow_clone(maxflow_ctx *src, maxflow_ctx **out)
         c->sc.bitem = dalloc_n<int2>(c, (int64_t)n + S / MF_BFS_CHUNK + 64);
         c->ctrl = (MfCtrl *)dalloc(c, sizeof(MfCtrl));
         c->dbuf = dalloc_n<long long>(c, 16);
+        c->feat = dalloc_n<float>(c, MF_FEATURES);
+        c->sched_y = dalloc_n<float>(c, 64);
         if (!c->g.off || !c->g.deg || !c->g.bdeg || !c->g.dst || !c->g.cf || !c->g.cap || !c->g.rev || !c->g.pcap ||
-            !c->g.h || !c->g.e || !c->sc.bitem || !c->ctrl || !c->dbuf)
+            !c->g.h || !c->g.e || !c->sc.bitem || !c->ctrl || !c->dbuf || !c->feat || !c->sched_y)
             rc = MAXFLOW_ERR_OOM;
     }
     if (rc == MAXFLOW_OK) rc = alloc_vertex_scratch(c);

@@ -184,5 +184,17 @@ int mf_rebuild_capacity(const MfParams &p, void *stream, float slack_factor, int
 int mf_rebuild_move(const MfParams &p, void *stream, const long long *noff, int32_t *off, int32_t *dst, int32_t *cf,
                     int32_t *cap, int32_t *rev, int32_t *pcap, long long slot_cap);
 
+// scheduler features of a batch (16 floats)
+#define MF_FEATURES 16
+struct MfFeatIn {
+    const int32_t *bu, *bv, *bc;
+    long long count;
+    int32_t n, s, t;
+    long long m;
+    float mean_cap;
+    float host[6];            // features 9..14, known on the host
+};
+int mf_features(const MfFeatIn &f, float *out_dev, void *stream);
+
 int mf_set_flow_items(const MfParams &p, void *stream, long long *dev_bad, long long count, const int32_t *du,
                       const int32_t *dv, const int32_t *df, int apply);

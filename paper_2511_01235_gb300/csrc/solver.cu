@@ -1687,3 +1687,50 @@ int mf_rebuild_move(const MfParams &p, void *stream, const long long *noff, int3
     k_clear_need<<<gv, 256, 0, st>>>(p);
     return cuda_rc(cudaGetLastError());
 }
+
+// ---- scheduler features of a batch (one CTA) ----
+__global__ void __launch_bounds__(256) k_features(MfFeatIn F, float *out)
+{
+    __shared__ float red[4][8];
+    float ts = 0.f, tt = 0.f, zero = 0.f, capsum = 0.f;
+    for (long long i = threadIdx.x; i < F.count; i += blockDim.x) {
+        const int u = F.bu[i], v = F.bv[i], c = F.bc[i];
+        ts += (u == F.s || v == F.s) ? 1.f : 0.f;
+        tt += (u == F.t || v == F.t) ? 1.f : 0.f;
+        zero += c == 0 ? 1.f : 0.f;
+        capsum += (float)c;
+    }
+    float vals[4] = {ts, tt, zero, capsum};
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float x = vals[k];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) red[k][w] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float tot[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int k = 0; k < 4; ++k)
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) tot[k] += red[k][q];
+        const float B = (float)F.count, m = (float)(F.m > 0 ? F.m : 1), n = (float)F.n;
+        const float inv = F.count > 0 ? 1.f / B : 0.f;
+        out[0] = log2f(1.f + B) / 20.f;
+        out[1] = fminf(B / m, 1.f);
+        out[2] = log2f(n) / 24.f;
+        out[3] = log2f(1.f + m) / 28.f;
+        out[4] = (m / n) / 16.f;
+        out[5] = tot[0] * inv;
+        out[6] = tot[1] * inv;
+        out[7] = tot[2] * inv;
+        out[8] = F.count > 0 && F.mean_cap > 0.f ? fminf(tot[3] * inv / F.mean_cap, 4.f) / 4.f : 0.f;
+        for (int k = 0; k < 6; ++k) out[9 + k] = F.host[k];
+        out[15] = 1.f;
+    }
+}
+
+int mf_features(const MfFeatIn &f, float *out_dev, void *stream)
+{
+    k_features<<<1, 256, 0, (cudaStream_t)stream>>>(f, out_dev);
+    return cuda_rc(cudaGetLastError());
+}

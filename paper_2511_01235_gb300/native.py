@@ -69,7 +69,8 @@ class Stats(C.Structure):
                 ("ms_last", C.c_double), ("ms_bfs", C.c_double), ("ms_discharge", C.c_double),
                 ("ms_fix", C.c_double), ("ms_worklist", C.c_double), ("ms_apply", C.c_double),
                 ("value", C.c_int64), ("ms_kernel", C.c_double), ("barriers", C.c_int64),
-                ("discharge_rounds", C.c_int64), ("rounds", C.c_int32), ("reserved0", C.c_int32)]
+                ("discharge_rounds", C.c_int64), ("rounds", C.c_int32), ("reserved0", C.c_int32),
+                ("ms_update", C.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -79,7 +80,10 @@ EXPORTS = ["maxflow_default_opts", "maxflow_init", "maxflow_update", "maxflow_qu
            "maxflow_get_flow", "maxflow_stats", "maxflow_destroy", "maxflow_strerror", "maxflow_set_flow",
            "maxflow_apply", "maxflow_global_relabel", "maxflow_resolve", "maxflow_get_residual",
            "maxflow_get_vertex_state", "maxflow_check", "maxflow_global_relabel_noalloc", "maxflow_trace",
-           "maxflow_set_kernel_cycles", "maxflow_clone", "maxflow_set_rounds"]
+           "maxflow_set_kernel_cycles", "maxflow_clone", "maxflow_set_rounds", "maxflow_sched_actions",
+           "maxflow_features", "maxflow_run_action", "maxflow_update_scheduled", "maxflow_mlp_create",
+           "maxflow_mlp_destroy", "maxflow_mlp_shape", "maxflow_mlp_get_params", "maxflow_mlp_set_params",
+           "maxflow_mlp_forward", "maxflow_mlp_grad", "maxflow_mlp_train"]
 
 TRACE_NAMES = ["start", "prologue", "batch_validated", "batch_located", "room_checked", "capacities_changed",
                "iteration_start", "bfs_roots", "bfs_level", "worklist", "discharge", "end"]
@@ -123,6 +127,19 @@ def load(build_if_missing: bool = False):
     L.maxflow_trace.argtypes = [vp, vp, vp, i32, P(i32)]
     L.maxflow_set_kernel_cycles.argtypes = [vp, i32]
     L.maxflow_set_rounds.argtypes = [vp, i32]
+    L.maxflow_sched_actions.argtypes = [vp, vp, vp, i32, P(i32)]
+    L.maxflow_features.argtypes = [vp, P(Batch), vp]
+    L.maxflow_run_action.argtypes = [vp, P(Batch), i32]
+    L.maxflow_update_scheduled.argtypes = [vp, P(Batch), vp, P(i32)]
+    L.maxflow_mlp_create.argtypes = [P(vp), i32, i32, i32, C.c_uint64, vp]
+    L.maxflow_mlp_destroy.argtypes = [vp]
+    L.maxflow_mlp_destroy.restype = None
+    L.maxflow_mlp_shape.argtypes = [vp, P(i32), P(i32), P(i32), P(i64)]
+    L.maxflow_mlp_get_params.argtypes = [vp, vp, i64]
+    L.maxflow_mlp_set_params.argtypes = [vp, vp, i64]
+    L.maxflow_mlp_forward.argtypes = [vp, vp, i32, vp]
+    L.maxflow_mlp_grad.argtypes = [vp, vp, vp, vp, i32, vp, P(C.c_float)]
+    L.maxflow_mlp_train.argtypes = [vp, vp, vp, vp, i32, i32, C.c_float, P(C.c_float)]
     L.maxflow_clone.argtypes = [vp, P(vp)]
     L.maxflow_global_relabel_noalloc.argtypes = [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, i32, vp]
     L.maxflow_destroy.argtypes = [vp]
@@ -130,7 +147,7 @@ def load(build_if_missing: bool = False):
     L.maxflow_strerror.argtypes = [C.c_int]
     L.maxflow_strerror.restype = C.c_char_p
     for name in EXPORTS:
-        if name not in ("maxflow_default_opts", "maxflow_destroy", "maxflow_strerror"):
+        if name not in ("maxflow_default_opts", "maxflow_destroy", "maxflow_strerror", "maxflow_mlp_destroy"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -323,6 +340,100 @@ def maxflow_clone(h):
     return out
 
 
+def maxflow_sched_actions():
+    """The fixed action table: list of (mode, rounds, cycles); mode 0 incremental, 1 static."""
+    L = load()
+    k = C.c_int32(0)
+    _check(L.maxflow_sched_actions(None, None, None, 0, C.byref(k)), "maxflow_sched_actions")
+    n = int(k.value)
+    mo, ro, cy = (np.zeros(n, np.int32) for _ in range(3))
+    _check(L.maxflow_sched_actions(_p(mo), _p(ro), _p(cy), n, C.byref(k)), "maxflow_sched_actions")
+    return list(zip(mo.tolist(), ro.tolist(), cy.tolist()))
+
+
+def maxflow_features(h, u, v, c) -> np.ndarray:
+    b, keep = _batch(u, v, c)
+    out = np.zeros(16, np.float32)
+    _check(load().maxflow_features(h, C.byref(b), _p(out)), "maxflow_features")
+    return out
+
+
+def maxflow_run_action(h, u, v, c, action: int):
+    b, keep = _batch(u, v, c)
+    _check(load().maxflow_run_action(h, C.byref(b), int(action)), "maxflow_run_action")
+
+
+def maxflow_update_scheduled(h, u, v, c, mlp) -> int:
+    b, keep = _batch(u, v, c)
+    a = C.c_int32(-1)
+    _check(load().maxflow_update_scheduled(h, C.byref(b), mlp.h, C.byref(a)), "maxflow_update_scheduled")
+    return int(a.value)
+
+
+class MLP:
+    """The scheduler's network on the device (fp32): n_in -> H -> H -> n_out, ReLU."""
+
+    def __init__(self, n_in=16, n_hidden=64, n_out=None, seed=0, stream=None):
+        L = load()
+        if n_out is None:
+            n_out = len(maxflow_sched_actions())
+        h = C.c_void_p()
+        st = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+        _check(L.maxflow_mlp_create(C.byref(h), int(n_in), int(n_hidden), int(n_out), C.c_uint64(seed), st),
+               "maxflow_mlp_create")
+        self.h = h
+        a, b, c, d = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int64()
+        _check(L.maxflow_mlp_shape(h, C.byref(a), C.byref(b), C.byref(c), C.byref(d)), "maxflow_mlp_shape")
+        self.n_in, self.n_hidden, self.n_out, self.n_params = a.value, b.value, c.value, d.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().maxflow_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def params(self) -> np.ndarray:
+        out = np.zeros(self.n_params, np.float32)
+        _check(load().maxflow_mlp_get_params(self.h, _p(out), self.n_params), "maxflow_mlp_get_params")
+        return out
+
+    @params.setter
+    def params(self, p):
+        p = np.ascontiguousarray(np.asarray(p, np.float32))
+        _check(load().maxflow_mlp_set_params(self.h, _p(p), int(p.size)), "maxflow_mlp_set_params")
+
+    def forward(self, x) -> np.ndarray:
+        x = np.ascontiguousarray(np.asarray(x, np.float32)).reshape(-1, self.n_in)
+        y = np.zeros((x.shape[0], self.n_out), np.float32)
+        _check(load().maxflow_mlp_forward(self.h, _p(x), x.shape[0], _p(y)), "maxflow_mlp_forward")
+        return y
+
+    def grad(self, x, target, mask):
+        x = np.ascontiguousarray(np.asarray(x, np.float32)).reshape(-1, self.n_in)
+        t = np.ascontiguousarray(np.asarray(target, np.float32)).reshape(-1, self.n_out)
+        m = np.ascontiguousarray(np.asarray(mask, np.float32)).reshape(-1, self.n_out)
+        g = np.zeros(self.n_params, np.float32)
+        loss = C.c_float()
+        _check(load().maxflow_mlp_grad(self.h, _p(x), _p(t), _p(m), x.shape[0], _p(g), C.byref(loss)),
+               "maxflow_mlp_grad")
+        return g, float(loss.value)
+
+    def train(self, x, target, mask, steps=500, lr=3e-3) -> float:
+        x = np.ascontiguousarray(np.asarray(x, np.float32)).reshape(-1, self.n_in)
+        t = np.ascontiguousarray(np.asarray(target, np.float32)).reshape(-1, self.n_out)
+        m = np.ascontiguousarray(np.asarray(mask, np.float32)).reshape(-1, self.n_out)
+        loss = C.c_float()
+        _check(load().maxflow_mlp_train(self.h, _p(x), _p(t), _p(m), x.shape[0], int(steps), float(lr),
+                                        C.byref(loss)), "maxflow_mlp_train")
+        return float(loss.value)
+
+
 def maxflow_destroy(h):
     if h:
         load().maxflow_destroy(h)
@@ -423,6 +534,15 @@ class Solver:
 
     def set_rounds(self, r: int):
         maxflow_set_rounds(self.h, r)
+
+    def features(self, u, v, c) -> np.ndarray:
+        return maxflow_features(self.h, u, v, c)
+
+    def run_action(self, u, v, c, action: int):
+        maxflow_run_action(self.h, u, v, c, action)
+
+    def update_scheduled(self, u, v, c, mlp: MLP) -> int:
+        return maxflow_update_scheduled(self.h, u, v, c, mlp)
 
     def clone(self) -> "Solver":
         """A deep copy of this instance's device state (same device, stream and allocator)."""
