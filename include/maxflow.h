@@ -221,6 +221,25 @@ int maxflow_mlp_train(maxflow_mlp *m, const float *x, const float *target, const
  * per action. */
 int maxflow_update_scheduled(maxflow_ctx *c, const maxflow_batch *b, maxflow_mlp *m, int32_t *action_out);
 
+/* Work split thresholds (by used slots of a vertex's row): the discharge gives
+ * rows of at most thread_max_slots one thread, rows of at most warp_max_slots
+ * one warp and longer rows a whole CTA (remove-invalid-edges: a warp up to
+ * warp_max_slots, then a CTA); the BFS splits rows longer than
+ * bfs_item_min_slots into 256-slot work items.  Defaults 8 / 512 / 256. */
+int maxflow_set_tuning(maxflow_ctx *c, int32_t thread_max_slots, int32_t warp_max_slots, int32_t bfs_item_min_slots);
+
+/* Solve many instances in ONE persistent cooperative launch (on the first
+ * context's device and stream): the grid is cut into groups of group_blocks
+ * CTAs, and each group takes the next instance (largest first) and runs its
+ * whole solve.  batches == NULL: a static re-solve of every instance (Alg. 1);
+ * otherwise batches[i] is applied to ctxs[i] and the flow repaired
+ * incrementally (Alg. 5).  Instances whose insertions overflow their rows are
+ * grown and re-run alone.  *ms_out (may be NULL): device time of the launch.
+ * Returns the first error of any instance; every instance's value is then
+ * available through maxflow_query. */
+int maxflow_solve_batched(maxflow_ctx *const *ctxs, int32_t count, const maxflow_batch *batches, int32_t group_blocks,
+                          double *ms_out);
+
 /* A deep copy of the context's state (graph, residual capacities, heights,
  * excesses, value) on the same device and stream, as a new context; used to
  * try several schedules from one state and to checkpoint a dynamic graph

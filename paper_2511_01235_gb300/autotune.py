@@ -1,0 +1,60 @@
+"""Autotuner for batched solves of many uneven instances.
+
+A batched solve (maxflow_solve_batched) runs every instance in one persistent
+launch, groups of CTAs taking instances from a queue.  Its speed depends on
+knobs that have no single best value across graph families: CTAs per group,
+discharge rounds and KERNEL_CYCLES per instance, and the work-split
+thresholds (rows handled by one thread / one warp / one CTA in the
+discharge, rows split into work items in the BFS).  The tuner measures static
+batched solves (their state is reset by the solve itself, so every trial
+starts from the same point) and does coordinate descent over the knobs.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import native
+
+GROUP_BLOCKS = (1, 2, 4, 8, 16, 32)
+ROUNDS = (1, 4, 16, 64)
+CYCLES = (0, 4, 16)                   # 0: the average-degree heuristic
+SPLITS = ((8, 512, 256), (4, 256, 128), (16, 2048, 1024), (32, 8192, 4096))
+DEFAULT = {"group_blocks": 8, "rounds": 4, "cycles": 0, "split": (8, 512, 256)}
+
+
+def apply_config(solvers, cfg):
+    for s in solvers:
+        s.set_rounds(cfg["rounds"])
+        s.set_kernel_cycles(cfg["cycles"])
+        s.set_tuning(*cfg["split"])
+
+
+def measure(solvers, cfg, reps=2):
+    apply_config(solvers, cfg)
+    return min(native.maxflow_solve_batched(solvers, None, group_blocks=cfg["group_blocks"]) for _ in range(reps))
+
+
+def tune(solvers, passes=2, reps=2, log=None):
+    """Coordinate descent from DEFAULT; returns (best config, its ms, trial log)."""
+    best = dict(DEFAULT)
+    best_ms = measure(solvers, best, reps)
+    trials = [(dict(best), best_ms)]
+    space = {"group_blocks": GROUP_BLOCKS, "rounds": ROUNDS, "cycles": CYCLES, "split": SPLITS}
+    for _ in range(passes):
+        improved = False
+        for key, values in space.items():
+            for v in values:
+                if v == best[key]:
+                    continue
+                cfg = dict(best)
+                cfg[key] = v
+                ms = measure(solvers, cfg, reps)
+                trials.append((cfg, ms))
+                if log:
+                    log(f"  {key}={v}: {ms:.3f} ms (best {best_ms:.3f})")
+                if ms < best_ms:
+                    best, best_ms, improved = cfg, ms, True
+        if not improved:
+            break
+    apply_config(solvers, best)
+    return best, best_ms, trials

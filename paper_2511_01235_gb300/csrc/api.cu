@@ -24,6 +24,11 @@ struct maxflow_ctx {
     int32_t n = 0, s = 0, t = 0;
     int32_t kernel_cycles = 1;
     int32_t rounds = 1;
+    int32_t small_deg = MF_SMALL_DEG, hub_deg = MF_HUB_DEG, bfs_hub = MF_BFS_HUB;
+    // batched launches started from this context (parameter list, group state)
+    MfParams *multi_plist = nullptr;
+    unsigned *multi_gstate = nullptr;
+    int multi_cap = 0;
     int grid = 1, per_sm = 1, sms = 1;
     MfGraph g{};
     MfScratch sc{};
@@ -124,6 +129,9 @@ MfParams base_params(maxflow_ctx *c)
     p.source = c->s;
     p.kernel_cycles = c->kernel_cycles;
     p.rounds = c->rounds;
+    p.small_deg = c->small_deg;
+    p.hub_deg = c->hub_deg;
+    p.bfs_hub = c->bfs_hub;
     p.fix_steep = c->opt.fix_steep ? 1 : 0;
     p.data_driven = c->opt.data_driven ? 1 : 0;
     p.max_iters = c->opt.max_iters > 0 ? c->opt.max_iters : 4LL * c->n + 1000;
@@ -865,6 +873,118 @@ int maxflow_update_scheduled(maxflow_ctx *c, const maxflow_batch *b, maxflow_mlp
     return run_action(c, &view, best);
 }
 
+int maxflow_set_tuning(maxflow_ctx *c, int32_t thread_max_slots, int32_t warp_max_slots, int32_t bfs_item_min_slots)
+{
+    if (!c || thread_max_slots < 1 || warp_max_slots < thread_max_slots || bfs_item_min_slots < 1)
+        return MAXFLOW_ERR_INVALID;
+    c->small_deg = thread_max_slots;
+    c->hub_deg = warp_max_slots;
+    c->bfs_hub = bfs_item_min_slots;
+    return MAXFLOW_OK;
+}
+
+int maxflow_solve_batched(maxflow_ctx *const *ctxs, int32_t count, const maxflow_batch *batches, int32_t group_blocks,
+                          double *ms_out)
+{
+    if (!ctxs || count < 1 || group_blocks < 1) return MAXFLOW_ERR_INVALID;
+    for (int32_t i = 0; i < count; ++i)
+        if (!ctxs[i] || ctxs[i]->device != ctxs[0]->device) return MAXFLOW_ERR_INVALID;
+    maxflow_ctx *c0 = ctxs[0];
+    DeviceGuard dg(c0->device);
+    if (!dg.ok) return MAXFLOW_ERR_CUDA;
+    // per-instance parameters, largest instance first in the queue
+    std::vector<int32_t> order((size_t)count);
+    for (int32_t i = 0; i < count; ++i) order[(size_t)i] = i;
+    std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return ctxs[a]->g.slot_cap > ctxs[b]->g.slot_cap; });
+    std::vector<MfParams> plist((size_t)count);
+    for (int32_t k = 0; k < count; ++k) {
+        maxflow_ctx *c = ctxs[order[(size_t)k]];
+        MfParams p = base_params(c);
+        if (batches) {
+            const maxflow_batch *b = &batches[order[(size_t)k]];
+            if (b->count < 0 || (b->count > 0 && (!b->u || !b->v || !b->new_cap))) return MAXFLOW_ERR_INVALID;
+            if (!b->on_device) MF_TRY(check_host_batch(c, b));
+            MF_TRY(ensure_batch(c, b->count));
+            p = base_params(c);
+            p.bcount = b->count;
+            if (b->count > 0 && !b->on_device) {
+                size_t bytes = sizeof(int32_t) * (size_t)b->count;
+                MF_TRY(rc_cuda(cudaMemcpyAsync(c->sc.bu, b->u, bytes, cudaMemcpyHostToDevice, c0->stream)));
+                MF_TRY(rc_cuda(cudaMemcpyAsync(c->sc.bv, b->v, bytes, cudaMemcpyHostToDevice, c0->stream)));
+                MF_TRY(rc_cuda(cudaMemcpyAsync(c->sc.bc, b->new_cap, bytes, cudaMemcpyHostToDevice, c0->stream)));
+                p.bu = c->sc.bu;
+                p.bv = c->sc.bv;
+                p.bc = c->sc.bc;
+            } else {
+                p.bu = b->u;
+                p.bv = b->v;
+                p.bc = b->new_cap;
+            }
+            p.mode = MF_M_APPLY | MF_M_SOLVE;
+        } else {
+            p.mode = MF_M_STATIC_INIT | MF_M_SOLVE;
+        }
+        plist[(size_t)k] = p;
+    }
+    const int maxg = c0->per_sm * c0->sms;
+    const int gsize = std::min<int>(group_blocks, maxg);
+    const int ngroups = std::max(1, std::min<int>(maxg / gsize, count));
+    if (c0->multi_cap < count || !c0->multi_plist) {
+        dfree(c0, c0->multi_plist);
+        dfree(c0, c0->multi_gstate);
+        c0->multi_cap = std::max(count, 64);
+        c0->multi_plist = (MfParams *)dalloc(c0, sizeof(MfParams) * (size_t)c0->multi_cap);
+        c0->multi_gstate = dalloc_n<unsigned>(c0, 32 * (int64_t)(maxg + 2));
+        if (!c0->multi_plist || !c0->multi_gstate) return MAXFLOW_ERR_OOM;
+    }
+    unsigned *gstate = c0->multi_gstate;
+    unsigned *head = gstate + 32 * maxg;
+    int *abort_flag = (int *)(head + 1);
+    MF_TRY(rc_cuda(cudaMemcpyAsync(c0->multi_plist, plist.data(), sizeof(MfParams) * (size_t)count,
+                                   cudaMemcpyHostToDevice, c0->stream)));
+    MF_TRY(rc_cuda(cudaMemsetAsync(gstate, 0, sizeof(unsigned) * 32 * (size_t)(maxg + 2), c0->stream)));
+    unsigned long long wait_ns = plist[0].wait_limit_ns;
+    MF_TRY(rc_cuda(cudaEventRecord(c0->ev0, c0->stream)));
+    MF_TRY(mf_launch_multi(c0->multi_plist, count, gsize, ngroups * gsize, gstate, head, wait_ns, abort_flag,
+                           (void *)c0->stream));
+    MF_TRY(rc_cuda(cudaEventRecord(c0->ev1, c0->stream)));
+    int abort_h = 0;
+    MF_TRY(rc_cuda(cudaMemcpyAsync(&abort_h, abort_flag, sizeof(int), cudaMemcpyDeviceToHost, c0->stream)));
+    for (int32_t i = 0; i < count; ++i)
+        MF_TRY(rc_cuda(cudaMemcpyAsync(ctxs[i]->hctrl, ctxs[i]->ctrl, sizeof(MfCtrl), cudaMemcpyDeviceToHost,
+                                       c0->stream)));
+    MF_TRY(rc_cuda(cudaStreamSynchronize(c0->stream)));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c0->ev0, c0->ev1);
+    if (ms_out) *ms_out = ms;
+    int first_rc = MAXFLOW_OK;
+    for (int32_t i = 0; i < count; ++i) {
+        maxflow_ctx *c = ctxs[i];
+        const int kerr = (int)c->hctrl->err.w[0], kst = c->hctrl->status;
+        c->acc_ms = ms;
+        fill_stats(c, *c->hctrl, ms);
+        if (abort_h || kerr != MF_E_NONE) {
+            MF_TRY(rc_cuda(cudaMemsetAsync(c->ctrl, 0, 2 * sizeof(MfLine), c->stream)));
+            MF_TRY(rc_cuda(cudaStreamSynchronize(c->stream)));
+        }
+        int rc;
+        if (kerr == MF_E_OVERFLOW && batches) {
+            rc = do_batch(c, &batches[i], MF_M_APPLY | MF_M_SOLVE);   // grows the rows, then runs alone
+        } else {
+            rc = abort_h ? MAXFLOW_ERR_INTERNAL : status_to_rc(kerr, kst);
+            c->st.solves++;
+            if (rc == MAXFLOW_OK || rc == MAXFLOW_ERR_NOT_CONVERGED) {
+                c->value = c->hctrl->value;
+                c->st.value = c->value;
+                c->solved = (rc == MAXFLOW_OK);
+                if (batches) c->st.updates++;
+            }
+        }
+        if (rc != MAXFLOW_OK && first_rc == MAXFLOW_OK) first_rc = rc;
+    }
+    return first_rc;
+}
+
 int maxflow_set_rounds(maxflow_ctx *c, int32_t rounds)
 {
     if (!c || rounds < 1 || rounds > (1 << 20)) return MAXFLOW_ERR_INVALID;
@@ -889,6 +1009,9 @@ int maxflow_clone(maxflow_ctx *src, maxflow_ctx **out)
     c->t = src->t;
     c->kernel_cycles = src->kernel_cycles;
     c->rounds = src->rounds;
+    c->small_deg = src->small_deg;
+    c->hub_deg = src->hub_deg;
+    c->bfs_hub = src->bfs_hub;
     c->per_sm = src->per_sm;
     c->sms = src->sms;
     c->st = src->st;

@@ -139,6 +139,9 @@ struct MfParams {
     int32_t mode;
     int32_t kernel_cycles;
     int32_t rounds;           // discharge rounds between two global relabels (1 = the paper's O1 worklist)
+    int32_t small_deg;        // discharge: rows up to this many slots get one thread
+    int32_t hub_deg;          // discharge / remove-invalid: rows above this many slots get a CTA
+    int32_t bfs_hub;          // BFS: rows above this many slots enter the frontier as work items
     int32_t fix_steep;
     int32_t data_driven;
     long long max_iters;
@@ -165,6 +168,8 @@ int mf_build_host(int32_t n, int64_t m, const int32_t *src, const int32_t *dst, 
 
 // solver.cu
 int mf_launch(const MfParams &p, int grid, void *stream);
+int mf_launch_multi(const MfParams *plist_dev, int count, int gsize, int grid, unsigned *gstate, unsigned *head,
+                    unsigned long long wait_ns, int *abort, void *stream);
 int mf_max_coresident_blocks(int device, int *per_sm, int *num_sms);
 int mf_launch_aux(int which, const MfParams &p, void *stream, long long *dev_out, const void *extra);
 

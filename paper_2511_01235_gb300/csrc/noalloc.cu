@@ -102,6 +102,10 @@ extern "C" int maxflow_global_relabel_noalloc(int32_t n, int32_t s, int32_t t, c
     p.source = s;
     p.mode = MF_M_BFS_ONLY | (deficit_roots ? 0 : MF_M_NO_DEFICIT_ROOTS);
     p.kernel_cycles = 1;
+    p.rounds = 1;
+    p.small_deg = MF_SMALL_DEG;
+    p.hub_deg = MF_HUB_DEG;
+    p.bfs_hub = MF_BFS_HUB;
     p.max_iters = 1;
     p.time_limit_ns = 60ull * 1000000000ull;
     p.wait_limit_ns = 1000000000ull;

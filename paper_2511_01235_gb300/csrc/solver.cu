@@ -30,6 +30,13 @@ namespace {
 
 constexpr unsigned long long kEmpty = ~0ull;
 
+// The CTAs that run one solve: the whole grid for mf_solve_kernel, one group
+// of the grid for mf_multi_kernel.  Every phase distributes its work over
+// vb() in [0, vn()), and the grid barrier waits for vn() CTAs.
+__shared__ int g_vb, g_vn;
+__device__ __forceinline__ int vb() { return g_vb; }
+__device__ __forceinline__ int vn() { return g_vn; }
+
 __device__ __forceinline__ int ldg_cg(const int *p) { return __ldcg(p); }
 __device__ __forceinline__ long long ldg_cg(const long long *p) { return __ldcg(p); }
 
@@ -295,7 +302,7 @@ __device__ bool grid_sync(const MfParams &P, int hook, Sh &sh)
         const unsigned gen = sh.gen;
         __threadfence();
         unsigned arrived = atomicAdd(&c->bar_count.w[0], 1u) + 1u;
-        if (arrived == gridDim.x) {
+        if (arrived == vn()) {
             atomicExch(&c->bar_count.w[0], 0u);
             run_hook(P, hook);
             __threadfence();
@@ -380,8 +387,8 @@ __device__ __forceinline__ void add_excess(const MfParams &P, Sh &sh, int z, lon
 
 __device__ __noinline__ void phase_static_reset(const MfParams &P)
 {
-    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long gs = (long long)gridDim.x * blockDim.x;
+    const long long gt = (long long)vb() * blockDim.x + threadIdx.x;
+    const long long gs = (long long)vn() * blockDim.x;
     for (long long x = gt; x < P.g.slot_cap; x += gs) P.cf[x] = __ldcg(P.g.cap + x);
     for (long long v = gt; v < P.g.n; v += gs) {
         P.e[v] = 0;
@@ -395,7 +402,7 @@ __device__ __noinline__ void phase_saturate_source(const MfParams &P, Sh &sh)
     const int r0 = P.g.off[s];
     const int d = ldg_cg(P.g.deg + s);
     long long acc = 0;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d; j += gridDim.x * blockDim.x) {
+    for (int j = vb() * blockDim.x + threadIdx.x; j < d; j += vn() * blockDim.x) {
         int x = r0 + j;
         int c = ldg_cg(P.g.cap + x);
         int y = ldg_cg(P.g.rev + x);
@@ -430,8 +437,8 @@ __device__ __noinline__ void phase_apply_validate(const MfParams &P)
     MfCtrl *ctl = P.ctrl;
     const int bits = P.sc.hash_bits;
     const unsigned mask = (1u << bits) - 1u;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P.bcount;
-         i += (long long)gridDim.x * blockDim.x) {
+    for (long long i = (long long)vb() * blockDim.x + threadIdx.x; i < P.bcount;
+         i += (long long)vn() * blockDim.x) {
         int u, v, c;
         if (!batch_entry(P, i, u, v, c)) {
             atomicCAS(&ctl->err.w[0], 0u, (unsigned)MF_E_INVALID);
@@ -491,8 +498,8 @@ __device__ __noinline__ void phase_apply_locate(const MfParams &P)
     MfCtrl *ctl = P.ctrl;
     const int bits = P.sc.hash_bits;
     const unsigned mask = (1u << bits) - 1u;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P.bcount;
-         i += (long long)gridDim.x * blockDim.x) {
+    for (long long i = (long long)vb() * blockDim.x + threadIdx.x; i < P.bcount;
+         i += (long long)vn() * blockDim.x) {
         int u, v, c;
         batch_entry(P, i, u, v, c);
         if (u == v) {
@@ -530,7 +537,7 @@ __device__ __noinline__ void phase_apply_check(const MfParams &P)
 {
     MfCtrl *ctl = P.ctrl;
     const int nins = vrd(&ctl->ins_n);
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nins; k += gridDim.x * blockDim.x) {
+    for (int k = vb() * blockDim.x + threadIdx.x; k < nins; k += vn() * blockDim.x) {
         unsigned long long pk = __ldcg(P.sc.pkey + __ldcg(P.sc.ins_list + k));
         int a = (int)(pk >> 32), b = (int)(pk & 0xffffffffu);
         int room_a = P.g.off[a + 1] - P.g.off[a] - ldg_cg(P.g.deg + a);
@@ -543,7 +550,7 @@ __device__ __noinline__ void phase_apply_insert(const MfParams &P)
 {
     MfCtrl *ctl = P.ctrl;
     const int nins = vrd(&ctl->ins_n);
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nins; k += gridDim.x * blockDim.x) {
+    for (int k = vb() * blockDim.x + threadIdx.x; k < nins; k += vn() * blockDim.x) {
         int pp = __ldcg(P.sc.ins_list + k);
         unsigned long long pk = __ldcg(P.sc.pkey + pp);
         int a = (int)(pk >> 32), b = (int)(pk & 0xffffffffu);
@@ -568,8 +575,8 @@ __device__ __noinline__ void phase_apply_delta(const MfParams &P, Sh &sh)
     MfCtrl *ctl = P.ctrl;
     const int bits = P.sc.hash_bits;
     long long applied = 0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P.bcount;
-         i += (long long)gridDim.x * blockDim.x) {
+    for (long long i = (long long)vb() * blockDim.x + threadIdx.x; i < P.bcount;
+         i += (long long)vn() * blockDim.x) {
         int x = __ldcg(P.sc.bslot + i);
         if (x == -2) continue;
         int u, v, c;
@@ -608,8 +615,8 @@ __device__ __noinline__ void phase_apply_clamp(const MfParams &P, Sh &sh)
 {
     MfCtrl *ctl = P.ctrl;
     const int nt = vrd(&ctl->touch_n);
-    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long gs = (long long)gridDim.x * blockDim.x;
+    const long long gt = (long long)vb() * blockDim.x + threadIdx.x;
+    const long long gs = (long long)vn() * blockDim.x;
     for (long long k = gt; k < nt; k += gs) {
         long long i = __ldcg(P.sc.clamp + k);
         int x = __ldcg(P.sc.bslot + i);
@@ -632,12 +639,12 @@ __device__ __noinline__ void phase_apply_cleanup(const MfParams &P, bool keep_ne
     MfCtrl *ctl = P.ctrl;
     const int nused = (int)*(volatile unsigned *)&ctl->misc.w[3];
     const int nins = (int)*(volatile unsigned *)&ctl->misc.w[0];
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nused; k += gridDim.x * blockDim.x) {
+    for (int k = vb() * blockDim.x + threadIdx.x; k < nused; k += vn() * blockDim.x) {
         int pos = __ldcg(P.sc.hused + k);
         P.sc.hkey[pos] = kEmpty;
         P.sc.hval[pos] = -1;
     }
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nins; k += gridDim.x * blockDim.x) {
+    for (int k = vb() * blockDim.x + threadIdx.x; k < nins; k += vn() * blockDim.x) {
         int pp = __ldcg(P.sc.ins_list + k);
         unsigned long long pk = __ldcg(P.sc.pkey + pp);
         if (pk != kEmpty && !keep_need) {
@@ -658,7 +665,7 @@ __device__ __noinline__ void phase_resaturate(const MfParams &P, Sh &sh)
     const int r0 = P.g.off[s];
     const int d = ldg_cg(P.g.deg + s);
     long long acc = 0;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d; j += gridDim.x * blockDim.x) {
+    for (int j = vb() * blockDim.x + threadIdx.x; j < d; j += vn() * blockDim.x) {
         int x = r0 + j;
         int c = ldg_cg(P.cf + x);
         if (c > 0) {
@@ -688,7 +695,7 @@ __device__ __forceinline__ void warp_append(unsigned *tail, int *arr, bool take,
 }
 
 // Labelled vertices enter the next frontier either as one entry of the
-// regular list (rows of at most MF_BFS_HUB slots, expanded warp-cooperatively)
+// regular list (rows of at most bfs_hub slots, expanded warp-cooperatively)
 // or, for longer rows, as ceil(deg / MF_BFS_CHUNK) work items (first slot,
 // length) that any warp can take: no row is ever walked by one warp alone.
 // With with_wl, a labelled vertex that has excess (and is neither the sink
@@ -712,11 +719,11 @@ __device__ __forceinline__ void frontier_push(const MfParams &P, const bool (&ta
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         if (!take[r]) continue;
-        const bool big = d[r] > MF_BFS_HUB;
+        const bool big = d[r] > P.bfs_hub;
         anybig |= big;
         if (!big) packed += 1u;
         if (with_wl && ev[r] > 0) {
-            const int bin = d[r] <= MF_SMALL_DEG ? 0 : (d[r] <= MF_HUB_DEG ? 1 : 2);
+            const int bin = d[r] <= P.small_deg ? 0 : (d[r] <= P.hub_deg ? 1 : 2);
             packed += 1u << (8 * (bin + 1));
         }
     }
@@ -747,9 +754,9 @@ __device__ __forceinline__ void frontier_push(const MfParams &P, const bool (&ta
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             if (!take[r]) continue;
-            if (d[r] <= MF_BFS_HUB) P.sc.border[pos[0]++] = z[r];
+            if (d[r] <= P.bfs_hub) P.sc.border[pos[0]++] = z[r];
             if (with_wl && ev[r] > 0) {
-                const int bin = d[r] <= MF_SMALL_DEG ? 0 : (d[r] <= MF_HUB_DEG ? 1 : 2);
+                const int bin = d[r] <= P.small_deg ? 0 : (d[r] <= P.hub_deg ? 1 : 2);
                 P.sc.wl[sel][bin][pos[bin + 1]++] = z[r];
             }
         }
@@ -763,7 +770,7 @@ __device__ __forceinline__ void frontier_push(const MfParams &P, const bool (&ta
         for (int r = 0; r < R; ++r) {
             const int zz = __shfl_sync(0xffffffffu, z[r], src);
             const int dd = __shfl_sync(0xffffffffu, take[r] ? d[r] : 0, src);
-            if (dd <= MF_BFS_HUB) continue;
+            if (dd <= P.bfs_hub) continue;
             const int nch = (dd + MF_BFS_CHUNK - 1) / MF_BFS_CHUNK;
             unsigned at = 0;
             if (lane == 0) at = atomicAdd(&ctl->hub_tail.w[0], (unsigned)nch);
@@ -782,8 +789,8 @@ __device__ __noinline__ void phase_bfs_init(const MfParams &P, Sh &sh)
     const int n = P.g.n;
     const bool deficit_roots = (P.mode & MF_M_NO_DEFICIT_ROOTS) == 0;
     const int lane = threadIdx.x & 31;
-    const long long gs = (long long)gridDim.x * blockDim.x;
-    for (long long base = (long long)blockIdx.x * blockDim.x + threadIdx.x - lane; base < n; base += gs) {
+    const long long gs = (long long)vn() * blockDim.x;
+    for (long long base = (long long)vb() * blockDim.x + threadIdx.x - lane; base < n; base += gs) {
         const int v = (int)base + lane;
         bool root[1] = {false};
         int zv[1] = {v}, dv[1] = {0};
@@ -909,8 +916,8 @@ __device__ __noinline__ void phase_worklist(const MfParams &P, Sh &sh)
     const int sel = vrd(&ctl->wl_sel);
     const int n = P.g.n;
     const int lane = threadIdx.x & 31;
-    const long long gs = (long long)gridDim.x * blockDim.x;
-    for (long long base = (long long)blockIdx.x * blockDim.x + threadIdx.x - lane; base < n; base += gs) {
+    const long long gs = (long long)vn() * blockDim.x;
+    for (long long base = (long long)vb() * blockDim.x + threadIdx.x - lane; base < n; base += gs) {
         int v = (int)base + lane;
         bool cand = v < n && v != P.sink && v != P.source;
         bool act = cand && ldg_cg(P.h + v) < n && ldg_cg(P.e + v) > 0;
@@ -918,7 +925,7 @@ __device__ __noinline__ void phase_worklist(const MfParams &P, Sh &sh)
         int bin = 0;
         if (listed) {
             int d = ldg_cg(P.g.deg + v);
-            bin = d <= MF_SMALL_DEG ? 0 : (d <= MF_HUB_DEG ? 1 : 2);
+            bin = d <= P.small_deg ? 0 : (d <= P.hub_deg ? 1 : 2);
         }
         unsigned am = __ballot_sync(0xffffffffu, act);
         if (lane == 0 && am) atomicAdd(&ctl->wl_tail.w[3], (unsigned)__popc(am));
@@ -950,7 +957,7 @@ __device__ __forceinline__ void enqueue_active(const MfParams &P, int z, const D
 {
     if (atomicExch(P.sc.vmark + z, dc.qstamp) == dc.qstamp) return;
     const int d = ldg_cg(P.g.deg + z);
-    const int bin = d <= MF_SMALL_DEG ? 0 : (d <= MF_HUB_DEG ? 1 : 2);
+    const int bin = d <= P.small_deg ? 0 : (d <= P.hub_deg ? 1 : 2);
     const unsigned pos = atomicAdd(&P.ctrl->aux_tail.w[bin], 1u);
     P.sc.wl[dc.nsel][bin][pos] = z;
 }
@@ -961,7 +968,7 @@ __device__ __forceinline__ void note_relabel(const MfParams &P, int u, const Dis
 {
     if (atomicExch(P.sc.fixmark + u, dc.fstamp) == dc.fstamp) return;
     const int d = ldg_cg(P.g.deg + u);
-    const int li = d > MF_HUB_DEG ? 1 : 0;
+    const int li = d > P.hub_deg ? 1 : 0;
     const unsigned pos = atomicAdd(&P.ctrl->aux_tail.w[3 + li], 1u);
     P.sc.fixl[li][pos] = u;
 }
@@ -1016,7 +1023,7 @@ __device__ __forceinline__ unsigned long long scan_lowest(const MfParams &P, int
     return best;
 }
 
-// One thread per vertex (rows of at most MF_SMALL_DEG slots).  Returns true
+// One thread per vertex (rows of at most small_deg slots).  Returns true
 // if u was relabelled (only then can it have steep residual edges, Alg. 3).
 __device__ bool discharge_thread(const MfParams &P, Sh &sh, int u, const DisCtx &dc)
 {
@@ -1215,7 +1222,7 @@ __device__ __noinline__ void phase_fix(const MfParams &P, Sh &sh)
     MfCtrl *ctl = P.ctrl;
     const int lane = threadIdx.x & 31;
     long long slots = 0, verts = 0;
-    // rows above MF_HUB_DEG: one CTA each
+    // rows above hub_deg: one CTA each
     const int nh = vrd(&ctl->fix_n[1]);
     for (;;) {
         if (threadIdx.x == 0) {
@@ -1260,97 +1267,180 @@ __device__ __noinline__ void phase_value(const MfParams &P)
 {
     const int n = P.g.n;
     long long acc = 0;
-    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x)
+    for (long long v = (long long)vb() * blockDim.x + threadIdx.x; v < n; v += (long long)vn() * blockDim.x)
         if ((int)v != P.source && ldg_cg(P.h + v) < n) acc += ldg_cg(P.e + v);
     acc = warp_sum_ll(acc);
     if ((threadIdx.x & 31) == 0 && acc) atomic_add_ll(&P.ctrl->value, acc);
 }
 
-__global__ void __launch_bounds__(MF_BLOCK, 1) mf_solve_kernel(MfParams P)
+// One whole solve of one instance by the vn() CTAs of the caller: the
+// optional static initialisation or batch repair, the push-relabel loop and
+// the value.  Returns false only if this CTA gave up waiting at a barrier
+// (the caller must then leave the kernel); every other exit is taken by all
+// CTAs together.
+__device__ __noinline__ bool solve_instance(const MfParams &P, Sh &sh)
 {
-    __shared__ Sh sh;
-    if (blockIdx.x == 0 && threadIdx.x == 0) P.ctrl->t_entry = gtimer();
+    if (vb() == 0 && threadIdx.x == 0) P.ctrl->t_entry = gtimer();
     if (threadIdx.x == 0) {
         sh.gen = ld_acquire(&P.ctrl->bar_gen.w[0]);   // nobody can pass the first barrier before all have read it
         sh.sink_e = sh.src_e = 0;
         sh.pushes = sh.relabels = sh.steep = sh.slots = sh.verts = sh.cycles = 0;
     }
-    if (!grid_sync(P, H_START, sh)) return;
+    if (!grid_sync(P, H_START, sh)) return false;
 
     if (P.mode & MF_M_STATIC_INIT) {
         phase_static_reset(P);
-        if (!grid_sync(P, H_NONE, sh)) return;
+        if (!grid_sync(P, H_NONE, sh)) return false;
         phase_saturate_source(P, sh);
         flush_acc(P, sh, 4);
-        if (!grid_sync(P, H_NONE, sh)) return;
+        if (!grid_sync(P, H_NONE, sh)) return false;
     }
     if (P.mode & MF_M_APPLY) {
         phase_apply_validate(P);
-        if (!grid_sync(P, H_APPLY_VALID, sh)) return;
+        if (!grid_sync(P, H_APPLY_VALID, sh)) return false;
         if (status_of(P) != MF_ST_RUNNING) {
             phase_apply_cleanup(P, false);
-            grid_sync(P, H_FINAL, sh);
-            return;
+            return grid_sync(P, H_FINAL, sh);
         }
         phase_apply_locate(P);
-        if (!grid_sync(P, H_APPLY_LOCATED, sh)) return;
+        if (!grid_sync(P, H_APPLY_LOCATED, sh)) return false;
         phase_apply_check(P);
-        if (!grid_sync(P, H_APPLY_CHECKED, sh)) return;
+        if (!grid_sync(P, H_APPLY_CHECKED, sh)) return false;
         if (status_of(P) != MF_ST_RUNNING) {
             phase_apply_cleanup(P, true);
-            grid_sync(P, H_FINAL, sh);
-            return;
+            return grid_sync(P, H_FINAL, sh);
         }
         phase_apply_insert(P);
-        if (!grid_sync(P, H_NONE, sh)) return;
+        if (!grid_sync(P, H_NONE, sh)) return false;
         phase_apply_delta(P, sh);
         flush_acc(P, sh, 4);
-        if (!grid_sync(P, H_APPLY_DELTA, sh)) return;
+        if (!grid_sync(P, H_APPLY_DELTA, sh)) return false;
         phase_apply_clamp(P, sh);
         phase_apply_cleanup(P, false);
         flush_acc(P, sh, 4);
-        if (!grid_sync(P, H_NONE, sh)) return;
+        if (!grid_sync(P, H_NONE, sh)) return false;
         if (!(P.mode & MF_M_SKIP_SOURCE_SAT)) {
             phase_resaturate(P, sh);
             flush_acc(P, sh, 4);
-            if (!grid_sync(P, H_NONE, sh)) return;
+            if (!grid_sync(P, H_NONE, sh)) return false;
         }
-        if (status_of(P) != MF_ST_RUNNING) return;
+        if (status_of(P) != MF_ST_RUNNING) return true;
     }
-    if (!(P.mode & (MF_M_SOLVE | MF_M_BFS_ONLY))) return;
+    if (!(P.mode & (MF_M_SOLVE | MF_M_BFS_ONLY))) return true;
 
-    if (!grid_sync(P, H_ITER, sh)) return;
+    if (!grid_sync(P, H_ITER, sh)) return false;
     for (;;) {
         // backward BFS
         phase_bfs_init(P, sh);
-        if (!grid_sync(P, H_BFS_START, sh)) return;
+        if (!grid_sync(P, H_BFS_START, sh)) return false;
         while (!vrd(&P.ctrl->bfs_done)) {
             phase_bfs_level(P, sh);
             flush_acc(P, sh, 0);
-            if (!grid_sync(P, H_BFS_NEXT, sh)) return;
+            if (!grid_sync(P, H_BFS_NEXT, sh)) return false;
         }
-        if (P.mode & MF_M_BFS_ONLY) return;
+        if (P.mode & MF_M_BFS_ONLY) return true;
         // worklist and termination test (built during the BFS when data-driven)
         if (!P.data_driven) {
             phase_worklist(P, sh);
-            if (!grid_sync(P, H_WL, sh)) return;
+            if (!grid_sync(P, H_WL, sh)) return false;
         }
         if (status_of(P) != MF_ST_RUNNING) break;
         // discharge rounds, then remove-invalid-edges
         do {
             phase_discharge(P, sh);
             flush_acc(P, sh, 1);
-            if (!grid_sync(P, H_DIS, sh)) return;
+            if (!grid_sync(P, H_DIS, sh)) return false;
         } while (vrd(&P.ctrl->dis_more));
         if (P.fix_steep) {
             phase_fix(P, sh);
             flush_acc(P, sh, 2);
         }
-        if (!grid_sync(P, H_ITER, sh)) return;
+        if (!grid_sync(P, H_ITER, sh)) return false;
     }
-    if (status_of(P) == MF_ST_ERROR) return;
+    if (status_of(P) == MF_ST_ERROR) return true;
     phase_value(P);
-    grid_sync(P, H_FINAL, sh);
+    return grid_sync(P, H_FINAL, sh);
+}
+
+__global__ void __launch_bounds__(MF_BLOCK, 2) mf_solve_kernel(MfParams P)
+{
+    __shared__ Sh sh;
+    if (threadIdx.x == 0) {
+        g_vb = blockIdx.x;
+        g_vn = gridDim.x;
+    }
+    __syncthreads();
+    solve_instance(P, sh);
+}
+
+// Barrier of one group of CTAs (no hook): w[0] arrivals, w[1] generation.
+__device__ bool group_sync(unsigned *w, unsigned &gen_local, unsigned long long wait_ns, int *abort)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int good = 1;
+        const unsigned gen = gen_local;
+        __threadfence();
+        if (atomicAdd(w, 1u) + 1u == (unsigned)vn()) {
+            atomicExch(w, 0u);
+            __threadfence();
+            st_release(w + 1, gen + 1u);
+        } else {
+            unsigned long long t0 = 0;
+            unsigned spins = 0;
+            while (ld_acquire(w + 1) == gen) {
+                ++spins;
+                if (spins > 64) __nanosleep(spins > 4096 ? 200 : 32);
+                if ((spins & 31u) == 0) {
+                    unsigned long long now = gtimer();
+                    if (t0 == 0) {
+                        t0 = now;
+                    } else if (now - t0 > wait_ns) {
+                        atomicExch(abort, 1);
+                        good = 0;
+                        break;
+                    }
+                }
+            }
+        }
+        __threadfence();
+        gen_local = gen + 1u;
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// Many instances in one persistent launch: the grid is cut into groups of
+// gsize CTAs; each group takes the next instance from a shared queue (the host
+// orders it largest first) and runs its whole solve, then takes another.
+// gstate holds, per group, 32 words: w[0] arrivals, w[1] generation, w[2] the
+// instance the group's first CTA took.
+__global__ void __launch_bounds__(MF_BLOCK, 2) mf_multi_kernel(const MfParams *__restrict__ plist, int count,
+                                                               int gsize, unsigned *gstate, unsigned *head,
+                                                               unsigned long long wait_ns, int *abort)
+{
+    __shared__ Sh sh;
+    __shared__ unsigned ggen;
+    const int grp = blockIdx.x / gsize;
+    unsigned *gw = gstate + 32 * grp;
+    if (threadIdx.x == 0) {
+        g_vb = blockIdx.x % gsize;
+        g_vn = gsize;
+        ggen = ld_acquire(gw + 1);
+    }
+    __syncthreads();
+    for (;;) {
+        if (vb() == 0 && threadIdx.x == 0) gw[2] = atomicAdd(head, 1u);
+        if (!group_sync(gw, ggen, wait_ns, abort)) return;
+        const int i = (int)__ldcg(gw + 2);
+        if (i >= count) return;
+        if (!solve_instance(plist[i], sh)) {
+            atomicExch(abort, 1);
+            return;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1582,6 +1672,15 @@ int mf_max_coresident_blocks(int device, int *per_sm, int *num_sms)
     *per_sm = k;
     *num_sms = sms;
     return k > 0 ? MAXFLOW_OK : MAXFLOW_ERR_CUDA;
+}
+
+int mf_launch_multi(const MfParams *plist_dev, int count, int gsize, int grid, unsigned *gstate, unsigned *head,
+                    unsigned long long wait_ns, int *abort, void *stream)
+{
+    void *args[] = {(void *)&plist_dev, &count, &gsize, &gstate, &head, &wait_ns, &abort};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)mf_multi_kernel, dim3(grid), dim3(MF_BLOCK), args, 0,
+                                                (cudaStream_t)stream);
+    return cuda_rc(e);
 }
 
 int mf_launch(const MfParams &p, int grid, void *stream)

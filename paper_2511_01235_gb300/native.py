@@ -83,7 +83,8 @@ EXPORTS = ["maxflow_default_opts", "maxflow_init", "maxflow_update", "maxflow_qu
            "maxflow_set_kernel_cycles", "maxflow_clone", "maxflow_set_rounds", "maxflow_sched_actions",
            "maxflow_features", "maxflow_run_action", "maxflow_update_scheduled", "maxflow_mlp_create",
            "maxflow_mlp_destroy", "maxflow_mlp_shape", "maxflow_mlp_get_params", "maxflow_mlp_set_params",
-           "maxflow_mlp_forward", "maxflow_mlp_grad", "maxflow_mlp_train"]
+           "maxflow_mlp_forward", "maxflow_mlp_grad", "maxflow_mlp_train", "maxflow_set_tuning",
+           "maxflow_solve_batched"]
 
 TRACE_NAMES = ["start", "prologue", "batch_validated", "batch_located", "room_checked", "capacities_changed",
                "iteration_start", "bfs_roots", "bfs_level", "worklist", "discharge", "end"]
@@ -127,6 +128,8 @@ def load(build_if_missing: bool = False):
     L.maxflow_trace.argtypes = [vp, vp, vp, i32, P(i32)]
     L.maxflow_set_kernel_cycles.argtypes = [vp, i32]
     L.maxflow_set_rounds.argtypes = [vp, i32]
+    L.maxflow_set_tuning.argtypes = [vp, i32, i32, i32]
+    L.maxflow_solve_batched.argtypes = [vp, i32, vp, i32, P(C.c_double)]
     L.maxflow_sched_actions.argtypes = [vp, vp, vp, i32, P(i32)]
     L.maxflow_features.argtypes = [vp, P(Batch), vp]
     L.maxflow_run_action.argtypes = [vp, P(Batch), i32]
@@ -334,6 +337,29 @@ def maxflow_set_rounds(h, r: int):
     _check(load().maxflow_set_rounds(h, int(r)), "maxflow_set_rounds")
 
 
+def maxflow_set_tuning(h, thread_max_slots: int, warp_max_slots: int, bfs_item_min_slots: int):
+    _check(load().maxflow_set_tuning(h, int(thread_max_slots), int(warp_max_slots), int(bfs_item_min_slots)),
+           "maxflow_set_tuning")
+
+
+def maxflow_solve_batched(solvers, batches=None, group_blocks=8) -> float:
+    """One persistent launch over many instances; returns the launch's device ms."""
+    hs = (C.c_void_p * len(solvers))(*[s.h.value for s in solvers])
+    keep = []
+    bp = None
+    if batches is not None:
+        arr = (Batch * len(solvers))()
+        for i, (u, v, c) in enumerate(batches):
+            b, k = _batch(u, v, c)
+            arr[i] = b
+            keep.append(k)
+        bp = C.cast(arr, C.c_void_p)
+    ms = C.c_double()
+    _check(load().maxflow_solve_batched(C.cast(hs, C.c_void_p), len(solvers), bp, int(group_blocks), C.byref(ms)),
+           "maxflow_solve_batched")
+    return float(ms.value)
+
+
 def maxflow_clone(h):
     out = C.c_void_p()
     _check(load().maxflow_clone(h, C.byref(out)), "maxflow_clone")
@@ -534,6 +560,9 @@ class Solver:
 
     def set_rounds(self, r: int):
         maxflow_set_rounds(self.h, r)
+
+    def set_tuning(self, thread_max_slots=8, warp_max_slots=512, bfs_item_min_slots=256):
+        maxflow_set_tuning(self.h, thread_max_slots, warp_max_slots, bfs_item_min_slots)
 
     def features(self, u, v, c) -> np.ndarray:
         return maxflow_features(self.h, u, v, c)
