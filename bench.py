@@ -314,6 +314,106 @@ def run_batched(args):
         s.close()
 
 
+def _serving_worker(job):
+    """One serving graph and its batch sequence (runs in a spawned process, no CUDA)."""
+    scale, gseed, sizes, bseed = job
+    from paper_2511_01235_gb300 import serving as SV
+    from paper_2511_01235_gb300 import workloads as W
+    g = W.rmat(scale, 16, 0.57, 0.19, 0.19, seed=gseed, cap_hi=1000)
+    return g, SV.graph_batches(g, sizes, bseed)
+
+
+def run_serving(args):
+    """Serving: 16 R-MAT graphs (scales 18x4, 19x3, 20x3, 21x3, 22x3) under a device-memory
+    budget, Poisson arrivals of mixed batches (sizes log-uniform in [10, 100K]), continuous
+    batching.  A step is one request."""
+    import multiprocessing as mp
+    from paper_2511_01235_gb300 import serving as SV
+    ws, rank, _ = dist_env()
+    if ws > 1 and rank != 0:
+        return
+    spec = args.workload.split(":", 1)
+    scales = SV.SERVING_SCALES if len(spec) == 1 else tuple(int(x) for x in spec[1].split(","))
+    n_cal = max(args.warmup, 1) * len(scales)
+    n_req = n_cal + args.steps
+    plan = SV.plan_requests(len(scales), n_req, 1.0, seed=77, size_lo=10, size_hi=100_000)
+    jobs = [(sc, 10 + k, [b for gi, b, _ in plan if gi == k], (77, k)) for k, sc in enumerate(scales)]
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(min(len(jobs), os.cpu_count() or 1)) as pool:   # before any CUDA call
+        res = pool.map(_serving_worker, jobs, chunksize=1)
+    gen_s = time.perf_counter() - t0
+    graphs = [r[0] for r in res]
+    reqs = SV.assemble(plan, [r[1] for r in res])
+    del res
+    import torch
+    from paper_2511_01235_gb300 import native
+    torch.cuda.set_device(0)
+    native.load()
+    budget = int(args.budget_gb * 2**30)
+    t0 = time.perf_counter()
+    srv = SV.Server(graphs, budget, group_blocks=args.group_blocks)
+    init_s = time.perf_counter() - t0
+    state_gb = sum(srv.bytes) / 2**30
+    # warm-up and calibration: the first requests one at a time, all arrived at 0
+    cal = reqs[:n_cal]
+    for r in cal:
+        r.arrival = 0.0
+    srv.max_per_tick = 1
+    cst = srv.run(cal)
+    mean_s = cst.wall_s / len(cal)
+    rate = args.utilization / mean_s
+    srv.max_per_tick = None
+    srv.stats = SV.ServeStats()
+    timed = SV.retime(reqs[n_cal:], rate, seed=78)
+    clk = ClockSampler(0)
+    clk.start()
+    st = srv.run(timed)
+    clocks = clk.stop()
+    sm = st.summary()
+    # the oracle on the smallest graph's final state; the exact alone-vs-mix check is a GPU test
+    import oracle
+    g0 = graphs[0]
+    es = W_edgeset(g0)
+    for r in reqs:
+        if r.graph == 0:
+            es.apply(r.u, r.v, r.cap)
+    u, v, c = es.coo()
+    tq = time.perf_counter()
+    want = oracle.maxflow(g0.n, u, v, c, g0.s, g0.t).value
+    oracle_s = time.perf_counter() - tq
+    got = srv.solvers[0].query()[0]
+    last0 = [r for r in reqs if r.graph == 0][-1]
+    peaks, peak_src = _peaks()
+    hbm = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
+    line = {"metric": "serving: dynamic maxflow updates/s and p50/p99 request latency (arrival to result)",
+            "value": sm["updates_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * st.wall_s / max(1, st.instances), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": f"{len(scales)} R-MAT graphs, scales {list(scales)}, edge factor 16, "
+                                   f"a/b/c=0.57/0.19/0.19, caps U[1,1000], seeds 10..{9 + len(scales)}; "
+                                   "Poisson arrivals, mixed batches 40/40/10/10, sizes log-uniform in [10, 100K]",
+                       "budget_gb": args.budget_gb, "states_gb": state_gb, "rate_per_s": rate,
+                       "target_utilization": args.utilization, "group_blocks": args.group_blocks,
+                       "l2": "states of several GB, larger than L2"},
+            "latency_ms": {"p50": sm["p50_ms"], "p99": sm["p99_ms"], "mean": sm["mean_ms"]},
+            "serving": sm, "calibration": {"requests": len(cal), "mean_wall_ms": 1e3 * mean_s},
+            "flow_check": {"graph": 0, "requests": sum(1 for r in reqs if r.graph == 0), "gpu": int(got),
+                           "oracle": int(want), "equal": bool(got == want)},
+            "gpu_launches": st.ticks,
+            "roofline": {"bound": "hbm", "achieved": sm["alg_gbs"], "peak": hbm, "unit": "GB/s",
+                         "frac": sm["alg_gbs"] / hbm, "traffic": None, "kernel": "mf_multi_kernel",
+                         "peak_source": f"{peak_src} hbm_gbs (copy)"},
+            "cpu_baseline": {"value": last0.size / oracle_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"one request ({last0.size} updates) on graph 0 (scale {scales[0]}): "
+                                       "Dinic from scratch on the updated graph, single thread"},
+            "e2e": {"value": sm["updates_per_s"], "unit": UNIT,
+                    "h2d_bytes_per_step": int(12 * np.mean([r.size for r in timed])), "d2h_bytes_per_step": 8,
+                    "note": "serving is end to end: host batches in, values out, arrival to result"},
+            "clocks": clocks, "gen_s": gen_s, "init_s": init_s}
+    print(json.dumps(line), flush=True)
+    srv.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -326,11 +426,16 @@ def main():
     ap.add_argument("--static-reps", type=int, default=3)
     ap.add_argument("--quick", action="store_true", help="timed steps only (for profiling runs)")
     ap.add_argument("--sched-steps", type=int, default=6, help="batches for the learned-vs-fixed schedule comparison")
+    ap.add_argument("--budget-gb", type=float, default=8.0, help="serving: device-memory budget of the states")
+    ap.add_argument("--utilization", type=float, default=0.7, help="serving: offered load vs one-at-a-time service")
+    ap.add_argument("--group-blocks", type=int, default=8, help="serving: CTAs per instance in a launch")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched64":
         return run_batched(args)
+    if args.workload.startswith("serving"):
+        return run_serving(args)
 
     import torch
     from paper_2511_01235_gb300 import native

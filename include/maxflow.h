@@ -240,6 +240,40 @@ int maxflow_set_tuning(maxflow_ctx *c, int32_t thread_max_slots, int32_t warp_ma
 int maxflow_solve_batched(maxflow_ctx *const *ctxs, int32_t count, const maxflow_batch *batches, int32_t group_blocks,
                           double *ms_out);
 
+/* Make `stream` (a cudaStream_t on the context's device; NULL = the legacy
+ * default stream) the stream of every later call on this context.  Every
+ * call of this library returns with its own device work finished, so the
+ * switch waits for nothing (in particular not for other work queued on the
+ * old stream); after a call that failed, synchronise the old stream first.
+ * maxflow_solve_batched issues on the stream of its first context.  No
+ * counterpart in the paper. */
+int maxflow_set_stream(maxflow_ctx *c, void *stream);
+
+/* Grow the batch scratch (dedup hash tables, staging) to hold batches of up to
+ * `count` updates now rather than inside the next update, so that
+ * maxflow_device_bytes accounts for it beforehand.  It never shrinks.
+ * MAXFLOW_ERR_TOO_LARGE past 2^29 updates.  No counterpart in the paper. */
+int maxflow_reserve_batch(maxflow_ctx *c, int64_t count);
+
+/* Device memory the context holds, in bytes (graph, vertex state, scratch).
+ * No counterpart in the paper; serving uses it to admit contexts by memory. */
+int maxflow_device_bytes(maxflow_ctx *c, int64_t *bytes);
+
+/* maxflow_evict parks the context's whole state (Bi-CSR slot arrays, residual
+ * capacities, heights, excesses) in one pinned host block and releases every
+ * device allocation; maxflow_restore allocates again and copies the state
+ * back.  The pinned block is kept after a restore for the next eviction and
+ * freed by maxflow_destroy.  While evicted, every call that needs the device
+ * returns MAXFLOW_ERR_STATE (maxflow_query without side/cut_cap still returns
+ * the last value; stats, trace and the setters work).  Since the dynamic
+ * algorithm resumes from any valid preflow and labelling (Sec. 4.2), a
+ * restored context continues exactly where it stopped.  Both are no-ops when
+ * already in the requested state; both synchronise the context's stream.
+ * On failure of maxflow_restore the context stays evicted.  No counterpart in
+ * the paper. */
+int maxflow_evict(maxflow_ctx *c);
+int maxflow_restore(maxflow_ctx *c);
+
 /* A deep copy of the context's state (graph, residual capacities, heights,
  * excesses, value) on the same device and stream, as a new context; used to
  * try several schedules from one state and to checkpoint a dynamic graph

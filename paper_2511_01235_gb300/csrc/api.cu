@@ -49,6 +49,12 @@ struct maxflow_ctx {
     int64_t init_iters = 0;
     float *feat = nullptr;        // [MF_FEATURES] device
     float *sched_y = nullptr;     // [64] device
+    // eviction: the state parked in host memory while the device memory is released
+    // (one pinned block, kept after a restore so that the next eviction reuses it)
+    bool evicted = false;
+    char *park = nullptr;
+    size_t park_bytes = 0;
+    int64_t park_slots = 0;
 };
 
 // exported by mlp.cu (C linkage)
@@ -544,6 +550,7 @@ void maxflow_destroy(maxflow_ctx *c)
         DeviceGuard dg(c->device);
         if (c->stream) cudaStreamSynchronize(c->stream);
         while (!c->allocs.empty()) dfree(c, c->allocs.back().first);
+        if (c->park) cudaFreeHost(c->park);
         if (c->hctrl) cudaFreeHost(c->hctrl);
         if (c->hbuf) cudaFreeHost(c->hbuf);
         if (c->ev0) cudaEventDestroy(c->ev0);
@@ -638,6 +645,7 @@ int maxflow_init(maxflow_ctx **out, const maxflow_graph *g, int32_t s, int32_t t
 
 int maxflow_update(maxflow_ctx *c, const maxflow_batch *b)
 {
+    if (c && c->evicted) return MAXFLOW_ERR_STATE;
     if (!c) return MAXFLOW_ERR_STATE;
     DeviceGuard dg(c->device);
     if (!dg.ok) return MAXFLOW_ERR_CUDA;
@@ -646,6 +654,7 @@ int maxflow_update(maxflow_ctx *c, const maxflow_batch *b)
 
 int maxflow_apply(maxflow_ctx *c, const maxflow_batch *b)
 {
+    if (c && c->evicted) return MAXFLOW_ERR_STATE;
     if (!c) return MAXFLOW_ERR_STATE;
     DeviceGuard dg(c->device);
     if (!dg.ok) return MAXFLOW_ERR_CUDA;
@@ -654,6 +663,7 @@ int maxflow_apply(maxflow_ctx *c, const maxflow_batch *b)
 
 int maxflow_resolve_static(maxflow_ctx *c)
 {
+    if (c && c->evicted) return MAXFLOW_ERR_STATE;
     if (!c) return MAXFLOW_ERR_STATE;
     DeviceGuard dg(c->device);
     if (!dg.ok) return MAXFLOW_ERR_CUDA;
@@ -664,6 +674,7 @@ int maxflow_resolve_static(maxflow_ctx *c)
 
 int maxflow_resolve(maxflow_ctx *c)
 {
+    if (c && c->evicted) return MAXFLOW_ERR_STATE;
     if (!c) return MAXFLOW_ERR_STATE;
     DeviceGuard dg(c->device);
     if (!dg.ok) return MAXFLOW_ERR_CUDA;
@@ -674,6 +685,7 @@ int maxflow_resolve(maxflow_ctx *c)
 
 int maxflow_global_relabel(maxflow_ctx *c)
 {
+    if (c && c->evicted) return MAXFLOW_ERR_STATE;
     if (!c) return MAXFLOW_ERR_STATE;
     DeviceGuard dg(c->device);
     if (!dg.ok) return MAXFLOW_ERR_CUDA;
@@ -688,6 +700,7 @@ int maxflow_query(maxflow_ctx *c, int64_t *value, uint8_t *side, int64_t *cut_ca
 {
     if (!c) return MAXFLOW_ERR_STATE;
     if (!c->solved) return MAXFLOW_ERR_STATE;
+    if (c->evicted && (side || cut_cap)) return MAXFLOW_ERR_STATE;
     DeviceGuard dg(c->device);
     if (!dg.ok) return MAXFLOW_ERR_CUDA;
     MfParams p = base_params(c);
@@ -837,6 +850,7 @@ int maxflow_sched_actions(int32_t *mode, int32_t *rounds, int32_t *cycles, int32
 
 int maxflow_features(maxflow_ctx *c, const maxflow_batch *b, float *out)
 {
+    if (c && c->evicted) return MAXFLOW_ERR_STATE;
     if (!c || !out) return MAXFLOW_ERR_INVALID;
     DeviceGuard dg(c->device);
     if (!dg.ok) return MAXFLOW_ERR_CUDA;
@@ -848,6 +862,7 @@ int maxflow_features(maxflow_ctx *c, const maxflow_batch *b, float *out)
 
 int maxflow_run_action(maxflow_ctx *c, const maxflow_batch *b, int32_t action)
 {
+    if (c && c->evicted) return MAXFLOW_ERR_STATE;
     if (!c || action < 0 || action >= kNumActions) return MAXFLOW_ERR_INVALID;
     DeviceGuard dg(c->device);
     if (!dg.ok) return MAXFLOW_ERR_CUDA;
@@ -856,6 +871,7 @@ int maxflow_run_action(maxflow_ctx *c, const maxflow_batch *b, int32_t action)
 
 int maxflow_update_scheduled(maxflow_ctx *c, const maxflow_batch *b, maxflow_mlp *m, int32_t *action_out)
 {
+    if (c && c->evicted) return MAXFLOW_ERR_STATE;
     if (!c || !m) return MAXFLOW_ERR_INVALID;
     if (mlp_n_in(m) != MF_FEATURES || mlp_n_out(m) != kNumActions) return MAXFLOW_ERR_INVALID;
     DeviceGuard dg(c->device);
@@ -887,8 +903,10 @@ int maxflow_solve_batched(maxflow_ctx *const *ctxs, int32_t count, const maxflow
                           double *ms_out)
 {
     if (!ctxs || count < 1 || group_blocks < 1) return MAXFLOW_ERR_INVALID;
-    for (int32_t i = 0; i < count; ++i)
+    for (int32_t i = 0; i < count; ++i) {
         if (!ctxs[i] || ctxs[i]->device != ctxs[0]->device) return MAXFLOW_ERR_INVALID;
+        if (ctxs[i]->evicted) return MAXFLOW_ERR_STATE;
+    }
     maxflow_ctx *c0 = ctxs[0];
     DeviceGuard dg(c0->device);
     if (!dg.ok) return MAXFLOW_ERR_CUDA;
@@ -985,6 +1003,156 @@ int maxflow_solve_batched(maxflow_ctx *const *ctxs, int32_t count, const maxflow
     return first_rc;
 }
 
+int maxflow_set_stream(maxflow_ctx *c, void *stream)
+{
+    if (!c) return MAXFLOW_ERR_INVALID;
+    c->stream = (cudaStream_t)stream;
+    return MAXFLOW_OK;
+}
+
+int maxflow_reserve_batch(maxflow_ctx *c, int64_t count)
+{
+    if (!c || count < 0) return MAXFLOW_ERR_INVALID;
+    if (c->evicted) return MAXFLOW_ERR_STATE;
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return MAXFLOW_ERR_CUDA;
+    MF_TRY(ensure_batch(c, count));
+    return rc_cuda(cudaStreamSynchronize(c->stream));
+}
+
+int maxflow_device_bytes(maxflow_ctx *c, int64_t *bytes)
+{
+    if (!c || !bytes) return MAXFLOW_ERR_INVALID;
+    int64_t b = 0;
+    for (const auto &a : c->allocs) b += (int64_t)a.second;
+    *bytes = b;
+    return MAXFLOW_OK;
+}
+
+// Host view of the parked state: slot arrays, vertex arrays, heights and excesses
+// in one pinned block (each part 256-byte aligned).
+struct ParkView {
+    MfHostGraph g;
+    int32_t *h = nullptr;
+    long long *e = nullptr;
+    size_t bytes = 0;
+};
+
+static ParkView park_view(char *base, int32_t n, int64_t S)
+{
+    ParkView v;
+    size_t o = 0;
+    auto take = [&](size_t b) {
+        char *p = base ? base + o : nullptr;
+        o += (b + 255) & ~(size_t)255;
+        return p;
+    };
+    v.g.n = n;
+    v.g.slot_cap = S;
+    v.g.off = (int32_t *)take(sizeof(int32_t) * ((size_t)n + 1));
+    v.g.deg = (int32_t *)take(sizeof(int32_t) * (size_t)n);
+    v.g.bdeg = (int32_t *)take(sizeof(int32_t) * (size_t)n);
+    v.g.dst = (int32_t *)take(sizeof(int32_t) * (size_t)S);
+    v.g.cap = (int32_t *)take(sizeof(int32_t) * (size_t)S);
+    v.g.cf = (int32_t *)take(sizeof(int32_t) * (size_t)S);
+    v.g.rev = (int32_t *)take(sizeof(int32_t) * (size_t)S);
+    v.g.pcap = (int32_t *)take(sizeof(int32_t) * (size_t)S);
+    v.h = (int32_t *)take(sizeof(int32_t) * (size_t)n);
+    v.e = (long long *)take(sizeof(long long) * (size_t)n);
+    v.bytes = o;
+    return v;
+}
+
+static void release_device(maxflow_ctx *c)
+{
+    while (!c->allocs.empty()) dfree(c, c->allocs.back().first);
+    c->g = MfGraph{};
+    c->sc = MfScratch{};
+    c->ctrl = nullptr;
+    c->dbuf = nullptr;
+    c->feat = c->sched_y = nullptr;
+    c->x_cf = c->x_cf2 = c->x_h = nullptr;
+    c->x_e = nullptr;
+    c->multi_plist = nullptr;
+    c->multi_gstate = nullptr;
+    c->multi_cap = 0;
+}
+
+int maxflow_evict(maxflow_ctx *c)
+{
+    if (!c) return MAXFLOW_ERR_INVALID;
+    if (c->evicted) return MAXFLOW_OK;
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return MAXFLOW_ERR_CUDA;
+    MF_TRY(rc_cuda(cudaStreamSynchronize(c->stream)));
+    const int32_t n = c->n;
+    const int64_t S = c->g.slot_cap;
+    const size_t need = park_view(nullptr, n, S).bytes;
+    if (c->park_bytes < need) {
+        if (c->park) cudaFreeHost(c->park);
+        c->park = nullptr;
+        c->park_bytes = 0;
+        MF_TRY(rc_cuda(cudaMallocHost((void **)&c->park, need)));
+        c->park_bytes = need;
+    }
+    ParkView v = park_view(c->park, n, S);
+    struct Cp { void *h; const void *d; size_t b; };
+    const Cp cps[] = {{v.g.off, c->g.off, sizeof(int32_t) * ((size_t)n + 1)},
+                      {v.g.deg, c->g.deg, sizeof(int32_t) * (size_t)n},
+                      {v.g.bdeg, c->g.bdeg, sizeof(int32_t) * (size_t)n},
+                      {v.g.dst, c->g.dst, sizeof(int32_t) * (size_t)S},
+                      {v.g.cap, c->g.cap, sizeof(int32_t) * (size_t)S},
+                      {v.g.cf, c->g.cf, sizeof(int32_t) * (size_t)S},
+                      {v.g.rev, c->g.rev, sizeof(int32_t) * (size_t)S},
+                      {v.g.pcap, c->g.pcap, sizeof(int32_t) * (size_t)S},
+                      {v.h, c->g.h, sizeof(int32_t) * (size_t)n},
+                      {v.e, c->g.e, sizeof(long long) * (size_t)n}};
+    for (const Cp &cp : cps) MF_TRY(rc_cuda(cudaMemcpyAsync(cp.h, cp.d, cp.b, cudaMemcpyDeviceToHost, c->stream)));
+    MF_TRY(rc_cuda(cudaStreamSynchronize(c->stream)));
+    c->park_slots = S;
+    release_device(c);
+    c->evicted = true;
+    return MAXFLOW_OK;
+}
+
+int maxflow_restore(maxflow_ctx *c)
+{
+    if (!c) return MAXFLOW_ERR_INVALID;
+    if (!c->evicted) return MAXFLOW_OK;
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return MAXFLOW_ERR_CUDA;
+    const int32_t n = c->n;
+    ParkView v = park_view(c->park, n, c->park_slots);
+    v.g.slots = c->st.slots;
+    v.g.m_merged = c->st.m_edges;
+    int rc = upload_graph(c, v.g);
+    if (rc == MAXFLOW_OK) {
+        c->g.h = dalloc_n<int32_t>(c, n);
+        c->g.e = dalloc_n<long long>(c, n);
+        c->ctrl = (MfCtrl *)dalloc(c, sizeof(MfCtrl));
+        c->dbuf = dalloc_n<long long>(c, 16);
+        c->feat = dalloc_n<float>(c, MF_FEATURES);
+        c->sched_y = dalloc_n<float>(c, 64);
+        if (!c->g.h || !c->g.e || !c->ctrl || !c->dbuf || !c->feat || !c->sched_y) rc = MAXFLOW_ERR_OOM;
+    }
+    if (rc == MAXFLOW_OK) rc = alloc_vertex_scratch(c);
+    if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMemsetAsync(c->ctrl, 0, sizeof(MfCtrl), c->stream));
+    if (rc == MAXFLOW_OK)
+        rc = rc_cuda(cudaMemcpyAsync(c->g.h, v.h, sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, c->stream));
+    if (rc == MAXFLOW_OK)
+        rc = rc_cuda(cudaMemcpyAsync(c->g.e, v.e, sizeof(long long) * (size_t)n, cudaMemcpyHostToDevice, c->stream));
+    if (rc == MAXFLOW_OK) rc = ensure_batch(c, 1024);
+    if (rc == MAXFLOW_OK) rc = rc_cuda(cudaStreamSynchronize(c->stream));
+    if (rc != MAXFLOW_OK) {
+        cudaStreamSynchronize(c->stream);
+        release_device(c);
+        return rc;
+    }
+    c->evicted = false;
+    choose_grid(c);
+    return MAXFLOW_OK;
+}
+
 int maxflow_set_rounds(maxflow_ctx *c, int32_t rounds)
 {
     if (!c || rounds < 1 || rounds > (1 << 20)) return MAXFLOW_ERR_INVALID;
@@ -995,6 +1163,7 @@ int maxflow_set_rounds(maxflow_ctx *c, int32_t rounds)
 
 int maxflow_clone(maxflow_ctx *src, maxflow_ctx **out)
 {
+    if (src && src->evicted) return MAXFLOW_ERR_STATE;
     if (!src || !out) return MAXFLOW_ERR_INVALID;
     *out = nullptr;
     DeviceGuard dg(src->device);
@@ -1085,6 +1254,7 @@ int maxflow_stats(maxflow_ctx *c, maxflow_stats_t *out)
 
 int maxflow_set_flow(maxflow_ctx *c, int64_t count, const int32_t *u, const int32_t *v, const int32_t *f)
 {
+    if (c && c->evicted) return MAXFLOW_ERR_STATE;
     if (!c || count < 0) return MAXFLOW_ERR_INVALID;
     if (count > 0 && (!u || !v || !f)) return MAXFLOW_ERR_INVALID;
     DeviceGuard dg(c->device);
@@ -1116,6 +1286,7 @@ int maxflow_set_flow(maxflow_ctx *c, int64_t count, const int32_t *u, const int3
 
 int maxflow_get_residual(maxflow_ctx *c, int64_t *count, int32_t *u, int32_t *v, int32_t *cap, int32_t *cf)
 {
+    if (c && c->evicted) return MAXFLOW_ERR_STATE;
     if (!c || !count) return MAXFLOW_ERR_INVALID;
     DeviceGuard dg(c->device);
     if (!dg.ok) return MAXFLOW_ERR_CUDA;
@@ -1136,6 +1307,7 @@ int maxflow_get_residual(maxflow_ctx *c, int64_t *count, int32_t *u, int32_t *v,
 
 int maxflow_get_vertex_state(maxflow_ctx *c, int32_t *h, int64_t *e)
 {
+    if (c && c->evicted) return MAXFLOW_ERR_STATE;
     if (!c) return MAXFLOW_ERR_INVALID;
     DeviceGuard dg(c->device);
     if (!dg.ok) return MAXFLOW_ERR_CUDA;
@@ -1146,6 +1318,7 @@ int maxflow_get_vertex_state(maxflow_ctx *c, int32_t *h, int64_t *e)
 
 int maxflow_check(maxflow_ctx *c, int64_t *out)
 {
+    if (c && c->evicted) return MAXFLOW_ERR_STATE;
     if (!c || !out) return MAXFLOW_ERR_INVALID;
     DeviceGuard dg(c->device);
     if (!dg.ok) return MAXFLOW_ERR_CUDA;
@@ -1160,6 +1333,7 @@ int maxflow_check(maxflow_ctx *c, int64_t *out)
 
 int maxflow_get_flow(maxflow_ctx *c, int64_t *count, int32_t *u, int32_t *v, int32_t *cap, int32_t *flow)
 {
+    if (c && c->evicted) return MAXFLOW_ERR_STATE;
     if (!c || !count) return MAXFLOW_ERR_INVALID;
     if (!c->solved) return MAXFLOW_ERR_STATE;
     DeviceGuard dg(c->device);

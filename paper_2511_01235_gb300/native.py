@@ -84,7 +84,8 @@ EXPORTS = ["maxflow_default_opts", "maxflow_init", "maxflow_update", "maxflow_qu
            "maxflow_features", "maxflow_run_action", "maxflow_update_scheduled", "maxflow_mlp_create",
            "maxflow_mlp_destroy", "maxflow_mlp_shape", "maxflow_mlp_get_params", "maxflow_mlp_set_params",
            "maxflow_mlp_forward", "maxflow_mlp_grad", "maxflow_mlp_train", "maxflow_set_tuning",
-           "maxflow_solve_batched"]
+           "maxflow_solve_batched", "maxflow_device_bytes", "maxflow_evict", "maxflow_restore",
+           "maxflow_set_stream", "maxflow_reserve_batch"]
 
 TRACE_NAMES = ["start", "prologue", "batch_validated", "batch_located", "room_checked", "capacities_changed",
                "iteration_start", "bfs_roots", "bfs_level", "worklist", "discharge", "end"]
@@ -129,6 +130,11 @@ def load(build_if_missing: bool = False):
     L.maxflow_set_kernel_cycles.argtypes = [vp, i32]
     L.maxflow_set_rounds.argtypes = [vp, i32]
     L.maxflow_set_tuning.argtypes = [vp, i32, i32, i32]
+    L.maxflow_device_bytes.argtypes = [vp, P(i64)]
+    L.maxflow_evict.argtypes = [vp]
+    L.maxflow_set_stream.argtypes = [vp, vp]
+    L.maxflow_reserve_batch.argtypes = [vp, i64]
+    L.maxflow_restore.argtypes = [vp]
     L.maxflow_solve_batched.argtypes = [vp, i32, vp, i32, P(C.c_double)]
     L.maxflow_sched_actions.argtypes = [vp, vp, vp, i32, P(i32)]
     L.maxflow_features.argtypes = [vp, P(Batch), vp]
@@ -482,6 +488,7 @@ class Solver:
         dev = torch.cuda.current_device() if device is None else int(device)
         self.device = dev
         self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self.evicted = False
         o = maxflow_default_opts()
         o.kernel_cycles = int(kernel_cycles)
         o.data_driven = int(bool(data_driven))
@@ -561,6 +568,29 @@ class Solver:
     def set_rounds(self, r: int):
         maxflow_set_rounds(self.h, r)
 
+    def device_bytes(self) -> int:
+        b = C.c_int64()
+        _check(load().maxflow_device_bytes(self.h, C.byref(b)), "maxflow_device_bytes")
+        return int(b.value)
+
+    def set_stream(self, stream):
+        """Issue this instance's later work on `stream` (a torch.cuda.Stream)."""
+        _check(load().maxflow_set_stream(self.h, int(stream.cuda_stream)), "maxflow_set_stream")
+        self.stream = stream
+
+    def reserve_batch(self, count: int):
+        """Grow the batch scratch for batches of up to `count` updates now."""
+        _check(load().maxflow_reserve_batch(self.h, int(count)), "maxflow_reserve_batch")
+
+    def evict(self):
+        """Park the state in pinned host memory and release the device memory."""
+        _check(load().maxflow_evict(self.h), "maxflow_evict")
+        self.evicted = True
+
+    def restore(self):
+        _check(load().maxflow_restore(self.h), "maxflow_restore")
+        self.evicted = False
+
     def set_tuning(self, thread_max_slots=8, warp_max_slots=512, bfs_item_min_slots=256):
         maxflow_set_tuning(self.h, thread_max_slots, warp_max_slots, bfs_item_min_slots)
 
@@ -578,6 +608,7 @@ class Solver:
         other = Solver.__new__(Solver)
         other.n, other.s, other.t = self.n, self.s, self.t
         other.device, other.stream = self.device, self.stream
+        other.evicted = False
         other._alloc, other._opts = self._alloc, self._opts
         other.h = maxflow_clone(self.h)
         return other
