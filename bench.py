@@ -409,6 +409,7 @@ def run_serving(args):
             "e2e": {"value": sm["updates_per_s"], "unit": UNIT,
                     "h2d_bytes_per_step": int(12 * np.mean([r.size for r in timed])), "d2h_bytes_per_step": 8,
                     "note": "serving is end to end: host batches in, values out, arrival to result"},
+            "arena": srv.arena.stats() if srv.arena is not None else None,
             "clocks": clocks, "gen_s": gen_s, "init_s": init_s}
     print(json.dumps(line), flush=True)
     srv.close()

@@ -274,6 +274,48 @@ int maxflow_device_bytes(maxflow_ctx *c, int64_t *bytes);
 int maxflow_evict(maxflow_ctx *c);
 int maxflow_restore(maxflow_ctx *c);
 
+/* Sizes in bytes of the device allocations an evicted context held, in
+ * allocation order: an upper bound of what maxflow_restore allocates (for an
+ * admission check with maxflow_arena_fits).  *count receives their number;
+ * sizes is filled when cap >= *count.  MAXFLOW_ERR_STATE when not evicted. */
+int maxflow_evicted_sizes(maxflow_ctx *c, int64_t *sizes, int32_t cap, int32_t *count);
+
+/* ---- device-memory arena (serving many contexts under one budget) -------
+ * No counterpart in the paper.  maxflow_arena_create reserves `bytes` of
+ * device memory with one cudaMalloc on `device` (base NULL), or manages the
+ * caller's region [base, base + bytes) (base 256-byte aligned; the caller
+ * keeps ownership and the arena never dereferences it); contexts created with
+ *     opts.alloc = maxflow_arena_alloc, opts.free = maxflow_arena_free,
+ *     opts.alloc_user = arena
+ * take their device memory from it, so that later allocations (restores,
+ * batch scratch) make no CUDA allocation call and the budget is a physical
+ * bound.  Placement is best fit with coalescing; requests of 1 MiB or more
+ * take the head of the smallest free block that fits, smaller ones the tail
+ * of the highest free block.  When nothing fits: with allow_overflow the
+ * request falls back to cudaMalloc (counted in fallbacks / overflow_*),
+ * otherwise it fails and the library call returns MAXFLOW_ERR_OOM.  Thread
+ * safe.  Frees return memory at once: the library's calls finish their
+ * device work before returning, so a freed block has no work in flight.
+ * maxflow_arena_destroy synchronises the device and frees what the arena
+ * allocated; every context using the arena must be destroyed first.
+ * MAXFLOW_ERR_INVALID for bytes <= 0 or a misaligned base; MAXFLOW_ERR_OOM
+ * when the reservation fails. */
+typedef struct maxflow_arena maxflow_arena;
+typedef struct {
+    int64_t capacity, in_use, peak_in_use, free_total, largest_free, free_blocks;
+    int64_t overflow_in_use, overflow_peak, fallbacks, failed;
+} maxflow_arena_stats_t;
+
+int maxflow_arena_create(int32_t device, int64_t bytes, int32_t allow_overflow, void *base, maxflow_arena **out);
+void maxflow_arena_destroy(maxflow_arena *a);
+void *maxflow_arena_alloc(size_t bytes, void *user, void *stream);
+void maxflow_arena_free(void *ptr, size_t bytes, void *user, void *stream);
+int maxflow_arena_stats(maxflow_arena *a, maxflow_arena_stats_t *out);
+/* *fits = 1 when allocations of the given sizes, made in this order now,
+ * would all be placed in the arena (same placement policy; nothing is
+ * allocated), else 0. */
+int maxflow_arena_fits(maxflow_arena *a, const int64_t *sizes, int32_t count, int32_t *fits);
+
 /* A deep copy of the context's state (graph, residual capacities, heights,
  * excesses, value) on the same device and stream, as a new context; used to
  * try several schedules from one state and to checkpoint a dynamic graph

@@ -20,7 +20,7 @@ ROOT = os.path.dirname(HERE)
 HEADER = os.path.join(ROOT, "include", "maxflow.h")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["solver.cu", "api.cu", "graph_build.cpp", "noalloc.cu", "mlp.cu"]
+SOURCES = ["solver.cu", "api.cu", "graph_build.cpp", "noalloc.cu", "mlp.cu", "arena.cpp"]
 
 
 def _nvcc() -> str:

@@ -6,9 +6,12 @@
 // buffers and, when an insertion finds a row without spare slots, rebuilds
 // the layout (keeping flows and excesses) and repeats the update.
 #include <cuda_runtime.h>
+#include <sys/mman.h>
+#include <unistd.h>
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <utility>
@@ -54,7 +57,10 @@ struct maxflow_ctx {
     bool evicted = false;
     char *park = nullptr;
     size_t park_bytes = 0;
+    void *park_map = nullptr;          // the mapping behind `park` when it is huge-page backed
+    size_t park_map_bytes = 0;
     int64_t park_slots = 0;
+    std::vector<int64_t> park_sizes;   // the device allocations held when evicted
 };
 
 // exported by mlp.cu (C linkage)
@@ -543,6 +549,8 @@ const char *maxflow_strerror(int code)
     }
 }
 
+static void park_free(maxflow_ctx *c);
+
 void maxflow_destroy(maxflow_ctx *c)
 {
     if (!c) return;
@@ -550,7 +558,7 @@ void maxflow_destroy(maxflow_ctx *c)
         DeviceGuard dg(c->device);
         if (c->stream) cudaStreamSynchronize(c->stream);
         while (!c->allocs.empty()) dfree(c, c->allocs.back().first);
-        if (c->park) cudaFreeHost(c->park);
+        park_free(c);
         if (c->hctrl) cudaFreeHost(c->hctrl);
         if (c->hbuf) cudaFreeHost(c->hbuf);
         if (c->ev0) cudaEventDestroy(c->ev0);
@@ -1020,12 +1028,82 @@ int maxflow_reserve_batch(maxflow_ctx *c, int64_t count)
     return rc_cuda(cudaStreamSynchronize(c->stream));
 }
 
+int maxflow_evicted_sizes(maxflow_ctx *c, int64_t *sizes, int32_t cap, int32_t *count)
+{
+    if (!c || !count) return MAXFLOW_ERR_INVALID;
+    if (!c->evicted) return MAXFLOW_ERR_STATE;
+    const int32_t k = (int32_t)c->park_sizes.size();
+    *count = k;
+    if (sizes && cap >= k) std::memcpy(sizes, c->park_sizes.data(), sizeof(int64_t) * (size_t)k);
+    return MAXFLOW_OK;
+}
+
 int maxflow_device_bytes(maxflow_ctx *c, int64_t *bytes)
 {
     if (!c || !bytes) return MAXFLOW_ERR_INVALID;
     int64_t b = 0;
     for (const auto &a : c->allocs) b += (int64_t)a.second;
     *bytes = b;
+    return MAXFLOW_OK;
+}
+
+// Host memory for a parked state.  Blocks of 64 MiB and more are anonymous
+// mappings advised to transparent huge pages and registered with the driver;
+// smaller ones (and any failure on that path) come from cudaMallocHost.  With
+// small base pages, device-to-host copies into long-lived pinned blocks were
+// measured to slow down by up to 20x after unrelated host memory activity in
+// the process (the device re-translates the host pages), while huge-page
+// blocks kept full speed (about 193 GB/s device-to-host on a GB300 host).
+static size_t huge_page_bytes()
+{
+    static size_t hp = 0;
+    if (!hp) {
+        hp = 2u << 20;
+        if (FILE *f = std::fopen("/sys/kernel/mm/transparent_hugepage/hpage_pmd_size", "r")) {
+            unsigned long long v = 0;
+            if (std::fscanf(f, "%llu", &v) == 1 && v >= 4096 && v <= (1ull << 31)) hp = (size_t)v;
+            std::fclose(f);
+        }
+    }
+    return hp;
+}
+
+static void park_free(maxflow_ctx *c)
+{
+    if (c->park_map) {
+        cudaHostUnregister(c->park);
+        munmap(c->park_map, c->park_map_bytes);
+    } else if (c->park) {
+        cudaFreeHost(c->park);
+    }
+    c->park = nullptr;
+    c->park_map = nullptr;
+    c->park_bytes = c->park_map_bytes = 0;
+}
+
+static int park_alloc(maxflow_ctx *c, size_t bytes)
+{
+    park_free(c);
+    if (bytes >= (64u << 20)) {
+        const size_t hp = huge_page_bytes();
+        const size_t sz = (bytes + hp - 1) / hp * hp;
+        void *m = mmap(nullptr, sz + hp, PROT_READ | PROT_WRITE, MAP_PRIVATE | MAP_ANONYMOUS, -1, 0);
+        if (m != MAP_FAILED) {
+            char *a = (char *)(((uintptr_t)m + hp - 1) / hp * hp);
+            madvise(a, sz, MADV_HUGEPAGE);
+            if (cudaHostRegister(a, sz, cudaHostRegisterDefault) == cudaSuccess) {
+                c->park = a;
+                c->park_bytes = sz;
+                c->park_map = m;
+                c->park_map_bytes = sz + hp;
+                return MAXFLOW_OK;
+            }
+            cudaGetLastError();
+            munmap(m, sz + hp);
+        }
+    }
+    MF_TRY(rc_cuda(cudaMallocHost((void **)&c->park, bytes)));
+    c->park_bytes = bytes;
     return MAXFLOW_OK;
 }
 
@@ -1088,13 +1166,7 @@ int maxflow_evict(maxflow_ctx *c)
     const int32_t n = c->n;
     const int64_t S = c->g.slot_cap;
     const size_t need = park_view(nullptr, n, S).bytes;
-    if (c->park_bytes < need) {
-        if (c->park) cudaFreeHost(c->park);
-        c->park = nullptr;
-        c->park_bytes = 0;
-        MF_TRY(rc_cuda(cudaMallocHost((void **)&c->park, need)));
-        c->park_bytes = need;
-    }
+    if (c->park_bytes < need) MF_TRY(park_alloc(c, need));
     ParkView v = park_view(c->park, n, S);
     struct Cp { void *h; const void *d; size_t b; };
     const Cp cps[] = {{v.g.off, c->g.off, sizeof(int32_t) * ((size_t)n + 1)},
@@ -1110,6 +1182,8 @@ int maxflow_evict(maxflow_ctx *c)
     for (const Cp &cp : cps) MF_TRY(rc_cuda(cudaMemcpyAsync(cp.h, cp.d, cp.b, cudaMemcpyDeviceToHost, c->stream)));
     MF_TRY(rc_cuda(cudaStreamSynchronize(c->stream)));
     c->park_slots = S;
+    c->park_sizes.clear();
+    for (const auto &a : c->allocs) c->park_sizes.push_back((int64_t)a.second);
     release_device(c);
     c->evicted = true;
     return MAXFLOW_OK;

@@ -56,6 +56,11 @@ class Opts(C.Structure):
                 ("alloc_user", C.c_void_p)]
 
 
+class ArenaStats(C.Structure):
+    _fields_ = [(k, C.c_int64) for k in ("capacity", "in_use", "peak_in_use", "free_total", "largest_free",
+                                          "free_blocks", "overflow_in_use", "overflow_peak", "fallbacks", "failed")]
+
+
 class Stats(C.Structure):
     _fields_ = [("n", C.c_int64), ("m_edges", C.c_int64), ("slots", C.c_int64), ("slot_capacity", C.c_int64),
                 ("kernel_cycles", C.c_int32), ("grid_blocks", C.c_int32), ("block_threads", C.c_int32),
@@ -85,7 +90,9 @@ EXPORTS = ["maxflow_default_opts", "maxflow_init", "maxflow_update", "maxflow_qu
            "maxflow_mlp_destroy", "maxflow_mlp_shape", "maxflow_mlp_get_params", "maxflow_mlp_set_params",
            "maxflow_mlp_forward", "maxflow_mlp_grad", "maxflow_mlp_train", "maxflow_set_tuning",
            "maxflow_solve_batched", "maxflow_device_bytes", "maxflow_evict", "maxflow_restore",
-           "maxflow_set_stream", "maxflow_reserve_batch"]
+           "maxflow_set_stream", "maxflow_reserve_batch",
+           "maxflow_arena_create", "maxflow_arena_destroy", "maxflow_arena_alloc", "maxflow_arena_free",
+           "maxflow_arena_stats", "maxflow_arena_fits", "maxflow_evicted_sizes"]
 
 TRACE_NAMES = ["start", "prologue", "batch_validated", "batch_located", "room_checked", "capacities_changed",
                "iteration_start", "bfs_roots", "bfs_level", "worklist", "discharge", "end"]
@@ -134,6 +141,16 @@ def load(build_if_missing: bool = False):
     L.maxflow_evict.argtypes = [vp]
     L.maxflow_set_stream.argtypes = [vp, vp]
     L.maxflow_reserve_batch.argtypes = [vp, i64]
+    L.maxflow_arena_create.argtypes = [i32, i64, i32, vp, P(vp)]
+    L.maxflow_arena_destroy.argtypes = [vp]
+    L.maxflow_arena_destroy.restype = None
+    L.maxflow_arena_alloc.argtypes = [C.c_size_t, vp, vp]
+    L.maxflow_arena_alloc.restype = vp
+    L.maxflow_arena_free.argtypes = [vp, C.c_size_t, vp, vp]
+    L.maxflow_arena_free.restype = None
+    L.maxflow_arena_stats.argtypes = [vp, P(ArenaStats)]
+    L.maxflow_arena_fits.argtypes = [vp, vp, i32, P(i32)]
+    L.maxflow_evicted_sizes.argtypes = [vp, vp, i32, P(i32)]
     L.maxflow_restore.argtypes = [vp]
     L.maxflow_solve_batched.argtypes = [vp, i32, vp, i32, P(C.c_double)]
     L.maxflow_sched_actions.argtypes = [vp, vp, vp, i32, P(i32)]
@@ -156,7 +173,8 @@ def load(build_if_missing: bool = False):
     L.maxflow_strerror.argtypes = [C.c_int]
     L.maxflow_strerror.restype = C.c_char_p
     for name in EXPORTS:
-        if name not in ("maxflow_default_opts", "maxflow_destroy", "maxflow_strerror", "maxflow_mlp_destroy"):
+        if name not in ("maxflow_default_opts", "maxflow_destroy", "maxflow_strerror", "maxflow_mlp_destroy",
+                        "maxflow_arena_destroy", "maxflow_arena_alloc", "maxflow_arena_free"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -473,12 +491,54 @@ def maxflow_destroy(h):
 
 # ---- object wrapper --------------------------------------------------------------
 
+class Arena:
+    """A device-memory arena (maxflow_arena_*) that Solvers can allocate from.
+
+    nbytes are reserved with one cudaMalloc on `device`, or, with `base` (an
+    int address, 256-byte aligned), the caller's region is managed instead.
+    """
+
+    def __init__(self, nbytes: int, device: int = 0, allow_overflow: bool = True, base: int | None = None):
+        L = load()
+        h = C.c_void_p()
+        _check(L.maxflow_arena_create(int(device), int(nbytes), int(bool(allow_overflow)), base, C.byref(h)),
+               "maxflow_arena_create")
+        self.h = h
+        self.device = int(device)
+        self.alloc_fn = ALLOC_FN(C.cast(L.maxflow_arena_alloc, C.c_void_p).value)
+        self.free_fn = FREE_FN(C.cast(L.maxflow_arena_free, C.c_void_p).value)
+
+    def alloc(self, nbytes: int) -> int:
+        return load().maxflow_arena_alloc(int(nbytes), self.h, None) or 0
+
+    def free(self, ptr: int):
+        load().maxflow_arena_free(ptr, 0, self.h, None)
+
+    def fits(self, sizes) -> bool:
+        """Would allocations of these sizes, in this order, all be placed now?"""
+        a = np.ascontiguousarray(np.asarray(sizes, dtype=np.int64))
+        f = C.c_int32(0)
+        _check(load().maxflow_arena_fits(self.h, a.ctypes.data if a.size else None, int(a.size), C.byref(f)),
+               "maxflow_arena_fits")
+        return bool(f.value)
+
+    def stats(self) -> dict:
+        st = ArenaStats()
+        _check(load().maxflow_arena_stats(self.h, C.byref(st)), "maxflow_arena_stats")
+        return {k: int(getattr(st, k)) for k, _ in ArenaStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().maxflow_arena_destroy(self.h)
+            self.h = None
+
+
 class Solver:
     """One dynamic max-flow instance on one GPU (thin wrapper over the C calls)."""
 
     def __init__(self, n, src, dst, cap, s, t, *, kernel_cycles=0, data_driven=True, fix_steep=True,
                  grid_blocks=0, max_iters=0, time_limit_s=0.0, wait_limit_s=0.0, slack_factor=0.25,
-                 slack_min=4, device=None, stream=None, torch_alloc=True):
+                 slack_min=4, device=None, stream=None, torch_alloc=True, arena=None):
         import torch
         load()
         if not torch.cuda.is_available():
@@ -501,8 +561,13 @@ class Solver:
         o.slack_min = int(slack_min)
         o.device = dev
         o.stream = int(self.stream.cuda_stream)
-        self._alloc = _TorchAllocator(dev) if torch_alloc else None
-        if self._alloc is not None:
+        self._alloc = _TorchAllocator(dev) if torch_alloc and arena is None else None
+        if arena is not None:
+            self._alloc = arena                  # keeps the arena alive as long as the instance
+            o.alloc = arena.alloc_fn
+            o.free = arena.free_fn
+            o.alloc_user = arena.h.value
+        elif self._alloc is not None:
             o.alloc = self._alloc.alloc
             o.free = self._alloc.free
         self._opts = o
@@ -577,6 +642,15 @@ class Solver:
         """Issue this instance's later work on `stream` (a torch.cuda.Stream)."""
         _check(load().maxflow_set_stream(self.h, int(stream.cuda_stream)), "maxflow_set_stream")
         self.stream = stream
+
+    def evicted_sizes(self) -> np.ndarray:
+        """Sizes of the device allocations held when evicted (what a restore needs at most)."""
+        L = load()
+        k = C.c_int32(0)
+        _check(L.maxflow_evicted_sizes(self.h, None, 0, C.byref(k)), "maxflow_evicted_sizes")
+        out = np.zeros(int(k.value), np.int64)
+        _check(L.maxflow_evicted_sizes(self.h, out.ctypes.data, int(out.size), C.byref(k)), "maxflow_evicted_sizes")
+        return out
 
     def reserve_batch(self, count: int):
         """Grow the batch scratch for batches of up to `count` updates now."""

@@ -13,9 +13,12 @@ persistent launch (maxflow_solve_batched).  Requests that arrive while a launch
 runs join the next tick.
 
 Admission by memory: the states do not all fit in the device-memory budget.
-A request whose graph is evicted needs its state restored first; the server
-evicts the least recently used graphs that are not in the running launch until
-the restore fits.  Evictions and restores of graphs outside the running launch
+The budget is one device arena (maxflow_arena_*): every state allocates from
+it, so a restore makes no CUDA allocation call (which would serialise it with
+the running launch) and the budget is physical.  A request whose graph is
+evicted needs its state restored first; the server evicts the least recently
+used graphs that are not in the running launch until the state fits, both in
+bytes and as a free block large enough for its largest array.  Evictions and restores of graphs outside the running launch
 go on a copy stream from the host thread while a worker thread waits for the
 launch on the compute stream, so state traffic overlaps the solve.
 """
@@ -61,8 +64,25 @@ class ServeStats:
     evict_ms: float = 0.0
     restore_ms: float = 0.0
     peak_resident_bytes: int = 0
+    arena_fallbacks: int = 0       # allocations the arena could not place (went to cudaMalloc)
+    moves: list = field(default_factory=list)   # (kind, graph, bytes, ms, launch running)
     alg_bytes: float = 0.0         # algorithmic bytes of the launches (the solver's traffic model)
     latencies_ms: list = field(default_factory=list)
+
+    def move_summary(self) -> dict:
+        """Evictions and restores: count, GB, ms and GB/s, split by whether a launch was running."""
+        out = {}
+        for kind in ("evict", "restore"):
+            for busy in (False, True):
+                mv = [m for m in self.moves if m[0] == kind and m[4] == busy]
+                if not mv:
+                    continue
+                gb = sum(m[2] for m in mv) / 1e9
+                ms = sum(m[3] for m in mv)
+                out[f"{kind}_{'during_launch' if busy else 'idle'}"] = {
+                    "count": len(mv), "gb": gb, "ms": ms, "gbs": gb / (ms / 1e3) if ms > 0 else None,
+                    "max_ms": max(m[3] for m in mv)}
+        return out
 
     def summary(self) -> dict:
         lat = np.asarray(self.latencies_ms, np.float64)
@@ -76,7 +96,8 @@ class ServeStats:
                 "ticks": self.ticks, "mean_batch": self.instances / max(1, self.ticks),
                 "evictions": self.evictions, "restores": self.restores,
                 "evict_ms": self.evict_ms, "restore_ms": self.restore_ms,
-                "peak_resident_gb": self.peak_resident_bytes / 2**30,
+                "peak_resident_gb": self.peak_resident_bytes / 2**30, "arena_fallbacks": self.arena_fallbacks,
+                "moves": self.move_summary(),
                 "alg_gbs": self.alg_bytes / (self.device_ms * 1e6) if self.device_ms > 0 else 0.0}
 
 
@@ -91,10 +112,16 @@ class Server:
 
     def __init__(self, graphs, budget_bytes: int, group_blocks: int = 8, overlap: bool = True,
                  max_per_tick: int | None = None, log=None, streams=None, solver_factory=None):
+        self.arena = None
         if streams is None:
             import torch
             streams = (torch.cuda.Stream(), torch.cuda.Stream())
-        make = solver_factory or native.Solver
+        if solver_factory is None:
+            import torch
+            self.arena = native.Arena(int(budget_bytes), device=torch.cuda.current_device(), allow_overflow=True)
+            make = lambda *a, **k: native.Solver(*a, arena=self.arena, **k)
+        else:
+            make = solver_factory
         self.budget = int(budget_bytes)
         self.group_blocks = int(group_blocks)
         self.overlap = bool(overlap)
@@ -105,13 +132,19 @@ class Server:
         self.bytes: list[int] = []
         self.last_use: list[int] = []
         self.clock = 0
+        self._busy = False
         self.stats = ServeStats()
         for i, g in enumerate(graphs):
+            fb = self._fallbacks()
             S = make(g.n, g.src, g.dst, g.cap, g.s, g.t, stream=self.compute)
             self.solvers.append(S)
             self.bytes.append(S.device_bytes())
             self.last_use.append(self._tick_id())
             self._make_room(0, keep={i}, stream=self.compute)
+            if self._fallbacks() > fb:            # created outside the arena: move it in
+                S.evict()
+                self._make_room(self.bytes[i], keep={i}, stream=self.compute, sizes=S.evicted_sizes())
+                S.restore()
             if log:
                 log(f"  graph {i}: n={g.n} m={g.src.size} value={S.query()[0]} "
                     f"{self.bytes[i] / 2**20:.0f} MiB, resident {self.resident_bytes() / 2**30:.2f} GiB")
@@ -122,6 +155,18 @@ class Server:
     def _tick_id(self):
         self.clock += 1
         return self.clock
+
+    def _fallbacks(self) -> int:
+        return self.arena.stats()["fallbacks"] if self.arena is not None else 0
+
+    def _sizes(self, i):
+        S = self.solvers[i]
+        return S.evicted_sizes() if self.arena is not None and S.evicted else None
+
+    def _fits(self, need, sizes) -> bool:
+        if self.resident_bytes() + need > self.budget:
+            return False
+        return self.arena is None or sizes is None or self.arena.fits(sizes)
 
     def resident(self, i) -> bool:
         return not self.solvers[i].evicted
@@ -135,8 +180,10 @@ class Server:
         if stream is not S.stream:
             S.set_stream(stream)
         S.evict()
-        self.stats.evict_ms += (time.perf_counter() - t0) * 1e3
+        ms = (time.perf_counter() - t0) * 1e3
+        self.stats.evict_ms += ms
         self.stats.evictions += 1
+        self.stats.moves.append(("evict", i, self.bytes[i], ms, self._busy))
 
     def _restore(self, i, stream):
         S = self.solvers[i]
@@ -147,12 +194,15 @@ class Server:
         if S.stream is not self.compute:
             S.set_stream(self.compute)
         self.bytes[i] = S.device_bytes()
-        self.stats.restore_ms += (time.perf_counter() - t0) * 1e3
+        ms = (time.perf_counter() - t0) * 1e3
+        self.stats.restore_ms += ms
         self.stats.restores += 1
+        self.stats.moves.append(("restore", i, self.bytes[i], ms, self._busy))
 
-    def _make_room(self, need, keep, stream) -> bool:
-        """Evict LRU states outside `keep` until `need` more bytes fit the budget."""
-        while self.resident_bytes() + need > self.budget:
+    def _make_room(self, need, keep, stream, sizes=None) -> bool:
+        """Evict LRU states outside `keep` until `need` more bytes fit the budget
+        (and, with the arena, allocations of `sizes` would all be placed)."""
+        while not self._fits(need, sizes):
             victims = [j for j in range(len(self.solvers)) if self.resident(j) and j not in keep]
             if not victims:
                 return False
@@ -175,7 +225,7 @@ class Server:
             i = r.graph
             keep = set(busy) | {r2.graph for r2 in chosen} | {i}
             if not self.resident(i):
-                if not self._make_room(self.bytes[i], keep, self.copy):
+                if not self._make_room(self.bytes[i], keep, self.copy, self._sizes(i)):
                     continue                      # waits for memory; younger resident requests may still go
                 self._restore(i, self.copy)
             S = self.solvers[i]
@@ -214,6 +264,7 @@ class Server:
                 r = pending.popleft()
                 queues[r.graph].append(r)
             busy = set() if running is None else {r.graph for r in running[2]}
+            self._busy = running is not None
             heads = [q[0] for i, q in enumerate(queues) if q and i not in busy]
             nxt = None
             if heads and (running is None or self.overlap):
@@ -223,7 +274,8 @@ class Server:
                 else:
                     for r in sorted(heads, key=lambda r: r.arrival):
                         if not self.resident(r.graph) and \
-                                self._make_room(self.bytes[r.graph], busy | {r.graph}, self.copy):
+                                self._make_room(self.bytes[r.graph], busy | {r.graph}, self.copy,
+                                                self._sizes(r.graph)):
                             self._restore(r.graph, self.copy)
                         break
             if running is not None:
@@ -270,6 +322,7 @@ class Server:
                 self._launch(nxt, out)
             running = (th, out, nxt)
         st.wall_s = now()
+        st.arena_fallbacks = self._fallbacks()
         for i, S in enumerate(self.solvers):
             if self.resident(i):
                 self.bytes[i] = S.device_bytes()
@@ -279,6 +332,9 @@ class Server:
         for S in self.solvers:
             S.close()
         self.solvers = []
+        if self.arena is not None:
+            self.arena.close()
+            self.arena = None
 
 
 class _Done:

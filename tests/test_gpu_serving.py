@@ -97,9 +97,11 @@ def test_serving_answers_equal_alone_under_a_binding_budget(overlap):
     graphs = _mix_graphs()
     reqs = SV.make_requests(graphs, 60, rate_per_s=400.0, seed=440, size_lo=10, size_hi=5000)
     alone, _ = SV.run_alone(graphs, reqs)
-    srv = SV.Server(graphs, budget_bytes=1, overlap=overlap)     # probe the footprints first
-    total = sum(srv.bytes)
-    srv.close()
+    total = 0
+    for g in graphs:                                             # the states' footprints
+        S = native.Solver(g.n, g.src, g.dst, g.cap, g.s, g.t)
+        total += S.device_bytes()
+        S.close()
     budget = int(0.5 * total)
     srv = SV.Server(graphs, budget_bytes=budget, overlap=overlap, group_blocks=4)
     assert srv.resident_bytes() <= budget
@@ -107,6 +109,7 @@ def test_serving_answers_equal_alone_under_a_binding_budget(overlap):
     assert [r.value for r in reqs] == [alone[k] for k in range(len(reqs))]
     assert st.evictions > 0 and st.restores > 0
     assert st.peak_resident_bytes <= budget
+    assert srv.arena.stats()["peak_in_use"] <= budget
     # final states agree with the oracle
     sets = [W.EdgeSet(g.n, g.src, g.dst, g.cap) for g in graphs]
     for r in reqs:
