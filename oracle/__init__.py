@@ -84,6 +84,22 @@ def _load():
     L.orc_rs_get_vertex.argtypes = [vp, vp, vp]
     L.orc_rs_cut.restype = C.c_int64
     L.orc_rs_cut.argtypes = [vp, vp]
+    L.orc_rs_saturate_sink.restype = None
+    L.orc_rs_saturate_sink.argtypes = [vp, C.c_int32]
+    L.orc_rs_heights_side.restype = None
+    L.orc_rs_heights_side.argtypes = [vp, C.c_int32, C.c_int32, vp, C.c_int]
+    L.orc_rs_pull_heights.restype = None
+    L.orc_rs_pull_heights.argtypes = [vp, C.c_int32, C.c_int32, vp, C.c_int, vp]
+    L.orc_rs_pull_value.restype = C.c_int64
+    L.orc_rs_pull_value.argtypes = [vp, C.c_int32]
+    L.orc_rs_push_side.restype = C.c_int
+    L.orc_rs_push_side.argtypes = [vp, C.c_int32, C.c_int32, vp, C.c_int, C.c_int32, C.c_int64]
+    L.orc_rs_pull_relabel.restype = C.c_int
+    L.orc_rs_pull_relabel.argtypes = [vp, C.c_int32, C.c_int32, vp, C.c_int, C.c_int32, C.c_int64, vp]
+    L.orc_rs_cut_side.restype = None
+    L.orc_rs_cut_side.argtypes = [vp, vp]
+    L.orc_rs_saturate_cut.restype = None
+    L.orc_rs_saturate_cut.argtypes = [vp, vp]
     _lib = L
     return L
 
@@ -193,6 +209,74 @@ class Residual:
         if v < 0 and v == -1:
             raise RuntimeError("sequential push-relabel did not converge")
         return int(v), int(it[0]), int(pu[0]), int(rl[0])
+
+    # ---- Sec. 5.2.2 (O2) push and pull (readings R8, R9 in oracle.c) ----
+
+    def saturate_sink(self, t):
+        self._L.orc_rs_saturate_sink(self._h, t)
+
+    def pull_heights(self, s, t, side=None, want=0):
+        h = np.zeros(self.n, np.int32)
+        sd = None if side is None else np.ascontiguousarray(side, dtype=np.uint8)
+        self._L.orc_rs_pull_heights(self._h, s, t, _ptr(sd), int(want), _ptr(h))
+        return h
+
+    def pull_value(self, t):
+        return int(self._L.orc_rs_pull_value(self._h, t))
+
+    def push_side(self, s, t, side, want, kernel_cycles, max_iters=1_000_000):
+        sd = None if side is None else np.ascontiguousarray(side, dtype=np.uint8)
+        if self._L.orc_rs_push_side(self._h, s, t, _ptr(sd), int(want), kernel_cycles, max_iters) != 0:
+            raise RuntimeError("sequential push did not converge")
+
+    def pull_relabel(self, s, t, kernel_cycles, side=None, want=0, max_iters=1_000_000):
+        it = np.zeros(1, np.int64)
+        sd = None if side is None else np.ascontiguousarray(side, dtype=np.uint8)
+        if self._L.orc_rs_pull_relabel(self._h, s, t, _ptr(sd), int(want), kernel_cycles, max_iters, _ptr(it)) != 0:
+            raise RuntimeError("sequential pull-relabel did not converge")
+        return int(it[0])
+
+    def cut_side(self):
+        side = np.zeros(self.n, np.uint8)
+        self._L.orc_rs_cut_side(self._h, _ptr(side))
+        return side
+
+    def saturate_cut(self, side):
+        self._L.orc_rs_saturate_cut(self._h, _ptr(np.ascontiguousarray(side, dtype=np.uint8)))
+
+    def static_pull(self, s, t, kernel_cycles):
+        """Max flow by pulling only: saturate the edges into t, then pull-relabel
+        with roots s (R8); returns the pull value."""
+        self.static_init_empty()
+        self.saturate_sink(t)
+        self.pull_relabel(s, t, kernel_cycles)
+        self.pull_heights(s, t)
+        return self.pull_value(t)
+
+    def static_init_empty(self):
+        """c_f = c, e = 0, h = 0 (Alg. 1's initialisation without the source step)."""
+        self.set_flow(np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int32))
+
+    def static_push_pull(self, s, t, kernel_cycles):
+        """Static push-pull (Sec. 5.2.2): saturate the edges out of s and into t,
+        then push with the deficient vertices as sinks; returns the value (R3)."""
+        self.static_init(s)
+        self.saturate_sink(t)
+        v, _, _, _ = self.push_relabel(s, t, kernel_cycles)
+        return v
+
+    def push_pull_update(self, s, t, u, v, c, kernel_cycles):
+        """The dynamic push-pull of Sec. 5.2.2 on a solved state: the sides of the
+        last cut, the batch (Alg. 5 lines 1-16), saturation across the cut, push
+        on T and pull on S with side-limited roots, then a final push solve (R9)."""
+        side = self.cut_side()
+        side[s], side[t] = 0, 1
+        self.apply(s, u, v, c)
+        self.saturate_cut(side)
+        self.push_side(s, t, side, 1, kernel_cycles)
+        self.pull_relabel(s, t, kernel_cycles, side=side, want=0)
+        val, _, _, _ = self.push_relabel(s, t, kernel_cycles)
+        return val
 
     def slots(self):
         K = int(self._L.orc_rs_num_slots(self._h))

@@ -29,6 +29,11 @@
  *        - Alg. 2 / Alg. 3 inside the Alg. 1 / Alg. 5 loop, run
  *          sequentially (one vertex at a time), and the value formula of
  *          Alg. 5.
+ *   5. Sec. 5.2.2 (O2) push and pull: saturating the edges into t, the pull
+ *      heights (distance from s and the overflowing vertices), pull-relabel
+ *      (the mirror of Alg. 2 / Alg. 3 for deficient vertices), the sides of
+ *      the last min cut, saturating the edges across it, and pushes / pulls
+ *      restricted to one side's roots.
  *
  * Readings of the paper that this oracle takes where the text is ambiguous:
  *   R1 the dynamic loop of Alg. 5 runs until no active vertex remains;
@@ -45,6 +50,18 @@
  *   R7 an update sets cap(u,v); a missing pair is inserted with capacity 0
  *      in both directions first; the last update of a pair in a batch wins;
  *      u == v is ignored.
+ *   R8 (O2) pull heights: h(v) = residual distance from the root set
+ *      {s} + {v not in {s,t}: e(v) > 0} to v; t is never labelled; a
+ *      deficient vertex u (e(u) < 0, h(u) < n) pulls min(-e(u), c_f(z,u))
+ *      from its lowest residual in-neighbour z when h(u) > h(z), else is
+ *      relabelled to 1 + that lowest height (clamped to n); the pull value
+ *      is the sum of -e(v) over v != t with h(v) < n;
+ *   R9 (O2) the old min cut is T = {h < n} of the push heights the last
+ *      solve ended with, S the rest; "saturate the edges across it" sends
+ *      all of c_f(u, v) for u in S, v in T; the push part then takes as roots
+ *      t and the deficient vertices of T only, the pull part s and the
+ *      overflowing vertices of S only, and a final unrestricted push solve
+ *      follows.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -668,6 +685,232 @@ int64_t orc_rs_push_relabel(orc_rstate *r, int32_t s, int32_t t, int32_t kernel_
     if (relabels_out) *relabels_out = relabels;
     if (nact != 0) return -1;
     return orc_rs_value(r, s);
+}
+
+/* ------------------------------------------------------------------------ */
+/* 5. Sec. 5.2.2 (O2): push and pull                                        */
+/* ------------------------------------------------------------------------ */
+
+/* Static push-pull initialisation: saturate every edge into t as well:
+ * for every pair (z, t), c_f(z, t) = 0, c_f(t, z) += that residual, the
+ * residual leaves z (e(z) decreases, possibly below 0) and reaches t. */
+void orc_rs_saturate_sink(orc_rstate *r, int32_t t)
+{
+    int64_t i;
+    for (i = r->row[t]; i < r->row[t + 1]; i++) {
+        int64_t j = r->rev[i];                 /* slot (z, t) */
+        int32_t z = r->head[i];
+        int64_t d = r->cf[j];
+        if (d > 0) {
+            r->cf[j] = 0;
+            r->cf[i] += d;
+            r->e[z] -= d;
+            r->e[t] += d;
+        }
+    }
+}
+
+/* Push heights with the deficit roots limited to one side (R9):
+ * roots are t and every v not in {s,t} with e(v) < 0 and side[v] == want
+ * (side == NULL: every such v).  Same BFS as orc_rs_heights otherwise. */
+void orc_rs_heights_side(orc_rstate *r, int32_t s, int32_t t, const uint8_t *side, int want)
+{
+    int32_t n = r->n, x;
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int64_t head = 0, tail = 0, i;
+    for (x = 0; x < n; x++) r->h[x] = n;
+    r->h[t] = 0;
+    queue[tail++] = t;
+    for (x = 0; x < n; x++)
+        if (x != s && x != t && r->e[x] < 0 && (!side || side[x] == want)) { r->h[x] = 0; queue[tail++] = x; }
+    while (head < tail) {
+        int32_t y = queue[head++];
+        for (i = r->row[y]; i < r->row[y + 1]; i++) {
+            int32_t z = r->head[i];
+            if (z != s && r->h[z] == n && r->cf[r->rev[i]] > 0) {
+                r->h[z] = r->h[y] + 1;
+                queue[tail++] = z;
+            }
+        }
+    }
+    free(queue);
+}
+
+/* Pull heights (R8): h(v) = residual distance from the roots s and every
+ * v not in {s,t} with e(v) > 0 (and side[v] == want when side is given) to
+ * v, following residual edges forward: y labelled, c_f(y, z) > 0 labels z. */
+void orc_rs_pull_heights(orc_rstate *r, int32_t s, int32_t t, const uint8_t *side, int want, int32_t *h_out)
+{
+    int32_t n = r->n, x;
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int64_t head = 0, tail = 0, i;
+    for (x = 0; x < n; x++) r->h[x] = n;
+    r->h[s] = 0;
+    queue[tail++] = s;
+    for (x = 0; x < n; x++)
+        if (x != s && x != t && r->e[x] > 0 && (!side || side[x] == want)) { r->h[x] = 0; queue[tail++] = x; }
+    while (head < tail) {
+        int32_t y = queue[head++];
+        for (i = r->row[y]; i < r->row[y + 1]; i++) {
+            int32_t z = r->head[i];                 /* residual edge (y, z) */
+            if (z != t && r->h[z] == n && r->cf[i] > 0) {
+                r->h[z] = r->h[y] + 1;
+                queue[tail++] = z;
+            }
+        }
+    }
+    free(queue);
+    if (h_out) memcpy(h_out, r->h, sizeof(int32_t) * (size_t)n);
+}
+
+/* Pull value (R8): sum of -e(v) over v != t with h(v) < n. */
+int64_t orc_rs_pull_value(const orc_rstate *r, int32_t t)
+{
+    int64_t v = 0;
+    int32_t x;
+    for (x = 0; x < r->n; x++) if (x != t && r->h[x] < r->n) v -= r->e[x];
+    return v;
+}
+
+/* Push-relabel as orc_rs_push_relabel, with the deficit roots of every BFS
+ * limited to side[v] == want.  Returns 0, or -1 when max_iters iterations did
+ * not reach a state without active vertices. */
+int orc_rs_push_side(orc_rstate *r, int32_t s, int32_t t, const uint8_t *side, int want, int32_t kernel_cycles,
+                     int64_t max_iters)
+{
+    int32_t n = r->n, x;
+    int32_t *active = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int64_t it, nact = 0, i;
+    for (it = 0; it < max_iters; it++) {
+        orc_rs_heights_side(r, s, t, side, want);
+        nact = 0;
+        for (x = 0; x < n; x++)
+            if (x != s && x != t && r->e[x] > 0 && r->h[x] < n) active[nact++] = x;
+        if (nact == 0) break;
+        for (i = 0; i < nact; i++) {
+            int32_t u = active[i], cnt;
+            for (cnt = 0; cnt < kernel_cycles; cnt++) {
+                int64_t best = -1, j;
+                int32_t hbest = INT32_MAX;
+                if (!(r->h[u] < n && r->e[u] > 0)) continue;
+                for (j = r->row[u]; j < r->row[u + 1]; j++)
+                    if (r->cf[j] > 0 && r->h[r->head[j]] < hbest) { best = j; hbest = r->h[r->head[j]]; }
+                if (best >= 0 && r->h[u] > hbest) {
+                    int64_t d = min64(r->e[u], r->cf[best]);
+                    r->cf[best] -= d;
+                    r->cf[r->rev[best]] += d;
+                    r->e[u] -= d;
+                    r->e[r->head[best]] += d;
+                } else {
+                    r->h[u] = (best < 0 || hbest >= n - 1) ? n : hbest + 1;
+                }
+            }
+        }
+        for (x = 0; x < n; x++) {
+            int64_t j;
+            if (x == s || x == t) continue;
+            for (j = r->row[x]; j < r->row[x + 1]; j++) {
+                int32_t v = r->head[j];
+                if (r->cf[j] > 0 && r->h[x] > r->h[v] + 1) {
+                    int64_t c = r->cf[j];
+                    r->e[x] -= c;
+                    r->e[v] += c;
+                    r->cf[r->rev[j]] += c;
+                    r->cf[j] = 0;
+                }
+            }
+        }
+    }
+    free(active);
+    return nact != 0 ? -1 : 0;
+}
+
+/* Pull-relabel (R8), the mirror of Alg. 2 / Alg. 3: repeat { pull heights;
+ * stop if no deficient vertex v not in {s,t} has h(v) < n; every such u, in
+ * increasing id order, up to kernel_cycles times: pull from the lowest
+ * residual in-neighbour or relabel; then for every u not in {s,t}, every
+ * in-neighbour z with c_f(z, u) > 0 and h(u) > h(z) + 1 gives all of it }.
+ * Roots limited to side[v] == want when side is given.  Returns 0 or -1. */
+int orc_rs_pull_relabel(orc_rstate *r, int32_t s, int32_t t, const uint8_t *side, int want, int32_t kernel_cycles,
+                        int64_t max_iters, int64_t *iters_out)
+{
+    int32_t n = r->n, x;
+    int32_t *active = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int64_t it, nact = 0, i;
+    for (it = 0; it < max_iters; it++) {
+        orc_rs_pull_heights(r, s, t, side, want, NULL);
+        nact = 0;
+        for (x = 0; x < n; x++)
+            if (x != s && x != t && r->e[x] < 0 && r->h[x] < n) active[nact++] = x;
+        if (nact == 0) break;
+        for (i = 0; i < nact; i++) {
+            int32_t u = active[i], cnt;
+            for (cnt = 0; cnt < kernel_cycles; cnt++) {
+                int64_t best = -1, j;
+                int32_t hbest = INT32_MAX;
+                if (!(r->h[u] < n && r->e[u] < 0)) continue;
+                for (j = r->row[u]; j < r->row[u + 1]; j++)      /* in-residual c_f(z, u) lives at rev[j] */
+                    if (r->cf[r->rev[j]] > 0 && r->h[r->head[j]] < hbest) { best = j; hbest = r->h[r->head[j]]; }
+                if (best >= 0 && r->h[u] > hbest) {
+                    int64_t in = r->rev[best];
+                    int64_t d = min64(-r->e[u], r->cf[in]);
+                    r->cf[in] -= d;
+                    r->cf[best] += d;
+                    r->e[u] += d;
+                    r->e[r->head[best]] -= d;
+                } else {
+                    r->h[u] = (best < 0 || hbest >= n - 1) ? n : hbest + 1;
+                }
+            }
+        }
+        for (x = 0; x < n; x++) {
+            int64_t j;
+            if (x == s || x == t) continue;
+            for (j = r->row[x]; j < r->row[x + 1]; j++) {
+                int32_t z = r->head[j];
+                int64_t in = r->rev[j];
+                if (r->cf[in] > 0 && r->h[x] > r->h[z] + 1) {
+                    int64_t c = r->cf[in];
+                    r->e[x] += c;
+                    r->e[z] -= c;
+                    r->cf[j] += c;
+                    r->cf[in] = 0;
+                }
+            }
+        }
+    }
+    free(active);
+    if (iters_out) *iters_out = it;
+    return nact != 0 ? -1 : 0;
+}
+
+/* Sides of the last min cut (R9) from the current push heights:
+ * side[v] = 1 (T) when h(v) < n, else 0 (S). */
+void orc_rs_cut_side(const orc_rstate *r, uint8_t *side)
+{
+    int32_t x;
+    for (x = 0; x < r->n; x++) side[x] = r->h[x] < r->n ? 1 : 0;
+}
+
+/* Saturate the edges across the cut (R9): every slot (u, v) with u in S,
+ * v in T sends all of c_f(u, v). */
+void orc_rs_saturate_cut(orc_rstate *r, const uint8_t *side)
+{
+    int32_t x;
+    int64_t i;
+    for (x = 0; x < r->n; x++) {
+        if (side[x] != 0) continue;
+        for (i = r->row[x]; i < r->row[x + 1]; i++) {
+            int32_t v = r->head[i];
+            int64_t d = r->cf[i];
+            if (side[v] == 1 && d > 0) {
+                r->cf[i] = 0;
+                r->cf[r->rev[i]] += d;
+                r->e[x] -= d;
+                r->e[v] += d;
+            }
+        }
+    }
 }
 
 /* ---- accessors ---------------------------------------------------------- */
