@@ -255,6 +255,41 @@ int maxflow_set_stream(maxflow_ctx *c, void *stream);
  * MAXFLOW_ERR_TOO_LARGE past 2^29 updates.  No counterpart in the paper. */
 int maxflow_reserve_batch(maxflow_ctx *c, int64_t count);
 
+/* ---- Sec. 5.2.2 (O2): push and pull ----------------------------------------
+ * maxflow_resolve_static_pp: the static push-pull.  Re-solve from scratch with
+ * the edges out of s and the edges into t both saturated; the deficient
+ * vertices this leaves act as sinks of the push-relabel loop.  The value is the
+ * max flow and the final heights give the min cut, as for
+ * maxflow_resolve_static.
+ *
+ * maxflow_resolve_static_pull: the pull-relabel of the same section on its own.
+ * Only the edges into t are saturated; every deficient vertex pulls from its
+ * lowest residual in-neighbour, with heights measured from s (and from any
+ * overflowing vertex) along residual edges; the value is the flow that leaves
+ * s.  A push-height BFS follows so that the cut, queries and later updates
+ * see the same labels as after a push solve.
+ *
+ * maxflow_update_pp: the dynamic push-pull ("dyn-pp-str").  Needs a solved
+ * context (otherwise it runs maxflow_update).  Three steps:
+ *   1 apply the batch (as maxflow_update), take the sides of the last min cut
+ *     from the heights the previous solve ended with (side 1: the vertex
+ *     reached t or a deficit), and send the whole residual of every edge from
+ *     side 0 to side 1, so that no residual path leads from side 0 to side 1;
+ *   2 one launch whose grid is split in two groups of CTAs: push-relabel on
+ *     side 1 (roots t and the deficient vertices of side 1) and pull-relabel
+ *     on side 0 (roots s and the overflowing vertices of side 0).  The two
+ *     parts touch disjoint vertices and edges (the paper runs them on two
+ *     streams);
+ *   3 a push solve over the whole graph for what is left (an overflowing
+ *     vertex of side 1 that reaches a deficient vertex of side 0).
+ * stop_after in {1, 2} returns after that step (for inspection; the context
+ * is then unsolved until the next update); 0 or 3 runs all.  The value equals
+ * maxflow_update's.  maxflow_stats reports the last launch; ms_update the
+ * three launches together.  No counterpart in the ABI of the paper. */
+int maxflow_resolve_static_pp(maxflow_ctx *c);
+int maxflow_resolve_static_pull(maxflow_ctx *c);
+int maxflow_update_pp(maxflow_ctx *c, const maxflow_batch *b, int32_t stop_after);
+
 /* Device memory the context holds, in bytes (graph, vertex state, scratch).
  * No counterpart in the paper; serving uses it to admit contexts by memory. */
 int maxflow_device_bytes(maxflow_ctx *c, int64_t *bytes);

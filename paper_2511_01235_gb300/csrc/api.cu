@@ -61,6 +61,16 @@ struct maxflow_ctx {
     size_t park_map_bytes = 0;
     int64_t park_slots = 0;
     std::vector<int64_t> park_sizes;   // the device allocations held when evicted
+    // the pull part of the dynamic push-pull (its own control block, labels and
+    // solve scratch) and the sides of the last cut; allocated on first use
+    struct {
+        MfCtrl *ctrl = nullptr;
+        MfCtrl *hctrl = nullptr;       // pinned
+        MfScratch sc{};
+        int32_t *h = nullptr;
+        uint8_t *side = nullptr;
+        int64_t items_for = -1;        // slot capacity sc.bitem was sized for
+    } pp;
 };
 
 // exported by mlp.cu (C linkage)
@@ -146,6 +156,9 @@ MfParams base_params(maxflow_ctx *c)
     p.bfs_hub = c->bfs_hub;
     p.fix_steep = c->opt.fix_steep ? 1 : 0;
     p.data_driven = c->opt.data_driven ? 1 : 0;
+    p.pull = 0;
+    p.side_root = -1;
+    p.side = c->pp.side;
     p.max_iters = c->opt.max_iters > 0 ? c->opt.max_iters : 4LL * c->n + 1000;
     double tl = c->opt.time_limit_s > 0 ? c->opt.time_limit_s : 120.0;
     double wl = c->opt.wait_limit_s > 0 ? c->opt.wait_limit_s : 1.0;
@@ -502,6 +515,55 @@ int do_batch(maxflow_ctx *c, const maxflow_batch *b, int mode)
     return MAXFLOW_ERR_INTERNAL;
 }
 
+// Parameter list and barrier words of a multi-instance launch, for `count` instances.
+int ensure_multi(maxflow_ctx *c, int32_t count)
+{
+    const int maxg = c->per_sm * c->sms;
+    if (c->multi_cap < count || !c->multi_plist) {
+        dfree(c, c->multi_plist);
+        dfree(c, c->multi_gstate);
+        c->multi_cap = std::max(count, 64);
+        c->multi_plist = (MfParams *)dalloc(c, sizeof(MfParams) * (size_t)c->multi_cap);
+        c->multi_gstate = dalloc_n<unsigned>(c, 32 * (int64_t)(maxg + 2));
+        if (!c->multi_plist || !c->multi_gstate) return MAXFLOW_ERR_OOM;
+    }
+    return MAXFLOW_OK;
+}
+
+// The pull part's control block, labels, solve scratch and the cut sides.
+int ensure_pp(maxflow_ctx *c)
+{
+    auto &q = c->pp;
+    const int32_t n = c->n;
+    if (!q.hctrl) MF_TRY(rc_cuda(cudaMallocHost((void **)&q.hctrl, sizeof(MfCtrl))));
+    if (!q.ctrl) {
+        q.ctrl = (MfCtrl *)dalloc(c, sizeof(MfCtrl));
+        q.h = dalloc_n<int32_t>(c, n);
+        q.side = (uint8_t *)dalloc(c, (size_t)n);
+        q.sc.border = dalloc_n<int32_t>(c, n);
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 3; ++b) q.sc.wl[a][b] = dalloc_n<int32_t>(c, n);
+        q.sc.vmark = dalloc_n<int32_t>(c, n);
+        q.sc.fixmark = dalloc_n<int32_t>(c, n);
+        q.sc.fixl[0] = dalloc_n<int32_t>(c, n);
+        q.sc.fixl[1] = dalloc_n<int32_t>(c, n);
+        bool ok = q.ctrl && q.h && q.side && q.sc.border && q.sc.vmark && q.sc.fixmark && q.sc.fixl[0] && q.sc.fixl[1];
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 3; ++b) ok = ok && q.sc.wl[a][b];
+        if (!ok) return MAXFLOW_ERR_OOM;
+        MF_TRY(rc_cuda(cudaMemsetAsync(q.ctrl, 0, sizeof(MfCtrl), c->stream)));
+        MF_TRY(rc_cuda(cudaMemsetAsync(q.sc.vmark, 0xff, sizeof(int32_t) * (size_t)n, c->stream)));
+        MF_TRY(rc_cuda(cudaMemsetAsync(q.sc.fixmark, 0xff, sizeof(int32_t) * (size_t)n, c->stream)));
+    }
+    if (q.items_for != c->g.slot_cap) {
+        dfree(c, q.sc.bitem);
+        q.sc.bitem = dalloc_n<int2>(c, (int64_t)n + c->g.slot_cap / MF_BFS_CHUNK + 64);
+        if (!q.sc.bitem) return MAXFLOW_ERR_OOM;
+        q.items_for = c->g.slot_cap;
+    }
+    return rc_cuda(cudaStreamSynchronize(c->stream));
+}
+
 int count_slots(maxflow_ctx *c, int64_t *used, int64_t *capped)
 {
     std::vector<int32_t> su, sv, scap, scf;
@@ -559,6 +621,7 @@ void maxflow_destroy(maxflow_ctx *c)
         if (c->stream) cudaStreamSynchronize(c->stream);
         while (!c->allocs.empty()) dfree(c, c->allocs.back().first);
         park_free(c);
+        if (c->pp.hctrl) cudaFreeHost(c->pp.hctrl);
         if (c->hctrl) cudaFreeHost(c->hctrl);
         if (c->hbuf) cudaFreeHost(c->hbuf);
         if (c->ev0) cudaEventDestroy(c->ev0);
@@ -955,14 +1018,7 @@ int maxflow_solve_batched(maxflow_ctx *const *ctxs, int32_t count, const maxflow
     const int maxg = c0->per_sm * c0->sms;
     const int gsize = std::min<int>(group_blocks, maxg);
     const int ngroups = std::max(1, std::min<int>(maxg / gsize, count));
-    if (c0->multi_cap < count || !c0->multi_plist) {
-        dfree(c0, c0->multi_plist);
-        dfree(c0, c0->multi_gstate);
-        c0->multi_cap = std::max(count, 64);
-        c0->multi_plist = (MfParams *)dalloc(c0, sizeof(MfParams) * (size_t)c0->multi_cap);
-        c0->multi_gstate = dalloc_n<unsigned>(c0, 32 * (int64_t)(maxg + 2));
-        if (!c0->multi_plist || !c0->multi_gstate) return MAXFLOW_ERR_OOM;
-    }
+    MF_TRY(ensure_multi(c0, count));
     unsigned *gstate = c0->multi_gstate;
     unsigned *head = gstate + 32 * maxg;
     int *abort_flag = (int *)(head + 1);
@@ -1154,6 +1210,11 @@ static void release_device(maxflow_ctx *c)
     c->multi_plist = nullptr;
     c->multi_gstate = nullptr;
     c->multi_cap = 0;
+    c->pp.ctrl = nullptr;
+    c->pp.sc = MfScratch{};
+    c->pp.h = nullptr;
+    c->pp.side = nullptr;
+    c->pp.items_for = -1;
 }
 
 int maxflow_evict(maxflow_ctx *c)
@@ -1225,6 +1286,115 @@ int maxflow_restore(maxflow_ctx *c)
     c->evicted = false;
     choose_grid(c);
     return MAXFLOW_OK;
+}
+
+int maxflow_resolve_static_pp(maxflow_ctx *c)
+{
+    if (c && c->evicted) return MAXFLOW_ERR_STATE;
+    if (!c) return MAXFLOW_ERR_STATE;
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return MAXFLOW_ERR_CUDA;
+    MfParams p = base_params(c);
+    p.mode = MF_M_STATIC_INIT | MF_M_SAT_SINK | MF_M_SOLVE;
+    int rc = run_solve(c, p);
+    c->st.ms_update = c->acc_ms;
+    return rc;
+}
+
+int maxflow_resolve_static_pull(maxflow_ctx *c)
+{
+    if (c && c->evicted) return MAXFLOW_ERR_STATE;
+    if (!c) return MAXFLOW_ERR_STATE;
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return MAXFLOW_ERR_CUDA;
+    MfParams p = base_params(c);
+    p.mode = MF_M_STATIC_INIT | MF_M_NO_SRC_SAT | MF_M_SAT_SINK | MF_M_SOLVE;
+    p.pull = 1;
+    int rc = run_solve(c, p);
+    double ms = c->acc_ms;
+    if (rc == MAXFLOW_OK) {
+        // leave push heights behind (the cut, queries and later updates read them)
+        MfParams q = base_params(c);
+        q.mode = MF_M_BFS_ONLY;
+        int kerr = 0, kst = 0;
+        MF_TRY(run_kernel(c, q, &kerr, &kst));
+        if (kerr != MF_E_NONE) rc = status_to_rc(kerr, kst);
+        ms = c->acc_ms;
+    }
+    c->st.ms_update = ms;
+    return rc;
+}
+
+int maxflow_update_pp(maxflow_ctx *c, const maxflow_batch *b, int32_t stop_after)
+{
+    if (c && c->evicted) return MAXFLOW_ERR_STATE;
+    if (!c) return MAXFLOW_ERR_STATE;
+    if (stop_after < 0 || stop_after > 3) return MAXFLOW_ERR_INVALID;
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return MAXFLOW_ERR_CUDA;
+    if (!c->solved) return do_batch(c, b, MF_M_APPLY | MF_M_SOLVE);   // no cut to start from
+    MF_TRY(ensure_pp(c));
+    // 1: the batch (Alg. 5 lines 1-16), the sides of the last cut, saturation across it
+    int rc = do_batch(c, b, MF_M_APPLY | MF_M_CUT);
+    double ms = c->acc_ms;
+    if (rc != MAXFLOW_OK || stop_after == 1) {
+        c->st.ms_update = ms;
+        return rc;
+    }
+    // 2: push on side 1 and pull on side 0, two CTA groups of one launch
+    MF_TRY(ensure_multi(c, 2));
+    MfParams pl[2];
+    pl[0] = base_params(c);
+    pl[0].mode = MF_M_SOLVE | MF_M_NO_VALUE;
+    pl[0].side_root = 1;
+    pl[1] = base_params(c);
+    pl[1].mode = MF_M_SOLVE | MF_M_NO_VALUE;
+    pl[1].pull = 1;
+    pl[1].side_root = 0;
+    pl[1].h = c->pp.h;
+    pl[1].ctrl = c->pp.ctrl;
+    pl[1].sc = c->pp.sc;
+    const int maxg = c->per_sm * c->sms;
+    const int gsize = std::max(1, std::min(c->grid, maxg) / 2);
+    unsigned *gstate = c->multi_gstate;
+    unsigned *head = gstate + 32 * maxg;
+    int *abort_flag = (int *)(head + 1);
+    MF_TRY(rc_cuda(cudaMemcpyAsync(c->multi_plist, pl, sizeof(pl), cudaMemcpyHostToDevice, c->stream)));
+    MF_TRY(rc_cuda(cudaMemsetAsync(gstate, 0, sizeof(unsigned) * 32 * (size_t)(maxg + 2), c->stream)));
+    MF_TRY(rc_cuda(cudaEventRecord(c->ev0, c->stream)));
+    MF_TRY(mf_launch_multi(c->multi_plist, 2, gsize, 2 * gsize, gstate, head, pl[0].wait_limit_ns, abort_flag,
+                           (void *)c->stream));
+    MF_TRY(rc_cuda(cudaEventRecord(c->ev1, c->stream)));
+    int abort_h = 0;
+    MF_TRY(rc_cuda(cudaMemcpyAsync(&abort_h, abort_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream)));
+    MF_TRY(rc_cuda(cudaMemcpyAsync(c->hctrl, c->ctrl, sizeof(MfCtrl), cudaMemcpyDeviceToHost, c->stream)));
+    MF_TRY(rc_cuda(cudaMemcpyAsync(c->pp.hctrl, c->pp.ctrl, sizeof(MfCtrl), cudaMemcpyDeviceToHost, c->stream)));
+    MF_TRY(rc_cuda(cudaStreamSynchronize(c->stream)));
+    float ms2 = 0.f;
+    cudaEventElapsedTime(&ms2, c->ev0, c->ev1);
+    ms += ms2;
+    const int e0 = (int)c->hctrl->err.w[0], e1 = (int)c->pp.hctrl->err.w[0];
+    if (abort_h || e0 != MF_E_NONE || e1 != MF_E_NONE) {
+        MF_TRY(rc_cuda(cudaMemsetAsync(c->ctrl, 0, 2 * sizeof(MfLine), c->stream)));
+        MF_TRY(rc_cuda(cudaMemsetAsync(c->pp.ctrl, 0, 2 * sizeof(MfLine), c->stream)));
+        MF_TRY(rc_cuda(cudaStreamSynchronize(c->stream)));
+        c->st.ms_update = ms;
+        if (abort_h) return MAXFLOW_ERR_INTERNAL;
+        return status_to_rc(e0 != MF_E_NONE ? e0 : e1, MF_ST_ERROR);
+    }
+    if (stop_after == 2) {
+        c->st.ms_update = ms;
+        return status_to_rc(MF_E_NONE, c->hctrl->status == MF_ST_CAP || c->pp.hctrl->status == MF_ST_CAP
+                                           ? MF_ST_CAP : MF_ST_CONVERGED);
+    }
+    // 3: a push solve over the whole graph finishes what the two parts left
+    MfParams p = base_params(c);
+    p.mode = MF_M_SOLVE;
+    rc = run_solve(c, p);
+    ms += c->acc_ms;
+    c->acc_ms = ms;
+    c->st.ms_update = ms;
+    return rc;
 }
 
 int maxflow_set_rounds(maxflow_ctx *c, int32_t rounds)

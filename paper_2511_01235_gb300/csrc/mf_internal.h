@@ -46,6 +46,10 @@
 #define MF_M_BFS_ONLY 8       // one backward BFS, then stop
 #define MF_M_NO_DEFICIT_ROOTS 16  // BFS roots: the sink only (flow extraction runs)
 #define MF_M_SKIP_SOURCE_SAT 32   // apply without saturating the source again
+#define MF_M_SAT_SINK 64          // static init also saturates every edge into the sink (Sec. 5.2.2 static push-pull)
+#define MF_M_NO_SRC_SAT 128       // static init leaves the source edges alone (the pull-only static solve)
+#define MF_M_CUT 256              // after the batch: record the sides of the last cut, saturate the edges S -> T
+#define MF_M_NO_VALUE 512         // skip the value phase (the side-limited push / pull parts)
 
 struct alignas(128) MfLine {
     unsigned int w[32];
@@ -144,6 +148,9 @@ struct MfParams {
     int32_t bfs_hub;          // BFS: rows above this many slots enter the frontier as work items
     int32_t fix_steep;
     int32_t data_driven;
+    int32_t pull;             // 0: push excess toward t and deficits; 1: pull for deficits from s and excess (Sec. 5.2.2)
+    int32_t side_root;        // -1: every deficient (push) / overflowing (pull) vertex is a root; else only side[v] == side_root
+    uint8_t *side;            // [n] sides of the last cut (1: reaches t or a deficit, 0: not); written by MF_M_CUT
     long long max_iters;
     unsigned long long time_limit_ns;
     unsigned long long wait_limit_ns;

@@ -418,6 +418,70 @@ __device__ __noinline__ void phase_saturate_source(const MfParams &P, Sh &sh)
     if (acc) atomicAdd((unsigned long long *)&sh.src_e, (unsigned long long)acc);
 }
 
+// Static push-pull (Sec. 5.2.2): every edge into t is saturated as well; its
+// tail keeps the deficit, and the deficient vertices then act as sinks.
+__device__ __noinline__ void phase_saturate_sink(const MfParams &P, Sh &sh)
+{
+    const int t = P.sink;
+    const int r0 = P.g.off[t];
+    const int d = ldg_cg(P.g.deg + t);
+    long long acc = 0;
+    for (int j = vb() * blockDim.x + threadIdx.x; j < d; j += vn() * blockDim.x) {
+        const int x = r0 + j;                  // slot (t, z)
+        const int y = ldg_cg(P.g.rev + x);     // slot (z, t)
+        const int c = ldg_cg(P.cf + y);
+        if (c > 0) {
+            P.cf[y] = 0;
+            P.cf[x] = ldg_cg(P.cf + x) + c;
+            add_excess(P, sh, ldg_cg(P.g.dst + x), -(long long)c);
+            acc += c;
+        }
+    }
+    if (acc) atomicAdd((unsigned long long *)&sh.sink_e, (unsigned long long)acc);
+}
+
+// Dynamic push-pull (Sec. 5.2.2): the sides of the last cut, read from the
+// heights the previous solve ended with (1: the vertex reached t or a
+// deficit, 0: it did not) ...
+__device__ __noinline__ void phase_cut_side(const MfParams &P)
+{
+    const int n = P.g.n;
+    const long long gs = (long long)vn() * blockDim.x;
+    for (long long v = (long long)vb() * blockDim.x + threadIdx.x; v < n; v += gs) {
+        uint8_t sd = ldg_cg(P.h + v) < n ? 1 : 0;
+        if (v == P.source) sd = 0;
+        if (v == P.sink) sd = 1;
+        P.side[v] = sd;
+    }
+}
+
+// ... then every residual edge from side 0 to side 1 sends all it can, so
+// that no residual path leads from side 0 to side 1.  One warp per row.
+__device__ __noinline__ void phase_saturate_cut(const MfParams &P, Sh &sh)
+{
+    const int n = P.g.n;
+    const int lane = threadIdx.x & 31;
+    const long long nw = ((long long)vn() * blockDim.x) >> 5;
+    for (long long u = ((long long)vb() * blockDim.x + threadIdx.x) >> 5; u < n; u += nw) {
+        if (P.side[u] != 0) continue;
+        const int r0 = P.g.off[u], d = ldg_cg(P.g.deg + u);
+        long long out = 0;
+        for (int j = lane; j < d; j += 32) {
+            const int x = r0 + j;
+            const int c = ldg_cg(P.cf + x);
+            if (c <= 0) continue;
+            const int z = ldg_cg(P.g.dst + x);
+            if (P.side[z] != 1) continue;
+            P.cf[x] = 0;
+            atomicAdd(P.cf + ldg_cg(P.g.rev + x), c);
+            add_excess(P, sh, z, (long long)c);
+            out += c;
+        }
+        out = warp_sum_ll(out);
+        if (lane == 0 && out) add_excess(P, sh, (int)u, -out);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Batch apply and repair (Alg. 5 lines 1-16)
 // ---------------------------------------------------------------------------
@@ -788,6 +852,7 @@ __device__ __noinline__ void phase_bfs_init(const MfParams &P, Sh &sh)
 {
     const int n = P.g.n;
     const bool deficit_roots = (P.mode & MF_M_NO_DEFICIT_ROOTS) == 0;
+    const bool pull = P.pull != 0;
     const int lane = threadIdx.x & 31;
     const long long gs = (long long)vn() * blockDim.x;
     for (long long base = (long long)vb() * blockDim.x + threadIdx.x - lane; base < n; base += gs) {
@@ -796,7 +861,13 @@ __device__ __noinline__ void phase_bfs_init(const MfParams &P, Sh &sh)
         int zv[1] = {v}, dv[1] = {0};
         long long ev[1] = {0};
         if (v < n) {
-            root[0] = (v == P.sink) || (deficit_roots && v != P.source && ldg_cg(P.e + v) < 0);
+            // push: t and the deficient vertices; pull (Sec. 5.2.2): s and the
+            // overflowing vertices; with a side given, only that side's
+            const bool side_ok = P.side_root < 0 || P.side[v] == P.side_root;
+            if (pull)
+                root[0] = (v == P.source) || (v != P.sink && side_ok && ldg_cg(P.e + v) > 0);
+            else
+                root[0] = (v == P.sink) || (deficit_roots && v != P.source && side_ok && ldg_cg(P.e + v) < 0);
             P.h[v] = root[0] ? 0 : n;
             if (root[0]) dv[0] = ldg_cg(P.g.deg + v);
         }
@@ -814,23 +885,27 @@ __device__ __forceinline__ void bfs_visit(const MfParams &P, const int (&x)[BR],
                                           int sel)
 {
     const bool with_wl = P.data_driven && !(P.mode & MF_M_BFS_ONLY);
+    const bool pull = P.pull != 0;
+    const int skip = pull ? P.sink : P.source;     // the terminal a BFS never labels
     const int n = P.g.n;
     int z[BR], rc[BR], hz[BR], d[BR];
     bool claim[BR];
     long long ev[BR];
 #pragma unroll
     for (int r = 0; r < BR; ++r) {
-        z[r] = valid[r] ? ldg_cg(P.g.dst + x[r]) : P.source;
-        rc[r] = valid[r] ? ldg_cg(P.g.pcap + x[r]) - ldg_cg(P.cf + x[r]) : 0;
+        z[r] = valid[r] ? ldg_cg(P.g.dst + x[r]) : skip;
+        // push heights follow c_f(z, u) (backward); pull heights c_f(u, z) (forward)
+        rc[r] = valid[r] ? (pull ? ldg_cg(P.cf + x[r]) : ldg_cg(P.g.pcap + x[r]) - ldg_cg(P.cf + x[r])) : 0;
     }
 #pragma unroll
-    for (int r = 0; r < BR; ++r) hz[r] = (rc[r] > 0 && z[r] != P.source) ? ldg_cg(P.h + z[r]) : 0;
+    for (int r = 0; r < BR; ++r) hz[r] = (rc[r] > 0 && z[r] != skip) ? ldg_cg(P.h + z[r]) : 0;
 #pragma unroll
     for (int r = 0; r < BR; ++r) claim[r] = hz[r] == n && atomicCAS(P.h + z[r], n, L + 1) == n;
 #pragma unroll
     for (int r = 0; r < BR; ++r) {
         d[r] = claim[r] ? ldg_cg(P.g.deg + z[r]) : 0;
-        ev[r] = (with_wl && claim[r] && z[r] != P.sink) ? ldg_cg(P.e + z[r]) : 0;
+        const bool term = z[r] == P.sink || z[r] == P.source;
+        ev[r] = (with_wl && claim[r] && !term) ? (pull ? -ldg_cg(P.e + z[r]) : ldg_cg(P.e + z[r])) : 0;
     }
     frontier_push<BR>(P, claim, z, d, ev, with_wl, sel);
 }
@@ -920,7 +995,8 @@ __device__ __noinline__ void phase_worklist(const MfParams &P, Sh &sh)
     for (long long base = (long long)vb() * blockDim.x + threadIdx.x - lane; base < n; base += gs) {
         int v = (int)base + lane;
         bool cand = v < n && v != P.sink && v != P.source;
-        bool act = cand && ldg_cg(P.h + v) < n && ldg_cg(P.e + v) > 0;
+        const long long ev = cand ? ldg_cg(P.e + v) : 0;
+        bool act = cand && ldg_cg(P.h + v) < n && (P.pull ? ev < 0 : ev > 0);
         bool listed = P.data_driven ? act : cand;
         int bin = 0;
         if (listed) {
@@ -973,9 +1049,32 @@ __device__ __forceinline__ void note_relabel(const MfParams &P, int u, const Dis
     P.sc.fixl[li][pos] = u;
 }
 
-// Push d = min(e', c_f(u, v^)) along slot x of u (Alg. 2 lines 11-15).
-__device__ __forceinline__ void do_push(const MfParams &P, Sh &sh, int u, int x, long long eu, const DisCtx &dc)
+// Push d = min(e', c_f(u, v^)) along slot x of u (Alg. 2 lines 11-15), or,
+// for a deficient u (PULL, Sec. 5.2.2), pull d = min(-e(u), c_f(v^, u)) over
+// the same pair: c_f(v^, u) lives at rev[x] and only u's owner lowers it.
+template <bool PULL>
+__device__ __forceinline__ void do_move(const MfParams &P, Sh &sh, int u, int x, long long eu, const DisCtx &dc)
 {
+    if (PULL) {
+        const int y = ldg_cg(P.g.rev + x);
+        const int c = ldg_cg(P.cf + y);
+        const long long d = eu < (long long)c ? eu : (long long)c;
+        if (d <= 0) return;
+        atomicSub(P.cf + y, (int)d);
+        atomicAdd(P.cf + x, (int)d);
+        atomic_add_ll(P.e + u, d);
+        const int z = ldg_cg(P.g.dst + x);
+        if (z == P.sink) {
+            atomicAdd((unsigned long long *)&sh.sink_e, (unsigned long long)(-d));
+        } else if (z == P.source) {
+            atomicAdd((unsigned long long *)&sh.src_e, (unsigned long long)(-d));
+        } else {
+            const long long old = atomic_add_ll(P.e + z, -d);
+            if (dc.queue && old >= 0 && old - d < 0) enqueue_active(P, z, dc);
+        }
+        atomicAdd((unsigned long long *)&sh.pushes, 1ull);
+        return;
+    }
     int c = ldg_cg(P.cf + x);
     long long d = eu < (long long)c ? eu : (long long)c;
     if (d <= 0) return;
@@ -998,7 +1097,7 @@ __device__ __forceinline__ void do_push(const MfParams &P, Sh &sh, int u, int x,
 // row at r0, as a key (h(v) << 32 | j) so the minimum also breaks ties by the
 // lowest slot index.  Slots are read kU at a time with their loads issued
 // together.
-template <int kU>
+template <int kU, bool PULL>
 __device__ __forceinline__ unsigned long long scan_lowest(const MfParams &P, int r0, int d, int j0, int step)
 {
     unsigned long long best = kEmpty;
@@ -1007,7 +1106,8 @@ __device__ __forceinline__ unsigned long long scan_lowest(const MfParams &P, int
 #pragma unroll
         for (int r = 0; r < kU; ++r) {
             int j = jb + r * step;
-            c[r] = j < d ? ldg_cg(P.cf + r0 + j) : 0;
+            // push: out-residual c_f(u, z); pull: in-residual c_f(z, u) = pcap - c_f(u, z)
+            c[r] = j < d ? (PULL ? ldg_cg(P.g.pcap + r0 + j) - ldg_cg(P.cf + r0 + j) : ldg_cg(P.cf + r0 + j)) : 0;
             z[r] = j < d ? ldg_cg(P.g.dst + r0 + j) : 0;
         }
 #pragma unroll
@@ -1025,6 +1125,8 @@ __device__ __forceinline__ unsigned long long scan_lowest(const MfParams &P, int
 
 // One thread per vertex (rows of at most small_deg slots).  Returns true
 // if u was relabelled (only then can it have steep residual edges, Alg. 3).
+// PULL: u is deficient and pulls (Sec. 5.2.2); its "excess" is -e(u).
+template <bool PULL>
 __device__ bool discharge_thread(const MfParams &P, Sh &sh, int u, const DisCtx &dc)
 {
     bool lifted = false;
@@ -1034,13 +1136,13 @@ __device__ bool discharge_thread(const MfParams &P, Sh &sh, int u, const DisCtx 
     int hu = ldg_cg(P.h + u);
     long long cyc_done = 0;
     for (int cyc = 0; cyc < P.kernel_cycles; ++cyc) {
-        long long eu = ldg_cg(P.e + u);
+        long long eu = PULL ? -ldg_cg(P.e + u) : ldg_cg(P.e + u);
         if (!(hu < n && eu > 0)) break;
         ++cyc_done;
-        unsigned long long best = scan_lowest<4>(P, r0, d, 0, 1);
+        unsigned long long best = scan_lowest<4, PULL>(P, r0, d, 0, 1);
         int best_h = best == kEmpty ? 0x7fffffff : (int)(best >> 32);
         if (best != kEmpty && hu > best_h) {
-            do_push(P, sh, u, r0 + (int)(best & 0xffffffffu), eu, dc);
+            do_move<PULL>(P, sh, u, r0 + (int)(best & 0xffffffffu), eu, dc);
         } else {
             hu = (best == kEmpty || best_h >= n - 1) ? n : best_h + 1;
             P.h[u] = hu;
@@ -1056,6 +1158,7 @@ __device__ bool discharge_thread(const MfParams &P, Sh &sh, int u, const DisCtx 
 }
 
 // One warp per vertex (returns the same value in every lane).
+template <bool PULL>
 __device__ bool discharge_warp(const MfParams &P, Sh &sh, int u, const DisCtx &dc)
 {
     bool lifted = false;
@@ -1066,13 +1169,13 @@ __device__ bool discharge_warp(const MfParams &P, Sh &sh, int u, const DisCtx &d
     int hu = ldg_cg(P.h + u);
     long long cyc_done = 0;
     for (int cyc = 0; cyc < P.kernel_cycles; ++cyc) {
-        long long eu = ldg_cg(P.e + u);
+        long long eu = PULL ? -ldg_cg(P.e + u) : ldg_cg(P.e + u);
         if (!(hu < n && eu > 0)) break;
         ++cyc_done;
-        unsigned long long best = warp_min_u64(scan_lowest<8>(P, r0, d, lane, 32));
+        unsigned long long best = warp_min_u64(scan_lowest<8, PULL>(P, r0, d, lane, 32));
         int best_h = best == kEmpty ? 0x7fffffff : (int)(best >> 32);
         if (best != kEmpty && hu > best_h) {
-            if (lane == 0) do_push(P, sh, u, r0 + (int)(best & 0xffffffffu), eu, dc);
+            if (lane == 0) do_move<PULL>(P, sh, u, r0 + (int)(best & 0xffffffffu), eu, dc);
         } else {
             hu = (best == kEmpty || best_h >= n - 1) ? n : best_h + 1;
             lifted = true;
@@ -1092,6 +1195,7 @@ __device__ bool discharge_warp(const MfParams &P, Sh &sh, int u, const DisCtx &d
 
 // One CTA per vertex (hubs).  All threads of the CTA call this together;
 // the return value is meaningful in thread 0.
+template <bool PULL>
 __device__ bool discharge_cta(const MfParams &P, Sh &sh, int u, const DisCtx &dc)
 {
     bool lifted = false;
@@ -1101,7 +1205,7 @@ __device__ bool discharge_cta(const MfParams &P, Sh &sh, int u, const DisCtx &dc
     const int d = ldg_cg(P.g.deg + u);
     for (int cyc = 0; cyc < P.kernel_cycles; ++cyc) {
         if (threadIdx.x == 0) {
-            sh.bcast_e = ldg_cg(P.e + u);
+            sh.bcast_e = PULL ? -ldg_cg(P.e + u) : ldg_cg(P.e + u);
             sh.bcast_h = ldg_cg(P.h + u);
         }
         __syncthreads();
@@ -1111,7 +1215,7 @@ __device__ bool discharge_cta(const MfParams &P, Sh &sh, int u, const DisCtx &dc
             __syncthreads();
             break;
         }
-        unsigned long long best = warp_min_u64(scan_lowest<8>(P, r0, d, threadIdx.x, blockDim.x));
+        unsigned long long best = warp_min_u64(scan_lowest<8, PULL>(P, r0, d, threadIdx.x, blockDim.x));
         if (lane == 0) sh.red[wid] = best;
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -1119,7 +1223,7 @@ __device__ bool discharge_cta(const MfParams &P, Sh &sh, int u, const DisCtx &dc
             for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = sh.red[w] < b ? sh.red[w] : b;
             int best_h = b == kEmpty ? 0x7fffffff : (int)(b >> 32);
             if (b != kEmpty && hu > best_h) {
-                do_push(P, sh, u, r0 + (int)(b & 0xffffffffu), eu, dc);
+                do_move<PULL>(P, sh, u, r0 + (int)(b & 0xffffffffu), eu, dc);
             } else {
                 P.h[u] = (b == kEmpty || best_h >= n - 1) ? n : best_h + 1;
                 lifted = true;
@@ -1133,6 +1237,7 @@ __device__ bool discharge_cta(const MfParams &P, Sh &sh, int u, const DisCtx &dc
     return lifted;
 }
 
+template <bool PULL>
 __device__ __noinline__ void phase_discharge(const MfParams &P, Sh &sh)
 {
     MfCtrl *ctl = P.ctrl;
@@ -1156,7 +1261,7 @@ __device__ __noinline__ void phase_discharge(const MfParams &P, Sh &sh)
         __syncthreads();
         if (i >= nh) break;
         const int u = __ldcg(wl2 + i);
-        if (discharge_cta(P, sh, u, dc) && threadIdx.x == 0) note_relabel(P, u, dc);
+        if (discharge_cta<PULL>(P, sh, u, dc) && threadIdx.x == 0) note_relabel(P, u, dc);
     }
     // mid-degree rows: one warp each
     const int nm = vrd(&ctl->wl_n[1]);
@@ -1164,7 +1269,7 @@ __device__ __noinline__ void phase_discharge(const MfParams &P, Sh &sh)
         const int i = warp_grab(&ctl->head1.w[0], nm, 1u);
         if (i >= nm) break;
         const int u = __ldcg(wl1 + i);
-        if (discharge_warp(P, sh, u, dc) && lane == 0) note_relabel(P, u, dc);
+        if (discharge_warp<PULL>(P, sh, u, dc) && lane == 0) note_relabel(P, u, dc);
     }
     // small rows: one thread each, 32 per grab
     const int ns = vrd(&ctl->wl_n[0]);
@@ -1173,7 +1278,7 @@ __device__ __noinline__ void phase_discharge(const MfParams &P, Sh &sh)
         if (b >= ns) break;
         if (b + lane < ns) {
             const int u = __ldcg(wl0 + b + lane);
-            if (discharge_thread(P, sh, u, dc)) note_relabel(P, u, dc);
+            if (discharge_thread<PULL>(P, sh, u, dc)) note_relabel(P, u, dc);
         }
     }
 }
@@ -1186,6 +1291,9 @@ __device__ __noinline__ void phase_discharge(const MfParams &P, Sh &sh)
 // of every steep slot (h(u) > h(v) + 1).  Returns the flow sent out of u.
 // Only vertices relabelled in the discharge can have steep slots (heights are
 // exact after the BFS and neighbours only rise), so only those are scanned.
+// PULL (Sec. 5.2.2): a steep in-residual c_f(v, u) is pulled whole, and the
+// return value is minus the flow received.
+template <bool PULL>
 __device__ __forceinline__ long long fix_scan(const MfParams &P, Sh &sh, int hu, int r0, int d, int j0, int step)
 {
     constexpr int kF = 4;
@@ -1195,7 +1303,7 @@ __device__ __forceinline__ long long fix_scan(const MfParams &P, Sh &sh, int hu,
 #pragma unroll
         for (int r = 0; r < kF; ++r) {
             const int j = jb + r * step;
-            c[r] = j < d ? ldg_cg(P.cf + r0 + j) : 0;
+            c[r] = j < d ? (PULL ? ldg_cg(P.g.pcap + r0 + j) - ldg_cg(P.cf + r0 + j) : ldg_cg(P.cf + r0 + j)) : 0;
             z[r] = j < d ? ldg_cg(P.g.dst + r0 + j) : 0;
         }
 #pragma unroll
@@ -1204,12 +1312,23 @@ __device__ __forceinline__ long long fix_scan(const MfParams &P, Sh &sh, int hu,
         for (int r = 0; r < kF; ++r) {
             if (c[r] > 0 && hu > hz[r] + 1) {
                 const int x = r0 + jb + r * step;
-                const int old = atomicExch(P.cf + x, 0);
-                if (old > 0) {
-                    atomicAdd(P.cf + ldg_cg(P.g.rev + x), old);
-                    add_excess(P, sh, z[r], (long long)old);
-                    atomicAdd((unsigned long long *)&sh.steep, 1ull);
-                    out += old;
+                if (PULL) {
+                    const int y = ldg_cg(P.g.rev + x);
+                    const int old = atomicExch(P.cf + y, 0);
+                    if (old > 0) {
+                        atomicAdd(P.cf + x, old);
+                        add_excess(P, sh, z[r], -(long long)old);
+                        atomicAdd((unsigned long long *)&sh.steep, 1ull);
+                        out -= old;
+                    }
+                } else {
+                    const int old = atomicExch(P.cf + x, 0);
+                    if (old > 0) {
+                        atomicAdd(P.cf + ldg_cg(P.g.rev + x), old);
+                        add_excess(P, sh, z[r], (long long)old);
+                        atomicAdd((unsigned long long *)&sh.steep, 1ull);
+                        out += old;
+                    }
                 }
             }
         }
@@ -1217,6 +1336,7 @@ __device__ __forceinline__ long long fix_scan(const MfParams &P, Sh &sh, int hu,
     return out;
 }
 
+template <bool PULL>
 __device__ __noinline__ void phase_fix(const MfParams &P, Sh &sh)
 {
     MfCtrl *ctl = P.ctrl;
@@ -1236,7 +1356,7 @@ __device__ __noinline__ void phase_fix(const MfParams &P, Sh &sh)
         const int u = __ldcg(P.sc.fixl[1] + i);
         const int hu = ldg_cg(P.h + u);
         const int r0 = P.g.off[u], d = ldg_cg(P.g.deg + u);
-        long long out = fix_scan(P, sh, hu, r0, d, threadIdx.x, blockDim.x);
+        long long out = fix_scan<PULL>(P, sh, hu, r0, d, threadIdx.x, blockDim.x);
         if (out) atomic_add_ll(P.e + u, -out);
         if (threadIdx.x == 0) { slots += d; ++verts; }
     }
@@ -1248,7 +1368,7 @@ __device__ __noinline__ void phase_fix(const MfParams &P, Sh &sh)
         const int u = __ldcg(P.sc.fixl[0] + i);
         const int hu = ldg_cg(P.h + u);
         const int r0 = P.g.off[u], d = ldg_cg(P.g.deg + u);
-        long long out = warp_sum_ll(fix_scan(P, sh, hu, r0, d, lane, 32));
+        long long out = warp_sum_ll(fix_scan<PULL>(P, sh, hu, r0, d, lane, 32));
         if (lane == 0) {
             if (out) atomic_add_ll(P.e + u, -out);
             slots += d;
@@ -1265,10 +1385,14 @@ __device__ __noinline__ void phase_fix(const MfParams &P, Sh &sh)
 
 __device__ __noinline__ void phase_value(const MfParams &P)
 {
+    // push (R3): sum of e(v) over v != s with h(v) < n; pull (Sec. 5.2.2, the
+    // mirror): sum of -e(v) over v != t with h(v) < n
     const int n = P.g.n;
+    const bool pull = P.pull != 0;
+    const int skip = pull ? P.sink : P.source;
     long long acc = 0;
     for (long long v = (long long)vb() * blockDim.x + threadIdx.x; v < n; v += (long long)vn() * blockDim.x)
-        if ((int)v != P.source && ldg_cg(P.h + v) < n) acc += ldg_cg(P.e + v);
+        if ((int)v != skip && ldg_cg(P.h + v) < n) acc += pull ? -ldg_cg(P.e + v) : ldg_cg(P.e + v);
     acc = warp_sum_ll(acc);
     if ((threadIdx.x & 31) == 0 && acc) atomic_add_ll(&P.ctrl->value, acc);
 }
@@ -1291,9 +1415,16 @@ __device__ __noinline__ bool solve_instance(const MfParams &P, Sh &sh)
     if (P.mode & MF_M_STATIC_INIT) {
         phase_static_reset(P);
         if (!grid_sync(P, H_NONE, sh)) return false;
-        phase_saturate_source(P, sh);
-        flush_acc(P, sh, 4);
-        if (!grid_sync(P, H_NONE, sh)) return false;
+        if (!(P.mode & MF_M_NO_SRC_SAT)) {
+            phase_saturate_source(P, sh);
+            flush_acc(P, sh, 4);
+            if (!grid_sync(P, H_NONE, sh)) return false;
+        }
+        if (P.mode & MF_M_SAT_SINK) {
+            phase_saturate_sink(P, sh);
+            flush_acc(P, sh, 4);
+            if (!grid_sync(P, H_NONE, sh)) return false;
+        }
     }
     if (P.mode & MF_M_APPLY) {
         phase_apply_validate(P);
@@ -1324,6 +1455,13 @@ __device__ __noinline__ bool solve_instance(const MfParams &P, Sh &sh)
             flush_acc(P, sh, 4);
             if (!grid_sync(P, H_NONE, sh)) return false;
         }
+        if (P.mode & MF_M_CUT) {
+            phase_cut_side(P);
+            if (!grid_sync(P, H_NONE, sh)) return false;
+            phase_saturate_cut(P, sh);
+            flush_acc(P, sh, 4);
+            if (!grid_sync(P, H_NONE, sh)) return false;
+        }
         if (status_of(P) != MF_ST_RUNNING) return true;
     }
     if (!(P.mode & (MF_M_SOLVE | MF_M_BFS_ONLY))) return true;
@@ -1347,18 +1485,20 @@ __device__ __noinline__ bool solve_instance(const MfParams &P, Sh &sh)
         if (status_of(P) != MF_ST_RUNNING) break;
         // discharge rounds, then remove-invalid-edges
         do {
-            phase_discharge(P, sh);
+            if (P.pull) phase_discharge<true>(P, sh);
+            else phase_discharge<false>(P, sh);
             flush_acc(P, sh, 1);
             if (!grid_sync(P, H_DIS, sh)) return false;
         } while (vrd(&P.ctrl->dis_more));
         if (P.fix_steep) {
-            phase_fix(P, sh);
+            if (P.pull) phase_fix<true>(P, sh);
+            else phase_fix<false>(P, sh);
             flush_acc(P, sh, 2);
         }
         if (!grid_sync(P, H_ITER, sh)) return false;
     }
     if (status_of(P) == MF_ST_ERROR) return true;
-    phase_value(P);
+    if (!(P.mode & MF_M_NO_VALUE)) phase_value(P);
     return grid_sync(P, H_FINAL, sh);
 }
 

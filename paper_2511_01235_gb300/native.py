@@ -92,7 +92,8 @@ EXPORTS = ["maxflow_default_opts", "maxflow_init", "maxflow_update", "maxflow_qu
            "maxflow_solve_batched", "maxflow_device_bytes", "maxflow_evict", "maxflow_restore",
            "maxflow_set_stream", "maxflow_reserve_batch",
            "maxflow_arena_create", "maxflow_arena_destroy", "maxflow_arena_alloc", "maxflow_arena_free",
-           "maxflow_arena_stats", "maxflow_arena_fits", "maxflow_evicted_sizes"]
+           "maxflow_arena_stats", "maxflow_arena_fits", "maxflow_evicted_sizes",
+           "maxflow_resolve_static_pp", "maxflow_resolve_static_pull", "maxflow_update_pp"]
 
 TRACE_NAMES = ["start", "prologue", "batch_validated", "batch_located", "room_checked", "capacities_changed",
                "iteration_start", "bfs_roots", "bfs_level", "worklist", "discharge", "end"]
@@ -151,6 +152,9 @@ def load(build_if_missing: bool = False):
     L.maxflow_arena_stats.argtypes = [vp, P(ArenaStats)]
     L.maxflow_arena_fits.argtypes = [vp, vp, i32, P(i32)]
     L.maxflow_evicted_sizes.argtypes = [vp, vp, i32, P(i32)]
+    L.maxflow_resolve_static_pp.argtypes = [vp]
+    L.maxflow_resolve_static_pull.argtypes = [vp]
+    L.maxflow_update_pp.argtypes = [vp, P(Batch), i32]
     L.maxflow_restore.argtypes = [vp]
     L.maxflow_solve_batched.argtypes = [vp, i32, vp, i32, P(C.c_double)]
     L.maxflow_sched_actions.argtypes = [vp, vp, vp, i32, P(i32)]
@@ -642,6 +646,19 @@ class Solver:
         """Issue this instance's later work on `stream` (a torch.cuda.Stream)."""
         _check(load().maxflow_set_stream(self.h, int(stream.cuda_stream)), "maxflow_set_stream")
         self.stream = stream
+
+    def resolve_static_pp(self):
+        """Static push-pull (Sec. 5.2.2): saturate out of s and into t, push with deficits as sinks."""
+        _check(load().maxflow_resolve_static_pp(self.h), "maxflow_resolve_static_pp")
+
+    def resolve_static_pull(self):
+        """Max flow by pull-relabel alone (Sec. 5.2.2): saturate into t, deficits pull from s."""
+        _check(load().maxflow_resolve_static_pull(self.h), "maxflow_resolve_static_pull")
+
+    def update_pp(self, u, v, c, stop_after: int = 0):
+        """Dynamic push-pull update (Sec. 5.2.2, dyn-pp-str); stop_after 1 or 2 stops early."""
+        b, keep = _batch(u, v, c)
+        _check(load().maxflow_update_pp(self.h, C.byref(b), int(stop_after)), "maxflow_update_pp")
 
     def evicted_sizes(self) -> np.ndarray:
         """Sizes of the device allocations held when evicted (what a restore needs at most)."""
