@@ -539,6 +539,22 @@ def main():
             sched["batches"] = len(sb)
             sched["note"] = "wall ms per update through the C ABI, host batches; paper = 1 round, K = avg degree"
 
+    # ---- dynamic push-pull (Sec. 5.2.2, O2) vs the default update, same batches on clones ----
+    pushpull = None
+    if not args.quick and args.sched_steps > 0:
+        pb = wl.batches(min(args.sched_steps, 4), args.batch)
+        pushpull = {}
+        for key in ("update", "push_pull"):
+            C = S.clone()
+            dms = []
+            for b in pb:
+                (C.update if key == "update" else C.update_pp)(b.u, b.v, b.cap)
+                dms.append(C.stats()["ms_update"])
+            pushpull[key + "_device_ms_mean"] = float(np.mean(dms))
+            pushpull[key + "_value"] = int(C.query()[0])
+            C.close()
+        pushpull["batches"] = len(pb)
+
     # ---- static re-solve comparator (same updated graph) ----
     static_ms = []
     for _ in range(args.static_reps):
@@ -584,6 +600,7 @@ def main():
                                                              "ms_fix", "ms_worklist", "ms_apply", "grid_blocks",
                                                              "kernel_cycles")},
             "scheduler": sched,
+            "push_pull": pushpull,
             "static_stats": {k: static_stats[k] for k in ("iterations", "bfs_levels", "pushes", "relabels",
                                                           "ms_bfs", "ms_discharge", "ms_fix", "ms_worklist")},
             "wall_s_timed": wall,
