@@ -104,6 +104,10 @@ struct Sh {
     long long sink_e, src_e;
     long long pushes, relabels, steep, slots, verts, cycles;
     unsigned long long red[MF_WARPS];
+    long long wsum[MF_WARPS];
+    int wcnt[MF_WARPS];
+    long long bcast_rem;
+    int bcast_k;
     int bcast_i;
     int bcast_h;
     long long bcast_e;
@@ -1049,48 +1053,47 @@ __device__ __forceinline__ void note_relabel(const MfParams &P, int u, const Dis
     P.sc.fixl[li][pos] = u;
 }
 
-// Push d = min(e', c_f(u, v^)) along slot x of u (Alg. 2 lines 11-15), or,
-// for a deficient u (PULL, Sec. 5.2.2), pull d = min(-e(u), c_f(v^, u)) over
-// the same pair: c_f(v^, u) lives at rev[x] and only u's owner lowers it.
+// Move amt > 0 along slot x = (u, z) of u, y = rev[x]: a push lowers c_f(u, z)
+// (slot x), a pull (Sec. 5.2.2) lowers c_f(z, u) (slot y); e(z) changes by
+// -/+ amt and z joins the next round's queue if that makes it active.  The
+// caller updates e(u).  Only u's owner lowers the slot it moves through, so
+// an amount read from that slot can always be moved.
 template <bool PULL>
-__device__ __forceinline__ void do_move(const MfParams &P, Sh &sh, int u, int x, long long eu, const DisCtx &dc)
+__device__ __forceinline__ void move_flow(const MfParams &P, Sh &sh, int x, int y, int z, long long amt,
+                                          const DisCtx &dc)
 {
     if (PULL) {
-        const int y = ldg_cg(P.g.rev + x);
-        const int c = ldg_cg(P.cf + y);
-        const long long d = eu < (long long)c ? eu : (long long)c;
-        if (d <= 0) return;
-        atomicSub(P.cf + y, (int)d);
-        atomicAdd(P.cf + x, (int)d);
-        atomic_add_ll(P.e + u, d);
-        const int z = ldg_cg(P.g.dst + x);
-        if (z == P.sink) {
-            atomicAdd((unsigned long long *)&sh.sink_e, (unsigned long long)(-d));
-        } else if (z == P.source) {
-            atomicAdd((unsigned long long *)&sh.src_e, (unsigned long long)(-d));
-        } else {
-            const long long old = atomic_add_ll(P.e + z, -d);
-            if (dc.queue && old >= 0 && old - d < 0) enqueue_active(P, z, dc);
-        }
-        atomicAdd((unsigned long long *)&sh.pushes, 1ull);
-        return;
-    }
-    int c = ldg_cg(P.cf + x);
-    long long d = eu < (long long)c ? eu : (long long)c;
-    if (d <= 0) return;
-    atomicSub(P.cf + x, (int)d);
-    atomicAdd(P.cf + ldg_cg(P.g.rev + x), (int)d);
-    atomic_add_ll(P.e + u, -d);
-    const int z = ldg_cg(P.g.dst + x);
-    if (z == P.sink) {
-        atomicAdd((unsigned long long *)&sh.sink_e, (unsigned long long)d);
-    } else if (z == P.source) {
-        atomicAdd((unsigned long long *)&sh.src_e, (unsigned long long)d);
+        atomicSub(P.cf + y, (int)amt);
+        atomicAdd(P.cf + x, (int)amt);
     } else {
-        const long long old = atomic_add_ll(P.e + z, d);
-        if (dc.queue && old <= 0 && old + d > 0) enqueue_active(P, z, dc);
+        atomicSub(P.cf + x, (int)amt);
+        atomicAdd(P.cf + y, (int)amt);
     }
-    atomicAdd((unsigned long long *)&sh.pushes, 1ull);
+    const long long dz = PULL ? -amt : amt;
+    if (z == P.sink) {
+        atomicAdd((unsigned long long *)&sh.sink_e, (unsigned long long)dz);
+    } else if (z == P.source) {
+        atomicAdd((unsigned long long *)&sh.src_e, (unsigned long long)dz);
+    } else {
+        const long long old = atomic_add_ll(P.e + z, dz);
+        const bool became = PULL ? (old >= 0 && old + dz < 0) : (old <= 0 && old + dz > 0);
+        if (dc.queue && became) enqueue_active(P, z, dc);
+    }
+}
+
+// Residual of slot x in the direction of the move, from the slot's own row:
+// c_f(u, z) for a push, c_f(z, u) = pcap - c_f(u, z) for a pull.
+template <bool PULL>
+__device__ __forceinline__ int residual_dir(const MfParams &P, int x)
+{
+    return PULL ? ldg_cg(P.g.pcap + x) - ldg_cg(P.cf + x) : ldg_cg(P.cf + x);
+}
+
+// The amount slot x of u can move now (exact): c_f(u, z) for a push, c_f(z, u) for a pull.
+template <bool PULL>
+__device__ __forceinline__ int movable(const MfParams &P, int x, int y)
+{
+    return PULL ? ldg_cg(P.cf + y) : ldg_cg(P.cf + x);
 }
 
 // Lowest residual neighbour over slots j = j0, j0 + step, ... (j < d) of the
@@ -1134,26 +1137,53 @@ __device__ bool discharge_thread(const MfParams &P, Sh &sh, int u, const DisCtx 
     const int r0 = P.g.off[u];
     const int d = ldg_cg(P.g.deg + u);
     int hu = ldg_cg(P.h + u);
-    long long cyc_done = 0;
-    for (int cyc = 0; cyc < P.kernel_cycles; ++cyc) {
-        long long eu = PULL ? -ldg_cg(P.e + u) : ldg_cg(P.e + u);
+    long long scans = 0, moves = 0, fused = 0;
+    int cyc = 0;
+    while (cyc < P.kernel_cycles) {
+        const long long eu = PULL ? -ldg_cg(P.e + u) : ldg_cg(P.e + u);
         if (!(hu < n && eu > 0)) break;
-        ++cyc_done;
+        ++scans;
         unsigned long long best = scan_lowest<4, PULL>(P, r0, d, 0, 1);
         int best_h = best == kEmpty ? 0x7fffffff : (int)(best >> 32);
         if (best != kEmpty && hu > best_h) {
-            do_move<PULL>(P, sh, u, r0 + (int)(best & 0xffffffffu), eu, dc);
+            // The cycles Alg. 2 would run next push to the lowest slots of height
+            // best_h in slot order until the excess or the cycles run out: do
+            // them in this one pass over the row.
+            long long rem = eu, sent = 0;
+            int k = 0;
+            int j = (int)(best & 0xffffffffu);
+            const int jstart = j;
+            for (; j < d && rem > 0 && cyc + k < P.kernel_cycles; ++j) {
+                const int x = r0 + j;
+                if (residual_dir<PULL>(P, x) <= 0) continue;
+                const int z = ldg_cg(P.g.dst + x);
+                if (ldg_cg(P.h + z) != best_h) continue;
+                const int y = ldg_cg(P.g.rev + x);
+                const int c = movable<PULL>(P, x, y);
+                if (c <= 0) continue;
+                const long long a = rem < (long long)c ? rem : (long long)c;
+                move_flow<PULL>(P, sh, x, y, z, a, dc);
+                rem -= a;
+                sent += a;
+                ++k;
+            }
+            if (sent) atomic_add_ll(P.e + u, PULL ? sent : -sent);
+            moves += k;
+            fused += j - jstart;
+            cyc += k > 0 ? k : 1;
         } else {
             hu = (best == kEmpty || best_h >= n - 1) ? n : best_h + 1;
             P.h[u] = hu;
             lifted = true;
             atomicAdd((unsigned long long *)&sh.relabels, 1ull);
+            ++cyc;
         }
     }
-    if (cyc_done) {
-        atomicAdd((unsigned long long *)&sh.cycles, (unsigned long long)cyc_done);
-        atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)(cyc_done * d));
+    if (scans) {
+        atomicAdd((unsigned long long *)&sh.cycles, (unsigned long long)scans);
+        atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)(scans * d + fused));
     }
+    if (moves) atomicAdd((unsigned long long *)&sh.pushes, (unsigned long long)moves);
     return lifted;
 }
 
@@ -1167,15 +1197,62 @@ __device__ bool discharge_warp(const MfParams &P, Sh &sh, int u, const DisCtx &d
     const int r0 = P.g.off[u];
     const int d = ldg_cg(P.g.deg + u);
     int hu = ldg_cg(P.h + u);
-    long long cyc_done = 0;
-    for (int cyc = 0; cyc < P.kernel_cycles; ++cyc) {
-        long long eu = PULL ? -ldg_cg(P.e + u) : ldg_cg(P.e + u);
+    long long scans = 0, moves = 0, fused = 0;
+    int cyc = 0;
+    while (cyc < P.kernel_cycles) {
+        const long long eu = PULL ? -ldg_cg(P.e + u) : ldg_cg(P.e + u);
         if (!(hu < n && eu > 0)) break;
-        ++cyc_done;
+        ++scans;
         unsigned long long best = warp_min_u64(scan_lowest<8, PULL>(P, r0, d, lane, 32));
         int best_h = best == kEmpty ? 0x7fffffff : (int)(best >> 32);
         if (best != kEmpty && hu > best_h) {
-            if (lane == 0) do_move<PULL>(P, sh, u, r0 + (int)(best & 0xffffffffu), eu, dc);
+            // Alg. 2's next cycles, fused: the slots of height best_h in slot
+            // order take min(residual, what is left), 32 slots per step with a
+            // warp prefix sum over the amounts.
+            const int j0 = (int)(best & 0xffffffffu);
+            long long rem = eu, sent = 0;
+            int k = 0;
+            for (int jb = j0 & ~31; jb < d && rem > 0 && cyc + k < P.kernel_cycles; jb += 32) {
+                const int j = jb + lane;
+                int x = 0, y = 0, z = 0;
+                long long a = 0;
+                if (j >= j0 && j < d) {
+                    x = r0 + j;
+                    if (residual_dir<PULL>(P, x) > 0) {
+                        z = ldg_cg(P.g.dst + x);
+                        if (ldg_cg(P.h + z) == best_h) {
+                            y = ldg_cg(P.g.rev + x);
+                            const int c = movable<PULL>(P, x, y);
+                            a = c > 0 ? c : 0;
+                        }
+                    }
+                }
+                fused += 32;
+                long long incl = a;
+                int cincl = a > 0 ? 1 : 0;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const long long t = __shfl_up_sync(0xffffffffu, incl, o);
+                    const int tc = __shfl_up_sync(0xffffffffu, cincl, o);
+                    if (lane >= o) {
+                        incl += t;
+                        cincl += tc;
+                    }
+                }
+                const long long excl = incl - a;
+                const int cexcl = cincl - (a > 0 ? 1 : 0);
+                long long give = 0;
+                if (a > 0 && excl < rem && cyc + k + cexcl < P.kernel_cycles) give = a < rem - excl ? a : rem - excl;
+                if (give > 0) move_flow<PULL>(P, sh, x, y, z, give, dc);
+                const long long tot = warp_sum_ll(give);
+                const int kk = __popc(__ballot_sync(0xffffffffu, give > 0));
+                rem -= tot;
+                sent += tot;
+                k += kk;
+            }
+            if (lane == 0 && sent) atomic_add_ll(P.e + u, PULL ? sent : -sent);
+            moves += k;
+            cyc += k > 0 ? k : 1;
         } else {
             hu = (best == kEmpty || best_h >= n - 1) ? n : best_h + 1;
             lifted = true;
@@ -1183,12 +1260,16 @@ __device__ bool discharge_warp(const MfParams &P, Sh &sh, int u, const DisCtx &d
                 P.h[u] = hu;
                 atomicAdd((unsigned long long *)&sh.relabels, 1ull);
             }
+            ++cyc;
         }
         __syncwarp();
     }
-    if (lane == 0 && cyc_done) {
-        atomicAdd((unsigned long long *)&sh.cycles, (unsigned long long)cyc_done);
-        atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)(cyc_done * d));
+    if (lane == 0) {
+        if (scans) {
+            atomicAdd((unsigned long long *)&sh.cycles, (unsigned long long)scans);
+            atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)(scans * d + fused));
+        }
+        if (moves) atomicAdd((unsigned long long *)&sh.pushes, (unsigned long long)moves);
     }
     return lifted;
 }
@@ -1201,16 +1282,18 @@ __device__ bool discharge_cta(const MfParams &P, Sh &sh, int u, const DisCtx &dc
     bool lifted = false;
     const int n = P.g.n;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
     const int r0 = P.g.off[u];
     const int d = ldg_cg(P.g.deg + u);
-    for (int cyc = 0; cyc < P.kernel_cycles; ++cyc) {
+    int cyc = 0;
+    while (cyc < P.kernel_cycles) {
         if (threadIdx.x == 0) {
             sh.bcast_e = PULL ? -ldg_cg(P.e + u) : ldg_cg(P.e + u);
             sh.bcast_h = ldg_cg(P.h + u);
         }
         __syncthreads();
-        long long eu = sh.bcast_e;
-        int hu = sh.bcast_h;
+        const long long eu = sh.bcast_e;
+        const int hu = sh.bcast_h;
         if (!(hu < n && eu > 0)) {
             __syncthreads();
             break;
@@ -1218,19 +1301,95 @@ __device__ bool discharge_cta(const MfParams &P, Sh &sh, int u, const DisCtx &dc
         unsigned long long best = warp_min_u64(scan_lowest<8, PULL>(P, r0, d, threadIdx.x, blockDim.x));
         if (lane == 0) sh.red[wid] = best;
         __syncthreads();
+        unsigned long long b = kEmpty;
+        for (int w = 0; w < nwarps; ++w) b = sh.red[w] < b ? sh.red[w] : b;
+        const int best_h = b == kEmpty ? 0x7fffffff : (int)(b >> 32);
         if (threadIdx.x == 0) {
-            unsigned long long b = kEmpty;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = sh.red[w] < b ? sh.red[w] : b;
-            int best_h = b == kEmpty ? 0x7fffffff : (int)(b >> 32);
-            if (b != kEmpty && hu > best_h) {
-                do_move<PULL>(P, sh, u, r0 + (int)(b & 0xffffffffu), eu, dc);
-            } else {
-                P.h[u] = (b == kEmpty || best_h >= n - 1) ? n : best_h + 1;
-                lifted = true;
-                atomicAdd((unsigned long long *)&sh.relabels, 1ull);
-            }
             atomicAdd((unsigned long long *)&sh.cycles, 1ull);
             atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)d);
+        }
+        if (b != kEmpty && hu > best_h) {
+            // Alg. 2's next cycles, fused (as in discharge_warp), blockDim slots
+            // per step with a CTA prefix sum over the amounts.
+            const int j0 = (int)(b & 0xffffffffu);
+            long long rem = eu;
+            int k = 0;
+            long long sent = 0;
+            for (int jb = j0 - j0 % (int)blockDim.x; jb < d && rem > 0 && cyc + k < P.kernel_cycles;
+                 jb += blockDim.x) {
+                const int j = jb + threadIdx.x;
+                int x = 0, y = 0, z = 0;
+                long long a = 0;
+                if (j >= j0 && j < d) {
+                    x = r0 + j;
+                    if (residual_dir<PULL>(P, x) > 0) {
+                        z = ldg_cg(P.g.dst + x);
+                        if (ldg_cg(P.h + z) == best_h) {
+                            y = ldg_cg(P.g.rev + x);
+                            const int c = movable<PULL>(P, x, y);
+                            a = c > 0 ? c : 0;
+                        }
+                    }
+                }
+                if (threadIdx.x == 0) atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)blockDim.x);
+                long long incl = a;
+                int cincl = a > 0 ? 1 : 0;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const long long t = __shfl_up_sync(0xffffffffu, incl, o);
+                    const int tc = __shfl_up_sync(0xffffffffu, cincl, o);
+                    if (lane >= o) {
+                        incl += t;
+                        cincl += tc;
+                    }
+                }
+                if (lane == 31) {
+                    sh.wsum[wid] = incl;
+                    sh.wcnt[wid] = cincl;
+                }
+                __syncthreads();
+                long long woff = 0;
+                int wcoff = 0;
+                for (int w = 0; w < wid; ++w) {
+                    woff += sh.wsum[w];
+                    wcoff += sh.wcnt[w];
+                }
+                const long long excl = woff + incl - a;
+                const int cexcl = wcoff + cincl - (a > 0 ? 1 : 0);
+                long long give = 0;
+                if (a > 0 && excl < rem && cyc + k + cexcl < P.kernel_cycles) give = a < rem - excl ? a : rem - excl;
+                if (give > 0) move_flow<PULL>(P, sh, x, y, z, give, dc);
+                const long long wt = warp_sum_ll(give);
+                const int wk = __popc(__ballot_sync(0xffffffffu, give > 0));
+                __syncthreads();               // every warp has read the prefix words
+                if (lane == 0) {
+                    sh.wsum[wid] = wt;
+                    sh.wcnt[wid] = wk;
+                }
+                __syncthreads();
+                long long tot = 0;
+                int kk = 0;
+                for (int w = 0; w < nwarps; ++w) {
+                    tot += sh.wsum[w];
+                    kk += sh.wcnt[w];
+                }
+                rem -= tot;
+                sent += tot;
+                k += kk;
+                __syncthreads();               // before the words are reused
+            }
+            if (threadIdx.x == 0) {
+                if (sent) atomic_add_ll(P.e + u, PULL ? sent : -sent);
+                if (k) atomicAdd((unsigned long long *)&sh.pushes, (unsigned long long)k);
+            }
+            cyc += k > 0 ? k : 1;
+        } else {
+            if (threadIdx.x == 0) {
+                P.h[u] = (b == kEmpty || best_h >= n - 1) ? n : best_h + 1;
+                atomicAdd((unsigned long long *)&sh.relabels, 1ull);
+            }
+            lifted = true;
+            ++cyc;
         }
         __syncthreads();
     }
