@@ -25,6 +25,8 @@
 #define MF_ACTIVE_HIST 64
 #define MF_DEFAULT_ROUNDS 4   // discharge rounds between global relabels unless set
 #define MF_TRACE 256          // hook timeline entries kept per launch
+#define MF_BU_ALPHA 14        // BFS: go bottom-up when the frontier's slots exceed the unexplored slots / alpha
+#define MF_BU_BETA 24         // BFS: go back top-down when the frontier holds fewer than n / beta vertices
 
 // Solve-kernel status (ctrl->status)
 #define MF_ST_RUNNING 0
@@ -71,6 +73,8 @@ struct MfCtrl {
     MfLine wl_tail;       // w[0..2]: worklist append positions per bin
     MfLine misc;          // w[0]: insert list tail, w[1]: touched tail, w[2]: overflow flag
     MfLine aux_tail;      // w[0..2]: next-round worklist tails, w[3]/w[4]: remove-invalid lists (warp / CTA)
+    MfLine bfs_acc;       // 64-bit words: [0] slots of the vertices labelled in this level, [1] their number,
+                          // [2] used slots of the whole graph (summed by the BFS initialisation)
     // ---- (hook) snapshots ----
     int status;
     int level;
@@ -84,6 +88,8 @@ struct MfCtrl {
     int dis_more;         // another discharge round follows
     int fix_n[2];         // vertices for remove-invalid-edges (warp list, CTA list)
     int qstamp, fstamp;   // dedupe stamps (never reset: they only grow across launches)
+    int bu_mode;          // the coming BFS level runs bottom-up
+    long long vis_slots;  // slots of the vertices labelled so far in this BFS
     long long iters;
     unsigned long long t_start, t_phase;
     // ---- results and statistics (atomics, flushed once per CTA per phase) ----

@@ -213,6 +213,8 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
         for (int i = 0; i < 8; ++i) c->misc.w[i] = 0;
         for (int i = 0; i < MF_ACTIVE_HIST; ++i) c->active_hist[i] = 0;
         for (int i = 0; i < 8; ++i) c->aux_tail.w[i] = 0;
+        for (int i = 0; i < 8; ++i) c->bfs_acc.w[i] = 0;
+        c->bu_mode = 0;
         c->round = 0;
         c->dis_more = 0;
         c->rounds_total = 0;
@@ -241,6 +243,8 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
         c->ns_fix = rd(c->ns_fix) + dt;
         c->bfs_tail.w[0] = 0;
         c->hub_tail.w[0] = 0;
+        for (int i = 0; i < 8; ++i) c->bfs_acc.w[i] = 0;
+        c->bu_mode = 0;
         for (int i = 0; i < 4; ++i) c->wl_tail.w[i] = 0;
         c->head0.w[0] = c->head1.w[0] = c->head2.w[0] = 0;
         break;
@@ -258,6 +262,21 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
         c->hub_hi = (int)item_tail;
         c->head0.w[0] = c->head1.w[0] = 0;
         c->bfs_done = done;
+        {
+            // direction of the coming level (Beamer's test): bottom-up once the
+            // frontier's slots exceed 1/alpha of the unexplored slots, back to
+            // top-down once it holds fewer than n/beta vertices
+            const unsigned long long *acc = (const unsigned long long *)c->bfs_acc.w;
+            const long long fr = (long long)__ldcg(acc + 0), cnt = (long long)__ldcg(acc + 1);
+            const long long tot = (long long)__ldcg(acc + 2);
+            const long long vis = (first ? 0 : rd(c->vis_slots)) + fr;
+            int bu = first ? 0 : rd(c->bu_mode);
+            if (!bu && fr * MF_BU_ALPHA > tot - vis) bu = 1;
+            else if (bu && cnt * MF_BU_BETA < (long long)P.g.n) bu = 0;
+            c->bu_mode = bu;
+            c->vis_slots = vis;
+            c->bfs_acc.w[0] = c->bfs_acc.w[1] = c->bfs_acc.w[2] = c->bfs_acc.w[3] = 0;   // per level; [2] stays
+        }
         if (done && want_wl) decide_iteration(P, c, now, wl, iters, t_start, qstamp, fstamp);
         break;
     }
@@ -784,9 +803,13 @@ __device__ __forceinline__ void frontier_push(const MfParams &P, const bool (&ta
     // per-lane counts packed 8 bits each: [0] regular, [1..3] worklist bins
     unsigned packed = 0;
     bool anybig = false;
+    long long lab_slots = 0;
+    int lab_n = 0;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         if (!take[r]) continue;
+        lab_slots += d[r];
+        ++lab_n;
         const bool big = d[r] > P.bfs_hub;
         anybig |= big;
         if (!big) packed += 1u;
@@ -803,6 +826,14 @@ __device__ __forceinline__ void frontier_push(const MfParams &P, const bool (&ta
     }
     const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
     const unsigned excl = incl - packed;
+    // slots and number of the vertices labelled (the BFS direction test reads them)
+    lab_slots = warp_sum_ll(lab_slots);
+    const long long lab_cnt = warp_sum_ll((long long)lab_n);
+    if (lane == 0 && lab_cnt) {
+        unsigned long long *acc = (unsigned long long *)ctl->bfs_acc.w;
+        atomicAdd(acc + 0, (unsigned long long)lab_slots);
+        atomicAdd(acc + 1, (unsigned long long)lab_cnt);
+    }
     if (total != 0) {
         unsigned base[4] = {0, 0, 0, 0};
         if (lane == 0) {
@@ -864,7 +895,9 @@ __device__ __noinline__ void phase_bfs_init(const MfParams &P, Sh &sh)
         bool root[1] = {false};
         int zv[1] = {v}, dv[1] = {0};
         long long ev[1] = {0};
+        long long dall = 0;
         if (v < n) {
+            dall = ldg_cg(P.g.deg + v);
             // push: t and the deficient vertices; pull (Sec. 5.2.2): s and the
             // overflowing vertices; with a side given, only that side's
             const bool side_ok = P.side_root < 0 || P.side[v] == P.side_root;
@@ -873,8 +906,10 @@ __device__ __noinline__ void phase_bfs_init(const MfParams &P, Sh &sh)
             else
                 root[0] = (v == P.sink) || (deficit_roots && v != P.source && side_ok && ldg_cg(P.e + v) < 0);
             P.h[v] = root[0] ? 0 : n;
-            if (root[0]) dv[0] = ldg_cg(P.g.deg + v);
+            if (root[0]) dv[0] = (int)dall;
         }
+        dall = warp_sum_ll(dall);
+        if (lane == 0 && dall) atomicAdd((unsigned long long *)P.ctrl->bfs_acc.w + 2, (unsigned long long)dall);
         frontier_push<1>(P, root, zv, dv, ev, false, 0);
     }
 }
@@ -981,6 +1016,60 @@ __device__ __noinline__ void phase_bfs_level(const MfParams &P, Sh &sh)
             }
             bfs_visit<kBR>(P, xs, vs, L, sel);
         }
+    }
+    if (slots) atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)slots);
+}
+
+// A BFS level bottom-up (direction-optimising BFS): every unlabelled vertex v
+// looks through its own row for a neighbour u of the current level with a
+// residual edge towards it -- c_f(v, u) > 0, v's own slot, for the push
+// heights; c_f(u, v) = pcap - c_f(v, u) for the pull heights -- and stops at
+// the first one.  The labels equal the top-down level's (each vertex is
+// labelled L + 1 exactly when it has such a neighbour); the work follows the
+// unlabelled vertices' rows up to the first hit instead of the frontier's
+// rows, which pays off once the frontier holds most of the graph.
+__device__ __noinline__ void phase_bfs_bottom_up(const MfParams &P, Sh &sh)
+{
+    MfCtrl *ctl = P.ctrl;
+    const int n = P.g.n;
+    const int L = vrd(&ctl->level);
+    const int sel = vrd(&ctl->wl_sel);
+    const bool pull = P.pull != 0;
+    const int skip = pull ? P.sink : P.source;
+    const bool with_wl = P.data_driven && !(P.mode & MF_M_BFS_ONLY);
+    const int lane = threadIdx.x & 31;
+    const long long gs = (long long)vn() * blockDim.x;
+    long long slots = 0;
+    for (long long base = (long long)vb() * blockDim.x + threadIdx.x - lane; base < n; base += gs) {
+        const int v = (int)base + lane;
+        bool take[1] = {false};
+        int zv[1] = {v}, dv[1] = {0};
+        long long ev[1] = {0};
+        if (v < n && v != skip && ldg_cg(P.h + v) == n) {
+            const int r0 = P.g.off[v], d = ldg_cg(P.g.deg + v);
+            int j = 0;
+            for (; j < d && !take[0]; j += 4) {
+                int c[4], z[4], hz[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int x = r0 + j + r;
+                    const bool ok = j + r < d;
+                    c[r] = ok ? (pull ? ldg_cg(P.g.pcap + x) - ldg_cg(P.cf + x) : ldg_cg(P.cf + x)) : 0;
+                    z[r] = ok ? ldg_cg(P.g.dst + x) : 0;
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r) hz[r] = c[r] > 0 ? ldg_cg(P.h + z[r]) : -1;
+#pragma unroll
+                for (int r = 0; r < 4; ++r) take[0] |= hz[r] == L;
+            }
+            slots += j < d ? j : d;
+            if (take[0]) {
+                P.h[v] = L + 1;
+                dv[0] = d;
+                if (with_wl && v != P.sink && v != P.source) ev[0] = pull ? -ldg_cg(P.e + v) : ldg_cg(P.e + v);
+            }
+        }
+        frontier_push<1>(P, take, zv, dv, ev, with_wl, sel);
     }
     if (slots) atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)slots);
 }
@@ -1631,7 +1720,8 @@ __device__ __noinline__ bool solve_instance(const MfParams &P, Sh &sh)
         phase_bfs_init(P, sh);
         if (!grid_sync(P, H_BFS_START, sh)) return false;
         while (!vrd(&P.ctrl->bfs_done)) {
-            phase_bfs_level(P, sh);
+            if (vrd(&P.ctrl->bu_mode)) phase_bfs_bottom_up(P, sh);
+            else phase_bfs_level(P, sh);
             flush_acc(P, sh, 0);
             if (!grid_sync(P, H_BFS_NEXT, sh)) return false;
         }
