@@ -89,6 +89,7 @@ struct MfCtrl {
     int fix_n[2];         // vertices for remove-invalid-edges (warp list, CTA list)
     int qstamp, fstamp;   // dedupe stamps (never reset: they only grow across launches)
     int bu_mode;          // the coming BFS level runs bottom-up
+    int need_total;       // the coming BFS initialisation sums the used slots (first BFS of a launch)
     long long vis_slots;  // slots of the vertices labelled so far in this BFS
     long long iters;
     unsigned long long t_start, t_phase;

@@ -215,6 +215,7 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
         for (int i = 0; i < 8; ++i) c->aux_tail.w[i] = 0;
         for (int i = 0; i < 8; ++i) c->bfs_acc.w[i] = 0;
         c->bu_mode = 0;
+        c->need_total = 1;
         c->round = 0;
         c->dis_more = 0;
         c->rounds_total = 0;
@@ -243,7 +244,10 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
         c->ns_fix = rd(c->ns_fix) + dt;
         c->bfs_tail.w[0] = 0;
         c->hub_tail.w[0] = 0;
-        for (int i = 0; i < 8; ++i) c->bfs_acc.w[i] = 0;
+        // the used-slot total (acc word 2) only changes with insertions, which
+        // come before the first BFS: later iterations keep it
+        for (int i = 0; i < 4; ++i) c->bfs_acc.w[i] = 0;
+        c->need_total = rd(c->bfs_acc.w[4]) == 0 && rd(c->bfs_acc.w[5]) == 0;
         c->bu_mode = 0;
         for (int i = 0; i < 4; ++i) c->wl_tail.w[i] = 0;
         c->head0.w[0] = c->head1.w[0] = c->head2.w[0] = 0;
@@ -888,6 +892,8 @@ __device__ __noinline__ void phase_bfs_init(const MfParams &P, Sh &sh)
     const int n = P.g.n;
     const bool deficit_roots = (P.mode & MF_M_NO_DEFICIT_ROOTS) == 0;
     const bool pull = P.pull != 0;
+    const bool need_total = vrd(&P.ctrl->need_total) != 0;
+    long long total = 0;
     const int lane = threadIdx.x & 31;
     const long long gs = (long long)vn() * blockDim.x;
     for (long long base = (long long)vb() * blockDim.x + threadIdx.x - lane; base < n; base += gs) {
@@ -895,9 +901,9 @@ __device__ __noinline__ void phase_bfs_init(const MfParams &P, Sh &sh)
         bool root[1] = {false};
         int zv[1] = {v}, dv[1] = {0};
         long long ev[1] = {0};
-        long long dall = 0;
+        int dall = 0;
         if (v < n) {
-            dall = ldg_cg(P.g.deg + v);
+            if (need_total) dall = ldg_cg(P.g.deg + v);
             // push: t and the deficient vertices; pull (Sec. 5.2.2): s and the
             // overflowing vertices; with a side given, only that side's
             const bool side_ok = P.side_root < 0 || P.side[v] == P.side_root;
@@ -906,11 +912,22 @@ __device__ __noinline__ void phase_bfs_init(const MfParams &P, Sh &sh)
             else
                 root[0] = (v == P.sink) || (deficit_roots && v != P.source && side_ok && ldg_cg(P.e + v) < 0);
             P.h[v] = root[0] ? 0 : n;
-            if (root[0]) dv[0] = (int)dall;
+            if (root[0]) dv[0] = need_total ? dall : ldg_cg(P.g.deg + v);
         }
-        dall = warp_sum_ll(dall);
-        if (lane == 0 && dall) atomicAdd((unsigned long long *)P.ctrl->bfs_acc.w + 2, (unsigned long long)dall);
-        frontier_push<1>(P, root, zv, dv, ev, false, 0);
+        total += dall;
+        if (__any_sync(0xffffffffu, root[0])) frontier_push<1>(P, root, zv, dv, ev, false, 0);
+    }
+    if (need_total) {
+        // one atomic per CTA for the used-slot total
+        total = warp_sum_ll(total);
+        if (lane == 0) sh.wsum[threadIdx.x >> 5] = total;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long t = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh.wsum[w];
+            if (t) atomicAdd((unsigned long long *)P.ctrl->bfs_acc.w + 2, (unsigned long long)t);
+        }
+        __syncthreads();
     }
 }
 
@@ -1069,7 +1086,7 @@ __device__ __noinline__ void phase_bfs_bottom_up(const MfParams &P, Sh &sh)
                 if (with_wl && v != P.sink && v != P.source) ev[0] = pull ? -ldg_cg(P.e + v) : ldg_cg(P.e + v);
             }
         }
-        frontier_push<1>(P, take, zv, dv, ev, with_wl, sel);
+        if (__any_sync(0xffffffffu, take[0])) frontier_push<1>(P, take, zv, dv, ev, with_wl, sel);
     }
     if (slots) atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)slots);
 }
