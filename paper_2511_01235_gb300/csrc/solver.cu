@@ -1251,7 +1251,17 @@ __device__ bool discharge_thread(const MfParams &P, Sh &sh, int u, const DisCtx 
         ++scans;
         unsigned long long best = scan_lowest<4, PULL>(P, r0, d, 0, 1);
         int best_h = best == kEmpty ? 0x7fffffff : (int)(best >> 32);
-        if (best != kEmpty && hu > best_h) {
+        if (best == kEmpty || hu <= best_h) {
+            // relabel (Alg. 2 lines 17-19); the next cycle would find the same
+            // lowest slots admissible, so it continues below without a rescan
+            hu = (best == kEmpty || best_h >= n - 1) ? n : best_h + 1;
+            P.h[u] = hu;
+            lifted = true;
+            atomicAdd((unsigned long long *)&sh.relabels, 1ull);
+            ++cyc;
+            if (hu >= n || cyc >= P.kernel_cycles) continue;
+        }
+        {
             // The cycles Alg. 2 would run next push to the lowest slots of height
             // best_h in slot order until the excess or the cycles run out: do
             // them in this one pass over the row.
@@ -1277,12 +1287,6 @@ __device__ bool discharge_thread(const MfParams &P, Sh &sh, int u, const DisCtx 
             moves += k;
             fused += j - jstart;
             cyc += k > 0 ? k : 1;
-        } else {
-            hu = (best == kEmpty || best_h >= n - 1) ? n : best_h + 1;
-            P.h[u] = hu;
-            lifted = true;
-            atomicAdd((unsigned long long *)&sh.relabels, 1ull);
-            ++cyc;
         }
     }
     if (scans) {
@@ -1311,7 +1315,21 @@ __device__ bool discharge_warp(const MfParams &P, Sh &sh, int u, const DisCtx &d
         ++scans;
         unsigned long long best = warp_min_u64(scan_lowest<8, PULL>(P, r0, d, lane, 32));
         int best_h = best == kEmpty ? 0x7fffffff : (int)(best >> 32);
-        if (best != kEmpty && hu > best_h) {
+        if (best == kEmpty || hu <= best_h) {
+            // relabel, then straight on to the pushes it makes admissible
+            hu = (best == kEmpty || best_h >= n - 1) ? n : best_h + 1;
+            lifted = true;
+            if (lane == 0) {
+                P.h[u] = hu;
+                atomicAdd((unsigned long long *)&sh.relabels, 1ull);
+            }
+            ++cyc;
+            if (hu >= n || cyc >= P.kernel_cycles) {
+                __syncwarp();
+                continue;
+            }
+        }
+        {
             // Alg. 2's next cycles, fused: the slots of height best_h in slot
             // order take min(residual, what is left), 32 slots per step with a
             // warp prefix sum over the amounts.
@@ -1359,14 +1377,6 @@ __device__ bool discharge_warp(const MfParams &P, Sh &sh, int u, const DisCtx &d
             if (lane == 0 && sent) atomic_add_ll(P.e + u, PULL ? sent : -sent);
             moves += k;
             cyc += k > 0 ? k : 1;
-        } else {
-            hu = (best == kEmpty || best_h >= n - 1) ? n : best_h + 1;
-            lifted = true;
-            if (lane == 0) {
-                P.h[u] = hu;
-                atomicAdd((unsigned long long *)&sh.relabels, 1ull);
-            }
-            ++cyc;
         }
         __syncwarp();
     }
@@ -1414,7 +1424,19 @@ __device__ bool discharge_cta(const MfParams &P, Sh &sh, int u, const DisCtx &dc
             atomicAdd((unsigned long long *)&sh.cycles, 1ull);
             atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)d);
         }
-        if (b != kEmpty && hu > best_h) {
+        bool go = b != kEmpty && hu > best_h;
+        if (!go) {
+            // relabel, then straight on to the pushes it makes admissible
+            const int nh = (b == kEmpty || best_h >= n - 1) ? n : best_h + 1;
+            if (threadIdx.x == 0) {
+                P.h[u] = nh;
+                atomicAdd((unsigned long long *)&sh.relabels, 1ull);
+            }
+            lifted = true;
+            ++cyc;
+            go = nh < n && cyc < P.kernel_cycles;
+        }
+        if (go) {
             // Alg. 2's next cycles, fused (as in discharge_warp), blockDim slots
             // per step with a CTA prefix sum over the amounts.
             const int j0 = (int)(b & 0xffffffffu);
@@ -1489,13 +1511,6 @@ __device__ bool discharge_cta(const MfParams &P, Sh &sh, int u, const DisCtx &dc
                 if (k) atomicAdd((unsigned long long *)&sh.pushes, (unsigned long long)k);
             }
             cyc += k > 0 ? k : 1;
-        } else {
-            if (threadIdx.x == 0) {
-                P.h[u] = (b == kEmpty || best_h >= n - 1) ? n : best_h + 1;
-                atomicAdd((unsigned long long *)&sh.relabels, 1ull);
-            }
-            lifted = true;
-            ++cyc;
         }
         __syncthreads();
     }
