@@ -118,7 +118,7 @@ typedef struct {
     double  ms_kernel;              /* device clock from kernel entry to its last grid barrier */
     int64_t barriers;               /* grid barriers the last solve kernel passed */
     int64_t discharge_rounds;       /* discharge rounds the last solve ran (all iterations) */
-    int32_t rounds;                 /* current setting of maxflow_set_rounds */
+    int32_t rounds;                 /* current setting of maxflow_set_rounds (0: adaptive) */
     int32_t reserved0;
     double  ms_update;              /* device time of every launch of the last update or solve call */
 } maxflow_stats_t;
@@ -166,12 +166,16 @@ int maxflow_get_flow(maxflow_ctx *c, int64_t *count, int32_t *u, int32_t *v, int
  * the wrong way). */
 int maxflow_set_kernel_cycles(maxflow_ctx *c, int32_t k);
 
-/* Discharge rounds per global relabel (>= 1).  1 is the paper's data-driven
- * kernel (Sec. 5.2.1 O1): the vertices active right after the backward BFS get
+/* Discharge rounds per global relabel.  1 is the paper's data-driven kernel
+ * (Sec. 5.2.1 O1): the vertices active right after the backward BFS get
  * KERNEL_CYCLES cycles each.  With r > 1, vertices that become active while a
  * round runs (they receive flow) are discharged in the next round, up to r
  * rounds, before the next BFS -- as in the paper's kernel, where every vertex
- * checks e(u) > 0 on each of its cycles. */
+ * checks e(u) > 0 on each of its cycles.  0 (the default) is adaptive, not in
+ * the paper: at least 4 rounds, then more while the discharge of the current
+ * iteration has taken less than half the time of its BFS, at most 1024, so
+ * that a global relabel that costs much (a deep BFS, as on grids) is spread
+ * over more discharge work.  MAXFLOW_ERR_INVALID below 0. */
 int maxflow_set_rounds(maxflow_ctx *c, int32_t rounds);
 
 /* ---- learned schedule (an addition to the paper's fixed KERNEL_CYCLES) ----
@@ -227,6 +231,16 @@ int maxflow_update_scheduled(maxflow_ctx *c, const maxflow_batch *b, maxflow_mlp
  * warp_max_slots, then a CTA); the BFS splits rows longer than
  * bfs_item_min_slots into 256-slot work items.  Defaults 8 / 512 / 256. */
 int maxflow_set_tuning(maxflow_ctx *c, int32_t thread_max_slots, int32_t warp_max_slots, int32_t bfs_item_min_slots);
+
+/* Direction of the global-relabel BFS levels (direction-optimising BFS, not
+ * in the paper, which sweeps top-down).  A level runs bottom-up -- each
+ * unlabelled vertex looks through its own row for a neighbour of the current
+ * level with residual towards it, stopping at the first -- once the frontier's
+ * slots exceed 1/alpha of the still unexplored slots, and top-down again once
+ * the frontier holds fewer than n/beta vertices.  The labels are the same
+ * either way.  alpha = 0 keeps every level top-down.  Defaults 14 and 24.
+ * MAXFLOW_ERR_INVALID for alpha < 0 or beta < 1. */
+int maxflow_set_bfs_switch(maxflow_ctx *c, int32_t alpha, int32_t beta);
 
 /* Solve many instances in ONE persistent cooperative launch (on the first
  * context's device and stream): the grid is cut into groups of group_blocks

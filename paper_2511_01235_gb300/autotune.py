@@ -16,10 +16,10 @@ import numpy as np
 from . import native
 
 GROUP_BLOCKS = (1, 2, 4, 8, 16, 32)
-ROUNDS = (1, 4, 16, 64)
+ROUNDS = (0, 1, 4, 16, 64)            # 0: the adaptive count
 CYCLES = (0, 4, 16)                   # 0: the average-degree heuristic
 SPLITS = ((8, 512, 256), (4, 256, 128), (16, 2048, 1024), (32, 8192, 4096))
-DEFAULT = {"group_blocks": 8, "rounds": 4, "cycles": 0, "split": (8, 512, 256)}
+DEFAULT = {"group_blocks": 8, "rounds": 0, "cycles": 0, "split": (8, 512, 256)}
 
 
 def apply_config(solvers, cfg):

@@ -28,6 +28,7 @@ struct maxflow_ctx {
     int32_t kernel_cycles = 1;
     int32_t rounds = 1;
     int32_t small_deg = MF_SMALL_DEG, hub_deg = MF_HUB_DEG, bfs_hub = MF_BFS_HUB;
+    int32_t bu_alpha = MF_BU_ALPHA, bu_beta = MF_BU_BETA;
     // batched launches started from this context (parameter list, group state)
     MfParams *multi_plist = nullptr;
     unsigned *multi_gstate = nullptr;
@@ -154,6 +155,8 @@ MfParams base_params(maxflow_ctx *c)
     p.small_deg = c->small_deg;
     p.hub_deg = c->hub_deg;
     p.bfs_hub = c->bfs_hub;
+    p.bu_alpha = c->bu_alpha;
+    p.bu_beta = c->bu_beta;
     p.fix_steep = c->opt.fix_steep ? 1 : 0;
     p.data_driven = c->opt.data_driven ? 1 : 0;
     p.pull = 0;
@@ -692,7 +695,7 @@ int maxflow_init(maxflow_ctx **out, const maxflow_graph *g, int32_t s, int32_t t
     if (rc == MAXFLOW_OK) {
         int64_t m = c->st.m_edges;
         c->kernel_cycles = o.kernel_cycles > 0 ? o.kernel_cycles : (int32_t)std::max<int64_t>(1, (m + c->n - 1) / c->n);
-        c->rounds = MF_DEFAULT_ROUNDS;
+        c->rounds = 0;   // adaptive
         c->st.rounds = c->rounds;
         choose_grid(c);
         MfParams p = base_params(c);
@@ -834,7 +837,7 @@ const SchedAction kActions[] = {
     {0, 4, 1}, {0, 4, 4}, {0, 4, 16}, {0, 4, 64},
     {0, 16, 1}, {0, 16, 4}, {0, 16, 16}, {0, 16, 64},
     {0, 64, 1}, {0, 64, 4}, {0, 64, 16}, {0, 64, 64},
-    {0, 1, 0}, {0, MF_DEFAULT_ROUNDS, 0},
+    {0, 1, 0}, {0, 0, 0},
     {1, 4, 4}, {1, 16, 16}, {1, 64, 16}, {1, 1, 0},
 };
 constexpr int kNumActions = (int)(sizeof(kActions) / sizeof(kActions[0]));
@@ -967,6 +970,14 @@ int maxflow_set_tuning(maxflow_ctx *c, int32_t thread_max_slots, int32_t warp_ma
     c->small_deg = thread_max_slots;
     c->hub_deg = warp_max_slots;
     c->bfs_hub = bfs_item_min_slots;
+    return MAXFLOW_OK;
+}
+
+int maxflow_set_bfs_switch(maxflow_ctx *c, int32_t alpha, int32_t beta)
+{
+    if (!c || alpha < 0 || beta < 1) return MAXFLOW_ERR_INVALID;
+    c->bu_alpha = alpha;
+    c->bu_beta = beta;
     return MAXFLOW_OK;
 }
 
@@ -1399,7 +1410,7 @@ int maxflow_update_pp(maxflow_ctx *c, const maxflow_batch *b, int32_t stop_after
 
 int maxflow_set_rounds(maxflow_ctx *c, int32_t rounds)
 {
-    if (!c || rounds < 1 || rounds > (1 << 20)) return MAXFLOW_ERR_INVALID;
+    if (!c || rounds < 0 || rounds > (1 << 20)) return MAXFLOW_ERR_INVALID;
     c->rounds = rounds;
     c->st.rounds = rounds;
     return MAXFLOW_OK;
@@ -1423,6 +1434,8 @@ int maxflow_clone(maxflow_ctx *src, maxflow_ctx **out)
     c->kernel_cycles = src->kernel_cycles;
     c->rounds = src->rounds;
     c->small_deg = src->small_deg;
+    c->bu_alpha = src->bu_alpha;
+    c->bu_beta = src->bu_beta;
     c->hub_deg = src->hub_deg;
     c->bfs_hub = src->bfs_hub;
     c->per_sm = src->per_sm;

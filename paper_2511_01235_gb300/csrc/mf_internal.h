@@ -23,10 +23,11 @@
 #define MF_BFS_HUB 256        // BFS: rows above this many slots enter the frontier as work items
 #define MF_BFS_CHUNK 256      // BFS: slots per work item
 #define MF_ACTIVE_HIST 64
-#define MF_DEFAULT_ROUNDS 4   // discharge rounds between global relabels unless set
+#define MF_DEFAULT_ROUNDS 4   // discharge rounds between global relabels: fixed count, or the adaptive minimum
+#define MF_MAX_ROUNDS 1024    // adaptive rounds: upper bound per iteration
 #define MF_TRACE 256          // hook timeline entries kept per launch
-#define MF_BU_ALPHA 14        // BFS: go bottom-up when the frontier's slots exceed the unexplored slots / alpha
-#define MF_BU_BETA 24         // BFS: go back top-down when the frontier holds fewer than n / beta vertices
+#define MF_BU_ALPHA 14        // BFS default: go bottom-up when the frontier's slots exceed the unexplored slots / alpha
+#define MF_BU_BETA 24         // BFS default: back to top-down when the frontier holds fewer than n / beta vertices
 
 // Solve-kernel status (ctrl->status)
 #define MF_ST_RUNNING 0
@@ -88,6 +89,7 @@ struct MfCtrl {
     int dis_more;         // another discharge round follows
     int fix_n[2];         // vertices for remove-invalid-edges (warp list, CTA list)
     int qstamp, fstamp;   // dedupe stamps (never reset: they only grow across launches)
+    unsigned long long t_bfs0, t_dis0;   // this iteration: BFS start, discharge start (adaptive rounds)
     int bu_mode;          // the coming BFS level runs bottom-up
     int need_total;       // the coming BFS initialisation sums the used slots (first BFS of a launch)
     long long vis_slots;  // slots of the vertices labelled so far in this BFS
@@ -149,10 +151,14 @@ struct MfParams {
     int32_t sink, source;
     int32_t mode;
     int32_t kernel_cycles;
-    int32_t rounds;           // discharge rounds between two global relabels (1 = the paper's O1 worklist)
+    int32_t rounds;           // discharge rounds between two global relabels (1 = the paper's O1 worklist);
+                              // 0: adaptive (at least MF_DEFAULT_ROUNDS, more while discharging has taken
+                              // less than half the time of this iteration's BFS)
     int32_t small_deg;        // discharge: rows up to this many slots get one thread
     int32_t hub_deg;          // discharge / remove-invalid: rows above this many slots get a CTA
     int32_t bfs_hub;          // BFS: rows above this many slots enter the frontier as work items
+    int32_t bu_alpha;         // BFS direction switch (0: top-down only), see MF_BU_ALPHA
+    int32_t bu_beta;
     int32_t fix_steep;
     int32_t data_driven;
     int32_t pull;             // 0: push excess toward t and deficits; 1: pull for deficits from s and excess (Sec. 5.2.2)

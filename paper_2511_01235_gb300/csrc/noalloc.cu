@@ -107,6 +107,8 @@ extern "C" int maxflow_global_relabel_noalloc(int32_t n, int32_t s, int32_t t, c
     p.small_deg = MF_SMALL_DEG;
     p.hub_deg = MF_HUB_DEG;
     p.bfs_hub = MF_BFS_HUB;
+    p.bu_alpha = MF_BU_ALPHA;
+    p.bu_beta = MF_BU_BETA;
     p.max_iters = 1;
     p.time_limit_ns = 60ull * 1000000000ull;
     p.wait_limit_ns = 1000000000ull;

@@ -146,6 +146,7 @@ __device__ __forceinline__ void decide_iteration(const MfParams &P, MfCtrl *c, u
     c->qstamp = qstamp + 1;
     c->fstamp = fstamp + 1;
     const int active = (int)wl[3];
+    c->t_dis0 = now;
     for (int b = 0; b < 3; ++b) c->wl_n[b] = (int)wl[b];
     c->head0.w[0] = c->head1.w[0] = c->head2.w[0] = 0;
     if (iters < MF_ACTIVE_HIST) c->active_hist[iters] = active;
@@ -242,6 +243,7 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
         break;
     case H_ITER:
         c->ns_fix = rd(c->ns_fix) + dt;
+        c->t_bfs0 = now;
         c->bfs_tail.w[0] = 0;
         c->hub_tail.w[0] = 0;
         // the used-slot total (acc word 2) only changes with insertions, which
@@ -275,8 +277,9 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
             const long long tot = (long long)__ldcg(acc + 2);
             const long long vis = (first ? 0 : rd(c->vis_slots)) + fr;
             int bu = first ? 0 : rd(c->bu_mode);
-            if (!bu && fr * MF_BU_ALPHA > tot - vis) bu = 1;
-            else if (bu && cnt * MF_BU_BETA < (long long)P.g.n) bu = 0;
+            if (P.bu_alpha <= 0) bu = 0;
+            else if (!bu && fr * P.bu_alpha > tot - vis) bu = 1;
+            else if (bu && cnt * P.bu_beta < (long long)P.g.n) bu = 0;
             c->bu_mode = bu;
             c->vis_slots = vis;
             c->bfs_acc.w[0] = c->bfs_acc.w[1] = c->bfs_acc.w[2] = c->bfs_acc.w[3] = 0;   // per level; [2] stays
@@ -295,7 +298,20 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
         c->head0.w[0] = c->head1.w[0] = c->head2.w[0] = 0;
         c->rounds_total = rounds_total + 1;
         const unsigned nxt = aux[0] + aux[1] + aux[2];
-        if (round + 1 < P.rounds && nxt > 0 && err == 0) {
+        // fixed: P.rounds rounds; adaptive (P.rounds == 0): at least
+        // MF_DEFAULT_ROUNDS, then more while this iteration's discharge has
+        // taken less than half of its BFS -- a global relabel that costs much
+        // (deep BFS, e.g. grids) is amortised over more rounds
+        bool more = nxt > 0 && err == 0 && round + 1 < MF_MAX_ROUNDS;
+        if (more && round + 1 >= (P.rounds > 0 ? P.rounds : MF_DEFAULT_ROUNDS)) {
+            if (P.rounds > 0) {
+                more = false;
+            } else {
+                const unsigned long long t_bfs0 = rd(c->t_bfs0), t_dis0 = rd(c->t_dis0);
+                more = 2 * (now - t_dis0) < t_dis0 - t_bfs0;
+            }
+        }
+        if (more) {
             c->wl_sel = sel ^ 1;
             for (int b = 0; b < 3; ++b) {
                 c->wl_n[b] = (int)aux[b];
@@ -1527,7 +1543,9 @@ __device__ __noinline__ void phase_discharge(const MfParams &P, Sh &sh)
     dc.nsel = sel ^ 1;
     dc.qstamp = vrd(&ctl->qstamp);
     dc.fstamp = vrd(&ctl->fstamp);
-    dc.queue = vrd(&ctl->round) + 1 < P.rounds;
+    // queue the vertices that become active for a next round if one may follow
+    // (adaptive rounds: the hook decides after this round)
+    dc.queue = vrd(&ctl->round) + 1 < (P.rounds > 0 ? P.rounds : MF_MAX_ROUNDS);
     const int *wl0 = P.sc.wl[sel][0], *wl1 = P.sc.wl[sel][1], *wl2 = P.sc.wl[sel][2];
     // hubs: one CTA each
     const int nh = vrd(&ctl->wl_n[2]);

@@ -93,7 +93,8 @@ EXPORTS = ["maxflow_default_opts", "maxflow_init", "maxflow_update", "maxflow_qu
            "maxflow_set_stream", "maxflow_reserve_batch",
            "maxflow_arena_create", "maxflow_arena_destroy", "maxflow_arena_alloc", "maxflow_arena_free",
            "maxflow_arena_stats", "maxflow_arena_fits", "maxflow_evicted_sizes",
-           "maxflow_resolve_static_pp", "maxflow_resolve_static_pull", "maxflow_update_pp"]
+           "maxflow_resolve_static_pp", "maxflow_resolve_static_pull", "maxflow_update_pp",
+           "maxflow_set_bfs_switch"]
 
 TRACE_NAMES = ["start", "prologue", "batch_validated", "batch_located", "room_checked", "capacities_changed",
                "iteration_start", "bfs_roots", "bfs_level", "worklist", "discharge", "end"]
@@ -155,6 +156,7 @@ def load(build_if_missing: bool = False):
     L.maxflow_resolve_static_pp.argtypes = [vp]
     L.maxflow_resolve_static_pull.argtypes = [vp]
     L.maxflow_update_pp.argtypes = [vp, P(Batch), i32]
+    L.maxflow_set_bfs_switch.argtypes = [vp, i32, i32]
     L.maxflow_restore.argtypes = [vp]
     L.maxflow_solve_batched.argtypes = [vp, i32, vp, i32, P(C.c_double)]
     L.maxflow_sched_actions.argtypes = [vp, vp, vp, i32, P(i32)]
@@ -681,6 +683,10 @@ class Solver:
     def restore(self):
         _check(load().maxflow_restore(self.h), "maxflow_restore")
         self.evicted = False
+
+    def set_bfs_switch(self, alpha=14, beta=24):
+        """Direction-optimising BFS thresholds (alpha = 0: top-down only)."""
+        _check(load().maxflow_set_bfs_switch(self.h, int(alpha), int(beta)), "maxflow_set_bfs_switch")
 
     def set_tuning(self, thread_max_slots=8, warp_max_slots=512, bfs_item_min_slots=256):
         maxflow_set_tuning(self.h, thread_max_slots, warp_max_slots, bfs_item_min_slots)

@@ -32,7 +32,7 @@ from . import workloads as W
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_WEIGHTS = os.path.join(HERE, "scheduler_weights.json")
 ACTION_PAPER = 16      # one discharge round, KERNEL_CYCLES = average degree (the paper's schedule)
-ACTION_DEFAULT = 17    # the library's default rounds, KERNEL_CYCLES = average degree
+ACTION_DEFAULT = 17    # the library's default (adaptive) rounds, KERNEL_CYCLES = average degree
 N_FEATURES = 16
 
 
