@@ -474,3 +474,33 @@ def test_discharge_rounds_do_not_change_the_value(rounds, k):
     if rounds == 0:
         assert S.stats()["discharge_rounds"] >= 1
     S.close()
+
+
+@pytest.mark.parametrize("alpha,beta", [(0, 24), (1, 1), (14, 24), (1000, 1000)])
+def test_bfs_direction_switch_does_not_change_labels_or_values(alpha, beta):
+    # bottom-up levels label exactly what top-down levels label: same heights after a BFS-only
+    # relabel of the same state, and the same values over updates
+    g = W.rmat(12, 16, 0.57, 0.19, 0.19, seed=171, cap_hi=1000)
+    es = W.EdgeSet(g.n, g.src, g.dst, g.cap)
+    rng = np.random.default_rng(172)
+    S = native.Solver(g.n, g.src, g.dst, g.cap, g.s, g.t)
+    R = S.clone()
+    S.set_bfs_switch(alpha, beta)
+    R.set_bfs_switch(0, 24)
+    for _ in range(3):
+        b = W.mixed_batch(es, 300, rng, ins_cap_hi=1000, st_bias=(g.s, g.t, 0.3))
+        es.apply(b.u, b.v, b.cap)
+        S.update(b.u, b.v, b.cap)
+        R.update(b.u, b.v, b.cap)
+        u2, v2, c2 = es.coo()
+        check_against_oracle(S, g.n, u2, v2, c2, g.s, g.t)
+        assert S.query()[0] == R.query()[0]
+    # same state, BFS only: identical heights whatever the direction
+    C = S.clone()
+    C.set_bfs_switch(0, 24)
+    S.global_relabel()
+    C.global_relabel()
+    assert np.array_equal(S.vertex_state()[0], C.vertex_state()[0])
+    with pytest.raises(native.MaxflowError):
+        S.set_bfs_switch(-1, 24)
+    C.close(); R.close(); S.close()
