@@ -1347,29 +1347,45 @@ __device__ bool discharge_warp(const MfParams &P, Sh &sh, int u, const DisCtx &d
         }
         {
             // Alg. 2's next cycles, fused: the slots of height best_h in slot
-            // order take min(residual, what is left), 32 slots per step with a
-            // warp prefix sum over the amounts.
+            // order take min(residual, what is left); each step covers 8 * 32
+            // slots, every lane 8 contiguous ones, with a warp prefix sum over
+            // the lanes' totals.
+            constexpr int kSeg = 8;
             const int j0 = (int)(best & 0xffffffffu);
             long long rem = eu, sent = 0;
             int k = 0;
-            for (int jb = j0 & ~31; jb < d && rem > 0 && cyc + k < P.kernel_cycles; jb += 32) {
-                const int j = jb + lane;
-                int x = 0, y = 0, z = 0;
-                long long a = 0;
-                if (j >= j0 && j < d) {
-                    x = r0 + j;
-                    if (residual_dir<PULL>(P, x) > 0) {
-                        z = ldg_cg(P.g.dst + x);
-                        if (ldg_cg(P.h + z) == best_h) {
-                            y = ldg_cg(P.g.rev + x);
-                            const int c = movable<PULL>(P, x, y);
-                            a = c > 0 ? c : 0;
-                        }
+            int seg = 1;    // one slot per lane first, kSeg after
+            for (int jb = j0; jb < d && rem > 0 && cyc + k < P.kernel_cycles; jb += seg * 32, seg = kSeg) {
+                const int js = jb + lane * seg;
+                int a[kSeg];
+                long long tsum = 0;
+                int tcnt = 0;
+#pragma unroll
+                for (int r = 0; r < kSeg; ++r) {
+                    a[r] = 0;
+                    const int j = js + r;
+                    if (r < seg && j < d && residual_dir<PULL>(P, r0 + j) > 0) a[r] = 1;
+                }
+#pragma unroll
+                for (int r = 0; r < kSeg; ++r) {
+                    if (a[r]) {
+                        const int x = r0 + js + r;
+                        a[r] = ldg_cg(P.h + ldg_cg(P.g.dst + x)) == best_h ? 1 : 0;
                     }
                 }
-                fused += 32;
-                long long incl = a;
-                int cincl = a > 0 ? 1 : 0;
+#pragma unroll
+                for (int r = 0; r < kSeg; ++r) {
+                    if (a[r]) {
+                        const int x = r0 + js + r;
+                        const int c = movable<PULL>(P, x, ldg_cg(P.g.rev + x));
+                        a[r] = c > 0 ? c : 0;
+                        tsum += a[r];
+                        tcnt += a[r] > 0 ? 1 : 0;
+                    }
+                }
+                fused += seg * 32;
+                long long incl = tsum;
+                int cincl = tcnt;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
                     const long long t = __shfl_up_sync(0xffffffffu, incl, o);
@@ -1379,13 +1395,27 @@ __device__ bool discharge_warp(const MfParams &P, Sh &sh, int u, const DisCtx &d
                         cincl += tc;
                     }
                 }
-                const long long excl = incl - a;
-                const int cexcl = cincl - (a > 0 ? 1 : 0);
-                long long give = 0;
-                if (a > 0 && excl < rem && cyc + k + cexcl < P.kernel_cycles) give = a < rem - excl ? a : rem - excl;
-                if (give > 0) move_flow<PULL>(P, sh, x, y, z, give, dc);
-                const long long tot = warp_sum_ll(give);
-                const int kk = __popc(__ballot_sync(0xffffffffu, give > 0));
+                long long off = incl - tsum;
+                int coff = cincl - tcnt;
+                long long mine = 0;
+                int mk = 0;
+                if (tcnt > 0 && off < rem && cyc + k + coff < P.kernel_cycles) {
+#pragma unroll
+                    for (int r = 0; r < kSeg; ++r) {
+                        if (a[r] <= 0) continue;
+                        if (off < rem && cyc + k + coff < P.kernel_cycles) {
+                            const long long g = a[r] < rem - off ? a[r] : rem - off;
+                            const int x = r0 + js + r;
+                            move_flow<PULL>(P, sh, x, ldg_cg(P.g.rev + x), ldg_cg(P.g.dst + x), g, dc);
+                            mine += g;
+                            ++mk;
+                        }
+                        off += a[r];
+                        ++coff;
+                    }
+                }
+                const long long tot = warp_sum_ll(mine);
+                const int kk = (int)warp_sum_ll((long long)mk);
                 rem -= tot;
                 sent += tot;
                 k += kk;
@@ -1453,31 +1483,50 @@ __device__ bool discharge_cta(const MfParams &P, Sh &sh, int u, const DisCtx &dc
             go = nh < n && cyc < P.kernel_cycles;
         }
         if (go) {
-            // Alg. 2's next cycles, fused (as in discharge_warp), blockDim slots
-            // per step with a CTA prefix sum over the amounts.
+            // Alg. 2's next cycles, fused (as in discharge_warp): a step covers
+            // seg * blockDim slots, every thread seg contiguous ones, so slot
+            // order is thread order and one CTA prefix sum over the threads'
+            // totals orders all the amounts of the step.  The first step takes
+            // one slot per thread (the excess often runs out there), later
+            // ones kSeg.
+            constexpr int kSeg = 8;
             const int j0 = (int)(b & 0xffffffffu);
             long long rem = eu;
             int k = 0;
             long long sent = 0;
-            for (int jb = j0 - j0 % (int)blockDim.x; jb < d && rem > 0 && cyc + k < P.kernel_cycles;
-                 jb += blockDim.x) {
-                const int j = jb + threadIdx.x;
-                int x = 0, y = 0, z = 0;
-                long long a = 0;
-                if (j >= j0 && j < d) {
-                    x = r0 + j;
-                    if (residual_dir<PULL>(P, x) > 0) {
-                        z = ldg_cg(P.g.dst + x);
-                        if (ldg_cg(P.h + z) == best_h) {
-                            y = ldg_cg(P.g.rev + x);
-                            const int c = movable<PULL>(P, x, y);
-                            a = c > 0 ? c : 0;
-                        }
+            int seg = 1;
+            for (int jb = j0; jb < d && rem > 0 && cyc + k < P.kernel_cycles; jb += seg * (int)blockDim.x, seg = kSeg) {
+                const int js = jb + (int)threadIdx.x * seg;
+                int a[kSeg];
+                long long tsum = 0;
+                int tcnt = 0;
+#pragma unroll
+                for (int r = 0; r < kSeg; ++r) {
+                    a[r] = 0;
+                    const int j = js + r;
+                    if (r < seg && j < d && residual_dir<PULL>(P, r0 + j) > 0) a[r] = 1;   // candidate
+                }
+#pragma unroll
+                for (int r = 0; r < kSeg; ++r) {
+                    if (a[r]) {
+                        const int x = r0 + js + r;
+                        const int z = ldg_cg(P.g.dst + x);
+                        a[r] = ldg_cg(P.h + z) == best_h ? 1 : 0;
                     }
                 }
-                if (threadIdx.x == 0) atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)blockDim.x);
-                long long incl = a;
-                int cincl = a > 0 ? 1 : 0;
+#pragma unroll
+                for (int r = 0; r < kSeg; ++r) {
+                    if (a[r]) {
+                        const int x = r0 + js + r;
+                        const int c = movable<PULL>(P, x, ldg_cg(P.g.rev + x));
+                        a[r] = c > 0 ? c : 0;
+                        tsum += a[r];
+                        tcnt += a[r] > 0 ? 1 : 0;
+                    }
+                }
+                if (threadIdx.x == 0) atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)(seg * blockDim.x));
+                long long incl = tsum;
+                int cincl = tcnt;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
                     const long long t = __shfl_up_sync(0xffffffffu, incl, o);
@@ -1492,19 +1541,31 @@ __device__ bool discharge_cta(const MfParams &P, Sh &sh, int u, const DisCtx &dc
                     sh.wcnt[wid] = cincl;
                 }
                 __syncthreads();
-                long long woff = 0;
-                int wcoff = 0;
+                long long off = incl - tsum;
+                int coff = cincl - tcnt;
                 for (int w = 0; w < wid; ++w) {
-                    woff += sh.wsum[w];
-                    wcoff += sh.wcnt[w];
+                    off += sh.wsum[w];
+                    coff += sh.wcnt[w];
                 }
-                const long long excl = woff + incl - a;
-                const int cexcl = wcoff + cincl - (a > 0 ? 1 : 0);
-                long long give = 0;
-                if (a > 0 && excl < rem && cyc + k + cexcl < P.kernel_cycles) give = a < rem - excl ? a : rem - excl;
-                if (give > 0) move_flow<PULL>(P, sh, x, y, z, give, dc);
-                const long long wt = warp_sum_ll(give);
-                const int wk = __popc(__ballot_sync(0xffffffffu, give > 0));
+                long long mine = 0;
+                int mk = 0;
+                if (tcnt > 0 && off < rem && cyc + k + coff < P.kernel_cycles) {
+#pragma unroll
+                    for (int r = 0; r < kSeg; ++r) {
+                        if (a[r] <= 0) continue;
+                        if (off < rem && cyc + k + coff < P.kernel_cycles) {
+                            const long long g = a[r] < rem - off ? a[r] : rem - off;
+                            const int x = r0 + js + r;
+                            move_flow<PULL>(P, sh, x, ldg_cg(P.g.rev + x), ldg_cg(P.g.dst + x), g, dc);
+                            mine += g;
+                            ++mk;
+                        }
+                        off += a[r];
+                        ++coff;
+                    }
+                }
+                const long long wt = warp_sum_ll(mine);
+                const int wk = (int)warp_sum_ll((long long)mk);
                 __syncthreads();               // every warp has read the prefix words
                 if (lane == 0) {
                     sh.wsum[wid] = wt;
