@@ -103,6 +103,7 @@ __device__ __forceinline__ int warp_grab(unsigned *head, int cnt, unsigned k)
 struct Sh {
     long long sink_e, src_e;
     long long pushes, relabels, steep, slots, verts, cycles;
+    long long lab_slots, lab_cnt;     // BFS: slots and number of the vertices labelled this level
     unsigned long long red[MF_WARPS];
     long long wsum[MF_WARPS];
     int wcnt[MF_WARPS];
@@ -407,8 +408,14 @@ __device__ void flush_acc(const MfParams &P, Sh &sh, int phase)
                 atomic_add_ll(&c->n_apply, sh.verts);
             }
         }
+        if (sh.lab_cnt) {
+            unsigned long long *acc = (unsigned long long *)c->bfs_acc.w;
+            atomicAdd(acc + 0, (unsigned long long)sh.lab_slots);
+            atomicAdd(acc + 1, (unsigned long long)sh.lab_cnt);
+        }
         sh.sink_e = sh.src_e = 0;
         sh.pushes = sh.relabels = sh.steep = sh.slots = sh.verts = sh.cycles = 0;
+        sh.lab_slots = sh.lab_cnt = 0;
     }
     __syncthreads();
 }
@@ -815,7 +822,7 @@ __device__ __forceinline__ void warp_append(unsigned *tail, int *arr, bool take,
 // atomics, so a warp pays one append round trip per R slots.  Called by the
 // whole warp.
 template <int R>
-__device__ __forceinline__ void frontier_push(const MfParams &P, const bool (&take)[R], const int (&z)[R],
+__device__ __forceinline__ void frontier_push(const MfParams &P, Sh &sh, const bool (&take)[R], const int (&z)[R],
                                               const int (&d)[R], const long long (&ev)[R], bool with_wl, int sel)
 {
     MfCtrl *ctl = P.ctrl;
@@ -849,10 +856,9 @@ __device__ __forceinline__ void frontier_push(const MfParams &P, const bool (&ta
     // slots and number of the vertices labelled (the BFS direction test reads them)
     lab_slots = warp_sum_ll(lab_slots);
     const long long lab_cnt = warp_sum_ll((long long)lab_n);
-    if (lane == 0 && lab_cnt) {
-        unsigned long long *acc = (unsigned long long *)ctl->bfs_acc.w;
-        atomicAdd(acc + 0, (unsigned long long)lab_slots);
-        atomicAdd(acc + 1, (unsigned long long)lab_cnt);
+    if (lane == 0 && lab_cnt) {      // per CTA in shared memory, flushed with the phase's counters
+        atomicAdd((unsigned long long *)&sh.lab_slots, (unsigned long long)lab_slots);
+        atomicAdd((unsigned long long *)&sh.lab_cnt, (unsigned long long)lab_cnt);
     }
     if (total != 0) {
         unsigned base[4] = {0, 0, 0, 0};
@@ -931,7 +937,7 @@ __device__ __noinline__ void phase_bfs_init(const MfParams &P, Sh &sh)
             if (root[0]) dv[0] = need_total ? dall : ldg_cg(P.g.deg + v);
         }
         total += dall;
-        if (__any_sync(0xffffffffu, root[0])) frontier_push<1>(P, root, zv, dv, ev, false, 0);
+        if (__any_sync(0xffffffffu, root[0])) frontier_push<1>(P, sh, root, zv, dv, ev, false, 0);
     }
     if (need_total) {
         // one atomic per CTA for the used-slot total
@@ -953,7 +959,7 @@ __device__ __noinline__ void phase_bfs_init(const MfParams &P, Sh &sh)
 // claims, degree/excess loads) is issued for all BR slots together, so each
 // lane keeps BR independent requests in flight.
 template <int BR>
-__device__ __forceinline__ void bfs_visit(const MfParams &P, const int (&x)[BR], const bool (&valid)[BR], int L,
+__device__ __forceinline__ void bfs_visit(const MfParams &P, Sh &sh, const int (&x)[BR], const bool (&valid)[BR], int L,
                                           int sel)
 {
     const bool with_wl = P.data_driven && !(P.mode & MF_M_BFS_ONLY);
@@ -979,7 +985,7 @@ __device__ __forceinline__ void bfs_visit(const MfParams &P, const int (&x)[BR],
         const bool term = z[r] == P.sink || z[r] == P.source;
         ev[r] = (with_wl && claim[r] && !term) ? (pull ? -ldg_cg(P.e + z[r]) : ldg_cg(P.e + z[r])) : 0;
     }
-    frontier_push<BR>(P, claim, z, d, ev, with_wl, sel);
+    frontier_push<BR>(P, sh, claim, z, d, ev, with_wl, sel);
 }
 
 constexpr int kBR = 4;
@@ -1007,7 +1013,7 @@ __device__ __noinline__ void phase_bfs_level(const MfParams &P, Sh &sh)
                 vs[r] = k < it.y;
                 xs[r] = it.x + k;
             }
-            bfs_visit<kBR>(P, xs, vs, L, sel);
+            bfs_visit<kBR>(P, sh, xs, vs, L, sel);
         }
     }
     // regular frontier: warps take 32 vertices at a time and expand their
@@ -1047,7 +1053,7 @@ __device__ __noinline__ void phase_bfs_level(const MfParams &P, Sh &sh)
                 vs[r] = k < T;
                 xs[r] = rb + (k - eb);
             }
-            bfs_visit<kBR>(P, xs, vs, L, sel);
+            bfs_visit<kBR>(P, sh, xs, vs, L, sel);
         }
     }
     if (slots) atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)slots);
@@ -1102,7 +1108,7 @@ __device__ __noinline__ void phase_bfs_bottom_up(const MfParams &P, Sh &sh)
                 if (with_wl && v != P.sink && v != P.source) ev[0] = pull ? -ldg_cg(P.e + v) : ldg_cg(P.e + v);
             }
         }
-        if (__any_sync(0xffffffffu, take[0])) frontier_push<1>(P, take, zv, dv, ev, with_wl, sel);
+        if (__any_sync(0xffffffffu, take[0])) frontier_push<1>(P, sh, take, zv, dv, ev, with_wl, sel);
     }
     if (slots) atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)slots);
 }
@@ -1768,6 +1774,7 @@ __device__ __noinline__ bool solve_instance(const MfParams &P, Sh &sh)
         sh.gen = ld_acquire(&P.ctrl->bar_gen.w[0]);   // nobody can pass the first barrier before all have read it
         sh.sink_e = sh.src_e = 0;
         sh.pushes = sh.relabels = sh.steep = sh.slots = sh.verts = sh.cycles = 0;
+        sh.lab_slots = sh.lab_cnt = 0;
     }
     if (!grid_sync(P, H_START, sh)) return false;
 
@@ -1829,6 +1836,7 @@ __device__ __noinline__ bool solve_instance(const MfParams &P, Sh &sh)
     for (;;) {
         // backward BFS
         phase_bfs_init(P, sh);
+        flush_acc(P, sh, 0);               // the roots' label counters feed the first level's direction
         if (!grid_sync(P, H_BFS_START, sh)) return false;
         while (!vrd(&P.ctrl->bfs_done)) {
             if (vrd(&P.ctrl->bu_mode)) phase_bfs_bottom_up(P, sh);
