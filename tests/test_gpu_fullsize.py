@@ -85,3 +85,22 @@ def test_grid2048_certificate_and_flow():
     u, vv, cap, f = S.get_flow()
     flow_invariants(g.n, g.s, g.t, u, vv, cap, f, v)
     S.close()
+
+
+def test_rmat20_push_pull_and_pull_only(rmat20):
+    # the push-pull update and the pull-only static solve at full size, against Dinic
+    g = rmat20
+    S = native.Solver(g.n, g.src, g.dst, g.cap, g.s, g.t)
+    es = W.EdgeSet(g.n, g.src, g.dst, g.cap)
+    rng = np.random.default_rng(78)
+    for B in (10000, 100000):
+        b = W.mixed_batch(es, B, rng, ins_cap_hi=1000, st_bias=(g.s, g.t, 0.3))
+        es.apply(b.u, b.v, b.cap)
+        S.update_pp(b.u, b.v, b.cap)
+        want = oracle.maxflow(g.n, *es.coo(), g.s, g.t).value
+        assert S.query()[0] == want
+        _cert(S, want)
+    S.resolve_static_pull()
+    assert S.query()[0] == want
+    _cert(S, want)
+    S.close()

@@ -154,3 +154,39 @@ def test_push_pull_after_an_unsolved_state_falls_back_to_update():
     assert ei.value.code == native.ERR_INVALID
     assert S.query()[0] == oracle.maxflow(g.n, *es.coo(), g.s, g.t).value   # unchanged by the refusals
     S.close()
+
+
+def _tiny(n, edges, s, t):
+    src = np.array([e[0] for e in edges], np.int32)
+    dst = np.array([e[1] for e in edges], np.int32)
+    cap = np.array([e[2] for e in edges], np.int32)
+    return src, dst, cap
+
+
+@pytest.mark.parametrize("case", ["no_path", "direct_st", "isolated", "chain"])
+def test_push_pull_degenerate_graphs(case):
+    if case == "no_path":                    # s reaches nothing that reaches t: value 0
+        n, edges = 6, [(0, 1, 5), (1, 2, 5), (3, 5, 7), (4, 3, 2)]
+    elif case == "direct_st":                # the only path is the edge s -> t
+        n, edges = 4, [(0, 3, 9), (1, 2, 4)]
+    elif case == "isolated":                 # s and t without edges
+        n, edges = 5, [(1, 2, 3), (2, 3, 3)]
+    else:                                    # a path whose middle edge is the cut
+        n, edges = 5, [(0, 1, 10), (1, 2, 3), (2, 3, 10), (3, 4, 10)]
+    s, t = 0, n - 1
+    src, dst, cap = _tiny(n, edges, s, t)
+    want = oracle.maxflow(n, src, dst, cap, s, t).value
+    S = native.Solver(n, src, dst, cap, s, t)
+    for fn in ("resolve_static_pull", "resolve_static_pp"):
+        getattr(S, fn)()
+        assert S.query()[0] == want, fn
+    # an empty batch, then a batch that opens (or closes) a path, both by push-pull
+    z = np.zeros(0, np.int32)
+    S.update_pp(z, z, z)
+    assert S.query()[0] == want
+    es = W.EdgeSet(n, src, dst, cap)
+    bu, bv, bc = np.array([s, 1], np.int32), np.array([1, t], np.int32), np.array([4, 6], np.int32)
+    es.apply(bu, bv, bc)
+    S.update_pp(bu, bv, bc)
+    assert S.query()[0] == oracle.maxflow(n, *es.coo(), s, t).value
+    S.close()
