@@ -199,19 +199,20 @@ class Server:
         self.stats.restores += 1
         self.stats.moves.append(("restore", i, self.bytes[i], ms, self._busy))
 
-    def _make_room(self, need, keep, stream, sizes=None) -> bool:
+    def _make_room(self, need, keep, stream, sizes=None, spare=()) -> bool:
         """Evict LRU states outside `keep` until `need` more bytes fit the budget
-        (and, with the arena, allocations of `sizes` would all be placed)."""
+        (and, with the arena, allocations of `sizes` would all be placed).  States
+        in `spare` (graphs with waiting requests) go last."""
         while not self._fits(need, sizes):
             victims = [j for j in range(len(self.solvers)) if self.resident(j) and j not in keep]
             if not victims:
                 return False
-            self._evict(min(victims, key=lambda j: self.last_use[j]), stream)
+            self._evict(min(victims, key=lambda j: (j in spare, self.last_use[j])), stream)
         return True
 
     # -- one tick --------------------------------------------------------------
 
-    def _admit(self, heads, busy):
+    def _admit(self, heads, busy, waiting=()):
         """Pick this tick's requests: oldest first, restoring evicted graphs as memory allows.
 
         busy: graphs of the launch still running (never evicted).  Each chosen
@@ -225,13 +226,13 @@ class Server:
             i = r.graph
             keep = set(busy) | {r2.graph for r2 in chosen} | {i}
             if not self.resident(i):
-                if not self._make_room(self.bytes[i], keep, self.copy, self._sizes(i)):
+                if not self._make_room(self.bytes[i], keep, self.copy, self._sizes(i), spare=waiting):
                     continue                      # waits for memory; younger resident requests may still go
                 self._restore(i, self.copy)
             S = self.solvers[i]
             S.reserve_batch(r.size)
             self.bytes[i] = S.device_bytes()
-            if not self._make_room(0, keep, self.copy):
+            if not self._make_room(0, keep, self.copy, spare=waiting):
                 self._evict(i, self.copy)         # does not fit beside this tick's others: wait
                 continue
             chosen.append(r)
@@ -269,15 +270,19 @@ class Server:
             nxt = None
             if heads and (running is None or self.overlap):
                 # with a launch running, only prepare: restore what the next tick will need
+                waiting = {i for i, q in enumerate(queues) if q}
                 if running is None:
-                    nxt = self._admit(heads, busy)
+                    nxt = self._admit(heads, busy, waiting)
                 else:
+                    # restore, in arrival order, every waiting graph that fits
+                    # without evicting another graph with waiting requests
                     for r in sorted(heads, key=lambda r: r.arrival):
-                        if not self.resident(r.graph) and \
-                                self._make_room(self.bytes[r.graph], busy | {r.graph}, self.copy,
-                                                self._sizes(r.graph)):
-                            self._restore(r.graph, self.copy)
-                        break
+                        if self.resident(r.graph):
+                            continue
+                        if not self._make_room(self.bytes[r.graph], busy | waiting, self.copy,
+                                               self._sizes(r.graph)):
+                            break
+                        self._restore(r.graph, self.copy)
             if running is not None:
                 th, out, ch = running
                 th.join()
