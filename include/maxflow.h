@@ -172,7 +172,7 @@ int maxflow_set_kernel_cycles(maxflow_ctx *c, int32_t k);
  * round runs (they receive flow) are discharged in the next round, up to r
  * rounds, before the next BFS -- as in the paper's kernel, where every vertex
  * checks e(u) > 0 on each of its cycles.  0 (the default) is adaptive, not in
- * the paper: at least 4 rounds, then more while the discharge of the current
+ * the paper: at least 2 rounds, then more while the discharge of the current
  * iteration has taken less than half the time of its BFS, at most 1024, so
  * that a global relabel that costs much (a deep BFS, as on grids) is spread
  * over more discharge work.  MAXFLOW_ERR_INVALID below 0. */

@@ -831,7 +831,7 @@ struct SchedAction {
 };
 
 // Index 16 is the paper's fixed schedule (one round, KERNEL_CYCLES = average
-// degree) and 17 the library's default (MF_DEFAULT_ROUNDS rounds).
+// degree) and 17 the library's default (adaptive rounds).
 const SchedAction kActions[] = {
     {0, 1, 1}, {0, 1, 4}, {0, 1, 16}, {0, 1, 64},
     {0, 4, 1}, {0, 4, 4}, {0, 4, 16}, {0, 4, 64},

@@ -23,7 +23,7 @@
 #define MF_BFS_HUB 256        // BFS: rows above this many slots enter the frontier as work items
 #define MF_BFS_CHUNK 256      // BFS: slots per work item
 #define MF_ACTIVE_HIST 64
-#define MF_DEFAULT_ROUNDS 4   // discharge rounds between global relabels: fixed count, or the adaptive minimum
+#define MF_DEFAULT_ROUNDS 2   // adaptive discharge rounds: the minimum per iteration
 #define MF_MAX_ROUNDS 1024    // adaptive rounds: upper bound per iteration
 #define MF_TRACE 256          // hook timeline entries kept per launch
 #define MF_BU_ALPHA 14        // BFS default: go bottom-up when the frontier's slots exceed the unexplored slots / alpha

@@ -455,7 +455,7 @@ def test_kernel_cycles_do_not_change_the_value(k):
 
 @pytest.mark.parametrize("rounds,k", [(0, 0), (0, 1), (4, 1), (32, 4), (256, 16)])
 def test_discharge_rounds_do_not_change_the_value(rounds, k):
-    # rounds 0: the adaptive count (at least 4, more while the discharge is cheap against its BFS)
+    # rounds 0: the adaptive count (at least 2, more while the discharge is cheap against its BFS)
     g = W.erdos_renyi(3000, 18000, seed=151, cap_hi=100)
     rng = np.random.default_rng(152)
     S = native.Solver(g.n, g.src, g.dst, g.cap, g.s, g.t)
