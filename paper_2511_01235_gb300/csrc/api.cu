@@ -243,7 +243,7 @@ int upload_graph(maxflow_ctx *c, const MfHostGraph &hg)
     MF_TRY(rc_cuda(cudaMemcpyAsync(c->g.cf, hg.cf, sizeof(int32_t) * S, cudaMemcpyHostToDevice, st)));
     MF_TRY(rc_cuda(cudaMemcpyAsync(c->g.cap, hg.cap, sizeof(int32_t) * S, cudaMemcpyHostToDevice, st)));
     MF_TRY(rc_cuda(cudaMemcpyAsync(c->g.rev, hg.rev, sizeof(int32_t) * S, cudaMemcpyHostToDevice, st)));
-    MF_TRY(rc_cuda(cudaMemcpyAsync(c->g.pcap, hg.pcap, sizeof(int32_t) * S, cudaMemcpyHostToDevice, st)));
+    if (hg.pcap) MF_TRY(rc_cuda(cudaMemcpyAsync(c->g.pcap, hg.pcap, sizeof(int32_t) * S, cudaMemcpyHostToDevice, st)));
     // the host arrays must stay valid until the copies complete
     MF_TRY(rc_cuda(cudaStreamSynchronize(st)));
     dfree(c, c->sc.bitem);
@@ -1201,7 +1201,7 @@ static ParkView park_view(char *base, int32_t n, int64_t S)
     v.g.cap = (int32_t *)take(sizeof(int32_t) * (size_t)S);
     v.g.cf = (int32_t *)take(sizeof(int32_t) * (size_t)S);
     v.g.rev = (int32_t *)take(sizeof(int32_t) * (size_t)S);
-    v.g.pcap = (int32_t *)take(sizeof(int32_t) * (size_t)S);
+    v.g.pcap = nullptr;                   // rebuilt from cap and rev on restore
     v.h = (int32_t *)take(sizeof(int32_t) * (size_t)n);
     v.e = (long long *)take(sizeof(long long) * (size_t)n);
     v.bytes = o;
@@ -1248,7 +1248,6 @@ int maxflow_evict(maxflow_ctx *c)
                       {v.g.cap, c->g.cap, sizeof(int32_t) * (size_t)S},
                       {v.g.cf, c->g.cf, sizeof(int32_t) * (size_t)S},
                       {v.g.rev, c->g.rev, sizeof(int32_t) * (size_t)S},
-                      {v.g.pcap, c->g.pcap, sizeof(int32_t) * (size_t)S},
                       {v.h, c->g.h, sizeof(int32_t) * (size_t)n},
                       {v.e, c->g.e, sizeof(long long) * (size_t)n}};
     for (const Cp &cp : cps) MF_TRY(rc_cuda(cudaMemcpyAsync(cp.h, cp.d, cp.b, cudaMemcpyDeviceToHost, c->stream)));
@@ -1281,6 +1280,7 @@ int maxflow_restore(maxflow_ctx *c)
         c->sched_y = dalloc_n<float>(c, 64);
         if (!c->g.h || !c->g.e || !c->ctrl || !c->dbuf || !c->feat || !c->sched_y) rc = MAXFLOW_ERR_OOM;
     }
+    if (rc == MAXFLOW_OK) rc = mf_launch_aux(MF_AUX_PCAP, base_params(c), (void *)c->stream, nullptr, nullptr);
     if (rc == MAXFLOW_OK) rc = alloc_vertex_scratch(c);
     if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMemsetAsync(c->ctrl, 0, sizeof(MfCtrl), c->stream));
     if (rc == MAXFLOW_OK)

@@ -203,6 +203,7 @@ int mf_launch_aux(int which, const MfParams &p, void *stream, long long *dev_out
 #define MF_AUX_CLEAR_SCRATCH 8    // reset hash tables and ins_need
 #define MF_AUX_DUMP 9             // extra = int32_t* rowid per slot (u of each slot index)
 #define MF_AUX_NEGATE_E 10        // e = -e
+#define MF_AUX_PCAP 11            // pcap = cap + cap[rev] on every used slot (after a restore)
 
 // device-side rebuild (rows grow, flows and excesses stay in place)
 int mf_rebuild_capacity(const MfParams &p, void *stream, float slack_factor, int slack_min, long long *noff);

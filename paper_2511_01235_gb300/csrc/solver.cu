@@ -2062,6 +2062,21 @@ __global__ void k_reverse_cf(MfParams P, const int32_t *in, int32_t *out)
         out[x] = in[P.g.rev[x]];
 }
 
+// pcap = c(u, v) + c(v, u) on every used slot, from cap and rev (the pair sum
+// a parked state does not keep).  One warp per row.
+__global__ void k_pcap(MfParams P)
+{
+    const int lane = threadIdx.x & 31;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long u = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < P.g.n; u += nw) {
+        const int r0 = P.g.off[u], d = P.g.deg[u];
+        for (int j = lane; j < d; j += 32) {
+            const int x = r0 + j;
+            P.g.pcap[x] = P.g.cap[x] + P.g.cap[P.g.rev[x]];
+        }
+    }
+}
+
 __global__ void k_rowid(MfParams P, int32_t *rowid)
 {
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < P.g.n;
@@ -2252,6 +2267,11 @@ int mf_launch_aux(int which, const MfParams &p, void *stream, long long *dev_out
     case MF_AUX_NEGATE_E:
         k_negate<<<gv, B, 0, st>>>(p.e, p.g.n);
         break;
+    case MF_AUX_PCAP: {
+        long long g = (nv * 32 + B - 1) / B;
+        k_pcap<<<(int)(g > 65535 ? 65535 : (g < 1 ? 1 : g)), B, 0, st>>>(p);
+        break;
+    }
     default:
         return MAXFLOW_ERR_INVALID;
     }
