@@ -232,6 +232,15 @@ int maxflow_update_scheduled(maxflow_ctx *c, const maxflow_batch *b, maxflow_mlp
  * bfs_item_min_slots into 256-slot work items.  Defaults 8 / 512 / 256. */
 int maxflow_set_tuning(maxflow_ctx *c, int32_t thread_max_slots, int32_t warp_max_slots, int32_t bfs_item_min_slots);
 
+/* Test of the bounded waits (no counterpart in the paper): one BFS-only launch
+ * in which CTA `cta` (0 <= cta < the context's grid) never arrives at its
+ * first grid barrier.  The other CTAs give up after maxflow_opts.wait_limit_s,
+ * record the wait error and leave the kernel, so the call returns
+ * MAXFLOW_ERR_INTERNAL instead of hanging; the barrier words are reset and the
+ * context stays usable (heights may be stale until the next solve).
+ * MAXFLOW_ERR_INVALID for cta out of range. */
+int maxflow_test_stalled_barrier(maxflow_ctx *c, int32_t cta);
+
 /* Direction of the global-relabel BFS levels (direction-optimising BFS, not
  * in the paper, which sweeps top-down).  A level runs bottom-up -- each
  * unlabelled vertex looks through its own row for a neighbour of the current

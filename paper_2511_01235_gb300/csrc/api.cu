@@ -161,6 +161,7 @@ MfParams base_params(maxflow_ctx *c)
     p.data_driven = c->opt.data_driven ? 1 : 0;
     p.pull = 0;
     p.side_root = -1;
+    p.test_skip_cta = -1;
     p.side = c->pp.side;
     p.max_iters = c->opt.max_iters > 0 ? c->opt.max_iters : 4LL * c->n + 1000;
     double tl = c->opt.time_limit_s > 0 ? c->opt.time_limit_s : 120.0;
@@ -971,6 +972,20 @@ int maxflow_set_tuning(maxflow_ctx *c, int32_t thread_max_slots, int32_t warp_ma
     c->hub_deg = warp_max_slots;
     c->bfs_hub = bfs_item_min_slots;
     return MAXFLOW_OK;
+}
+
+int maxflow_test_stalled_barrier(maxflow_ctx *c, int32_t cta)
+{
+    if (c && c->evicted) return MAXFLOW_ERR_STATE;
+    if (!c || cta < 0 || cta >= c->grid) return MAXFLOW_ERR_INVALID;
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return MAXFLOW_ERR_CUDA;
+    MfParams p = base_params(c);
+    p.mode = MF_M_BFS_ONLY;
+    p.test_skip_cta = cta;
+    int kerr = 0, kst = 0;
+    MF_TRY(run_kernel(c, p, &kerr, &kst));   // resets the barrier words after an error
+    return kerr == MF_E_NONE ? MAXFLOW_OK : status_to_rc(kerr, kst);
 }
 
 int maxflow_set_bfs_switch(maxflow_ctx *c, int32_t alpha, int32_t beta)

@@ -102,6 +102,7 @@ extern "C" int maxflow_global_relabel_noalloc(int32_t n, int32_t s, int32_t t, c
     p.source = s;
     p.mode = MF_M_BFS_ONLY | (deficit_roots ? 0 : MF_M_NO_DEFICIT_ROOTS);
     p.side_root = -1;
+    p.test_skip_cta = -1;
     p.kernel_cycles = 1;
     p.rounds = 1;
     p.small_deg = MF_SMALL_DEG;

@@ -1776,6 +1776,9 @@ __device__ __noinline__ bool solve_instance(const MfParams &P, Sh &sh)
         sh.pushes = sh.relabels = sh.steep = sh.slots = sh.verts = sh.cycles = 0;
         sh.lab_slots = sh.lab_cnt = 0;
     }
+    // a CTA that never arrives (tests only): the others give up after
+    // wait_limit_ns, record MF_E_WAIT and leave the kernel
+    if (P.test_skip_cta == vb()) return true;
     if (!grid_sync(P, H_START, sh)) return false;
 
     if (P.mode & MF_M_STATIC_INIT) {

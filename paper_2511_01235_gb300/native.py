@@ -94,7 +94,7 @@ EXPORTS = ["maxflow_default_opts", "maxflow_init", "maxflow_update", "maxflow_qu
            "maxflow_arena_create", "maxflow_arena_destroy", "maxflow_arena_alloc", "maxflow_arena_free",
            "maxflow_arena_stats", "maxflow_arena_fits", "maxflow_evicted_sizes",
            "maxflow_resolve_static_pp", "maxflow_resolve_static_pull", "maxflow_update_pp",
-           "maxflow_set_bfs_switch"]
+           "maxflow_set_bfs_switch", "maxflow_test_stalled_barrier"]
 
 TRACE_NAMES = ["start", "prologue", "batch_validated", "batch_located", "room_checked", "capacities_changed",
                "iteration_start", "bfs_roots", "bfs_level", "worklist", "discharge", "end"]
@@ -157,6 +157,7 @@ def load(build_if_missing: bool = False):
     L.maxflow_resolve_static_pull.argtypes = [vp]
     L.maxflow_update_pp.argtypes = [vp, P(Batch), i32]
     L.maxflow_set_bfs_switch.argtypes = [vp, i32, i32]
+    L.maxflow_test_stalled_barrier.argtypes = [vp, i32]
     L.maxflow_restore.argtypes = [vp]
     L.maxflow_solve_batched.argtypes = [vp, i32, vp, i32, P(C.c_double)]
     L.maxflow_sched_actions.argtypes = [vp, vp, vp, i32, P(i32)]

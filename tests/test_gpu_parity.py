@@ -504,3 +504,27 @@ def test_bfs_direction_switch_does_not_change_labels_or_values(alpha, beta):
     with pytest.raises(native.MaxflowError):
         S.set_bfs_switch(-1, 24)
     C.close(); R.close(); S.close()
+
+
+def test_a_stalled_barrier_times_out_and_leaves_the_context_usable():
+    # one CTA never arrives at a grid barrier: the others give up after the
+    # context's wait limit, the call reports the failure, and the context still
+    # solves correctly afterwards (no hang, no fault)
+    import time
+    g = W.erdos_renyi(3000, 20000, seed=181, cap_hi=100)
+    S = native.Solver(g.n, g.src, g.dst, g.cap, g.s, g.t, wait_limit_s=0.05)
+    L = native.load()
+    t0 = time.perf_counter()
+    rc = L.maxflow_test_stalled_barrier(S.h, 0)
+    assert rc == native.ERR_INTERNAL
+    assert time.perf_counter() - t0 < 5.0
+    assert L.maxflow_test_stalled_barrier(S.h, 1 << 20) == native.ERR_INVALID
+    es = W.EdgeSet(g.n, g.src, g.dst, g.cap)
+    rng = np.random.default_rng(182)
+    for _ in range(2):
+        b = W.mixed_batch(es, 500, rng, ins_cap_hi=100)
+        es.apply(b.u, b.v, b.cap)
+        S.update(b.u, b.v, b.cap)
+        u2, v2, c2 = es.coo()
+        check_against_oracle(S, g.n, u2, v2, c2, g.s, g.t)
+    S.close()
