@@ -48,3 +48,43 @@ def test_single_process_aggregate():
     import bench
     value, tot_ms, ws = bench.aggregate_over_ranks(50.0, 1000)
     assert ws == 1 and tot_ms == 50.0 and value == pytest.approx(20000.0)
+
+
+def _failing_worker(rank, world, port, q):
+    # rank 1 fails between steps (before the timing exchange); rank 0 must get an
+    # error from the collective within the process-group timeout, not hang
+    import datetime
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    if rank == 1:
+        q.put((rank, "left"))
+        q.close()
+        q.join_thread()                           # the message is out before the process ends
+        os._exit(3)
+    import bench
+    try:
+        bench.aggregate_over_ranks(100.0, 5000)
+        q.put((rank, "no error"))
+    except Exception as exc:                      # gloo reports the lost peer
+        q.put((rank, "error: " + type(exc).__name__))
+    q.close()
+    q.join_thread()
+    os._exit(0)
+
+
+def test_a_rank_that_leaves_is_detected_by_the_other():
+    import time
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_failing_worker, args=(r, 2, port, q)) for r in range(2)]
+    t0 = time.perf_counter()
+    for p in procs:
+        p.start()
+    out = dict(q.get(timeout=120) for _ in range(2))
+    for p in procs:
+        p.join(timeout=60)
+    assert out[1] == "left"
+    assert out[0].startswith("error"), out
+    assert time.perf_counter() - t0 < 90
+    assert procs[1].exitcode == 3 and procs[0].exitcode == 0
