@@ -406,14 +406,14 @@ const char *maxflow_strerror(int code);
  * Host arrays.  Heights are left as they are. */
 int maxflow_set_flow(maxflow_ctx *c, int64_t count, const int32_t *u, const int32_t *v, const int32_t *f);
 
-/* Alg. 5 lines 1-16 only (apply, clamp, excess, source saturation); no re-solve. */
+/* The batch part of Alg. 5 only (apply, clamp, excess, source saturation); no re-solve. */
 int maxflow_apply(maxflow_ctx *c, const maxflow_batch *b);
 
 /* Alg. 6 only: heights = residual distance to {t} and every deficient vertex,
  * h(s) = n, unreached vertices n.  Leaves flows and excesses unchanged. */
 int maxflow_global_relabel(maxflow_ctx *c);
 
-/* Resume the push-relabel loop (Alg. 5 lines 17-24) on the current state,
+/* Resume the push-relabel loop (the re-solve loop of Alg. 5) on the current state,
  * without applying anything or saturating the source. */
 int maxflow_resolve(maxflow_ctx *c);
 

@@ -267,7 +267,7 @@ class Residual:
 
     def push_pull_update(self, s, t, u, v, c, kernel_cycles):
         """The dynamic push-pull of Sec. 5.2.2 on a solved state: the sides of the
-        last cut, the batch (Alg. 5 lines 1-16), saturation across the cut, push
+        last cut, the batch (Alg. 5), saturation across the cut, push
         on T and pull on S with side-limited roots, then a final push solve (R9)."""
         side = self.cut_side()
         side[s], side[t] = 0, 1

@@ -21,10 +21,10 @@
  *      directed slot (u,v) for every pair that has an edge in either
  *      direction, with cap(u,v), c_f(u,v), and the excess e(v).
  *        - flow load and the excess definition e(v) = sum_w (c_f(v,w) - c(v,w))
- *        - Alg. 1 lines 1-14 (static initialisation and source saturation)
+ *        - Alg. 1, initialisation (static initialisation and source saturation)
  *        - Alg. 4 / Alg. 6 (backward BFS heights = residual distance to the
  *          root set), written as a plain BFS
- *        - Alg. 5 lines 1-16 (apply a batch, clamp negative residuals,
+ *        - Alg. 5, batch part (apply a batch, clamp negative residuals,
  *          recompute excess, saturate the source edges again)
  *        - Alg. 2 / Alg. 3 inside the Alg. 1 / Alg. 5 loop, run
  *          sequentially (one vertex at a time), and the value formula of
@@ -432,7 +432,7 @@ static orc_rstate *rs_from_edges(int32_t n, int64_t m, const int32_t *mu, const 
 }
 
 /* The excess definition: e(x) = sum over slots (x, w) of c_f(x, w) - c(x, w),
- * the net flow into x ("calculate excess for each vertex", Alg. 5 line 10). */
+ * the net flow into x ("calculate excess for each vertex", the excess step of Alg. 5). */
 void orc_rs_recompute_excess(orc_rstate *r)
 {
     int32_t x;
@@ -483,7 +483,7 @@ int orc_rs_set_flow(orc_rstate *r, int64_t k, const int32_t *u, const int32_t *v
     return ORC_OK;
 }
 
-/* Alg. 1 lines 1-14: e = 0, h = 0, c_f = c, then saturate every edge out of s:
+/* Alg. 1, initialisation: e = 0, h = 0, c_f = c, then saturate every edge out of s:
  * c_f(s,u) = 0, c_f(u,s) = c_us + c_su, e(u) = c_su, e(s) -= c_su. */
 void orc_rs_static_init(orc_rstate *r, int32_t s)
 {
@@ -531,7 +531,7 @@ void orc_rs_heights(orc_rstate *r, int32_t s, int32_t t, int deficit_roots, int3
     if (h_out) memcpy(h_out, r->h, sizeof(int32_t) * (size_t)n);
 }
 
-/* Alg. 5 lines 1-16 with readings R2 and R7.
+/* Alg. 5, batch part, with readings R2 and R7.
  * Returns ORC_ERR_INVALID without changing the state if any update names a
  * vertex out of range or a negative capacity. */
 int orc_rs_apply(orc_rstate **pr, int32_t s, int64_t B, const int32_t *bu, const int32_t *bv, const int32_t *bc)
@@ -584,23 +584,23 @@ int orc_rs_apply(orc_rstate **pr, int32_t s, int64_t B, const int32_t *bu, const
         *pr = r;
     }
 
-    /* line 2: c_f(u, v) += c'_uv - c_uv */
+    /* capacity step: c_f(u, v) += c'_uv - c_uv */
     for (i = 0; i < k; i++) {
         int64_t a = rs_find(r, U[i].u, U[i].v);
         r->cf[a] += U[i].c - r->cap[a];
         r->cap[a] = U[i].c;
     }
     free(U);
-    /* lines 4-9: send back the flow that no longer fits */
+    /* clamp step: send back the flow that no longer fits */
     for (i = 0; i < r->K; i++) {
         if (r->cf[i] < 0) {
             r->cf[r->rev[i]] += r->cf[i];
             r->cf[i] = 0;
         }
     }
-    /* line 10: excess from its definition */
+    /* excess step: excess from its definition */
     orc_rs_recompute_excess(r);
-    /* lines 11-16 (R2): saturate every edge out of s again */
+    /* source step (R2): saturate every edge out of s again */
     for (i = r->row[s]; i < r->row[s + 1]; i++) {
         int64_t d = r->cf[i];
         if (d > 0) {

@@ -1360,7 +1360,7 @@ int maxflow_update_pp(maxflow_ctx *c, const maxflow_batch *b, int32_t stop_after
     if (!dg.ok) return MAXFLOW_ERR_CUDA;
     if (!c->solved) return do_batch(c, b, MF_M_APPLY | MF_M_SOLVE);   // no cut to start from
     MF_TRY(ensure_pp(c));
-    // 1: the batch (Alg. 5 lines 1-16), the sides of the last cut, saturation across it
+    // 1: the batch (Alg. 5), the sides of the last cut, saturation across it
     int rc = do_batch(c, b, MF_M_APPLY | MF_M_CUT);
     double ms = c->acc_ms;
     if (rc != MAXFLOW_OK || stop_after == 1) {

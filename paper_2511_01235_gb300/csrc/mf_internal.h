@@ -43,8 +43,8 @@
 #define MF_E_INTERNAL 4
 
 // Kernel modes (bit mask)
-#define MF_M_STATIC_INIT 1    // c_f = cap, e = 0, h = 0, saturate the source (Alg. 1 lines 1-14)
-#define MF_M_APPLY 2          // Alg. 5 lines 1-16
+#define MF_M_STATIC_INIT 1    // c_f = cap, e = 0, h = 0, saturate the source (Alg. 1)
+#define MF_M_APPLY 2          // the batch part of Alg. 5
 #define MF_M_SOLVE 4          // the push-relabel loop
 #define MF_M_BFS_ONLY 8       // one backward BFS, then stop
 #define MF_M_NO_DEFICIT_ROOTS 16  // BFS roots: the sink only (flow extraction runs)

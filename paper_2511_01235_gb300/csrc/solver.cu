@@ -1,7 +1,7 @@
 // Device code of the GB300 dynamic max-flow library (sm_103a).
 //
 // One cooperative, persistent kernel runs a whole solve: the optional static
-// initialisation (Alg. 1 lines 1-14) or batch repair (Alg. 5 lines 1-16),
+// initialisation (Alg. 1) or batch repair (Alg. 5),
 // then the loop { backward BFS (Alg. 4 / Alg. 6) ; active-vertex worklist
 // (Sec. 5.2.1 O1) ; stop if empty ; push-relabel discharge (Alg. 2) ;
 // remove-invalid-edges (Alg. 3) }, then the value formula of Alg. 5.  Phases
@@ -432,7 +432,7 @@ __device__ __forceinline__ void add_excess(const MfParams &P, Sh &sh, int z, lon
 }
 
 // ---------------------------------------------------------------------------
-// Static initialisation (Alg. 1 lines 1-14)
+// Static initialisation (Alg. 1)
 // ---------------------------------------------------------------------------
 
 __device__ __noinline__ void phase_static_reset(const MfParams &P)
@@ -533,7 +533,7 @@ __device__ __noinline__ void phase_saturate_cut(const MfParams &P, Sh &sh)
 }
 
 // ---------------------------------------------------------------------------
-// Batch apply and repair (Alg. 5 lines 1-16)
+// Batch apply and repair (Alg. 5)
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ bool batch_entry(const MfParams &P, long long i, int &u, int &v, int &c)
@@ -683,7 +683,7 @@ __device__ __noinline__ void phase_apply_insert(const MfParams &P)
     }
 }
 
-// Alg. 5 line 2: c_f(u,v) += c' - c; cap(u,v) = c'.
+// Alg. 5, capacity step: c_f(u,v) += c' - c; cap(u,v) = c'.
 __device__ __noinline__ void phase_apply_delta(const MfParams &P, Sh &sh)
 {
     MfCtrl *ctl = P.ctrl;
@@ -723,7 +723,7 @@ __device__ __noinline__ void phase_apply_delta(const MfParams &P, Sh &sh)
     if (applied) atomicAdd((unsigned long long *)&sh.verts, (unsigned long long)applied);
 }
 
-// Alg. 5 lines 4-9 on the slots whose capacity went down, with the excess
+// The clamp step of Alg. 5 on the slots whose capacity went down, with the excess
 // change of the flow sent back; then clear the hash tables for the next batch.
 __device__ __noinline__ void phase_apply_clamp(const MfParams &P, Sh &sh)
 {
@@ -771,7 +771,7 @@ __device__ __noinline__ void phase_apply_cleanup(const MfParams &P, bool keep_ne
     }
 }
 
-// Alg. 5 lines 11-16 (reading: push the remaining residual of every edge out
+// The source step of Alg. 5 (reading: push the remaining residual of every edge out
 // of the source and add it to the head's excess).
 __device__ __noinline__ void phase_resaturate(const MfParams &P, Sh &sh)
 {
@@ -1274,7 +1274,7 @@ __device__ bool discharge_thread(const MfParams &P, Sh &sh, int u, const DisCtx 
         unsigned long long best = scan_lowest<4, PULL>(P, r0, d, 0, 1);
         int best_h = best == kEmpty ? 0x7fffffff : (int)(best >> 32);
         if (best == kEmpty || hu <= best_h) {
-            // relabel (Alg. 2 lines 17-19); the next cycle would find the same
+            // relabel (the relabel step of Alg. 2); the next cycle would find the same
             // lowest slots admissible, so it continues below without a rescan
             hu = (best == kEmpty || best_h >= n - 1) ? n : best_h + 1;
             P.h[u] = hu;

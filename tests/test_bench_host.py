@@ -1,0 +1,22 @@
+"""Host-side helpers of bench.py: the code digest that decides whether the
+recorded DRAM traffic still describes the kernel."""
+import bench
+
+
+def test_code_only_ignores_comments_and_whitespace():
+    a = "int f(int x) {  // add one\n  return x + 1; /* done */\n}\n"
+    b = "/* header */\nint f(int x) {\n\treturn x + 1;\n}  // changed comment\n"
+    assert bench.code_only(a) == bench.code_only(b) == "int f(int x) { return x + 1; }"
+
+
+def test_code_only_sees_code_changes_and_keeps_literals():
+    a = 'const char *p = "a // b /* c */"; char q = \'"\'; int k = 2;'
+    assert bench.code_only(a) == a
+    assert bench.code_only(a) != bench.code_only(a.replace("k = 2", "k = 3"))
+    # a block comment separates tokens like whitespace does
+    assert bench.code_only("int/**/x;") == "int x;"
+
+
+def test_traffic_only_for_the_captured_workload():
+    assert bench.measured_traffic("rmat18", 10000) is None
+    assert bench.measured_traffic("rmat20", 1000) is None

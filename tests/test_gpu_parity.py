@@ -239,7 +239,7 @@ def test_slack_overflow_rebuild():
 
 
 # ---------------------------------------------------------------------------
-# step-level parity: heights (Alg. 4/6) and batch repair (Alg. 5 lines 1-16)
+# step-level parity: heights (Alg. 4/6) and batch repair (Alg. 5)
 # ---------------------------------------------------------------------------
 
 
