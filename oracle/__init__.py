@@ -9,8 +9,11 @@ function follows in the paper and which readings it takes).
 Parity pins (tests/test_oracle.py): brute-force min-cut enumeration on tiny
 graphs, scipy's independent max-flow, an independent Edmonds-Karp, closed
 forms, flow invariants, scipy shortest paths for the heights, hand-derived
-fixtures in tests/golden/ for the batch repair, and agreement of the
-sequential push-relabel restatement with Dinic on random graphs and batches.
+fixtures in tests/golden/ for the batch repair and for single steps of
+Alg. 2 / Alg. 3 and their pull mirrors, and agreement of the sequential
+push-relabel restatement with Dinic on random graphs and batches.
+tests/test_oracle_mutations.py plants plausible mistakes in copies of
+oracle.c (loaded through MAXFLOW_ORACLE_LIB) and checks that a pin fails.
 """
 from __future__ import annotations
 
@@ -39,12 +42,20 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def library_path() -> str:
+    """The shared library the wrappers call: liboracle.so built from oracle.c,
+    or the prebuilt file named by MAXFLOW_ORACLE_LIB (the mutation tests build
+    copies of oracle.c with one planted mistake and point this at them)."""
+    return os.environ.get("MAXFLOW_ORACLE_LIB") or _LIB
+
+
 def _load():
     global _lib
     if _lib is not None:
         return _lib
-    build()
-    L = C.CDLL(_LIB)
+    if not os.environ.get("MAXFLOW_ORACLE_LIB"):
+        build()
+    L = C.CDLL(library_path())
     i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
     i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
     u8p = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
@@ -100,6 +111,16 @@ def _load():
     L.orc_rs_cut_side.argtypes = [vp, vp]
     L.orc_rs_saturate_cut.restype = None
     L.orc_rs_saturate_cut.argtypes = [vp, vp]
+    L.orc_rs_set_heights.restype = None
+    L.orc_rs_set_heights.argtypes = [vp, i32p]
+    L.orc_rs_discharge.restype = C.c_int64
+    L.orc_rs_discharge.argtypes = [vp, C.c_int32, C.c_int32, vp]
+    L.orc_rs_remove_invalid.restype = None
+    L.orc_rs_remove_invalid.argtypes = [vp, C.c_int32, C.c_int32]
+    L.orc_rs_pull_discharge.restype = None
+    L.orc_rs_pull_discharge.argtypes = [vp, C.c_int32, C.c_int32]
+    L.orc_rs_pull_remove_invalid.restype = None
+    L.orc_rs_pull_remove_invalid.argtypes = [vp, C.c_int32, C.c_int32]
     _lib = L
     return L
 
@@ -209,6 +230,32 @@ class Residual:
         if v < 0 and v == -1:
             raise RuntimeError("sequential push-relabel did not converge")
         return int(v), int(it[0]), int(pu[0]), int(rl[0])
+
+    # ---- single steps from heights the caller sets ----
+
+    def set_heights(self, h):
+        h = _a32(h)
+        if h.shape != (self.n,) or h.min() < 0 or h.max() > self.n:
+            raise ValueError("heights must be n values in [0, n]")
+        self._L.orc_rs_set_heights(self._h, h)
+
+    def discharge(self, u, kernel_cycles):
+        """Alg. 2 on vertex u for kernel_cycles cycles; returns (pushes, relabels)."""
+        rl = np.zeros(1, np.int64)
+        pu = self._L.orc_rs_discharge(self._h, int(u), int(kernel_cycles), _ptr(rl))
+        return int(pu), int(rl[0])
+
+    def remove_invalid(self, s, t):
+        """Alg. 3 on every vertex not in {s, t}."""
+        self._L.orc_rs_remove_invalid(self._h, s, t)
+
+    def pull_discharge(self, u, kernel_cycles):
+        """The mirror of Alg. 2 for a deficient vertex u (R8)."""
+        self._L.orc_rs_pull_discharge(self._h, int(u), int(kernel_cycles))
+
+    def pull_remove_invalid(self, s, t):
+        """The mirror of Alg. 3 (R8)."""
+        self._L.orc_rs_pull_remove_invalid(self._h, s, t)
 
     # ---- Sec. 5.2.2 (O2) push and pull (readings R8, R9 in oracle.c) ----
 

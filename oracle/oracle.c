@@ -26,9 +26,10 @@
  *          root set), written as a plain BFS
  *        - Alg. 5, batch part (apply a batch, clamp negative residuals,
  *          recompute excess, saturate the source edges again)
- *        - Alg. 2 / Alg. 3 inside the Alg. 1 / Alg. 5 loop, run
- *          sequentially (one vertex at a time), and the value formula of
- *          Alg. 5.
+ *        - Alg. 2 on one vertex and Alg. 3, each callable as a single step
+ *          from heights the caller sets, and both inside the Alg. 1 /
+ *          Alg. 5 loop, run sequentially (one vertex at a time), and the
+ *          value formula of Alg. 5.
  *   5. Sec. 5.2.2 (O2) push and pull: saturating the edges into t, the pull
  *      heights (distance from s and the overflowing vertices), pull-relabel
  *      (the mirror of Alg. 2 / Alg. 3 for deficient vertices), the sides of
@@ -623,6 +624,69 @@ int64_t orc_rs_value(const orc_rstate *r, int32_t s)
     return v;
 }
 
+/* Heights given by the caller (h[v] in [0, n] for every v), for running the
+ * single steps below from a state of the test's choosing. */
+void orc_rs_set_heights(orc_rstate *r, const int32_t *h)
+{
+    memcpy(r->h, h, sizeof(int32_t) * (size_t)r->n);
+}
+
+/* Alg. 2 on one vertex u: kernel_cycles cycles; a cycle does nothing once u
+ * is inactive (h(u) >= n or e(u) <= 0).  A cycle takes the residual slot
+ * (u, v) (c_f > 0) whose head has the lowest height, the first slot in row
+ * order on ties (R6).  If h(u) is above that height, it pushes
+ * min(e(u), c_f(u, v)) along the slot; otherwise it relabels u to that
+ * height + 1, or to n when u has no residual slot or the result would
+ * exceed n - 1 (R5).  Returns the number of pushes; adds the relabels to
+ * *relabels (may be NULL). */
+int64_t orc_rs_discharge(orc_rstate *r, int32_t u, int32_t kernel_cycles, int64_t *relabels)
+{
+    int32_t n = r->n, cnt;
+    int64_t pushes = 0;
+    for (cnt = 0; cnt < kernel_cycles; cnt++) {
+        int64_t best = -1, j;
+        int32_t hbest = INT32_MAX;
+        if (!(r->h[u] < n && r->e[u] > 0)) continue;
+        for (j = r->row[u]; j < r->row[u + 1]; j++)
+            if (r->cf[j] > 0 && r->h[r->head[j]] < hbest) { best = j; hbest = r->h[r->head[j]]; }
+        if (best >= 0 && r->h[u] > hbest) {
+            int64_t d = min64(r->e[u], r->cf[best]);
+            int32_t v = r->head[best];
+            r->cf[best] -= d;
+            r->cf[r->rev[best]] += d;
+            r->e[u] -= d;
+            r->e[v] += d;
+            pushes++;
+        } else {
+            r->h[u] = (best < 0 || hbest >= n - 1) ? n : hbest + 1;
+            if (relabels) (*relabels)++;
+        }
+    }
+    return pushes;
+}
+
+/* Alg. 3 on every vertex x not in {s, t}, in increasing id order: every slot
+ * (x, v) with c_f(x, v) > 0 and h(x) > h(v) + 1 sends all of c_f(x, v) to v
+ * (e(x) falls by it, possibly below 0; e(v) rises by it). */
+void orc_rs_remove_invalid(orc_rstate *r, int32_t s, int32_t t)
+{
+    int32_t x;
+    for (x = 0; x < r->n; x++) {
+        int64_t j;
+        if (x == s || x == t) continue;
+        for (j = r->row[x]; j < r->row[x + 1]; j++) {
+            int32_t v = r->head[j];
+            if (r->cf[j] > 0 && r->h[x] > r->h[v] + 1) {
+                int64_t c = r->cf[j];
+                r->e[x] -= c;
+                r->e[v] += c;
+                r->cf[r->rev[j]] += c;
+                r->cf[j] = 0;
+            }
+        }
+    }
+}
+
 /* The method's loop run sequentially: repeat { Alg. 6 BFS; stop if no active
  * vertex; Alg. 2 on every active vertex in increasing id order; Alg. 3 on
  * every vertex not in {s,t} }.  Returns the value (R3) or -1 when max_iters
@@ -639,45 +703,8 @@ int64_t orc_rs_push_relabel(orc_rstate *r, int32_t s, int32_t t, int32_t kernel_
         for (x = 0; x < n; x++)
             if (x != s && x != t && r->e[x] > 0 && r->h[x] < n) active[nact++] = x;
         if (nact == 0) break;
-        /* Alg. 2 */
-        for (i = 0; i < nact; i++) {
-            int32_t u = active[i], cnt;
-            for (cnt = 0; cnt < kernel_cycles; cnt++) {
-                int64_t e1, best = -1, j;
-                int32_t hbest = INT32_MAX;
-                if (!(r->h[u] < n && r->e[u] > 0)) continue;
-                e1 = r->e[u];
-                for (j = r->row[u]; j < r->row[u + 1]; j++)
-                    if (r->cf[j] > 0 && r->h[r->head[j]] < hbest) { best = j; hbest = r->h[r->head[j]]; }
-                if (best >= 0 && r->h[u] > hbest) {
-                    int64_t d = min64(e1, r->cf[best]);
-                    int32_t v = r->head[best];
-                    r->cf[best] -= d;
-                    r->cf[r->rev[best]] += d;
-                    r->e[u] -= d;
-                    r->e[v] += d;
-                    pushes++;
-                } else {
-                    r->h[u] = (best < 0 || hbest >= n - 1) ? n : hbest + 1;   /* R5 */
-                    relabels++;
-                }
-            }
-        }
-        /* Alg. 3 */
-        for (x = 0; x < n; x++) {
-            int64_t j;
-            if (x == s || x == t) continue;
-            for (j = r->row[x]; j < r->row[x + 1]; j++) {
-                int32_t v = r->head[j];
-                if (r->cf[j] > 0 && r->h[x] > r->h[v] + 1) {
-                    int64_t c = r->cf[j];
-                    r->e[x] -= c;
-                    r->e[v] += c;
-                    r->cf[r->rev[j]] += c;
-                    r->cf[j] = 0;
-                }
-            }
-        }
+        for (i = 0; i < nact; i++) pushes += orc_rs_discharge(r, active[i], kernel_cycles, &relabels);
+        orc_rs_remove_invalid(r, s, t);
     }
     free(active);
     if (iters_out) *iters_out = it;
@@ -787,42 +814,61 @@ int orc_rs_push_side(orc_rstate *r, int32_t s, int32_t t, const uint8_t *side, i
         for (x = 0; x < n; x++)
             if (x != s && x != t && r->e[x] > 0 && r->h[x] < n) active[nact++] = x;
         if (nact == 0) break;
-        for (i = 0; i < nact; i++) {
-            int32_t u = active[i], cnt;
-            for (cnt = 0; cnt < kernel_cycles; cnt++) {
-                int64_t best = -1, j;
-                int32_t hbest = INT32_MAX;
-                if (!(r->h[u] < n && r->e[u] > 0)) continue;
-                for (j = r->row[u]; j < r->row[u + 1]; j++)
-                    if (r->cf[j] > 0 && r->h[r->head[j]] < hbest) { best = j; hbest = r->h[r->head[j]]; }
-                if (best >= 0 && r->h[u] > hbest) {
-                    int64_t d = min64(r->e[u], r->cf[best]);
-                    r->cf[best] -= d;
-                    r->cf[r->rev[best]] += d;
-                    r->e[u] -= d;
-                    r->e[r->head[best]] += d;
-                } else {
-                    r->h[u] = (best < 0 || hbest >= n - 1) ? n : hbest + 1;
-                }
-            }
-        }
-        for (x = 0; x < n; x++) {
-            int64_t j;
-            if (x == s || x == t) continue;
-            for (j = r->row[x]; j < r->row[x + 1]; j++) {
-                int32_t v = r->head[j];
-                if (r->cf[j] > 0 && r->h[x] > r->h[v] + 1) {
-                    int64_t c = r->cf[j];
-                    r->e[x] -= c;
-                    r->e[v] += c;
-                    r->cf[r->rev[j]] += c;
-                    r->cf[j] = 0;
-                }
-            }
-        }
+        for (i = 0; i < nact; i++) orc_rs_discharge(r, active[i], kernel_cycles, NULL);
+        orc_rs_remove_invalid(r, s, t);
     }
     free(active);
     return nact != 0 ? -1 : 0;
+}
+
+/* The mirror of Alg. 2 for one deficient vertex u (R8): kernel_cycles
+ * cycles; a cycle does nothing once h(u) >= n or e(u) >= 0.  A cycle takes
+ * the in-neighbour z with c_f(z, u) > 0 of lowest height (the first slot
+ * (u, z) in row order on ties).  If h(u) is above it, u pulls
+ * min(-e(u), c_f(z, u)) over (z, u); otherwise u is relabelled as in Alg. 2. */
+void orc_rs_pull_discharge(orc_rstate *r, int32_t u, int32_t kernel_cycles)
+{
+    int32_t n = r->n, cnt;
+    for (cnt = 0; cnt < kernel_cycles; cnt++) {
+        int64_t best = -1, j;
+        int32_t hbest = INT32_MAX;
+        if (!(r->h[u] < n && r->e[u] < 0)) continue;
+        for (j = r->row[u]; j < r->row[u + 1]; j++)      /* in-residual c_f(z, u) lives at rev[j] */
+            if (r->cf[r->rev[j]] > 0 && r->h[r->head[j]] < hbest) { best = j; hbest = r->h[r->head[j]]; }
+        if (best >= 0 && r->h[u] > hbest) {
+            int64_t in = r->rev[best];
+            int64_t d = min64(-r->e[u], r->cf[in]);
+            r->cf[in] -= d;
+            r->cf[best] += d;
+            r->e[u] += d;
+            r->e[r->head[best]] -= d;
+        } else {
+            r->h[u] = (best < 0 || hbest >= n - 1) ? n : hbest + 1;
+        }
+    }
+}
+
+/* The mirror of Alg. 3 (R8), every vertex x not in {s, t} in increasing id
+ * order: every in-neighbour z with c_f(z, x) > 0 and h(x) > h(z) + 1 gives
+ * all of c_f(z, x) to x (e(z) falls by it, e(x) rises by it). */
+void orc_rs_pull_remove_invalid(orc_rstate *r, int32_t s, int32_t t)
+{
+    int32_t x;
+    for (x = 0; x < r->n; x++) {
+        int64_t j;
+        if (x == s || x == t) continue;
+        for (j = r->row[x]; j < r->row[x + 1]; j++) {
+            int32_t z = r->head[j];
+            int64_t in = r->rev[j];
+            if (r->cf[in] > 0 && r->h[x] > r->h[z] + 1) {
+                int64_t c = r->cf[in];
+                r->e[x] += c;
+                r->e[z] -= c;
+                r->cf[j] += c;
+                r->cf[in] = 0;
+            }
+        }
+    }
 }
 
 /* Pull-relabel (R8), the mirror of Alg. 2 / Alg. 3: repeat { pull heights;
@@ -843,41 +889,8 @@ int orc_rs_pull_relabel(orc_rstate *r, int32_t s, int32_t t, const uint8_t *side
         for (x = 0; x < n; x++)
             if (x != s && x != t && r->e[x] < 0 && r->h[x] < n) active[nact++] = x;
         if (nact == 0) break;
-        for (i = 0; i < nact; i++) {
-            int32_t u = active[i], cnt;
-            for (cnt = 0; cnt < kernel_cycles; cnt++) {
-                int64_t best = -1, j;
-                int32_t hbest = INT32_MAX;
-                if (!(r->h[u] < n && r->e[u] < 0)) continue;
-                for (j = r->row[u]; j < r->row[u + 1]; j++)      /* in-residual c_f(z, u) lives at rev[j] */
-                    if (r->cf[r->rev[j]] > 0 && r->h[r->head[j]] < hbest) { best = j; hbest = r->h[r->head[j]]; }
-                if (best >= 0 && r->h[u] > hbest) {
-                    int64_t in = r->rev[best];
-                    int64_t d = min64(-r->e[u], r->cf[in]);
-                    r->cf[in] -= d;
-                    r->cf[best] += d;
-                    r->e[u] += d;
-                    r->e[r->head[best]] -= d;
-                } else {
-                    r->h[u] = (best < 0 || hbest >= n - 1) ? n : hbest + 1;
-                }
-            }
-        }
-        for (x = 0; x < n; x++) {
-            int64_t j;
-            if (x == s || x == t) continue;
-            for (j = r->row[x]; j < r->row[x + 1]; j++) {
-                int32_t z = r->head[j];
-                int64_t in = r->rev[j];
-                if (r->cf[in] > 0 && r->h[x] > r->h[z] + 1) {
-                    int64_t c = r->cf[in];
-                    r->e[x] += c;
-                    r->e[z] -= c;
-                    r->cf[j] += c;
-                    r->cf[in] = 0;
-                }
-            }
-        }
+        for (i = 0; i < nact; i++) orc_rs_pull_discharge(r, active[i], kernel_cycles);
+        orc_rs_pull_remove_invalid(r, s, t);
     }
     free(active);
     if (iters_out) *iters_out = it;

@@ -131,3 +131,22 @@ def test_push_pull_update_helper_matches_dinic_over_a_sequence():
         b = W.mixed_batch(es, 200, rng, ins_cap_hi=100) if kind == "mixed" else W.kind_batch(es, 200, rng, kind)
         es.apply(b.u, b.v, b.cap)
         assert R.push_pull_update(g.s, g.t, b.u, b.v, b.cap, 8) == oracle.maxflow(g.n, *es.coo(), g.s, g.t).value
+
+
+@pytest.mark.parametrize("gi", range(len(GRAPHS)))
+def test_cut_side_of_a_solved_state_is_a_minimum_cut(gi):
+    # R9's S / T split, pinned to Dinic: after a solve, side 0 holds s, side 1
+    # holds t, the capacity from side 0 to side 1 is the max-flow value, and
+    # side 0 lies between the smallest and the largest minimum source sides
+    g = GRAPHS[gi]
+    R = oracle.Residual(g.n, g.src, g.dst, g.cap)
+    R.static_init(g.s)
+    val, *_ = R.push_relabel(g.s, g.t, 4)
+    d = oracle.maxflow(g.n, g.src, g.dst, g.cap, g.s, g.t)
+    assert val == d.value
+    side = R.cut_side()
+    assert side[g.s] == 0 and side[g.t] == 1
+    u, v, cap, _ = R.slots()
+    assert int(cap[(side[u] == 0) & (side[v] == 1)].sum()) == d.value
+    S = side == 0
+    assert np.all(S[d.smin]) and np.all(d.smax[S])
