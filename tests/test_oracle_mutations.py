@@ -129,3 +129,58 @@ def test_a_planted_mistake_fails_a_pin(tmp_path, name, find, repl):
     lib = _build(tmp_path, text.replace(find, repl), name)
     rc, tail = _run_pins(lib)
     assert rc != 0, f"{name} survived every pin:\n{tail}"
+
+
+# The scheduler network's numpy reference (oracle/mlp_ref.py), pinned by
+# tests/test_mlp_ref.py: finite differences, torch autograd, torch's Adam.
+MLP_SRC = os.path.join(ROOT, "oracle", "mlp_ref.py")
+MLP_MUTANTS = [
+    ("forward_drops_a_bias", "a2 = h1 @ W2.T + b2", "a2 = h1 @ W2.T"),
+    ("forward_without_relu", "h1 = np.maximum(a1, 0.0)", "h1 = a1"),
+    ("loss_mean_over_all_outputs", "return float((m * d * d).sum() / m.sum())",
+     "return float((m * d * d).sum() / m.size)"),
+    ("grad_ignores_the_mask", "dy = 2.0 * m * (y - np.asarray(t, np.float64).reshape(y.shape)) / m.sum()",
+     "dy = 2.0 * (y - np.asarray(t, np.float64).reshape(y.shape)) / m.sum()"),
+    ("grad_wrong_relu_gate", "dh2 = (dy @ W3) * (a2 > 0)", "dh2 = (dy @ W3) * (a2 >= 0) * (a1 > 0)"),
+    ("grad_drops_bias_term", "gb2 = dh2.sum(0)", "gb2 = 0.0 * dh2.sum(0)"),
+    ("layout_biases_first", "for shape in ((H, n_in), (H,), (H, H), (H,), (n_out, H), (n_out,)):",
+     "for shape in ((H,), (H, n_in), (H, H), (H,), (n_out, H), (n_out,)):"),
+    ("adam_first_moment_of_squares", "m2 = b2 * m2 + (1 - b2) * g * g", "m2 = b2 * m2 + (1 - b2) * g * abs(g)"),
+    ("adam_no_bias_correction", "mh = m1 / (1 - b1 ** step)", "mh = m1"),
+    ("adam_eps_inside_sqrt", "np.sqrt(vh) + eps", "np.sqrt(vh + eps)"),
+]
+
+_MLP_DRIVER = """
+import importlib.util, sys
+import oracle
+spec = importlib.util.spec_from_file_location("oracle.mlp_ref", sys.argv[1])
+mod = importlib.util.module_from_spec(spec)
+spec.loader.exec_module(mod)
+sys.modules["oracle.mlp_ref"] = mod
+oracle.mlp_ref = mod
+import pytest
+sys.exit(pytest.main(["-x", "-q", "-p", "no:cacheprovider", "tests/test_mlp_ref.py"]))
+"""
+
+
+def _run_mlp_pins(path):
+    r = subprocess.run([sys.executable, "-c", _MLP_DRIVER, path], cwd=ROOT, capture_output=True, text=True,
+                       timeout=240)
+    return r.returncode, r.stdout[-2000:]
+
+
+def test_mlp_control_copy_passes(tmp_path):
+    f = tmp_path / "mlp_ref_control.py"
+    f.write_text(open(MLP_SRC).read())
+    rc, tail = _run_mlp_pins(str(f))
+    assert rc == 0, tail
+
+
+@pytest.mark.parametrize("name,find,repl", MLP_MUTANTS, ids=[m[0] for m in MLP_MUTANTS])
+def test_a_planted_mistake_in_the_network_reference_fails_a_pin(tmp_path, name, find, repl):
+    text = open(MLP_SRC).read()
+    assert text.count(find) == 1, f"{name}: the mutation site must occur exactly once"
+    f = tmp_path / f"mlp_ref_{name}.py"
+    f.write_text(text.replace(find, repl))
+    rc, tail = _run_mlp_pins(str(f))
+    assert rc != 0, f"{name} survived every pin:\n{tail}"
