@@ -398,6 +398,16 @@ void maxflow_destroy(maxflow_ctx *c);
 /* A static string naming a status code. */
 const char *maxflow_strerror(int code);
 
+/* Number of kernels this library has launched in the calling process, over
+ * every context, batched launch, network and no-allocation call since the
+ * library was loaded.  Read it before and after a region to count that
+ * region's launches (a solve is one cooperative launch; an update whose
+ * insertions overflow a row's slack adds the layout rebuild's four kernels
+ * and a second solve launch).  A launch counts when it was enqueued
+ * without an error.  Needs no GPU and no context; never fails.  Not a
+ * passage of the paper: instrumentation of this library. */
+int64_t maxflow_kernel_launches(void);
+
 /* ---- step-level entry points (each runs one step of the path) ------------ */
 
 /* Replace the state by the flow assignment f(u[i], v[i]) = f[i] on the listed

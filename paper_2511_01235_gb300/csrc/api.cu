@@ -10,6 +10,7 @@
 #include <unistd.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -19,6 +20,19 @@
 
 #include "../../include/maxflow.h"
 #include "mf_internal.h"
+
+// Kernels this library has launched in the process (maxflow_kernel_launches).
+static std::atomic<long long> g_kernel_launches{0};
+
+// Also called by noalloc.cu and mlp.cu for their own launches.
+void mf_note_launches(int kernels) { g_kernel_launches.fetch_add(kernels, std::memory_order_relaxed); }
+
+// The status of a launch helper that starts `kernels` kernels, counted when it succeeded.
+static inline int counted(int rc, int kernels)
+{
+    if (rc == MAXFLOW_OK) mf_note_launches(kernels);
+    return rc;
+}
 
 struct maxflow_ctx {
     int device = 0;
@@ -329,7 +343,7 @@ void fill_stats(maxflow_ctx *c, const MfCtrl &h, float ms)
 int run_kernel(maxflow_ctx *c, const MfParams &p, int *kerr, int *kstatus)
 {
     MF_TRY(rc_cuda(cudaEventRecord(c->ev0, c->stream)));
-    MF_TRY(mf_launch(p, c->grid, (void *)c->stream));
+    MF_TRY(counted(mf_launch(p, c->grid, (void *)c->stream), 1));
     MF_TRY(rc_cuda(cudaEventRecord(c->ev1, c->stream)));
     MF_TRY(rc_cuda(cudaMemcpyAsync(c->hctrl, c->ctrl, sizeof(MfCtrl), cudaMemcpyDeviceToHost, c->stream)));
     MF_TRY(rc_cuda(cudaStreamSynchronize(c->stream)));
@@ -380,7 +394,7 @@ int dump_slots(maxflow_ctx *c, std::vector<int32_t> &su, std::vector<int32_t> &s
     int32_t *rowid = dalloc_n<int32_t>(c, S);
     if (!rowid) return MAXFLOW_ERR_OOM;
     MfParams p = base_params(c);
-    int rc = mf_launch_aux(MF_AUX_DUMP, p, (void *)c->stream, nullptr, rowid);
+    int rc = counted(mf_launch_aux(MF_AUX_DUMP, p, (void *)c->stream, nullptr, rowid), 1);
     std::vector<int32_t> hr((size_t)S), hd((size_t)S), hc((size_t)S), hf((size_t)S);
     if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMemcpyAsync(hr.data(), rowid, sizeof(int32_t) * S, cudaMemcpyDeviceToHost, c->stream));
     if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMemcpyAsync(hd.data(), c->g.dst, sizeof(int32_t) * S, cudaMemcpyDeviceToHost, c->stream));
@@ -410,7 +424,8 @@ int rebuild_device(maxflow_ctx *c)
     MfParams p = base_params(c);
     long long *noff = dalloc_n<long long>(c, (int64_t)n + 1);
     if (!noff) return MAXFLOW_ERR_OOM;
-    int rc = mf_rebuild_capacity(p, (void *)c->stream, c->opt.slack_factor, c->opt.slack_min, noff);
+    int rc =
+        counted(mf_rebuild_capacity(p, (void *)c->stream, c->opt.slack_factor, c->opt.slack_min, noff), 2);
     long long total = 0;
     if (rc == MAXFLOW_OK)
         rc = rc_cuda(cudaMemcpyAsync(&total, noff + n, sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
@@ -426,7 +441,8 @@ int rebuild_device(maxflow_ctx *c)
         pcap = dalloc_n<int32_t>(c, total);
         if (!off || !dst || !cf || !cap || !rev || !pcap) rc = MAXFLOW_ERR_OOM;
     }
-    if (rc == MAXFLOW_OK) rc = mf_rebuild_move(p, (void *)c->stream, noff, off, dst, cf, cap, rev, pcap, total);
+    if (rc == MAXFLOW_OK)
+        rc = counted(mf_rebuild_move(p, (void *)c->stream, noff, off, dst, cf, cap, rev, pcap, total), 2);
     if (rc == MAXFLOW_OK) rc = rc_cuda(cudaStreamSynchronize(c->stream));
     if (rc != MAXFLOW_OK) {
         int32_t *tmp[] = {off, dst, cf, cap, rev, pcap};
@@ -599,6 +615,8 @@ void maxflow_default_opts(maxflow_opts *o)
     o->device = -1;
     o->stream = nullptr;
 }
+
+int64_t maxflow_kernel_launches(void) { return (int64_t)g_kernel_launches.load(std::memory_order_relaxed); }
 
 const char *maxflow_strerror(int code)
 {
@@ -782,7 +800,7 @@ int maxflow_query(maxflow_ctx *c, int64_t *value, uint8_t *side, int64_t *cut_ca
     if (side) {
         uint8_t *ds = (uint8_t *)dalloc(c, (size_t)c->n);
         if (!ds) return MAXFLOW_ERR_OOM;
-        int rc = mf_launch_aux(MF_AUX_SIDE, p, (void *)c->stream, nullptr, ds);
+        int rc = counted(mf_launch_aux(MF_AUX_SIDE, p, (void *)c->stream, nullptr, ds), 1);
         if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMemcpyAsync(side, ds, (size_t)c->n, cudaMemcpyDeviceToHost, c->stream));
         if (rc == MAXFLOW_OK) rc = rc_cuda(cudaStreamSynchronize(c->stream));
         dfree(c, ds);
@@ -790,7 +808,7 @@ int maxflow_query(maxflow_ctx *c, int64_t *value, uint8_t *side, int64_t *cut_ca
     }
     if (cut_cap) {
         MF_TRY(rc_cuda(cudaMemsetAsync(c->dbuf, 0, sizeof(long long), c->stream)));
-        MF_TRY(mf_launch_aux(MF_AUX_CUT, p, (void *)c->stream, c->dbuf, nullptr));
+        MF_TRY(counted(mf_launch_aux(MF_AUX_CUT, p, (void *)c->stream, c->dbuf, nullptr), 1));
         MF_TRY(rc_cuda(cudaMemcpyAsync(c->hbuf, c->dbuf, sizeof(long long), cudaMemcpyDeviceToHost, c->stream)));
         MF_TRY(rc_cuda(cudaStreamSynchronize(c->stream)));
         *cut_cap = c->hbuf[0];
@@ -879,7 +897,7 @@ int stage_and_features(maxflow_ctx *c, const maxflow_batch *b, maxflow_batch *de
     f.host[3] = lg((double)c->init_iters) / 8.f;
     f.host[4] = lg(c->init_ms * 1000.0) / 16.f;
     f.host[5] = lg((double)c->st.bfs_levels) / 12.f;
-    return mf_features(f, c->feat, (void *)c->stream);
+    return counted(mf_features(f, c->feat, (void *)c->stream), 1);
 }
 
 int run_action(maxflow_ctx *c, const maxflow_batch *dev_batch, int a)
@@ -1053,8 +1071,8 @@ int maxflow_solve_batched(maxflow_ctx *const *ctxs, int32_t count, const maxflow
     MF_TRY(rc_cuda(cudaMemsetAsync(gstate, 0, sizeof(unsigned) * 32 * (size_t)(maxg + 2), c0->stream)));
     unsigned long long wait_ns = plist[0].wait_limit_ns;
     MF_TRY(rc_cuda(cudaEventRecord(c0->ev0, c0->stream)));
-    MF_TRY(mf_launch_multi(c0->multi_plist, count, gsize, ngroups * gsize, gstate, head, wait_ns, abort_flag,
-                           (void *)c0->stream));
+    MF_TRY(counted(mf_launch_multi(c0->multi_plist, count, gsize, ngroups * gsize, gstate, head, wait_ns, abort_flag,
+                           (void *)c0->stream), 1));
     MF_TRY(rc_cuda(cudaEventRecord(c0->ev1, c0->stream)));
     int abort_h = 0;
     MF_TRY(rc_cuda(cudaMemcpyAsync(&abort_h, abort_flag, sizeof(int), cudaMemcpyDeviceToHost, c0->stream)));
@@ -1295,7 +1313,8 @@ int maxflow_restore(maxflow_ctx *c)
         c->sched_y = dalloc_n<float>(c, 64);
         if (!c->g.h || !c->g.e || !c->ctrl || !c->dbuf || !c->feat || !c->sched_y) rc = MAXFLOW_ERR_OOM;
     }
-    if (rc == MAXFLOW_OK) rc = mf_launch_aux(MF_AUX_PCAP, base_params(c), (void *)c->stream, nullptr, nullptr);
+    if (rc == MAXFLOW_OK)
+        rc = counted(mf_launch_aux(MF_AUX_PCAP, base_params(c), (void *)c->stream, nullptr, nullptr), 1);
     if (rc == MAXFLOW_OK) rc = alloc_vertex_scratch(c);
     if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMemsetAsync(c->ctrl, 0, sizeof(MfCtrl), c->stream));
     if (rc == MAXFLOW_OK)
@@ -1388,8 +1407,8 @@ int maxflow_update_pp(maxflow_ctx *c, const maxflow_batch *b, int32_t stop_after
     MF_TRY(rc_cuda(cudaMemcpyAsync(c->multi_plist, pl, sizeof(pl), cudaMemcpyHostToDevice, c->stream)));
     MF_TRY(rc_cuda(cudaMemsetAsync(gstate, 0, sizeof(unsigned) * 32 * (size_t)(maxg + 2), c->stream)));
     MF_TRY(rc_cuda(cudaEventRecord(c->ev0, c->stream)));
-    MF_TRY(mf_launch_multi(c->multi_plist, 2, gsize, 2 * gsize, gstate, head, pl[0].wait_limit_ns, abort_flag,
-                           (void *)c->stream));
+    MF_TRY(counted(mf_launch_multi(c->multi_plist, 2, gsize, 2 * gsize, gstate, head, pl[0].wait_limit_ns, abort_flag,
+                           (void *)c->stream), 1));
     MF_TRY(rc_cuda(cudaEventRecord(c->ev1, c->stream)));
     int abort_h = 0;
     MF_TRY(rc_cuda(cudaMemcpyAsync(&abort_h, abort_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream)));
@@ -1541,13 +1560,15 @@ int maxflow_set_flow(maxflow_ctx *c, int64_t count, const int32_t *u, const int3
     }
     MfParams p = base_params(c);
     if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMemsetAsync(c->dbuf, 0, sizeof(long long), c->stream));
-    if (rc == MAXFLOW_OK && count > 0) rc = mf_set_flow_items(p, (void *)c->stream, c->dbuf, count, du, dv, df, 0);
+    if (rc == MAXFLOW_OK && count > 0)
+        rc = counted(mf_set_flow_items(p, (void *)c->stream, c->dbuf, count, du, dv, df, 0), 1);
     if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMemcpyAsync(c->hbuf, c->dbuf, sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
     if (rc == MAXFLOW_OK) rc = rc_cuda(cudaStreamSynchronize(c->stream));
     if (rc == MAXFLOW_OK && c->hbuf[0] != 0) rc = MAXFLOW_ERR_INVALID;
-    if (rc == MAXFLOW_OK) rc = mf_launch_aux(MF_AUX_SET_CF_RESET, p, (void *)c->stream, nullptr, nullptr);
-    if (rc == MAXFLOW_OK && count > 0) rc = mf_set_flow_items(p, (void *)c->stream, c->dbuf, count, du, dv, df, 1);
-    if (rc == MAXFLOW_OK) rc = mf_launch_aux(MF_AUX_EXCESS, p, (void *)c->stream, nullptr, nullptr);
+    if (rc == MAXFLOW_OK) rc = counted(mf_launch_aux(MF_AUX_SET_CF_RESET, p, (void *)c->stream, nullptr, nullptr), 1);
+    if (rc == MAXFLOW_OK && count > 0)
+        rc = counted(mf_set_flow_items(p, (void *)c->stream, c->dbuf, count, du, dv, df, 1), 1);
+    if (rc == MAXFLOW_OK) rc = counted(mf_launch_aux(MF_AUX_EXCESS, p, (void *)c->stream, nullptr, nullptr), 1);
     if (rc == MAXFLOW_OK) rc = rc_cuda(cudaStreamSynchronize(c->stream));
     dfree(c, du);
     dfree(c, dv);
@@ -1596,7 +1617,7 @@ int maxflow_check(maxflow_ctx *c, int64_t *out)
     if (!dg.ok) return MAXFLOW_ERR_CUDA;
     MfParams p = base_params(c);
     MF_TRY(rc_cuda(cudaMemsetAsync(c->dbuf, 0, 8 * sizeof(long long), c->stream)));
-    MF_TRY(mf_launch_aux(MF_AUX_CHECK, p, (void *)c->stream, c->dbuf, nullptr));
+    MF_TRY(counted(mf_launch_aux(MF_AUX_CHECK, p, (void *)c->stream, c->dbuf, nullptr), 2));
     MF_TRY(rc_cuda(cudaMemcpyAsync(c->hbuf, c->dbuf, 6 * sizeof(long long), cudaMemcpyDeviceToHost, c->stream)));
     MF_TRY(rc_cuda(cudaStreamSynchronize(c->stream)));
     for (int i = 0; i < 6; ++i) out[i] = c->hbuf[i];
@@ -1640,8 +1661,8 @@ int maxflow_get_flow(maxflow_ctx *c, int64_t *count, int32_t *u, int32_t *v, int
     // (b) fill the deficits on the sink side from t (Sec. 4.3 Claim): the
     //     same run on the reversed residual graph with negated excess.
     const int32_t *io1[2] = {c->x_cf, c->x_cf2};
-    if (rc == MAXFLOW_OK) rc = mf_launch_aux(MF_AUX_REVERSE_CF, p, (void *)c->stream, nullptr, io1);
-    if (rc == MAXFLOW_OK) rc = mf_launch_aux(MF_AUX_NEGATE_E, p, (void *)c->stream, nullptr, nullptr);
+    if (rc == MAXFLOW_OK) rc = counted(mf_launch_aux(MF_AUX_REVERSE_CF, p, (void *)c->stream, nullptr, io1), 1);
+    if (rc == MAXFLOW_OK) rc = counted(mf_launch_aux(MF_AUX_NEGATE_E, p, (void *)c->stream, nullptr, nullptr), 1);
     if (rc == MAXFLOW_OK) {
         MfParams q = p;
         q.cf = c->x_cf2;
@@ -1651,8 +1672,8 @@ int maxflow_get_flow(maxflow_ctx *c, int64_t *count, int32_t *u, int32_t *v, int
         rc = status_to_rc(kerr, kst);
     }
     const int32_t *io2[2] = {c->x_cf2, c->x_cf};
-    if (rc == MAXFLOW_OK) rc = mf_launch_aux(MF_AUX_REVERSE_CF, p, (void *)c->stream, nullptr, io2);
-    if (rc == MAXFLOW_OK) rc = mf_launch_aux(MF_AUX_NEGATE_E, p, (void *)c->stream, nullptr, nullptr);
+    if (rc == MAXFLOW_OK) rc = counted(mf_launch_aux(MF_AUX_REVERSE_CF, p, (void *)c->stream, nullptr, io2), 1);
+    if (rc == MAXFLOW_OK) rc = counted(mf_launch_aux(MF_AUX_NEGATE_E, p, (void *)c->stream, nullptr, nullptr), 1);
     c->st = keep;
     MF_TRY(rc);
     std::vector<int32_t> su, sv, scap, scf;

@@ -23,6 +23,8 @@
 
 #include "../../include/maxflow.h"
 
+void mf_note_launches(int kernels);   // the library's launch counter (api.cu)
+
 #define MLP_MAX_IN 64
 #define MLP_MAX_H 256
 #define MLP_MAX_OUT 64
@@ -254,6 +256,7 @@ int maxflow_mlp_forward(maxflow_mlp *m, const float *x, int32_t rows, float *y)
         k_mlp_fwd_bwd<<<rows, threads_for(m), 0, m->stream>>>(L, m->p, m->x, nullptr, nullptr, 0.f, m->y, nullptr,
                                                               nullptr);
         rc = ok(cudaGetLastError());
+        if (rc == MAXFLOW_OK) mf_note_launches(1);
     }
     if (rc == MAXFLOW_OK)
         rc = ok(cudaMemcpyAsync(y, m->y, sizeof(float) * (size_t)rows * m->n_out, cudaMemcpyDeviceToHost, m->stream));
@@ -266,7 +269,9 @@ int mlp_forward_device(maxflow_mlp *m, const float *x_dev, int32_t rows, float *
 {
     Layout L{m->n_in, m->H, m->n_out};
     k_mlp_fwd_bwd<<<rows, threads_for(m), 0, st>>>(L, m->p, x_dev, nullptr, nullptr, 0.f, y_dev, nullptr, nullptr);
-    return ok(cudaGetLastError());
+    int rc = ok(cudaGetLastError());
+    if (rc == MAXFLOW_OK) mf_note_launches(1);
+    return rc;
 }
 
 int mlp_n_out(const maxflow_mlp *m) { return m->n_out; }
@@ -283,6 +288,7 @@ static int grad_pass(maxflow_mlp *m, int32_t rows, float *loss_host)
         k_mlp_fwd_bwd<<<rows, threads_for(m), 0, m->stream>>>(L, m->p, m->x, m->t, m->mask, (float)(1.0 / cnt),
                                                               m->y, m->g, m->loss);
         rc = ok(cudaGetLastError());
+        if (rc == MAXFLOW_OK) mf_note_launches(1);
     }
     if (rc == MAXFLOW_OK && loss_host) {
         rc = ok(cudaMemcpyAsync(loss_host, m->loss, sizeof(float), cudaMemcpyDeviceToHost, m->stream));
@@ -336,6 +342,7 @@ int maxflow_mlp_train(maxflow_mlp *m, const float *x, const float *t, const floa
         int g = (int)((m->np + 255) / 256);
         k_adam<<<g, 256, 0, m->stream>>>(m->p, m->g, m->m1, m->m2, m->np, lr, b1, b2, eps, c1, c2);
         rc = ok(cudaGetLastError());
+        if (rc == MAXFLOW_OK) mf_note_launches(1);
     }
     if (rc == MAXFLOW_OK) rc = ok(cudaStreamSynchronize(m->stream));
     return rc;

@@ -24,6 +24,8 @@
 #include "../../include/maxflow.h"
 #include "mf_internal.h"
 
+void mf_note_launches(int kernels);   // the library's launch counter (api.cu)
+
 namespace {
 
 // control block + frontier list (one int per vertex) + work items of long rows
@@ -129,6 +131,7 @@ extern "C" int maxflow_global_relabel_noalloc(int32_t n, int32_t s, int32_t t, c
     if (grid > maxg) grid = maxg;
     rc = mf_launch(p, grid, stream);
     if (rc != MAXFLOW_OK) return rc;
+    mf_note_launches(1);
     unsigned err = 0;
     if (cudaMemcpyAsync(&err, &ctrl->err.w[0], sizeof(err), cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return MAXFLOW_ERR_CUDA;

@@ -81,7 +81,7 @@ class Stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-EXPORTS = ["maxflow_default_opts", "maxflow_init", "maxflow_update", "maxflow_query", "maxflow_resolve_static",
+EXPORTS = ["maxflow_kernel_launches", "maxflow_default_opts", "maxflow_init", "maxflow_update", "maxflow_query", "maxflow_resolve_static",
            "maxflow_get_flow", "maxflow_stats", "maxflow_destroy", "maxflow_strerror", "maxflow_set_flow",
            "maxflow_apply", "maxflow_global_relabel", "maxflow_resolve", "maxflow_get_residual",
            "maxflow_get_vertex_state", "maxflow_check", "maxflow_global_relabel_noalloc", "maxflow_trace",
@@ -179,9 +179,11 @@ def load(build_if_missing: bool = False):
     L.maxflow_destroy.restype = None
     L.maxflow_strerror.argtypes = [C.c_int]
     L.maxflow_strerror.restype = C.c_char_p
+    L.maxflow_kernel_launches.argtypes = []
+    L.maxflow_kernel_launches.restype = C.c_int64
     for name in EXPORTS:
-        if name not in ("maxflow_default_opts", "maxflow_destroy", "maxflow_strerror", "maxflow_mlp_destroy",
-                        "maxflow_arena_destroy", "maxflow_arena_alloc", "maxflow_arena_free"):
+        if name not in ("maxflow_kernel_launches", "maxflow_default_opts", "maxflow_destroy", "maxflow_strerror",
+                        "maxflow_mlp_destroy", "maxflow_arena_destroy", "maxflow_arena_alloc", "maxflow_arena_free"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -192,6 +194,11 @@ def strerror(code: int) -> str:
         return load().maxflow_strerror(int(code)).decode()
     except ImportError:
         return f"status {code}"
+
+
+def kernel_launches() -> int:
+    """Kernels the library has launched in this process (maxflow_kernel_launches)."""
+    return int(load().maxflow_kernel_launches())
 
 
 def _check(rc: int, where: str):

@@ -106,3 +106,9 @@ def test_no_cpu_fallback_when_library_missing(monkeypatch, tmp_path):
     monkeypatch.setattr(build_ext, "LIB", str(tmp_path / "missing.so"))
     with pytest.raises(ImportError):
         native.load()
+
+
+def test_kernel_launch_counter_needs_no_gpu(lib):
+    # nothing has been launched in a process without a GPU
+    assert lib.maxflow_kernel_launches() == 0
+    assert native.kernel_launches() == 0

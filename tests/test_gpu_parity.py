@@ -238,6 +238,31 @@ def test_slack_overflow_rebuild():
     S.close()
 
 
+def test_kernel_launch_counter():
+    """maxflow_kernel_launches: an update is one launch; an update whose insertion
+    overflows a row's slack adds the rebuild's four kernels and a second solve."""
+    g = W.erdos_renyi(800, 4000, seed=73, cap_hi=100)
+    S = native.Solver(g.n, g.src, g.dst, g.cap, g.s, g.t, slack_factor=0.0, slack_min=0)
+    es = W.EdgeSet(g.n, g.src, g.dst, g.cap)
+    rng = np.random.default_rng(74)
+    b = W.kind_batch(es, 50, rng, "inc")                 # existing edges only: no insertion
+    es.apply(b.u, b.v, b.cap)
+    l0, r0 = native.kernel_launches(), S.stats()["rebuilds"]
+    S.update(b.u, b.v, b.cap)
+    assert native.kernel_launches() - l0 == 1 and S.stats()["rebuilds"] == r0
+    u, v = next((a, c) for a in range(1, g.n) for c in range(1, g.n)
+                if a != c and not es.contains(a, c) and not es.contains(c, a) and g.t not in (a, c))
+    bu, bv, bc = np.array([u], np.int32), np.array([v], np.int32), np.array([7], np.int32)
+    es.apply(bu, bv, bc)
+    l0 = native.kernel_launches()
+    S.update(bu, bv, bc)                                 # a new pair: both rows are full
+    assert S.stats()["rebuilds"] == r0 + 1
+    assert native.kernel_launches() - l0 == 6
+    u2, v2, c2 = es.coo()
+    check_against_oracle(S, g.n, u2, v2, c2, g.s, g.t)
+    S.close()
+
+
 # ---------------------------------------------------------------------------
 # step-level parity: heights (Alg. 4/6) and batch repair (Alg. 5)
 # ---------------------------------------------------------------------------
