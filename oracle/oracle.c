@@ -58,7 +58,7 @@
  *      relabelled to 1 + that lowest height (clamped to n); the pull value
  *      is the sum of -e(v) over v != t with h(v) < n;
  *   R9 (O2) the old min cut is T = {h < n} of the push heights the last
- *      solve ended with, S the rest; "saturate the edges across it" sends
+ *      solve ended with, S the rest; saturating the edges across it sends
  *      all of c_f(u, v) for u in S, v in T; the push part then takes as roots
  *      t and the deficient vertices of T only, the pull part s and the
  *      overflowing vertices of S only, and a final unrestricted push solve
@@ -433,7 +433,7 @@ static orc_rstate *rs_from_edges(int32_t n, int64_t m, const int32_t *mu, const 
 }
 
 /* The excess definition: e(x) = sum over slots (x, w) of c_f(x, w) - c(x, w),
- * the net flow into x ("calculate excess for each vertex", the excess step of Alg. 5). */
+ * the net flow into x (the excess step of Alg. 5 recomputes it for every vertex). */
 void orc_rs_recompute_excess(orc_rstate *r)
 {
     int32_t x;
