@@ -20,3 +20,16 @@ def test_code_only_sees_code_changes_and_keeps_literals():
 def test_traffic_only_for_the_captured_workload():
     assert bench.measured_traffic("rmat18", 10000) is None
     assert bench.measured_traffic("rmat20", 1000) is None
+
+
+def test_batched_cpu_baseline_runs_the_oracle_on_every_instance_in_parallel():
+    import oracle
+    from paper_2511_01235_gb300 import workloads as W
+    gs = [W.erdos_renyi(300 + 50 * k, 2000, seed=900 + k, cap_hi=50) for k in range(6)]
+    rate, threads, vals = bench.cpu_baseline_batched(gs)
+    assert rate > 0 and threads >= 1
+    assert vals == [oracle.maxflow(g.n, g.src, g.dst, g.cap, g.s, g.t).value for g in gs]
+
+
+def test_roofline_nominal_peak_is_the_parts_bandwidth():
+    assert bench.HBM_NOMINAL_GBS == 7900.0 and bench.HBM_FALLBACK_GBS < bench.HBM_NOMINAL_GBS
