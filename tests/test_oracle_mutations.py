@@ -50,6 +50,15 @@ MUTANTS = [
     ("apply_source_step_dropped_term", "r->e[u] += d;\n            r->e[s] -= d;\n",
      "r->e[u] += d;\n"),
     ("apply_first_update_wins", "for (i = B - 1; i >= 0; i--) {", "for (i = 0; i < B; i++) {"),
+    ("apply_insertion_resets_carried_flow",
+     "r2->cf[rs_find(r2, (int32_t)x, r->head[j])] = r->cf[j];",
+     "r2->cf[rs_find(r2, (int32_t)x, r->head[j])] = r->cap[j];"),
+    ("slots_placeholder_counted_as_capacity",
+     "if (S[i].c >= 0) S[K - 1].c = (S[K - 1].c < 0 ? 0 : S[K - 1].c) + S[i].c;",
+     "if (S[i].c >= 0) S[K - 1].c = S[K - 1].c + S[i].c;"),
+    ("certificate_cut_counts_inner_edges",
+     "if (r->h[r->head[i]] == r->n) continue;\n            c += r->cap[i];",
+     "c += r->cap[i];"),
     ("value_counts_source_side", "if (x != s && r->h[x] < r->n) v += r->e[x];",
      "if (x != s && r->h[x] <= r->n) v += r->e[x];"),
     ("value_drops_deficits", "if (x != s && r->h[x] < r->n) v += r->e[x];",
