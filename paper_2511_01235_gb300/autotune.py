@@ -11,8 +11,6 @@ starts from the same point) and does coordinate descent over the knobs.
 """
 from __future__ import annotations
 
-import numpy as np
-
 from . import native
 
 GROUP_BLOCKS = (1, 2, 4, 8, 16, 32)

@@ -5,7 +5,6 @@ enumeration of every s-t cut, scipy's own max-flow routines, an independent
 Edmonds-Karp, closed forms, flow invariants, scipy shortest paths, and
 hand-derived fixtures under tests/golden/.
 """
-import itertools
 import json
 import os
 
