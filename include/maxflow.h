@@ -398,6 +398,28 @@ void maxflow_destroy(maxflow_ctx *c);
 /* A static string naming a status code. */
 const char *maxflow_strerror(int code);
 
+/* The residual Bi-CSR of Sec. 5.1 that maxflow_init builds from the graph
+ * (self-loops dropped, parallel edges summed, one slot at u and one at v for
+ * every pair with an edge in either direction) and the slack options,
+ * computed on the host only: no GPU and no context are needed.
+ *   *slot_capacity  in: length of the caller's per-slot arrays; out: S, the
+ *                   reserved slots (used slots plus each row's slack,
+ *                   max(slack_min, ceil(deg * slack_factor))).
+ *   off   [n + 1]   reserved start of each row;   deg [n]  used slots of each row
+ *   slot_dst, slot_cap, slot_rev, slot_pcap [S]:  per slot, its head v, c(u, v),
+ *                   the index of the slot (v, u), and c(u, v) + c(v, u).  The
+ *                   used slots of row u are off[u] .. off[u] + deg[u] - 1,
+ *                   sorted by head; slack slots hold (u, 0, itself, 0).
+ * Every output may be NULL.  With all of them NULL the call only reports S.
+ * With any array given and *slot_capacity < S it returns MAXFLOW_ERR_INVALID
+ * (and S), writing nothing.  Other errors as maxflow_init for the graph:
+ * MAXFLOW_ERR_INVALID (n < 2, an id out of range, a negative capacity, a
+ * negative slack option, NULL slot_capacity), MAXFLOW_ERR_TOO_LARGE,
+ * MAXFLOW_ERR_OOM.  Host arrays, owned by the caller. */
+int maxflow_build_layout(int32_t n, int64_t m, const int32_t *src, const int32_t *dst, const int32_t *cap,
+                         float slack_factor, int32_t slack_min, int64_t *slot_capacity, int32_t *off, int32_t *deg,
+                         int32_t *slot_dst, int32_t *slot_cap, int32_t *slot_rev, int32_t *slot_pcap);
+
 /* Number of kernels this library has launched in the calling process, over
  * every context, batched launch, network and no-allocation call since the
  * library was loaded.  Read it before and after a region to count that

@@ -616,6 +616,30 @@ void maxflow_default_opts(maxflow_opts *o)
     o->stream = nullptr;
 }
 
+int maxflow_build_layout(int32_t n, int64_t m, const int32_t *src, const int32_t *dst, const int32_t *cap,
+                         float slack_factor, int32_t slack_min, int64_t *slot_capacity, int32_t *off, int32_t *deg,
+                         int32_t *slot_dst, int32_t *slot_cap, int32_t *slot_rev, int32_t *slot_pcap)
+{
+    if (!slot_capacity || !(slack_factor >= 0.f) || slack_min < 0) return MAXFLOW_ERR_INVALID;
+    MfHostGraph hg;
+    int rc = mf_build_host(n, m, src, dst, cap, slack_factor, slack_min, hg);
+    if (rc != MAXFLOW_OK) return rc;
+    const int64_t S = hg.slot_cap;
+    const bool any = off || deg || slot_dst || slot_cap || slot_rev || slot_pcap;
+    if (any && *slot_capacity < S) rc = MAXFLOW_ERR_INVALID;
+    if (any && rc == MAXFLOW_OK) {
+        if (off) memcpy(off, hg.off, sizeof(int32_t) * ((size_t)n + 1));
+        if (deg) memcpy(deg, hg.deg, sizeof(int32_t) * (size_t)n);
+        if (slot_dst) memcpy(slot_dst, hg.dst, sizeof(int32_t) * (size_t)S);
+        if (slot_cap) memcpy(slot_cap, hg.cap, sizeof(int32_t) * (size_t)S);
+        if (slot_rev) memcpy(slot_rev, hg.rev, sizeof(int32_t) * (size_t)S);
+        if (slot_pcap) memcpy(slot_pcap, hg.pcap, sizeof(int32_t) * (size_t)S);
+    }
+    *slot_capacity = S;
+    hg.release();
+    return rc;
+}
+
 int64_t maxflow_kernel_launches(void) { return (int64_t)g_kernel_launches.load(std::memory_order_relaxed); }
 
 const char *maxflow_strerror(int code)

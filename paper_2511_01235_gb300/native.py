@@ -81,7 +81,7 @@ class Stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-EXPORTS = ["maxflow_kernel_launches", "maxflow_default_opts", "maxflow_init", "maxflow_update", "maxflow_query", "maxflow_resolve_static",
+EXPORTS = ["maxflow_build_layout", "maxflow_kernel_launches", "maxflow_default_opts", "maxflow_init", "maxflow_update", "maxflow_query", "maxflow_resolve_static",
            "maxflow_get_flow", "maxflow_stats", "maxflow_destroy", "maxflow_strerror", "maxflow_set_flow",
            "maxflow_apply", "maxflow_global_relabel", "maxflow_resolve", "maxflow_get_residual",
            "maxflow_get_vertex_state", "maxflow_check", "maxflow_global_relabel_noalloc", "maxflow_trace",
@@ -181,6 +181,9 @@ def load(build_if_missing: bool = False):
     L.maxflow_strerror.restype = C.c_char_p
     L.maxflow_kernel_launches.argtypes = []
     L.maxflow_kernel_launches.restype = C.c_int64
+    L.maxflow_build_layout.argtypes = [C.c_int32, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_float,
+                                       C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_void_p, C.c_void_p]
     for name in EXPORTS:
         if name not in ("maxflow_kernel_launches", "maxflow_default_opts", "maxflow_destroy", "maxflow_strerror",
                         "maxflow_mlp_destroy", "maxflow_arena_destroy", "maxflow_arena_alloc", "maxflow_arena_free"):
@@ -194,6 +197,21 @@ def strerror(code: int) -> str:
         return load().maxflow_strerror(int(code)).decode()
     except ImportError:
         return f"status {code}"
+
+
+def build_layout(n, src, dst, cap, slack_factor: float = 0.25, slack_min: int = 4) -> dict:
+    """The residual Bi-CSR maxflow_init would build (maxflow_build_layout), on the host."""
+    L = load()
+    src, dst, cap = _i32(src), _i32(dst), _i32(cap)
+    S = np.zeros(1, np.int64)
+    args = (int(n), int(src.size), _p(src), _p(dst), _p(cap), float(slack_factor), int(slack_min))
+    _check(L.maxflow_build_layout(*args, _p(S), None, None, None, None, None, None), "maxflow_build_layout")
+    out = {"off": np.zeros(int(n) + 1, np.int32), "deg": np.zeros(int(n), np.int32)}
+    for k in ("dst", "cap", "rev", "pcap"):
+        out[k] = np.zeros(int(S[0]), np.int32)
+    _check(L.maxflow_build_layout(*args, _p(S), _p(out["off"]), _p(out["deg"]), _p(out["dst"]), _p(out["cap"]),
+                                  _p(out["rev"]), _p(out["pcap"])), "maxflow_build_layout")
+    return out
 
 
 def kernel_launches() -> int:
