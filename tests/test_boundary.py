@@ -112,3 +112,21 @@ def test_kernel_launch_counter_needs_no_gpu(lib):
     # nothing has been launched in a process without a GPU
     assert lib.maxflow_kernel_launches() == 0
     assert native.kernel_launches() == 0
+
+
+def test_committed_scheduler_weights_fit_the_action_table(lib):
+    # the trained network shipped with the library: 16 features in, one
+    # predicted log time per action out, trained for the current action table
+    import json
+    from oracle import mlp_ref
+    from paper_2511_01235_gb300 import scheduler as SCH
+    with open(SCH.DEFAULT_WEIGHTS) as f:
+        doc = json.load(f)
+    acts = native.maxflow_sched_actions()
+    assert [tuple(a) for a in doc["actions"]] == [tuple(a) for a in acts]
+    n_in, H, n_out = doc["n_in"], doc["n_hidden"], doc["n_out"]
+    assert n_in == SCH.N_FEATURES == 16 and n_out == len(acts)
+    assert len(doc["params"]) == H * n_in + H + H * H + H + n_out * H + n_out
+    assert 0 <= SCH.ACTION_PAPER < n_out and 0 <= SCH.ACTION_DEFAULT < n_out
+    y, _ = mlp_ref.forward(np.asarray(doc["params"]), np.full((3, n_in), 0.5), n_in, H, n_out)
+    assert np.all(np.isfinite(y))
