@@ -430,7 +430,9 @@ class GridSegmentation:
         y0 = self.origin[1]
         rng = np.random.default_rng(100 + k)
         eta = _blur_periodic(rng.standard_normal((w, w)), self.sigma)
-        eta = (eta - eta.mean()) / eta.std()
+        sd = eta.std()
+        # a window much smaller than the blur leaves no variation: no perturbation then
+        eta = (eta - eta.mean()) / sd if sd > 0 else np.zeros_like(eta)
         Iw = np.clip(self.I[y0:y0 + w, x0:x0 + w] + 0.2 * eta, 0.0, 1.0)
         dbg, dfg = self._D(Iw.ravel())
         ys, xs = np.meshgrid(np.arange(y0, y0 + w), np.arange(x0, x0 + w), indexing="ij")
