@@ -33,3 +33,19 @@ def test_batched_cpu_baseline_runs_the_oracle_on_every_instance_in_parallel():
 
 def test_roofline_nominal_peak_is_the_parts_bandwidth():
     assert bench.HBM_NOMINAL_GBS == 7900.0 and bench.HBM_FALLBACK_GBS < bench.HBM_NOMINAL_GBS
+
+
+def test_cpu_baseline_sample_is_bounded_by_its_budget():
+    import numpy as np
+    from paper_2511_01235_gb300 import workloads as W
+    g = W.erdos_renyi(300, 2000, seed=31, cap_hi=50)
+    es = W.EdgeSet(g.n, g.src, g.dst, g.cap)
+    rng = np.random.default_rng(32)
+    batches = []
+    for _ in range(4):
+        b = W.mixed_batch(es, 50, rng, ins_cap_hi=50)
+        es.apply(b.u, b.v, b.cap)
+        batches.append(b)
+    assert len(bench.cpu_baseline_sample(g, batches, budget_s=0.0)) == 1       # stops after the first batch
+    times = bench.cpu_baseline_sample(g, batches, budget_s=60.0)
+    assert len(times) == 4 and all(t > 0 for t in times)
