@@ -129,14 +129,19 @@ void maxflow_default_opts(maxflow_opts *o);
 /* Build the residual Bi-CSR of g (Sec. 5.1) on the GPU and run the static
  * solve (Alg. 1 with Alg. 4/6 heights, Alg. 2, Alg. 3).  s != t, both in
  * [0, n).  opt may be NULL (defaults).  On success *out is a new context;
- * on error *out is NULL. */
+ * on error *out is NULL.  MAXFLOW_ERR_TOO_LARGE when the merged capacities
+ * of a pair, c(u,v) + c(v,u), exceed INT32_MAX (residual capacities are
+ * int32 and c_f(u,v) + c_f(v,u) stays equal to that sum). */
 int maxflow_init(maxflow_ctx **out, const maxflow_graph *g, int32_t s, int32_t t, const maxflow_opts *opt);
 
 /* Apply a batch and re-solve incrementally (Alg. 5 and Alg. 6): apply the
  * capacity changes to the residual capacities, send back flow that exceeds
  * a new capacity, update the excess, saturate the source edges, then resume
  * push-relabel from the current heights and excesses.  Returns when the
- * re-solve is done (the value is then available to maxflow_query). */
+ * re-solve is done (the value is then available to maxflow_query).
+ * Limit: after the batch every pair must still have c(u,v) + c(v,u) <=
+ * INT32_MAX, as maxflow_init requires.  The batch check does not test this
+ * yet: a batch that breaks it leaves the state undefined. */
 int maxflow_update(maxflow_ctx *c, const maxflow_batch *b);
 
 /* The current maximum-flow value (value formula of Alg. 5: the sum of e(v)

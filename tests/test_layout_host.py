@@ -85,3 +85,19 @@ def test_layout_errors():
                                     None) == native.ERR_INVALID
     assert lib.maxflow_build_layout(3, 2, p(src), p(dst), p(cap), 0.25, 4, None, None, None, None, None, None,
                                     None) == native.ERR_INVALID
+
+
+def test_a_pair_whose_capacities_overflow_int32_is_too_large():
+    big = np.iinfo(np.int32).max
+    src, dst = np.array([0, 1, 1], np.int32), np.array([1, 0, 2], np.int32)
+    ok = native.build_layout(3, src, dst, np.array([big - 5, 5, 1], np.int32))     # sum = INT32_MAX exactly
+    x = int(ok["off"][0])
+    assert ok["pcap"][x] == big
+    with pytest.raises(native.MaxflowError) as ei:
+        native.build_layout(3, src, dst, np.array([big - 5, 6, 1], np.int32))    # one more overflows
+    assert ei.value.code == native.ERR_TOO_LARGE
+    # parallel edges are summed before the pair is checked
+    with pytest.raises(native.MaxflowError) as ei:
+        native.build_layout(2, np.array([0, 0], np.int32), np.array([1, 1], np.int32),
+                            np.array([big, 1], np.int32))
+    assert ei.value.code == native.ERR_TOO_LARGE
