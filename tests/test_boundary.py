@@ -130,3 +130,16 @@ def test_committed_scheduler_weights_fit_the_action_table(lib):
     assert 0 <= SCH.ACTION_PAPER < n_out and 0 <= SCH.ACTION_DEFAULT < n_out
     y, _ = mlp_ref.forward(np.asarray(doc["params"]), np.full((3, n_in), 0.5), n_in, H, n_out)
     assert np.all(np.isfinite(y))
+
+
+def test_scheduler_action_table():
+    # mode 0: incremental (Alg. 5) with rounds R and KERNEL_CYCLES K in {1, 4, 16, 64};
+    # the paper's fixed schedule (R = 1, K = average degree, written 0); the library
+    # default (adaptive rounds, K = average degree); mode 1: static re-solves (Alg. 1)
+    from paper_2511_01235_gb300 import scheduler as SCH
+    acts = native.maxflow_sched_actions()
+    grid = [(0, r, k) for r in (1, 4, 16, 64) for k in (1, 4, 16, 64)]
+    assert acts[:16] == grid
+    assert acts[SCH.ACTION_PAPER] == (0, 1, 0) and acts[SCH.ACTION_DEFAULT] == (0, 0, 0)
+    statics = [a for a in acts if a[0] == 1]
+    assert len(acts) == 22 and len(statics) == 4 and all(a[0] in (0, 1) for a in acts)
