@@ -198,15 +198,28 @@ int maxflow_sched_actions(int32_t *mode, int32_t *rounds, int32_t *cycles, int32
  * fractions of updates touching s, touching t and deleting, the mean new
  * capacity over the graph's mean, the last solve's iterations, time, first
  * active count and BFS levels, the initial static solve's iterations and time,
- * and a constant 1. */
+ * and a constant 1.  Reads the batch only (no change to the state).  Sec. 6.1
+ * ties the choice of KERNEL_CYCLES to the graph, which these features describe.
+ * MAXFLOW_ERR_INVALID for NULL c or out, MAXFLOW_ERR_STATE while evicted,
+ * MAXFLOW_ERR_CUDA. */
 int maxflow_features(maxflow_ctx *c, const maxflow_batch *b, float *out);
 
-/* Apply the batch and re-solve with the given action (index into the table). */
+/* Apply the batch and re-solve with the given action (index into the table):
+ * maxflow_update (Alg. 5) with that action's rounds and KERNEL_CYCLES, or the
+ * batch then a static re-solve (Alg. 1).  Errors as maxflow_update, plus
+ * MAXFLOW_ERR_INVALID for an action outside the table. */
 int maxflow_run_action(maxflow_ctx *c, const maxflow_batch *b, int32_t action);
 
 /* A fully connected network x (n_in) -> ReLU(H) -> ReLU(H) -> y (n_out) in
  * fp32 on the device, trained with Adam on masked squared error; used to
- * predict the log device time of each action from the features. */
+ * predict the log device time of each action from the features.  No
+ * counterpart in the paper.  The network owns its device memory (destroy
+ * releases it; NULL is a no-op); every array argument below is a host array
+ * owned by the caller, row-major.  create: MAXFLOW_ERR_INVALID for NULL out or
+ * sizes outside 1..64 inputs, 1..256 hidden units, 1..64 outputs; every other
+ * call: MAXFLOW_ERR_INVALID for NULL pointers, rows < 1 or a parameter count
+ * other than the network's; MAXFLOW_ERR_CUDA / MAXFLOW_ERR_OOM from the
+ * device. */
 typedef struct maxflow_mlp maxflow_mlp;
 int maxflow_mlp_create(maxflow_mlp **out, int32_t n_in, int32_t n_hidden, int32_t n_out, uint64_t seed, void *stream);
 void maxflow_mlp_destroy(maxflow_mlp *m);
@@ -227,7 +240,8 @@ int maxflow_mlp_train(maxflow_mlp *m, const float *x, const float *target, const
 /* Compute the batch's features, let the network predict each action's log
  * time, and run the action with the smallest prediction (written to
  * *action_out, may be NULL).  The network must have 16 inputs and one output
- * per action. */
+ * per action (else MAXFLOW_ERR_INVALID).  Every action gives the same maximum
+ * flow; errors as maxflow_run_action. */
 int maxflow_update_scheduled(maxflow_ctx *c, const maxflow_batch *b, maxflow_mlp *m, int32_t *action_out);
 
 /* Work split thresholds (by used slots of a vertex's row): the discharge gives
@@ -386,7 +400,9 @@ int maxflow_arena_fits(maxflow_arena *a, const int64_t *sizes, int32_t count, in
  * (the dynamic algorithm resumes from any saved state, Sec. 4.2). */
 int maxflow_clone(maxflow_ctx *c, maxflow_ctx **out);
 
-/* Counters and timings of the context and of its last solve. */
+/* Counters and timings of the context and of its last solve, into a
+ * caller-owned struct.  Host-side copy, no GPU work.  MAXFLOW_ERR_INVALID for
+ * NULL c or out. */
 int maxflow_stats(maxflow_ctx *c, maxflow_stats_t *out);
 
 /* Timeline of the last solve kernel: for each grid barrier (at most `cap`),
@@ -439,8 +455,10 @@ int64_t maxflow_kernel_launches(void);
 
 /* Replace the state by the flow assignment f(u[i], v[i]) = f[i] on the listed
  * directed edges (all others 0): c_f(u,v) = c(u,v) - f(u,v) + f(v,u) and
- * e(x) = inflow - outflow.  Each (u, v) must be an edge with 0 <= f <= cap.
- * Host arrays.  Heights are left as they are. */
+ * e(x) = inflow - outflow (the residual graph of Sec. 2.1 and the excess of
+ * Sec. 3).  Each (u, v) must be an edge with 0 <= f <= cap, else
+ * MAXFLOW_ERR_INVALID with the state unchanged.  Host arrays, copied.  Heights
+ * are left as they are.  MAXFLOW_ERR_STATE while evicted. */
 int maxflow_set_flow(maxflow_ctx *c, int64_t count, const int32_t *u, const int32_t *v, const int32_t *f);
 
 /* The batch part of Alg. 5 only (apply, clamp, excess, source saturation); no re-solve. */
@@ -454,11 +472,15 @@ int maxflow_global_relabel(maxflow_ctx *c);
  * without applying anything or saturating the source. */
 int maxflow_resolve(maxflow_ctx *c);
 
-/* Residual slots, row by row: (u, v, cap(u,v), c_f(u,v)).  *count in/out as
- * in maxflow_get_flow (the number of used slots).  Host arrays. */
+/* Residual slots, row by row: (u, v, cap(u,v), c_f(u,v)) of the Sec. 5.1
+ * Bi-CSR.  *count in/out as in maxflow_get_flow (the number of used slots).
+ * Host arrays, owned by the caller.  MAXFLOW_ERR_INVALID for NULL c or count,
+ * MAXFLOW_ERR_STATE while evicted, MAXFLOW_ERR_CUDA. */
 int maxflow_get_residual(maxflow_ctx *c, int64_t *count, int32_t *u, int32_t *v, int32_t *cap, int32_t *cf);
 
-/* Heights and excesses (n entries each; either may be NULL).  Host arrays. */
+/* Heights and excesses (n entries each; either may be NULL).  Host arrays,
+ * owned by the caller.  MAXFLOW_ERR_INVALID for NULL c, MAXFLOW_ERR_STATE while
+ * evicted, MAXFLOW_ERR_CUDA. */
 int maxflow_get_vertex_state(maxflow_ctx *c, int32_t *h, int64_t *e);
 
 /* Self-check of the state on the device.  Writes, for the current state:
