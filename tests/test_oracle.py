@@ -367,3 +367,57 @@ def test_apply_last_update_wins_and_loops_ignored():
     R.apply(0, [1, 1, 2, 1], [2, 2, 2, 2], [9, 1, 4, 3])
     S = _slots_dict(R)
     assert S[(1, 2)][0] == 3 and (2, 2) not in S
+
+
+def _brute_min_cuts_vectorised(n, src, dst, cap, s, t):
+    """Every s-t cut at once (numpy): (min capacity, intersection and union of all minimum source sides)."""
+    others = np.array([x for x in range(n) if x not in (s, t)], np.int64)
+    k = others.size
+    codes = np.arange(1 << k, dtype=np.int64)
+    S = np.zeros((codes.size, n), bool)
+    S[:, s] = True
+    S[:, others] = ((codes[:, None] >> np.arange(k)) & 1).astype(bool)
+    keep = src != dst
+    u, v, c = src[keep], dst[keep], cap[keep].astype(np.int64)
+    caps = (S[:, u] & ~S[:, v]).astype(np.int64) @ c
+    best = int(caps.min())
+    sides = S[caps == best]
+    return best, sides.all(axis=0), sides.any(axis=0)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_dinic_equals_bruteforce_min_cut_up_to_18_vertices(seed):
+    # every s-t cut of graphs of 12-18 vertices (up to 2^16 cuts each)
+    rng = np.random.default_rng(5000 + seed)
+    n = int(rng.integers(12, 19))
+    m = int(rng.integers(n, 4 * n))
+    src, dst, cap = W.random_multigraph(n, m, seed=5000 + seed, cap_hi=9)
+    s, t = 0, n - 1
+    best, inter, union = _brute_min_cuts_vectorised(n, src, dst, cap, s, t)
+    r = oracle.maxflow(n, src, dst, cap, s, t)
+    assert r.value == best == r.cut_cap
+    np.testing.assert_array_equal(r.smin, inter)
+    np.testing.assert_array_equal(r.smax, union)
+
+
+def test_vectorised_enumeration_agrees_with_the_loop():
+    for seed in range(20):
+        rng = np.random.default_rng(6000 + seed)
+        n = int(rng.integers(2, 9))
+        src, dst, cap = W.random_multigraph(n, int(rng.integers(0, 3 * n + 1)), seed=6000 + seed, cap_hi=9)
+        a = brute_min_cuts(n, src, dst, cap, 0, n - 1)
+        b = _brute_min_cuts_vectorised(n, src, dst, cap, 0, n - 1)
+        assert a[0] == b[0] and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+
+
+def test_dinic_equals_edmonds_karp_on_ten_thousand_graphs():
+    # the two independent algorithms agree on 10,000 random small and medium multigraphs
+    rng = np.random.default_rng(7000)
+    for i in range(10_000):
+        n = int(rng.integers(2, 40))
+        m = int(rng.integers(0, 5 * n))
+        src = rng.integers(0, n, m).astype(np.int32)
+        dst = rng.integers(0, n, m).astype(np.int32)
+        cap = rng.integers(0, 30, m).astype(np.int32)
+        s, t = (0, n - 1) if i % 2 else tuple(int(x) for x in rng.choice(n, 2, replace=False))
+        assert oracle.maxflow(n, src, dst, cap, s, t).value == oracle.maxflow_ek(n, src, dst, cap, s, t), i
