@@ -252,7 +252,8 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic", "config": config_of(args, g, wl),
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{len(times)} batches of {args.batch} (of {args.steps} asked; bounded to ~60 s); "
+                             "sample": f"{len(times)} batches of {args.batch} "
+                                       f"(of {args.steps} asked; bounded to ~60 s); "
                                        "Dinic recomputed from scratch per batch"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -541,7 +542,8 @@ def main():
         S.update(*dev_batches[args.warmup + k])
         b.record(stream)
         st = S.stats()
-        kbytes.append(st["bytes_bfs"] + st["bytes_discharge"] + st["bytes_fix"] + st["bytes_worklist"] + st["bytes_apply"])
+        kbytes.append(st["bytes_bfs"] + st["bytes_discharge"] + st["bytes_fix"] + st["bytes_worklist"]
+                      + st["bytes_apply"])
         kms.append(st["ms_last"])
         detail.append([round(st["ms_last"], 3), st["iterations"], st["bfs_levels"], st["pushes"], st["relabels"]])
     torch.cuda.synchronize()

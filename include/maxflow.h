@@ -340,7 +340,8 @@ int maxflow_device_bytes(maxflow_ctx *c, int64_t *bytes);
  * capacities, heights, excesses) in one pinned host block and releases every
  * device allocation; maxflow_restore allocates again and copies the state
  * back (the per-slot pair sums c(u,v) + c(v,u) are not parked: the restore
- * rebuilds them on the device from the capacities and the reverse index).  The pinned block is kept after a restore for the next eviction and
+ * rebuilds them on the device from the capacities and the reverse index).
+ * The pinned block is kept after a restore for the next eviction and
  * freed by maxflow_destroy.  While evicted, every call that needs the device
  * returns MAXFLOW_ERR_STATE (maxflow_query without side/cut_cap still returns
  * the last value; stats, trace and the setters work).  Since the dynamic

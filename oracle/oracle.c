@@ -567,7 +567,9 @@ int orc_rs_apply(orc_rstate **pr, int32_t s, int64_t B, const int32_t *bu, const
         mv = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m_old + nmiss + 1));
         mc = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m_old + nmiss + 1));
         for (x = 0; x < n; x++)
-            for (j = r->row[x]; j < r->row[x + 1]; j++) { mu[q] = (int32_t)x; mv[q] = r->head[j]; mc[q] = r->cap[j]; q++; }
+            for (j = r->row[x]; j < r->row[x + 1]; j++) {
+                mu[q] = (int32_t)x; mv[q] = r->head[j]; mc[q] = r->cap[j]; q++;
+            }
         for (i = 0; i < k; i++)
             if (rs_find(r, U[i].u, U[i].v) < 0) { mu[q] = U[i].u; mv[q] = U[i].v; mc[q] = 0; q++; }
         r2 = rs_from_edges(n, q, mu, mv, mc);

@@ -396,10 +396,14 @@ int dump_slots(maxflow_ctx *c, std::vector<int32_t> &su, std::vector<int32_t> &s
     MfParams p = base_params(c);
     int rc = counted(mf_launch_aux(MF_AUX_DUMP, p, (void *)c->stream, nullptr, rowid), 1);
     std::vector<int32_t> hr((size_t)S), hd((size_t)S), hc((size_t)S), hf((size_t)S);
-    if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMemcpyAsync(hr.data(), rowid, sizeof(int32_t) * S, cudaMemcpyDeviceToHost, c->stream));
-    if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMemcpyAsync(hd.data(), c->g.dst, sizeof(int32_t) * S, cudaMemcpyDeviceToHost, c->stream));
-    if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMemcpyAsync(hc.data(), c->g.cap, sizeof(int32_t) * S, cudaMemcpyDeviceToHost, c->stream));
-    if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMemcpyAsync(hf.data(), cf_dev, sizeof(int32_t) * S, cudaMemcpyDeviceToHost, c->stream));
+    if (rc == MAXFLOW_OK)
+        rc = rc_cuda(cudaMemcpyAsync(hr.data(), rowid, sizeof(int32_t) * S, cudaMemcpyDeviceToHost, c->stream));
+    if (rc == MAXFLOW_OK)
+        rc = rc_cuda(cudaMemcpyAsync(hd.data(), c->g.dst, sizeof(int32_t) * S, cudaMemcpyDeviceToHost, c->stream));
+    if (rc == MAXFLOW_OK)
+        rc = rc_cuda(cudaMemcpyAsync(hc.data(), c->g.cap, sizeof(int32_t) * S, cudaMemcpyDeviceToHost, c->stream));
+    if (rc == MAXFLOW_OK)
+        rc = rc_cuda(cudaMemcpyAsync(hf.data(), cf_dev, sizeof(int32_t) * S, cudaMemcpyDeviceToHost, c->stream));
     if (rc == MAXFLOW_OK) rc = rc_cuda(cudaStreamSynchronize(c->stream));
     dfree(c, rowid);
     if (rc != MAXFLOW_OK) return rc;
@@ -1052,7 +1056,8 @@ int maxflow_solve_batched(maxflow_ctx *const *ctxs, int32_t count, const maxflow
     // per-instance parameters, largest instance first in the queue
     std::vector<int32_t> order((size_t)count);
     for (int32_t i = 0; i < count; ++i) order[(size_t)i] = i;
-    std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return ctxs[a]->g.slot_cap > ctxs[b]->g.slot_cap; });
+    std::sort(order.begin(), order.end(),
+              [&](int32_t a, int32_t b) { return ctxs[a]->g.slot_cap > ctxs[b]->g.slot_cap; });
     std::vector<MfParams> plist((size_t)count);
     for (int32_t k = 0; k < count; ++k) {
         maxflow_ctx *c = ctxs[order[(size_t)k]];
@@ -1586,7 +1591,8 @@ int maxflow_set_flow(maxflow_ctx *c, int64_t count, const int32_t *u, const int3
     if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMemsetAsync(c->dbuf, 0, sizeof(long long), c->stream));
     if (rc == MAXFLOW_OK && count > 0)
         rc = counted(mf_set_flow_items(p, (void *)c->stream, c->dbuf, count, du, dv, df, 0), 1);
-    if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMemcpyAsync(c->hbuf, c->dbuf, sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+    if (rc == MAXFLOW_OK)
+        rc = rc_cuda(cudaMemcpyAsync(c->hbuf, c->dbuf, sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
     if (rc == MAXFLOW_OK) rc = rc_cuda(cudaStreamSynchronize(c->stream));
     if (rc == MAXFLOW_OK && c->hbuf[0] != 0) rc = MAXFLOW_ERR_INVALID;
     if (rc == MAXFLOW_OK) rc = counted(mf_launch_aux(MF_AUX_SET_CF_RESET, p, (void *)c->stream, nullptr, nullptr), 1);

@@ -161,8 +161,10 @@ struct MfParams {
     int32_t bu_beta;
     int32_t fix_steep;
     int32_t data_driven;
-    int32_t pull;             // 0: push excess toward t and deficits; 1: pull for deficits from s and excess (Sec. 5.2.2)
-    int32_t side_root;        // -1: every deficient (push) / overflowing (pull) vertex is a root; else only side[v] == side_root
+    int32_t pull;             // 0: push excess toward t and deficits;
+                              // 1: pull for deficits from s and excess (Sec. 5.2.2)
+    int32_t side_root;        // -1: every deficient (push) / overflowing (pull) vertex is a root;
+                              // else only side[v] == side_root
     uint8_t *side;            // [n] sides of the last cut (1: reaches t or a deficit, 0: not); written by MF_M_CUT
     int32_t test_skip_cta;    // >= 0: that CTA never arrives at the first barrier (tests the bounded waits)
     long long max_iters;

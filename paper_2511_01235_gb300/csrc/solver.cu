@@ -1530,7 +1530,8 @@ __device__ bool discharge_cta(const MfParams &P, Sh &sh, int u, const DisCtx &dc
                         tcnt += a[r] > 0 ? 1 : 0;
                     }
                 }
-                if (threadIdx.x == 0) atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)(seg * blockDim.x));
+                if (threadIdx.x == 0)
+                    atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)(seg * blockDim.x));
                 long long incl = tsum;
                 int cincl = tcnt;
 #pragma unroll
@@ -2012,7 +2013,8 @@ __global__ void k_check(MfParams P, long long *out)
 {
     const int n = P.g.n;
     long long pair_bad = 0, cross = 0, act = 0, cut = 0, val = 0;
-    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x) {
         int r0 = P.g.off[v], d = P.g.deg[v];
         int hv = P.h[v];
         for (int j = 0; j < d; ++j) {
@@ -2100,7 +2102,8 @@ __global__ void k_negate(long long *e, int n)
 // New reserved size of every row: used slots + pending insertions + slack.
 __global__ void k_row_capacity(MfParams P, float slack_factor, int slack_min, long long *cap_out)
 {
-    for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < P.g.n; u += (long long)gridDim.x * blockDim.x) {
+    for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < P.g.n;
+         u += (long long)gridDim.x * blockDim.x) {
         long long need = (long long)P.g.deg[u] + P.sc.ins_need[u];
         double want = (double)need * (double)slack_factor;
         long long sl = (long long)want;
@@ -2181,7 +2184,8 @@ __global__ void k_move_rows(MfParams P, MoveOut M)
 
 __global__ void k_clear_need(MfParams P)
 {
-    for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < P.g.n; u += (long long)gridDim.x * blockDim.x)
+    for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < P.g.n;
+         u += (long long)gridDim.x * blockDim.x)
         P.sc.ins_need[u] = 0;
 }
 

@@ -81,7 +81,8 @@ class Stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-EXPORTS = ["maxflow_build_layout", "maxflow_kernel_launches", "maxflow_default_opts", "maxflow_init", "maxflow_update", "maxflow_query", "maxflow_resolve_static",
+EXPORTS = ["maxflow_build_layout", "maxflow_kernel_launches", "maxflow_default_opts", "maxflow_init",
+           "maxflow_update", "maxflow_query", "maxflow_resolve_static",
            "maxflow_get_flow", "maxflow_stats", "maxflow_destroy", "maxflow_strerror", "maxflow_set_flow",
            "maxflow_apply", "maxflow_global_relabel", "maxflow_resolve", "maxflow_get_residual",
            "maxflow_get_vertex_state", "maxflow_check", "maxflow_global_relabel_noalloc", "maxflow_trace",

@@ -18,9 +18,10 @@ it, so a restore makes no CUDA allocation call (which would serialise it with
 the running launch) and the budget is physical.  A request whose graph is
 evicted needs its state restored first; the server evicts the least recently
 used graphs that are not in the running launch until the state fits, both in
-bytes and as a free block large enough for its largest array.  Evictions and restores of graphs outside the running launch
-go on a copy stream from the host thread while a worker thread waits for the
-launch on the compute stream, so state traffic overlaps the solve.
+bytes and as a free block large enough for its largest array.  Evictions and
+restores of graphs outside the running launch go on a copy stream from the
+host thread while a worker thread waits for the launch on the compute stream,
+so state traffic overlaps the solve.
 """
 from __future__ import annotations
 

@@ -36,14 +36,18 @@ MUTANTS = [
     ("set_flow_no_reverse_credit", "r->cf[r->rev[a]] += f[i];", "r->cf[r->rev[a]] -= f[i];"),
     ("static_init_dropped_term", "r->cf[j] = c_us + c_su;", "r->cf[j] = c_su;"),
     ("heights_forward_residual",
-     "/* candidate predecessor z with edge (z, y) */\n            if (z != s && r->h[z] == n && r->cf[r->rev[i]] > 0) {",
+     "/* candidate predecessor z with edge (z, y) */\n"
+     "            if (z != s && r->h[z] == n && r->cf[r->rev[i]] > 0) {",
      "/* candidate predecessor z with edge (z, y) */\n            if (z != s && r->h[z] == n && r->cf[i] > 0) {"),
     ("heights_step_two",
-     "r->cf[r->rev[i]] > 0) {\n                r->h[z] = r->h[y] + 1;\n                queue[tail++] = z;\n            }\n        }\n    }\n    free(queue);\n    if (h_out)",
-     "r->cf[r->rev[i]] > 0) {\n                r->h[z] = r->h[y] + 2;\n                queue[tail++] = z;\n            }\n        }\n    }\n    free(queue);\n    if (h_out)"),
+     "r->cf[r->rev[i]] > 0) {\n                r->h[z] = r->h[y] + 1;\n"
+     "                queue[tail++] = z;\n            }\n        }\n    }\n    free(queue);\n    if (h_out)",
+     "r->cf[r->rev[i]] > 0) {\n                r->h[z] = r->h[y] + 2;\n"
+     "                queue[tail++] = z;\n            }\n        }\n    }\n    free(queue);\n    if (h_out)"),
     ("heights_no_deficit_roots", "if (deficit_roots)\n", "if (0)\n"),
     ("heights_label_the_source",
-     "/* candidate predecessor z with edge (z, y) */\n            if (z != s && r->h[z] == n && r->cf[r->rev[i]] > 0) {",
+     "/* candidate predecessor z with edge (z, y) */\n"
+     "            if (z != s && r->h[z] == n && r->cf[r->rev[i]] > 0) {",
      "/* candidate predecessor z with edge (z, y) */\n            if (r->h[z] == n && r->cf[r->rev[i]] > 0) {"),
     ("apply_capacity_sign", "r->cf[a] += U[i].c - r->cap[a];", "r->cf[a] += r->cap[a] - U[i].c;"),
     ("apply_clamp_sign", "r->cf[r->rev[i]] += r->cf[i];", "r->cf[r->rev[i]] -= r->cf[i];"),

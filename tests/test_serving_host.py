@@ -26,7 +26,8 @@ class FakeSolver:
         self.h = hashlib.sha1(f"{n}:{int(np.sum(cap))}".encode()).hexdigest()
 
     def _feed(self, u, v, c):
-        self.h = hashlib.sha1((self.h + hashlib.sha1(np.concatenate([u, v, c]).tobytes()).hexdigest()).encode()).hexdigest()
+        batch = hashlib.sha1(np.concatenate([u, v, c]).tobytes()).hexdigest()
+        self.h = hashlib.sha1((self.h + batch).encode()).hexdigest()
 
     def query(self):
         return (int(self.h[:12], 16), None, None)
