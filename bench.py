@@ -11,10 +11,19 @@ delete) of --batch updates.  The residual state (~0.6 GB) is larger than the
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--impl ours|reference]
 
-With N > 1 (torchrun), every rank runs its own replica (the path does not
-shard) and rank 0 reports the aggregate.  --impl reference
-times the CPU oracle (Dinic recomputed from scratch after each batch) on
-rank 0 only.
+With N > 1 every rank runs its own replica on its own GPU: push-relabel on
+one graph needs an exchange at every sweep and a global BFS, so the path does
+not shard, and replicas need no collective on the data path.  Rank 0 reports
+the aggregate (the units of all ranks over the slowest rank's timed region).
+Launched as `python bench.py --gpus N` without torchrun, the script starts the
+N ranks itself through torch.distributed.run.  --impl reference times the CPU
+oracle (Dinic recomputed from scratch after each batch) on rank 0 only.
+
+Besides the headline workload the default run measures the other shapes of
+the metric in a `configs` block: the small Erdos-Renyi graph (n=4096,
+m=32768, batches of 256), R-MAT 20 with batches of 1K and 100K, the 2048x2048
+segmentation grid with its window batches, and 64 uneven instances in one
+batched launch; each with kernel latency, the static re-solve and their ratio.
 """
 from __future__ import annotations
 
@@ -250,7 +259,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": len(times), "warmup": warm, "ms_per_step": 1e3 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-            "data": "synthetic", "config": config_of(args, g, wl),
+            "data": "synthetic", "config": config_of(args, g, wl, ws),
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{len(times)} batches of {args.batch} "
                                        f"(of {args.steps} asked; bounded to ~60 s); "
@@ -264,11 +273,33 @@ def W_edgeset(g):
     return W.EdgeSet(g.n, g.src, g.dst, g.cap)
 
 
-def config_of(args, g, wl):
+def config_of(args, g, wl, world=1):
     return {"workload": wl.describe(),
             "n": int(g.n), "m_merged": int(g.m), "s": int(g.s), "t": int(g.t), "batch": args.batch,
             "l2": "inputs larger than L2 (residual state of R-MAT 20 / grid 2048 ~0.6 GB vs 129 MB L2)",
-            "parallelism": f"replicas x{args.gpus}"}
+            "parallelism": f"replicas x{world}"}
+
+
+def replica_command(argv, n, port):
+    """The torch.distributed.run command that starts n ranks of this script, one per local GPU."""
+    return [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+            "--master-addr=127.0.0.1", f"--master-port={port}", os.path.abspath(__file__)] + list(argv)
+
+
+def launch_replicas(argv, n):
+    """Start n replicas of this script (one process per GPU) and return their exit status.
+    Refuses cleanly when the host has fewer than n GPUs."""
+    import socket
+    import torch
+    have = torch.cuda.device_count() if torch.cuda.is_available() else 0
+    if have < n:
+        sys.stderr.write(f"bench.py: --gpus {n} needs {n} GPUs on this host, found {have}\n")
+        return 2
+    sk = socket.socket()
+    sk.bind(("127.0.0.1", 0))
+    port = sk.getsockname()[1]
+    sk.close()
+    return subprocess.call(replica_command(argv, n, port))
 
 
 def cpu_baseline_sample(g, batches, budget_s=20.0):
@@ -300,6 +331,140 @@ def cpu_baseline_batched(gs):
     with ThreadPoolExecutor(threads) as ex:
         vals = list(ex.map(lambda g: oracle.maxflow(g.n, g.src, g.dst, g.cap, g.s, g.t).value, gs))
     return len(gs) / (time.perf_counter() - t0), threads, vals
+
+
+def _phase_rates(S, totals):
+    """Add the last call's per-phase algorithmic bytes and device time to totals."""
+    st = S.stats()
+    for ph, bk, mk in (("bfs", "bytes_bfs", "ms_bfs"), ("discharge", "bytes_discharge", "ms_discharge"),
+                       ("fix", "bytes_fix", "ms_fix"), ("apply", "bytes_apply", "ms_apply")):
+        t = totals.setdefault(ph, [0.0, 0.0])
+        t[0] += st[bk]
+        t[1] += st[mk]
+    return st
+
+
+def phase_roofline(totals, hbm):
+    """Per phase: algorithmic bytes over the phase's device time (hook timestamps), against the peak."""
+    out = {}
+    for ph, (b, ms) in totals.items():
+        gbs = b / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+        out[ph] = {"bytes": int(b), "ms": float(ms), "gbs": gbs, "frac": gbs / hbm}
+    return out
+
+
+def dynamic_config(name, S, es, batch_fn, steps, warm, static_reps, check_each, hbm, describe):
+    """Incremental updates on S (kernel device time per update), then the static re-solve of the
+    final graph; the oracle checks the final value (and every batch's with check_each)."""
+    import oracle
+    import torch
+    batches = []
+    for _ in range(warm + steps):
+        b = batch_fn(es)
+        es.apply(b.u, b.v, b.cap)
+        batches.append((b, es.copy() if check_each else None))
+    kms, totals, checked, equal = [], {}, 0, True
+    detail = []
+    for k, (b, es_k) in enumerate(batches):
+        S.update(torch.from_numpy(b.u).cuda(), torch.from_numpy(b.v).cuda(), torch.from_numpy(b.cap).cuda())
+        if k < warm:
+            continue
+        st = _phase_rates(S, totals)
+        kms.append(st["ms_update"])
+        detail.append([round(st["ms_update"], 3), st["iterations"], st["bfs_levels"], st["barriers"]])
+        if check_each:
+            u, v, c = es_k.coo()
+            equal &= S.query()[0] == oracle.maxflow(es_k.n, u, v, c, S.s, S.t).value
+            checked += 1
+    value = S.query()[0]
+    if not check_each:
+        u, v, c = es.coo()
+        equal &= value == oracle.maxflow(es.n, u, v, c, S.s, S.t).value
+        checked += 1
+    static_ms = []
+    for _ in range(static_reps):
+        S.resolve_static()
+        static_ms.append(S.stats()["ms_update"])
+        equal &= S.query()[0] == value
+    kp50 = float(np.percentile(kms, 50))
+    sms = float(np.median(static_ms))
+    B = int(batches[0][0].size)
+    return {"workload": describe, "batch": B, "steps": steps, "warmup": warm,
+            "kernel_ms": {"p50": kp50, "p99": float(np.percentile(kms, 99)), "mean": float(np.mean(kms))},
+            "updates_per_s": B * len(kms) / (sum(kms) / 1e3),
+            "static_resolve_ms": sms, "speedup_vs_static": sms / kp50 if kp50 > 0 else None,
+            "phases": phase_roofline(totals, hbm),
+            "flow_check": {"batches_checked": checked, "equal": bool(equal)},
+            "steps_detail": {"cols": ["kernel_ms", "iterations", "bfs_levels", "barriers"], "rows": detail}}
+
+
+def run_configs(S, es_main, hbm):
+    """The other shapes of the metric, each with kernel latency, static re-solve and their ratio."""
+    import torch
+    from paper_2511_01235_gb300 import native
+    from paper_2511_01235_gb300 import workloads as W
+    out = {}
+    t0 = time.perf_counter()
+    # small Erdos-Renyi: n=4096, m=32768, caps U[1,100]; 10 batches of 256 (40/40/10/10), every one checked
+    g = W.er_small()
+    C1 = native.Solver(g.n, g.src, g.dst, g.cap, g.s, g.t, stream=torch.cuda.current_stream())
+    rng = np.random.default_rng(11)
+    out["er_small"] = dynamic_config(
+        "er_small", C1, W.EdgeSet(g.n, g.src, g.dst, g.cap),
+        lambda es: W.mixed_batch(es, 256, rng, ins_cap_hi=100), 10, 3, 3, True, hbm,
+        "Erdos-Renyi n=4096 m=32768 caps U[1,100], s=0, t=4095; batches of 256 (40/40/10/10)")
+    C1.close()
+    # R-MAT 20 with small (1K) and large (100K) batches, on clones of the headline state
+    for B, steps in ((1000, 10), (100000, 4)):
+        C = S.clone()
+        rng = np.random.default_rng(2000 + B)
+        out[f"rmat20_{B // 1000}k"] = dynamic_config(
+            f"rmat20_{B // 1000}k", C, es_main.copy(), lambda es, B=B: W.mixed_batch(es, B, rng, ins_cap_hi=1000),
+            steps, 2, 2, False, hbm, f"R-MAT scale 20 (the headline graph and state); batches of {B} (40/40/10/10)")
+        C.close()
+    # segmentation grid 2048x2048: t-links re-drawn in a 256x256 window shifting 8 px per batch
+    grid = W.GridSegmentation(side=2048, seed=3)
+    g = grid.graph()
+    G = native.Solver(g.n, g.src, g.dst, g.cap, g.s, g.t, stream=torch.cuda.current_stream())
+    ks = iter(range(30))
+    out["grid2048"] = dynamic_config(
+        "grid2048", G, W.EdgeSet(g.n, g.src, g.dst, g.cap), lambda es: grid.window_batch(next(ks)), 3, 1, 2, False,
+        hbm, "2048x2048 4-connected segmentation grid (n=4,194,306), t-links re-drawn in a 256x256 window "
+             "shifting 8 px per batch (131,072 updates)")
+    G.close()
+    out["batched64"] = batched_summary()
+    out["wall_s"] = time.perf_counter() - t0
+    return out
+
+
+def batched_summary():
+    """64 uneven instances in one persistent launch (default configuration, no autotuning)."""
+    import torch
+    from paper_2511_01235_gb300 import autotune, native
+    from paper_2511_01235_gb300 import workloads as W
+    gs = W.batched_instances(count=64, seed=4)
+    S = [native.Solver(g.n, g.src, g.dst, g.cap, g.s, g.t, stream=torch.cuda.current_stream()) for g in gs]
+    vals = [s.query()[0] for s in S]
+    cfg = autotune.DEFAULT
+    autotune.apply_config(S, cfg)
+    native.maxflow_solve_batched(S, None, group_blocks=cfg["group_blocks"])
+    ms = [native.maxflow_solve_batched(S, None, group_blocks=cfg["group_blocks"]) for _ in range(3)]
+    same = [s.query()[0] for s in S] == vals
+    one = 0.0
+    for s in S:
+        s.resolve_static()
+        one += s.stats()["ms_update"]
+    cpu_rate, cpu_threads, cpu_vals = cpu_baseline_batched(gs)
+    for s in S:
+        s.close()
+    best = float(np.median(ms))
+    return {"workload": "64 instances, n log-uniform in [1e3, 2e5], ER / layered DAG / geometric, caps U[1,500]",
+            "instances_per_s": len(gs) / (best / 1e3), "ms_per_batched_solve": best, "one_by_one_ms": one,
+            "speedup_vs_one_by_one": one / best, "config": {k: (list(v) if isinstance(v, tuple) else v)
+                                                            for k, v in cfg.items()},
+            "cpu_baseline": {"value": cpu_rate, "unit": "instances/s", "cores": cpu_threads, "kind": "oracle",
+                             "sample": f"all {len(gs)} instances, one per thread"},
+            "flow_check": {"instances": len(gs), "equal": bool(same and cpu_vals == vals)}}
 
 
 def run_batched(args):
@@ -482,6 +647,7 @@ def main():
     ap.add_argument("--workload", default="rmat20")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="headline workload only (no configs block)")
     ap.add_argument("--static-reps", type=int, default=3)
     ap.add_argument("--quick", action="store_true", help="timed steps only (for profiling runs)")
     ap.add_argument("--sched-steps", type=int, default=6, help="batches for the learned-vs-fixed schedule comparison")
@@ -491,6 +657,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        return launch_replicas(sys.argv[1:], args.gpus)
     if args.workload == "batched64":
         return run_batched(args)
     if args.workload.startswith("serving"):
@@ -500,6 +668,9 @@ def main():
     from paper_2511_01235_gb300 import native
 
     ws, rank, local = dist_env()
+    if ws != args.gpus:
+        sys.stderr.write(f"bench.py: --gpus {args.gpus} but WORLD_SIZE is {ws}\n")
+        return 2
     if ws > 1:
         import torch.distributed as dist
         torch.cuda.set_device(local)
@@ -532,7 +703,7 @@ def main():
     clk.start()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     lat = []
-    kbytes, kms, detail = [], [], []
+    kbytes, kms, detail, barriers, phase_tot = [], [], [], [], {}
     torch.cuda.synchronize()
     l0 = native.kernel_launches()
     t_wall = time.perf_counter()
@@ -542,6 +713,12 @@ def main():
         S.update(*dev_batches[args.warmup + k])
         b.record(stream)
         st = S.stats()
+        for ph, bk, mk in (("bfs", "bytes_bfs", "ms_bfs"), ("discharge", "bytes_discharge", "ms_discharge"),
+                           ("fix", "bytes_fix", "ms_fix"), ("apply", "bytes_apply", "ms_apply")):
+            t = phase_tot.setdefault(ph, [0.0, 0.0])
+            t[0] += st[bk]
+            t[1] += st[mk]
+        barriers.append(st["barriers"])
         kbytes.append(st["bytes_bfs"] + st["bytes_discharge"] + st["bytes_fix"] + st["bytes_worklist"]
                       + st["bytes_apply"])
         kms.append(st["ms_last"])
@@ -574,6 +751,7 @@ def main():
         native.maxflow_query(S.h, S.n)
     e2e_s = time.perf_counter() - t0
     e2e_val = ws * args.batch * len(pinned) / e2e_s if pinned else None
+    es_state = wl.es.copy()            # the graph S holds now (the comparisons below run on clones)
 
     # ---- learned schedule vs the fixed ones on the same batch stream (clones of one state) ----
     sched = None
@@ -623,9 +801,12 @@ def main():
         static_ms.append(S.stats()["ms_last"])
     static_stats = S.stats()
 
+    peaks, peak_src = _peaks()
+    hbm = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
+    configs = None
+    if ws == 1 and not args.quick and not args.no_configs:
+        configs = run_configs(S, es_state, hbm)
     if rank == 0:
-        peaks, peak_src = _peaks()
-        hbm = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
         avg_bytes = float(np.mean(kbytes))
         avg_ms = float(np.mean(kms))
         achieved = avg_bytes / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0.0
@@ -642,7 +823,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": config_of(args, g, wl),
+            "config": config_of(args, g, wl, ws),
             "latency_ms": {"p50": p50, "p99": p99, "mean": float(lat.mean())},
             "kernel_ms": {"p50": kp50, "mean": float(np.mean(kms))},
             "static_resolve_ms": float(np.median(static_ms)) if static_ms else None,
@@ -655,7 +836,10 @@ def main():
                          "frac": achieved / hbm, "traffic": measured_traffic(args.workload, args.batch),
                          "kernel": "mf_solve_kernel", "peak_source": f"{peak_src} hbm_gbs (copy)",
                          "algorithmic_bytes_per_launch": avg_bytes, "avg_launch_ms": avg_ms,
-                         "frac_of_nominal": achieved / HBM_NOMINAL_GBS},
+                         "frac_of_nominal": achieved / HBM_NOMINAL_GBS,
+                         "phases": phase_roofline(phase_tot, hbm)},
+            "barriers_per_update": float(np.mean(barriers)),
+            "configs": configs,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 12 * args.batch,
                     "d2h_bytes_per_step": 2048 + 8},
@@ -679,4 +863,4 @@ def main():
 
 
 if __name__ == "__main__":
-    main()
+    sys.exit(main() or 0)

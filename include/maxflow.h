@@ -139,9 +139,13 @@ int maxflow_init(maxflow_ctx **out, const maxflow_graph *g, int32_t s, int32_t t
  * a new capacity, update the excess, saturate the source edges, then resume
  * push-relabel from the current heights and excesses.  Returns when the
  * re-solve is done (the value is then available to maxflow_query).
- * Limit: after the batch every pair must still have c(u,v) + c(v,u) <=
- * INT32_MAX, as maxflow_init requires.  The batch check does not test this
- * yet: a batch that breaks it leaves the state undefined. */
+ * Errors: MAXFLOW_ERR_INVALID for an endpoint out of [0, n) or a negative
+ * capacity; MAXFLOW_ERR_TOO_LARGE when the batch would leave a pair with
+ * c(u,v) + c(v,u) > INT32_MAX (the final capacity of both directions counts,
+ * including the batch's own update of the reverse direction), the limit
+ * maxflow_init also enforces.  Both are detected on the whole batch before
+ * any capacity, slot or excess changes: a refused batch leaves the state as
+ * it was. */
 int maxflow_update(maxflow_ctx *c, const maxflow_batch *b);
 
 /* The current maximum-flow value (value formula of Alg. 5: the sum of e(v)
@@ -414,6 +418,17 @@ int maxflow_stats(maxflow_ctx *c, maxflow_stats_t *out);
  * 11 end.  *count receives the number of entries written.  Host arrays. */
 int maxflow_trace(maxflow_ctx *c, int32_t *boundary, double *t_us, int32_t cap, int32_t *count);
 
+/* The work of the phases in the same timeline (entry i belongs to boundary i
+ * of maxflow_trace): slots[i] = slots scanned by the BFS, discharge and
+ * remove-invalid phases from kernel entry up to that barrier (cumulative);
+ * info[i] for a BFS level (boundaries 7 and 8): bit 30 set if the level ran
+ * bottom-up, bits 20-29 the work items of long rows it expanded (capped at
+ * 1023), bits 0-19 the vertices it labelled (capped at 2^20 - 1); for a
+ * discharge round (boundary 10): bits 20-29 the vertices of the CTA-per-vertex
+ * bin, bits 0-19 all vertices of the round's lists; 0 otherwise.  Either array
+ * may be NULL.  Host arrays.  No counterpart in the paper (instrumentation). */
+int maxflow_trace_work(maxflow_ctx *c, int64_t *slots, int32_t *info, int32_t cap, int32_t *count);
+
 /* Release every resource of the context (NULL is a no-op). */
 void maxflow_destroy(maxflow_ctx *c);
 
@@ -462,7 +477,8 @@ int64_t maxflow_kernel_launches(void);
  * are left as they are.  MAXFLOW_ERR_STATE while evicted. */
 int maxflow_set_flow(maxflow_ctx *c, int64_t count, const int32_t *u, const int32_t *v, const int32_t *f);
 
-/* The batch part of Alg. 5 only (apply, clamp, excess, source saturation); no re-solve. */
+/* The batch part of Alg. 5 only (apply, clamp, excess, source saturation); no
+ * re-solve.  The batch is checked as in maxflow_update, with the same errors. */
 int maxflow_apply(maxflow_ctx *c, const maxflow_batch *b);
 
 /* Alg. 6 only: heights = residual distance to {t} and every deficient vertex,
@@ -500,23 +516,33 @@ int maxflow_check(maxflow_ctx *c, int64_t *out);
  * application that owns the GPU allocator -- because an allocation can fail
  * under their fixed budget, block, or synchronise the device.
  *
- * It computes the same heights as maxflow_global_relabel (Alg. 6 when
- * deficit_roots != 0, Alg. 4 otherwise) on a residual graph the caller holds
- * in device memory, and allocates nothing: the step's scratch (frontier lists and
- * control block) is a file-scope device array sized for MAXFLOW_NOALLOC_MAX_N
- * vertices and MAXFLOW_NOALLOC_MAX_SLOTS slots (about 14 MB, held on every GPU
- * that loads the library until the process exits).
+ * It computes the same heights as maxflow_global_relabel on a residual graph
+ * the caller holds in device memory: the residual distance of every vertex to
+ * the sink and, when deficit_roots != 0, to every vertex other than s with a
+ * negative excess as well (deficit_roots == 0: to the sink only); s gets n, and
+ * so does every vertex that reaches none of them.  It allocates nothing: the
+ * step's scratch (frontier lists and control block) is a file-scope device
+ * array sized for MAXFLOW_NOALLOC_MAX_N vertices and MAXFLOW_NOALLOC_MAX_SLOTS
+ * slots (about 14 MB, held on every GPU that loads the library until the
+ * process exits).
  *   rows:  slots of vertex u are off[u] .. off[u] + deg[u] - 1 (off: n+1 ints, deg: n ints)
  *   slots: dst[x] = head v of slot (u, v); cf[x] = c_f(u, v); pcap[x] = c(u,v) + c(v,u),
  *          so that c_f(v, u) = pcap[x] - cf[x]
  *   e:     n excesses (int64); h: n heights (output)
  * All pointers are device pointers on the current device; nothing is copied.
- * The first call on a device looks up the array's device address and should
- * come before any stream capture.  Calls share the array: two calls that overlap
- * on the GPU race.  The call returns when the heights are written.
+ * Preparing a device: the CUDA driver may load the library's device code, and
+ * with it the array, only when it is first used, and that load takes device
+ * memory.  A call with n = 0 (s, t and the arrays ignored; deficit_roots and
+ * stream used) does that loading for the current device and runs the step once
+ * on a two-vertex graph kept inside the array: make it once per device at
+ * start-up, so that later calls take no device memory.
+ * Each call reads off[n] back and waits for its kernel, so it synchronises the
+ * stream: it must not be issued while that stream is being captured into a
+ * CUDA graph.  Calls share the array: two calls that overlap on the GPU race.
+ * The call returns when the heights are written.
  * Errors: MAXFLOW_ERR_TOO_LARGE if n > MAXFLOW_NOALLOC_MAX_N or off[n] >
  * MAXFLOW_NOALLOC_MAX_SLOTS (off[n] is read back first); MAXFLOW_ERR_INVALID
- * for n < 2, s or t out of range, s == t, or a NULL pointer. */
+ * for n = 1 or n < 0, s or t out of range, s == t, or a NULL pointer. */
 #define MAXFLOW_NOALLOC_MAX_N (1 << 20)
 #define MAXFLOW_NOALLOC_MAX_SLOTS (1 << 25)
 int maxflow_global_relabel_noalloc(int32_t n, int32_t s, int32_t t, const int32_t *off, const int32_t *deg,

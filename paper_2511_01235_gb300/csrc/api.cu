@@ -48,6 +48,7 @@ struct maxflow_ctx {
     unsigned *multi_gstate = nullptr;
     int multi_cap = 0;
     int grid = 1, per_sm = 1, sms = 1;
+    int32_t stage_slots = 0;      // dynamic shared memory of the solve launches, in ints
     MfGraph g{};
     MfScratch sc{};
     MfCtrl *ctrl = nullptr;
@@ -176,6 +177,7 @@ MfParams base_params(maxflow_ctx *c)
     p.pull = 0;
     p.side_root = -1;
     p.test_skip_cta = -1;
+    p.stage_slots = c->stage_slots;
     p.side = c->pp.side;
     p.max_iters = c->opt.max_iters > 0 ? c->opt.max_iters : 4LL * c->n + 1000;
     double tl = c->opt.time_limit_s > 0 ? c->opt.time_limit_s : 120.0;
@@ -262,8 +264,10 @@ int upload_graph(maxflow_ctx *c, const MfHostGraph &hg)
     // the host arrays must stay valid until the copies complete
     MF_TRY(rc_cuda(cudaStreamSynchronize(st)));
     dfree(c, c->sc.bitem);
+    dfree(c, c->sc.bdefer);
     c->sc.bitem = dalloc_n<int2>(c, (int64_t)n + S / MF_BFS_CHUNK + 64);
-    if (!c->sc.bitem) return MAXFLOW_ERR_OOM;
+    c->sc.bdefer = dalloc_n<int2>(c, (int64_t)n + S / MF_BFS_CHUNK + 64);
+    if (!c->sc.bitem || !c->sc.bdefer) return MAXFLOW_ERR_OOM;
     c->st.slot_capacity = S;
     c->st.slots = hg.slots;
     c->st.m_edges = hg.m_merged;
@@ -316,15 +320,22 @@ void fill_stats(maxflow_ctx *c, const MfCtrl &h, float ms)
     s.steep_fixes = h.steep;
     s.active_first = h.active_first;
     s.active_total = h.active_total;
-    // algorithmic bytes of the paper's Bi-CSR (int32 per slot field, int64 excess):
-    //   BFS: per scanned slot dst + cf + pcap + h[dst] = 16 B; per vertex off + deg + h write + append = 16 B
-    //   discharge: per scanned slot in a cycle dst + cf + h[dst] = 12 B; per cycle off + deg + h + e = 20 B
-    //   remove-invalid: per slot 12 B; per vertex 20 B; worklist: h + e + deg + append per vertex = 20 B
-    s.bytes_bfs = 16 * h.slots_bfs + 16 * h.verts_bfs;
-    s.bytes_discharge = 12 * h.slots_dis + 20 * h.cycles_dis;
-    s.bytes_fix = 12 * h.slots_fix + 20 * h.verts_fix;
-    s.bytes_worklist = 16LL * c->n * (h.iters + 1);
-    s.bytes_apply = 100 * h.n_apply;
+    // algorithmic bytes of the paper's Bi-CSR (int32 per slot field, int64 excess), counted by the kernel:
+    //   BFS: per scanned slot dst + cf + pcap + h[dst] = 16 B; per vertex record read (roots pass: e + h;
+    //        bottom-up, unlabelled vertex: h + off + deg) 12 B; per height read in a bottom-up pass 4 B;
+    //        per labelled vertex h claim + deg + e + append = 20 B
+    //   discharge: per scanned slot in a cycle dst + cf + h[dst] = 12 B; per cycle off + deg + h + e = 20 B;
+    //        per push two c_f and two excess read-modify-writes = 48 B
+    //   remove-invalid: per slot 12 B; per vertex 20 B; per steep push 48 B
+    //   worklist (only when it is a pass of its own, data_driven = 0): e + h + deg per vertex = 16 B
+    //   apply: per applied update the record, the slot's cap, cf, pcap and its reverse's pcap
+    //        (read-modify-write), rev and the dedup entry = 12 + 8 + 8 + 8 + 8 + 4 + 12 = 60 B;
+    //        per slot read by the search or the source row 4 B; per clamp two c_f and two excess RMWs 48 B
+    s.bytes_bfs = 16 * h.slots_bfs + 12 * h.verts_bfs + 4 * h.hscan_bfs + 20 * h.lab_bfs;
+    s.bytes_discharge = 12 * h.slots_dis + 20 * h.cycles_dis + 48 * h.pushes;
+    s.bytes_fix = 12 * h.slots_fix + 20 * h.verts_fix + 48 * h.steep;
+    s.bytes_worklist = c->opt.data_driven ? 0 : 16LL * c->n * (h.iters + 1);
+    s.bytes_apply = 60 * h.n_apply + 4 * h.slots_apply + 48 * h.clamps_apply;
     s.ms_last = ms;
     s.ms_bfs = h.ns_bfs * 1e-6;
     s.ms_discharge = h.ns_dis * 1e-6;
@@ -364,6 +375,7 @@ int run_kernel(maxflow_ctx *c, const MfParams &p, int *kerr, int *kstatus)
 int status_to_rc(int kerr, int kstatus)
 {
     if (kerr == MF_E_INVALID) return MAXFLOW_ERR_INVALID;
+    if (kerr == MF_E_TOO_LARGE) return MAXFLOW_ERR_TOO_LARGE;
     if (kerr == MF_E_WAIT || kerr == MF_E_INTERNAL) return MAXFLOW_ERR_INTERNAL;
     if (kerr != MF_E_NONE) return MAXFLOW_ERR_INTERNAL;
     if (kstatus == MF_ST_CAP) return MAXFLOW_ERR_NOT_CONVERGED;
@@ -468,8 +480,10 @@ int rebuild_device(maxflow_ctx *c)
     dfree(c, c->x_cf2);
     c->x_cf = c->x_cf2 = nullptr;
     dfree(c, c->sc.bitem);
+    dfree(c, c->sc.bdefer);
     c->sc.bitem = dalloc_n<int2>(c, (int64_t)n + total / MF_BFS_CHUNK + 64);
-    if (!c->sc.bitem) return MAXFLOW_ERR_OOM;
+    c->sc.bdefer = dalloc_n<int2>(c, (int64_t)n + total / MF_BFS_CHUNK + 64);
+    if (!c->sc.bitem || !c->sc.bdefer) return MAXFLOW_ERR_OOM;
     c->st.slot_capacity = total;
     c->st.rebuilds++;
     choose_grid(c);
@@ -581,8 +595,10 @@ int ensure_pp(maxflow_ctx *c)
     }
     if (q.items_for != c->g.slot_cap) {
         dfree(c, q.sc.bitem);
+        dfree(c, q.sc.bdefer);
         q.sc.bitem = dalloc_n<int2>(c, (int64_t)n + c->g.slot_cap / MF_BFS_CHUNK + 64);
-        if (!q.sc.bitem) return MAXFLOW_ERR_OOM;
+        q.sc.bdefer = dalloc_n<int2>(c, (int64_t)n + c->g.slot_cap / MF_BFS_CHUNK + 64);
+        if (!q.sc.bitem || !q.sc.bdefer) return MAXFLOW_ERR_OOM;
         q.items_for = c->g.slot_cap;
     }
     return rc_cuda(cudaStreamSynchronize(c->stream));
@@ -719,7 +735,10 @@ int maxflow_init(maxflow_ctx **out, const maxflow_graph *g, int32_t s, int32_t t
     }
     DeviceGuard dg(dev);
     rc = dg.ok ? MAXFLOW_OK : MAXFLOW_ERR_CUDA;
-    if (rc == MAXFLOW_OK) rc = mf_max_coresident_blocks(dev, &c->per_sm, &c->sms);
+    int stage_bytes = 0;
+    if (rc == MAXFLOW_OK) rc = mf_stage_bytes(dev, &stage_bytes);
+    if (rc == MAXFLOW_OK) rc = mf_max_coresident_blocks(dev, &c->per_sm, &c->sms, stage_bytes);
+    c->stage_slots = stage_bytes / (int)sizeof(int);
     if (rc == MAXFLOW_OK) rc = rc_cuda(cudaEventCreate(&c->ev0));
     if (rc == MAXFLOW_OK) rc = rc_cuda(cudaEventCreate(&c->ev1));
     if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMallocHost((void **)&c->hctrl, sizeof(MfCtrl)));
@@ -853,6 +872,19 @@ int maxflow_trace(maxflow_ctx *c, int32_t *boundary, double *t_us, int32_t cap, 
     for (int i = 0; i < k; ++i) {
         if (boundary) boundary[i] = h.trace_hook[i];
         if (t_us) t_us[i] = (double)(h.trace_t[i] - h.t_entry) * 1e-3;
+    }
+    *count = k;
+    return MAXFLOW_OK;
+}
+
+int maxflow_trace_work(maxflow_ctx *c, int64_t *slots, int32_t *info, int32_t cap, int32_t *count)
+{
+    if (!c || !count || cap < 0) return MAXFLOW_ERR_INVALID;
+    const MfCtrl &h = *c->hctrl;
+    int k = std::min<int>(h.trace_n, std::min<int>(cap, MF_TRACE));
+    for (int i = 0; i < k; ++i) {
+        if (slots) slots[i] = h.trace_slots[i];
+        if (info) info[i] = h.trace_info[i];
     }
     *count = k;
     return MAXFLOW_OK;
@@ -1101,7 +1133,7 @@ int maxflow_solve_batched(maxflow_ctx *const *ctxs, int32_t count, const maxflow
     unsigned long long wait_ns = plist[0].wait_limit_ns;
     MF_TRY(rc_cuda(cudaEventRecord(c0->ev0, c0->stream)));
     MF_TRY(counted(mf_launch_multi(c0->multi_plist, count, gsize, ngroups * gsize, gstate, head, wait_ns, abort_flag,
-                           (void *)c0->stream), 1));
+                           (void *)c0->stream, c0->stage_slots * (int)sizeof(int)), 1));
     MF_TRY(rc_cuda(cudaEventRecord(c0->ev1, c0->stream)));
     int abort_h = 0;
     MF_TRY(rc_cuda(cudaMemcpyAsync(&abort_h, abort_flag, sizeof(int), cudaMemcpyDeviceToHost, c0->stream)));
@@ -1437,7 +1469,7 @@ int maxflow_update_pp(maxflow_ctx *c, const maxflow_batch *b, int32_t stop_after
     MF_TRY(rc_cuda(cudaMemsetAsync(gstate, 0, sizeof(unsigned) * 32 * (size_t)(maxg + 2), c->stream)));
     MF_TRY(rc_cuda(cudaEventRecord(c->ev0, c->stream)));
     MF_TRY(counted(mf_launch_multi(c->multi_plist, 2, gsize, 2 * gsize, gstate, head, pl[0].wait_limit_ns, abort_flag,
-                           (void *)c->stream), 1));
+                           (void *)c->stream, c->stage_slots * (int)sizeof(int)), 1));
     MF_TRY(rc_cuda(cudaEventRecord(c->ev1, c->stream)));
     int abort_h = 0;
     MF_TRY(rc_cuda(cudaMemcpyAsync(&abort_h, abort_flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream)));
@@ -1502,6 +1534,7 @@ int maxflow_clone(maxflow_ctx *src, maxflow_ctx **out)
     c->hub_deg = src->hub_deg;
     c->bfs_hub = src->bfs_hub;
     c->per_sm = src->per_sm;
+    c->stage_slots = src->stage_slots;
     c->sms = src->sms;
     c->st = src->st;
     c->solved = src->solved;
@@ -1529,12 +1562,13 @@ int maxflow_clone(maxflow_ctx *src, maxflow_ctx **out)
         c->g.h = dalloc_n<int32_t>(c, n);
         c->g.e = dalloc_n<long long>(c, n);
         c->sc.bitem = dalloc_n<int2>(c, (int64_t)n + S / MF_BFS_CHUNK + 64);
+        c->sc.bdefer = dalloc_n<int2>(c, (int64_t)n + S / MF_BFS_CHUNK + 64);
         c->ctrl = (MfCtrl *)dalloc(c, sizeof(MfCtrl));
         c->dbuf = dalloc_n<long long>(c, 16);
         c->feat = dalloc_n<float>(c, MF_FEATURES);
         c->sched_y = dalloc_n<float>(c, 64);
         if (!c->g.off || !c->g.deg || !c->g.bdeg || !c->g.dst || !c->g.cf || !c->g.cap || !c->g.rev || !c->g.pcap ||
-            !c->g.h || !c->g.e || !c->sc.bitem || !c->ctrl || !c->dbuf || !c->feat || !c->sched_y)
+            !c->g.h || !c->g.e || !c->sc.bitem || !c->sc.bdefer || !c->ctrl || !c->dbuf || !c->feat || !c->sched_y)
             rc = MAXFLOW_ERR_OOM;
     }
     if (rc == MAXFLOW_OK) rc = alloc_vertex_scratch(c);
@@ -1685,6 +1719,11 @@ int maxflow_get_flow(maxflow_ctx *c, int64_t *count, int32_t *u, int32_t *v, int
     p.sink = c->s;
     p.source = c->t;
     p.mode = MF_M_SOLVE | MF_M_NO_DEFICIT_ROOTS;
+    // No Alg. 3 here: it moves whole residuals and can leave a deficit, which
+    // these runs do not take as a root; a deficit left in A would then be
+    // filled from t in (b) and lower the flow.  The loop's termination test
+    // after a full backward BFS does not depend on Alg. 3.
+    p.fix_steep = 0;
     int kerr = 0, kst = 0;
     MF_TRY(run_kernel(c, p, &kerr, &kst));
     int rc = status_to_rc(kerr, kst);

@@ -28,6 +28,9 @@
 #define MF_TRACE 256          // hook timeline entries kept per launch
 #define MF_BU_ALPHA 14        // BFS default: go bottom-up when the frontier's slots exceed the unexplored slots / alpha
 #define MF_BU_BETA 24         // BFS default: back to top-down when the frontier holds fewer than n / beta vertices
+#define MF_WARP_STAGE 512     // discharge: largest row a warp keeps on chip (per-warp slice of the snapshot)
+#define MF_BU_SCAN 32         // bottom-up BFS: slots of its row a thread scans itself before deferring the rest
+#define MF_BU_CHUNK 256       // bottom-up BFS: slots per deferred work item (one warp, 8 per lane)
 
 // Solve-kernel status (ctrl->status)
 #define MF_ST_RUNNING 0
@@ -41,6 +44,7 @@
 #define MF_E_OVERFLOW 2       // insertion needs more slack than a row has
 #define MF_E_WAIT 3           // a grid barrier wait gave up
 #define MF_E_INTERNAL 4
+#define MF_E_TOO_LARGE 5      // a batch would leave a pair with c(u,v) + c(v,u) > INT32_MAX
 
 // Kernel modes (bit mask)
 #define MF_M_STATIC_INIT 1    // c_f = cap, e = 0, h = 0, saturate the source (Alg. 1)
@@ -74,6 +78,7 @@ struct MfCtrl {
     MfLine wl_tail;       // w[0..2]: worklist append positions per bin
     MfLine misc;          // w[0]: insert list tail, w[1]: touched tail, w[2]: overflow flag
     MfLine aux_tail;      // w[0..2]: next-round worklist tails, w[3]/w[4]: remove-invalid lists (warp / CTA)
+    MfLine defer_tail;    // w[0]: bottom-up work items of long rows deferred to the level's second pass
     MfLine bfs_acc;       // 64-bit words: [0] slots of the vertices labelled in this level, [1] their number,
                           // [2] used slots of the whole graph (summed by the BFS initialisation)
     // ---- (hook) snapshots ----
@@ -91,6 +96,8 @@ struct MfCtrl {
     int qstamp, fstamp;   // dedupe stamps (never reset: they only grow across launches)
     unsigned long long t_bfs0, t_dis0;   // this iteration: BFS start, discharge start (adaptive rounds)
     int bu_mode;          // the coming BFS level runs bottom-up
+    int bu_split;         // the bottom-up level just scanned deferred long rows: their pass follows
+    int defer_n;          // work items of that pass
     int need_total;       // the coming BFS initialisation sums the used slots (first BFS of a launch)
     long long vis_slots;  // slots of the vertices labelled so far in this BFS
     long long iters;
@@ -99,6 +106,10 @@ struct MfCtrl {
     long long value;
     long long pushes, relabels, steep, bfs_levels, active_total, active_first;
     long long slots_bfs, verts_bfs, slots_dis, cycles_dis, slots_fix, verts_fix, verts_wl, n_apply;
+    long long lab_bfs;        // vertices labelled by all BFS levels
+    long long hscan_bfs;      // heights read by the passes over all vertices of bottom-up levels
+    long long slots_apply;    // slots read by the batch phases (slot search, source row)
+    long long clamps_apply;   // slots whose residual went negative and was sent back
     unsigned long long ns_bfs, ns_dis, ns_fix, ns_wl, ns_apply;
     int active_hist[MF_ACTIVE_HIST];
     long long rounds_total;
@@ -108,6 +119,11 @@ struct MfCtrl {
     int trace_n;
     int trace_hook[MF_TRACE];
     unsigned long long trace_t[MF_TRACE];
+    // work per traced phase: slots scanned so far (BFS + discharge + remove-invalid, cumulative), and
+    // BFS: bit 30 = the level ran bottom-up, bits 20..29 = work items, bits 0..19 = vertices labelled;
+    // discharge round: bits 20..29 = CTA-bin (hub) vertices, bits 0..19 = vertices in the round's lists
+    long long trace_slots[MF_TRACE];
+    int trace_info[MF_TRACE];
 };
 
 struct MfGraph {
@@ -122,6 +138,8 @@ struct MfGraph {
 struct MfScratch {
     int32_t *border;          // [n] BFS order (level segments)
     int2 *bitem;              // [n + slot_cap / MF_BFS_CHUNK + 64] frontier work items (first slot, length)
+    int2 *bdefer;             // [n + slot_cap / MF_BFS_CHUNK + 64] bottom-up deferred chunks (vertex, first slot);
+                              // nullptr: bottom-up threads scan whole rows themselves
     int32_t *wl[2][3];        // [n] worklists (two buffers for discharge rounds): small, mid, hub rows
     int32_t *vmark;           // [n] round stamp of the last time a vertex was queued
     int32_t *fixmark;         // [n] iteration stamp of the last time a vertex was listed for Alg. 3
@@ -167,6 +185,8 @@ struct MfParams {
                               // else only side[v] == side_root
     uint8_t *side;            // [n] sides of the last cut (1: reaches t or a deficit, 0: not); written by MF_M_CUT
     int32_t test_skip_cta;    // >= 0: that CTA never arrives at the first barrier (tests the bounded waits)
+    int32_t stage_slots;      // dynamic shared memory of the launch in ints: the discharge's on-chip row snapshot
+                              // (a CTA keeps rows up to this many slots; 0: none)
     long long max_iters;
     unsigned long long time_limit_ns;
     unsigned long long wait_limit_ns;
@@ -192,8 +212,9 @@ int mf_build_host(int32_t n, int64_t m, const int32_t *src, const int32_t *dst, 
 // solver.cu
 int mf_launch(const MfParams &p, int grid, void *stream);
 int mf_launch_multi(const MfParams *plist_dev, int count, int gsize, int grid, unsigned *gstate, unsigned *head,
-                    unsigned long long wait_ns, int *abort, void *stream);
-int mf_max_coresident_blocks(int device, int *per_sm, int *num_sms);
+                    unsigned long long wait_ns, int *abort, void *stream, int stage_bytes);
+int mf_stage_bytes(int device, int *bytes);
+int mf_max_coresident_blocks(int device, int *per_sm, int *num_sms, int dyn_bytes);
 int mf_launch_aux(int which, const MfParams &p, void *stream, long long *dev_out, const void *extra);
 
 #define MF_AUX_SET_CF_RESET 1     // cf = cap on all used slots

@@ -34,36 +34,41 @@ constexpr size_t kCtrlBytes = (sizeof(MfCtrl) + 255) & ~(size_t)255;
 constexpr size_t kListBytes = (sizeof(int32_t) * (size_t)MAXFLOW_NOALLOC_MAX_N + 255) & ~(size_t)255;
 constexpr size_t kItemBytes =
     sizeof(int2) * ((size_t)MAXFLOW_NOALLOC_MAX_N + (size_t)MAXFLOW_NOALLOC_MAX_SLOTS / MF_BFS_CHUNK + 64);
-constexpr size_t kScratchBytes = kCtrlBytes + kListBytes + kItemBytes;
+// a two-vertex graph with no slots (off, deg, e, h), for the prepare call
+constexpr size_t kPrepBytes = 256;
+constexpr size_t kScratchBytes = kCtrlBytes + kListBytes + kItemBytes + kPrepBytes;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 struct DeviceSetup {
     bool ready = false;
-    unsigned char *base = nullptr;  // device address of g_noalloc_scratch on this device
-    int per_sm = 0, sms = 0;
+    int per_sm = 0, sms = 0;        // co-resident CTAs of the solve kernel (a property of the device)
 };
 
 constexpr int kMaxDevices = 64;
 DeviceSetup g_setup[kMaxDevices];
 std::mutex g_setup_mu;
 
-// Once per device, with that device current: the device address of the
-// scratch array (host code cannot use the symbol itself as a device pointer).
-int setup_device(int dev, DeviceSetup **out)
+// With the device current: the device address of the scratch array (host
+// code cannot use the symbol itself as a device pointer), looked up on every
+// call -- after a cudaDeviceReset the module is loaded again at another
+// address -- and the occupancy of the solve kernel, queried once per device.
+// Both lookups make the driver load the modules that hold the array and the
+// kernel if it has not yet (lazy loading), which is what the n = 0 call is for.
+int setup_device(int dev, DeviceSetup **out, unsigned char **base)
 {
     if (dev < 0 || dev >= kMaxDevices) return MAXFLOW_ERR_INVALID;
+    void *ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || ptr == nullptr) return MAXFLOW_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_setup_mu);
     DeviceSetup &d = g_setup[dev];
     if (!d.ready) {
-        void *ptr = nullptr;
-        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || ptr == nullptr) return MAXFLOW_ERR_CUDA;
-        int rc = mf_max_coresident_blocks(dev, &d.per_sm, &d.sms);
+        int rc = mf_max_coresident_blocks(dev, &d.per_sm, &d.sms, 0);
         if (rc != MAXFLOW_OK) return rc;
-        d.base = (unsigned char *)ptr;
         d.ready = true;
     }
     *out = &d;
+    *base = (unsigned char *)ptr;
     return MAXFLOW_OK;
 }
 
@@ -74,16 +79,30 @@ extern "C" int maxflow_global_relabel_noalloc(int32_t n, int32_t s, int32_t t, c
                                               const int32_t *pcap, const int64_t *e, int32_t *h,
                                               int32_t deficit_roots, void *stream)
 {
-    if (n < 2 || s < 0 || t < 0 || s >= n || t >= n || s == t) return MAXFLOW_ERR_INVALID;
     if (n > MAXFLOW_NOALLOC_MAX_N) return MAXFLOW_ERR_TOO_LARGE;
-    if (!off || !deg || !dst || !cf || !pcap || !e || !h) return MAXFLOW_ERR_INVALID;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return MAXFLOW_ERR_CUDA;
     DeviceSetup *ds = nullptr;
-    int rc = setup_device(dev, &ds);
+    unsigned char *base = nullptr;
+    if (n == 0) {
+        // prepare the device: load the modules (setup_device), then run the step
+        // once on a two-vertex graph without slots held in the array itself, so
+        // that nothing the driver sets up at a first launch is left for later calls
+        int rc = setup_device(dev, &ds, &base);
+        if (rc != MAXFLOW_OK) return rc;
+        unsigned char *g2 = base + kCtrlBytes + kListBytes + kItemBytes;
+        if (cudaMemsetAsync(g2, 0, kPrepBytes, (cudaStream_t)stream) != cudaSuccess) return MAXFLOW_ERR_CUDA;
+        int32_t *o = (int32_t *)g2;                       // off[3] = 0, deg[2] = 0
+        int64_t *e2 = (int64_t *)(g2 + 64);               // e[2] = 0
+        int32_t *h2 = (int32_t *)(g2 + 128);
+        return maxflow_global_relabel_noalloc(2, 0, 1, o, o + 4, o, o, o, e2, h2, deficit_roots, stream);
+    }
+    if (n < 2 || s < 0 || t < 0 || s >= n || t >= n || s == t) return MAXFLOW_ERR_INVALID;
+    if (!off || !deg || !dst || !cf || !pcap || !e || !h) return MAXFLOW_ERR_INVALID;
+    int rc = setup_device(dev, &ds, &base);
     if (rc != MAXFLOW_OK) return rc;
 
-    MfCtrl *ctrl = (MfCtrl *)ds->base;
+    MfCtrl *ctrl = (MfCtrl *)base;
     MfParams p;
     std::memset(&p, 0, sizeof(p));
     p.g.n = n;
@@ -94,8 +113,9 @@ extern "C" int maxflow_global_relabel_noalloc(int32_t n, int32_t s, int32_t t, c
     p.g.cf = const_cast<int32_t *>(cf);
     p.g.h = h;
     p.g.e = (long long *)const_cast<int64_t *>(e);
-    p.sc.border = (int32_t *)(ds->base + kCtrlBytes);
-    p.sc.bitem = (int2 *)(ds->base + kCtrlBytes + kListBytes);
+    p.sc.border = (int32_t *)(base + kCtrlBytes);
+    p.sc.bitem = (int2 *)(base + kCtrlBytes + kListBytes);
+    p.sc.bdefer = nullptr;          // bottom-up threads scan whole rows (no deferred chunks: no room for them)
     p.ctrl = ctrl;
     p.cf = p.g.cf;
     p.h = h;

@@ -23,6 +23,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "../../include/maxflow.h"
 #include "mf_internal.h"
 
@@ -34,6 +36,10 @@ constexpr unsigned long long kEmpty = ~0ull;
 // of the grid for mf_multi_kernel.  Every phase distributes its work over
 // vb() in [0, vn()), and the grid barrier waits for vn() CTAs.
 __shared__ int g_vb, g_vn;
+
+// Dynamic shared memory of the persistent kernels: the on-chip snapshot of a
+// row during its discharge (P.stage_slots ints).
+extern __shared__ __align__(16) int mf_stage[];
 __device__ __forceinline__ int vb() { return g_vb; }
 __device__ __forceinline__ int vn() { return g_vn; }
 
@@ -129,6 +135,7 @@ enum Hook {
     H_WL,
     H_DIS,
     H_FINAL,
+    H_BU_SPLIT,
 };
 
 __device__ __forceinline__ int rd(const int &x) { return __ldcg(&x); }
@@ -169,11 +176,25 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
 {
     MfCtrl *c = P.ctrl;
     const unsigned long long now = gtimer();
+    if (hook == H_BU_SPLIT) {
+        // after the first pass of a bottom-up level: a second pass over the
+        // deferred long rows, or (none deferred) the level is complete
+        const unsigned dn = rd(c->defer_tail.w[0]);
+        if (dn == 0) {
+            c->bu_split = 0;
+            hook = H_BFS_NEXT;
+        } else {
+            c->bu_split = 1;
+            c->defer_n = (int)dn;
+            c->defer_tail.w[0] = 0;
+            c->head1.w[0] = 0;
+        }
+    }
     const unsigned long long t_phase = rd(c->t_phase);
     const int trace_n = hook == H_START ? 0 : rd(c->trace_n);
     const long long barriers = hook == H_START ? 0 : rd(c->barriers);
     const unsigned bfs_tail = rd(c->bfs_tail.w[0]), item_tail = rd(c->hub_tail.w[0]);
-    const int lvl_hi = rd(c->lvl_hi), hub_hi = rd(c->hub_hi), level = rd(c->level);
+    const int lvl_hi = rd(c->lvl_hi), hub_hi = rd(c->hub_hi), level = rd(c->level), hub_lo_old = rd(c->hub_lo);
     const long long iters = rd(c->iters), bfs_levels = rd(c->bfs_levels);
     const unsigned long long t_start = rd(c->t_start);
     unsigned wl[4], misc[4];
@@ -185,6 +206,11 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
     for (int i = 0; i < 5; ++i) aux[i] = rd(c->aux_tail.w[i]);
     const int sel = rd(c->wl_sel), round = rd(c->round), qstamp = rd(c->qstamp), fstamp = rd(c->fstamp);
     const long long rounds_total = rd(c->rounds_total);
+    const long long slots_all = rd(c->slots_bfs) + rd(c->slots_dis) + rd(c->slots_fix);
+    const int bu_prev = rd(c->bu_mode);
+    int wl_prev[3];
+    for (int b = 0; b < 3; ++b) wl_prev[b] = rd(c->wl_n[b]);
+    int tinfo = 0;
     unsigned err = rd(c->err.w[0]);
     const unsigned long long dt = now - t_phase;
     const bool want_wl = P.data_driven && !(P.mode & MF_M_BFS_ONLY);
@@ -192,10 +218,6 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
     c->t_phase = now;
     c->barriers = barriers + 1;
     c->t_exit = now;
-    if (trace_n < MF_TRACE) {
-        c->trace_hook[trace_n] = hook;
-        c->trace_t[trace_n] = now;
-    }
     c->trace_n = trace_n + 1;
     switch (hook) {
     case H_START:
@@ -207,9 +229,12 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
         c->pushes = c->relabels = c->steep = c->bfs_levels = c->active_total = c->active_first = 0;
         c->slots_bfs = c->verts_bfs = c->slots_dis = c->cycles_dis = c->slots_fix = c->verts_fix = 0;
         c->verts_wl = c->n_apply = 0;
+        c->lab_bfs = c->slots_apply = c->clamps_apply = c->hscan_bfs = 0;
         c->ns_bfs = c->ns_dis = c->ns_fix = c->ns_wl = c->ns_apply = 0;
         c->bfs_tail.w[0] = 0;
         c->hub_tail.w[0] = 0;
+        c->defer_tail.w[0] = 0;
+        c->bu_split = 0;
         c->head0.w[0] = c->head1.w[0] = c->head2.w[0] = 0;
         for (int i = 0; i < 4; ++i) c->wl_tail.w[i] = 0;
         for (int i = 0; i < 8; ++i) c->misc.w[i] = 0;
@@ -277,6 +302,8 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
             const long long fr = (long long)__ldcg(acc + 0), cnt = (long long)__ldcg(acc + 1);
             const long long tot = (long long)__ldcg(acc + 2);
             const long long vis = (first ? 0 : rd(c->vis_slots)) + fr;
+            tinfo = ((first ? 0 : bu_prev) << 30) | ((first ? 0 : min(hub_hi - hub_lo_old, 1023)) << 20) |
+                    (int)min(cnt, (long long)((1 << 20) - 1));
             int bu = first ? 0 : rd(c->bu_mode);
             if (P.bu_alpha <= 0) bu = 0;
             else if (!bu && fr * P.bu_alpha > tot - vis) bu = 1;
@@ -296,6 +323,7 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
         // after a discharge round: run another one over the vertices that
         // became active during it, or end the discharge of this iteration
         c->ns_dis = rd(c->ns_dis) + dt;
+        tinfo = (min(wl_prev[2], 1023) << 20) | min(wl_prev[0] + wl_prev[1] + wl_prev[2], (1 << 20) - 1);
         c->head0.w[0] = c->head1.w[0] = c->head2.w[0] = 0;
         c->rounds_total = rounds_total + 1;
         const unsigned nxt = aux[0] + aux[1] + aux[2];
@@ -330,6 +358,16 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
     }
     case H_FINAL:
         break;
+    case H_BU_SPLIT:
+        c->ns_bfs = rd(c->ns_bfs) + dt;
+        tinfo = (1 << 30) | (int)min((long long)rd(c->defer_n), (long long)((1 << 20) - 1));
+        break;
+    }
+    if (trace_n < MF_TRACE) {
+        c->trace_hook[trace_n] = hook;
+        c->trace_t[trace_n] = now;
+        c->trace_slots[trace_n] = slots_all;
+        c->trace_info[trace_n] = tinfo;
     }
     if (err != 0) c->status = MF_ST_ERROR;
 }
@@ -396,6 +434,7 @@ __device__ void flush_acc(const MfParams &P, Sh &sh, int phase)
             if (phase == 0) {
                 atomic_add_ll(&c->slots_bfs, sh.slots);
                 atomic_add_ll(&c->verts_bfs, sh.verts);
+                atomic_add_ll(&c->hscan_bfs, sh.cycles);
             } else if (phase == 1) {
                 atomic_add_ll(&c->slots_dis, sh.slots);
                 atomic_add_ll(&c->cycles_dis, sh.cycles);
@@ -406,9 +445,12 @@ __device__ void flush_acc(const MfParams &P, Sh &sh, int phase)
                 atomic_add_ll(&c->verts_wl, sh.verts);
             } else {
                 atomic_add_ll(&c->n_apply, sh.verts);
+                atomic_add_ll(&c->slots_apply, sh.slots);
+                atomic_add_ll(&c->clamps_apply, sh.cycles);
             }
         }
         if (sh.lab_cnt) {
+            atomic_add_ll(&c->lab_bfs, sh.lab_cnt);
             unsigned long long *acc = (unsigned long long *)c->bfs_acc.w;
             atomicAdd(acc + 0, (unsigned long long)sh.lab_slots);
             atomicAdd(acc + 1, (unsigned long long)sh.lab_cnt);
@@ -435,11 +477,26 @@ __device__ __forceinline__ void add_excess(const MfParams &P, Sh &sh, int z, lon
 // Static initialisation (Alg. 1)
 // ---------------------------------------------------------------------------
 
+// c_f = c on every slot, e = h = 0: a streaming copy, 16-byte vectors with four
+// in flight per thread (the slot arrays start on 256-byte boundaries).
 __device__ __noinline__ void phase_static_reset(const MfParams &P)
 {
     const long long gt = (long long)vb() * blockDim.x + threadIdx.x;
     const long long gs = (long long)vn() * blockDim.x;
-    for (long long x = gt; x < P.g.slot_cap; x += gs) P.cf[x] = __ldcg(P.g.cap + x);
+    const long long n4 = P.g.slot_cap >> 2;
+    const int4 *src = reinterpret_cast<const int4 *>(P.g.cap);
+    int4 *dst = reinterpret_cast<int4 *>(P.cf);
+    long long x = gt;
+    for (; x + 3 * gs < n4; x += 4 * gs) {
+        const int4 a = __ldcs(src + x), b = __ldcs(src + x + gs), c = __ldcs(src + x + 2 * gs),
+                   d = __ldcs(src + x + 3 * gs);
+        __stcg(dst + x, a);
+        __stcg(dst + x + gs, b);
+        __stcg(dst + x + 2 * gs, c);
+        __stcg(dst + x + 3 * gs, d);
+    }
+    for (; x < n4; x += gs) __stcg(dst + x, __ldcs(src + x));
+    for (long long y = (n4 << 2) + gt; y < P.g.slot_cap; y += gs) P.cf[y] = __ldcg(P.g.cap + y);
     for (long long v = gt; v < P.g.n; v += gs) {
         P.e[v] = 0;
         P.h[v] = 0;
@@ -532,6 +589,20 @@ __device__ __noinline__ void phase_saturate_cut(const MfParams &P, Sh &sh)
     }
 }
 
+// Append val to arr for the lanes with take, one atomic per warp.  Called by
+// the whole warp.
+__device__ __forceinline__ void warp_append(unsigned *tail, int *arr, bool take, int val)
+{
+    const unsigned m = __ballot_sync(0xffffffffu, take);
+    if (m == 0) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(tail, (unsigned)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (take) arr[base + __popc(m & ((1u << lane) - 1u))] = val;
+}
+
 // ---------------------------------------------------------------------------
 // Batch apply and repair (Alg. 5)
 // ---------------------------------------------------------------------------
@@ -551,45 +622,75 @@ __device__ __noinline__ void phase_apply_validate(const MfParams &P)
     MfCtrl *ctl = P.ctrl;
     const int bits = P.sc.hash_bits;
     const unsigned mask = (1u << bits) - 1u;
-    for (long long i = (long long)vb() * blockDim.x + threadIdx.x; i < P.bcount;
-         i += (long long)vn() * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    // warp-uniform loop: the positions taken in the table are appended with one atomic per warp
+    for (long long base = (long long)vb() * blockDim.x + threadIdx.x - lane; base < P.bcount;
+         base += (long long)vn() * blockDim.x) {
+        const long long i = base + lane;
+        bool fresh = false;
+        unsigned pos = 0;
         int u, v, c;
-        if (!batch_entry(P, i, u, v, c)) {
-            atomicCAS(&ctl->err.w[0], 0u, (unsigned)MF_E_INVALID);
-            continue;
-        }
-        if (u == v) continue;
-        unsigned long long key = ((unsigned long long)(unsigned)u << 32) | (unsigned)v;
-        unsigned pos = hash_slot(key, bits);
-        for (unsigned probe = 0; probe <= mask; ++probe) {
-            unsigned long long prev = atomicCAS(P.sc.hkey + pos, kEmpty, key);
-            if (prev == kEmpty || prev == key) {
-                if (prev == kEmpty) {
-                    unsigned k = atomicAdd(&ctl->misc.w[3], 1u);
-                    P.sc.hused[k] = (int)pos;       // positions to clear afterwards
+        if (i < P.bcount) {
+            if (!batch_entry(P, i, u, v, c)) {
+                atomicCAS(&ctl->err.w[0], 0u, (unsigned)MF_E_INVALID);
+            } else if (u != v) {
+                unsigned long long key = ((unsigned long long)(unsigned)u << 32) | (unsigned)v;
+                pos = hash_slot(key, bits);
+                for (unsigned probe = 0; probe <= mask; ++probe) {
+                    unsigned long long prev = atomicCAS(P.sc.hkey + pos, kEmpty, key);
+                    if (prev == kEmpty || prev == key) {
+                        fresh = prev == kEmpty;
+                        atomicMax(P.sc.hval + pos, (int)i);
+                        break;
+                    }
+                    pos = (pos + 1u) & mask;
                 }
-                atomicMax(P.sc.hval + pos, (int)i);
-                break;
             }
-            pos = (pos + 1u) & mask;
         }
+        warp_append(&ctl->misc.w[3], P.sc.hused, fresh, (int)pos);   // positions to clear afterwards
     }
 }
 
-__device__ __forceinline__ int find_slot(const MfParams &P, int u, int v)
+// Slot of (u, v) in u's row, or -1: an 8-way search of the sorted base slots
+// (seven pivots loaded together per round, so a row of 2^15 slots takes five
+// dependent rounds instead of fifteen), then a scan of the inserted slots.
+// *probes counts the dst entries read.
+__device__ __forceinline__ int find_slot(const MfParams &P, int u, int v, int *probes = nullptr)
 {
     const int r0 = P.g.off[u];
-    int lo = r0, hi = r0 + ldg_cg(P.g.bdeg + u);
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if (ldg_cg(P.g.dst + mid) < v) lo = mid + 1;
-        else hi = mid;
+    const int bd = ldg_cg(P.g.bdeg + u);
+    int lo = r0, hi = r0 + bd;      // the first base slot with dst >= v lies in [lo, hi]
+    int k = 0;
+    while (hi - lo > 8) {
+        const int step = (hi - lo) >> 3;
+        int below = 0;
+#pragma unroll
+        for (int q = 1; q < 8; ++q) below += ldg_cg(P.g.dst + lo + q * step) < v ? 1 : 0;
+        k += 7;
+        const int nlo = below > 0 ? lo + below * step + 1 : lo;
+        if (below < 7) hi = lo + (below + 1) * step;
+        lo = nlo;
     }
-    if (lo < r0 + ldg_cg(P.g.bdeg + u) && ldg_cg(P.g.dst + lo) == v) return lo;
-    const int end = r0 + ldg_cg(P.g.deg + u);
-    for (int x = r0 + ldg_cg(P.g.bdeg + u); x < end; ++x)
-        if (ldg_cg(P.g.dst + x) == v) return x;
-    return -1;
+    int below = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) below += (lo + q < hi && ldg_cg(P.g.dst + lo + q) < v) ? 1 : 0;
+    k += hi - lo;
+    int found = -1;
+    const int lb = lo + below;
+    if (lb < r0 + bd && ldg_cg(P.g.dst + lb) == v) found = lb;
+    ++k;
+    if (found < 0) {
+        const int end = r0 + ldg_cg(P.g.deg + u);
+        for (int x = r0 + bd; x < end; ++x) {
+            ++k;
+            if (ldg_cg(P.g.dst + x) == v) {
+                found = x;
+                break;
+            }
+        }
+    }
+    if (probes) *probes += k;
+    return found;
 }
 
 __device__ __forceinline__ unsigned hash_find(const unsigned long long *keys, int bits, unsigned long long key)
@@ -606,45 +707,65 @@ __device__ __forceinline__ unsigned hash_find(const unsigned long long *keys, in
 }
 
 // Locate the slot of every surviving update; a missing pair is entered once
-// into the new-pair table and counted against both rows' spare slots.
-__device__ __noinline__ void phase_apply_locate(const MfParams &P)
+// into the new-pair table and counted against both rows' spare slots.  The
+// pair sum the batch leaves behind is checked here, before anything changes:
+// c' plus the final capacity of the reverse direction -- the batch's own
+// update of (v, u) if it has one, else the current c(v, u), else 0 for a new
+// pair -- must fit int32 (residual capacities are int32 and c_f(u,v) +
+// c_f(v,u) equals that sum).  A batch that breaks it sets MF_E_TOO_LARGE and
+// is refused whole.
+__device__ __noinline__ void phase_apply_locate(const MfParams &P, Sh &sh)
 {
     MfCtrl *ctl = P.ctrl;
     const int bits = P.sc.hash_bits;
     const unsigned mask = (1u << bits) - 1u;
-    for (long long i = (long long)vb() * blockDim.x + threadIdx.x; i < P.bcount;
-         i += (long long)vn() * blockDim.x) {
-        int u, v, c;
-        batch_entry(P, i, u, v, c);
-        if (u == v) {
-            P.sc.bslot[i] = -2;
-            continue;
-        }
+    const int lane = threadIdx.x & 31;
+    int probes = 0;
+    for (long long base = (long long)vb() * blockDim.x + threadIdx.x - lane; base < P.bcount;
+         base += (long long)vn() * blockDim.x) {
+        const long long i = base + lane;
+        bool fresh = false;
+        unsigned pp = 0;
+        int u = 0, v = 0, c = 0;
+        if (i < P.bcount) batch_entry(P, i, u, v, c);
         unsigned long long key = ((unsigned long long)(unsigned)u << 32) | (unsigned)v;
-        unsigned pos = hash_find(P.sc.hkey, bits, key);
-        if (pos == 0xffffffffu || __ldcg(P.sc.hval + pos) != (int)i) {
-            P.sc.bslot[i] = -2;     // a later update of the same pair wins
-            continue;
-        }
-        int x = find_slot(P, u, v);
-        P.sc.bslot[i] = x;
-        if (x >= 0) continue;
-        int a = min(u, v), b = max(u, v);
-        unsigned long long pk = ((unsigned long long)(unsigned)a << 32) | (unsigned)b;
-        unsigned pp = hash_slot(pk, bits);
-        for (unsigned probe = 0; probe <= mask; ++probe) {
-            unsigned long long prev = atomicCAS(P.sc.pkey + pp, kEmpty, pk);
-            if (prev == kEmpty) {
-                unsigned k = atomicAdd(&ctl->misc.w[0], 1u);
-                P.sc.ins_list[k] = (int)pp;
-                atomicAdd(P.sc.ins_need + a, 1);
-                atomicAdd(P.sc.ins_need + b, 1);
-                break;
+        const unsigned pos = (i < P.bcount && u != v) ? hash_find(P.sc.hkey, bits, key) : 0xffffffffu;
+        if (i >= P.bcount) {
+            // past the batch
+        } else if (pos == 0xffffffffu || __ldcg(P.sc.hval + pos) != (int)i) {
+            P.sc.bslot[i] = -2;     // a self-loop, or a later update of the same pair wins
+        } else {
+            const int x = find_slot(P, u, v, &probes);
+            P.sc.bslot[i] = x;
+            {
+                const unsigned long long rkey = ((unsigned long long)(unsigned)v << 32) | (unsigned)u;
+                const unsigned rp = hash_find(P.sc.hkey, bits, rkey);
+                long long crev = 0;
+                if (rp != 0xffffffffu) crev = __ldcg(P.bc + __ldcg(P.sc.hval + rp));
+                else if (x >= 0) crev = ldg_cg(P.g.cap + ldg_cg(P.g.rev + x));
+                if ((long long)c + crev > (long long)INT32_MAX)
+                    atomicCAS(&ctl->err.w[0], 0u, (unsigned)MF_E_TOO_LARGE);
             }
-            if (prev == pk) break;
-            pp = (pp + 1u) & mask;
+            if (x < 0) {
+                const int a = min(u, v), b = max(u, v);
+                const unsigned long long pk = ((unsigned long long)(unsigned)a << 32) | (unsigned)b;
+                pp = hash_slot(pk, bits);
+                for (unsigned probe = 0; probe <= mask; ++probe) {
+                    unsigned long long prev = atomicCAS(P.sc.pkey + pp, kEmpty, pk);
+                    if (prev == kEmpty) {
+                        fresh = true;
+                        atomicAdd(P.sc.ins_need + a, 1);
+                        atomicAdd(P.sc.ins_need + b, 1);
+                        break;
+                    }
+                    if (prev == pk) break;
+                    pp = (pp + 1u) & mask;
+                }
+            }
         }
+        warp_append(&ctl->misc.w[0], P.sc.ins_list, fresh, (int)pp);   // each new pair once
     }
+    if (probes) atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)probes);
 }
 
 __device__ __noinline__ void phase_apply_check(const MfParams &P)
@@ -660,90 +781,77 @@ __device__ __noinline__ void phase_apply_check(const MfParams &P)
     }
 }
 
-__device__ __noinline__ void phase_apply_insert(const MfParams &P)
+// Winning new capacity of the directed pair (a, b) in the batch, or -1 if the
+// batch does not set it.
+__device__ __forceinline__ int batch_cap_of(const MfParams &P, int a, int b)
+{
+    const unsigned long long key = ((unsigned long long)(unsigned)a << 32) | (unsigned)b;
+    const unsigned pos = hash_find(P.sc.hkey, P.sc.hash_bits, key);
+    return pos == 0xffffffffu ? -1 : __ldcg(P.bc + __ldcg(P.sc.hval + pos));
+}
+
+// Alg. 5, capacity step, in one phase: (1) every new pair gets its two slots,
+// with the batch's capacities set directly (no flow runs on a new pair, so
+// c_f = c); (2) every located update sets c(u,v) = c', adds c' - c to c_f(u,v)
+// and to both pair sums, and when c_f(u,v) drops below zero sends the
+// difference back (the clamp step: c_f(v,u) -= d, e(u) += d, e(v) -= d).
+// The dedup table gives every directed pair one owner; the only other writer
+// of c_f(u,v) is the owner of (v,u), and the two clamps cannot both fire (the
+// pair's residuals sum to the new c(u,v) + c(v,u) >= 0), so the order of the
+// atomics does not matter.
+__device__ __noinline__ void phase_apply_change(const MfParams &P, Sh &sh)
 {
     MfCtrl *ctl = P.ctrl;
     const int nins = vrd(&ctl->ins_n);
+    long long applied = 0, clamped = 0;
     for (int k = vb() * blockDim.x + threadIdx.x; k < nins; k += vn() * blockDim.x) {
         int pp = __ldcg(P.sc.ins_list + k);
         unsigned long long pk = __ldcg(P.sc.pkey + pp);
         int a = (int)(pk >> 32), b = (int)(pk & 0xffffffffu);
-        int xa = P.g.off[a] + atomicAdd(P.g.deg + a, 1);
-        int xb = P.g.off[b] + atomicAdd(P.g.deg + b, 1);
+        const int ca = batch_cap_of(P, a, b), cb = batch_cap_of(P, b, a);
+        const int xa = P.g.off[a] + atomicAdd(P.g.deg + a, 1);
+        const int xb = P.g.off[b] + atomicAdd(P.g.deg + b, 1);
+        const int va = ca > 0 ? ca : 0, vb2 = cb > 0 ? cb : 0;
         P.g.dst[xa] = b;
         P.g.dst[xb] = a;
         P.g.rev[xa] = xb;
         P.g.rev[xb] = xa;
-        P.g.cap[xa] = P.g.cap[xb] = 0;
-        P.g.pcap[xa] = P.g.pcap[xb] = 0;
-        P.cf[xa] = P.cf[xb] = 0;
+        P.g.cap[xa] = va;
+        P.g.cap[xb] = vb2;
+        P.g.pcap[xa] = P.g.pcap[xb] = va + vb2;
+        P.cf[xa] = va;
+        P.cf[xb] = vb2;
         P.sc.pval[pp] = xa;
         P.sc.ins_need[a] = 0;
         P.sc.ins_need[b] = 0;
+        applied += (ca >= 0 ? 1 : 0) + (cb >= 0 ? 1 : 0);
     }
-}
-
-// Alg. 5, capacity step: c_f(u,v) += c' - c; cap(u,v) = c'.
-__device__ __noinline__ void phase_apply_delta(const MfParams &P, Sh &sh)
-{
-    MfCtrl *ctl = P.ctrl;
-    const int bits = P.sc.hash_bits;
-    long long applied = 0;
     for (long long i = (long long)vb() * blockDim.x + threadIdx.x; i < P.bcount;
          i += (long long)vn() * blockDim.x) {
-        int x = __ldcg(P.sc.bslot + i);
-        if (x == -2) continue;
+        const int x = __ldcg(P.sc.bslot + i);
+        if (x < 0) continue;                 // superseded, ignored, or a new pair (set above)
         int u, v, c;
         batch_entry(P, i, u, v, c);
-        if (x == -1) {
-            int a = min(u, v), b = max(u, v);
-            unsigned long long pk = ((unsigned long long)(unsigned)a << 32) | (unsigned)b;
-            unsigned pp = hash_find(P.sc.pkey, bits, pk);
-            if (pp == 0xffffffffu) {
-                atomicCAS(&ctl->err.w[0], 0u, (unsigned)MF_E_INTERNAL);
-                continue;
-            }
-            int xa = __ldcg(P.sc.pval + pp);
-            x = (u == a) ? xa : ldg_cg(P.g.rev + xa);
-            P.sc.bslot[i] = x;
-        }
-        int old = ldg_cg(P.g.cap + x);
-        int delta = c - old;
+        const int old = ldg_cg(P.g.cap + x);
+        const int delta = c - old;
         ++applied;
         if (delta == 0) continue;
+        const int y = ldg_cg(P.g.rev + x);
         P.g.cap[x] = c;
-        atomicAdd(P.cf + x, delta);
+        const int cf_new = atomicAdd(P.cf + x, delta) + delta;
         atomicAdd(P.g.pcap + x, delta);
-        atomicAdd(P.g.pcap + ldg_cg(P.g.rev + x), delta);
-        if (delta < 0) {
-            unsigned k = atomicAdd(&ctl->misc.w[1], 1u);
-            P.sc.clamp[k] = (int)i;
+        atomicAdd(P.g.pcap + y, delta);
+        if (cf_new < 0) {
+            const int d = -cf_new;
+            atomicAdd(P.cf + x, d);
+            atomicAdd(P.cf + y, -d);
+            add_excess(P, sh, u, (long long)d);
+            add_excess(P, sh, v, -(long long)d);
+            ++clamped;
         }
     }
     if (applied) atomicAdd((unsigned long long *)&sh.verts, (unsigned long long)applied);
-}
-
-// The clamp step of Alg. 5 on the slots whose capacity went down, with the excess
-// change of the flow sent back; then clear the hash tables for the next batch.
-__device__ __noinline__ void phase_apply_clamp(const MfParams &P, Sh &sh)
-{
-    MfCtrl *ctl = P.ctrl;
-    const int nt = vrd(&ctl->touch_n);
-    const long long gt = (long long)vb() * blockDim.x + threadIdx.x;
-    const long long gs = (long long)vn() * blockDim.x;
-    for (long long k = gt; k < nt; k += gs) {
-        long long i = __ldcg(P.sc.clamp + k);
-        int x = __ldcg(P.sc.bslot + i);
-        int cfx = ldg_cg(P.cf + x);
-        if (cfx < 0) {
-            int u = __ldcg(P.bu + i), v = __ldcg(P.bv + i);
-            int d = -cfx;
-            atomicAdd(P.cf + x, d);
-            atomicAdd(P.cf + ldg_cg(P.g.rev + x), -d);
-            add_excess(P, sh, u, (long long)d);
-            add_excess(P, sh, v, -(long long)d);
-        }
-    }
+    if (clamped) atomicAdd((unsigned long long *)&sh.cycles, (unsigned long long)clamped);
 }
 
 // keep_need: leave ins_need[] as it is (the rows' demand of spare slots after
@@ -779,6 +887,7 @@ __device__ __noinline__ void phase_resaturate(const MfParams &P, Sh &sh)
     const int r0 = P.g.off[s];
     const int d = ldg_cg(P.g.deg + s);
     long long acc = 0;
+    if (vb() == 0 && threadIdx.x == 0) atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)d);
     for (int j = vb() * blockDim.x + threadIdx.x; j < d; j += vn() * blockDim.x) {
         int x = r0 + j;
         int c = ldg_cg(P.cf + x);
@@ -796,17 +905,6 @@ __device__ __noinline__ void phase_resaturate(const MfParams &P, Sh &sh)
 // Backward BFS (Alg. 4 / Alg. 6)
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ void warp_append(unsigned *tail, int *arr, bool take, int val)
-{
-    const unsigned m = __ballot_sync(0xffffffffu, take);
-    if (m == 0) return;
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(m) - 1;
-    unsigned base = 0;
-    if (lane == leader) base = atomicAdd(tail, (unsigned)__popc(m));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (take) arr[base + __popc(m & ((1u << lane) - 1u))] = val;
-}
 
 // Labelled vertices enter the next frontier either as one entry of the
 // regular list (rows of at most bfs_hub slots, expanded warp-cooperatively)
@@ -886,24 +984,30 @@ __device__ __forceinline__ void frontier_push(const MfParams &P, Sh &sh, const b
             }
         }
     }
-    // long rows: the whole warp writes each row's work items
-    unsigned bm = __ballot_sync(0xffffffffu, anybig);
-    while (bm) {
-        const int src = __ffs(bm) - 1;
-        bm &= bm - 1u;
+    // long rows: ceil(deg / MF_BFS_CHUNK) work items each, reserved for the whole
+    // warp with one scan and one atomic; every lane then writes its own rows' items
+    if (__any_sync(0xffffffffu, anybig)) {
+        int nch = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (take[r] && d[r] > P.bfs_hub) nch += (d[r] + MF_BFS_CHUNK - 1) / MF_BFS_CHUNK;
+        int cincl = nch;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, cincl, o);
+            if (lane >= o) cincl += y;
+        }
+        const int ctot = __shfl_sync(0xffffffffu, cincl, 31);
+        unsigned at = 0;
+        if (lane == 0) at = atomicAdd(&ctl->hub_tail.w[0], (unsigned)ctot);
+        at = __shfl_sync(0xffffffffu, at, 0) + (unsigned)(cincl - nch);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const int zz = __shfl_sync(0xffffffffu, z[r], src);
-            const int dd = __shfl_sync(0xffffffffu, take[r] ? d[r] : 0, src);
-            if (dd <= P.bfs_hub) continue;
-            const int nch = (dd + MF_BFS_CHUNK - 1) / MF_BFS_CHUNK;
-            unsigned at = 0;
-            if (lane == 0) at = atomicAdd(&ctl->hub_tail.w[0], (unsigned)nch);
-            at = __shfl_sync(0xffffffffu, at, 0);
-            const int x0 = P.g.off[zz];
-            for (int c = lane; c < nch; c += 32) {
-                const int len = dd - c * MF_BFS_CHUNK;
-                P.sc.bitem[at + c] = make_int2(x0 + c * MF_BFS_CHUNK, len < MF_BFS_CHUNK ? len : MF_BFS_CHUNK);
+            if (!take[r] || d[r] <= P.bfs_hub) continue;
+            const int x0 = P.g.off[z[r]];
+            for (int c = 0; c * MF_BFS_CHUNK < d[r]; ++c) {
+                const int len = d[r] - c * MF_BFS_CHUNK;
+                P.sc.bitem[at++] = make_int2(x0 + c * MF_BFS_CHUNK, len < MF_BFS_CHUNK ? len : MF_BFS_CHUNK);
             }
         }
     }
@@ -918,6 +1022,7 @@ __device__ __noinline__ void phase_bfs_init(const MfParams &P, Sh &sh)
     long long total = 0;
     const int lane = threadIdx.x & 31;
     const long long gs = (long long)vn() * blockDim.x;
+    if (vb() == 0 && threadIdx.x == 0) sh.verts += n;     // every vertex: e read, h written
     for (long long base = (long long)vb() * blockDim.x + threadIdx.x - lane; base < n; base += gs) {
         const int v = (int)base + lane;
         bool root[1] = {false};
@@ -1078,21 +1183,29 @@ __device__ __noinline__ void phase_bfs_bottom_up(const MfParams &P, Sh &sh)
     const bool with_wl = P.data_driven && !(P.mode & MF_M_BFS_ONLY);
     const int lane = threadIdx.x & 31;
     const long long gs = (long long)vn() * blockDim.x;
-    long long slots = 0;
+    // a thread scans at most MF_BU_SCAN slots of its row; the rest of a longer
+    // row goes to the level's second pass as work items, so no thread walks a
+    // long row alone
+    const int cap = P.sc.bdefer != nullptr ? MF_BU_SCAN : 0x7fffffff;
+    long long slots = 0, unl = 0;
+    if (vb() == 0 && threadIdx.x == 0) sh.cycles += n;    // every vertex's height is read
     for (long long base = (long long)vb() * blockDim.x + threadIdx.x - lane; base < n; base += gs) {
         const int v = (int)base + lane;
         bool take[1] = {false};
         int zv[1] = {v}, dv[1] = {0};
         long long ev[1] = {0};
+        int nitem = 0, x0 = 0;
         if (v < n && v != skip && ldg_cg(P.h + v) == n) {
             const int r0 = P.g.off[v], d = ldg_cg(P.g.deg + v);
+            const int lim = d < cap ? d : cap;
+            ++unl;
             int j = 0;
-            for (; j < d && !take[0]; j += 4) {
+            for (; j < lim && !take[0]; j += 4) {
                 int c[4], z[4], hz[4];
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
                     const int x = r0 + j + r;
-                    const bool ok = j + r < d;
+                    const bool ok = j + r < lim;
                     c[r] = ok ? (pull ? ldg_cg(P.g.pcap + x) - ldg_cg(P.cf + x) : ldg_cg(P.cf + x)) : 0;
                     z[r] = ok ? ldg_cg(P.g.dst + x) : 0;
                 }
@@ -1101,14 +1214,85 @@ __device__ __noinline__ void phase_bfs_bottom_up(const MfParams &P, Sh &sh)
 #pragma unroll
                 for (int r = 0; r < 4; ++r) take[0] |= hz[r] == L;
             }
-            slots += j < d ? j : d;
+            slots += j < lim ? j : lim;
             if (take[0]) {
                 P.h[v] = L + 1;
                 dv[0] = d;
                 if (with_wl && v != P.sink && v != P.source) ev[0] = pull ? -ldg_cg(P.e + v) : ldg_cg(P.e + v);
+            } else if (d > lim) {
+                nitem = (d - lim + MF_BU_CHUNK - 1) / MF_BU_CHUNK;
+                x0 = r0 + lim;
             }
         }
         if (__any_sync(0xffffffffu, take[0])) frontier_push<1>(P, sh, take, zv, dv, ev, with_wl, sel);
+        if (__any_sync(0xffffffffu, nitem > 0)) {
+            int incl = nitem;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int tot = __shfl_sync(0xffffffffu, incl, 31);
+            unsigned at = 0;
+            if (lane == 0) at = atomicAdd(&ctl->defer_tail.w[0], (unsigned)tot);
+            at = __shfl_sync(0xffffffffu, at, 0) + (unsigned)(incl - nitem);
+            for (int c = 0; c < nitem; ++c) P.sc.bdefer[at + c] = make_int2(v, x0 + c * MF_BU_CHUNK);
+        }
+    }
+    if (slots) atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)slots);
+    if (unl) atomicAdd((unsigned long long *)&sh.verts, (unsigned long long)unl);
+}
+
+// Second pass of a bottom-up level: the deferred chunks of long rows whose
+// first MF_BU_SCAN slots held no neighbour of level L with a residual edge
+// towards it.  One warp per chunk of MF_BU_CHUNK slots, 8 per lane; the first
+// chunk of a row that finds one labels the vertex (a claim by CAS, as other
+// chunks of the same row may find one too).
+__device__ __noinline__ void phase_bfs_bottom_up_long(const MfParams &P, Sh &sh)
+{
+    MfCtrl *ctl = P.ctrl;
+    const int n = P.g.n;
+    const int L = vrd(&ctl->level);
+    const int sel = vrd(&ctl->wl_sel);
+    const bool pull = P.pull != 0;
+    const bool with_wl = P.data_driven && !(P.mode & MF_M_BFS_ONLY);
+    const int lane = threadIdx.x & 31;
+    const int cnt = vrd(&ctl->defer_n);
+    constexpr int kR = MF_BU_CHUNK / 32;
+    long long slots = 0;
+    for (;;) {
+        const int i = warp_grab(&ctl->head1.w[0], cnt, 1u);
+        if (i >= cnt) break;
+        const int2 it = __ldcg(P.sc.bdefer + i);
+        const int v = it.x;
+        if (ldg_cg(P.h + v) != n) continue;       // another chunk of the row labelled it (same value in every lane)
+        const int d = ldg_cg(P.g.deg + v);
+        const int end = P.g.off[v] + d;
+        const int len = end - it.y < MF_BU_CHUNK ? end - it.y : MF_BU_CHUNK;
+        int c[kR], z[kR];
+        bool hit = false;
+#pragma unroll
+        for (int r = 0; r < kR; ++r) {
+            const int j = r * 32 + lane;
+            const int x = it.y + j;
+            const bool ok = j < len;
+            c[r] = ok ? (pull ? ldg_cg(P.g.pcap + x) - ldg_cg(P.cf + x) : ldg_cg(P.cf + x)) : 0;
+            z[r] = ok ? ldg_cg(P.g.dst + x) : 0;
+        }
+#pragma unroll
+        for (int r = 0; r < kR; ++r) hit |= c[r] > 0 && ldg_cg(P.h + z[r]) == L;
+        if (lane == 0) slots += len;
+        bool won[1] = {false};
+        int zv[1] = {v}, dv[1] = {d};
+        long long ev[1] = {0};
+        if (__any_sync(0xffffffffu, hit)) {
+            if (lane == 0) {
+                won[0] = atomicCAS(P.h + v, n, L + 1) == n;
+                if (won[0] && with_wl && v != P.sink && v != P.source)
+                    ev[0] = pull ? -ldg_cg(P.e + v) : ldg_cg(P.e + v);
+            }
+            if (__any_sync(0xffffffffu, won[0])) frontier_push<1>(P, sh, won, zv, dv, ev, with_wl, sel);
+        }
     }
     if (slots) atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)slots);
 }
@@ -1254,39 +1438,172 @@ __device__ __forceinline__ unsigned long long scan_lowest(const MfParams &P, int
     return best;
 }
 
+// Heights of a row's heads kept on chip for the cycles after the first scan:
+// stg[j] = h(head of slot j) for a slot with residual capacity in the move's
+// direction, kNoRes for the others.  A snapshot: heights only rise while the
+// discharge runs and residuals of u's own slots only rise except through u's
+// own moves (which update stg), so every candidate is checked against global
+// memory before flow moves through it.  Slots that gain residual capacity
+// meanwhile wait for the next discharge call.
+constexpr int kNoRes = 0x7fffffff;
+
+// The first scan of a row: the lowest residual height as scan_lowest does, and
+// the snapshot of every slot of the row in stg.
+template <int kU, bool PULL>
+__device__ __forceinline__ unsigned long long scan_and_stage(const MfParams &P, int r0, int d, int j0, int step,
+                                                             int *stg)
+{
+    unsigned long long best = kEmpty;
+    for (int jb = j0; jb < d; jb += step * kU) {
+        int c[kU], z[kU], hz[kU];
+#pragma unroll
+        for (int r = 0; r < kU; ++r) {
+            const int j = jb + r * step;
+            c[r] = j < d ? (PULL ? ldg_cg(P.g.pcap + r0 + j) - ldg_cg(P.cf + r0 + j) : ldg_cg(P.cf + r0 + j)) : 0;
+            z[r] = j < d ? ldg_cg(P.g.dst + r0 + j) : 0;
+        }
+#pragma unroll
+        for (int r = 0; r < kU; ++r) hz[r] = c[r] > 0 ? ldg_cg(P.h + z[r]) : kNoRes;
+#pragma unroll
+        for (int r = 0; r < kU; ++r) {
+            const int j = jb + r * step;
+            if (j < d) stg[j] = hz[r];
+            if (c[r] > 0) {
+                const unsigned long long key = ((unsigned long long)(unsigned)hz[r] << 32) | (unsigned)j;
+                best = key < best ? key : best;
+            }
+        }
+    }
+    return best;
+}
+
+// Later scans: the lowest entry of the snapshot, from shared memory only.
+__device__ __forceinline__ unsigned long long scan_staged(const int *stg, int d, int j0, int step)
+{
+    unsigned long long best = kEmpty;
+    for (int j = j0; j < d; j += step) {
+        const int hz = stg[j];
+        if (hz != kNoRes) {
+            const unsigned long long key = ((unsigned long long)(unsigned)hz << 32) | (unsigned)j;
+            best = key < best ? key : best;
+        }
+    }
+    return best;
+}
+
+// What slot x of u (row position j, snapshot entry *sj) can move now towards
+// a head of height want: 0 unless the head still has that height and the slot
+// still has residual capacity; the snapshot entry is corrected on the way.
+template <bool PULL>
+__device__ __forceinline__ int staged_amount(const MfParams &P, int x, int want, int &sj)
+{
+    const int hz = ldg_cg(P.h + ldg_cg(P.g.dst + x));
+    if (hz != want) {
+        sj = hz;
+        return 0;
+    }
+    const int c = movable<PULL>(P, x, ldg_cg(P.g.rev + x));
+    if (c <= 0) {
+        sj = kNoRes;
+        return 0;
+    }
+    return c;
+}
+
 // One thread per vertex (rows of at most small_deg slots).  Returns true
 // if u was relabelled (only then can it have steep residual edges, Alg. 3).
 // PULL: u is deficient and pulls (Sec. 5.2.2); its "excess" is -e(u).
+// Rows of at most kTS slots keep the heads' heights in registers after the
+// first scan.
 template <bool PULL>
-__device__ bool discharge_thread(const MfParams &P, Sh &sh, int u, const DisCtx &dc)
+__device__ __noinline__ bool discharge_thread(const MfParams &P, Sh &sh, int u, const DisCtx &dc)
 {
+    constexpr int kTS = 8;
     bool lifted = false;
     const int n = P.g.n;
     const int r0 = P.g.off[u];
     const int d = ldg_cg(P.g.deg + u);
     int hu = ldg_cg(P.h + u);
-    long long scans = 0, moves = 0, fused = 0;
+    long long scans = 0, moves = 0, fused = 0, gscan = 0;
     int cyc = 0;
-    while (cyc < P.kernel_cycles) {
-        const long long eu = PULL ? -ldg_cg(P.e + u) : ldg_cg(P.e + u);
-        if (!(hu < n && eu > 0)) break;
-        ++scans;
-        unsigned long long best = scan_lowest<4, PULL>(P, r0, d, 0, 1);
-        int best_h = best == kEmpty ? 0x7fffffff : (int)(best >> 32);
-        if (best == kEmpty || hu <= best_h) {
-            // relabel (the relabel step of Alg. 2); the next cycle would find the same
-            // lowest slots admissible, so it continues below without a rescan
-            hu = (best == kEmpty || best_h >= n - 1) ? n : best_h + 1;
-            P.h[u] = hu;
-            lifted = true;
-            atomicAdd((unsigned long long *)&sh.relabels, 1ull);
-            ++cyc;
-            if (hu >= n || cyc >= P.kernel_cycles) continue;
+    if (d <= kTS) {
+        int hc[kTS];
+        bool have = false;
+        while (cyc < P.kernel_cycles) {
+            const long long eu = PULL ? -ldg_cg(P.e + u) : ldg_cg(P.e + u);
+            if (!(hu < n && eu > 0)) break;
+            ++scans;
+            if (!have) {
+                int c[kTS], z[kTS];
+#pragma unroll
+                for (int j = 0; j < kTS; ++j) {
+                    c[j] = j < d ? residual_dir<PULL>(P, r0 + j) : 0;
+                    z[j] = j < d ? ldg_cg(P.g.dst + r0 + j) : 0;
+                }
+#pragma unroll
+                for (int j = 0; j < kTS; ++j) hc[j] = c[j] > 0 ? ldg_cg(P.h + z[j]) : kNoRes;
+                have = true;
+                gscan += d;
+            }
+            unsigned long long best = kEmpty;
+#pragma unroll
+            for (int j = 0; j < kTS; ++j) {
+                if (hc[j] != kNoRes) {
+                    const unsigned long long key = ((unsigned long long)(unsigned)hc[j] << 32) | (unsigned)j;
+                    best = key < best ? key : best;
+                }
+            }
+            const int best_h = best == kEmpty ? 0x7fffffff : (int)(best >> 32);
+            if (best == kEmpty || hu <= best_h) {
+                // relabel (the relabel step of Alg. 2), then on to the pushes it makes admissible
+                hu = (best == kEmpty || best_h >= n - 1) ? n : best_h + 1;
+                P.h[u] = hu;
+                lifted = true;
+                atomicAdd((unsigned long long *)&sh.relabels, 1ull);
+                ++cyc;
+                if (hu >= n || cyc >= P.kernel_cycles) continue;
+            }
+            // the cycles Alg. 2 would run next: the slots of height best_h in slot
+            // order, each taking min(residual, what is left)
+            long long rem = eu, sent = 0;
+            int k = 0;
+            const int jstart = (int)(best & 0xffffffffu);
+#pragma unroll
+            for (int j = 0; j < kTS; ++j) {
+                if (j < jstart || j >= d || rem <= 0 || cyc + k >= P.kernel_cycles || hc[j] != best_h) continue;
+                const int x = r0 + j;
+                int sj = hc[j];
+                const int c = staged_amount<PULL>(P, x, best_h, sj);
+                hc[j] = sj;
+                ++fused;
+                if (c <= 0) continue;
+                const long long a = rem < (long long)c ? rem : (long long)c;
+                move_flow<PULL>(P, sh, x, ldg_cg(P.g.rev + x), ldg_cg(P.g.dst + x), a, dc);
+                if (a == c) hc[j] = kNoRes;
+                rem -= a;
+                sent += a;
+                ++k;
+            }
+            if (sent) atomic_add_ll(P.e + u, PULL ? sent : -sent);
+            moves += k;
+            cyc += k > 0 ? k : 1;
         }
-        {
-            // The cycles Alg. 2 would run next push to the lowest slots of height
-            // best_h in slot order until the excess or the cycles run out: do
-            // them in this one pass over the row.
+    } else {
+        while (cyc < P.kernel_cycles) {
+            const long long eu = PULL ? -ldg_cg(P.e + u) : ldg_cg(P.e + u);
+            if (!(hu < n && eu > 0)) break;
+            ++scans;
+            gscan += d;
+            unsigned long long best = scan_lowest<4, PULL>(P, r0, d, 0, 1);
+            int best_h = best == kEmpty ? 0x7fffffff : (int)(best >> 32);
+            if (best == kEmpty || hu <= best_h) {
+                hu = (best == kEmpty || best_h >= n - 1) ? n : best_h + 1;
+                P.h[u] = hu;
+                lifted = true;
+                atomicAdd((unsigned long long *)&sh.relabels, 1ull);
+                ++cyc;
+                if (hu >= n || cyc >= P.kernel_cycles) continue;
+            }
             long long rem = eu, sent = 0;
             int k = 0;
             int j = (int)(best & 0xffffffffu);
@@ -1313,29 +1630,42 @@ __device__ bool discharge_thread(const MfParams &P, Sh &sh, int u, const DisCtx 
     }
     if (scans) {
         atomicAdd((unsigned long long *)&sh.cycles, (unsigned long long)scans);
-        atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)(scans * d + fused));
+        atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)(gscan + fused));
     }
     if (moves) atomicAdd((unsigned long long *)&sh.pushes, (unsigned long long)moves);
     return lifted;
 }
 
-// One warp per vertex (returns the same value in every lane).
-template <bool PULL>
-__device__ bool discharge_warp(const MfParams &P, Sh &sh, int u, const DisCtx &dc)
+// One warp per vertex; ST: the row's heads are kept in stg (this warp's slice
+// of the on-chip snapshot) after the first scan.
+template <bool PULL, bool ST>
+__device__ __noinline__ bool discharge_warp_rows(const MfParams &P, Sh &sh, int u, int d, const DisCtx &dc, int *stg)
 {
     bool lifted = false;
     const int n = P.g.n;
     const int lane = threadIdx.x & 31;
     const int r0 = P.g.off[u];
-    const int d = ldg_cg(P.g.deg + u);
+    constexpr bool st = ST;
+    bool have = false;
     int hu = ldg_cg(P.h + u);
-    long long scans = 0, moves = 0, fused = 0;
+    long long scans = 0, moves = 0, fused = 0, gscan = 0;
     int cyc = 0;
     while (cyc < P.kernel_cycles) {
         const long long eu = PULL ? -ldg_cg(P.e + u) : ldg_cg(P.e + u);
         if (!(hu < n && eu > 0)) break;
         ++scans;
-        unsigned long long best = warp_min_u64(scan_lowest<8, PULL>(P, r0, d, lane, 32));
+        unsigned long long best;
+        if (!st) {
+            best = warp_min_u64(scan_lowest<8, PULL>(P, r0, d, lane, 32));
+            gscan += d;
+        } else if (!have) {
+            best = warp_min_u64(scan_and_stage<8, PULL>(P, r0, d, lane, 32, stg));
+            have = true;
+            gscan += d;
+            __syncwarp();
+        } else {
+            best = warp_min_u64(scan_staged(stg, d, lane, 32));
+        }
         int best_h = best == kEmpty ? 0x7fffffff : (int)(best >> 32);
         if (best == kEmpty || hu <= best_h) {
             // relabel, then straight on to the pushes it makes admissible
@@ -1366,30 +1696,49 @@ __device__ bool discharge_warp(const MfParams &P, Sh &sh, int u, const DisCtx &d
                 int a[kSeg];
                 long long tsum = 0;
                 int tcnt = 0;
+                if (st) {
 #pragma unroll
-                for (int r = 0; r < kSeg; ++r) {
-                    a[r] = 0;
-                    const int j = js + r;
-                    if (r < seg && j < d && residual_dir<PULL>(P, r0 + j) > 0) a[r] = 1;
-                }
-#pragma unroll
-                for (int r = 0; r < kSeg; ++r) {
-                    if (a[r]) {
-                        const int x = r0 + js + r;
-                        a[r] = ldg_cg(P.h + ldg_cg(P.g.dst + x)) == best_h ? 1 : 0;
+                    for (int r = 0; r < kSeg; ++r) {
+                        const int j = js + r;
+                        a[r] = (r < seg && j < d && stg[j] == best_h) ? 1 : 0;
                     }
-                }
 #pragma unroll
-                for (int r = 0; r < kSeg; ++r) {
-                    if (a[r]) {
-                        const int x = r0 + js + r;
-                        const int c = movable<PULL>(P, x, ldg_cg(P.g.rev + x));
-                        a[r] = c > 0 ? c : 0;
-                        tsum += a[r];
-                        tcnt += a[r] > 0 ? 1 : 0;
+                    for (int r = 0; r < kSeg; ++r) {
+                        if (a[r]) {
+                            int sj = stg[js + r];
+                            a[r] = staged_amount<PULL>(P, r0 + js + r, best_h, sj);
+                            stg[js + r] = sj;
+                            ++fused;
+                            tsum += a[r];
+                            tcnt += a[r] > 0 ? 1 : 0;
+                        }
                     }
+                } else {
+#pragma unroll
+                    for (int r = 0; r < kSeg; ++r) {
+                        a[r] = 0;
+                        const int j = js + r;
+                        if (r < seg && j < d && residual_dir<PULL>(P, r0 + j) > 0) a[r] = 1;
+                    }
+#pragma unroll
+                    for (int r = 0; r < kSeg; ++r) {
+                        if (a[r]) {
+                            const int x = r0 + js + r;
+                            a[r] = ldg_cg(P.h + ldg_cg(P.g.dst + x)) == best_h ? 1 : 0;
+                        }
+                    }
+#pragma unroll
+                    for (int r = 0; r < kSeg; ++r) {
+                        if (a[r]) {
+                            const int x = r0 + js + r;
+                            const int c = movable<PULL>(P, x, ldg_cg(P.g.rev + x));
+                            a[r] = c > 0 ? c : 0;
+                            tsum += a[r];
+                            tcnt += a[r] > 0 ? 1 : 0;
+                        }
+                    }
+                    fused += seg;
                 }
-                fused += seg * 32;
                 long long incl = tsum;
                 int cincl = tcnt;
 #pragma unroll
@@ -1413,6 +1762,7 @@ __device__ bool discharge_warp(const MfParams &P, Sh &sh, int u, const DisCtx &d
                             const long long g = a[r] < rem - off ? a[r] : rem - off;
                             const int x = r0 + js + r;
                             move_flow<PULL>(P, sh, x, ldg_cg(P.g.rev + x), ldg_cg(P.g.dst + x), g, dc);
+                            if (st && g == a[r]) stg[js + r] = kNoRes;
                             mine += g;
                             ++mk;
                         }
@@ -1425,6 +1775,7 @@ __device__ bool discharge_warp(const MfParams &P, Sh &sh, int u, const DisCtx &d
                 rem -= tot;
                 sent += tot;
                 k += kk;
+                __syncwarp();              // snapshot entries written above are read by other lanes next
             }
             if (lane == 0 && sent) atomic_add_ll(P.e + u, PULL ? sent : -sent);
             moves += k;
@@ -1432,27 +1783,40 @@ __device__ bool discharge_warp(const MfParams &P, Sh &sh, int u, const DisCtx &d
         }
         __syncwarp();
     }
+    fused = warp_sum_ll(fused);
     if (lane == 0) {
         if (scans) {
             atomicAdd((unsigned long long *)&sh.cycles, (unsigned long long)scans);
-            atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)(scans * d + fused));
+            atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)(gscan + fused));
         }
         if (moves) atomicAdd((unsigned long long *)&sh.pushes, (unsigned long long)moves);
     }
     return lifted;
 }
 
-// One CTA per vertex (hubs).  All threads of the CTA call this together;
-// the return value is meaningful in thread 0.
+// One warp per vertex (returns the same value in every lane).  stg: this
+// warp's slice of the on-chip snapshot (wcap entries), used when the row fits.
 template <bool PULL>
-__device__ bool discharge_cta(const MfParams &P, Sh &sh, int u, const DisCtx &dc)
+__device__ __forceinline__ bool discharge_warp(const MfParams &P, Sh &sh, int u, const DisCtx &dc, int *stg, int wcap)
+{
+    const int d = ldg_cg(P.g.deg + u);
+    if (stg != nullptr && d <= wcap) return discharge_warp_rows<PULL, true>(P, sh, u, d, dc, stg);
+    return discharge_warp_rows<PULL, false>(P, sh, u, d, dc, nullptr);
+}
+
+// One CTA per vertex; ST: the row's heads are kept in stg (the CTA's on-chip
+// snapshot) after the first scan.
+template <bool PULL, bool ST>
+__device__ __noinline__ bool discharge_cta_rows(const MfParams &P, Sh &sh, int u, int d, const DisCtx &dc, int *stg)
 {
     bool lifted = false;
     const int n = P.g.n;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     const int r0 = P.g.off[u];
-    const int d = ldg_cg(P.g.deg + u);
+    constexpr bool st = ST;
+    bool have = false;
+    long long cand = 0;
     int cyc = 0;
     while (cyc < P.kernel_cycles) {
         if (threadIdx.x == 0) {
@@ -1466,7 +1830,13 @@ __device__ bool discharge_cta(const MfParams &P, Sh &sh, int u, const DisCtx &dc
             __syncthreads();
             break;
         }
-        unsigned long long best = warp_min_u64(scan_lowest<8, PULL>(P, r0, d, threadIdx.x, blockDim.x));
+        unsigned long long best;
+        const bool global_scan = !st || !have;
+        if (!st) best = scan_lowest<8, PULL>(P, r0, d, threadIdx.x, blockDim.x);
+        else if (!have) best = scan_and_stage<8, PULL>(P, r0, d, threadIdx.x, blockDim.x, stg);
+        else best = scan_staged(stg, d, threadIdx.x, blockDim.x);
+        have = true;
+        best = warp_min_u64(best);
         if (lane == 0) sh.red[wid] = best;
         __syncthreads();
         unsigned long long b = kEmpty;
@@ -1474,7 +1844,7 @@ __device__ bool discharge_cta(const MfParams &P, Sh &sh, int u, const DisCtx &dc
         const int best_h = b == kEmpty ? 0x7fffffff : (int)(b >> 32);
         if (threadIdx.x == 0) {
             atomicAdd((unsigned long long *)&sh.cycles, 1ull);
-            atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)d);
+            if (global_scan) atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)d);
         }
         bool go = b != kEmpty && hu > best_h;
         if (!go) {
@@ -1506,32 +1876,51 @@ __device__ bool discharge_cta(const MfParams &P, Sh &sh, int u, const DisCtx &dc
                 int a[kSeg];
                 long long tsum = 0;
                 int tcnt = 0;
+                if (st) {
 #pragma unroll
-                for (int r = 0; r < kSeg; ++r) {
-                    a[r] = 0;
-                    const int j = js + r;
-                    if (r < seg && j < d && residual_dir<PULL>(P, r0 + j) > 0) a[r] = 1;   // candidate
-                }
-#pragma unroll
-                for (int r = 0; r < kSeg; ++r) {
-                    if (a[r]) {
-                        const int x = r0 + js + r;
-                        const int z = ldg_cg(P.g.dst + x);
-                        a[r] = ldg_cg(P.h + z) == best_h ? 1 : 0;
+                    for (int r = 0; r < kSeg; ++r) {
+                        const int j = js + r;
+                        a[r] = (r < seg && j < d && stg[j] == best_h) ? 1 : 0;
                     }
-                }
 #pragma unroll
-                for (int r = 0; r < kSeg; ++r) {
-                    if (a[r]) {
-                        const int x = r0 + js + r;
-                        const int c = movable<PULL>(P, x, ldg_cg(P.g.rev + x));
-                        a[r] = c > 0 ? c : 0;
-                        tsum += a[r];
-                        tcnt += a[r] > 0 ? 1 : 0;
+                    for (int r = 0; r < kSeg; ++r) {
+                        if (a[r]) {
+                            int sj = stg[js + r];
+                            a[r] = staged_amount<PULL>(P, r0 + js + r, best_h, sj);
+                            stg[js + r] = sj;
+                            ++cand;
+                            tsum += a[r];
+                            tcnt += a[r] > 0 ? 1 : 0;
+                        }
                     }
+                } else {
+#pragma unroll
+                    for (int r = 0; r < kSeg; ++r) {
+                        a[r] = 0;
+                        const int j = js + r;
+                        if (r < seg && j < d && residual_dir<PULL>(P, r0 + j) > 0) a[r] = 1;   // candidate
+                    }
+#pragma unroll
+                    for (int r = 0; r < kSeg; ++r) {
+                        if (a[r]) {
+                            const int x = r0 + js + r;
+                            const int z = ldg_cg(P.g.dst + x);
+                            a[r] = ldg_cg(P.h + z) == best_h ? 1 : 0;
+                        }
+                    }
+#pragma unroll
+                    for (int r = 0; r < kSeg; ++r) {
+                        if (a[r]) {
+                            const int x = r0 + js + r;
+                            const int c = movable<PULL>(P, x, ldg_cg(P.g.rev + x));
+                            a[r] = c > 0 ? c : 0;
+                            tsum += a[r];
+                            tcnt += a[r] > 0 ? 1 : 0;
+                        }
+                    }
+                    if (threadIdx.x == 0)
+                        atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)(seg * blockDim.x));
                 }
-                if (threadIdx.x == 0)
-                    atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)(seg * blockDim.x));
                 long long incl = tsum;
                 int cincl = tcnt;
 #pragma unroll
@@ -1564,6 +1953,7 @@ __device__ bool discharge_cta(const MfParams &P, Sh &sh, int u, const DisCtx &dc
                             const long long g = a[r] < rem - off ? a[r] : rem - off;
                             const int x = r0 + js + r;
                             move_flow<PULL>(P, sh, x, ldg_cg(P.g.rev + x), ldg_cg(P.g.dst + x), g, dc);
+                            if (st && g == a[r]) stg[js + r] = kNoRes;
                             mine += g;
                             ++mk;
                         }
@@ -1598,7 +1988,19 @@ __device__ bool discharge_cta(const MfParams &P, Sh &sh, int u, const DisCtx &dc
         }
         __syncthreads();
     }
+    if (cand) atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)cand);
     return lifted;
+}
+
+// One CTA per vertex (hubs).  All threads of the CTA call this together;
+// the return value is meaningful in thread 0.  stg: the CTA's on-chip
+// snapshot (ccap entries), used when the row fits.
+template <bool PULL>
+__device__ __forceinline__ bool discharge_cta(const MfParams &P, Sh &sh, int u, const DisCtx &dc, int *stg, int ccap)
+{
+    const int d = ldg_cg(P.g.deg + u);
+    if (stg != nullptr && d <= ccap) return discharge_cta_rows<PULL, true>(P, sh, u, d, dc, stg);
+    return discharge_cta_rows<PULL, false>(P, sh, u, d, dc, nullptr);
 }
 
 template <bool PULL>
@@ -1615,6 +2017,7 @@ __device__ __noinline__ void phase_discharge(const MfParams &P, Sh &sh)
     // (adaptive rounds: the hook decides after this round)
     dc.queue = vrd(&ctl->round) + 1 < (P.rounds > 0 ? P.rounds : MF_MAX_ROUNDS);
     const int *wl0 = P.sc.wl[sel][0], *wl1 = P.sc.wl[sel][1], *wl2 = P.sc.wl[sel][2];
+    int *stage = P.stage_slots > 0 ? mf_stage : nullptr;
     // hubs: one CTA each
     const int nh = vrd(&ctl->wl_n[2]);
     for (;;) {
@@ -1627,15 +2030,18 @@ __device__ __noinline__ void phase_discharge(const MfParams &P, Sh &sh)
         __syncthreads();
         if (i >= nh) break;
         const int u = __ldcg(wl2 + i);
-        if (discharge_cta<PULL>(P, sh, u, dc) && threadIdx.x == 0) note_relabel(P, u, dc);
+        if (discharge_cta<PULL>(P, sh, u, dc, stage, P.stage_slots) && threadIdx.x == 0) note_relabel(P, u, dc);
     }
-    // mid-degree rows: one warp each
+    // mid-degree rows: one warp each (the CTA's snapshot buffer is free again:
+    // every thread has left the loop above, so each warp takes a slice)
     const int nm = vrd(&ctl->wl_n[1]);
+    const int wcap = min(MF_WARP_STAGE, P.stage_slots / MF_WARPS);
+    int *wstage = stage != nullptr && wcap > 0 ? stage + (threadIdx.x >> 5) * wcap : nullptr;
     for (;;) {
         const int i = warp_grab(&ctl->head1.w[0], nm, 1u);
         if (i >= nm) break;
         const int u = __ldcg(wl1 + i);
-        if (discharge_warp<PULL>(P, sh, u, dc) && lane == 0) note_relabel(P, u, dc);
+        if (discharge_warp<PULL>(P, sh, u, dc, wstage, wcap) && lane == 0) note_relabel(P, u, dc);
     }
     // small rows: one thread each, 32 per grab
     const int ns = vrd(&ctl->wl_n[0]);
@@ -1803,28 +2209,31 @@ __device__ __noinline__ bool solve_instance(const MfParams &P, Sh &sh)
             phase_apply_cleanup(P, false);
             return grid_sync(P, H_FINAL, sh);
         }
-        phase_apply_locate(P);
+        phase_apply_locate(P, sh);
+        flush_acc(P, sh, 4);
         if (!grid_sync(P, H_APPLY_LOCATED, sh)) return false;
         phase_apply_check(P);
         if (!grid_sync(P, H_APPLY_CHECKED, sh)) return false;
         if (status_of(P) != MF_ST_RUNNING) {
-            phase_apply_cleanup(P, true);
+            // a row overflow keeps the rows' demand for the rebuild that follows;
+            // a refused batch (pair sum) leaves nothing behind
+            phase_apply_cleanup(P, *(volatile unsigned *)&P.ctrl->err.w[0] == MF_E_OVERFLOW);
             return grid_sync(P, H_FINAL, sh);
         }
-        phase_apply_insert(P);
-        if (!grid_sync(P, H_NONE, sh)) return false;
-        phase_apply_delta(P, sh);
+        phase_apply_change(P, sh);
         flush_acc(P, sh, 4);
         if (!grid_sync(P, H_APPLY_DELTA, sh)) return false;
-        phase_apply_clamp(P, sh);
+        // the source step reads the final residuals; the tables are cleared beside it
         phase_apply_cleanup(P, false);
+        if (!(P.mode & MF_M_SKIP_SOURCE_SAT)) phase_resaturate(P, sh);
         flush_acc(P, sh, 4);
-        if (!grid_sync(P, H_NONE, sh)) return false;
-        if (!(P.mode & MF_M_SKIP_SOURCE_SAT)) {
-            phase_resaturate(P, sh);
-            flush_acc(P, sh, 4);
-            if (!grid_sync(P, H_NONE, sh)) return false;
+        // straight on to the loop: this barrier opens its first iteration
+        if (!(P.mode & MF_M_CUT) && (P.mode & (MF_M_SOLVE | MF_M_BFS_ONLY))) {
+            if (!grid_sync(P, H_ITER, sh)) return false;
+            if (status_of(P) != MF_ST_RUNNING) return true;
+            goto loop;
         }
+        if (!grid_sync(P, H_NONE, sh)) return false;
         if (P.mode & MF_M_CUT) {
             phase_cut_side(P);
             if (!grid_sync(P, H_NONE, sh)) return false;
@@ -1837,16 +2246,27 @@ __device__ __noinline__ bool solve_instance(const MfParams &P, Sh &sh)
     if (!(P.mode & (MF_M_SOLVE | MF_M_BFS_ONLY))) return true;
 
     if (!grid_sync(P, H_ITER, sh)) return false;
+loop:
     for (;;) {
         // backward BFS
         phase_bfs_init(P, sh);
         flush_acc(P, sh, 0);               // the roots' label counters feed the first level's direction
         if (!grid_sync(P, H_BFS_START, sh)) return false;
         while (!vrd(&P.ctrl->bfs_done)) {
-            if (vrd(&P.ctrl->bu_mode)) phase_bfs_bottom_up(P, sh);
-            else phase_bfs_level(P, sh);
-            flush_acc(P, sh, 0);
-            if (!grid_sync(P, H_BFS_NEXT, sh)) return false;
+            if (vrd(&P.ctrl->bu_mode)) {
+                phase_bfs_bottom_up(P, sh);
+                flush_acc(P, sh, 0);
+                if (!grid_sync(P, H_BU_SPLIT, sh)) return false;     // ends the level if nothing was deferred
+                if (vrd(&P.ctrl->bu_split)) {
+                    phase_bfs_bottom_up_long(P, sh);
+                    flush_acc(P, sh, 0);
+                    if (!grid_sync(P, H_BFS_NEXT, sh)) return false;
+                }
+            } else {
+                phase_bfs_level(P, sh);
+                flush_acc(P, sh, 0);
+                if (!grid_sync(P, H_BFS_NEXT, sh)) return false;
+            }
         }
         if (P.mode & MF_M_BFS_ONLY) return true;
         // worklist and termination test (built during the BFS when data-driven)
@@ -2193,10 +2613,53 @@ inline int cuda_rc(cudaError_t e) { return e == cudaSuccess ? MAXFLOW_OK : MAXFL
 
 }  // namespace
 
-int mf_max_coresident_blocks(int device, int *per_sm, int *num_sms)
+// Dynamic shared memory per CTA of the persistent kernels: as much as still
+// lets two CTAs share an SM (the register budget allows two).  Computed once per
+// device, with that device current; the kernels' attributes are set to allow it.
+int mf_stage_bytes(int device, int *bytes)
+{
+    static std::mutex mu;
+    static int cache[64];
+    static bool init = false;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!init) {
+        for (int &x : cache) x = -1;
+        init = true;
+    }
+    if (device < 0 || device >= 64) return MAXFLOW_ERR_INVALID;
+    if (cache[device] < 0) {
+        cudaFuncAttributes a1{}, a2{};
+        int smem_sm = 0, reserved = 0, optin = 0;
+        if (cudaFuncGetAttributes(&a1, mf_solve_kernel) != cudaSuccess ||
+            cudaFuncGetAttributes(&a2, mf_multi_kernel) != cudaSuccess ||
+            cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device) != cudaSuccess ||
+            cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, device) != cudaSuccess ||
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess)
+            return MAXFLOW_ERR_CUDA;
+        const long long stat = (long long)(a1.sharedSizeBytes > a2.sharedSizeBytes ? a1.sharedSizeBytes
+                                                                                   : a2.sharedSizeBytes);
+        long long b = (long long)smem_sm / 2 - reserved - stat;
+        if (b > (long long)optin - stat) b = (long long)optin - stat;
+        b &= ~255ll;
+        if (b < 0) b = 0;
+        if (cudaFuncSetAttribute(mf_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b) != cudaSuccess ||
+            cudaFuncSetAttribute(mf_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b) != cudaSuccess)
+            return MAXFLOW_ERR_CUDA;
+        cudaFuncSetAttribute(mf_solve_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        cudaFuncSetAttribute(mf_multi_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        cudaGetLastError();
+        cache[device] = (int)b;
+    }
+    *bytes = cache[device];
+    return MAXFLOW_OK;
+}
+
+int mf_max_coresident_blocks(int device, int *per_sm, int *num_sms, int dyn_bytes)
 {
     int k = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, mf_solve_kernel, MF_BLOCK, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, mf_solve_kernel, MF_BLOCK, (size_t)dyn_bytes) != cudaSuccess)
         return MAXFLOW_ERR_CUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return MAXFLOW_ERR_CUDA;
     *per_sm = k;
@@ -2205,11 +2668,11 @@ int mf_max_coresident_blocks(int device, int *per_sm, int *num_sms)
 }
 
 int mf_launch_multi(const MfParams *plist_dev, int count, int gsize, int grid, unsigned *gstate, unsigned *head,
-                    unsigned long long wait_ns, int *abort, void *stream)
+                    unsigned long long wait_ns, int *abort, void *stream, int stage_bytes)
 {
     void *args[] = {(void *)&plist_dev, &count, &gsize, &gstate, &head, &wait_ns, &abort};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void *)mf_multi_kernel, dim3(grid), dim3(MF_BLOCK), args, 0,
-                                                (cudaStream_t)stream);
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)mf_multi_kernel, dim3(grid), dim3(MF_BLOCK), args,
+                                                (size_t)stage_bytes, (cudaStream_t)stream);
     return cuda_rc(e);
 }
 
@@ -2217,8 +2680,8 @@ int mf_launch(const MfParams &p, int grid, void *stream)
 {
     MfParams q = p;
     void *args[] = {&q};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void *)mf_solve_kernel, dim3(grid), dim3(MF_BLOCK), args, 0,
-                                                (cudaStream_t)stream);
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)mf_solve_kernel, dim3(grid), dim3(MF_BLOCK), args,
+                                                (size_t)p.stage_slots * sizeof(int), (cudaStream_t)stream);
     return cuda_rc(e);
 }
 

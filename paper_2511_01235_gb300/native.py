@@ -86,6 +86,7 @@ EXPORTS = ["maxflow_build_layout", "maxflow_kernel_launches", "maxflow_default_o
            "maxflow_get_flow", "maxflow_stats", "maxflow_destroy", "maxflow_strerror", "maxflow_set_flow",
            "maxflow_apply", "maxflow_global_relabel", "maxflow_resolve", "maxflow_get_residual",
            "maxflow_get_vertex_state", "maxflow_check", "maxflow_global_relabel_noalloc", "maxflow_trace",
+           "maxflow_trace_work",
            "maxflow_set_kernel_cycles", "maxflow_clone", "maxflow_set_rounds", "maxflow_sched_actions",
            "maxflow_features", "maxflow_run_action", "maxflow_update_scheduled", "maxflow_mlp_create",
            "maxflow_mlp_destroy", "maxflow_mlp_shape", "maxflow_mlp_get_params", "maxflow_mlp_set_params",
@@ -137,6 +138,7 @@ def load(build_if_missing: bool = False):
     L.maxflow_stats.argtypes = [vp, P(Stats)]
     L.maxflow_check.argtypes = [vp, vp]
     L.maxflow_trace.argtypes = [vp, vp, vp, i32, P(i32)]
+    L.maxflow_trace_work.argtypes = [vp, vp, vp, i32, P(i32)]
     L.maxflow_set_kernel_cycles.argtypes = [vp, i32]
     L.maxflow_set_rounds.argtypes = [vp, i32]
     L.maxflow_set_tuning.argtypes = [vp, i32, i32, i32]
@@ -384,6 +386,16 @@ def maxflow_trace(h, cap: int = 256):
     _check(load().maxflow_trace(h, _p(b), _p(t), cap, C.byref(k)), "maxflow_trace")
     k = int(k.value)
     return [TRACE_NAMES[i] if 0 <= i < len(TRACE_NAMES) else str(i) for i in b[:k]], t[:k]
+
+
+def maxflow_trace_work(h, cap: int = 256):
+    """(cumulative slots scanned, packed phase info) per entry of maxflow_trace."""
+    sl = np.zeros(cap, np.int64)
+    inf = np.zeros(cap, np.int32)
+    k = C.c_int32(0)
+    _check(load().maxflow_trace_work(h, _p(sl), _p(inf), cap, C.byref(k)), "maxflow_trace_work")
+    k = int(k.value)
+    return sl[:k], inf[:k]
 
 
 def maxflow_set_kernel_cycles(h, k: int):
@@ -659,6 +671,9 @@ class Solver:
 
     def trace(self):
         return maxflow_trace(self.h)
+
+    def trace_work(self):
+        return maxflow_trace_work(self.h)
 
     def set_kernel_cycles(self, k: int):
         maxflow_set_kernel_cycles(self.h, k)

@@ -429,6 +429,55 @@ def test_invalid_batch_rejected_whole():
     S.close()
 
 
+def test_pair_sum_limit_refuses_the_whole_batch():
+    """Residual capacities are int32 and c_f(u,v) + c_f(v,u) = c(u,v) + c(v,u)
+    (Sec. 3.1 Theorem 3.3), so a batch (Sec. 4.1: it sets new capacities) that
+    would leave a pair above INT32_MAX is refused before anything changes.  The
+    final capacity of both directions counts, the batch's own update of the
+    reverse included."""
+    M = 2**31 - 1
+    # three disjoint paths of capacity INT32_MAX (value 3 * INT32_MAX in int64),
+    # and a dead-end pair (1, 4) whose sum is INT32_MAX - 5
+    src = [0, 1, 0, 2, 0, 3, 1, 4]
+    dst = [1, 5, 2, 5, 3, 5, 4, 1]
+    cap = [M, M, M, M, M, M, M - 10, 5]
+    n, s, t = 6, 0, 5
+    S = native.Solver(n, src, dst, cap, s, t)
+    assert S.query()[0] == 3 * M
+    before = slot_dict(*S.residual())
+    h0, e0 = S.vertex_state()
+    over = [
+        ([4], [1], [11]),                       # one direction: (M - 10) + 11
+        ([1, 4], [4, 1], [M - 7, 8]),           # both: each fits with the other's old value, not together
+        ([2, 3], [3, 2], [M, 1]),               # a new pair, both directions in the batch
+        ([1, 4, 1], [4, 1, 4], [5, M, M - 10]),  # last update wins: (M - 10) + M
+    ]
+    for u, v, c in over:
+        with pytest.raises(native.MaxflowError) as ei:
+            S.update(np.array(u), np.array(v), np.array(c, dtype=np.int64).astype(np.int32))
+        assert ei.value.code == native.ERR_TOO_LARGE
+        assert slot_dict(*S.residual()) == before
+        h1, e1 = S.vertex_state()
+        np.testing.assert_array_equal(e1, e0)
+        assert S.query()[0] == 3 * M
+    import torch
+    with pytest.raises(native.MaxflowError) as ei:      # a device batch: refused by the kernel too
+        S.update(torch.tensor([4], dtype=torch.int32, device="cuda"), torch.tensor([1], dtype=torch.int32, device="cuda"),
+                 torch.tensor([11], dtype=torch.int32, device="cuda"))
+    assert ei.value.code == native.ERR_TOO_LARGE
+    assert slot_dict(*S.residual()) == before
+    # exactly at the limit: accepted, and the value equals Dinic's int64 value
+    es = W.EdgeSet(n, np.array(src), np.array(dst), np.array(cap))
+    for u, v, c in [([1, 4], [4, 1], [M - 2, 2]), ([2], [3], [M]), ([3, 4], [5, 5], [M, M])]:
+        S.update(np.array(u), np.array(v), np.array(c, dtype=np.int64).astype(np.int32))
+        es.apply(np.array(u), np.array(v), np.array(c))
+        uu, vv, cc = es.coo()
+        got = check_against_oracle(S, n, uu, vv, cc, s, t)
+        cpu_certificate(S, got)
+    assert S.query()[0] == 3 * M               # the source's out-capacity still bounds it
+    S.close()
+
+
 def test_iteration_cap_reports_not_converged():
     g = W.erdos_renyi(3000, 24000, seed=91, cap_hi=100)
     with pytest.raises(native.MaxflowError) as ei:

@@ -1,13 +1,15 @@
-"""The allocation-free heights call, checked against the ordinary one.
+"""The allocation-free heights call, checked against the oracle and the ordinary call.
 
 maxflow_global_relabel_noalloc serves callers that may not allocate device
 memory while running (a serving process with a device pool fixed at
-start-up, a plugin inside an application that owns the GPU allocator).  It
-must give exactly the heights that maxflow_global_relabel gives on the same
-residual state (integer BFS distances, so equality is the tolerance), on two
-calls in a row: the second call reuses the static scratch the first one left
-behind.  This file is collected last so that a failure here comes after
-every other test has run.
+start-up, a plugin inside an application that owns the GPU allocator).  On
+the same residual state it must give exactly the oracle's residual distances
+(integer BFS distances, so equality is the tolerance) for both root sets --
+the sink and the deficient vertices, and the sink alone -- and, for the first,
+exactly what maxflow_global_relabel gives.  Several calls run in a row: each
+reuses the static scratch the previous one left behind.  After the prepare
+call (n = 0) a call takes no device memory.  This file is collected last so
+that a failure here comes after every other test has run.
 """
 import ctypes as C
 
@@ -41,12 +43,16 @@ def _device_csr(torch, S):
             "cf": dev(cf, torch.int32), "pcap": dev(pcap, torch.int32), "e": dev(e, torch.int64)}
 
 
-def _noalloc_heights(torch, S, arrs):
-    h = torch.full((S.n,), -1, dtype=torch.int32, device="cuda")
+def _call(torch, n, s, t, arrs, h, deficit_roots):
     stream = torch.cuda.current_stream().cuda_stream
-    rc = native.maxflow_global_relabel_noalloc(
-        S.n, S.s, S.t, arrs["off"].data_ptr(), arrs["deg"].data_ptr(), arrs["dst"].data_ptr(),
-        arrs["cf"].data_ptr(), arrs["pcap"].data_ptr(), arrs["e"].data_ptr(), h.data_ptr(), True, stream)
+    return native.maxflow_global_relabel_noalloc(
+        n, s, t, arrs["off"].data_ptr(), arrs["deg"].data_ptr(), arrs["dst"].data_ptr(),
+        arrs["cf"].data_ptr(), arrs["pcap"].data_ptr(), arrs["e"].data_ptr(), h.data_ptr(), deficit_roots, stream)
+
+
+def _noalloc_heights(torch, S, arrs, deficit_roots):
+    h = torch.full((S.n,), -1, dtype=torch.int32, device="cuda")
+    rc = _call(torch, S.n, S.s, S.t, arrs, h, deficit_roots)
     assert rc == native.OK, native.strerror(rc)
     return h.cpu().numpy()
 
@@ -65,20 +71,51 @@ def _state(seed, n, hubs=False):
     return src, dst, cap, mu, mv, f
 
 
-def test_noalloc_heights_match_existing_entry_point_twice():
+def test_noalloc_heights_match_the_oracle_and_the_existing_entry_point():
     import torch
     assert torch.cuda.is_available()
     native.load()
-    for call, (seed, n, hubs) in enumerate([(4242, 5000, True), (4343, 2000, False)]):
+    calls = 0
+    for seed, n, hubs in [(4242, 5000, True), (4343, 2000, False)]:
         src, dst, cap, mu, mv, f = _state(seed, n, hubs)
+        R = oracle.Residual(n, src, dst, cap)
+        R.set_flow(mu, mv, f)
         S = native.Solver(n, src, dst, cap, 0, n - 1)
         S.set_flow(mu, mv, f)
         arrs = _device_csr(torch, S)
-        S.global_relabel()                         # the existing entry point
-        want, _ = S.vertex_state()
-        got = _noalloc_heights(torch, S, arrs)
-        np.testing.assert_array_equal(got, want, err_msg=f"call {call + 1}")
+        for deficit_roots in (True, False):
+            want = R.heights(0, n - 1, deficit_roots=deficit_roots)
+            got = _noalloc_heights(torch, S, arrs, deficit_roots)
+            calls += 1
+            np.testing.assert_array_equal(got, want, err_msg=f"call {calls}, deficit_roots={deficit_roots}")
+        S.global_relabel()                         # the existing entry point (sink and deficits)
+        existing, _ = S.vertex_state()
+        np.testing.assert_array_equal(_noalloc_heights(torch, S, arrs, True), existing)
         S.close()
+
+
+def test_noalloc_call_after_prepare_takes_no_device_memory():
+    import torch
+    native.load()
+    rc = native.maxflow_global_relabel_noalloc(0, 0, 0, None, None, None, None, None, None, None, True,
+                                               torch.cuda.current_stream().cuda_stream)
+    assert rc == native.OK, native.strerror(rc)
+    src, dst, cap, mu, mv, f = _state(4545, 3000, True)
+    R = oracle.Residual(3000, src, dst, cap)
+    R.set_flow(mu, mv, f)
+    S = native.Solver(3000, src, dst, cap, 0, 2999)
+    S.set_flow(mu, mv, f)
+    arrs = _device_csr(torch, S)
+    h = torch.full((S.n,), -1, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for deficit_roots in (True, False):
+        assert _call(torch, S.n, S.s, S.t, arrs, h, deficit_roots) == native.OK
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        assert free1 == free0, (free0, free1)
+        np.testing.assert_array_equal(h.cpu().numpy(), R.heights(0, 2999, deficit_roots=deficit_roots))
+    S.close()
 
 
 def test_noalloc_rejects_sizes_beyond_the_maximum():
@@ -88,4 +125,6 @@ def test_noalloc_rejects_sizes_beyond_the_maximum():
     rc = native.maxflow_global_relabel_noalloc(big, 0, 1, fake, fake, fake, fake, fake, fake, fake, True, None)
     assert rc == native.ERR_TOO_LARGE
     rc = native.maxflow_global_relabel_noalloc(10, 3, 3, fake, fake, fake, fake, fake, fake, fake, True, None)
+    assert rc == native.ERR_INVALID
+    rc = native.maxflow_global_relabel_noalloc(1, 0, 0, fake, fake, fake, fake, fake, fake, fake, True, None)
     assert rc == native.ERR_INVALID
