@@ -89,12 +89,16 @@ typedef struct {
     int32_t kernel_cycles;      /* push/relabel cycles per vertex per discharge (Alg. 2's KERNEL_CYCLES);
                                    0 = max(1, ceil(m / n)), the paper's average-degree heuristic (Sec. 6.1) */
     int32_t data_driven;        /* 1: worklist of active vertices (Sec. 5.2.1 O1); 0: topology-driven */
-    int32_t fix_steep;          /* 1: run remove-invalid-edges (Alg. 3) after each discharge */
+    int32_t fix_steep;          /* 1: run remove-invalid-edges (Alg. 3) after each iteration's discharge;
+                                   0 (the default): skip it -- every iteration starts with an exact global
+                                   relabel, which restores h(u) <= h(v) + 1 on every residual edge, and
+                                   Alg. 3's whole-residual pushes create deficits that cost iterations */
     int32_t grid_blocks;        /* cooperative grid size; 0 = sized from the graph and the GPU */
     int64_t max_iters;          /* outer-iteration cap per solve; 0 = 4n + 1000 */
     double  time_limit_s;       /* device wall-clock cap per solve; 0 = 120 s */
     double  wait_limit_s;       /* cap on any single device-side wait (grid barrier); 0 = 1 s */
-    float   slack_factor;       /* spare slots per vertex for insertions: max(slack_min, ceil(deg * factor)) */
+    float   slack_factor;       /* spare slots per vertex for insertions: max(slack_min, ceil(deg * factor)),
+                                   rounded up so that every row's size is a multiple of 4 slots */
     int32_t slack_min;
     int32_t device;             /* CUDA device ordinal; -1 = the current device */
     void   *stream;             /* cudaStream_t for all work of the context; NULL = legacy default stream */
@@ -187,15 +191,48 @@ int maxflow_set_kernel_cycles(maxflow_ctx *c, int32_t k);
  * over more discharge work.  MAXFLOW_ERR_INVALID below 0. */
 int maxflow_set_rounds(maxflow_ctx *c, int32_t rounds);
 
+/* With on = 1 (the default), a vertex that still has excess and a height
+ * below n after its KERNEL_CYCLES cycles in a discharge round is discharged
+ * again in the next round of the same iteration (when one follows), instead of
+ * waiting for the next global relabel; on = 0 keeps only the vertices that
+ * became active during the round.  Not in the paper (it steers work only: the
+ * value and the certificate do not depend on it).  MAXFLOW_ERR_INVALID unless
+ * on is 0 or 1. */
+int maxflow_set_requeue(maxflow_ctx *c, int32_t on);
+
+/* Cycles by row length: with div > 0, a vertex whose row has d slots gets
+ * max(KERNEL_CYCLES, d / div) cycles per discharge call, so a long row (whose
+ * first scan costs most of its discharge) makes more pushes per scan; 0 (the
+ * default) gives every vertex KERNEL_CYCLES.  Not in the paper (it steers
+ * work only).  MAXFLOW_ERR_INVALID below 0. */
+int maxflow_set_cycle_div(maxflow_ctx *c, int32_t div);
+
+/* Small BFS levels on one CTA: a top-down level whose frontier holds at most
+ * `slots` slots (and at most as many vertices) runs in the first CTA alone,
+ * level after level, without a grid barrier between levels (the labels are
+ * those of Alg. 4 / Alg. 6 either way); the grid meets again when a frontier
+ * grows past the limit, the BFS ends, or after 256 such levels.  0 turns it
+ * off; the default is 2048.  Not in the paper.  MAXFLOW_ERR_INVALID below 0. */
+int maxflow_set_bfs_tail(maxflow_ctx *c, int32_t slots);
+
+/* Run remove-invalid-edges (Alg. 3) after each iteration's discharge rounds
+ * (on = 1) or not (on = 0) from the next solve on; the same switch as
+ * maxflow_opts.fix_steep.  MAXFLOW_ERR_INVALID unless on is 0 or 1. */
+int maxflow_set_fix_steep(maxflow_ctx *c, int32_t on);
+
 /* ---- learned schedule (an addition to the paper's fixed KERNEL_CYCLES) ----
  *
  * A schedule (action) is a mode -- 0: incremental re-solve (Alg. 5), 1: apply
  * the batch then re-solve from zero flow (Alg. 1) -- with a number of
- * discharge rounds and of KERNEL_CYCLES (0: the average-degree heuristic).
- * The action table is fixed; maxflow_sched_actions returns it (pass NULL
- * arrays to get only the count).  A schedule never changes the result, only
- * the work. */
-int maxflow_sched_actions(int32_t *mode, int32_t *rounds, int32_t *cycles, int32_t cap, int32_t *count);
+ * discharge rounds (0: adaptive), of KERNEL_CYCLES (0: the average-degree
+ * heuristic of Sec. 6.1), a row-length divisor for the cycles
+ * (maxflow_set_cycle_div) and whether remove-invalid-edges (Alg. 3) runs.
+ * Action 0 is the library's default schedule, action 5 the paper's fixed
+ * one.  The action table is fixed; maxflow_sched_actions returns it (host
+ * arrays of cap entries; pass all NULL to get only the count).  A schedule
+ * never changes the result, only the work. */
+int maxflow_sched_actions(int32_t *mode, int32_t *rounds, int32_t *cycles, int32_t *cycle_div, int32_t *fix,
+                          int32_t cap, int32_t *count);
 
 /* The 16 scheduler features of a batch for this context (host array of 16
  * floats): batch size and fraction of the graph, graph size and degree, the
@@ -415,7 +452,9 @@ int maxflow_stats(maxflow_ctx *c, maxflow_stats_t *out);
  * entry.  Boundary ids: 0 start, 1 prologue step, 2 batch validated,
  * 3 batch located, 4 room checked, 5 capacities changed, 6 iteration start,
  * 7 BFS roots set, 8 BFS level done, 9 worklist built, 10 discharge done,
- * 11 end.  *count receives the number of entries written.  Host arrays. */
+ * 11 end, 12 first pass of a bottom-up BFS level done (its long rows follow),
+ * 13 the grid meets again after BFS levels that the first CTA ran alone.
+ * *count receives the number of entries written.  Host arrays. */
 int maxflow_trace(maxflow_ctx *c, int32_t *boundary, double *t_us, int32_t cap, int32_t *count);
 
 /* The work of the phases in the same timeline (entry i belongs to boundary i
@@ -425,9 +464,14 @@ int maxflow_trace(maxflow_ctx *c, int32_t *boundary, double *t_us, int32_t cap, 
  * bottom-up, bits 20-29 the work items of long rows it expanded (capped at
  * 1023), bits 0-19 the vertices it labelled (capped at 2^20 - 1); for a
  * discharge round (boundary 10): bits 20-29 the vertices of the CTA-per-vertex
- * bin, bits 0-19 all vertices of the round's lists; 0 otherwise.  Either array
- * may be NULL.  Host arrays.  No counterpart in the paper (instrumentation). */
-int maxflow_trace_work(maxflow_ctx *c, int64_t *slots, int32_t *info, int32_t cap, int32_t *count);
+ * bin, bits 0-19 all vertices of the round's lists; 0 otherwise.
+ * cta_last_us[i] / cta_mean_us[i]: when the last CTA and the average CTA
+ * finished the phase that barrier i closed, in microseconds after the release
+ * of the barrier before it (0 for phases that do not record it): a last CTA
+ * far behind the mean marks a phase bound by a few long rows.  Any array may
+ * be NULL.  Host arrays.  No counterpart in the paper (instrumentation). */
+int maxflow_trace_work(maxflow_ctx *c, int64_t *slots, int32_t *info, double *cta_last_us, double *cta_mean_us,
+                       int32_t cap, int32_t *count);
 
 /* Release every resource of the context (NULL is a no-op). */
 void maxflow_destroy(maxflow_ctx *c);

@@ -49,6 +49,9 @@ struct maxflow_ctx {
     int multi_cap = 0;
     int grid = 1, per_sm = 1, sms = 1;
     int32_t stage_slots = 0;      // dynamic shared memory of the solve launches, in ints
+    int32_t requeue = 1;          // discharge rounds re-queue vertices still active after their cycles
+    int32_t cycle_div = 0;        // > 0: long rows get max(kernel_cycles, deg / cycle_div) cycles
+    int32_t tail_slots = MF_TAIL_SLOTS;   // BFS frontiers of at most this many slots run in one CTA
     MfGraph g{};
     MfScratch sc{};
     MfCtrl *ctrl = nullptr;
@@ -178,6 +181,9 @@ MfParams base_params(maxflow_ctx *c)
     p.side_root = -1;
     p.test_skip_cta = -1;
     p.stage_slots = c->stage_slots;
+    p.requeue = c->requeue;
+    p.cycle_div = c->cycle_div;
+    p.tail_slots = c->tail_slots;
     p.side = c->pp.side;
     p.max_iters = c->opt.max_iters > 0 ? c->opt.max_iters : 4LL * c->n + 1000;
     double tl = c->opt.time_limit_s > 0 ? c->opt.time_limit_s : 120.0;
@@ -625,7 +631,7 @@ void maxflow_default_opts(maxflow_opts *o)
     std::memset(o, 0, sizeof(*o));
     o->kernel_cycles = 0;
     o->data_driven = 1;
-    o->fix_steep = 1;
+    o->fix_steep = 0;        // Alg. 3 off by default: the exact global relabel opens every iteration
     o->grid_blocks = 0;
     o->max_iters = 0;
     o->time_limit_s = 0;
@@ -877,7 +883,8 @@ int maxflow_trace(maxflow_ctx *c, int32_t *boundary, double *t_us, int32_t cap, 
     return MAXFLOW_OK;
 }
 
-int maxflow_trace_work(maxflow_ctx *c, int64_t *slots, int32_t *info, int32_t cap, int32_t *count)
+int maxflow_trace_work(maxflow_ctx *c, int64_t *slots, int32_t *info, double *cta_last_us, double *cta_mean_us,
+                       int32_t cap, int32_t *count)
 {
     if (!c || !count || cap < 0) return MAXFLOW_ERR_INVALID;
     const MfCtrl &h = *c->hctrl;
@@ -885,6 +892,8 @@ int maxflow_trace_work(maxflow_ctx *c, int64_t *slots, int32_t *info, int32_t ca
     for (int i = 0; i < k; ++i) {
         if (slots) slots[i] = h.trace_slots[i];
         if (info) info[i] = h.trace_info[i];
+        if (cta_last_us) cta_last_us[i] = h.trace_fin_max[i] * 1e-3;
+        if (cta_mean_us) cta_mean_us[i] = h.trace_fin_mean[i] * 1e-3;
     }
     *count = k;
     return MAXFLOW_OK;
@@ -905,19 +914,20 @@ namespace {
 
 struct SchedAction {
     int32_t mode;      // 0: incremental (Alg. 5), 1: apply the batch, then re-solve from zero flow (Alg. 1)
-    int32_t rounds;
-    int32_t cycles;    // 0: the average-degree heuristic of Sec. 6.1
+    int32_t rounds;    // discharge rounds per global relabel (0: adaptive)
+    int32_t cycles;    // KERNEL_CYCLES (0: the average-degree heuristic of Sec. 6.1)
+    int32_t cycle_div; // > 0: rows of d slots get max(cycles, d / cycle_div) cycles
+    int32_t fix;       // 1: remove-invalid-edges (Alg. 3) after each iteration's discharge
 };
 
-// Index 16 is the paper's fixed schedule (one round, KERNEL_CYCLES = average
-// degree) and 17 the library's default (adaptive rounds).
+// Index 0 is the library's default schedule, 5 the paper's fixed one (one
+// round, KERNEL_CYCLES = average degree, Alg. 3 after every discharge) and 18
+// the paper's static re-solve.
 const SchedAction kActions[] = {
-    {0, 1, 1}, {0, 1, 4}, {0, 1, 16}, {0, 1, 64},
-    {0, 4, 1}, {0, 4, 4}, {0, 4, 16}, {0, 4, 64},
-    {0, 16, 1}, {0, 16, 4}, {0, 16, 16}, {0, 16, 64},
-    {0, 64, 1}, {0, 64, 4}, {0, 64, 16}, {0, 64, 64},
-    {0, 1, 0}, {0, 0, 0},
-    {1, 4, 4}, {1, 16, 16}, {1, 64, 16}, {1, 1, 0},
+    {0, 0, 0, 0, 0},   {0, 0, 0, 256, 0}, {0, 0, 4, 0, 0},   {0, 0, 64, 0, 0},  {0, 0, 64, 256, 0},
+    {0, 1, 0, 0, 1},   {0, 1, 16, 0, 0},  {0, 1, 64, 0, 0},  {0, 4, 4, 0, 0},   {0, 4, 16, 0, 0},
+    {0, 4, 64, 0, 0},  {0, 16, 4, 0, 0},  {0, 16, 16, 0, 0}, {0, 16, 64, 0, 0}, {0, 64, 16, 0, 0},
+    {0, 64, 64, 0, 0}, {1, 0, 0, 0, 0},   {1, 0, 64, 0, 0},  {1, 1, 0, 0, 1},   {1, 16, 16, 0, 0},
 };
 constexpr int kNumActions = (int)(sizeof(kActions) / sizeof(kActions[0]));
 
@@ -963,10 +973,12 @@ int stage_and_features(maxflow_ctx *c, const maxflow_batch *b, maxflow_batch *de
 int run_action(maxflow_ctx *c, const maxflow_batch *dev_batch, int a)
 {
     const SchedAction &A = kActions[a];
-    const int32_t keep_k = c->kernel_cycles, keep_r = c->rounds;
+    const int32_t keep_k = c->kernel_cycles, keep_r = c->rounds, keep_div = c->cycle_div, keep_fix = c->opt.fix_steep;
     int64_t m = c->st.m_edges;
     c->kernel_cycles = A.cycles > 0 ? A.cycles : (int32_t)std::max<int64_t>(1, (m + c->n - 1) / c->n);
     c->rounds = A.rounds;
+    c->cycle_div = A.cycle_div;
+    c->opt.fix_steep = A.fix;
     int rc;
     if (A.mode == 0) {
         rc = do_batch(c, dev_batch, MF_M_APPLY | MF_M_SOLVE);
@@ -983,12 +995,15 @@ int run_action(maxflow_ctx *c, const maxflow_batch *dev_batch, int a)
     }
     c->kernel_cycles = keep_k;
     c->rounds = keep_r;
+    c->cycle_div = keep_div;
+    c->opt.fix_steep = keep_fix;
     return rc;
 }
 
 }  // namespace
 
-int maxflow_sched_actions(int32_t *mode, int32_t *rounds, int32_t *cycles, int32_t cap, int32_t *count)
+int maxflow_sched_actions(int32_t *mode, int32_t *rounds, int32_t *cycles, int32_t *cycle_div, int32_t *fix,
+                          int32_t cap, int32_t *count)
 {
     if (!count || cap < 0) return MAXFLOW_ERR_INVALID;
     int k = std::min(cap, kNumActions);
@@ -996,8 +1011,10 @@ int maxflow_sched_actions(int32_t *mode, int32_t *rounds, int32_t *cycles, int32
         if (mode) mode[i] = kActions[i].mode;
         if (rounds) rounds[i] = kActions[i].rounds;
         if (cycles) cycles[i] = kActions[i].cycles;
+        if (cycle_div) cycle_div[i] = kActions[i].cycle_div;
+        if (fix) fix[i] = kActions[i].fix;
     }
-    *count = (mode || rounds || cycles) ? k : kNumActions;
+    *count = (mode || rounds || cycles || cycle_div || fix) ? k : kNumActions;
     return MAXFLOW_OK;
 }
 
@@ -1503,6 +1520,34 @@ int maxflow_update_pp(maxflow_ctx *c, const maxflow_batch *b, int32_t stop_after
     return rc;
 }
 
+int maxflow_set_requeue(maxflow_ctx *c, int32_t on)
+{
+    if (!c || on < 0 || on > 1) return MAXFLOW_ERR_INVALID;
+    c->requeue = on;
+    return MAXFLOW_OK;
+}
+
+int maxflow_set_cycle_div(maxflow_ctx *c, int32_t div)
+{
+    if (!c || div < 0) return MAXFLOW_ERR_INVALID;
+    c->cycle_div = div;
+    return MAXFLOW_OK;
+}
+
+int maxflow_set_bfs_tail(maxflow_ctx *c, int32_t slots)
+{
+    if (!c || slots < 0) return MAXFLOW_ERR_INVALID;
+    c->tail_slots = slots;
+    return MAXFLOW_OK;
+}
+
+int maxflow_set_fix_steep(maxflow_ctx *c, int32_t on)
+{
+    if (!c || on < 0 || on > 1) return MAXFLOW_ERR_INVALID;
+    c->opt.fix_steep = on;
+    return MAXFLOW_OK;
+}
+
 int maxflow_set_rounds(maxflow_ctx *c, int32_t rounds)
 {
     if (!c || rounds < 0 || rounds > (1 << 20)) return MAXFLOW_ERR_INVALID;
@@ -1535,6 +1580,9 @@ int maxflow_clone(maxflow_ctx *src, maxflow_ctx **out)
     c->bfs_hub = src->bfs_hub;
     c->per_sm = src->per_sm;
     c->stage_slots = src->stage_slots;
+    c->requeue = src->requeue;
+    c->cycle_div = src->cycle_div;
+    c->tail_slots = src->tail_slots;
     c->sms = src->sms;
     c->st = src->st;
     c->solved = src->solved;

@@ -62,10 +62,14 @@ int layout(int32_t n, std::vector<int64_t> &rstart, std::vector<SlotRec> &recs, 
            int32_t slack_min, MfHostGraph &out)
 {
     out.n = n;
+    // every row starts on a multiple of MF_ROW_ALIGN slots (16 bytes), so the
+    // kernels can read a row's slot fields four at a time with 16-byte loads
     std::vector<int64_t> offs((size_t)n + 1, 0);
     for (int32_t u = 0; u < n; ++u) {
         int64_t d = rstart[u + 1] - rstart[u];
-        offs[u + 1] = offs[u] + d + slack_of(d, slack_factor, slack_min);
+        int64_t r = d + slack_of(d, slack_factor, slack_min);
+        r = (r + MF_ROW_ALIGN - 1) / MF_ROW_ALIGN * MF_ROW_ALIGN;
+        offs[u + 1] = offs[u] + r;
     }
     if (offs[n] >= (int64_t)INT32_MAX - 1) return MAXFLOW_ERR_TOO_LARGE;
     out.slot_cap = offs[n];

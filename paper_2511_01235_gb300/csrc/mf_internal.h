@@ -29,8 +29,11 @@
 #define MF_BU_ALPHA 14        // BFS default: go bottom-up when the frontier's slots exceed the unexplored slots / alpha
 #define MF_BU_BETA 24         // BFS default: back to top-down when the frontier holds fewer than n / beta vertices
 #define MF_WARP_STAGE 512     // discharge: largest row a warp keeps on chip (per-warp slice of the snapshot)
-#define MF_BU_SCAN 32         // bottom-up BFS: slots of its row a thread scans itself before deferring the rest
+#define MF_ROW_ALIGN 4        // rows start on multiples of this many slots (16-byte loads of slot fields)
+#define MF_BU_SCAN 256        // bottom-up BFS: slots of a row its warp scans before deferring the rest
 #define MF_BU_CHUNK 256       // bottom-up BFS: slots per deferred work item (one warp, 8 per lane)
+#define MF_TAIL_SLOTS 2048    // BFS default: frontiers up to this many slots run in one CTA
+#define MF_TAIL_RUN 256       // BFS: levels CTA 0 runs alone before the grid meets once (bounds the others' wait)
 
 // Solve-kernel status (ctrl->status)
 #define MF_ST_RUNNING 0
@@ -97,6 +100,7 @@ struct MfCtrl {
     unsigned long long t_bfs0, t_dis0;   // this iteration: BFS start, discharge start (adaptive rounds)
     int bu_mode;          // the coming BFS level runs bottom-up
     int bu_split;         // the bottom-up level just scanned deferred long rows: their pass follows
+    int bfs_cta_mode;     // the coming top-down level is small: CTA 0 runs it (and the next small ones) alone
     int defer_n;          // work items of that pass
     int need_total;       // the coming BFS initialisation sums the used slots (first BFS of a launch)
     long long vis_slots;  // slots of the vertices labelled so far in this BFS
@@ -124,6 +128,10 @@ struct MfCtrl {
     // discharge round: bits 20..29 = CTA-bin (hub) vertices, bits 0..19 = vertices in the round's lists
     long long trace_slots[MF_TRACE];
     int trace_info[MF_TRACE];
+    // when the CTAs finished the phase that a barrier closes (ns after the previous barrier's release):
+    // the last one and the mean, per traced barrier
+    unsigned long long fin_max, fin_sum;
+    unsigned trace_fin_max[MF_TRACE], trace_fin_mean[MF_TRACE];
 };
 
 struct MfGraph {
@@ -185,6 +193,10 @@ struct MfParams {
                               // else only side[v] == side_root
     uint8_t *side;            // [n] sides of the last cut (1: reaches t or a deficit, 0: not); written by MF_M_CUT
     int32_t test_skip_cta;    // >= 0: that CTA never arrives at the first barrier (tests the bounded waits)
+    int32_t requeue;          // discharge rounds: a vertex still active after its cycles joins the next round
+    int32_t cycle_div;        // > 0: a row of d slots gets max(kernel_cycles, d / cycle_div) cycles
+    int32_t tail_slots;       // BFS: a top-down level whose frontier holds at most this many slots (and
+                              // vertices) runs in CTA 0 alone, without grid barriers; 0: never
     int32_t stage_slots;      // dynamic shared memory of the launch in ints: the discharge's on-chip row snapshot
                               // (a CTA keeps rows up to this many slots; 0: none)
     long long max_iters;

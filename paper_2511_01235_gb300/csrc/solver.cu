@@ -43,6 +43,17 @@ extern __shared__ __align__(16) int mf_stage[];
 __device__ __forceinline__ int vb() { return g_vb; }
 __device__ __forceinline__ int vn() { return g_vn; }
 
+// First work index of this thread in a grid-stride loop (stride vn() *
+// blockDim.x) that spreads a short list over the whole grid: consecutive
+// indices go to different CTAs, so a batch of a few thousand updates keeps
+// every SM's memory pipeline busy instead of crowding onto the first CTAs.
+// spread_warp keeps 32 consecutive indices in one warp (warp-uniform loops).
+__device__ __forceinline__ long long spread_thread() { return (long long)threadIdx.x * vn() + vb(); }
+__device__ __forceinline__ long long spread_warp()
+{
+    return ((long long)(threadIdx.x >> 5) * vn() + vb()) * 32 + (threadIdx.x & 31);
+}
+
 __device__ __forceinline__ int ldg_cg(const int *p) { return __ldcg(p); }
 __device__ __forceinline__ long long ldg_cg(const long long *p) { return __ldcg(p); }
 
@@ -136,6 +147,7 @@ enum Hook {
     H_DIS,
     H_FINAL,
     H_BU_SPLIT,
+    H_BFS_JOIN,
 };
 
 __device__ __forceinline__ int rd(const int &x) { return __ldcg(&x); }
@@ -207,6 +219,7 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
     const int sel = rd(c->wl_sel), round = rd(c->round), qstamp = rd(c->qstamp), fstamp = rd(c->fstamp);
     const long long rounds_total = rd(c->rounds_total);
     const long long slots_all = rd(c->slots_bfs) + rd(c->slots_dis) + rd(c->slots_fix);
+    const unsigned long long fin_max = rd(c->fin_max), fin_sum = rd(c->fin_sum);
     const int bu_prev = rd(c->bu_mode);
     int wl_prev[3];
     for (int b = 0; b < 3; ++b) wl_prev[b] = rd(c->wl_n[b]);
@@ -230,6 +243,7 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
         c->slots_bfs = c->verts_bfs = c->slots_dis = c->cycles_dis = c->slots_fix = c->verts_fix = 0;
         c->verts_wl = c->n_apply = 0;
         c->lab_bfs = c->slots_apply = c->clamps_apply = c->hscan_bfs = 0;
+        c->fin_max = c->fin_sum = 0;
         c->ns_bfs = c->ns_dis = c->ns_fix = c->ns_wl = c->ns_apply = 0;
         c->bfs_tail.w[0] = 0;
         c->hub_tail.w[0] = 0;
@@ -242,6 +256,7 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
         for (int i = 0; i < 8; ++i) c->aux_tail.w[i] = 0;
         for (int i = 0; i < 8; ++i) c->bfs_acc.w[i] = 0;
         c->bu_mode = 0;
+        c->bfs_cta_mode = 0;
         c->need_total = 1;
         c->round = 0;
         c->dis_more = 0;
@@ -310,6 +325,9 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
             else if (bu && cnt * P.bu_beta < (long long)P.g.n) bu = 0;
             c->bu_mode = bu;
             c->vis_slots = vis;
+            // a small top-down frontier is expanded by CTA 0 alone: a level of a
+            // few hundred slots costs a grid barrier otherwise
+            c->bfs_cta_mode = (!done && !bu && P.tail_slots > 0 && fr <= P.tail_slots && cnt <= P.tail_slots) ? 1 : 0;
             c->bfs_acc.w[0] = c->bfs_acc.w[1] = c->bfs_acc.w[2] = c->bfs_acc.w[3] = 0;   // per level; [2] stays
         }
         if (done && want_wl) decide_iteration(P, c, now, wl, iters, t_start, qstamp, fstamp);
@@ -358,6 +376,9 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
     }
     case H_FINAL:
         break;
+    case H_BFS_JOIN:
+        c->ns_bfs = rd(c->ns_bfs) + dt;
+        break;
     case H_BU_SPLIT:
         c->ns_bfs = rd(c->ns_bfs) + dt;
         tinfo = (1 << 30) | (int)min((long long)rd(c->defer_n), (long long)((1 << 20) - 1));
@@ -368,7 +389,11 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
         c->trace_t[trace_n] = now;
         c->trace_slots[trace_n] = slots_all;
         c->trace_info[trace_n] = tinfo;
+        c->trace_fin_max[trace_n] = (unsigned)min(fin_max, 0xffffffffull);
+        c->trace_fin_mean[trace_n] = (unsigned)min(fin_sum / (unsigned long long)vn(), 0xffffffffull);
     }
+    c->fin_max = 0;
+    c->fin_sum = 0;
     if (err != 0) c->status = MF_ST_ERROR;
 }
 
@@ -425,6 +450,13 @@ __device__ void flush_acc(const MfParams &P, Sh &sh, int phase)
     __syncthreads();
     if (threadIdx.x == 0) {
         MfCtrl *c = P.ctrl;
+        {
+            // when this CTA finished the phase, after the release of the barrier that opened it
+            const unsigned long long t0 = rd(c->t_phase), now = gtimer();
+            const unsigned long long d = now > t0 ? now - t0 : 0;
+            atomicMax(&c->fin_max, d);
+            atomicAdd(&c->fin_sum, d);
+        }
         if (sh.sink_e) atomic_add_ll(P.e + P.sink, sh.sink_e);
         if (sh.src_e) atomic_add_ll(P.e + P.source, sh.src_e);
         if (sh.pushes) atomic_add_ll(&c->pushes, sh.pushes);
@@ -624,8 +656,7 @@ __device__ __noinline__ void phase_apply_validate(const MfParams &P)
     const unsigned mask = (1u << bits) - 1u;
     const int lane = threadIdx.x & 31;
     // warp-uniform loop: the positions taken in the table are appended with one atomic per warp
-    for (long long base = (long long)vb() * blockDim.x + threadIdx.x - lane; base < P.bcount;
-         base += (long long)vn() * blockDim.x) {
+    for (long long base = spread_warp() - lane; base < P.bcount; base += (long long)vn() * blockDim.x) {
         const long long i = base + lane;
         bool fresh = false;
         unsigned pos = 0;
@@ -721,8 +752,7 @@ __device__ __noinline__ void phase_apply_locate(const MfParams &P, Sh &sh)
     const unsigned mask = (1u << bits) - 1u;
     const int lane = threadIdx.x & 31;
     int probes = 0;
-    for (long long base = (long long)vb() * blockDim.x + threadIdx.x - lane; base < P.bcount;
-         base += (long long)vn() * blockDim.x) {
+    for (long long base = spread_warp() - lane; base < P.bcount; base += (long long)vn() * blockDim.x) {
         const long long i = base + lane;
         bool fresh = false;
         unsigned pp = 0;
@@ -772,7 +802,7 @@ __device__ __noinline__ void phase_apply_check(const MfParams &P)
 {
     MfCtrl *ctl = P.ctrl;
     const int nins = vrd(&ctl->ins_n);
-    for (int k = vb() * blockDim.x + threadIdx.x; k < nins; k += vn() * blockDim.x) {
+    for (long long k = spread_thread(); k < nins; k += (long long)vn() * blockDim.x) {
         unsigned long long pk = __ldcg(P.sc.pkey + __ldcg(P.sc.ins_list + k));
         int a = (int)(pk >> 32), b = (int)(pk & 0xffffffffu);
         int room_a = P.g.off[a + 1] - P.g.off[a] - ldg_cg(P.g.deg + a);
@@ -804,7 +834,7 @@ __device__ __noinline__ void phase_apply_change(const MfParams &P, Sh &sh)
     MfCtrl *ctl = P.ctrl;
     const int nins = vrd(&ctl->ins_n);
     long long applied = 0, clamped = 0;
-    for (int k = vb() * blockDim.x + threadIdx.x; k < nins; k += vn() * blockDim.x) {
+    for (long long k = spread_thread(); k < nins; k += (long long)vn() * blockDim.x) {
         int pp = __ldcg(P.sc.ins_list + k);
         unsigned long long pk = __ldcg(P.sc.pkey + pp);
         int a = (int)(pk >> 32), b = (int)(pk & 0xffffffffu);
@@ -826,8 +856,7 @@ __device__ __noinline__ void phase_apply_change(const MfParams &P, Sh &sh)
         P.sc.ins_need[b] = 0;
         applied += (ca >= 0 ? 1 : 0) + (cb >= 0 ? 1 : 0);
     }
-    for (long long i = (long long)vb() * blockDim.x + threadIdx.x; i < P.bcount;
-         i += (long long)vn() * blockDim.x) {
+    for (long long i = spread_thread(); i < P.bcount; i += (long long)vn() * blockDim.x) {
         const int x = __ldcg(P.sc.bslot + i);
         if (x < 0) continue;                 // superseded, ignored, or a new pair (set above)
         int u, v, c;
@@ -1121,14 +1150,18 @@ __device__ __noinline__ void phase_bfs_level(const MfParams &P, Sh &sh)
             bfs_visit<kBR>(P, sh, xs, vs, L, sel);
         }
     }
-    // regular frontier: warps take 32 vertices at a time and expand their
-    // rows together (each lane finds the vertex that owns its slot)
+    // regular frontier: warps take up to 32 vertices at a time and expand their
+    // rows together (each lane finds the vertex that owns its slot); a small
+    // frontier is dealt out fewer vertices per warp, so that its rows spread
+    // over many warps instead of queueing in one
     const int lo = vrd(&ctl->lvl_lo), cnt = vrd(&ctl->lvl_hi) - lo;
+    const int nwarps = (vrd(&ctl->bfs_cta_mode) ? 1 : vn()) * (int)(blockDim.x >> 5);
+    const int take = max(1, min(32, cnt / max(1, nwarps)));
     for (;;) {
-        const int b = warp_grab(&ctl->head0.w[0], cnt, 32u);
+        const int b = warp_grab(&ctl->head0.w[0], cnt, (unsigned)take);
         if (b >= cnt) break;
         int idx = b + lane;
-        int u = idx < cnt ? __ldcg(P.sc.border + lo + idx) : -1;
+        int u = (lane < take && idx < cnt) ? __ldcg(P.sc.border + lo + idx) : -1;
         int d = u >= 0 ? ldg_cg(P.g.deg + u) : 0;
         int r0 = u >= 0 ? P.g.off[u] : 0;
         int incl = d;
@@ -1183,60 +1216,103 @@ __device__ __noinline__ void phase_bfs_bottom_up(const MfParams &P, Sh &sh)
     const bool with_wl = P.data_driven && !(P.mode & MF_M_BFS_ONLY);
     const int lane = threadIdx.x & 31;
     const long long gs = (long long)vn() * blockDim.x;
-    // a thread scans at most MF_BU_SCAN slots of its row; the rest of a longer
-    // row goes to the level's second pass as work items, so no thread walks a
-    // long row alone
+    // A warp takes 32 vertices.  Each unlabelled one first looks at kA slots of
+    // its row alone; the rows still open after that are scanned by the whole
+    // warp together, 128 slots per step over their concatenation (each lane
+    // finds the row that owns its slot), and a row drops out of the scan as
+    // soon as one of its slots finds a neighbour of level L.  Slots past
+    // MF_BU_SCAN of a row go to the level's second pass as work items, so no
+    // warp walks a very long row alone.
+    constexpr int kA = 4;
     const int cap = P.sc.bdefer != nullptr ? MF_BU_SCAN : 0x7fffffff;
     long long slots = 0, unl = 0;
     if (vb() == 0 && threadIdx.x == 0) sh.cycles += n;    // every vertex's height is read
     for (long long base = (long long)vb() * blockDim.x + threadIdx.x - lane; base < n; base += gs) {
         const int v = (int)base + lane;
+        const bool ok = v < n && v != skip;
+        const int hv = ok ? ldg_cg(P.h + v) : 0;
+        const int r0 = ok ? P.g.off[v] : 0;
+        const int d = ok ? ldg_cg(P.g.deg + v) : 0;
+        const bool open = ok && hv == n;
         bool take[1] = {false};
-        int zv[1] = {v}, dv[1] = {0};
+        int zv[1] = {v}, dv[1] = {d};
         long long ev[1] = {0};
-        int nitem = 0, x0 = 0;
-        if (v < n && v != skip && ldg_cg(P.h + v) == n) {
-            const int r0 = P.g.off[v], d = ldg_cg(P.g.deg + v);
-            const int lim = d < cap ? d : cap;
+        if (open) {
             ++unl;
-            int j = 0;
-            for (; j < lim && !take[0]; j += 4) {
-                int c[4], z[4], hz[4];
+            int c[kA], z[kA];
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const int x = r0 + j + r;
-                    const bool ok = j + r < lim;
-                    c[r] = ok ? (pull ? ldg_cg(P.g.pcap + x) - ldg_cg(P.cf + x) : ldg_cg(P.cf + x)) : 0;
-                    z[r] = ok ? ldg_cg(P.g.dst + x) : 0;
+            for (int r = 0; r < kA; ++r) {
+                const int x = r0 + r;
+                const bool in = r < d;
+                c[r] = in ? (pull ? ldg_cg(P.g.pcap + x) - ldg_cg(P.cf + x) : ldg_cg(P.cf + x)) : 0;
+                z[r] = in ? ldg_cg(P.g.dst + x) : 0;
+            }
+#pragma unroll
+            for (int r = 0; r < kA; ++r) take[0] |= c[r] > 0 && ldg_cg(P.h + z[r]) == L;
+            slots += d < kA ? d : kA;
+        }
+        // the warp-cooperative scan of the rows still open
+        const int lim = d < cap ? d : cap;
+        const int rem = (open && !take[0] && lim > kA) ? lim - kA : 0;
+        int incl = rem;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int excl = incl - rem;
+        const int T = __shfl_sync(0xffffffffu, incl, 31);
+        const unsigned pend = __ballot_sync(0xffffffffu, rem > 0);
+        unsigned hit = 0;
+        for (int kb = 0; kb < T && (pend & ~hit) != 0; kb += 32 * kA) {
+            int c[kA], z[kA], ow[kA];
+#pragma unroll
+            for (int r = 0; r < kA; ++r) {
+                const int k = kb + r * 32 + lane;
+                int owner = 0;
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1) {
+                    const int cand = owner + step;
+                    const int ec = __shfl_sync(0xffffffffu, excl, cand & 31);
+                    if (cand < 32 && ec <= k) owner = cand;
                 }
-#pragma unroll
-                for (int r = 0; r < 4; ++r) hz[r] = c[r] > 0 ? ldg_cg(P.h + z[r]) : -1;
-#pragma unroll
-                for (int r = 0; r < 4; ++r) take[0] |= hz[r] == L;
+                const int rb = __shfl_sync(0xffffffffu, r0, owner);
+                const int eb = __shfl_sync(0xffffffffu, excl, owner);
+                const bool live = k < T && !((hit >> owner) & 1u);
+                const int x = rb + kA + (k - eb);
+                ow[r] = owner;
+                c[r] = live ? (pull ? ldg_cg(P.g.pcap + x) - ldg_cg(P.cf + x) : ldg_cg(P.cf + x)) : 0;
+                z[r] = live ? ldg_cg(P.g.dst + x) : 0;
+                slots += live ? 1 : 0;
             }
-            slots += j < lim ? j : lim;
-            if (take[0]) {
-                P.h[v] = L + 1;
-                dv[0] = d;
-                if (with_wl && v != P.sink && v != P.source) ev[0] = pull ? -ldg_cg(P.e + v) : ldg_cg(P.e + v);
-            } else if (d > lim) {
-                nitem = (d - lim + MF_BU_CHUNK - 1) / MF_BU_CHUNK;
-                x0 = r0 + lim;
-            }
+            unsigned mine = 0;
+#pragma unroll
+            for (int r = 0; r < kA; ++r)
+                if (c[r] > 0 && ldg_cg(P.h + z[r]) == L) mine |= 1u << ow[r];
+            hit |= __reduce_or_sync(0xffffffffu, mine);
+        }
+        if ((hit >> lane) & 1u) take[0] = true;
+        int nitem = 0, x0 = 0;
+        if (take[0]) {
+            P.h[v] = L + 1;
+            if (with_wl && v != P.sink && v != P.source) ev[0] = pull ? -ldg_cg(P.e + v) : ldg_cg(P.e + v);
+        } else if (open && d > lim) {
+            nitem = (d - lim + MF_BU_CHUNK - 1) / MF_BU_CHUNK;
+            x0 = r0 + lim;
         }
         if (__any_sync(0xffffffffu, take[0])) frontier_push<1>(P, sh, take, zv, dv, ev, with_wl, sel);
         if (__any_sync(0xffffffffu, nitem > 0)) {
-            int incl = nitem;
+            int ic = nitem;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
+                const int y = __shfl_up_sync(0xffffffffu, ic, o);
+                if (lane >= o) ic += y;
             }
-            const int tot = __shfl_sync(0xffffffffu, incl, 31);
+            const int tot = __shfl_sync(0xffffffffu, ic, 31);
             unsigned at = 0;
             if (lane == 0) at = atomicAdd(&ctl->defer_tail.w[0], (unsigned)tot);
-            at = __shfl_sync(0xffffffffu, at, 0) + (unsigned)(incl - nitem);
-            for (int c = 0; c < nitem; ++c) P.sc.bdefer[at + c] = make_int2(v, x0 + c * MF_BU_CHUNK);
+            at = __shfl_sync(0xffffffffu, at, 0) + (unsigned)(ic - nitem);
+            for (int cc = 0; cc < nitem; ++cc) P.sc.bdefer[at + cc] = make_int2(v, x0 + cc * MF_BU_CHUNK);
         }
     }
     if (slots) atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)slots);
@@ -1354,6 +1430,17 @@ __device__ __forceinline__ void enqueue_active(const MfParams &P, int z, const D
     P.sc.wl[dc.nsel][bin][pos] = z;
 }
 
+// u still has something to move after its KERNEL_CYCLES cycles (excess for a
+// push, a deficit for a pull) and a height below n: with P.requeue it joins the
+// next round's queue too, instead of waiting for the next global relabel.
+template <bool PULL>
+__device__ __forceinline__ void requeue_if_active(const MfParams &P, int u, const DisCtx &dc)
+{
+    if (!P.requeue || !dc.queue) return;
+    const long long eu = ldg_cg(P.e + u);
+    if ((PULL ? eu < 0 : eu > 0) && ldg_cg(P.h + u) < P.g.n) enqueue_active(P, u, dc);
+}
+
 // u was relabelled: list it (once per iteration) for remove-invalid-edges;
 // only relabelled vertices can have steep residual edges.
 __device__ __forceinline__ void note_relabel(const MfParams &P, int u, const DisCtx &dc)
@@ -1447,6 +1534,19 @@ __device__ __forceinline__ unsigned long long scan_lowest(const MfParams &P, int
 // meanwhile wait for the next discharge call.
 constexpr int kNoRes = 0x7fffffff;
 
+// KERNEL_CYCLES of Alg. 2 for a row of d slots: P.kernel_cycles, or with
+// P.cycle_div > 0 at least d / P.cycle_div, so that a long row, whose first
+// scan dominates its discharge, makes more of its pushes per scan.
+__device__ __forceinline__ int cycles_for(const MfParams &P, int d)
+{
+    if (P.cycle_div <= 0) return P.kernel_cycles;
+    const int k = d / P.cycle_div;
+    return k > P.kernel_cycles ? k : P.kernel_cycles;
+}
+// push passes of one discharge call that may find only stale snapshot entries
+// without using up a cycle (each such pass corrects at least one entry upward)
+constexpr int kStaleMax = 8;
+
 // The first scan of a row: the lowest residual height as scan_lowest does, and
 // the snapshot of every slot of the row in stg.
 template <int kU, bool PULL>
@@ -1471,6 +1571,67 @@ __device__ __forceinline__ unsigned long long scan_and_stage(const MfParams &P, 
             if (c[r] > 0) {
                 const unsigned long long key = ((unsigned long long)(unsigned)hz[r] << 32) | (unsigned)j;
                 best = key < best ? key : best;
+            }
+        }
+    }
+    return best;
+}
+
+__device__ __forceinline__ int comp4(const int4 &a, int e)
+{
+    return e == 0 ? a.x : (e == 1 ? a.y : (e == 2 ? a.z : a.w));
+}
+
+// The first scan of a row with 16-byte loads: rows start on multiples of four
+// slots (MF_ROW_ALIGN), so slot group g (slots 4g .. 4g+3) is one int4 of
+// each slot array.  Thread t of nt takes groups t, t + nt, ... two at a time
+// (eight slots in flight).  Same result as scan_and_stage.
+template <bool PULL>
+__device__ __forceinline__ unsigned long long scan_and_stage_v4(const MfParams &P, int r0, int d, int t, int nt,
+                                                                int *stg)
+{
+    unsigned long long best = kEmpty;
+    const int ng = (d + 3) >> 2;
+    const int4 *cf4 = reinterpret_cast<const int4 *>(P.cf + r0);
+    const int4 *dst4 = reinterpret_cast<const int4 *>(P.g.dst + r0);
+    const int4 *pc4 = reinterpret_cast<const int4 *>(P.g.pcap + r0);
+    for (int g0 = t; g0 < ng; g0 += 2 * nt) {
+        int4 c[2], z[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int g = g0 + q * nt;
+            if (g < ng) {
+                c[q] = __ldcg(cf4 + g);
+                z[q] = __ldcg(dst4 + g);
+                if (PULL) {
+                    const int4 pc = __ldcg(pc4 + g);
+                    c[q] = make_int4(pc.x - c[q].x, pc.y - c[q].y, pc.z - c[q].z, pc.w - c[q].w);
+                }
+            } else {
+                c[q] = make_int4(0, 0, 0, 0);
+                z[q] = make_int4(0, 0, 0, 0);
+            }
+        }
+        int hz[8], res[8];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int j = 4 * (g0 + q * nt) + e;
+                res[4 * q + e] = j < d ? comp4(c[q], e) : 0;
+                hz[4 * q + e] = res[4 * q + e] > 0 ? ldg_cg(P.h + comp4(z[q], e)) : kNoRes;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int j = 4 * (g0 + q * nt) + e;
+                if (j < d) stg[j] = hz[4 * q + e];
+                if (res[4 * q + e] > 0) {
+                    const unsigned long long key = ((unsigned long long)(unsigned)hz[4 * q + e] << 32) | (unsigned)j;
+                    best = key < best ? key : best;
+                }
             }
         }
     }
@@ -1529,6 +1690,7 @@ __device__ __noinline__ bool discharge_thread(const MfParams &P, Sh &sh, int u, 
     if (d <= kTS) {
         int hc[kTS];
         bool have = false;
+        int stale = 0;
         while (cyc < P.kernel_cycles) {
             const long long eu = PULL ? -ldg_cg(P.e + u) : ldg_cg(P.e + u);
             if (!(hu < n && eu > 0)) break;
@@ -1586,7 +1748,9 @@ __device__ __noinline__ bool discharge_thread(const MfParams &P, Sh &sh, int u, 
             }
             if (sent) atomic_add_ll(P.e + u, PULL ? sent : -sent);
             moves += k;
-            cyc += k > 0 ? k : 1;
+            // a pass that found only stale entries corrected them and costs no cycle (bounded)
+            if (k > 0) cyc += k;
+            else if (++stale > kStaleMax) cyc += 1;
         }
     } else {
         while (cyc < P.kernel_cycles) {
@@ -1645,12 +1809,14 @@ __device__ __noinline__ bool discharge_warp_rows(const MfParams &P, Sh &sh, int 
     const int n = P.g.n;
     const int lane = threadIdx.x & 31;
     const int r0 = P.g.off[u];
+    const int kcyc = cycles_for(P, d);
     constexpr bool st = ST;
     bool have = false;
+    int stale = 0;
     int hu = ldg_cg(P.h + u);
     long long scans = 0, moves = 0, fused = 0, gscan = 0;
     int cyc = 0;
-    while (cyc < P.kernel_cycles) {
+    while (cyc < kcyc) {
         const long long eu = PULL ? -ldg_cg(P.e + u) : ldg_cg(P.e + u);
         if (!(hu < n && eu > 0)) break;
         ++scans;
@@ -1659,7 +1825,7 @@ __device__ __noinline__ bool discharge_warp_rows(const MfParams &P, Sh &sh, int 
             best = warp_min_u64(scan_lowest<8, PULL>(P, r0, d, lane, 32));
             gscan += d;
         } else if (!have) {
-            best = warp_min_u64(scan_and_stage<8, PULL>(P, r0, d, lane, 32, stg));
+            best = warp_min_u64(scan_and_stage_v4<PULL>(P, r0, d, lane, 32, stg));
             have = true;
             gscan += d;
             __syncwarp();
@@ -1676,7 +1842,7 @@ __device__ __noinline__ bool discharge_warp_rows(const MfParams &P, Sh &sh, int 
                 atomicAdd((unsigned long long *)&sh.relabels, 1ull);
             }
             ++cyc;
-            if (hu >= n || cyc >= P.kernel_cycles) {
+            if (hu >= n || cyc >= kcyc) {
                 __syncwarp();
                 continue;
             }
@@ -1691,7 +1857,7 @@ __device__ __noinline__ bool discharge_warp_rows(const MfParams &P, Sh &sh, int 
             long long rem = eu, sent = 0;
             int k = 0;
             int seg = 1;    // one slot per lane first, kSeg after
-            for (int jb = j0; jb < d && rem > 0 && cyc + k < P.kernel_cycles; jb += seg * 32, seg = kSeg) {
+            for (int jb = j0; jb < d && rem > 0 && cyc + k < kcyc; jb += seg * 32, seg = kSeg) {
                 const int js = jb + lane * seg;
                 int a[kSeg];
                 long long tsum = 0;
@@ -1754,11 +1920,11 @@ __device__ __noinline__ bool discharge_warp_rows(const MfParams &P, Sh &sh, int 
                 int coff = cincl - tcnt;
                 long long mine = 0;
                 int mk = 0;
-                if (tcnt > 0 && off < rem && cyc + k + coff < P.kernel_cycles) {
+                if (tcnt > 0 && off < rem && cyc + k + coff < kcyc) {
 #pragma unroll
                     for (int r = 0; r < kSeg; ++r) {
                         if (a[r] <= 0) continue;
-                        if (off < rem && cyc + k + coff < P.kernel_cycles) {
+                        if (off < rem && cyc + k + coff < kcyc) {
                             const long long g = a[r] < rem - off ? a[r] : rem - off;
                             const int x = r0 + js + r;
                             move_flow<PULL>(P, sh, x, ldg_cg(P.g.rev + x), ldg_cg(P.g.dst + x), g, dc);
@@ -1779,7 +1945,9 @@ __device__ __noinline__ bool discharge_warp_rows(const MfParams &P, Sh &sh, int 
             }
             if (lane == 0 && sent) atomic_add_ll(P.e + u, PULL ? sent : -sent);
             moves += k;
-            cyc += k > 0 ? k : 1;
+            // staged: a pass that found only stale entries corrected them and costs no cycle (bounded)
+            if (k > 0) cyc += k;
+            else if (!st || ++stale > kStaleMax) cyc += 1;
         }
         __syncwarp();
     }
@@ -1814,11 +1982,13 @@ __device__ __noinline__ bool discharge_cta_rows(const MfParams &P, Sh &sh, int u
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     const int r0 = P.g.off[u];
+    const int kcyc = cycles_for(P, d);
     constexpr bool st = ST;
     bool have = false;
+    int stale = 0;
     long long cand = 0;
     int cyc = 0;
-    while (cyc < P.kernel_cycles) {
+    while (cyc < kcyc) {
         if (threadIdx.x == 0) {
             sh.bcast_e = PULL ? -ldg_cg(P.e + u) : ldg_cg(P.e + u);
             sh.bcast_h = ldg_cg(P.h + u);
@@ -1833,7 +2003,7 @@ __device__ __noinline__ bool discharge_cta_rows(const MfParams &P, Sh &sh, int u
         unsigned long long best;
         const bool global_scan = !st || !have;
         if (!st) best = scan_lowest<8, PULL>(P, r0, d, threadIdx.x, blockDim.x);
-        else if (!have) best = scan_and_stage<8, PULL>(P, r0, d, threadIdx.x, blockDim.x, stg);
+        else if (!have) best = scan_and_stage_v4<PULL>(P, r0, d, threadIdx.x, blockDim.x, stg);
         else best = scan_staged(stg, d, threadIdx.x, blockDim.x);
         have = true;
         best = warp_min_u64(best);
@@ -1856,7 +2026,7 @@ __device__ __noinline__ bool discharge_cta_rows(const MfParams &P, Sh &sh, int u
             }
             lifted = true;
             ++cyc;
-            go = nh < n && cyc < P.kernel_cycles;
+            go = nh < n && cyc < kcyc;
         }
         if (go) {
             // Alg. 2's next cycles, fused (as in discharge_warp): a step covers
@@ -1871,7 +2041,7 @@ __device__ __noinline__ bool discharge_cta_rows(const MfParams &P, Sh &sh, int u
             int k = 0;
             long long sent = 0;
             int seg = 1;
-            for (int jb = j0; jb < d && rem > 0 && cyc + k < P.kernel_cycles; jb += seg * (int)blockDim.x, seg = kSeg) {
+            for (int jb = j0; jb < d && rem > 0 && cyc + k < kcyc; jb += seg * (int)blockDim.x, seg = kSeg) {
                 const int js = jb + (int)threadIdx.x * seg;
                 int a[kSeg];
                 long long tsum = 0;
@@ -1945,11 +2115,11 @@ __device__ __noinline__ bool discharge_cta_rows(const MfParams &P, Sh &sh, int u
                 }
                 long long mine = 0;
                 int mk = 0;
-                if (tcnt > 0 && off < rem && cyc + k + coff < P.kernel_cycles) {
+                if (tcnt > 0 && off < rem && cyc + k + coff < kcyc) {
 #pragma unroll
                     for (int r = 0; r < kSeg; ++r) {
                         if (a[r] <= 0) continue;
-                        if (off < rem && cyc + k + coff < P.kernel_cycles) {
+                        if (off < rem && cyc + k + coff < kcyc) {
                             const long long g = a[r] < rem - off ? a[r] : rem - off;
                             const int x = r0 + js + r;
                             move_flow<PULL>(P, sh, x, ldg_cg(P.g.rev + x), ldg_cg(P.g.dst + x), g, dc);
@@ -1984,7 +2154,9 @@ __device__ __noinline__ bool discharge_cta_rows(const MfParams &P, Sh &sh, int u
                 if (sent) atomic_add_ll(P.e + u, PULL ? sent : -sent);
                 if (k) atomicAdd((unsigned long long *)&sh.pushes, (unsigned long long)k);
             }
-            cyc += k > 0 ? k : 1;
+            // staged: a pass that found only stale entries corrected them and costs no cycle (bounded)
+            if (k > 0) cyc += k;
+            else if (!st || ++stale > kStaleMax) cyc += 1;
         }
         __syncthreads();
     }
@@ -2030,7 +2202,11 @@ __device__ __noinline__ void phase_discharge(const MfParams &P, Sh &sh)
         __syncthreads();
         if (i >= nh) break;
         const int u = __ldcg(wl2 + i);
-        if (discharge_cta<PULL>(P, sh, u, dc, stage, P.stage_slots) && threadIdx.x == 0) note_relabel(P, u, dc);
+        const bool lifted = discharge_cta<PULL>(P, sh, u, dc, stage, P.stage_slots);
+        if (threadIdx.x == 0) {
+            if (lifted) note_relabel(P, u, dc);
+            requeue_if_active<PULL>(P, u, dc);
+        }
     }
     // mid-degree rows: one warp each (the CTA's snapshot buffer is free again:
     // every thread has left the loop above, so each warp takes a slice)
@@ -2041,7 +2217,11 @@ __device__ __noinline__ void phase_discharge(const MfParams &P, Sh &sh)
         const int i = warp_grab(&ctl->head1.w[0], nm, 1u);
         if (i >= nm) break;
         const int u = __ldcg(wl1 + i);
-        if (discharge_warp<PULL>(P, sh, u, dc, wstage, wcap) && lane == 0) note_relabel(P, u, dc);
+        const bool lifted = discharge_warp<PULL>(P, sh, u, dc, wstage, wcap);
+        if (lane == 0) {
+            if (lifted) note_relabel(P, u, dc);
+            requeue_if_active<PULL>(P, u, dc);
+        }
     }
     // small rows: one thread each, 32 per grab
     const int ns = vrd(&ctl->wl_n[0]);
@@ -2051,6 +2231,7 @@ __device__ __noinline__ void phase_discharge(const MfParams &P, Sh &sh)
         if (b + lane < ns) {
             const int u = __ldcg(wl0 + b + lane);
             if (discharge_thread<PULL>(P, sh, u, dc)) note_relabel(P, u, dc);
+            requeue_if_active<PULL>(P, u, dc);
         }
     }
 }
@@ -2253,6 +2434,21 @@ loop:
         flush_acc(P, sh, 0);               // the roots' label counters feed the first level's direction
         if (!grid_sync(P, H_BFS_START, sh)) return false;
         while (!vrd(&P.ctrl->bfs_done)) {
+            if (vrd(&P.ctrl->bfs_cta_mode)) {
+                // small levels: CTA 0 alone, its own thread 0 running the level
+                // hook; the other CTAs wait at the next grid barrier
+                if (vb() == 0) {
+                    int run = 0;
+                    do {
+                        phase_bfs_level(P, sh);
+                        flush_acc(P, sh, 0);
+                        if (threadIdx.x == 0) run_hook(P, H_BFS_NEXT);
+                        __syncthreads();
+                    } while (++run < MF_TAIL_RUN && !vrd(&P.ctrl->bfs_done) && vrd(&P.ctrl->bfs_cta_mode));
+                }
+                if (!grid_sync(P, H_BFS_JOIN, sh)) return false;
+                continue;
+            }
             if (vrd(&P.ctrl->bu_mode)) {
                 phase_bfs_bottom_up(P, sh);
                 flush_acc(P, sh, 0);
@@ -2530,7 +2726,7 @@ __global__ void k_row_capacity(MfParams P, float slack_factor, int slack_min, lo
         if ((double)sl < want) ++sl;
         if (sl < slack_min) sl = slack_min;
         if (sl > (1 << 24)) sl = 1 << 24;
-        cap_out[u] = need + sl;
+        cap_out[u] = (need + sl + MF_ROW_ALIGN - 1) / MF_ROW_ALIGN * MF_ROW_ALIGN;   // rows stay 16-byte aligned
     }
 }
 

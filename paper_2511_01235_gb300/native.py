@@ -96,10 +96,12 @@ EXPORTS = ["maxflow_build_layout", "maxflow_kernel_launches", "maxflow_default_o
            "maxflow_arena_create", "maxflow_arena_destroy", "maxflow_arena_alloc", "maxflow_arena_free",
            "maxflow_arena_stats", "maxflow_arena_fits", "maxflow_evicted_sizes",
            "maxflow_resolve_static_pp", "maxflow_resolve_static_pull", "maxflow_update_pp",
-           "maxflow_set_bfs_switch", "maxflow_test_stalled_barrier"]
+           "maxflow_set_bfs_switch", "maxflow_test_stalled_barrier", "maxflow_set_requeue",
+           "maxflow_set_cycle_div", "maxflow_set_fix_steep", "maxflow_set_bfs_tail"]
 
 TRACE_NAMES = ["start", "prologue", "batch_validated", "batch_located", "room_checked", "capacities_changed",
-               "iteration_start", "bfs_roots", "bfs_level", "worklist", "discharge", "end"]
+               "iteration_start", "bfs_roots", "bfs_level", "worklist", "discharge", "end", "bfs_bottom_up_first",
+               "bfs_cta_join"]
 
 _lib = None
 
@@ -138,9 +140,13 @@ def load(build_if_missing: bool = False):
     L.maxflow_stats.argtypes = [vp, P(Stats)]
     L.maxflow_check.argtypes = [vp, vp]
     L.maxflow_trace.argtypes = [vp, vp, vp, i32, P(i32)]
-    L.maxflow_trace_work.argtypes = [vp, vp, vp, i32, P(i32)]
+    L.maxflow_trace_work.argtypes = [vp, vp, vp, vp, vp, i32, P(i32)]
     L.maxflow_set_kernel_cycles.argtypes = [vp, i32]
     L.maxflow_set_rounds.argtypes = [vp, i32]
+    L.maxflow_set_requeue.argtypes = [vp, i32]
+    L.maxflow_set_cycle_div.argtypes = [vp, i32]
+    L.maxflow_set_fix_steep.argtypes = [vp, i32]
+    L.maxflow_set_bfs_tail.argtypes = [vp, i32]
     L.maxflow_set_tuning.argtypes = [vp, i32, i32, i32]
     L.maxflow_device_bytes.argtypes = [vp, P(i64)]
     L.maxflow_evict.argtypes = [vp]
@@ -163,7 +169,7 @@ def load(build_if_missing: bool = False):
     L.maxflow_test_stalled_barrier.argtypes = [vp, i32]
     L.maxflow_restore.argtypes = [vp]
     L.maxflow_solve_batched.argtypes = [vp, i32, vp, i32, P(C.c_double)]
-    L.maxflow_sched_actions.argtypes = [vp, vp, vp, i32, P(i32)]
+    L.maxflow_sched_actions.argtypes = [vp, vp, vp, vp, vp, i32, P(i32)]
     L.maxflow_features.argtypes = [vp, P(Batch), vp]
     L.maxflow_run_action.argtypes = [vp, P(Batch), i32]
     L.maxflow_update_scheduled.argtypes = [vp, P(Batch), vp, P(i32)]
@@ -389,13 +395,17 @@ def maxflow_trace(h, cap: int = 256):
 
 
 def maxflow_trace_work(h, cap: int = 256):
-    """(cumulative slots scanned, packed phase info) per entry of maxflow_trace."""
+    """Per entry of maxflow_trace: cumulative slots scanned, packed phase info, and when the
+    last and the average CTA finished the phase (microseconds after the previous barrier)."""
     sl = np.zeros(cap, np.int64)
     inf = np.zeros(cap, np.int32)
+    last = np.zeros(cap, np.float64)
+    mean = np.zeros(cap, np.float64)
     k = C.c_int32(0)
-    _check(load().maxflow_trace_work(h, _p(sl), _p(inf), cap, C.byref(k)), "maxflow_trace_work")
+    _check(load().maxflow_trace_work(h, _p(sl), _p(inf), _p(last), _p(mean), cap, C.byref(k)),
+           "maxflow_trace_work")
     k = int(k.value)
-    return sl[:k], inf[:k]
+    return sl[:k], inf[:k], last[:k], mean[:k]
 
 
 def maxflow_set_kernel_cycles(h, k: int):
@@ -436,14 +446,14 @@ def maxflow_clone(h):
 
 
 def maxflow_sched_actions():
-    """The fixed action table: list of (mode, rounds, cycles); mode 0 incremental, 1 static."""
+    """The fixed action table: list of (mode, rounds, cycles, cycle_div, fix); mode 0 incremental, 1 static."""
     L = load()
     k = C.c_int32(0)
-    _check(L.maxflow_sched_actions(None, None, None, 0, C.byref(k)), "maxflow_sched_actions")
+    _check(L.maxflow_sched_actions(None, None, None, None, None, 0, C.byref(k)), "maxflow_sched_actions")
     n = int(k.value)
-    mo, ro, cy = (np.zeros(n, np.int32) for _ in range(3))
-    _check(L.maxflow_sched_actions(_p(mo), _p(ro), _p(cy), n, C.byref(k)), "maxflow_sched_actions")
-    return list(zip(mo.tolist(), ro.tolist(), cy.tolist()))
+    mo, ro, cy, dv, fx = (np.zeros(n, np.int32) for _ in range(5))
+    _check(L.maxflow_sched_actions(_p(mo), _p(ro), _p(cy), _p(dv), _p(fx), n, C.byref(k)), "maxflow_sched_actions")
+    return list(zip(mo.tolist(), ro.tolist(), cy.tolist(), dv.tolist(), fx.tolist()))
 
 
 def maxflow_features(h, u, v, c) -> np.ndarray:
@@ -581,7 +591,7 @@ class Arena:
 class Solver:
     """One dynamic max-flow instance on one GPU (thin wrapper over the C calls)."""
 
-    def __init__(self, n, src, dst, cap, s, t, *, kernel_cycles=0, data_driven=True, fix_steep=True,
+    def __init__(self, n, src, dst, cap, s, t, *, kernel_cycles=0, data_driven=True, fix_steep=False,
                  grid_blocks=0, max_iters=0, time_limit_s=0.0, wait_limit_s=0.0, slack_factor=0.25,
                  slack_min=4, device=None, stream=None, torch_alloc=True, arena=None):
         import torch
@@ -680,6 +690,18 @@ class Solver:
 
     def set_rounds(self, r: int):
         maxflow_set_rounds(self.h, r)
+
+    def set_requeue(self, on: bool):
+        _check(load().maxflow_set_requeue(self.h, int(bool(on))), "maxflow_set_requeue")
+
+    def set_cycle_div(self, div: int):
+        _check(load().maxflow_set_cycle_div(self.h, int(div)), "maxflow_set_cycle_div")
+
+    def set_bfs_tail(self, slots: int):
+        _check(load().maxflow_set_bfs_tail(self.h, int(slots)), "maxflow_set_bfs_tail")
+
+    def set_fix_steep(self, on: bool):
+        _check(load().maxflow_set_fix_steep(self.h, int(bool(on))), "maxflow_set_fix_steep")
 
     def device_bytes(self) -> int:
         b = C.c_int64()

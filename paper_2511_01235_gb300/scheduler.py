@@ -31,8 +31,8 @@ from . import workloads as W
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_WEIGHTS = os.path.join(HERE, "scheduler_weights.json")
-ACTION_PAPER = 16      # one discharge round, KERNEL_CYCLES = average degree (the paper's schedule)
-ACTION_DEFAULT = 17    # the library's default (adaptive) rounds, KERNEL_CYCLES = average degree
+ACTION_DEFAULT = 0     # the library's default schedule (adaptive rounds, KERNEL_CYCLES = average degree)
+ACTION_PAPER = 5       # one discharge round, KERNEL_CYCLES = average degree, Alg. 3 (the paper's schedule)
 N_FEATURES = 16
 
 
@@ -181,9 +181,9 @@ def evaluate(mlp: native.MLP, X, T, M):
             "picks": np.bincount(pick, minlength=T.shape[1]).tolist()}
 
 
-TRAIN_PLAN = [("er4096", 101, 24), ("er16384", 102, 16), ("rmat16", 103, 16), ("rmat18", 104, 16),
-              ("rmat20", 2, 10), ("grid256", 105, 10), ("grid512", 106, 6)]
-HELDOUT_PLAN = [("er4096", 201, 12), ("rmat18", 204, 8), ("grid256", 205, 6)]
+TRAIN_PLAN = [("er4096", 101, 24), ("er16384", 102, 16), ("rmat16", 103, 20), ("rmat18", 104, 20),
+              ("rmat20", 2, 16), ("grid256", 105, 10), ("grid512", 106, 6)]
+HELDOUT_PLAN = [("er4096", 201, 12), ("rmat16", 203, 8), ("rmat18", 204, 8), ("grid256", 205, 6)]
 
 
 def main():

@@ -73,7 +73,7 @@ int main(void) {
 
 def test_default_opts_and_strerror(lib):
     o = native.maxflow_default_opts()
-    assert (o.data_driven, o.fix_steep, o.kernel_cycles, o.slack_min) == (1, 1, 0, 4)
+    assert (o.data_driven, o.fix_steep, o.kernel_cycles, o.slack_min) == (1, 0, 0, 4)
     assert abs(o.slack_factor - 0.25) < 1e-6
     for code in range(8):
         assert native.strerror(code)
@@ -133,13 +133,16 @@ def test_committed_scheduler_weights_fit_the_action_table(lib):
 
 
 def test_scheduler_action_table():
-    # mode 0: incremental (Alg. 5) with rounds R and KERNEL_CYCLES K in {1, 4, 16, 64};
-    # the paper's fixed schedule (R = 1, K = average degree, written 0); the library
-    # default (adaptive rounds, K = average degree); mode 1: static re-solves (Alg. 1)
+    # (mode, rounds, KERNEL_CYCLES, cycle divisor, Alg. 3): mode 0 incremental (Alg. 5),
+    # mode 1 static re-solve (Alg. 1); rounds 0 = adaptive, cycles 0 = the average degree.
+    # Action 0 is the library default, the paper's fixed schedule is one round with
+    # the average degree and Alg. 3 after every discharge.
     from paper_2511_01235_gb300 import scheduler as SCH
     acts = native.maxflow_sched_actions()
-    grid = [(0, r, k) for r in (1, 4, 16, 64) for k in (1, 4, 16, 64)]
-    assert acts[:16] == grid
-    assert acts[SCH.ACTION_PAPER] == (0, 1, 0) and acts[SCH.ACTION_DEFAULT] == (0, 0, 0)
+    assert acts[SCH.ACTION_DEFAULT] == (0, 0, 0, 0, 0)
+    assert acts[SCH.ACTION_PAPER] == (0, 1, 0, 0, 1)
+    assert (1, 1, 0, 0, 1) in acts                          # the paper's static solve
+    assert len(set(acts)) == len(acts) == 20
     statics = [a for a in acts if a[0] == 1]
-    assert len(acts) == 22 and len(statics) == 4 and all(a[0] in (0, 1) for a in acts)
+    assert len(statics) == 4 and all(a[0] in (0, 1) and a[4] in (0, 1) for a in acts)
+    assert all(a[1] in (0, 1, 4, 16, 64) and a[2] in (0, 4, 16, 64) and a[3] in (0, 256) for a in acts)

@@ -5,11 +5,11 @@ Forward, gradient and one Adam step of the CUDA network agree with the
 float64 restatement in oracle/mlp_ref.py to fp32 rounding.  Running updates
 through maxflow_update_scheduled never changes the flow value, and with the
 committed weights the learned schedule spends less device time than the
-paper's fixed schedule (one discharge round, KERNEL_CYCLES = average degree)
-on held-out batches it was not trained on (wall time per update call).
+paper's fixed schedule (one discharge round, KERNEL_CYCLES = average degree,
+Alg. 3) and than the library's default schedule on held-out batches it was not
+trained on (device time per update call, from CUDA events).
 """
 import os
-import time
 
 import numpy as np
 import pytest
@@ -32,7 +32,7 @@ def _data(seed, n_in, n_out, rows):
     return x, t, m
 
 
-@pytest.mark.parametrize("shape", [(16, 64, 22), (5, 33, 7)])
+@pytest.mark.parametrize("shape", [(16, 64, 20), (5, 33, 7)])
 def test_forward_and_gradient_match_numpy(shape):
     n_in, H, n_out = shape
     mlp = native.MLP(n_in, H, n_out, seed=7)
@@ -49,7 +49,7 @@ def test_forward_and_gradient_match_numpy(shape):
 
 
 def test_one_adam_step_matches_numpy():
-    n_in, H, n_out = 16, 64, 22
+    n_in, H, n_out = 16, 64, 20
     mlp = native.MLP(n_in, H, n_out, seed=9)
     p0 = mlp.params.astype(np.float64)
     x, t, m = _data(2, n_in, n_out, 50)
@@ -60,7 +60,7 @@ def test_one_adam_step_matches_numpy():
 
 
 def test_training_lowers_the_loss():
-    n_in, H, n_out = 16, 64, 22
+    n_in, H, n_out = 16, 64, 20
     mlp = native.MLP(n_in, H, n_out, seed=3)
     rng = np.random.default_rng(4)
     x = rng.normal(size=(200, n_in)).astype(np.float32)
@@ -100,10 +100,16 @@ def test_scheduled_updates_keep_the_flow_exact():
 
 
 @pytest.mark.skipif(not os.path.exists(SCH.DEFAULT_WEIGHTS), reason="no trained scheduler weights")
-def test_learned_schedule_beats_the_fixed_schedule_on_heldout_batches():
+def test_learned_schedule_beats_the_fixed_schedules_on_heldout_batches():
+    """Held-out streams (seeds the network was not trained on) of mixed batch
+    sizes: the learned schedule's device time, its features and forward pass
+    included (CUDA events around each call on the solver's stream), is below
+    the paper's fixed schedule by a wide margin and below the library's own
+    default schedule; the flow value is the same whatever the schedule."""
+    import torch
     mlp = SCH.load()
     totals = {"learned": 0.0, "paper": 0.0, "default": 0.0}
-    for name, seed, k in [("er4096", 301, 8), ("grid256", 305, 4), ("rmat16", 303, 8)]:
+    for name, seed, k in [("er4096", 301, 8), ("grid256", 305, 4), ("rmat16", 303, 8), ("rmat18", 304, 8)]:
         g, make = SCH.family(name, seed)
         batches = make(k)
         runs = {}
@@ -111,17 +117,21 @@ def test_learned_schedule_beats_the_fixed_schedule_on_heldout_batches():
             S = native.Solver(g.n, g.src, g.dst, g.cap, g.s, g.t)
             t = 0.0
             for b in batches:
-                t0 = time.perf_counter()      # wall time: the learned path pays for its features and forward pass
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(S.stream)
                 if key == "learned":
                     S.update_scheduled(b.u, b.v, b.cap, mlp)
                 else:
                     S.run_action(b.u, b.v, b.cap, SCH.ACTION_PAPER if key == "paper" else SCH.ACTION_DEFAULT)
-                t += (time.perf_counter() - t0) * 1e3
+                e1.record(S.stream)
+                e1.synchronize()
+                t += e0.elapsed_time(e1)
             runs[key] = (t, S.query()[0])
             S.close()
         assert len({v for _, v in runs.values()}) == 1        # same flow value whatever the schedule
         for key in totals:
             totals[key] += runs[key][0]
-    print("scheduler totals (ms):", totals)
+    print("scheduler totals (device ms):", totals)
     assert totals["learned"] < 0.8 * totals["paper"], totals
-    assert totals["learned"] < 1.25 * totals["default"], totals
+    assert totals["learned"] < 0.95 * totals["default"], totals

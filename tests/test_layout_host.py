@@ -31,9 +31,11 @@ def _check_layout(n, src, dst, cap, factor, smin):
         got_u += [u] * d
         got_v += list(heads)
         got_c += list(L["cap"][row])
-        # slack: max(slack_min, ceil(deg * factor)); slack slots point at themselves
+        # slack: max(slack_min, ceil(deg * factor)), the row rounded up to a multiple of
+        # 4 slots (rows start on 16-byte boundaries); slack slots point at themselves
         want_slack = max(smin, math.ceil(d * np.float32(factor)))
-        assert int(off[u + 1]) - lo - d == want_slack
+        assert lo % 4 == 0
+        assert int(off[u + 1]) - lo == -(-(d + want_slack) // 4) * 4
         for x in range(lo + d, int(off[u + 1])):
             assert (L["dst"][x], L["cap"][x], L["rev"][x], L["pcap"][x]) == (u, 0, x, 0)
         for j in range(d):
@@ -76,7 +78,7 @@ def test_layout_errors():
     assert call(3, bad, None, None, None, None, None, None) == native.ERR_INVALID           # negative capacity
     assert call(3, cap, None, None, None, None, None, None) == native.OK
     need = int(S[0])
-    assert need == 4 + 3 * 4                    # slots (0,1) (1,0) (1,2) (2,1), slack 4 per row
+    assert need == 8 + 8 + 8                    # slots (0,1) (1,0) (1,2) (2,1), slack 4 per row, rows of 4k
     small = np.zeros(need - 1, np.int32)
     S[0] = need - 1
     assert call(3, cap, None, None, p(small), None, None, None) == native.ERR_INVALID     # array too short
@@ -117,5 +119,6 @@ def test_layout_at_scale_equals_the_oracle_vectorised():
     assert np.array_equal(L["rev"][rev], used)                     # an involution on the used slots
     assert np.array_equal(L["dst"][rev], row)                      # the reverse slot points back
     assert np.array_equal(L["pcap"][used], L["cap"][used] + L["cap"][rev])
-    slack = off[1:] - off[:-1] - deg
-    assert np.array_equal(slack, np.maximum(4, np.ceil(deg * 0.25).astype(np.int64)))
+    want = deg + np.maximum(4, np.ceil(deg * 0.25).astype(np.int64))
+    assert np.array_equal(off[1:] - off[:-1], (want + 3) // 4 * 4)       # rows of a multiple of 4 slots
+    assert np.all(off % 4 == 0)

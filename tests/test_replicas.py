@@ -87,3 +87,38 @@ def test_a_rank_that_leaves_is_detected_by_the_other():
     assert out[0].startswith("error"), out
     assert time.perf_counter() - t0 < 90
     assert procs[1].exitcode == 3 and procs[0].exitcode == 0
+
+
+def test_gpus_n_without_torchrun_starts_n_ranks_itself():
+    """bench.py --gpus N (no torchrun) re-launches itself as N ranks through
+    torch.distributed.run on 127.0.0.1, one per GPU; on a host with fewer GPUs
+    it refuses cleanly (exit status 2, one line on stderr, no traceback)."""
+    import subprocess
+    import sys
+
+    import bench
+    cmd = bench.replica_command(["--gpus", "2", "--steps", "3"], 2, 29555)
+    assert cmd[1:3] == ["-m", "torch.distributed.run"]
+    assert "--nproc-per-node=2" in cmd and "--master-addr=127.0.0.1" in cmd and "--master-port=29555" in cmd
+    assert cmd[-4:] == ["--gpus", "2", "--steps", "3"] and cmd[-5].endswith("bench.py")
+    import torch
+    if torch.cuda.is_available() and torch.cuda.device_count() >= 2:
+        pytest.skip("this host has two GPUs: the refusal path does not apply")
+    env = dict(os.environ)
+    env.pop("WORLD_SIZE", None)
+    r = subprocess.run([sys.executable, bench.__file__, "--gpus", "2", "--steps", "1", "--warmup", "1"],
+                       capture_output=True, text=True, timeout=300, env=env)
+    assert r.returncode == 2, (r.returncode, r.stderr[-2000:])
+    assert "needs 2 GPUs" in r.stderr and "Traceback" not in r.stderr
+    assert r.stdout.strip() == ""
+
+
+def test_parallelism_label_follows_the_world_size():
+    import types
+
+    import bench
+    g = types.SimpleNamespace(n=10, m=20, s=0, t=9)
+    wl = types.SimpleNamespace(describe=lambda: "tiny")
+    args = types.SimpleNamespace(batch=5, gpus=4)
+    assert bench.config_of(args, g, wl, 4)["parallelism"] == "replicas x4"
+    assert bench.config_of(args, g, wl)["parallelism"] == "replicas x1"

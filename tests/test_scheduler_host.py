@@ -15,7 +15,7 @@ class FixedNet:
 
 
 def test_evaluate_sums_the_picked_and_the_fixed_actions():
-    A = 22
+    A = 20
     rng = np.random.default_rng(3)
     T = rng.uniform(1.0, 9.0, size=(5, A))
     M = np.ones_like(T)
