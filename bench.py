@@ -467,6 +467,61 @@ def batched_summary():
             "flow_check": {"instances": len(gs), "equal": bool(same and cpu_vals == vals)}}
 
 
+def scheduler_comparison(S, wl, count):
+    """The learned schedule against the paper's fixed one and the library default on the same
+    held-out batches (sizes log-uniform in [1K, 100K], the headline mix), each on its own clone
+    of one state.  Device time per call from CUDA events on the solver's stream: the learned
+    path pays for its features and forward pass."""
+    import math
+
+    import torch
+    from paper_2511_01235_gb300 import scheduler as SCH
+    from paper_2511_01235_gb300 import workloads as W
+    if not os.path.exists(SCH.DEFAULT_WEIGHTS):
+        return None
+    mlp = SCH.load()
+    rng = np.random.default_rng(4321)
+    es = wl.es.copy()
+    sizes = [int(x) for x in np.exp(rng.uniform(math.log(1000), math.log(100_000), size=count))]
+    batches = []
+    for B in sizes:
+        b = W.mixed_batch(es, B, rng, ins_cap_hi=wl.ins_hi)
+        es.apply(b.u, b.v, b.cap)
+        batches.append(b)
+    out = {"batches": len(batches), "sizes": sizes}
+    picks = []
+    for key in ("learned", "paper", "default"):
+        C = S.clone()
+        ts = []
+        for b in batches:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(C.stream)
+            if key == "learned":
+                picks.append(C.update_scheduled(b.u, b.v, b.cap, mlp))
+            else:
+                C.run_action(b.u, b.v, b.cap, SCH.ACTION_PAPER if key == "paper" else SCH.ACTION_DEFAULT)
+            e1.record(C.stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        out[key + "_ms_total"] = float(np.sum(ts))
+        out[key + "_ms_mean"] = float(np.mean(ts))
+        out[key + "_value"] = int(C.query()[0])
+        C.close()
+    out["learned_vs_default"] = out["learned_ms_total"] / out["default_ms_total"]
+    out["learned_vs_paper"] = out["learned_ms_total"] / out["paper_ms_total"]
+    out["learned_picks"] = np.bincount(picks, minlength=len(native_actions())).tolist()
+    out["values_equal"] = len({out["learned_value"], out["paper_value"], out["default_value"]}) == 1
+    out["note"] = ("device ms per update call (CUDA events), host batches; paper = 1 round, K = avg degree, "
+                   "Alg. 3; default = the library's adaptive schedule")
+    return out
+
+
+def native_actions():
+    from paper_2511_01235_gb300 import native
+    return native.maxflow_sched_actions()
+
+
 def run_batched(args):
     """Many uneven instances in one persistent launch (64 graphs of 1K-200K vertices)."""
     import torch
@@ -650,7 +705,7 @@ def main():
     ap.add_argument("--no-configs", action="store_true", help="headline workload only (no configs block)")
     ap.add_argument("--static-reps", type=int, default=3)
     ap.add_argument("--quick", action="store_true", help="timed steps only (for profiling runs)")
-    ap.add_argument("--sched-steps", type=int, default=6, help="batches for the learned-vs-fixed schedule comparison")
+    ap.add_argument("--sched-steps", type=int, default=30, help="held-out batches for the learned-vs-fixed schedule comparison")
     ap.add_argument("--budget-gb", type=float, default=8.0, help="serving: device-memory budget of the states")
     ap.add_argument("--utilization", type=float, default=0.7, help="serving: offered load vs one-at-a-time service")
     ap.add_argument("--group-blocks", type=int, default=8, help="serving: CTAs per instance in a launch")
@@ -753,30 +808,10 @@ def main():
     e2e_val = ws * args.batch * len(pinned) / e2e_s if pinned else None
     es_state = wl.es.copy()            # the graph S holds now (the comparisons below run on clones)
 
-    # ---- learned schedule vs the fixed ones on the same batch stream (clones of one state) ----
+    # ---- learned schedule vs the fixed ones on one held-out stream of mixed sizes (clones of one state) ----
     sched = None
     if not args.quick and args.sched_steps > 0:
-        from paper_2511_01235_gb300 import scheduler as SCH
-        if os.path.exists(SCH.DEFAULT_WEIGHTS):
-            mlp = SCH.load()
-            sb = wl.batches(args.sched_steps, args.batch)
-            sched = {}
-            for key in ("learned", "paper", "default"):
-                C = S.clone()
-                ts = []
-                for b in sb:
-                    torch.cuda.synchronize()
-                    t0 = time.perf_counter()
-                    if key == "learned":
-                        C.update_scheduled(b.u, b.v, b.cap, mlp)
-                    else:
-                        C.run_action(b.u, b.v, b.cap, SCH.ACTION_PAPER if key == "paper" else SCH.ACTION_DEFAULT)
-                    ts.append((time.perf_counter() - t0) * 1e3)
-                sched[key + "_ms_mean"] = float(np.mean(ts))
-                sched[key + "_value"] = int(C.query()[0])
-                C.close()
-            sched["batches"] = len(sb)
-            sched["note"] = "wall ms per update through the C ABI, host batches; paper = 1 round, K = avg degree"
+        sched = scheduler_comparison(S, wl, args.sched_steps)
 
     # ---- dynamic push-pull (Sec. 5.2.2, O2) vs the default update, same batches on clones ----
     pushpull = None

@@ -125,6 +125,12 @@ typedef struct {
     int32_t rounds;                 /* current setting of maxflow_set_rounds (0: adaptive) */
     int32_t reserved0;
     double  ms_update;              /* device time of every launch of the last update or solve call */
+    /* where the last solve's discharge rounds spent their time, summed over all
+       warps (microseconds): on rows above warp_max_slots (CTAs and 4-warp groups),
+       on rows up to it (one warp each), on the thread-per-vertex rows */
+    double  us_discharge_cta_rows;
+    double  us_discharge_warp_rows;
+    double  us_discharge_thread_rows;
 } maxflow_stats_t;
 
 /* Fill o with the defaults documented above. */
@@ -211,8 +217,10 @@ int maxflow_set_cycle_div(maxflow_ctx *c, int32_t div);
  * `slots` slots (and at most as many vertices) runs in the first CTA alone,
  * level after level, without a grid barrier between levels (the labels are
  * those of Alg. 4 / Alg. 6 either way); the grid meets again when a frontier
- * grows past the limit, the BFS ends, or after 256 such levels.  0 turns it
- * off; the default is 2048.  Not in the paper.  MAXFLOW_ERR_INVALID below 0. */
+ * grows past the limit, the BFS ends, or after 256 such levels.  0 (the
+ * default) turns it off: measured on R-MAT, grids and the batched instances it
+ * did not pay (a level of a few hundred slots costs about as much in one CTA as
+ * the grid's barrier does).  Not in the paper.  MAXFLOW_ERR_INVALID below 0. */
 int maxflow_set_bfs_tail(maxflow_ctx *c, int32_t slots);
 
 /* Run remove-invalid-edges (Alg. 3) after each iteration's discharge rounds
@@ -441,6 +449,19 @@ int maxflow_arena_fits(maxflow_arena *a, const int64_t *sizes, int32_t count, in
  * try several schedules from one state and to checkpoint a dynamic graph
  * (the dynamic algorithm resumes from any saved state, Sec. 4.2). */
 int maxflow_clone(maxflow_ctx *c, maxflow_ctx **out);
+
+/* Rollback for a failed re-solve (no counterpart in the paper; recovery around
+ * the dynamic algorithm, which can resume from any saved state, Sec. 4.2).
+ * maxflow_checkpoint keeps a deep copy of the context's state (as
+ * maxflow_clone; it replaces an earlier checkpoint and costs one copy of the
+ * device state).  maxflow_rollback makes the context exactly that saved state
+ * again -- graph, residual capacities, heights, excesses, value and settings
+ * -- and drops the checkpoint; use it when a call since the checkpoint
+ * returned an error (MAXFLOW_ERR_NOT_CONVERGED, MAXFLOW_ERR_INTERNAL, ...).
+ * Both synchronise the context's stream.  Rollback without a checkpoint:
+ * MAXFLOW_ERR_STATE (nothing changes); either while evicted: MAXFLOW_ERR_STATE. */
+int maxflow_checkpoint(maxflow_ctx *c);
+int maxflow_rollback(maxflow_ctx *c);
 
 /* Counters and timings of the context and of its last solve, into a
  * caller-owned struct.  Host-side copy, no GPU work.  MAXFLOW_ERR_INVALID for

@@ -37,11 +37,13 @@ static inline int counted(int rc, int kernels)
 struct maxflow_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
+    maxflow_ctx *ckpt = nullptr;      // maxflow_checkpoint's saved copy (a clone), or none
     maxflow_opts opt{};
     int32_t n = 0, s = 0, t = 0;
     int32_t kernel_cycles = 1;
     int32_t rounds = 1;
     int32_t small_deg = MF_SMALL_DEG, hub_deg = MF_HUB_DEG, bfs_hub = MF_BFS_HUB;
+    int32_t group_deg = MF_HUB_DEG;   // rows above this get a CTA: a quarter of the snapshot buffer
     int32_t bu_alpha = MF_BU_ALPHA, bu_beta = MF_BU_BETA;
     // batched launches started from this context (parameter list, group state)
     MfParams *multi_plist = nullptr;
@@ -51,7 +53,7 @@ struct maxflow_ctx {
     int32_t stage_slots = 0;      // dynamic shared memory of the solve launches, in ints
     int32_t requeue = 1;          // discharge rounds re-queue vertices still active after their cycles
     int32_t cycle_div = 0;        // > 0: long rows get max(kernel_cycles, deg / cycle_div) cycles
-    int32_t tail_slots = MF_TAIL_SLOTS;   // BFS frontiers of at most this many slots run in one CTA
+    int32_t tail_slots = 0;       // BFS frontiers of at most this many slots run in one CTA (0: off)
     MfGraph g{};
     MfScratch sc{};
     MfCtrl *ctrl = nullptr;
@@ -172,6 +174,7 @@ MfParams base_params(maxflow_ctx *c)
     p.rounds = c->rounds;
     p.small_deg = c->small_deg;
     p.hub_deg = c->hub_deg;
+    p.group_deg = c->group_deg;
     p.bfs_hub = c->bfs_hub;
     p.bu_alpha = c->bu_alpha;
     p.bu_beta = c->bu_beta;
@@ -286,7 +289,7 @@ int alloc_vertex_scratch(maxflow_ctx *c)
     const int32_t n = c->n;
     c->sc.border = dalloc_n<int32_t>(c, n);
     for (int q = 0; q < 2; ++q)
-        for (int b = 0; b < 3; ++b) c->sc.wl[q][b] = dalloc_n<int32_t>(c, n);
+        for (int b = 0; b < MF_NBIN; ++b) c->sc.wl[q][b] = dalloc_n<int32_t>(c, n);
     c->sc.vmark = dalloc_n<int32_t>(c, n);
     c->sc.fixmark = dalloc_n<int32_t>(c, n);
     c->sc.fixl[0] = dalloc_n<int32_t>(c, n);
@@ -295,7 +298,7 @@ int alloc_vertex_scratch(maxflow_ctx *c)
     if (!c->sc.border || !c->sc.vmark || !c->sc.fixmark || !c->sc.fixl[0] || !c->sc.fixl[1] || !c->sc.ins_need)
         return MAXFLOW_ERR_OOM;
     for (int q = 0; q < 2; ++q)
-        for (int b = 0; b < 3; ++b)
+        for (int b = 0; b < MF_NBIN; ++b)
             if (!c->sc.wl[q][b]) return MAXFLOW_ERR_OOM;
     MF_TRY(rc_cuda(cudaMemsetAsync(c->sc.vmark, 0xff, sizeof(int32_t) * n, c->stream)));
     MF_TRY(rc_cuda(cudaMemsetAsync(c->sc.fixmark, 0xff, sizeof(int32_t) * n, c->stream)));
@@ -350,6 +353,9 @@ void fill_stats(maxflow_ctx *c, const MfCtrl &h, float ms)
     s.ms_apply = h.ns_apply * 1e-6;
     s.ms_kernel = (h.t_exit - h.t_entry) * 1e-6;
     s.ms_update = c->acc_ms;   // run_kernel has added this launch already
+    s.us_discharge_cta_rows = h.ns_dis_cta * 1e-3;
+    s.us_discharge_warp_rows = h.ns_dis_warp * 1e-3;
+    s.us_discharge_thread_rows = h.ns_dis_thread * 1e-3;
     s.discharge_rounds = h.rounds_total;
     s.barriers = h.barriers;
     s.kernel_cycles = c->kernel_cycles;
@@ -586,14 +592,14 @@ int ensure_pp(maxflow_ctx *c)
         q.side = (uint8_t *)dalloc(c, (size_t)n);
         q.sc.border = dalloc_n<int32_t>(c, n);
         for (int a = 0; a < 2; ++a)
-            for (int b = 0; b < 3; ++b) q.sc.wl[a][b] = dalloc_n<int32_t>(c, n);
+            for (int b = 0; b < MF_NBIN; ++b) q.sc.wl[a][b] = dalloc_n<int32_t>(c, n);
         q.sc.vmark = dalloc_n<int32_t>(c, n);
         q.sc.fixmark = dalloc_n<int32_t>(c, n);
         q.sc.fixl[0] = dalloc_n<int32_t>(c, n);
         q.sc.fixl[1] = dalloc_n<int32_t>(c, n);
         bool ok = q.ctrl && q.h && q.side && q.sc.border && q.sc.vmark && q.sc.fixmark && q.sc.fixl[0] && q.sc.fixl[1];
         for (int a = 0; a < 2; ++a)
-            for (int b = 0; b < 3; ++b) ok = ok && q.sc.wl[a][b];
+            for (int b = 0; b < MF_NBIN; ++b) ok = ok && q.sc.wl[a][b];
         if (!ok) return MAXFLOW_ERR_OOM;
         MF_TRY(rc_cuda(cudaMemsetAsync(q.ctrl, 0, sizeof(MfCtrl), c->stream)));
         MF_TRY(rc_cuda(cudaMemsetAsync(q.sc.vmark, 0xff, sizeof(int32_t) * (size_t)n, c->stream)));
@@ -688,6 +694,10 @@ static void park_free(maxflow_ctx *c);
 void maxflow_destroy(maxflow_ctx *c)
 {
     if (!c) return;
+    if (c->ckpt) {
+        maxflow_destroy(c->ckpt);
+        c->ckpt = nullptr;
+    }
     {
         DeviceGuard dg(c->device);
         if (c->stream) cudaStreamSynchronize(c->stream);
@@ -745,6 +755,7 @@ int maxflow_init(maxflow_ctx **out, const maxflow_graph *g, int32_t s, int32_t t
     if (rc == MAXFLOW_OK) rc = mf_stage_bytes(dev, &stage_bytes);
     if (rc == MAXFLOW_OK) rc = mf_max_coresident_blocks(dev, &c->per_sm, &c->sms, stage_bytes);
     c->stage_slots = stage_bytes / (int)sizeof(int);
+    c->group_deg = std::max<int32_t>(c->hub_deg, c->stage_slots / (MF_BLOCK / (32 * MF_GROUP_WARPS)));
     if (rc == MAXFLOW_OK) rc = rc_cuda(cudaEventCreate(&c->ev0));
     if (rc == MAXFLOW_OK) rc = rc_cuda(cudaEventCreate(&c->ev1));
     if (rc == MAXFLOW_OK) rc = rc_cuda(cudaMallocHost((void **)&c->hctrl, sizeof(MfCtrl)));
@@ -1577,6 +1588,7 @@ int maxflow_clone(maxflow_ctx *src, maxflow_ctx **out)
     c->bu_alpha = src->bu_alpha;
     c->bu_beta = src->bu_beta;
     c->hub_deg = src->hub_deg;
+    c->group_deg = src->group_deg;
     c->bfs_hub = src->bfs_hub;
     c->per_sm = src->per_sm;
     c->stage_slots = src->stage_slots;
@@ -1644,6 +1656,35 @@ int maxflow_clone(maxflow_ctx *src, maxflow_ctx **out)
     }
     c->grid = src->grid;
     *out = c;
+    return MAXFLOW_OK;
+}
+
+int maxflow_checkpoint(maxflow_ctx *c)
+{
+    if (c && c->evicted) return MAXFLOW_ERR_STATE;
+    if (!c) return MAXFLOW_ERR_INVALID;
+    maxflow_ctx *copy = nullptr;
+    MF_TRY(maxflow_clone(c, &copy));
+    if (c->ckpt) maxflow_destroy(c->ckpt);
+    c->ckpt = copy;
+    return MAXFLOW_OK;
+}
+
+int maxflow_rollback(maxflow_ctx *c)
+{
+    if (c && c->evicted) return MAXFLOW_ERR_STATE;
+    if (!c) return MAXFLOW_ERR_INVALID;
+    if (!c->ckpt) return MAXFLOW_ERR_STATE;
+    maxflow_ctx *saved = c->ckpt;
+    c->ckpt = nullptr;
+    {
+        DeviceGuard dg(c->device);
+        if (c->stream) cudaStreamSynchronize(c->stream);      // nothing of the failed call is still running
+    }
+    std::swap(*c, *saved);           // c takes the saved state (and its device buffers); saved the old one
+    c->ckpt = nullptr;
+    saved->ckpt = nullptr;
+    maxflow_destroy(saved);
     return MAXFLOW_OK;
 }
 

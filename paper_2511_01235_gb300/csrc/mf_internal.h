@@ -19,7 +19,9 @@
 #define MF_BLOCK 512          // threads per CTA of the persistent kernel
 #define MF_WARPS (MF_BLOCK / 32)
 #define MF_SMALL_DEG 8        // discharge: rows up to this many slots get one thread
-#define MF_HUB_DEG 512        // discharge: rows above this many slots get a whole CTA
+#define MF_HUB_DEG 512        // discharge: rows above this many slots get a 4-warp group (or a whole CTA)
+#define MF_NBIN 4             // discharge row kinds: thread, warp, 4-warp group, CTA
+#define MF_GROUP_WARPS 4      // warps of a group; a group keeps rows up to a quarter of the snapshot
 #define MF_BFS_HUB 256        // BFS: rows above this many slots enter the frontier as work items
 #define MF_BFS_CHUNK 256      // BFS: slots per work item
 #define MF_ACTIVE_HIST 64
@@ -78,9 +80,10 @@ struct MfCtrl {
     MfLine head0;         // w[0]: dynamic work head
     MfLine head1;
     MfLine head2;
-    MfLine wl_tail;       // w[0..2]: worklist append positions per bin
+    MfLine head3;
+    MfLine wl_tail;       // w[0..3]: worklist append positions per bin, w[4]: active vertices
     MfLine misc;          // w[0]: insert list tail, w[1]: touched tail, w[2]: overflow flag
-    MfLine aux_tail;      // w[0..2]: next-round worklist tails, w[3]/w[4]: remove-invalid lists (warp / CTA)
+    MfLine aux_tail;      // w[0..3]: next-round worklist tails, w[4]/w[5]: remove-invalid lists (warp / CTA)
     MfLine defer_tail;    // w[0]: bottom-up work items of long rows deferred to the level's second pass
     MfLine bfs_acc;       // 64-bit words: [0] slots of the vertices labelled in this level, [1] their number,
                           // [2] used slots of the whole graph (summed by the BFS initialisation)
@@ -89,7 +92,7 @@ struct MfCtrl {
     int level;
     int lvl_lo, lvl_hi;
     int hub_lo, hub_hi;
-    int wl_n[3];
+    int wl_n[MF_NBIN];
     int ins_n, touch_n;
     int bfs_done;
     int wl_sel;           // which worklist buffer the current round reads
@@ -115,6 +118,7 @@ struct MfCtrl {
     long long slots_apply;    // slots read by the batch phases (slot search, source row)
     long long clamps_apply;   // slots whose residual went negative and was sent back
     unsigned long long ns_bfs, ns_dis, ns_fix, ns_wl, ns_apply;
+    unsigned long long ns_dis_cta, ns_dis_warp, ns_dis_thread;   // discharge time by row kind, summed over workers
     int active_hist[MF_ACTIVE_HIST];
     long long rounds_total;
     // ---- tracing: kernel entry (block 0, before the first barrier), last hook, hook timeline ----
@@ -148,7 +152,8 @@ struct MfScratch {
     int2 *bitem;              // [n + slot_cap / MF_BFS_CHUNK + 64] frontier work items (first slot, length)
     int2 *bdefer;             // [n + slot_cap / MF_BFS_CHUNK + 64] bottom-up deferred chunks (vertex, first slot);
                               // nullptr: bottom-up threads scan whole rows themselves
-    int32_t *wl[2][3];        // [n] worklists (two buffers for discharge rounds): small, mid, hub rows
+    int32_t *wl[2][MF_NBIN];  // [n] worklists (two buffers for discharge rounds) per row kind: thread, warp,
+                              // 4-warp group, CTA
     int32_t *vmark;           // [n] round stamp of the last time a vertex was queued
     int32_t *fixmark;         // [n] iteration stamp of the last time a vertex was listed for Alg. 3
     int32_t *fixl[2];         // [n] vertices relabelled this iteration: rows <= MF_HUB_DEG, rows above
@@ -181,7 +186,8 @@ struct MfParams {
                               // 0: adaptive (at least MF_DEFAULT_ROUNDS, more while discharging has taken
                               // less than half the time of this iteration's BFS)
     int32_t small_deg;        // discharge: rows up to this many slots get one thread
-    int32_t hub_deg;          // discharge / remove-invalid: rows above this many slots get a CTA
+    int32_t hub_deg;          // discharge / remove-invalid: rows above this many slots get a group (or a CTA)
+    int32_t group_deg;        // discharge: rows above this many slots get a whole CTA (<= hub_deg: no groups)
     int32_t bfs_hub;          // BFS: rows above this many slots enter the frontier as work items
     int32_t bu_alpha;         // BFS direction switch (0: top-down only), see MF_BU_ALPHA
     int32_t bu_beta;

@@ -48,6 +48,12 @@ __device__ __forceinline__ int vn() { return g_vn; }
 // indices go to different CTAs, so a batch of a few thousand updates keeps
 // every SM's memory pipeline busy instead of crowding onto the first CTAs.
 // spread_warp keeps 32 consecutive indices in one warp (warp-uniform loops).
+// Row kind of a vertex with d used slots: 0 thread, 1 warp, 2 four-warp group, 3 CTA.
+__device__ __forceinline__ int row_bin(const MfParams &P, int d)
+{
+    return d <= P.small_deg ? 0 : (d <= P.hub_deg ? 1 : (d <= P.group_deg ? 2 : 3));
+}
+
 __device__ __forceinline__ long long spread_thread() { return (long long)threadIdx.x * vn() + vb(); }
 __device__ __forceinline__ long long spread_warp()
 {
@@ -121,12 +127,16 @@ struct Sh {
     long long sink_e, src_e;
     long long pushes, relabels, steep, slots, verts, cycles;
     long long lab_slots, lab_cnt;     // BFS: slots and number of the vertices labelled this level
+    unsigned long long dis_cta_ns, dis_warp_ns, dis_thread_ns;   // discharge: time of this CTA's warps by row kind
     unsigned long long red[MF_WARPS];
     long long wsum[MF_WARPS];
     int wcnt[MF_WARPS];
     long long bcast_rem;
     int bcast_k;
     int bcast_i;
+    long long tb_e[MF_BLOCK / (32 * MF_GROUP_WARPS)];   // per team (CTA: [0]; 4-warp groups: [g]) broadcasts
+    int tb_h[MF_BLOCK / (32 * MF_GROUP_WARPS)];
+    int tb_i[MF_BLOCK / (32 * MF_GROUP_WARPS)];
     int bcast_h;
     long long bcast_e;
     int ok;
@@ -158,17 +168,17 @@ __device__ __forceinline__ unsigned long long rd(const unsigned long long &x) { 
 // The termination test of the loop (Alg. 1 / Alg. 5: stop when no active
 // vertex remains), taken right after a complete backward BFS.
 __device__ __forceinline__ void decide_iteration(const MfParams &P, MfCtrl *c, unsigned long long now,
-                                                 const unsigned (&wl)[4], long long iters,
+                                                 const unsigned (&wl)[MF_NBIN + 1], long long iters,
                                                  unsigned long long t_start, int qstamp, int fstamp)
 {
     c->round = 0;
     for (int i = 0; i < 8; ++i) c->aux_tail.w[i] = 0;
     c->qstamp = qstamp + 1;
     c->fstamp = fstamp + 1;
-    const int active = (int)wl[3];
+    const int active = (int)wl[MF_NBIN];
     c->t_dis0 = now;
-    for (int b = 0; b < 3; ++b) c->wl_n[b] = (int)wl[b];
-    c->head0.w[0] = c->head1.w[0] = c->head2.w[0] = 0;
+    for (int b = 0; b < MF_NBIN; ++b) c->wl_n[b] = (int)wl[b];
+    c->head0.w[0] = c->head1.w[0] = c->head2.w[0] = c->head3.w[0] = 0;
     if (iters < MF_ACTIVE_HIST) c->active_hist[iters] = active;
     if (iters == 0) c->active_first = active;
     c->active_total = rd(c->active_total) + active;
@@ -209,20 +219,18 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
     const int lvl_hi = rd(c->lvl_hi), hub_hi = rd(c->hub_hi), level = rd(c->level), hub_lo_old = rd(c->hub_lo);
     const long long iters = rd(c->iters), bfs_levels = rd(c->bfs_levels);
     const unsigned long long t_start = rd(c->t_start);
-    unsigned wl[4], misc[4];
-    for (int i = 0; i < 4; ++i) {
-        wl[i] = rd(c->wl_tail.w[i]);
-        misc[i] = rd(c->misc.w[i]);
-    }
-    unsigned aux[5];
-    for (int i = 0; i < 5; ++i) aux[i] = rd(c->aux_tail.w[i]);
+    unsigned wl[MF_NBIN + 1], misc[4];
+    for (int i = 0; i <= MF_NBIN; ++i) wl[i] = rd(c->wl_tail.w[i]);
+    for (int i = 0; i < 4; ++i) misc[i] = rd(c->misc.w[i]);
+    unsigned aux[MF_NBIN + 2];
+    for (int i = 0; i < MF_NBIN + 2; ++i) aux[i] = rd(c->aux_tail.w[i]);
     const int sel = rd(c->wl_sel), round = rd(c->round), qstamp = rd(c->qstamp), fstamp = rd(c->fstamp);
     const long long rounds_total = rd(c->rounds_total);
     const long long slots_all = rd(c->slots_bfs) + rd(c->slots_dis) + rd(c->slots_fix);
     const unsigned long long fin_max = rd(c->fin_max), fin_sum = rd(c->fin_sum);
     const int bu_prev = rd(c->bu_mode);
-    int wl_prev[3];
-    for (int b = 0; b < 3; ++b) wl_prev[b] = rd(c->wl_n[b]);
+    int wl_prev[MF_NBIN];
+    for (int b = 0; b < MF_NBIN; ++b) wl_prev[b] = rd(c->wl_n[b]);
     int tinfo = 0;
     unsigned err = rd(c->err.w[0]);
     const unsigned long long dt = now - t_phase;
@@ -245,12 +253,13 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
         c->lab_bfs = c->slots_apply = c->clamps_apply = c->hscan_bfs = 0;
         c->fin_max = c->fin_sum = 0;
         c->ns_bfs = c->ns_dis = c->ns_fix = c->ns_wl = c->ns_apply = 0;
+        c->ns_dis_cta = c->ns_dis_warp = c->ns_dis_thread = 0;
         c->bfs_tail.w[0] = 0;
         c->hub_tail.w[0] = 0;
         c->defer_tail.w[0] = 0;
         c->bu_split = 0;
-        c->head0.w[0] = c->head1.w[0] = c->head2.w[0] = 0;
-        for (int i = 0; i < 4; ++i) c->wl_tail.w[i] = 0;
+        c->head0.w[0] = c->head1.w[0] = c->head2.w[0] = c->head3.w[0] = 0;
+        for (int i = 0; i < 8; ++i) c->wl_tail.w[i] = 0;
         for (int i = 0; i < 8; ++i) c->misc.w[i] = 0;
         for (int i = 0; i < MF_ACTIVE_HIST; ++i) c->active_hist[i] = 0;
         for (int i = 0; i < 8; ++i) c->aux_tail.w[i] = 0;
@@ -292,8 +301,8 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
         for (int i = 0; i < 4; ++i) c->bfs_acc.w[i] = 0;
         c->need_total = rd(c->bfs_acc.w[4]) == 0 && rd(c->bfs_acc.w[5]) == 0;
         c->bu_mode = 0;
-        for (int i = 0; i < 4; ++i) c->wl_tail.w[i] = 0;
-        c->head0.w[0] = c->head1.w[0] = c->head2.w[0] = 0;
+        for (int i = 0; i < 8; ++i) c->wl_tail.w[i] = 0;
+        c->head0.w[0] = c->head1.w[0] = c->head2.w[0] = c->head3.w[0] = 0;
         break;
     case H_BFS_START:
     case H_BFS_NEXT: {
@@ -341,10 +350,11 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
         // after a discharge round: run another one over the vertices that
         // became active during it, or end the discharge of this iteration
         c->ns_dis = rd(c->ns_dis) + dt;
-        tinfo = (min(wl_prev[2], 1023) << 20) | min(wl_prev[0] + wl_prev[1] + wl_prev[2], (1 << 20) - 1);
-        c->head0.w[0] = c->head1.w[0] = c->head2.w[0] = 0;
+        tinfo = (min(wl_prev[2] + wl_prev[3], 1023) << 20) |
+                min(wl_prev[0] + wl_prev[1] + wl_prev[2] + wl_prev[3], (1 << 20) - 1);
+        c->head0.w[0] = c->head1.w[0] = c->head2.w[0] = c->head3.w[0] = 0;
         c->rounds_total = rounds_total + 1;
-        const unsigned nxt = aux[0] + aux[1] + aux[2];
+        const unsigned nxt = aux[0] + aux[1] + aux[2] + aux[3];
         // fixed: P.rounds rounds; adaptive (P.rounds == 0): at least
         // MF_DEFAULT_ROUNDS, then more while this iteration's discharge has
         // taken less than half of its BFS -- a global relabel that costs much
@@ -360,7 +370,7 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
         }
         if (more) {
             c->wl_sel = sel ^ 1;
-            for (int b = 0; b < 3; ++b) {
+            for (int b = 0; b < MF_NBIN; ++b) {
                 c->wl_n[b] = (int)aux[b];
                 c->aux_tail.w[b] = 0;
             }
@@ -369,8 +379,8 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
             c->dis_more = 1;
         } else {
             c->dis_more = 0;
-            c->fix_n[0] = (int)aux[3];
-            c->fix_n[1] = (int)aux[4];
+            c->fix_n[0] = (int)aux[MF_NBIN];
+            c->fix_n[1] = (int)aux[MF_NBIN + 1];
         }
         break;
     }
@@ -480,6 +490,12 @@ __device__ void flush_acc(const MfParams &P, Sh &sh, int phase)
                 atomic_add_ll(&c->slots_apply, sh.slots);
                 atomic_add_ll(&c->clamps_apply, sh.cycles);
             }
+        }
+        if (sh.dis_cta_ns || sh.dis_warp_ns || sh.dis_thread_ns) {
+            atomicAdd(&c->ns_dis_cta, sh.dis_cta_ns);
+            atomicAdd(&c->ns_dis_warp, sh.dis_warp_ns);
+            atomicAdd(&c->ns_dis_thread, sh.dis_thread_ns);
+            sh.dis_cta_ns = sh.dis_warp_ns = sh.dis_thread_ns = 0;
         }
         if (sh.lab_cnt) {
             atomic_add_ll(&c->lab_bfs, sh.lab_cnt);
@@ -954,8 +970,8 @@ __device__ __forceinline__ void frontier_push(const MfParams &P, Sh &sh, const b
 {
     MfCtrl *ctl = P.ctrl;
     const int lane = threadIdx.x & 31;
-    // per-lane counts packed 8 bits each: [0] regular, [1..3] worklist bins
-    unsigned packed = 0;
+    // per-lane counts packed 8 bits each: [0] regular, [1..MF_NBIN] worklist bins
+    unsigned long long packed = 0;
     bool anybig = false;
     long long lab_slots = 0;
     int lab_n = 0;
@@ -966,20 +982,17 @@ __device__ __forceinline__ void frontier_push(const MfParams &P, Sh &sh, const b
         ++lab_n;
         const bool big = d[r] > P.bfs_hub;
         anybig |= big;
-        if (!big) packed += 1u;
-        if (with_wl && ev[r] > 0) {
-            const int bin = d[r] <= P.small_deg ? 0 : (d[r] <= P.hub_deg ? 1 : 2);
-            packed += 1u << (8 * (bin + 1));
-        }
+        if (!big) packed += 1ull;
+        if (with_wl && ev[r] > 0) packed += 1ull << (8 * (row_bin(P, d[r]) + 1));
     }
-    unsigned incl = packed;
+    unsigned long long incl = packed;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+        unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += y;
     }
-    const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
-    const unsigned excl = incl - packed;
+    const unsigned long long total = __shfl_sync(0xffffffffu, incl, 31);
+    const unsigned long long excl = incl - packed;
     // slots and number of the vertices labelled (the BFS direction test reads them)
     lab_slots = warp_sum_ll(lab_slots);
     const long long lab_cnt = warp_sum_ll((long long)lab_n);
@@ -988,27 +1001,30 @@ __device__ __forceinline__ void frontier_push(const MfParams &P, Sh &sh, const b
         atomicAdd((unsigned long long *)&sh.lab_cnt, (unsigned long long)lab_cnt);
     }
     if (total != 0) {
-        unsigned base[4] = {0, 0, 0, 0};
+        unsigned base[MF_NBIN + 1];
+#pragma unroll
+        for (int b = 0; b <= MF_NBIN; ++b) base[b] = 0;
         if (lane == 0) {
-            if (total & 0xffu) base[0] = atomicAdd(&ctl->bfs_tail.w[0], total & 0xffu);
-            for (int b = 0; b < 3; ++b) {
-                unsigned k = (total >> (8 * (b + 1))) & 0xffu;
+            if (total & 0xffull) base[0] = atomicAdd(&ctl->bfs_tail.w[0], (unsigned)(total & 0xffull));
+            unsigned act = 0;
+            for (int b = 0; b < MF_NBIN; ++b) {
+                const unsigned k = (unsigned)((total >> (8 * (b + 1))) & 0xffull);
                 if (k) base[b + 1] = atomicAdd(&ctl->wl_tail.w[b], k);
+                act += k;
             }
-            unsigned act = ((total >> 8) & 0xffu) + ((total >> 16) & 0xffu) + ((total >> 24) & 0xffu);
-            if (act) atomicAdd(&ctl->wl_tail.w[3], act);
+            if (act) atomicAdd(&ctl->wl_tail.w[MF_NBIN], act);
         }
 #pragma unroll
-        for (int b = 0; b < 4; ++b) base[b] = __shfl_sync(0xffffffffu, base[b], 0);
-        unsigned pos[4];
+        for (int b = 0; b <= MF_NBIN; ++b) base[b] = __shfl_sync(0xffffffffu, base[b], 0);
+        unsigned pos[MF_NBIN + 1];
 #pragma unroll
-        for (int b = 0; b < 4; ++b) pos[b] = base[b] + ((excl >> (8 * b)) & 0xffu);
+        for (int b = 0; b <= MF_NBIN; ++b) pos[b] = base[b] + (unsigned)((excl >> (8 * b)) & 0xffull);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             if (!take[r]) continue;
             if (d[r] <= P.bfs_hub) P.sc.border[pos[0]++] = z[r];
             if (with_wl && ev[r] > 0) {
-                const int bin = d[r] <= P.small_deg ? 0 : (d[r] <= P.hub_deg ? 1 : 2);
+                const int bin = row_bin(P, d[r]);
                 P.sc.wl[sel][bin][pos[bin + 1]++] = z[r];
             }
         }
@@ -1391,15 +1407,11 @@ __device__ __noinline__ void phase_worklist(const MfParams &P, Sh &sh)
         bool act = cand && ldg_cg(P.h + v) < n && (P.pull ? ev < 0 : ev > 0);
         bool listed = P.data_driven ? act : cand;
         int bin = 0;
-        if (listed) {
-            int d = ldg_cg(P.g.deg + v);
-            bin = d <= P.small_deg ? 0 : (d <= P.hub_deg ? 1 : 2);
-        }
+        if (listed) bin = row_bin(P, ldg_cg(P.g.deg + v));
         unsigned am = __ballot_sync(0xffffffffu, act);
-        if (lane == 0 && am) atomicAdd(&ctl->wl_tail.w[3], (unsigned)__popc(am));
-        warp_append(&ctl->wl_tail.w[0], P.sc.wl[sel][0], listed && bin == 0, v);
-        warp_append(&ctl->wl_tail.w[1], P.sc.wl[sel][1], listed && bin == 1, v);
-        warp_append(&ctl->wl_tail.w[2], P.sc.wl[sel][2], listed && bin == 2, v);
+        if (lane == 0 && am) atomicAdd(&ctl->wl_tail.w[MF_NBIN], (unsigned)__popc(am));
+#pragma unroll
+        for (int b = 0; b < MF_NBIN; ++b) warp_append(&ctl->wl_tail.w[b], P.sc.wl[sel][b], listed && bin == b, v);
     }
 }
 
@@ -1424,8 +1436,7 @@ struct DisCtx {
 __device__ __forceinline__ void enqueue_active(const MfParams &P, int z, const DisCtx &dc)
 {
     if (atomicExch(P.sc.vmark + z, dc.qstamp) == dc.qstamp) return;
-    const int d = ldg_cg(P.g.deg + z);
-    const int bin = d <= P.small_deg ? 0 : (d <= P.hub_deg ? 1 : 2);
+    const int bin = row_bin(P, ldg_cg(P.g.deg + z));
     const unsigned pos = atomicAdd(&P.ctrl->aux_tail.w[bin], 1u);
     P.sc.wl[dc.nsel][bin][pos] = z;
 }
@@ -1448,7 +1459,7 @@ __device__ __forceinline__ void note_relabel(const MfParams &P, int u, const Dis
     if (atomicExch(P.sc.fixmark + u, dc.fstamp) == dc.fstamp) return;
     const int d = ldg_cg(P.g.deg + u);
     const int li = d > P.hub_deg ? 1 : 0;
-    const unsigned pos = atomicAdd(&P.ctrl->aux_tail.w[3 + li], 1u);
+    const unsigned pos = atomicAdd(&P.ctrl->aux_tail.w[MF_NBIN + li], 1u);
     P.sc.fixl[li][pos] = u;
 }
 
@@ -1695,25 +1706,33 @@ __device__ __noinline__ bool discharge_thread(const MfParams &P, Sh &sh, int u, 
             const long long eu = PULL ? -ldg_cg(P.e + u) : ldg_cg(P.e + u);
             if (!(hu < n && eu > 0)) break;
             ++scans;
-            if (!have) {
-                int c[kTS], z[kTS];
+            unsigned long long best = kEmpty;
+            // the snapshot serves the pushes; a relabel is decided on fresh values
+            // (a slot that gained residual capacity since the snapshot may be lower)
+            for (int pass = 0; pass < 2; ++pass) {
+                if (!have || pass == 1) {
+                    int c[kTS], z[kTS];
+#pragma unroll
+                    for (int j = 0; j < kTS; ++j) {
+                        c[j] = j < d ? residual_dir<PULL>(P, r0 + j) : 0;
+                        z[j] = j < d ? ldg_cg(P.g.dst + r0 + j) : 0;
+                    }
+#pragma unroll
+                    for (int j = 0; j < kTS; ++j) hc[j] = c[j] > 0 ? ldg_cg(P.h + z[j]) : kNoRes;
+                    gscan += d;
+                }
+                const bool fresh = !have || pass == 1;
+                have = true;
+                best = kEmpty;
 #pragma unroll
                 for (int j = 0; j < kTS; ++j) {
-                    c[j] = j < d ? residual_dir<PULL>(P, r0 + j) : 0;
-                    z[j] = j < d ? ldg_cg(P.g.dst + r0 + j) : 0;
+                    if (hc[j] != kNoRes) {
+                        const unsigned long long key = ((unsigned long long)(unsigned)hc[j] << 32) | (unsigned)j;
+                        best = key < best ? key : best;
+                    }
                 }
-#pragma unroll
-                for (int j = 0; j < kTS; ++j) hc[j] = c[j] > 0 ? ldg_cg(P.h + z[j]) : kNoRes;
-                have = true;
-                gscan += d;
-            }
-            unsigned long long best = kEmpty;
-#pragma unroll
-            for (int j = 0; j < kTS; ++j) {
-                if (hc[j] != kNoRes) {
-                    const unsigned long long key = ((unsigned long long)(unsigned)hc[j] << 32) | (unsigned)j;
-                    best = key < best ? key : best;
-                }
+                const int bh = best == kEmpty ? 0x7fffffff : (int)(best >> 32);
+                if (fresh || !(best == kEmpty || hu <= bh)) break;
             }
             const int best_h = best == kEmpty ? 0x7fffffff : (int)(best >> 32);
             if (best == kEmpty || hu <= best_h) {
@@ -1831,6 +1850,14 @@ __device__ __noinline__ bool discharge_warp_rows(const MfParams &P, Sh &sh, int 
             __syncwarp();
         } else {
             best = warp_min_u64(scan_staged(stg, d, lane, 32));
+            const int bh = best == kEmpty ? 0x7fffffff : (int)(best >> 32);
+            if (best == kEmpty || hu <= bh) {
+                // a relabel is decided on fresh values: refresh the snapshot first
+                __syncwarp();
+                best = warp_min_u64(scan_and_stage_v4<PULL>(P, r0, d, lane, 32, stg));
+                gscan += d;
+                __syncwarp();
+            }
         }
         int best_h = best == kEmpty ? 0x7fffffff : (int)(best >> 32);
         if (best == kEmpty || hu <= best_h) {
@@ -1972,15 +1999,37 @@ __device__ __forceinline__ bool discharge_warp(const MfParams &P, Sh &sh, int u,
     return discharge_warp_rows<PULL, false>(P, sh, u, d, dc, nullptr);
 }
 
-// One CTA per vertex; ST: the row's heads are kept in stg (the CTA's on-chip
-// snapshot) after the first scan.
-template <bool PULL, bool ST>
-__device__ __noinline__ bool discharge_cta_rows(const MfParams &P, Sh &sh, int u, int d, const DisCtx &dc, int *stg)
+// The threads that discharge one long row together: the whole CTA, or a group
+// of MF_GROUP_WARPS warps (a quarter of the CTA, with its own named barrier and
+// its own quarter of the snapshot), so that four rows of moderate length are
+// discharged side by side.  tid: thread index in the team, n: its threads,
+// w0 / nw: its first warp and warp count in the CTA, g: its broadcast slot.
+struct CtaTeam {
+    int tid, n, w0, nw, g;
+    __device__ CtaTeam() : tid((int)threadIdx.x), n((int)blockDim.x), w0(0), nw((int)(blockDim.x >> 5)), g(0) {}
+    __device__ void sync() const { __syncthreads(); }
+};
+
+struct GroupTeam {
+    int tid, n, w0, nw, g;
+    __device__ GroupTeam()
+        : tid((int)threadIdx.x & (32 * MF_GROUP_WARPS - 1)), n(32 * MF_GROUP_WARPS),
+          w0((int)(threadIdx.x >> 5) & ~(MF_GROUP_WARPS - 1)), nw(MF_GROUP_WARPS),
+          g((int)threadIdx.x / (32 * MF_GROUP_WARPS))
+    {
+    }
+    __device__ void sync() const { asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(n) : "memory"); }
+};
+
+// One team per vertex; ST: the row's heads are kept in stg (the team's share of
+// the on-chip snapshot) after the first scan.
+template <bool PULL, bool ST, class Team>
+__device__ __noinline__ bool discharge_team_rows(const MfParams &P, Sh &sh, int u, int d, const DisCtx &dc, int *stg)
 {
+    const Team T;
     bool lifted = false;
     const int n = P.g.n;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
     const int r0 = P.g.off[u];
     const int kcyc = cycles_for(P, d);
     constexpr bool st = ST;
@@ -1989,30 +2038,40 @@ __device__ __noinline__ bool discharge_cta_rows(const MfParams &P, Sh &sh, int u
     long long cand = 0;
     int cyc = 0;
     while (cyc < kcyc) {
-        if (threadIdx.x == 0) {
-            sh.bcast_e = PULL ? -ldg_cg(P.e + u) : ldg_cg(P.e + u);
-            sh.bcast_h = ldg_cg(P.h + u);
+        if (T.tid == 0) {
+            sh.tb_e[T.g] = PULL ? -ldg_cg(P.e + u) : ldg_cg(P.e + u);
+            sh.tb_h[T.g] = ldg_cg(P.h + u);
         }
-        __syncthreads();
-        const long long eu = sh.bcast_e;
-        const int hu = sh.bcast_h;
+        T.sync();
+        const long long eu = sh.tb_e[T.g];
+        const int hu = sh.tb_h[T.g];
         if (!(hu < n && eu > 0)) {
-            __syncthreads();
+            T.sync();
             break;
         }
         unsigned long long best;
-        const bool global_scan = !st || !have;
-        if (!st) best = scan_lowest<8, PULL>(P, r0, d, threadIdx.x, blockDim.x);
-        else if (!have) best = scan_and_stage_v4<PULL>(P, r0, d, threadIdx.x, blockDim.x, stg);
-        else best = scan_staged(stg, d, threadIdx.x, blockDim.x);
+        bool global_scan = !st || !have;
+        if (!st) best = scan_lowest<8, PULL>(P, r0, d, T.tid, T.n);
+        else if (!have) best = scan_and_stage_v4<PULL>(P, r0, d, T.tid, T.n, stg);
+        else best = scan_staged(stg, d, T.tid, T.n);
         have = true;
         best = warp_min_u64(best);
         if (lane == 0) sh.red[wid] = best;
-        __syncthreads();
+        T.sync();
         unsigned long long b = kEmpty;
-        for (int w = 0; w < nwarps; ++w) b = sh.red[w] < b ? sh.red[w] : b;
+        for (int w = T.w0; w < T.w0 + T.nw; ++w) b = sh.red[w] < b ? sh.red[w] : b;
+        if (!global_scan && (b == kEmpty || hu <= (int)(b >> 32))) {
+            // a relabel is decided on fresh values: refresh the snapshot first
+            T.sync();               // every warp has read sh.red
+            best = warp_min_u64(scan_and_stage_v4<PULL>(P, r0, d, T.tid, T.n, stg));
+            if (lane == 0) sh.red[wid] = best;
+            T.sync();
+            b = kEmpty;
+            for (int w = T.w0; w < T.w0 + T.nw; ++w) b = sh.red[w] < b ? sh.red[w] : b;
+            global_scan = true;
+        }
         const int best_h = b == kEmpty ? 0x7fffffff : (int)(b >> 32);
-        if (threadIdx.x == 0) {
+        if (T.tid == 0) {
             atomicAdd((unsigned long long *)&sh.cycles, 1ull);
             if (global_scan) atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)d);
         }
@@ -2020,7 +2079,7 @@ __device__ __noinline__ bool discharge_cta_rows(const MfParams &P, Sh &sh, int u
         if (!go) {
             // relabel, then straight on to the pushes it makes admissible
             const int nh = (b == kEmpty || best_h >= n - 1) ? n : best_h + 1;
-            if (threadIdx.x == 0) {
+            if (T.tid == 0) {
                 P.h[u] = nh;
                 atomicAdd((unsigned long long *)&sh.relabels, 1ull);
             }
@@ -2030,8 +2089,8 @@ __device__ __noinline__ bool discharge_cta_rows(const MfParams &P, Sh &sh, int u
         }
         if (go) {
             // Alg. 2's next cycles, fused (as in discharge_warp): a step covers
-            // seg * blockDim slots, every thread seg contiguous ones, so slot
-            // order is thread order and one CTA prefix sum over the threads'
+            // seg * T.n slots, every thread seg contiguous ones, so slot
+            // order is thread order and one team prefix sum over the threads'
             // totals orders all the amounts of the step.  The first step takes
             // one slot per thread (the excess often runs out there), later
             // ones kSeg.
@@ -2041,8 +2100,8 @@ __device__ __noinline__ bool discharge_cta_rows(const MfParams &P, Sh &sh, int u
             int k = 0;
             long long sent = 0;
             int seg = 1;
-            for (int jb = j0; jb < d && rem > 0 && cyc + k < kcyc; jb += seg * (int)blockDim.x, seg = kSeg) {
-                const int js = jb + (int)threadIdx.x * seg;
+            for (int jb = j0; jb < d && rem > 0 && cyc + k < kcyc; jb += seg * T.n, seg = kSeg) {
+                const int js = jb + T.tid * seg;
                 int a[kSeg];
                 long long tsum = 0;
                 int tcnt = 0;
@@ -2088,8 +2147,8 @@ __device__ __noinline__ bool discharge_cta_rows(const MfParams &P, Sh &sh, int u
                             tcnt += a[r] > 0 ? 1 : 0;
                         }
                     }
-                    if (threadIdx.x == 0)
-                        atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)(seg * blockDim.x));
+                    if (T.tid == 0)
+                        atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)(seg * T.n));
                 }
                 long long incl = tsum;
                 int cincl = tcnt;
@@ -2106,10 +2165,10 @@ __device__ __noinline__ bool discharge_cta_rows(const MfParams &P, Sh &sh, int u
                     sh.wsum[wid] = incl;
                     sh.wcnt[wid] = cincl;
                 }
-                __syncthreads();
+                T.sync();
                 long long off = incl - tsum;
                 int coff = cincl - tcnt;
-                for (int w = 0; w < wid; ++w) {
+                for (int w = T.w0; w < wid; ++w) {
                     off += sh.wsum[w];
                     coff += sh.wcnt[w];
                 }
@@ -2133,24 +2192,24 @@ __device__ __noinline__ bool discharge_cta_rows(const MfParams &P, Sh &sh, int u
                 }
                 const long long wt = warp_sum_ll(mine);
                 const int wk = (int)warp_sum_ll((long long)mk);
-                __syncthreads();               // every warp has read the prefix words
+                T.sync();               // every warp has read the prefix words
                 if (lane == 0) {
                     sh.wsum[wid] = wt;
                     sh.wcnt[wid] = wk;
                 }
-                __syncthreads();
+                T.sync();
                 long long tot = 0;
                 int kk = 0;
-                for (int w = 0; w < nwarps; ++w) {
+                for (int w = T.w0; w < T.w0 + T.nw; ++w) {
                     tot += sh.wsum[w];
                     kk += sh.wcnt[w];
                 }
                 rem -= tot;
                 sent += tot;
                 k += kk;
-                __syncthreads();               // before the words are reused
+                T.sync();               // before the words are reused
             }
-            if (threadIdx.x == 0) {
+            if (T.tid == 0) {
                 if (sent) atomic_add_ll(P.e + u, PULL ? sent : -sent);
                 if (k) atomicAdd((unsigned long long *)&sh.pushes, (unsigned long long)k);
             }
@@ -2158,7 +2217,7 @@ __device__ __noinline__ bool discharge_cta_rows(const MfParams &P, Sh &sh, int u
             if (k > 0) cyc += k;
             else if (!st || ++stale > kStaleMax) cyc += 1;
         }
-        __syncthreads();
+        T.sync();
     }
     if (cand) atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)cand);
     return lifted;
@@ -2171,8 +2230,19 @@ template <bool PULL>
 __device__ __forceinline__ bool discharge_cta(const MfParams &P, Sh &sh, int u, const DisCtx &dc, int *stg, int ccap)
 {
     const int d = ldg_cg(P.g.deg + u);
-    if (stg != nullptr && d <= ccap) return discharge_cta_rows<PULL, true>(P, sh, u, d, dc, stg);
-    return discharge_cta_rows<PULL, false>(P, sh, u, d, dc, nullptr);
+    if (stg != nullptr && d <= ccap) return discharge_team_rows<PULL, true, CtaTeam>(P, sh, u, d, dc, stg);
+    return discharge_team_rows<PULL, false, CtaTeam>(P, sh, u, d, dc, nullptr);
+}
+
+// One 4-warp group per vertex (rows up to group_deg slots, which fit the
+// group's share of the snapshot).  All threads of the group call this
+// together; the return value is meaningful in the group's thread 0.
+template <bool PULL>
+__device__ __forceinline__ bool discharge_group(const MfParams &P, Sh &sh, int u, const DisCtx &dc, int *stg, int gcap)
+{
+    const int d = ldg_cg(P.g.deg + u);
+    if (stg != nullptr && d <= gcap) return discharge_team_rows<PULL, true, GroupTeam>(P, sh, u, d, dc, stg);
+    return discharge_team_rows<PULL, false, GroupTeam>(P, sh, u, d, dc, nullptr);
 }
 
 template <bool PULL>
@@ -2188,10 +2258,11 @@ __device__ __noinline__ void phase_discharge(const MfParams &P, Sh &sh)
     // queue the vertices that become active for a next round if one may follow
     // (adaptive rounds: the hook decides after this round)
     dc.queue = vrd(&ctl->round) + 1 < (P.rounds > 0 ? P.rounds : MF_MAX_ROUNDS);
-    const int *wl0 = P.sc.wl[sel][0], *wl1 = P.sc.wl[sel][1], *wl2 = P.sc.wl[sel][2];
+    const int *wl0 = P.sc.wl[sel][0], *wl1 = P.sc.wl[sel][1], *wl2 = P.sc.wl[sel][2], *wl3 = P.sc.wl[sel][3];
     int *stage = P.stage_slots > 0 ? mf_stage : nullptr;
-    // hubs: one CTA each
-    const int nh = vrd(&ctl->wl_n[2]);
+    const unsigned long long t_a = gtimer();
+    // the longest rows: one CTA each
+    const int nh = vrd(&ctl->wl_n[3]);
     for (;;) {
         if (threadIdx.x == 0) {
             unsigned cur = *(volatile unsigned *)&ctl->head2.w[0];
@@ -2201,13 +2272,39 @@ __device__ __noinline__ void phase_discharge(const MfParams &P, Sh &sh)
         int i = sh.bcast_i;
         __syncthreads();
         if (i >= nh) break;
-        const int u = __ldcg(wl2 + i);
+        const int u = __ldcg(wl3 + i);
         const bool lifted = discharge_cta<PULL>(P, sh, u, dc, stage, P.stage_slots);
         if (threadIdx.x == 0) {
             if (lifted) note_relabel(P, u, dc);
             requeue_if_active<PULL>(P, u, dc);
         }
     }
+    // long rows up to group_deg: one 4-warp group each, four side by side per
+    // CTA, each group on its own quarter of the snapshot buffer
+    {
+        const GroupTeam T;
+        const int gcap = P.stage_slots / (MF_BLOCK / (32 * MF_GROUP_WARPS));
+        int *gstage = stage != nullptr ? stage + T.g * gcap : nullptr;
+        const int ng = vrd(&ctl->wl_n[2]);
+        for (;;) {
+            if (T.tid == 0) {
+                unsigned cur = *(volatile unsigned *)&ctl->head3.w[0];
+                sh.tb_i[T.g] = (int)(cur >= (unsigned)ng ? cur : atomicAdd(&ctl->head3.w[0], 1u));
+            }
+            T.sync();
+            const int i = sh.tb_i[T.g];
+            T.sync();
+            if (i >= ng) break;
+            const int u = __ldcg(wl2 + i);
+            const bool lifted = discharge_group<PULL>(P, sh, u, dc, gstage, gcap);
+            if (T.tid == 0) {
+                if (lifted) note_relabel(P, u, dc);
+                requeue_if_active<PULL>(P, u, dc);
+            }
+        }
+    }
+    const unsigned long long t_b = gtimer();
+    if (lane == 0) atomicAdd((unsigned long long *)&sh.dis_cta_ns, t_b - t_a);
     // mid-degree rows: one warp each (the CTA's snapshot buffer is free again:
     // every thread has left the loop above, so each warp takes a slice)
     const int nm = vrd(&ctl->wl_n[1]);
@@ -2223,6 +2320,7 @@ __device__ __noinline__ void phase_discharge(const MfParams &P, Sh &sh)
             requeue_if_active<PULL>(P, u, dc);
         }
     }
+    const unsigned long long t_c = gtimer();
     // small rows: one thread each, 32 per grab
     const int ns = vrd(&ctl->wl_n[0]);
     for (;;) {
@@ -2233,6 +2331,13 @@ __device__ __noinline__ void phase_discharge(const MfParams &P, Sh &sh)
             if (discharge_thread<PULL>(P, sh, u, dc)) note_relabel(P, u, dc);
             requeue_if_active<PULL>(P, u, dc);
         }
+    }
+    __syncwarp();
+    const unsigned long long t_d = gtimer();
+    if (lane == 0) {
+        // per warp, into the CTA's accumulators (one global atomic per CTA and phase)
+        atomicAdd((unsigned long long *)&sh.dis_warp_ns, t_c - t_b);
+        atomicAdd((unsigned long long *)&sh.dis_thread_ns, t_d - t_c);
     }
 }
 
@@ -2363,6 +2468,7 @@ __device__ __noinline__ bool solve_instance(const MfParams &P, Sh &sh)
         sh.sink_e = sh.src_e = 0;
         sh.pushes = sh.relabels = sh.steep = sh.slots = sh.verts = sh.cycles = 0;
         sh.lab_slots = sh.lab_cnt = 0;
+        sh.dis_cta_ns = sh.dis_warp_ns = sh.dis_thread_ns = 0;
     }
     // a CTA that never arrives (tests only): the others give up after
     // wait_limit_ns, record MF_E_WAIT and leave the kernel

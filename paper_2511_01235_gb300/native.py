@@ -75,7 +75,8 @@ class Stats(C.Structure):
                 ("ms_fix", C.c_double), ("ms_worklist", C.c_double), ("ms_apply", C.c_double),
                 ("value", C.c_int64), ("ms_kernel", C.c_double), ("barriers", C.c_int64),
                 ("discharge_rounds", C.c_int64), ("rounds", C.c_int32), ("reserved0", C.c_int32),
-                ("ms_update", C.c_double)]
+                ("ms_update", C.c_double), ("us_discharge_cta_rows", C.c_double),
+                ("us_discharge_warp_rows", C.c_double), ("us_discharge_thread_rows", C.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -97,7 +98,8 @@ EXPORTS = ["maxflow_build_layout", "maxflow_kernel_launches", "maxflow_default_o
            "maxflow_arena_stats", "maxflow_arena_fits", "maxflow_evicted_sizes",
            "maxflow_resolve_static_pp", "maxflow_resolve_static_pull", "maxflow_update_pp",
            "maxflow_set_bfs_switch", "maxflow_test_stalled_barrier", "maxflow_set_requeue",
-           "maxflow_set_cycle_div", "maxflow_set_fix_steep", "maxflow_set_bfs_tail"]
+           "maxflow_set_cycle_div", "maxflow_set_fix_steep", "maxflow_set_bfs_tail", "maxflow_checkpoint",
+           "maxflow_rollback"]
 
 TRACE_NAMES = ["start", "prologue", "batch_validated", "batch_located", "room_checked", "capacities_changed",
                "iteration_start", "bfs_roots", "bfs_level", "worklist", "discharge", "end", "bfs_bottom_up_first",
@@ -147,6 +149,8 @@ def load(build_if_missing: bool = False):
     L.maxflow_set_cycle_div.argtypes = [vp, i32]
     L.maxflow_set_fix_steep.argtypes = [vp, i32]
     L.maxflow_set_bfs_tail.argtypes = [vp, i32]
+    L.maxflow_checkpoint.argtypes = [vp]
+    L.maxflow_rollback.argtypes = [vp]
     L.maxflow_set_tuning.argtypes = [vp, i32, i32, i32]
     L.maxflow_device_bytes.argtypes = [vp, P(i64)]
     L.maxflow_evict.argtypes = [vp]
@@ -696,6 +700,14 @@ class Solver:
 
     def set_cycle_div(self, div: int):
         _check(load().maxflow_set_cycle_div(self.h, int(div)), "maxflow_set_cycle_div")
+
+    def checkpoint(self):
+        """Keep a deep copy of the state (replacing an earlier checkpoint)."""
+        _check(load().maxflow_checkpoint(self.h), "maxflow_checkpoint")
+
+    def rollback(self):
+        """Return to the last checkpoint's state exactly (after a call that failed)."""
+        _check(load().maxflow_rollback(self.h), "maxflow_rollback")
 
     def set_bfs_tail(self, slots: int):
         _check(load().maxflow_set_bfs_tail(self.h, int(slots)), "maxflow_set_bfs_tail")

@@ -590,6 +590,79 @@ def test_bfs_direction_switch_does_not_change_labels_or_values(alpha, beta):
     C.close(); R.close(); S.close()
 
 
+@pytest.mark.parametrize("family", ["rmat12", "grid64", "geometric"])
+def test_one_cta_bfs_levels_give_the_same_heights_and_values(family):
+    # small top-down levels run in the first CTA alone (maxflow_set_bfs_tail):
+    # the heights of a BFS-only relabel and the values over updates are those of
+    # the grid-wide levels, and the oracle's heights
+    if family == "rmat12":
+        g = W.rmat(12, 16, 0.57, 0.19, 0.19, seed=181, cap_hi=1000)
+        mk = lambda es, rng: W.mixed_batch(es, 300, rng, ins_cap_hi=1000, st_bias=(g.s, g.t, 0.3))
+    elif family == "grid64":
+        G = W.GridSegmentation(side=64, seed=3, window=16, origin=(16, 16), step=1)
+        g = G.graph()
+        ks = iter(range(30))
+        mk = lambda es, rng: G.window_batch(next(ks))
+    else:
+        g = W.geometric(4000, seed=183)
+        mk = lambda es, rng: W.mixed_batch(es, 200, rng, ins_cap_hi=500)
+    es = W.EdgeSet(g.n, g.src, g.dst, g.cap)
+    rng = np.random.default_rng(182)
+    S = native.Solver(g.n, g.src, g.dst, g.cap, g.s, g.t)
+    R = S.clone()
+    S.set_bfs_tail(1 << 20)          # every top-down level qualifies
+    R.set_bfs_tail(0)
+    for _ in range(3):
+        b = mk(es, rng)
+        es.apply(b.u, b.v, b.cap)
+        S.update(b.u, b.v, b.cap)
+        R.update(b.u, b.v, b.cap)
+        u2, v2, c2 = es.coo()
+        check_against_oracle(S, g.n, u2, v2, c2, g.s, g.t)
+        assert S.query()[0] == R.query()[0]
+    C = S.clone()
+    C.set_bfs_tail(0)
+    S.global_relabel()
+    C.global_relabel()
+    h = S.vertex_state()[0]
+    assert np.array_equal(h, C.vertex_state()[0])
+    su, sv, scap, scf = S.residual()
+    Ro = oracle.Residual(g.n, *es.coo())
+    _, e = S.vertex_state()
+    # the oracle's heights on the same residual state (loaded as a flow)
+    flow = np.maximum(scap.astype(np.int64) - scf, 0)
+    keep = scap > 0
+    Ro.set_flow(su[keep], sv[keep], flow[keep].astype(np.int32))
+    assert np.array_equal(h, Ro.heights(g.s, g.t, deficit_roots=True))
+    with pytest.raises(native.MaxflowError):
+        S.set_bfs_tail(-1)
+    C.close(); R.close(); S.close()
+
+
+@pytest.mark.parametrize("rq,div", [(0, 0), (1, 256), (1, 4)])
+def test_requeue_and_cycle_budget_do_not_change_values(rq, div):
+    # discharge settings that steer work only: the same values as the oracle
+    g = W.rmat(12, 16, 0.57, 0.19, 0.19, seed=191, cap_hi=1000)
+    es = W.EdgeSet(g.n, g.src, g.dst, g.cap)
+    rng = np.random.default_rng(192)
+    S = native.Solver(g.n, g.src, g.dst, g.cap, g.s, g.t)
+    S.set_requeue(rq)
+    S.set_cycle_div(div)
+    for _ in range(3):
+        b = W.mixed_batch(es, 500, rng, ins_cap_hi=1000)
+        es.apply(b.u, b.v, b.cap)
+        S.update(b.u, b.v, b.cap)
+        u2, v2, c2 = es.coo()
+        v = check_against_oracle(S, g.n, u2, v2, c2, g.s, g.t)
+        cpu_certificate(S, v)
+    S.resolve_static()
+    check_against_oracle(S, g.n, *es.coo(), g.s, g.t)
+    L = native.load()
+    assert L.maxflow_set_requeue(S.h, 2) == native.ERR_INVALID
+    assert L.maxflow_set_cycle_div(S.h, -1) == native.ERR_INVALID
+    S.close()
+
+
 def test_a_stalled_barrier_times_out_and_leaves_the_context_usable():
     # one CTA never arrives at a grid barrier: the others give up after the
     # context's wait limit, the call reports the failure, and the context still
@@ -611,4 +684,40 @@ def test_a_stalled_barrier_times_out_and_leaves_the_context_usable():
         S.update(b.u, b.v, b.cap)
         u2, v2, c2 = es.coo()
         check_against_oracle(S, g.n, u2, v2, c2, g.s, g.t)
+    S.close()
+
+
+def test_checkpoint_and_rollback_restore_the_saved_state_exactly():
+    # a checkpoint, then an update and a call that fails (a stalled barrier):
+    # rollback gives back the checkpointed residuals, heights, excesses and value
+    # bit for bit, and the context goes on solving correctly
+    g = W.erdos_renyi(3000, 20000, seed=191, cap_hi=100)
+    S = native.Solver(g.n, g.src, g.dst, g.cap, g.s, g.t, wait_limit_s=0.05)
+    es = W.EdgeSet(g.n, g.src, g.dst, g.cap)
+    rng = np.random.default_rng(192)
+    b = W.mixed_batch(es, 400, rng, ins_cap_hi=100)
+    es.apply(b.u, b.v, b.cap)
+    S.update(b.u, b.v, b.cap)
+    with pytest.raises(native.MaxflowError) as ei:
+        S.rollback()                                   # nothing to roll back to yet
+    assert ei.value.code == native.ERR_STATE
+    S.checkpoint()
+    saved = (slot_dict(*S.residual()), S.vertex_state(), S.query()[0])
+    saved_es = es.copy()
+    b2 = W.mixed_batch(es, 600, rng, ins_cap_hi=100, frac=(0.2, 0.2, 0.5))   # insertions too
+    es.apply(b2.u, b2.v, b2.cap)
+    S.update(b2.u, b2.v, b2.cap)
+    L = native.load()
+    assert L.maxflow_test_stalled_barrier(S.h, 0) == native.ERR_INTERNAL
+    S.rollback()
+    assert slot_dict(*S.residual()) == saved[0]
+    h, e = S.vertex_state()
+    np.testing.assert_array_equal(h, saved[1][0])
+    np.testing.assert_array_equal(e, saved[1][1])
+    assert S.query()[0] == saved[2]
+    with pytest.raises(native.MaxflowError):
+        S.rollback()                                   # the checkpoint was used up
+    S.update(b2.u, b2.v, b2.cap)                       # the same batch again, from the restored state
+    check_against_oracle(S, g.n, *es.coo(), g.s, g.t)
+    assert saved_es.m <= es.m
     S.close()
