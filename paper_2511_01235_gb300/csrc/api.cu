@@ -374,7 +374,7 @@ int run_kernel(maxflow_ctx *c, const MfParams &p, int *kerr, int *kstatus)
     cudaEventElapsedTime(&ms, c->ev0, c->ev1);
     c->acc_ms += ms;
     *kerr = (int)c->hctrl->err.w[0];
-    *kstatus = c->hctrl->status;
+    *kstatus = c->hctrl->d.status;
     fill_stats(c, *c->hctrl, ms);
     if (*kerr != MF_E_NONE) {
         // a barrier may have been left half-way: reset it for the next launch
@@ -1175,7 +1175,7 @@ int maxflow_solve_batched(maxflow_ctx *const *ctxs, int32_t count, const maxflow
     int first_rc = MAXFLOW_OK;
     for (int32_t i = 0; i < count; ++i) {
         maxflow_ctx *c = ctxs[i];
-        const int kerr = (int)c->hctrl->err.w[0], kst = c->hctrl->status;
+        const int kerr = (int)c->hctrl->err.w[0], kst = c->hctrl->d.status;
         c->acc_ms = ms;
         fill_stats(c, *c->hctrl, ms);
         if (abort_h || kerr != MF_E_NONE) {
@@ -1518,7 +1518,7 @@ int maxflow_update_pp(maxflow_ctx *c, const maxflow_batch *b, int32_t stop_after
     }
     if (stop_after == 2) {
         c->st.ms_update = ms;
-        return status_to_rc(MF_E_NONE, c->hctrl->status == MF_ST_CAP || c->pp.hctrl->status == MF_ST_CAP
+        return status_to_rc(MF_E_NONE, c->hctrl->d.status == MF_ST_CAP || c->pp.hctrl->d.status == MF_ST_CAP
                                            ? MF_ST_CAP : MF_ST_CONVERGED);
     }
     // 3: a push solve over the whole graph finishes what the two parts left

@@ -71,6 +71,34 @@ struct alignas(128) MfLine {
 // sit on their own 128-byte lines.  Fields marked (hook) are written only by
 // the single thread that completes a grid barrier, while every other CTA
 // waits, and are read by all CTAs after it: every CTA sees the same value.
+// Hook-written values that the phases and the kernel's loop read.  They fill
+// one 128-byte line of their own; after every grid barrier one thread of each
+// CTA copies them into shared memory with 16-byte loads issued together, so a
+// phase pays one round trip to L2 for all of them instead of one per field.
+struct alignas(128) MfDesc {
+    int status;
+    int level;
+    int lvl_lo, lvl_hi;
+    int hub_lo, hub_hi;
+    int bfs_done;
+    int wl_sel;           // which worklist buffer the current round reads
+    int wl_n[MF_NBIN];
+    int ins_n, touch_n;
+    int round;            // discharge round within the iteration
+    int dis_more;         // another discharge round follows
+    int fix_n[2];         // vertices for remove-invalid-edges (warp list, CTA list)
+    int qstamp, fstamp;   // dedupe stamps (never reset: they only grow across launches)
+    int bu_mode;          // the coming BFS level runs bottom-up
+    int bu_split;         // the bottom-up level just scanned deferred long rows: their pass follows
+    int bfs_cta_mode;     // the coming top-down level is small: CTA 0 runs it (and the next small ones) alone
+    int defer_n;          // work items of that pass
+    int need_total;       // the coming BFS initialisation sums the used slots (first BFS of a launch)
+    int pad0;
+    unsigned long long t_phase;   // when the last barrier's hook ran
+    int pad1[4];
+};
+static_assert(sizeof(MfDesc) == 128, "MfDesc is one 128-byte line, copied as 16-byte vectors");
+
 struct MfCtrl {
     MfLine bar_count;     // w[0]: arrivals at the current barrier
     MfLine bar_gen;       // w[0]: barrier generation
@@ -87,28 +115,12 @@ struct MfCtrl {
     MfLine defer_tail;    // w[0]: bottom-up work items of long rows deferred to the level's second pass
     MfLine bfs_acc;       // 64-bit words: [0] slots of the vertices labelled in this level, [1] their number,
                           // [2] used slots of the whole graph (summed by the BFS initialisation)
-    // ---- (hook) snapshots ----
-    int status;
-    int level;
-    int lvl_lo, lvl_hi;
-    int hub_lo, hub_hi;
-    int wl_n[MF_NBIN];
-    int ins_n, touch_n;
-    int bfs_done;
-    int wl_sel;           // which worklist buffer the current round reads
-    int round;            // discharge round within the iteration
-    int dis_more;         // another discharge round follows
-    int fix_n[2];         // vertices for remove-invalid-edges (warp list, CTA list)
-    int qstamp, fstamp;   // dedupe stamps (never reset: they only grow across launches)
+    // ---- (hook) snapshots: what the phases read, copied to shared memory once per barrier ----
+    MfDesc d;
     unsigned long long t_bfs0, t_dis0;   // this iteration: BFS start, discharge start (adaptive rounds)
-    int bu_mode;          // the coming BFS level runs bottom-up
-    int bu_split;         // the bottom-up level just scanned deferred long rows: their pass follows
-    int bfs_cta_mode;     // the coming top-down level is small: CTA 0 runs it (and the next small ones) alone
-    int defer_n;          // work items of that pass
-    int need_total;       // the coming BFS initialisation sums the used slots (first BFS of a launch)
     long long vis_slots;  // slots of the vertices labelled so far in this BFS
     long long iters;
-    unsigned long long t_start, t_phase;
+    unsigned long long t_start;
     // ---- results and statistics (atomics, flushed once per CTA per phase) ----
     long long value;
     long long pushes, relabels, steep, bfs_levels, active_total, active_first;

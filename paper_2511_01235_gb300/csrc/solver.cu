@@ -122,6 +122,44 @@ __device__ __forceinline__ int warp_grab(unsigned *head, int cnt, unsigned k)
     return __shfl_sync(0xffffffffu, b, 0);
 }
 
+// Items [0, cnt) dealt out to nw workers without a rush on one counter: the
+// worker of rank w takes chunk [w*k, w*k + k) first, with no atomic; the
+// chunks past nw*k are grabbed k at a time from the head (which starts at 0).
+// A grab-only scheme sends, when every warp of the grid starts a short phase at
+// once, one atomic per warp to the same word; the L2 serialises them, and a
+// warp that comes back for more work waits behind all of them.  `first` is the
+// caller's flag, true before the first call.  Called by the whole warp.
+__device__ __forceinline__ int warp_deal(unsigned *head, int cnt, unsigned k, int w, int nw, bool &first)
+{
+    if (first) {
+        first = false;
+        const long long b = (long long)w * k;
+        if (b < cnt) return (int)b;
+    }
+    const long long base = (long long)nw * k;
+    if (base >= cnt) return cnt;
+    long long b = 0;
+    if ((threadIdx.x & 31) == 0) {
+        const unsigned cur = *(volatile unsigned *)head;
+        b = base + (base + cur >= cnt ? cur : atomicAdd(head, k));
+    }
+    b = __shfl_sync(0xffffffffu, b, 0);
+    return b < cnt ? (int)b : cnt;
+}
+
+// Rank of this warp for warp_deal among the warps of nctas CTAs (all of the
+// grid, or CTA 0 alone): consecutive ranks sit in different CTAs, so a few
+// items spread over many SMs, and the ranks are rotated by `skip`, so that the
+// warps that took the first `skip` items of an earlier list come last in this
+// one.
+__device__ __forceinline__ int warp_rank(int nctas, int skip)
+{
+    const int nw = nctas * (int)(blockDim.x >> 5);
+    const int r = (int)(threadIdx.x >> 5) * nctas + vb();
+    const int s = skip % nw;
+    return r >= s ? r - s : r - s + nw;
+}
+
 // Per-CTA accumulators, flushed to global memory once per phase.
 struct Sh {
     long long sink_e, src_e;
@@ -141,6 +179,7 @@ struct Sh {
     long long bcast_e;
     int ok;
     unsigned gen;
+    MfDesc d;         // the hook's snapshot, copied after every barrier
 };
 
 enum Hook {
@@ -171,21 +210,21 @@ __device__ __forceinline__ void decide_iteration(const MfParams &P, MfCtrl *c, u
                                                  const unsigned (&wl)[MF_NBIN + 1], long long iters,
                                                  unsigned long long t_start, int qstamp, int fstamp)
 {
-    c->round = 0;
+    c->d.round = 0;
     for (int i = 0; i < 8; ++i) c->aux_tail.w[i] = 0;
-    c->qstamp = qstamp + 1;
-    c->fstamp = fstamp + 1;
+    c->d.qstamp = qstamp + 1;
+    c->d.fstamp = fstamp + 1;
     const int active = (int)wl[MF_NBIN];
     c->t_dis0 = now;
-    for (int b = 0; b < MF_NBIN; ++b) c->wl_n[b] = (int)wl[b];
+    for (int b = 0; b < MF_NBIN; ++b) c->d.wl_n[b] = (int)wl[b];
     c->head0.w[0] = c->head1.w[0] = c->head2.w[0] = c->head3.w[0] = 0;
     if (iters < MF_ACTIVE_HIST) c->active_hist[iters] = active;
     if (iters == 0) c->active_first = active;
     c->active_total = rd(c->active_total) + active;
     if (active == 0) {
-        c->status = MF_ST_CONVERGED;
+        c->d.status = MF_ST_CONVERGED;
     } else if (iters >= P.max_iters || now - t_start > P.time_limit_ns) {
-        c->status = MF_ST_CAP;
+        c->d.status = MF_ST_CAP;
     } else {
         c->iters = iters + 1;
     }
@@ -203,20 +242,20 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
         // deferred long rows, or (none deferred) the level is complete
         const unsigned dn = rd(c->defer_tail.w[0]);
         if (dn == 0) {
-            c->bu_split = 0;
+            c->d.bu_split = 0;
             hook = H_BFS_NEXT;
         } else {
-            c->bu_split = 1;
-            c->defer_n = (int)dn;
+            c->d.bu_split = 1;
+            c->d.defer_n = (int)dn;
             c->defer_tail.w[0] = 0;
             c->head1.w[0] = 0;
         }
     }
-    const unsigned long long t_phase = rd(c->t_phase);
+    const unsigned long long t_phase = rd(c->d.t_phase);
     const int trace_n = hook == H_START ? 0 : rd(c->trace_n);
     const long long barriers = hook == H_START ? 0 : rd(c->barriers);
     const unsigned bfs_tail = rd(c->bfs_tail.w[0]), item_tail = rd(c->hub_tail.w[0]);
-    const int lvl_hi = rd(c->lvl_hi), hub_hi = rd(c->hub_hi), level = rd(c->level), hub_lo_old = rd(c->hub_lo);
+    const int lvl_hi = rd(c->d.lvl_hi), hub_hi = rd(c->d.hub_hi), level = rd(c->d.level), hub_lo_old = rd(c->d.hub_lo);
     const long long iters = rd(c->iters), bfs_levels = rd(c->bfs_levels);
     const unsigned long long t_start = rd(c->t_start);
     unsigned wl[MF_NBIN + 1], misc[4];
@@ -224,19 +263,19 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
     for (int i = 0; i < 4; ++i) misc[i] = rd(c->misc.w[i]);
     unsigned aux[MF_NBIN + 2];
     for (int i = 0; i < MF_NBIN + 2; ++i) aux[i] = rd(c->aux_tail.w[i]);
-    const int sel = rd(c->wl_sel), round = rd(c->round), qstamp = rd(c->qstamp), fstamp = rd(c->fstamp);
+    const int sel = rd(c->d.wl_sel), round = rd(c->d.round), qstamp = rd(c->d.qstamp), fstamp = rd(c->d.fstamp);
     const long long rounds_total = rd(c->rounds_total);
     const long long slots_all = rd(c->slots_bfs) + rd(c->slots_dis) + rd(c->slots_fix);
     const unsigned long long fin_max = rd(c->fin_max), fin_sum = rd(c->fin_sum);
-    const int bu_prev = rd(c->bu_mode);
+    const int bu_prev = rd(c->d.bu_mode);
     int wl_prev[MF_NBIN];
-    for (int b = 0; b < MF_NBIN; ++b) wl_prev[b] = rd(c->wl_n[b]);
+    for (int b = 0; b < MF_NBIN; ++b) wl_prev[b] = rd(c->d.wl_n[b]);
     int tinfo = 0;
     unsigned err = rd(c->err.w[0]);
     const unsigned long long dt = now - t_phase;
     const bool want_wl = P.data_driven && !(P.mode & MF_M_BFS_ONLY);
 
-    c->t_phase = now;
+    c->d.t_phase = now;
     c->barriers = barriers + 1;
     c->t_exit = now;
     c->trace_n = trace_n + 1;
@@ -244,7 +283,7 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
     case H_START:
         err = 0;
         c->err.w[0] = 0;
-        c->status = MF_ST_RUNNING;
+        c->d.status = MF_ST_RUNNING;
         c->iters = 0;
         c->value = 0;
         c->pushes = c->relabels = c->steep = c->bfs_levels = c->active_total = c->active_first = 0;
@@ -257,18 +296,18 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
         c->bfs_tail.w[0] = 0;
         c->hub_tail.w[0] = 0;
         c->defer_tail.w[0] = 0;
-        c->bu_split = 0;
+        c->d.bu_split = 0;
         c->head0.w[0] = c->head1.w[0] = c->head2.w[0] = c->head3.w[0] = 0;
         for (int i = 0; i < 8; ++i) c->wl_tail.w[i] = 0;
         for (int i = 0; i < 8; ++i) c->misc.w[i] = 0;
         for (int i = 0; i < MF_ACTIVE_HIST; ++i) c->active_hist[i] = 0;
         for (int i = 0; i < 8; ++i) c->aux_tail.w[i] = 0;
         for (int i = 0; i < 8; ++i) c->bfs_acc.w[i] = 0;
-        c->bu_mode = 0;
-        c->bfs_cta_mode = 0;
-        c->need_total = 1;
-        c->round = 0;
-        c->dis_more = 0;
+        c->d.bu_mode = 0;
+        c->d.bfs_cta_mode = 0;
+        c->d.need_total = 1;
+        c->d.round = 0;
+        c->d.dis_more = 0;
         c->rounds_total = 0;
         c->t_start = now;
         break;
@@ -282,11 +321,11 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
         break;
     case H_APPLY_LOCATED:
         c->ns_apply = rd(c->ns_apply) + dt;
-        c->ins_n = (int)misc[0];
+        c->d.ins_n = (int)misc[0];
         break;
     case H_APPLY_DELTA:
         c->ns_apply = rd(c->ns_apply) + dt;
-        c->touch_n = (int)misc[1];
+        c->d.touch_n = (int)misc[1];
         break;
     case H_NONE:
         c->ns_apply = rd(c->ns_apply) + dt;
@@ -299,8 +338,8 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
         // the used-slot total (acc word 2) only changes with insertions, which
         // come before the first BFS: later iterations keep it
         for (int i = 0; i < 4; ++i) c->bfs_acc.w[i] = 0;
-        c->need_total = rd(c->bfs_acc.w[4]) == 0 && rd(c->bfs_acc.w[5]) == 0;
-        c->bu_mode = 0;
+        c->d.need_total = rd(c->bfs_acc.w[4]) == 0 && rd(c->bfs_acc.w[5]) == 0;
+        c->d.bu_mode = 0;
         for (int i = 0; i < 8; ++i) c->wl_tail.w[i] = 0;
         c->head0.w[0] = c->head1.w[0] = c->head2.w[0] = c->head3.w[0] = 0;
         break;
@@ -311,13 +350,13 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
         const int lo = first ? 0 : lvl_hi, hlo = first ? 0 : hub_hi;
         const bool done = lo == (int)bfs_tail && hlo == (int)item_tail;
         if (!first && !done) c->bfs_levels = bfs_levels + 1;
-        c->level = first ? 0 : level + 1;
-        c->lvl_lo = lo;
-        c->lvl_hi = (int)bfs_tail;
-        c->hub_lo = hlo;
-        c->hub_hi = (int)item_tail;
+        c->d.level = first ? 0 : level + 1;
+        c->d.lvl_lo = lo;
+        c->d.lvl_hi = (int)bfs_tail;
+        c->d.hub_lo = hlo;
+        c->d.hub_hi = (int)item_tail;
         c->head0.w[0] = c->head1.w[0] = 0;
-        c->bfs_done = done;
+        c->d.bfs_done = done;
         {
             // direction of the coming level (Beamer's test): bottom-up once the
             // frontier's slots exceed 1/alpha of the unexplored slots, back to
@@ -328,15 +367,15 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
             const long long vis = (first ? 0 : rd(c->vis_slots)) + fr;
             tinfo = ((first ? 0 : bu_prev) << 30) | ((first ? 0 : min(hub_hi - hub_lo_old, 1023)) << 20) |
                     (int)min(cnt, (long long)((1 << 20) - 1));
-            int bu = first ? 0 : rd(c->bu_mode);
+            int bu = first ? 0 : rd(c->d.bu_mode);
             if (P.bu_alpha <= 0) bu = 0;
             else if (!bu && fr * P.bu_alpha > tot - vis) bu = 1;
             else if (bu && cnt * P.bu_beta < (long long)P.g.n) bu = 0;
-            c->bu_mode = bu;
+            c->d.bu_mode = bu;
             c->vis_slots = vis;
             // a small top-down frontier is expanded by CTA 0 alone: a level of a
             // few hundred slots costs a grid barrier otherwise
-            c->bfs_cta_mode = (!done && !bu && P.tail_slots > 0 && fr <= P.tail_slots && cnt <= P.tail_slots) ? 1 : 0;
+            c->d.bfs_cta_mode = (!done && !bu && P.tail_slots > 0 && fr <= P.tail_slots && cnt <= P.tail_slots) ? 1 : 0;
             c->bfs_acc.w[0] = c->bfs_acc.w[1] = c->bfs_acc.w[2] = c->bfs_acc.w[3] = 0;   // per level; [2] stays
         }
         if (done && want_wl) decide_iteration(P, c, now, wl, iters, t_start, qstamp, fstamp);
@@ -369,18 +408,18 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
             }
         }
         if (more) {
-            c->wl_sel = sel ^ 1;
+            c->d.wl_sel = sel ^ 1;
             for (int b = 0; b < MF_NBIN; ++b) {
-                c->wl_n[b] = (int)aux[b];
+                c->d.wl_n[b] = (int)aux[b];
                 c->aux_tail.w[b] = 0;
             }
-            c->round = round + 1;
-            c->qstamp = qstamp + 1;
-            c->dis_more = 1;
+            c->d.round = round + 1;
+            c->d.qstamp = qstamp + 1;
+            c->d.dis_more = 1;
         } else {
-            c->dis_more = 0;
-            c->fix_n[0] = (int)aux[MF_NBIN];
-            c->fix_n[1] = (int)aux[MF_NBIN + 1];
+            c->d.dis_more = 0;
+            c->d.fix_n[0] = (int)aux[MF_NBIN];
+            c->d.fix_n[1] = (int)aux[MF_NBIN + 1];
         }
         break;
     }
@@ -391,7 +430,7 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
         break;
     case H_BU_SPLIT:
         c->ns_bfs = rd(c->ns_bfs) + dt;
-        tinfo = (1 << 30) | (int)min((long long)rd(c->defer_n), (long long)((1 << 20) - 1));
+        tinfo = (1 << 30) | (int)min((long long)rd(c->d.defer_n), (long long)((1 << 20) - 1));
         break;
     }
     if (trace_n < MF_TRACE) {
@@ -404,13 +443,28 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
     }
     c->fin_max = 0;
     c->fin_sum = 0;
-    if (err != 0) c->status = MF_ST_ERROR;
+    if (err != 0) c->d.status = MF_ST_ERROR;
+}
+
+// The hook's snapshot into shared memory: eight 16-byte loads through L2,
+// issued together (one round trip).  Called by one thread, after the barrier's
+// acquire (or by the thread that ran the hook itself).
+__device__ __forceinline__ void load_desc(const MfCtrl *c, Sh &sh)
+{
+    constexpr int kN = (int)(sizeof(MfDesc) / sizeof(int4));
+    const int4 *src = reinterpret_cast<const int4 *>(&c->d);
+    int4 v[kN];
+#pragma unroll
+    for (int i = 0; i < kN; ++i) v[i] = __ldcg(src + i);
+    int4 *dst = reinterpret_cast<int4 *>(&sh.d);
+#pragma unroll
+    for (int i = 0; i < kN; ++i) dst[i] = v[i];
 }
 
 // Grid-wide barrier with a hook.  Returns false if this CTA gave up waiting
 // (the caller must return from the kernel at once).  Each CTA counts the
 // barrier generations it has passed (sh.gen), so arriving needs no read.
-__device__ bool grid_sync(const MfParams &P, int hook, Sh &sh)
+__device__ __noinline__ bool grid_sync(const MfParams &P, int hook, Sh &sh)
 {
     MfCtrl *c = P.ctrl;
     __syncthreads();
@@ -445,14 +499,12 @@ __device__ bool grid_sync(const MfParams &P, int hook, Sh &sh)
         __threadfence();
         sh.gen = gen + 1u;
         sh.ok = ok;
+        if (ok) load_desc(c, sh);
     }
     __syncthreads();
     return sh.ok != 0;
 }
 
-// Hook-written control fields are read through L2 (never a stale L1 line).
-__device__ __forceinline__ int vrd(const int *p) { return *(volatile const int *)p; }
-__device__ __forceinline__ int status_of(const MfParams &P) { return vrd(&P.ctrl->status); }
 
 // Flush per-CTA accumulators (excess of sink/source and counters).
 __device__ void flush_acc(const MfParams &P, Sh &sh, int phase)
@@ -462,7 +514,7 @@ __device__ void flush_acc(const MfParams &P, Sh &sh, int phase)
         MfCtrl *c = P.ctrl;
         {
             // when this CTA finished the phase, after the release of the barrier that opened it
-            const unsigned long long t0 = rd(c->t_phase), now = gtimer();
+            const unsigned long long t0 = sh.d.t_phase, now = gtimer();
             const unsigned long long d = now > t0 ? now - t0 : 0;
             atomicMax(&c->fin_max, d);
             atomicAdd(&c->fin_sum, d);
@@ -814,10 +866,10 @@ __device__ __noinline__ void phase_apply_locate(const MfParams &P, Sh &sh)
     if (probes) atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)probes);
 }
 
-__device__ __noinline__ void phase_apply_check(const MfParams &P)
+__device__ __noinline__ void phase_apply_check(const MfParams &P, const Sh &sh)
 {
     MfCtrl *ctl = P.ctrl;
-    const int nins = vrd(&ctl->ins_n);
+    const int nins = sh.d.ins_n;
     for (long long k = spread_thread(); k < nins; k += (long long)vn() * blockDim.x) {
         unsigned long long pk = __ldcg(P.sc.pkey + __ldcg(P.sc.ins_list + k));
         int a = (int)(pk >> 32), b = (int)(pk & 0xffffffffu);
@@ -847,8 +899,7 @@ __device__ __forceinline__ int batch_cap_of(const MfParams &P, int a, int b)
 // atomics does not matter.
 __device__ __noinline__ void phase_apply_change(const MfParams &P, Sh &sh)
 {
-    MfCtrl *ctl = P.ctrl;
-    const int nins = vrd(&ctl->ins_n);
+    const int nins = sh.d.ins_n;
     long long applied = 0, clamped = 0;
     for (long long k = spread_thread(); k < nins; k += (long long)vn() * blockDim.x) {
         int pp = __ldcg(P.sc.ins_list + k);
@@ -1063,7 +1114,7 @@ __device__ __noinline__ void phase_bfs_init(const MfParams &P, Sh &sh)
     const int n = P.g.n;
     const bool deficit_roots = (P.mode & MF_M_NO_DEFICIT_ROOTS) == 0;
     const bool pull = P.pull != 0;
-    const bool need_total = vrd(&P.ctrl->need_total) != 0;
+    const bool need_total = sh.d.need_total != 0;
     long long total = 0;
     const int lane = threadIdx.x & 31;
     const long long gs = (long long)vn() * blockDim.x;
@@ -1143,14 +1194,18 @@ constexpr int kBR = 4;
 __device__ __noinline__ void phase_bfs_level(const MfParams &P, Sh &sh)
 {
     MfCtrl *ctl = P.ctrl;
-    const int L = vrd(&ctl->level);
-    const int sel = vrd(&ctl->wl_sel);
+    const int L = sh.d.level;
+    const int sel = sh.d.wl_sel;
     const int lane = threadIdx.x & 31;
     long long slots = 0;
+    const int nctas = sh.d.bfs_cta_mode ? 1 : vn();      // CTA 0 alone runs the small levels
+    const int nwarps = nctas * (int)(blockDim.x >> 5);
     // chunks of long rows: one warp per item (at most MF_BFS_CHUNK slots)
-    const int ilo = vrd(&ctl->hub_lo), icnt = vrd(&ctl->hub_hi) - ilo;
+    const int ilo = sh.d.hub_lo, icnt = sh.d.hub_hi - ilo;
+    bool first = true;
+    const int rank_i = warp_rank(nctas, 0);
     for (;;) {
-        const int i = warp_grab(&ctl->head1.w[0], icnt, 1u);
+        const int i = warp_deal(&ctl->head1.w[0], icnt, 1u, rank_i, nwarps, first);
         if (i >= icnt) break;
         const int2 it = __ldcg(P.sc.bitem + ilo + i);
         if (lane == 0) slots += it.y;
@@ -1170,11 +1225,12 @@ __device__ __noinline__ void phase_bfs_level(const MfParams &P, Sh &sh)
     // rows together (each lane finds the vertex that owns its slot); a small
     // frontier is dealt out fewer vertices per warp, so that its rows spread
     // over many warps instead of queueing in one
-    const int lo = vrd(&ctl->lvl_lo), cnt = vrd(&ctl->lvl_hi) - lo;
-    const int nwarps = (vrd(&ctl->bfs_cta_mode) ? 1 : vn()) * (int)(blockDim.x >> 5);
+    const int lo = sh.d.lvl_lo, cnt = sh.d.lvl_hi - lo;
     const int take = max(1, min(32, cnt / max(1, nwarps)));
+    first = true;
+    const int rank_f = warp_rank(nctas, icnt);
     for (;;) {
-        const int b = warp_grab(&ctl->head0.w[0], cnt, (unsigned)take);
+        const int b = warp_deal(&ctl->head0.w[0], cnt, (unsigned)take, rank_f, nwarps, first);
         if (b >= cnt) break;
         int idx = b + lane;
         int u = (lane < take && idx < cnt) ? __ldcg(P.sc.border + lo + idx) : -1;
@@ -1225,8 +1281,8 @@ __device__ __noinline__ void phase_bfs_bottom_up(const MfParams &P, Sh &sh)
 {
     MfCtrl *ctl = P.ctrl;
     const int n = P.g.n;
-    const int L = vrd(&ctl->level);
-    const int sel = vrd(&ctl->wl_sel);
+    const int L = sh.d.level;
+    const int sel = sh.d.wl_sel;
     const bool pull = P.pull != 0;
     const int skip = pull ? P.sink : P.source;
     const bool with_wl = P.data_driven && !(P.mode & MF_M_BFS_ONLY);
@@ -1344,16 +1400,19 @@ __device__ __noinline__ void phase_bfs_bottom_up_long(const MfParams &P, Sh &sh)
 {
     MfCtrl *ctl = P.ctrl;
     const int n = P.g.n;
-    const int L = vrd(&ctl->level);
-    const int sel = vrd(&ctl->wl_sel);
+    const int L = sh.d.level;
+    const int sel = sh.d.wl_sel;
     const bool pull = P.pull != 0;
     const bool with_wl = P.data_driven && !(P.mode & MF_M_BFS_ONLY);
     const int lane = threadIdx.x & 31;
-    const int cnt = vrd(&ctl->defer_n);
+    const int cnt = sh.d.defer_n;
     constexpr int kR = MF_BU_CHUNK / 32;
     long long slots = 0;
+    const int nwarps = vn() * (int)(blockDim.x >> 5);
+    const int rank = warp_rank(vn(), 0);
+    bool first = true;
     for (;;) {
-        const int i = warp_grab(&ctl->head1.w[0], cnt, 1u);
+        const int i = warp_deal(&ctl->head1.w[0], cnt, 1u, rank, nwarps, first);
         if (i >= cnt) break;
         const int2 it = __ldcg(P.sc.bdefer + i);
         const int v = it.x;
@@ -1396,7 +1455,7 @@ __device__ __noinline__ void phase_bfs_bottom_up_long(const MfParams &P, Sh &sh)
 __device__ __noinline__ void phase_worklist(const MfParams &P, Sh &sh)
 {
     MfCtrl *ctl = P.ctrl;
-    const int sel = vrd(&ctl->wl_sel);
+    const int sel = sh.d.wl_sel;
     const int n = P.g.n;
     const int lane = threadIdx.x & 31;
     const long long gs = (long long)vn() * blockDim.x;
@@ -2250,19 +2309,19 @@ __device__ __noinline__ void phase_discharge(const MfParams &P, Sh &sh)
 {
     MfCtrl *ctl = P.ctrl;
     const int lane = threadIdx.x & 31;
-    const int sel = vrd(&ctl->wl_sel);
+    const int sel = sh.d.wl_sel;
     DisCtx dc;
     dc.nsel = sel ^ 1;
-    dc.qstamp = vrd(&ctl->qstamp);
-    dc.fstamp = vrd(&ctl->fstamp);
+    dc.qstamp = sh.d.qstamp;
+    dc.fstamp = sh.d.fstamp;
     // queue the vertices that become active for a next round if one may follow
     // (adaptive rounds: the hook decides after this round)
-    dc.queue = vrd(&ctl->round) + 1 < (P.rounds > 0 ? P.rounds : MF_MAX_ROUNDS);
+    dc.queue = sh.d.round + 1 < (P.rounds > 0 ? P.rounds : MF_MAX_ROUNDS);
     const int *wl0 = P.sc.wl[sel][0], *wl1 = P.sc.wl[sel][1], *wl2 = P.sc.wl[sel][2], *wl3 = P.sc.wl[sel][3];
     int *stage = P.stage_slots > 0 ? mf_stage : nullptr;
     const unsigned long long t_a = gtimer();
     // the longest rows: one CTA each
-    const int nh = vrd(&ctl->wl_n[3]);
+    const int nh = sh.d.wl_n[3];
     for (;;) {
         if (threadIdx.x == 0) {
             unsigned cur = *(volatile unsigned *)&ctl->head2.w[0];
@@ -2285,7 +2344,7 @@ __device__ __noinline__ void phase_discharge(const MfParams &P, Sh &sh)
         const GroupTeam T;
         const int gcap = P.stage_slots / (MF_BLOCK / (32 * MF_GROUP_WARPS));
         int *gstage = stage != nullptr ? stage + T.g * gcap : nullptr;
-        const int ng = vrd(&ctl->wl_n[2]);
+        const int ng = sh.d.wl_n[2];
         for (;;) {
             if (T.tid == 0) {
                 unsigned cur = *(volatile unsigned *)&ctl->head3.w[0];
@@ -2305,11 +2364,15 @@ __device__ __noinline__ void phase_discharge(const MfParams &P, Sh &sh)
     }
     const unsigned long long t_b = gtimer();
     if (lane == 0) atomicAdd((unsigned long long *)&sh.dis_cta_ns, t_b - t_a);
-    // mid-degree rows: one warp each (the CTA's snapshot buffer is free again:
-    // every thread has left the loop above, so each warp takes a slice)
-    const int nm = vrd(&ctl->wl_n[1]);
-    const int wcap = min(MF_WARP_STAGE, P.stage_slots / MF_WARPS);
-    int *wstage = stage != nullptr && wcap > 0 ? stage + (threadIdx.x >> 5) * wcap : nullptr;
+    // mid-degree rows: one warp each, on a slice of its own group's quarter of
+    // the snapshot buffer (free once the group has left the loop above, while
+    // the other groups may still be on their rows)
+    const int nm = sh.d.wl_n[1];
+    const int gq = P.stage_slots / (MF_BLOCK / (32 * MF_GROUP_WARPS));
+    const int wcap = min(MF_WARP_STAGE, gq / MF_GROUP_WARPS);
+    const int wid = (int)(threadIdx.x >> 5);
+    int *wstage = stage != nullptr && wcap > 0
+                      ? stage + (wid / MF_GROUP_WARPS) * gq + (wid % MF_GROUP_WARPS) * wcap : nullptr;
     for (;;) {
         const int i = warp_grab(&ctl->head1.w[0], nm, 1u);
         if (i >= nm) break;
@@ -2322,7 +2385,7 @@ __device__ __noinline__ void phase_discharge(const MfParams &P, Sh &sh)
     }
     const unsigned long long t_c = gtimer();
     // small rows: one thread each, 32 per grab
-    const int ns = vrd(&ctl->wl_n[0]);
+    const int ns = sh.d.wl_n[0];
     for (;;) {
         const int b = warp_grab(&ctl->head0.w[0], ns, 32u);
         if (b >= ns) break;
@@ -2401,7 +2464,7 @@ __device__ __noinline__ void phase_fix(const MfParams &P, Sh &sh)
     const int lane = threadIdx.x & 31;
     long long slots = 0, verts = 0;
     // rows above hub_deg: one CTA each
-    const int nh = vrd(&ctl->fix_n[1]);
+    const int nh = sh.d.fix_n[1];
     for (;;) {
         if (threadIdx.x == 0) {
             unsigned cur = *(volatile unsigned *)&ctl->head2.w[0];
@@ -2419,7 +2482,7 @@ __device__ __noinline__ void phase_fix(const MfParams &P, Sh &sh)
         if (threadIdx.x == 0) { slots += d; ++verts; }
     }
     // the others: one warp each
-    const int nw = vrd(&ctl->fix_n[0]);
+    const int nw = sh.d.fix_n[0];
     for (;;) {
         const int i = warp_grab(&ctl->head1.w[0], nw, 1u);
         if (i >= nw) break;
@@ -2492,16 +2555,16 @@ __device__ __noinline__ bool solve_instance(const MfParams &P, Sh &sh)
     if (P.mode & MF_M_APPLY) {
         phase_apply_validate(P);
         if (!grid_sync(P, H_APPLY_VALID, sh)) return false;
-        if (status_of(P) != MF_ST_RUNNING) {
+        if (sh.d.status != MF_ST_RUNNING) {
             phase_apply_cleanup(P, false);
             return grid_sync(P, H_FINAL, sh);
         }
         phase_apply_locate(P, sh);
         flush_acc(P, sh, 4);
         if (!grid_sync(P, H_APPLY_LOCATED, sh)) return false;
-        phase_apply_check(P);
+        phase_apply_check(P, sh);
         if (!grid_sync(P, H_APPLY_CHECKED, sh)) return false;
-        if (status_of(P) != MF_ST_RUNNING) {
+        if (sh.d.status != MF_ST_RUNNING) {
             // a row overflow keeps the rows' demand for the rebuild that follows;
             // a refused batch (pair sum) leaves nothing behind
             phase_apply_cleanup(P, *(volatile unsigned *)&P.ctrl->err.w[0] == MF_E_OVERFLOW);
@@ -2517,7 +2580,7 @@ __device__ __noinline__ bool solve_instance(const MfParams &P, Sh &sh)
         // straight on to the loop: this barrier opens its first iteration
         if (!(P.mode & MF_M_CUT) && (P.mode & (MF_M_SOLVE | MF_M_BFS_ONLY))) {
             if (!grid_sync(P, H_ITER, sh)) return false;
-            if (status_of(P) != MF_ST_RUNNING) return true;
+            if (sh.d.status != MF_ST_RUNNING) return true;
             goto loop;
         }
         if (!grid_sync(P, H_NONE, sh)) return false;
@@ -2528,7 +2591,7 @@ __device__ __noinline__ bool solve_instance(const MfParams &P, Sh &sh)
             flush_acc(P, sh, 4);
             if (!grid_sync(P, H_NONE, sh)) return false;
         }
-        if (status_of(P) != MF_ST_RUNNING) return true;
+        if (sh.d.status != MF_ST_RUNNING) return true;
     }
     if (!(P.mode & (MF_M_SOLVE | MF_M_BFS_ONLY))) return true;
 
@@ -2539,8 +2602,8 @@ loop:
         phase_bfs_init(P, sh);
         flush_acc(P, sh, 0);               // the roots' label counters feed the first level's direction
         if (!grid_sync(P, H_BFS_START, sh)) return false;
-        while (!vrd(&P.ctrl->bfs_done)) {
-            if (vrd(&P.ctrl->bfs_cta_mode)) {
+        while (!sh.d.bfs_done) {
+            if (sh.d.bfs_cta_mode) {
                 // small levels: CTA 0 alone, its own thread 0 running the level
                 // hook; the other CTAs wait at the next grid barrier
                 if (vb() == 0) {
@@ -2548,18 +2611,21 @@ loop:
                     do {
                         phase_bfs_level(P, sh);
                         flush_acc(P, sh, 0);
-                        if (threadIdx.x == 0) run_hook(P, H_BFS_NEXT);
+                        if (threadIdx.x == 0) {
+                            run_hook(P, H_BFS_NEXT);
+                            load_desc(P.ctrl, sh);
+                        }
                         __syncthreads();
-                    } while (++run < MF_TAIL_RUN && !vrd(&P.ctrl->bfs_done) && vrd(&P.ctrl->bfs_cta_mode));
+                    } while (++run < MF_TAIL_RUN && !sh.d.bfs_done && sh.d.bfs_cta_mode);
                 }
                 if (!grid_sync(P, H_BFS_JOIN, sh)) return false;
                 continue;
             }
-            if (vrd(&P.ctrl->bu_mode)) {
+            if (sh.d.bu_mode) {
                 phase_bfs_bottom_up(P, sh);
                 flush_acc(P, sh, 0);
                 if (!grid_sync(P, H_BU_SPLIT, sh)) return false;     // ends the level if nothing was deferred
-                if (vrd(&P.ctrl->bu_split)) {
+                if (sh.d.bu_split) {
                     phase_bfs_bottom_up_long(P, sh);
                     flush_acc(P, sh, 0);
                     if (!grid_sync(P, H_BFS_NEXT, sh)) return false;
@@ -2576,14 +2642,14 @@ loop:
             phase_worklist(P, sh);
             if (!grid_sync(P, H_WL, sh)) return false;
         }
-        if (status_of(P) != MF_ST_RUNNING) break;
+        if (sh.d.status != MF_ST_RUNNING) break;
         // discharge rounds, then remove-invalid-edges
         do {
             if (P.pull) phase_discharge<true>(P, sh);
             else phase_discharge<false>(P, sh);
             flush_acc(P, sh, 1);
             if (!grid_sync(P, H_DIS, sh)) return false;
-        } while (vrd(&P.ctrl->dis_more));
+        } while (sh.d.dis_more);
         if (P.fix_steep) {
             if (P.pull) phase_fix<true>(P, sh);
             else phase_fix<false>(P, sh);
@@ -2591,7 +2657,7 @@ loop:
         }
         if (!grid_sync(P, H_ITER, sh)) return false;
     }
-    if (status_of(P) == MF_ST_ERROR) return true;
+    if (sh.d.status == MF_ST_ERROR) return true;
     if (!(P.mode & MF_M_NO_VALUE)) phase_value(P);
     return grid_sync(P, H_FINAL, sh);
 }
