@@ -433,8 +433,32 @@ def run_configs(S, es_main, hbm):
              "shifting 8 px per batch (131,072 updates)")
     G.close()
     out["batched64"] = batched_summary()
+    out["serving"] = serving_summary()
     out["wall_s"] = time.perf_counter() - t0
     return out
+
+
+SERVING_SMALL = ["--workload", "serving:18,18,19,19,20", "--steps", "60", "--warmup", "1", "--budget-gb", "1.5"]
+
+
+def serving_summary():
+    """A small serving run (five R-MAT graphs of scales 18-20 under a 1.5 GB budget, 60 Poisson
+    requests) in a child process of this script; the full one is --workload serving."""
+    import subprocess
+    cmd = [sys.executable, os.path.abspath(__file__)] + SERVING_SMALL
+    t0 = time.perf_counter()
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT)
+    except subprocess.TimeoutExpired:
+        return {"error": "timed out after 600 s", "command": " ".join(SERVING_SMALL)}
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    if r.returncode != 0 or not lines:
+        return {"error": f"exit {r.returncode}: {r.stderr.strip().splitlines()[-1:]}", "command": " ".join(SERVING_SMALL)}
+    d = json.loads(lines[-1])
+    return {"command": "bench.py " + " ".join(SERVING_SMALL), "workload": d["config"]["workload"],
+            "updates_per_s": d["value"], "latency_ms": d["latency_ms"], "states_gb": d["config"]["states_gb"],
+            "budget_gb": d["config"]["budget_gb"], "evictions": d["serving"].get("evictions"),
+            "flow_check": d["flow_check"], "gpu_launches": d["gpu_launches"], "wall_s": time.perf_counter() - t0}
 
 
 def batched_summary():

@@ -245,9 +245,11 @@ int maxflow_sched_actions(int32_t *mode, int32_t *rounds, int32_t *cycles, int32
 /* The 16 scheduler features of a batch for this context (host array of 16
  * floats): batch size and fraction of the graph, graph size and degree, the
  * fractions of updates touching s, touching t and deleting, the mean new
- * capacity over the graph's mean, the last solve's iterations, time, first
- * active count and BFS levels, the initial static solve's iterations and time,
- * and a constant 1.  Reads the batch only (no change to the state).  Sec. 6.1
+ * capacity over the graph's mean, the last incremental solve's iterations,
+ * time, first active count and BFS levels (the initial solve's until the first
+ * update; a static re-solve leaves them), the initial static solve's
+ * iterations and time, and a constant 1.  Reads the batch only (no change to
+ * the state).  Sec. 6.1
  * ties the choice of KERNEL_CYCLES to the graph, which these features describe.
  * MAXFLOW_ERR_INVALID for NULL c or out, MAXFLOW_ERR_STATE while evicted,
  * MAXFLOW_ERR_CUDA. */
@@ -471,7 +473,8 @@ int maxflow_stats(maxflow_ctx *c, maxflow_stats_t *out);
 /* Timeline of the last solve kernel: for each grid barrier (at most `cap`),
  * the phase boundary it closed and its time in microseconds after kernel
  * entry.  Boundary ids: 0 start, 1 prologue step, 2 batch validated,
- * 3 batch located, 4 room checked, 5 capacities changed, 6 iteration start,
+ * 3 batch located (and the rows' room for new pairs checked), 4 unused,
+ * 5 capacities changed, 6 iteration start,
  * 7 BFS roots set, 8 BFS level done, 9 worklist built, 10 discharge done,
  * 11 end, 12 first pass of a bottom-up BFS level done (its long rows follow),
  * 13 the grid meets again after BFS levels that the first CTA ran alone.

@@ -71,6 +71,11 @@ struct maxflow_ctx {
     float mean_cap = 0.f;         // mean capacity of the initial edges (scheduler feature)
     double init_ms = 0;           // static solve at init (scheduler feature)
     int64_t init_iters = 0;
+    // the last incremental solve (scheduler features): a static re-solve leaves
+    // them as they were, so what the features describe does not depend on
+    // which kind of action ran last
+    int64_t inc_iters = 0, inc_active_first = 0, inc_levels = 0;
+    double inc_ms = 0;
     float *feat = nullptr;        // [MF_FEATURES] device
     float *sched_y = nullptr;     // [64] device
     // eviction: the state parked in host memory while the device memory is released
@@ -317,6 +322,16 @@ void choose_grid(maxflow_ctx *c)
     c->st.grid_blocks = c->grid;
     c->st.block_threads = MF_BLOCK;
     c->st.blocks_per_sm = c->per_sm;
+}
+
+// The statistics of the solve that just ended become the scheduler's view of
+// the last incremental solve.
+void note_incremental(maxflow_ctx *c)
+{
+    c->inc_iters = c->st.iterations;
+    c->inc_active_first = c->st.active_first;
+    c->inc_levels = c->st.bfs_levels;
+    c->inc_ms = c->st.ms_last;
 }
 
 void fill_stats(maxflow_ctx *c, const MfCtrl &h, float ms)
@@ -786,6 +801,7 @@ int maxflow_init(maxflow_ctx **out, const maxflow_graph *g, int32_t s, int32_t t
         rc = run_solve(c, p);
         c->init_ms = c->st.ms_last;
         c->init_iters = c->st.iterations;
+        note_incremental(c);
     }
     if (rc == MAXFLOW_OK) {
         c->feat = dalloc_n<float>(c, MF_FEATURES);
@@ -806,7 +822,9 @@ int maxflow_update(maxflow_ctx *c, const maxflow_batch *b)
     if (!c) return MAXFLOW_ERR_STATE;
     DeviceGuard dg(c->device);
     if (!dg.ok) return MAXFLOW_ERR_CUDA;
-    return do_batch(c, b, MF_M_APPLY | MF_M_SOLVE);
+    const int rc = do_batch(c, b, MF_M_APPLY | MF_M_SOLVE);
+    if (rc == MAXFLOW_OK) note_incremental(c);
+    return rc;
 }
 
 int maxflow_apply(maxflow_ctx *c, const maxflow_batch *b)
@@ -972,12 +990,12 @@ int stage_and_features(maxflow_ctx *c, const maxflow_batch *b, maxflow_batch *de
     f.t = c->t;
     f.m = c->st.m_edges;
     f.mean_cap = c->mean_cap;
-    f.host[0] = lg((double)c->st.iterations) / 8.f;
-    f.host[1] = lg(c->st.ms_last * 1000.0) / 16.f;
-    f.host[2] = lg((double)c->st.active_first) / 20.f;
+    f.host[0] = lg((double)c->inc_iters) / 8.f;
+    f.host[1] = lg(c->inc_ms * 1000.0) / 16.f;
+    f.host[2] = lg((double)c->inc_active_first) / 20.f;
     f.host[3] = lg((double)c->init_iters) / 8.f;
     f.host[4] = lg(c->init_ms * 1000.0) / 16.f;
-    f.host[5] = lg((double)c->st.bfs_levels) / 12.f;
+    f.host[5] = lg((double)c->inc_levels) / 12.f;
     return counted(mf_features(f, c->feat, (void *)c->stream), 1);
 }
 
@@ -993,6 +1011,7 @@ int run_action(maxflow_ctx *c, const maxflow_batch *dev_batch, int a)
     int rc;
     if (A.mode == 0) {
         rc = do_batch(c, dev_batch, MF_M_APPLY | MF_M_SOLVE);
+        if (rc == MAXFLOW_OK) note_incremental(c);
     } else {
         rc = do_batch(c, dev_batch, MF_M_APPLY | MF_M_SKIP_SOURCE_SAT);
         double ms = c->acc_ms;
@@ -1602,6 +1621,10 @@ int maxflow_clone(maxflow_ctx *src, maxflow_ctx **out)
     c->mean_cap = src->mean_cap;
     c->init_ms = src->init_ms;
     c->init_iters = src->init_iters;
+    c->inc_iters = src->inc_iters;
+    c->inc_active_first = src->inc_active_first;
+    c->inc_levels = src->inc_levels;
+    c->inc_ms = src->inc_ms;
     const int32_t n = c->n;
     const int64_t S = src->g.slot_cap;
     int rc = rc_cuda(cudaEventCreate(&c->ev0));

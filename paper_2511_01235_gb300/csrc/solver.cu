@@ -187,7 +187,7 @@ enum Hook {
     H_NONE,
     H_APPLY_VALID,
     H_APPLY_LOCATED,
-    H_APPLY_CHECKED,
+    H_APPLY_CHECKED,      // unused (the room check runs inside the locate phase); keeps the trace ids
     H_APPLY_DELTA,
     H_ITER,
     H_BFS_START,
@@ -228,6 +228,21 @@ __device__ __forceinline__ void decide_iteration(const MfParams &P, MfCtrl *c, u
     } else {
         c->iters = iters + 1;
     }
+}
+
+// Hook work that opens an iteration of the loop (its BFS comes next).
+__device__ __forceinline__ void begin_iteration(MfCtrl *c, unsigned long long now)
+{
+    c->t_bfs0 = now;
+    c->bfs_tail.w[0] = 0;
+    c->hub_tail.w[0] = 0;
+    // the used-slot total (acc word 2) only changes with insertions, which
+    // come before the first BFS: later iterations keep it
+    for (int i = 0; i < 4; ++i) c->bfs_acc.w[i] = 0;
+    c->d.need_total = rd(c->bfs_acc.w[4]) == 0 && rd(c->bfs_acc.w[5]) == 0;
+    c->d.bu_mode = 0;
+    for (int i = 0; i < 8; ++i) c->wl_tail.w[i] = 0;
+    c->head0.w[0] = c->head1.w[0] = c->head2.w[0] = c->head3.w[0] = 0;
 }
 
 // Executed by the one thread that completes a grid barrier, while every
@@ -312,16 +327,15 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
         c->t_start = now;
         break;
     case H_APPLY_VALID:
-    case H_APPLY_CHECKED:
         c->ns_apply = rd(c->ns_apply) + dt;
-        if (hook == H_APPLY_CHECKED && misc[2] != 0 && err == 0) {
-            err = MF_E_OVERFLOW;
-            c->err.w[0] = err;
-        }
         break;
     case H_APPLY_LOCATED:
         c->ns_apply = rd(c->ns_apply) + dt;
         c->d.ins_n = (int)misc[0];
+        if (misc[2] != 0 && err == 0) {      // a row has no room for its new pairs
+            err = MF_E_OVERFLOW;
+            c->err.w[0] = err;
+        }
         break;
     case H_APPLY_DELTA:
         c->ns_apply = rd(c->ns_apply) + dt;
@@ -332,16 +346,7 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
         break;
     case H_ITER:
         c->ns_fix = rd(c->ns_fix) + dt;
-        c->t_bfs0 = now;
-        c->bfs_tail.w[0] = 0;
-        c->hub_tail.w[0] = 0;
-        // the used-slot total (acc word 2) only changes with insertions, which
-        // come before the first BFS: later iterations keep it
-        for (int i = 0; i < 4; ++i) c->bfs_acc.w[i] = 0;
-        c->d.need_total = rd(c->bfs_acc.w[4]) == 0 && rd(c->bfs_acc.w[5]) == 0;
-        c->d.bu_mode = 0;
-        for (int i = 0; i < 8; ++i) c->wl_tail.w[i] = 0;
-        c->head0.w[0] = c->head1.w[0] = c->head2.w[0] = c->head3.w[0] = 0;
+        begin_iteration(c, now);
         break;
     case H_BFS_START:
     case H_BFS_NEXT: {
@@ -420,6 +425,9 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
             c->d.dis_more = 0;
             c->d.fix_n[0] = (int)aux[MF_NBIN];
             c->d.fix_n[1] = (int)aux[MF_NBIN + 1];
+            // without Alg. 3 the next iteration's BFS follows at once: this
+            // barrier opens it
+            if (!P.fix_steep) begin_iteration(c, now);
         }
         break;
     }
@@ -851,9 +859,14 @@ __device__ __noinline__ void phase_apply_locate(const MfParams &P, Sh &sh)
                 for (unsigned probe = 0; probe <= mask; ++probe) {
                     unsigned long long prev = atomicCAS(P.sc.pkey + pp, kEmpty, pk);
                     if (prev == kEmpty) {
+                        // the room check: the increment that reaches a row's final
+                        // demand sees it, so a row short of spare slots is flagged
                         fresh = true;
-                        atomicAdd(P.sc.ins_need + a, 1);
-                        atomicAdd(P.sc.ins_need + b, 1);
+                        const int na = atomicAdd(P.sc.ins_need + a, 1) + 1;
+                        const int nb = atomicAdd(P.sc.ins_need + b, 1) + 1;
+                        if (na > P.g.off[a + 1] - P.g.off[a] - ldg_cg(P.g.deg + a) ||
+                            nb > P.g.off[b + 1] - P.g.off[b] - ldg_cg(P.g.deg + b))
+                            atomicExch(&ctl->misc.w[2], 1u);
                         break;
                     }
                     if (prev == pk) break;
@@ -864,19 +877,6 @@ __device__ __noinline__ void phase_apply_locate(const MfParams &P, Sh &sh)
         warp_append(&ctl->misc.w[0], P.sc.ins_list, fresh, (int)pp);   // each new pair once
     }
     if (probes) atomicAdd((unsigned long long *)&sh.slots, (unsigned long long)probes);
-}
-
-__device__ __noinline__ void phase_apply_check(const MfParams &P, const Sh &sh)
-{
-    MfCtrl *ctl = P.ctrl;
-    const int nins = sh.d.ins_n;
-    for (long long k = spread_thread(); k < nins; k += (long long)vn() * blockDim.x) {
-        unsigned long long pk = __ldcg(P.sc.pkey + __ldcg(P.sc.ins_list + k));
-        int a = (int)(pk >> 32), b = (int)(pk & 0xffffffffu);
-        int room_a = P.g.off[a + 1] - P.g.off[a] - ldg_cg(P.g.deg + a);
-        int room_b = P.g.off[b + 1] - P.g.off[b] - ldg_cg(P.g.deg + b);
-        if (ldg_cg(P.sc.ins_need + a) > room_a || ldg_cg(P.sc.ins_need + b) > room_b) atomicExch(&ctl->misc.w[2], 1u);
-    }
 }
 
 // Winning new capacity of the directed pair (a, b) in the batch, or -1 if the
@@ -2562,8 +2562,6 @@ __device__ __noinline__ bool solve_instance(const MfParams &P, Sh &sh)
         phase_apply_locate(P, sh);
         flush_acc(P, sh, 4);
         if (!grid_sync(P, H_APPLY_LOCATED, sh)) return false;
-        phase_apply_check(P, sh);
-        if (!grid_sync(P, H_APPLY_CHECKED, sh)) return false;
         if (sh.d.status != MF_ST_RUNNING) {
             // a row overflow keeps the rows' demand for the rebuild that follows;
             // a refused batch (pair sum) leaves nothing behind
@@ -2654,8 +2652,8 @@ loop:
             if (P.pull) phase_fix<true>(P, sh);
             else phase_fix<false>(P, sh);
             flush_acc(P, sh, 2);
+            if (!grid_sync(P, H_ITER, sh)) return false;
         }
-        if (!grid_sync(P, H_ITER, sh)) return false;
     }
     if (sh.d.status == MF_ST_ERROR) return true;
     if (!(P.mode & MF_M_NO_VALUE)) phase_value(P);
