@@ -465,28 +465,33 @@ int rebuild_device(maxflow_ctx *c)
 {
     const int32_t n = c->n;
     MfParams p = base_params(c);
-    long long *noff = dalloc_n<long long>(c, (int64_t)n + 1);
+    long long *noff = dalloc_n<long long>(c, mf_rebuild_scratch(n));
     if (!noff) return MAXFLOW_ERR_OOM;
     int rc =
-        counted(mf_rebuild_capacity(p, (void *)c->stream, c->opt.slack_factor, c->opt.slack_min, noff), 2);
+        counted(mf_rebuild_capacity(p, (void *)c->stream, c->opt.slack_factor, c->opt.slack_min, noff), 4);
     long long total = 0;
     if (rc == MAXFLOW_OK)
         rc = rc_cuda(cudaMemcpyAsync(&total, noff + n, sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
     if (rc == MAXFLOW_OK) rc = rc_cuda(cudaStreamSynchronize(c->stream));
     if (rc == MAXFLOW_OK && total >= (long long)INT32_MAX - 1) rc = MAXFLOW_ERR_TOO_LARGE;
     int32_t *off = nullptr, *dst = nullptr, *cf = nullptr, *cap = nullptr, *rev = nullptr, *pcap = nullptr;
+    int2 *items = nullptr;     // pieces of the long rows for the copy; the last entry holds their count
     if (rc == MAXFLOW_OK) {
+        items = dalloc_n<int2>(c, mf_move_items(total) + 1);
         off = dalloc_n<int32_t>(c, (int64_t)n + 1);
         dst = dalloc_n<int32_t>(c, total);
         cf = dalloc_n<int32_t>(c, total);
         cap = dalloc_n<int32_t>(c, total);
         rev = dalloc_n<int32_t>(c, total);
         pcap = dalloc_n<int32_t>(c, total);
-        if (!off || !dst || !cf || !cap || !rev || !pcap) rc = MAXFLOW_ERR_OOM;
+        if (!items || !off || !dst || !cf || !cap || !rev || !pcap) rc = MAXFLOW_ERR_OOM;
     }
     if (rc == MAXFLOW_OK)
-        rc = counted(mf_rebuild_move(p, (void *)c->stream, noff, off, dst, cf, cap, rev, pcap, total), 2);
+        rc = counted(mf_rebuild_move(p, (void *)c->stream, noff, off, dst, cf, cap, rev, pcap, total, items,
+                                     reinterpret_cast<unsigned *>(items + mf_move_items(total))),
+                     3);
     if (rc == MAXFLOW_OK) rc = rc_cuda(cudaStreamSynchronize(c->stream));
+    dfree(c, items);
     if (rc != MAXFLOW_OK) {
         int32_t *tmp[] = {off, dst, cf, cap, rev, pcap};
         for (int32_t *q : tmp) dfree(c, q);

@@ -259,10 +259,18 @@ int mf_launch_aux(int which, const MfParams &p, void *stream, long long *dev_out
 #define MF_AUX_NEGATE_E 10        // e = -e
 #define MF_AUX_PCAP 11            // pcap = cap + cap[rev] on every used slot (after a restore)
 
-// device-side rebuild (rows grow, flows and excesses stay in place)
+// device-side rebuild (rows grow, flows and excesses stay in place); noff holds
+// n + 1 row starts followed by the scan's tile totals: mf_rebuild_scratch(n) int64
+#define MF_SCAN_TILE 4096
+inline long long mf_scan_tiles(long long n) { return n / MF_SCAN_TILE + 1; }
+inline long long mf_rebuild_scratch(long long n) { return n + 1 + mf_scan_tiles(n) + 1; }
 int mf_rebuild_capacity(const MfParams &p, void *stream, float slack_factor, int slack_min, long long *noff);
+// the copy: rows of more than MF_MOVE_PIECE new slots are moved in pieces of that
+// size, listed in items[] (mf_move_items(slot_cap) entries) with their count in *nitems
+#define MF_MOVE_PIECE 1024
+inline long long mf_move_items(long long slot_cap) { return 2 * (slot_cap / MF_MOVE_PIECE) + 64; }
 int mf_rebuild_move(const MfParams &p, void *stream, const long long *noff, int32_t *off, int32_t *dst, int32_t *cf,
-                    int32_t *cap, int32_t *rev, int32_t *pcap, long long slot_cap);
+                    int32_t *cap, int32_t *rev, int32_t *pcap, long long slot_cap, int2 *items, unsigned *nitems);
 
 // scheduler features of a batch (16 floats)
 #define MF_FEATURES 16

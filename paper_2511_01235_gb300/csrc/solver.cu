@@ -2900,68 +2900,195 @@ __global__ void k_row_capacity(MfParams P, float slack_factor, int slack_min, lo
     }
 }
 
-// Exclusive scan of n int64 values in place, by one CTA of 1024 threads
-// (rows are few enough that a single pass over them is a few microseconds
-// per million vertices); writes the total to out[n].
-__global__ void __launch_bounds__(1024) k_scan_single(long long *a, long long n)
+// Exclusive scan of n int64 values in place, in three passes: every CTA scans
+// its tile of MF_SCAN_TILE values and leaves the tile's total in part[]; one CTA
+// scans the totals; every CTA adds its tile's offset.  a[n] gets the total.
+constexpr int kScanThreads = 1024, kScanPer = MF_SCAN_TILE / kScanThreads;
+
+__device__ __forceinline__ long long block_exclusive_scan(long long x, long long *warp_sums, long long &total)
 {
-    __shared__ long long part[1024];
-    const long long per = (n + blockDim.x - 1) / blockDim.x;
-    const long long lo = threadIdx.x * per, hi = lo + per < n ? lo + per : n;
-    long long sum = 0;
-    for (long long i = lo; i < hi; ++i) sum += a[i];
-    part[threadIdx.x] = sum;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    long long incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_sums[w] = incl;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        long long run = 0;
-        for (int k = 0; k < (int)blockDim.x; ++k) {
-            long long v = part[k];
-            part[k] = run;
-            run += v;
+    if (w == 0) {
+        const long long ws = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0;
+        long long wi = ws;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
         }
-        a[n] = run;
+        warp_sums[lane] = wi - ws;              // exclusive offset of each warp
+        if (lane == 31) warp_sums[32] = wi;     // the CTA's total
     }
     __syncthreads();
-    long long run = part[threadIdx.x];
-    for (long long i = lo; i < hi; ++i) {
-        long long v = a[i];
-        a[i] = run;
-        run += v;
+    total = warp_sums[32];
+    const long long r = warp_sums[w] + incl - x;
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(long long *a, long long n, long long *part)
+{
+    __shared__ long long ws[33];
+    const long long base = (long long)blockIdx.x * MF_SCAN_TILE + (long long)threadIdx.x * kScanPer;
+    long long v[kScanPer], sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+        v[k] = base + k < n ? a[base + k] : 0;
+        sum += v[k];
     }
+    long long total;
+    long long run = block_exclusive_scan(sum, ws, total);
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+        if (base + k < n) a[base + k] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = total;
+}
+
+// One CTA: exclusive scan of the tile totals (any count), total into part[nt].
+__global__ void __launch_bounds__(kScanThreads) k_scan_parts(long long *part, long long nt)
+{
+    __shared__ long long ws[33];
+    long long carry = 0;
+    for (long long b0 = 0; b0 < nt; b0 += blockDim.x) {
+        const long long i = b0 + threadIdx.x;
+        const long long x = i < nt ? part[i] : 0;
+        long long total;
+        const long long r = block_exclusive_scan(x, ws, total);
+        if (i < nt) part[i] = carry + r;
+        carry += total;
+    }
+    if (threadIdx.x == 0) part[nt] = carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_add(long long *a, long long n, const long long *part,
+                                                            long long nt)
+{
+    const long long off = part[blockIdx.x];
+    const long long base = (long long)blockIdx.x * MF_SCAN_TILE;
+    for (int k = threadIdx.x; k < MF_SCAN_TILE; k += blockDim.x)
+        if (base + k < n) a[base + k] += off;
+    if (blockIdx.x == 0 && threadIdx.x == 0) a[n] = part[nt];
 }
 
 struct MoveOut {
     const long long *noff;   // new row starts (int64, n + 1)
     int32_t *off, *dst, *cf, *cap, *rev, *pcap;   // new arrays
     long long slot_cap;
+    int2 *items;             // pieces of the long rows: (row, first slot of the piece)
+    unsigned *nitems;        // their number
 };
 
-// Copy every row to its new place; the reverse index of slot (u, v) moves with
-// row v: new_rev = new_off[v] + (rev - old_off[v]).
+// New slot y of row u at position j: the old slot's values when j < d (the
+// reverse index of slot (u, v) moves with row v: new_rev = new_off[v] + (rev -
+// old_off[v])), else an empty slot (dst = u, no capacity, rev = itself).
+__device__ __forceinline__ void move_slot(const MfParams &P, const MoveOut &M, int u, int o0, int d, int j,
+                                          long long y)
+{
+    if (j < d) {
+        const int x = o0 + j;
+        const int v = __ldcs(P.g.dst + x);
+        const int cf = __ldcs(P.g.cf + x), cap = __ldcs(P.g.cap + x), pc = __ldcs(P.g.pcap + x);
+        const int rv = __ldcs(P.g.rev + x);
+        const int rn = (int)__ldg(M.noff + v) + (rv - __ldg(P.g.off + v));
+        M.dst[y] = v;
+        M.cf[y] = cf;
+        M.cap[y] = cap;
+        M.pcap[y] = pc;
+        M.rev[y] = rn;
+    } else {
+        M.dst[y] = u;
+        M.cf[y] = 0;
+        M.cap[y] = 0;
+        M.pcap[y] = 0;
+        M.rev[y] = (int)y;
+    }
+}
+
+// Rows longer than MF_MOVE_PIECE slots (new size) become pieces of that many
+// slots, listed once the new sizes are known.
+__global__ void k_move_items(MfParams P, MoveOut M)
+{
+    for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < P.g.n;
+         u += (long long)gridDim.x * blockDim.x) {
+        const long long S = M.noff[u + 1] - M.noff[u];
+        if (S <= MF_MOVE_PIECE) continue;
+        const int np = (int)((S + MF_MOVE_PIECE - 1) / MF_MOVE_PIECE);
+        const unsigned at = atomicAdd(M.nitems, (unsigned)np);
+        for (int k = 0; k < np; ++k) M.items[at + k] = make_int2((int)u, k * MF_MOVE_PIECE);
+    }
+}
+
+// Copy every row to its new place.  Warps take either 32 consecutive rows, of
+// which they copy the rows of at most MF_MOVE_PIECE slots as one concatenated
+// range (each lane finds the row that owns its slot), or one piece of a long
+// row; each lane moves kMv slots per step, so a step keeps kMv independent
+// load chains in flight per lane.
+constexpr int kMv = 4;
 __global__ void k_move_rows(MfParams P, MoveOut M)
 {
     const int lane = threadIdx.x & 31;
-    for (long long u = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < P.g.n;
-         u += ((long long)gridDim.x * blockDim.x) >> 5) {
-        const int o0 = P.g.off[u], d = P.g.deg[u];
-        const int n0 = (int)M.noff[u], n1 = (int)M.noff[u + 1];
-        if (lane == 0) M.off[u] = n0;
-        for (int j = lane; j < n1 - n0; j += 32) {
-            const int y = n0 + j;
-            if (j < d) {
-                const int x = o0 + j;
-                const int v = P.g.dst[x];
-                M.dst[y] = v;
-                M.cf[y] = P.g.cf[x];
-                M.cap[y] = P.g.cap[x];
-                M.pcap[y] = P.g.pcap[x];
-                M.rev[y] = (int)M.noff[v] + (P.g.rev[x] - P.g.off[v]);
-            } else {
-                M.dst[y] = (int)u;
-                M.cf[y] = 0;
-                M.cap[y] = 0;
-                M.pcap[y] = 0;
-                M.rev[y] = y;
+    const long long nblk = ((long long)P.g.n + 31) >> 5;
+    const long long nw = nblk + *(volatile unsigned *)M.nitems;
+    for (long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw;
+         w += ((long long)gridDim.x * blockDim.x) >> 5) {
+        if (w >= nblk) {
+            const int2 it = M.items[w - nblk];
+            const int u = it.x;
+            const long long n0 = M.noff[u];
+            const int S = (int)(M.noff[u + 1] - n0);
+            const int o0 = P.g.off[u], d = P.g.deg[u];
+            const int end = it.y + MF_MOVE_PIECE < S ? it.y + MF_MOVE_PIECE : S;
+            for (int jb = it.y; jb < end; jb += 32 * kMv) {
+#pragma unroll
+                for (int r = 0; r < kMv; ++r) {
+                    const int j = jb + r * 32 + lane;
+                    if (j < end) move_slot(P, M, u, o0, d, j, n0 + j);
+                }
+            }
+            continue;
+        }
+        const int u0 = (int)(w << 5);
+        const int u = u0 + lane;
+        const bool ok = u < P.g.n;
+        const long long n0 = ok ? M.noff[u] : 0;
+        const int S = ok ? (int)(M.noff[u + 1] - n0) : 0;
+        const int Ss = S <= MF_MOVE_PIECE ? S : 0;      // long rows go by pieces
+        const int o0 = ok ? P.g.off[u] : 0, d = ok ? P.g.deg[u] : 0;
+        if (ok) M.off[u] = (int)n0;
+        int incl = Ss;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int excl = incl - Ss;
+        const int T = __shfl_sync(0xffffffffu, incl, 31);
+        for (int kb = 0; kb < T; kb += 32 * kMv) {        // the same trip count in every lane
+#pragma unroll
+            for (int r = 0; r < kMv; ++r) {
+                const int k = kb + r * 32 + lane;
+                int owner = 0;
+#pragma unroll
+                for (int st = 16; st >= 1; st >>= 1) {
+                    const int cand = owner + st;
+                    const int ec = __shfl_sync(0xffffffffu, excl, cand & 31);
+                    if (cand < 32 && ec <= k) owner = cand;
+                }
+                const long long rn0 = __shfl_sync(0xffffffffu, n0, owner);
+                const int ro = __shfl_sync(0xffffffffu, o0, owner);
+                const int rd_ = __shfl_sync(0xffffffffu, d, owner);
+                const int re = __shfl_sync(0xffffffffu, excl, owner);
+                if (k < T) move_slot(P, M, u0 + owner, ro, rd_, k - re, rn0 + (k - re));
             }
         }
     }
@@ -3129,20 +3256,34 @@ int mf_rebuild_capacity(const MfParams &p, void *stream, float slack_factor, int
     if (g < 1) g = 1;
     k_row_capacity<<<g, 256, 0, st>>>(p, slack_factor, slack_min, noff);
     if (cudaGetLastError() != cudaSuccess) return MAXFLOW_ERR_CUDA;
-    k_scan_single<<<1, 1024, 0, st>>>(noff, p.g.n);
+    // the tile totals sit behind the n + 1 row starts (mf_rebuild_scratch)
+    const long long nt = mf_scan_tiles(p.g.n);
+    long long *part = noff + p.g.n + 1;
+    k_scan_tiles<<<(int)nt, kScanThreads, 0, st>>>(noff, p.g.n, part);
+    if (cudaGetLastError() != cudaSuccess) return MAXFLOW_ERR_CUDA;
+    k_scan_parts<<<1, kScanThreads, 0, st>>>(part, nt);
+    if (cudaGetLastError() != cudaSuccess) return MAXFLOW_ERR_CUDA;
+    k_scan_add<<<(int)nt, kScanThreads, 0, st>>>(noff, p.g.n, part, nt);
     return cuda_rc(cudaGetLastError());
 }
 
 int mf_rebuild_move(const MfParams &p, void *stream, const long long *noff, int32_t *off, int32_t *dst, int32_t *cf,
-                    int32_t *cap, int32_t *rev, int32_t *pcap, long long slot_cap)
+                    int32_t *cap, int32_t *rev, int32_t *pcap, long long slot_cap, int2 *items, unsigned *nitems)
 {
     cudaStream_t st = (cudaStream_t)stream;
-    MoveOut M{noff, off, dst, cf, cap, rev, pcap, slot_cap};
-    long long thr = (long long)p.g.n * 32;
-    int g = (int)((thr + 255) / 256);
-    if (g > 65535) g = 65535;
-    if (g < 1) g = 1;
-    k_move_rows<<<g, 256, 0, st>>>(p, M);
+    MoveOut M{noff, off, dst, cf, cap, rev, pcap, slot_cap, items, nitems};
+    if (cudaMemsetAsync(nitems, 0, sizeof(unsigned), st) != cudaSuccess) return MAXFLOW_ERR_CUDA;
+    int gi = (int)((p.g.n + 255) / 256);
+    if (gi > 65535) gi = 65535;
+    if (gi < 1) gi = 1;
+    k_move_items<<<gi, 256, 0, st>>>(p, M);
+    if (cudaGetLastError() != cudaSuccess) return MAXFLOW_ERR_CUDA;
+    // a persistent grid: warps stride over the blocks of 32 rows, then the pieces
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return MAXFLOW_ERR_CUDA;
+    k_move_rows<<<sms * 8, 256, 0, st>>>(p, M);
     if (cudaGetLastError() != cudaSuccess) return MAXFLOW_ERR_CUDA;
     int gv = (int)((p.g.n + 255) / 256);
     if (gv > 65535) gv = 65535;

@@ -105,7 +105,10 @@ def family(name: str, seed: int):
 # ---------------------------------------------------------------------------
 
 def collect(solver: native.Solver, batches, actions=None, log=None):
-    """Features and per-action device time (ms) of every batch, each action on a clone."""
+    """Features and per-action device time (ms) of every batch, each action on a
+    clone.  The state then advances by the batch's fastest action: the states a
+    good schedule meets are those it makes itself, and a static re-solve or a
+    many-round update leaves a different preflow than the default would."""
     if actions is None:
         actions = list(range(len(native.maxflow_sched_actions())))
     A = len(native.maxflow_sched_actions())
@@ -120,7 +123,7 @@ def collect(solver: native.Solver, batches, actions=None, log=None):
             T[i, a] = C.stats()["ms_update"]
             M[i, a] = 1.0
             C.close()
-        solver.run_action(b.u, b.v, b.cap, ACTION_DEFAULT)
+        solver.run_action(b.u, b.v, b.cap, int(np.argmin(np.where(M[i] > 0, T[i], np.inf))))
         if log:
             log(f"  batch {i} B={b.size} best action {int(np.argmin(np.where(M[i] > 0, T[i], np.inf)))} "
                 f"{T[i][M[i] > 0].min():.3f} ms, paper {T[i, ACTION_PAPER]:.3f} ms")
