@@ -297,9 +297,16 @@ int maxflow_update_scheduled(maxflow_ctx *c, const maxflow_batch *b, maxflow_mlp
 
 /* Work split thresholds (by used slots of a vertex's row): the discharge gives
  * rows of at most thread_max_slots one thread, rows of at most warp_max_slots
- * one warp and longer rows a whole CTA (remove-invalid-edges: a warp up to
- * warp_max_slots, then a CTA); the BFS splits rows longer than
- * bfs_item_min_slots into 256-slot work items.  Defaults 8 / 512 / 256. */
+ * one warp, longer rows a 4-warp group up to a quarter of the CTA's snapshot
+ * buffer (about 7.2 K slots) and the longest a whole CTA (remove-invalid-edges:
+ * a warp up to warp_max_slots, then a CTA); the BFS splits rows longer than
+ * bfs_item_min_slots into 256-slot work items.  All three 0: the defaults,
+ * thread_max_slots 8, or 4 on a graph of at most 8 merged directed edges per
+ * vertex (grids, geometric and layered graphs: many short discharge rounds,
+ * where a warp's parallel scan of a short row beats one thread's), then 512
+ * and 256.  Not in the paper (it steers work only).  MAXFLOW_ERR_INVALID for
+ * NULL c, a zero or negative threshold (unless all three are 0) or
+ * warp_max_slots < thread_max_slots. */
 int maxflow_set_tuning(maxflow_ctx *c, int32_t thread_max_slots, int32_t warp_max_slots, int32_t bfs_item_min_slots);
 
 /* Test of the bounded waits (no counterpart in the paper): one BFS-only launch

@@ -16,8 +16,9 @@ from . import native
 GROUP_BLOCKS = (1, 2, 4, 8, 16, 32)
 ROUNDS = (0, 1, 4, 16, 64)            # 0: the adaptive count
 CYCLES = (0, 4, 16)                   # 0: the average-degree heuristic
-SPLITS = ((8, 512, 256), (4, 256, 128), (16, 2048, 1024), (32, 8192, 4096))
-DEFAULT = {"group_blocks": 8, "rounds": 0, "cycles": 0, "split": (8, 512, 256)}
+# (0, 0, 0): each instance's own default split (thread rows of 4 or 8 slots by its average degree)
+SPLITS = ((0, 0, 0), (8, 512, 256), (4, 256, 128), (16, 2048, 1024), (32, 8192, 4096))
+DEFAULT = {"group_blocks": 8, "rounds": 0, "cycles": 0, "split": (0, 0, 0)}
 
 
 def apply_config(solvers, cfg):

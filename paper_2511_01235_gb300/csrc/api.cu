@@ -324,6 +324,21 @@ void choose_grid(maxflow_ctx *c)
     c->st.blocks_per_sm = c->per_sm;
 }
 
+// The default work split: rows of up to 8 slots get a thread, or up to 4 on a
+// sparse graph (at most 8 merged directed edges per vertex: grids, geometric
+// and layered graphs), where the rounds are many and short and a warp's
+// parallel scan of a 5-8 slot row beats one thread's; then warps up to 512
+// slots, 4-warp groups up to a quarter of the snapshot buffer, CTAs above; BFS
+// work items for rows of more than 256 slots.
+void default_split(maxflow_ctx *c)
+{
+    const int64_t m = c->st.m_edges;
+    c->small_deg = m <= (int64_t)MF_SPARSE_DEG * c->n ? MF_SMALL_DEG_SPARSE : MF_SMALL_DEG;
+    c->hub_deg = MF_HUB_DEG;
+    c->bfs_hub = MF_BFS_HUB;
+    c->group_deg = std::max<int32_t>(c->hub_deg, c->stage_slots / (MF_BLOCK / (32 * MF_GROUP_WARPS)));
+}
+
 // The statistics of the solve that just ended become the scheduler's view of
 // the last incremental solve.
 void note_incremental(maxflow_ctx *c)
@@ -798,6 +813,7 @@ int maxflow_init(maxflow_ctx **out, const maxflow_graph *g, int32_t s, int32_t t
     if (rc == MAXFLOW_OK) {
         int64_t m = c->st.m_edges;
         c->kernel_cycles = o.kernel_cycles > 0 ? o.kernel_cycles : (int32_t)std::max<int64_t>(1, (m + c->n - 1) / c->n);
+        default_split(c);
         c->rounds = 0;   // adaptive
         c->st.rounds = c->rounds;
         choose_grid(c);
@@ -1096,11 +1112,17 @@ int maxflow_update_scheduled(maxflow_ctx *c, const maxflow_batch *b, maxflow_mlp
 
 int maxflow_set_tuning(maxflow_ctx *c, int32_t thread_max_slots, int32_t warp_max_slots, int32_t bfs_item_min_slots)
 {
-    if (!c || thread_max_slots < 1 || warp_max_slots < thread_max_slots || bfs_item_min_slots < 1)
+    if (!c) return MAXFLOW_ERR_INVALID;
+    if (thread_max_slots == 0 && warp_max_slots == 0 && bfs_item_min_slots == 0) {
+        default_split(c);
+        return MAXFLOW_OK;
+    }
+    if (thread_max_slots < 1 || warp_max_slots < thread_max_slots || bfs_item_min_slots < 1)
         return MAXFLOW_ERR_INVALID;
     c->small_deg = thread_max_slots;
     c->hub_deg = warp_max_slots;
     c->bfs_hub = bfs_item_min_slots;
+    c->group_deg = std::max<int32_t>(c->hub_deg, c->stage_slots / (MF_BLOCK / (32 * MF_GROUP_WARPS)));
     return MAXFLOW_OK;
 }
 

@@ -19,6 +19,8 @@
 #define MF_BLOCK 512          // threads per CTA of the persistent kernel
 #define MF_WARPS (MF_BLOCK / 32)
 #define MF_SMALL_DEG 8        // discharge: rows up to this many slots get one thread
+#define MF_SMALL_DEG_SPARSE 4 // ... on a graph of at most MF_SPARSE_DEG merged directed edges per vertex
+#define MF_SPARSE_DEG 8
 #define MF_HUB_DEG 512        // discharge: rows above this many slots get a 4-warp group (or a whole CTA)
 #define MF_NBIN 4             // discharge row kinds: thread, warp, 4-warp group, CTA
 #define MF_GROUP_WARPS 4      // warps of a group; a group keeps rows up to a quarter of the snapshot

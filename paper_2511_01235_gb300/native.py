@@ -764,7 +764,8 @@ class Solver:
         """Direction-optimising BFS thresholds (alpha = 0: top-down only)."""
         _check(load().maxflow_set_bfs_switch(self.h, int(alpha), int(beta)), "maxflow_set_bfs_switch")
 
-    def set_tuning(self, thread_max_slots=8, warp_max_slots=512, bfs_item_min_slots=256):
+    def set_tuning(self, thread_max_slots=0, warp_max_slots=0, bfs_item_min_slots=0):
+        """Work split thresholds; all 0 (the default) restores the library's defaults."""
         maxflow_set_tuning(self.h, thread_max_slots, warp_max_slots, bfs_item_min_slots)
 
     def features(self, u, v, c) -> np.ndarray:

@@ -38,7 +38,7 @@ def _install(monkeypatch, cost):
 
 
 def test_separable_cost_reaches_the_optimum(monkeypatch):
-    want = {"group_blocks": 4, "rounds": 16, "cycles": 4, "split": (16, 2048, 1024)}
+    want = {"group_blocks": 4, "rounds": 16, "cycles": 4, "split": autotune.SPLITS[2]}
 
     def cost(gb, r, k, sp):
         return (10.0 + abs(autotune.GROUP_BLOCKS.index(gb) - 2) + abs(autotune.ROUNDS.index(r) - 3)
@@ -48,12 +48,12 @@ def test_separable_cost_reaches_the_optimum(monkeypatch):
     S = [FakeSolver() for _ in range(3)]
     best, best_ms, trials = autotune.tune(S, passes=3, reps=1)
     assert best == want and best_ms == 10.0
-    assert all((s.rounds, s.cycles, s.split) == (16, 4, (16, 2048, 1024)) for s in S)
+    assert all((s.rounds, s.cycles, s.split) == (16, 4, autotune.SPLITS[2]) for s in S)
     assert min(ms for _, ms in trials) == best_ms
 
 
 def test_never_worse_than_the_default_and_stops_without_gain(monkeypatch):
-    calls = _install(monkeypatch, lambda gb, r, k, sp: 5.0 if (gb, r, k, sp) == (8, 0, 0, (8, 512, 256)) else 7.0)
+    calls = _install(monkeypatch, lambda gb, r, k, sp: 5.0 if (gb, r, k, sp) == (8, 0, 0, (0, 0, 0)) else 7.0)
     S = [FakeSolver()]
     best, best_ms, trials = autotune.tune(S, passes=4, reps=2)
     assert best == autotune.DEFAULT and best_ms == 5.0
