@@ -111,9 +111,11 @@ struct MfCtrl {
     MfLine head1;
     MfLine head2;
     MfLine head3;
-    MfLine wl_tail;       // w[0..3]: worklist append positions per bin, w[4]: active vertices
+    // each counter that many warps bump at once on a line of its own: returning
+    // atomics on one line are served one after another
+    MfLine wl_tail[MF_NBIN + 1];   // [0..3]: worklist append positions per bin, [4]: active vertices
     MfLine misc;          // w[0]: insert list tail, w[1]: touched tail, w[2]: overflow flag
-    MfLine aux_tail;      // w[0..3]: next-round worklist tails, w[4]/w[5]: remove-invalid lists (warp / CTA)
+    MfLine aux_tail[MF_NBIN + 2];  // [0..3]: next-round worklist tails, [4]/[5]: remove-invalid lists (warp / CTA)
     MfLine defer_tail;    // w[0]: bottom-up work items of long rows deferred to the level's second pass
     MfLine bfs_acc;       // 64-bit words: [0] slots of the vertices labelled in this level, [1] their number,
                           // [2] used slots of the whole graph (summed by the BFS initialisation)

@@ -211,7 +211,7 @@ __device__ __forceinline__ void decide_iteration(const MfParams &P, MfCtrl *c, u
                                                  unsigned long long t_start, int qstamp, int fstamp)
 {
     c->d.round = 0;
-    for (int i = 0; i < 8; ++i) c->aux_tail.w[i] = 0;
+    for (int i = 0; i < MF_NBIN + 2; ++i) c->aux_tail[i].w[0] = 0;
     c->d.qstamp = qstamp + 1;
     c->d.fstamp = fstamp + 1;
     const int active = (int)wl[MF_NBIN];
@@ -241,7 +241,7 @@ __device__ __forceinline__ void begin_iteration(MfCtrl *c, unsigned long long no
     for (int i = 0; i < 4; ++i) c->bfs_acc.w[i] = 0;
     c->d.need_total = rd(c->bfs_acc.w[4]) == 0 && rd(c->bfs_acc.w[5]) == 0;
     c->d.bu_mode = 0;
-    for (int i = 0; i < 8; ++i) c->wl_tail.w[i] = 0;
+    for (int i = 0; i <= MF_NBIN; ++i) c->wl_tail[i].w[0] = 0;
     c->head0.w[0] = c->head1.w[0] = c->head2.w[0] = c->head3.w[0] = 0;
 }
 
@@ -274,10 +274,10 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
     const long long iters = rd(c->iters), bfs_levels = rd(c->bfs_levels);
     const unsigned long long t_start = rd(c->t_start);
     unsigned wl[MF_NBIN + 1], misc[4];
-    for (int i = 0; i <= MF_NBIN; ++i) wl[i] = rd(c->wl_tail.w[i]);
+    for (int i = 0; i <= MF_NBIN; ++i) wl[i] = rd(c->wl_tail[i].w[0]);
     for (int i = 0; i < 4; ++i) misc[i] = rd(c->misc.w[i]);
     unsigned aux[MF_NBIN + 2];
-    for (int i = 0; i < MF_NBIN + 2; ++i) aux[i] = rd(c->aux_tail.w[i]);
+    for (int i = 0; i < MF_NBIN + 2; ++i) aux[i] = rd(c->aux_tail[i].w[0]);
     const int sel = rd(c->d.wl_sel), round = rd(c->d.round), qstamp = rd(c->d.qstamp), fstamp = rd(c->d.fstamp);
     const long long rounds_total = rd(c->rounds_total);
     const long long slots_all = rd(c->slots_bfs) + rd(c->slots_dis) + rd(c->slots_fix);
@@ -313,10 +313,10 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
         c->defer_tail.w[0] = 0;
         c->d.bu_split = 0;
         c->head0.w[0] = c->head1.w[0] = c->head2.w[0] = c->head3.w[0] = 0;
-        for (int i = 0; i < 8; ++i) c->wl_tail.w[i] = 0;
+        for (int i = 0; i <= MF_NBIN; ++i) c->wl_tail[i].w[0] = 0;
         for (int i = 0; i < 8; ++i) c->misc.w[i] = 0;
         for (int i = 0; i < MF_ACTIVE_HIST; ++i) c->active_hist[i] = 0;
-        for (int i = 0; i < 8; ++i) c->aux_tail.w[i] = 0;
+        for (int i = 0; i < MF_NBIN + 2; ++i) c->aux_tail[i].w[0] = 0;
         for (int i = 0; i < 8; ++i) c->bfs_acc.w[i] = 0;
         c->d.bu_mode = 0;
         c->d.bfs_cta_mode = 0;
@@ -416,7 +416,7 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
             c->d.wl_sel = sel ^ 1;
             for (int b = 0; b < MF_NBIN; ++b) {
                 c->d.wl_n[b] = (int)aux[b];
-                c->aux_tail.w[b] = 0;
+                c->aux_tail[b].w[0] = 0;
             }
             c->d.round = round + 1;
             c->d.qstamp = qstamp + 1;
@@ -1001,7 +1001,6 @@ __device__ __noinline__ void phase_resaturate(const MfParams &P, Sh &sh)
 // Backward BFS (Alg. 4 / Alg. 6)
 // ---------------------------------------------------------------------------
 
-
 // Labelled vertices enter the next frontier either as one entry of the
 // regular list (rows of at most bfs_hub slots, expanded warp-cooperatively)
 // or, for longer rows, as ceil(deg / MF_BFS_CHUNK) work items (first slot,
@@ -1011,19 +1010,20 @@ __device__ __noinline__ void phase_resaturate(const MfParams &P, Sh &sh)
 // O1): it is active exactly when this BFS labels it, so no separate pass over
 // all vertices is needed.
 //
-// Each lane brings R candidates; the four lists (regular frontier, three
-// worklist bins) are reserved with one packed warp scan and one round of
-// atomics, so a warp pays one append round trip per R slots.  Called by the
-// whole warp.
+// Each lane brings R candidates; the six lists (regular frontier, four
+// worklist bins, work items) are reserved with one warp scan and one round of
+// atomics issued together, so a warp pays one append round trip per R slots.
+// Called by the whole warp.
 template <int R>
 __device__ __forceinline__ void frontier_push(const MfParams &P, Sh &sh, const bool (&take)[R], const int (&z)[R],
                                               const int (&d)[R], const long long (&ev)[R], bool with_wl, int sel)
 {
     MfCtrl *ctl = P.ctrl;
     const int lane = threadIdx.x & 31;
-    // per-lane counts packed 8 bits each: [0] regular, [1..MF_NBIN] worklist bins
+    // per-lane counts packed 8 bits each: [0] regular, [1..MF_NBIN] worklist
+    // bins; and the work items of this lane's long rows
     unsigned long long packed = 0;
-    bool anybig = false;
+    int nch = 0;
     long long lab_slots = 0;
     int lab_n = 0;
 #pragma unroll
@@ -1031,18 +1031,23 @@ __device__ __forceinline__ void frontier_push(const MfParams &P, Sh &sh, const b
         if (!take[r]) continue;
         lab_slots += d[r];
         ++lab_n;
-        const bool big = d[r] > P.bfs_hub;
-        anybig |= big;
-        if (!big) packed += 1ull;
+        if (d[r] > P.bfs_hub) nch += (d[r] + MF_BFS_CHUNK - 1) / MF_BFS_CHUNK;
+        else packed += 1ull;
         if (with_wl && ev[r] > 0) packed += 1ull << (8 * (row_bin(P, d[r]) + 1));
     }
     unsigned long long incl = packed;
+    int cincl = nch;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+        const int yc = __shfl_up_sync(0xffffffffu, cincl, o);
+        if (lane >= o) {
+            incl += y;
+            cincl += yc;
+        }
     }
     const unsigned long long total = __shfl_sync(0xffffffffu, incl, 31);
+    const int ctot = __shfl_sync(0xffffffffu, cincl, 31);
     const unsigned long long excl = incl - packed;
     // slots and number of the vertices labelled (the BFS direction test reads them)
     lab_slots = warp_sum_ll(lab_slots);
@@ -1051,60 +1056,80 @@ __device__ __forceinline__ void frontier_push(const MfParams &P, Sh &sh, const b
         atomicAdd((unsigned long long *)&sh.lab_slots, (unsigned long long)lab_slots);
         atomicAdd((unsigned long long *)&sh.lab_cnt, (unsigned long long)lab_cnt);
     }
-    if (total != 0) {
-        unsigned base[MF_NBIN + 1];
+    if (total == 0 && ctot == 0) return;
+    static_assert(MF_NBIN == 4, "one reservation per worklist bin below");
+    // One lane reserves room in every list the warp appends to.  The
+    // reservations are independent, so they are issued back to back and the
+    // warp waits for one round trip, not one per list.
+    const unsigned k0 = (unsigned)(total & 0xffull), k1 = (unsigned)((total >> 8) & 0xffull),
+                   k2 = (unsigned)((total >> 16) & 0xffull), k3 = (unsigned)((total >> 24) & 0xffull),
+                   k4 = (unsigned)((total >> 32) & 0xffull);
+    unsigned b0 = 0, b1 = 0, b2 = 0, b3 = 0, b4 = 0, bi = 0;
+    if (lane == 0) {
+        if (k0) b0 = atomicAdd(&ctl->bfs_tail.w[0], k0);
+        if (k1) b1 = atomicAdd(&ctl->wl_tail[0].w[0], k1);
+        if (k2) b2 = atomicAdd(&ctl->wl_tail[1].w[0], k2);
+        if (k3) b3 = atomicAdd(&ctl->wl_tail[2].w[0], k3);
+        if (k4) b4 = atomicAdd(&ctl->wl_tail[3].w[0], k4);
+        if (ctot) bi = atomicAdd(&ctl->hub_tail.w[0], (unsigned)ctot);
+        const unsigned act = k1 + k2 + k3 + k4;
+        if (act) atomicAdd(&ctl->wl_tail[MF_NBIN].w[0], act);
+    }
+    unsigned pos[MF_NBIN + 1];
+    pos[0] = __shfl_sync(0xffffffffu, b0, 0) + (unsigned)(excl & 0xffull);
+    pos[1] = __shfl_sync(0xffffffffu, b1, 0) + (unsigned)((excl >> 8) & 0xffull);
+    pos[2] = __shfl_sync(0xffffffffu, b2, 0) + (unsigned)((excl >> 16) & 0xffull);
+    pos[3] = __shfl_sync(0xffffffffu, b3, 0) + (unsigned)((excl >> 24) & 0xffull);
+    pos[4] = __shfl_sync(0xffffffffu, b4, 0) + (unsigned)((excl >> 32) & 0xffull);
 #pragma unroll
-        for (int b = 0; b <= MF_NBIN; ++b) base[b] = 0;
-        if (lane == 0) {
-            if (total & 0xffull) base[0] = atomicAdd(&ctl->bfs_tail.w[0], (unsigned)(total & 0xffull));
-            unsigned act = 0;
-            for (int b = 0; b < MF_NBIN; ++b) {
-                const unsigned k = (unsigned)((total >> (8 * (b + 1))) & 0xffull);
-                if (k) base[b + 1] = atomicAdd(&ctl->wl_tail.w[b], k);
-                act += k;
-            }
-            if (act) atomicAdd(&ctl->wl_tail.w[MF_NBIN], act);
-        }
-#pragma unroll
-        for (int b = 0; b <= MF_NBIN; ++b) base[b] = __shfl_sync(0xffffffffu, base[b], 0);
-        unsigned pos[MF_NBIN + 1];
-#pragma unroll
-        for (int b = 0; b <= MF_NBIN; ++b) pos[b] = base[b] + (unsigned)((excl >> (8 * b)) & 0xffull);
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            if (!take[r]) continue;
-            if (d[r] <= P.bfs_hub) P.sc.border[pos[0]++] = z[r];
-            if (with_wl && ev[r] > 0) {
-                const int bin = row_bin(P, d[r]);
-                P.sc.wl[sel][bin][pos[bin + 1]++] = z[r];
-            }
+    for (int r = 0; r < R; ++r) {
+        if (!take[r]) continue;
+        if (d[r] <= P.bfs_hub) P.sc.border[pos[0]++] = z[r];
+        if (with_wl && ev[r] > 0) {
+            const int bin = row_bin(P, d[r]);
+            P.sc.wl[sel][bin][pos[bin + 1]++] = z[r];
         }
     }
-    // long rows: ceil(deg / MF_BFS_CHUNK) work items each, reserved for the whole
-    // warp with one scan and one atomic; every lane then writes its own rows' items
-    if (__any_sync(0xffffffffu, anybig)) {
-        int nch = 0;
+    if (ctot == 0) return;
+    // long rows: ceil(deg / MF_BFS_CHUNK) work items each, which any warp can
+    // take.  A hub of 10^5 slots has hundreds of items, so the warp writes all
+    // its rows' items together, 32 at a time (each lane finds the row that owns
+    // its item), instead of each lane walking its own rows' items.
+    int x0[R], nc[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r)
-            if (take[r] && d[r] > P.bfs_hub) nch += (d[r] + MF_BFS_CHUNK - 1) / MF_BFS_CHUNK;
-        int cincl = nch;
+    for (int r = 0; r < R; ++r) {
+        const bool big = take[r] && d[r] > P.bfs_hub;
+        nc[r] = big ? (d[r] + MF_BFS_CHUNK - 1) / MF_BFS_CHUNK : 0;
+        x0[r] = big ? P.g.off[z[r]] : 0;
+    }
+    const unsigned ibase = __shfl_sync(0xffffffffu, bi, 0);
+    const int cexcl = cincl - nch;
+    for (int i0 = 0; i0 < ctot; i0 += 32) {         // the same trip count in every lane
+        const int i = i0 + lane;
+        int owner = 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, cincl, o);
-            if (lane >= o) cincl += y;
+        for (int st = 16; st >= 1; st >>= 1) {
+            const int cand = owner + st;
+            const int ec = __shfl_sync(0xffffffffu, cexcl, cand & 31);
+            if (cand < 32 && ec <= i) owner = cand;
         }
-        const int ctot = __shfl_sync(0xffffffffu, cincl, 31);
-        unsigned at = 0;
-        if (lane == 0) at = atomicAdd(&ctl->hub_tail.w[0], (unsigned)ctot);
-        at = __shfl_sync(0xffffffffu, at, 0) + (unsigned)(cincl - nch);
+        int j = i - __shfl_sync(0xffffffffu, cexcl, owner);
+        int ix = 0, idg = 0, ic = -1;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            if (!take[r] || d[r] <= P.bfs_hub) continue;
-            const int x0 = P.g.off[z[r]];
-            for (int c = 0; c * MF_BFS_CHUNK < d[r]; ++c) {
-                const int len = d[r] - c * MF_BFS_CHUNK;
-                P.sc.bitem[at++] = make_int2(x0 + c * MF_BFS_CHUNK, len < MF_BFS_CHUNK ? len : MF_BFS_CHUNK);
+            const int ncr = __shfl_sync(0xffffffffu, nc[r], owner);
+            const int xr = __shfl_sync(0xffffffffu, x0[r], owner);
+            const int dr = __shfl_sync(0xffffffffu, d[r], owner);
+            if (ic < 0 && j >= 0 && j < ncr) {
+                ic = j;
+                ix = xr;
+                idg = dr;
             }
+            j -= ncr;
+        }
+        if (i < ctot) {
+            const int len = idg - ic * MF_BFS_CHUNK;
+            P.sc.bitem[ibase + (unsigned)i] = make_int2(ix + ic * MF_BFS_CHUNK, len < MF_BFS_CHUNK ? len : MF_BFS_CHUNK);
         }
     }
 }
@@ -1468,9 +1493,9 @@ __device__ __noinline__ void phase_worklist(const MfParams &P, Sh &sh)
         int bin = 0;
         if (listed) bin = row_bin(P, ldg_cg(P.g.deg + v));
         unsigned am = __ballot_sync(0xffffffffu, act);
-        if (lane == 0 && am) atomicAdd(&ctl->wl_tail.w[MF_NBIN], (unsigned)__popc(am));
+        if (lane == 0 && am) atomicAdd(&ctl->wl_tail[MF_NBIN].w[0], (unsigned)__popc(am));
 #pragma unroll
-        for (int b = 0; b < MF_NBIN; ++b) warp_append(&ctl->wl_tail.w[b], P.sc.wl[sel][b], listed && bin == b, v);
+        for (int b = 0; b < MF_NBIN; ++b) warp_append(&ctl->wl_tail[b].w[0], P.sc.wl[sel][b], listed && bin == b, v);
     }
 }
 
@@ -1494,9 +1519,10 @@ struct DisCtx {
 // so a vertex that receives flow while the kernel runs is discharged too).
 __device__ __forceinline__ void enqueue_active(const MfParams &P, int z, const DisCtx &dc)
 {
+    const int dz = ldg_cg(P.g.deg + z);      // in flight together with the stamp exchange
     if (atomicExch(P.sc.vmark + z, dc.qstamp) == dc.qstamp) return;
-    const int bin = row_bin(P, ldg_cg(P.g.deg + z));
-    const unsigned pos = atomicAdd(&P.ctrl->aux_tail.w[bin], 1u);
+    const int bin = row_bin(P, dz);
+    const unsigned pos = atomicAdd(&P.ctrl->aux_tail[bin].w[0], 1u);
     P.sc.wl[dc.nsel][bin][pos] = z;
 }
 
@@ -1518,7 +1544,7 @@ __device__ __forceinline__ void note_relabel(const MfParams &P, int u, const Dis
     if (atomicExch(P.sc.fixmark + u, dc.fstamp) == dc.fstamp) return;
     const int d = ldg_cg(P.g.deg + u);
     const int li = d > P.hub_deg ? 1 : 0;
-    const unsigned pos = atomicAdd(&P.ctrl->aux_tail.w[MF_NBIN + li], 1u);
+    const unsigned pos = atomicAdd(&P.ctrl->aux_tail[MF_NBIN + li].w[0], 1u);
     P.sc.fixl[li][pos] = u;
 }
 
