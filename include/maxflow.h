@@ -484,7 +484,9 @@ int maxflow_stats(maxflow_ctx *c, maxflow_stats_t *out);
  * 5 capacities changed, 6 iteration start,
  * 7 BFS roots set, 8 BFS level done, 9 worklist built, 10 discharge done,
  * 11 end, 12 first pass of a bottom-up BFS level done (its long rows follow),
- * 13 the grid meets again after BFS levels that the first CTA ran alone.
+ * 13 the grid meets again after BFS levels that the first CTA ran alone,
+ * 14 the long rows labelled by the last level are split into work items (a
+ * top-down level follows).
  * *count receives the number of entries written.  Host arrays. */
 int maxflow_trace(maxflow_ctx *c, int32_t *boundary, double *t_us, int32_t cap, int32_t *count);
 

@@ -300,7 +300,9 @@ int alloc_vertex_scratch(maxflow_ctx *c)
     c->sc.fixl[0] = dalloc_n<int32_t>(c, n);
     c->sc.fixl[1] = dalloc_n<int32_t>(c, n);
     c->sc.ins_need = dalloc_n<int32_t>(c, n);
-    if (!c->sc.border || !c->sc.vmark || !c->sc.fixmark || !c->sc.fixl[0] || !c->sc.fixl[1] || !c->sc.ins_need)
+    c->sc.blong = dalloc_n<int32_t>(c, n);
+    if (!c->sc.border || !c->sc.vmark || !c->sc.fixmark || !c->sc.fixl[0] || !c->sc.fixl[1] || !c->sc.ins_need ||
+        !c->sc.blong)
         return MAXFLOW_ERR_OOM;
     for (int q = 0; q < 2; ++q)
         for (int b = 0; b < MF_NBIN; ++b)

@@ -97,7 +97,9 @@ struct alignas(128) MfDesc {
     int need_total;       // the coming BFS initialisation sums the used slots (first BFS of a launch)
     int pad0;
     unsigned long long t_phase;   // when the last barrier's hook ran
-    int pad1[4];
+    int long_lo, long_hi;         // long-row vertices labelled by the last level (blong)
+    int expand;                   // the coming top-down level first splits them into work items
+    int pad1;
 };
 static_assert(sizeof(MfDesc) == 128, "MfDesc is one 128-byte line, copied as 16-byte vectors");
 
@@ -117,6 +119,7 @@ struct MfCtrl {
     MfLine misc;          // w[0]: insert list tail, w[1]: touched tail, w[2]: overflow flag
     MfLine aux_tail[MF_NBIN + 2];  // [0..3]: next-round worklist tails, [4]/[5]: remove-invalid lists (warp / CTA)
     MfLine defer_tail;    // w[0]: bottom-up work items of long rows deferred to the level's second pass
+    MfLine long_tail;     // w[0]: append position of the long-row vertex list (blong)
     MfLine bfs_acc;       // 64-bit words: [0] slots of the vertices labelled in this level, [1] their number,
                           // [2] used slots of the whole graph (summed by the BFS initialisation)
     // ---- (hook) snapshots: what the phases read, copied to shared memory once per barrier ----
@@ -166,6 +169,8 @@ struct MfGraph {
 struct MfScratch {
     int32_t *border;          // [n] BFS order (level segments)
     int2 *bitem;              // [n + slot_cap / MF_BFS_CHUNK + 64] frontier work items (first slot, length)
+    int32_t *blong;           // [n] vertices with rows longer than bfs_hub labelled by the BFS, split into
+                              // work items only if a top-down level follows; nullptr: items at once
     int2 *bdefer;             // [n + slot_cap / MF_BFS_CHUNK + 64] bottom-up deferred chunks (vertex, first slot);
                               // nullptr: bottom-up threads scan whole rows themselves
     int32_t *wl[2][MF_NBIN];  // [n] worklists (two buffers for discharge rounds) per row kind: thread, warp,

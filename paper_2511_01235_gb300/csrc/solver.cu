@@ -197,6 +197,7 @@ enum Hook {
     H_FINAL,
     H_BU_SPLIT,
     H_BFS_JOIN,
+    H_EXPANDED,
 };
 
 __device__ __forceinline__ int rd(const int &x) { return __ldcg(&x); }
@@ -236,6 +237,7 @@ __device__ __forceinline__ void begin_iteration(MfCtrl *c, unsigned long long no
     c->t_bfs0 = now;
     c->bfs_tail.w[0] = 0;
     c->hub_tail.w[0] = 0;
+    c->long_tail.w[0] = 0;
     // the used-slot total (acc word 2) only changes with insertions, which
     // come before the first BFS: later iterations keep it
     for (int i = 0; i < 4; ++i) c->bfs_acc.w[i] = 0;
@@ -310,6 +312,7 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
         c->ns_dis_cta = c->ns_dis_warp = c->ns_dis_thread = 0;
         c->bfs_tail.w[0] = 0;
         c->hub_tail.w[0] = 0;
+        c->long_tail.w[0] = 0;
         c->defer_tail.w[0] = 0;
         c->d.bu_split = 0;
         c->head0.w[0] = c->head1.w[0] = c->head2.w[0] = c->head3.w[0] = 0;
@@ -352,14 +355,17 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
     case H_BFS_NEXT: {
         c->ns_bfs = rd(c->ns_bfs) + dt;
         const bool first = hook == H_BFS_START;
-        const int lo = first ? 0 : lvl_hi, hlo = first ? 0 : hub_hi;
-        const bool done = lo == (int)bfs_tail && hlo == (int)item_tail;
+        const int lo = first ? 0 : lvl_hi, hlo = first ? 0 : hub_hi, llo = first ? 0 : rd(c->d.long_hi);
+        const unsigned long_tail = rd(c->long_tail.w[0]);
+        const bool done = lo == (int)bfs_tail && hlo == (int)item_tail && llo == (int)long_tail;
         if (!first && !done) c->bfs_levels = bfs_levels + 1;
         c->d.level = first ? 0 : level + 1;
         c->d.lvl_lo = lo;
         c->d.lvl_hi = (int)bfs_tail;
         c->d.hub_lo = hlo;
         c->d.hub_hi = (int)item_tail;
+        c->d.long_lo = llo;
+        c->d.long_hi = (int)long_tail;
         c->head0.w[0] = c->head1.w[0] = 0;
         c->d.bfs_done = done;
         {
@@ -378,9 +384,14 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
             else if (bu && cnt * P.bu_beta < (long long)P.g.n) bu = 0;
             c->d.bu_mode = bu;
             c->vis_slots = vis;
+            // a top-down level after one that labelled long rows first splits them
+            // into work items (a bottom-up level never reads them)
+            const int expand = (!done && !bu && (int)long_tail > llo) ? 1 : 0;
+            c->d.expand = expand;
             // a small top-down frontier is expanded by CTA 0 alone: a level of a
             // few hundred slots costs a grid barrier otherwise
-            c->d.bfs_cta_mode = (!done && !bu && P.tail_slots > 0 && fr <= P.tail_slots && cnt <= P.tail_slots) ? 1 : 0;
+            c->d.bfs_cta_mode =
+                (!done && !bu && !expand && P.tail_slots > 0 && fr <= P.tail_slots && cnt <= P.tail_slots) ? 1 : 0;
             c->bfs_acc.w[0] = c->bfs_acc.w[1] = c->bfs_acc.w[2] = c->bfs_acc.w[3] = 0;   // per level; [2] stays
         }
         if (done && want_wl) decide_iteration(P, c, now, wl, iters, t_start, qstamp, fstamp);
@@ -435,6 +446,13 @@ __device__ __noinline__ void run_hook(const MfParams &P, int hook)
         break;
     case H_BFS_JOIN:
         c->ns_bfs = rd(c->ns_bfs) + dt;
+        break;
+    case H_EXPANDED:
+        // the long rows' work items are written: the level takes them with the rest
+        c->ns_bfs = rd(c->ns_bfs) + dt;
+        c->d.hub_hi = (int)item_tail;
+        c->d.expand = 0;
+        c->head0.w[0] = c->head1.w[0] = 0;
         break;
     case H_BU_SPLIT:
         c->ns_bfs = rd(c->ns_bfs) + dt;
@@ -1001,6 +1019,10 @@ __device__ __noinline__ void phase_resaturate(const MfParams &P, Sh &sh)
 // Backward BFS (Alg. 4 / Alg. 6)
 // ---------------------------------------------------------------------------
 
+template <int R>
+__device__ __forceinline__ void write_items(const MfParams &P, const int (&nc)[R], const int (&x0)[R],
+                                            const int (&d)[R], unsigned ibase, int cexcl, int ctot);
+
 // Labelled vertices enter the next frontier either as one entry of the
 // regular list (rows of at most bfs_hub slots, expanded warp-cooperatively)
 // or, for longer rows, as ceil(deg / MF_BFS_CHUNK) work items (first slot,
@@ -1016,12 +1038,17 @@ __device__ __noinline__ void phase_resaturate(const MfParams &P, Sh &sh)
 // Called by the whole warp.
 template <int R>
 __device__ __forceinline__ void frontier_push(const MfParams &P, Sh &sh, const bool (&take)[R], const int (&z)[R],
-                                              const int (&d)[R], const long long (&ev)[R], bool with_wl, int sel)
+                                              const int (&d)[R], const long long (&ev)[R], bool with_wl, int sel,
+                                              bool eager = false)
 {
     MfCtrl *ctl = P.ctrl;
     const int lane = threadIdx.x & 31;
+    // long rows go to the long-row list, to be split into work items only if a
+    // top-down level follows (a bottom-up level never reads them); `eager`
+    // (the roots: the first level is top-down) or no list: items at once
+    const bool lazy = !eager && P.sc.blong != nullptr;
     // per-lane counts packed 8 bits each: [0] regular, [1..MF_NBIN] worklist
-    // bins; and the work items of this lane's long rows
+    // bins; and this lane's long rows (lazy) or their work items
     unsigned long long packed = 0;
     int nch = 0;
     long long lab_slots = 0;
@@ -1031,7 +1058,7 @@ __device__ __forceinline__ void frontier_push(const MfParams &P, Sh &sh, const b
         if (!take[r]) continue;
         lab_slots += d[r];
         ++lab_n;
-        if (d[r] > P.bfs_hub) nch += (d[r] + MF_BFS_CHUNK - 1) / MF_BFS_CHUNK;
+        if (d[r] > P.bfs_hub) nch += lazy ? 1 : (d[r] + MF_BFS_CHUNK - 1) / MF_BFS_CHUNK;
         else packed += 1ull;
         if (with_wl && ev[r] > 0) packed += 1ull << (8 * (row_bin(P, d[r]) + 1));
     }
@@ -1071,7 +1098,7 @@ __device__ __forceinline__ void frontier_push(const MfParams &P, Sh &sh, const b
         if (k2) b2 = atomicAdd(&ctl->wl_tail[1].w[0], k2);
         if (k3) b3 = atomicAdd(&ctl->wl_tail[2].w[0], k3);
         if (k4) b4 = atomicAdd(&ctl->wl_tail[3].w[0], k4);
-        if (ctot) bi = atomicAdd(&ctl->hub_tail.w[0], (unsigned)ctot);
+        if (ctot) bi = atomicAdd(lazy ? &ctl->long_tail.w[0] : &ctl->hub_tail.w[0], (unsigned)ctot);
         const unsigned act = k1 + k2 + k3 + k4;
         if (act) atomicAdd(&ctl->wl_tail[MF_NBIN].w[0], act);
     }
@@ -1091,10 +1118,15 @@ __device__ __forceinline__ void frontier_push(const MfParams &P, Sh &sh, const b
         }
     }
     if (ctot == 0) return;
-    // long rows: ceil(deg / MF_BFS_CHUNK) work items each, which any warp can
-    // take.  A hub of 10^5 slots has hundreds of items, so the warp writes all
-    // its rows' items together, 32 at a time (each lane finds the row that owns
-    // its item), instead of each lane walking its own rows' items.
+    const unsigned ibase = __shfl_sync(0xffffffffu, bi, 0);
+    const int cexcl = cincl - nch;
+    if (lazy) {
+        unsigned at = ibase + (unsigned)cexcl;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (take[r] && d[r] > P.bfs_hub) P.sc.blong[at++] = z[r];
+        return;
+    }
     int x0[R], nc[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -1102,8 +1134,19 @@ __device__ __forceinline__ void frontier_push(const MfParams &P, Sh &sh, const b
         nc[r] = big ? (d[r] + MF_BFS_CHUNK - 1) / MF_BFS_CHUNK : 0;
         x0[r] = big ? P.g.off[z[r]] : 0;
     }
-    const unsigned ibase = __shfl_sync(0xffffffffu, bi, 0);
-    const int cexcl = cincl - nch;
+    write_items<R>(P, nc, x0, d, ibase, cexcl, ctot);
+}
+
+// Long rows: ceil(deg / MF_BFS_CHUNK) work items each (first slot, length),
+// which any warp can take.  A hub of 10^5 slots has hundreds of items, so the
+// warp writes all its rows' items together, 32 at a time (each lane finds the
+// row that owns its item), at ibase + [0, ctot); lane L's rows own the items
+// from cexcl (the exclusive prefix of nc over the lanes).  Called by the whole warp.
+template <int R>
+__device__ __forceinline__ void write_items(const MfParams &P, const int (&nc)[R], const int (&x0)[R],
+                                            const int (&d)[R], unsigned ibase, int cexcl, int ctot)
+{
+    const int lane = threadIdx.x & 31;
     for (int i0 = 0; i0 < ctot; i0 += 32) {         // the same trip count in every lane
         const int i = i0 + lane;
         int owner = 0;
@@ -1163,7 +1206,7 @@ __device__ __noinline__ void phase_bfs_init(const MfParams &P, Sh &sh)
             if (root[0]) dv[0] = need_total ? dall : ldg_cg(P.g.deg + v);
         }
         total += dall;
-        if (__any_sync(0xffffffffu, root[0])) frontier_push<1>(P, sh, root, zv, dv, ev, false, 0);
+        if (__any_sync(0xffffffffu, root[0])) frontier_push<1>(P, sh, root, zv, dv, ev, false, 0, true);
     }
     if (need_total) {
         // one atomic per CTA for the used-slot total
@@ -1215,6 +1258,40 @@ __device__ __forceinline__ void bfs_visit(const MfParams &P, Sh &sh, const int (
 }
 
 constexpr int kBR = 4;
+
+// Before a top-down level that follows one which labelled long rows: each
+// long row becomes its ceil(deg / MF_BFS_CHUNK) work items.  Warps take the
+// long-row vertices 32 at a time and write their items together.
+__device__ __noinline__ void phase_bfs_expand(const MfParams &P, Sh &sh)
+{
+    MfCtrl *ctl = P.ctrl;
+    const int lane = threadIdx.x & 31;
+    const int lo = sh.d.long_lo, cnt = sh.d.long_hi - lo;
+    const int nwarps = vn() * (int)(blockDim.x >> 5);
+    const int rank = warp_rank(vn(), 0);
+    bool first = true;
+    for (;;) {
+        const int b = warp_deal(&ctl->head0.w[0], cnt, 32u, rank, nwarps, first);
+        if (b >= cnt) break;
+        const int k = b + lane;
+        const int z = k < cnt ? __ldcg(P.sc.blong + lo + k) : -1;
+        int d[1], x0[1], nc[1];
+        d[0] = z >= 0 ? ldg_cg(P.g.deg + z) : 0;
+        x0[0] = z >= 0 ? P.g.off[z] : 0;
+        nc[0] = (d[0] + MF_BFS_CHUNK - 1) / MF_BFS_CHUNK;
+        int incl = nc[0];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int tot = __shfl_sync(0xffffffffu, incl, 31);
+        unsigned bi = 0;
+        if (lane == 0 && tot) bi = atomicAdd(&ctl->hub_tail.w[0], (unsigned)tot);
+        bi = __shfl_sync(0xffffffffu, bi, 0);
+        write_items<1>(P, nc, x0, d, bi, incl - nc[0], tot);
+    }
+}
 
 __device__ __noinline__ void phase_bfs_level(const MfParams &P, Sh &sh)
 {
@@ -2655,6 +2732,10 @@ loop:
                     if (!grid_sync(P, H_BFS_NEXT, sh)) return false;
                 }
             } else {
+                if (sh.d.expand) {
+                    phase_bfs_expand(P, sh);
+                    if (!grid_sync(P, H_EXPANDED, sh)) return false;
+                }
                 phase_bfs_level(P, sh);
                 flush_acc(P, sh, 0);
                 if (!grid_sync(P, H_BFS_NEXT, sh)) return false;

@@ -103,7 +103,7 @@ EXPORTS = ["maxflow_build_layout", "maxflow_kernel_launches", "maxflow_default_o
 
 TRACE_NAMES = ["start", "prologue", "batch_validated", "batch_located", "room_checked", "capacities_changed",
                "iteration_start", "bfs_roots", "bfs_level", "worklist", "discharge", "end", "bfs_bottom_up_first",
-               "bfs_cta_join"]
+               "bfs_cta_join", "bfs_items_split"]
 
 _lib = None
 
