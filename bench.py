@@ -484,7 +484,7 @@ def run_configs(S, es_main, hbm):
     return out
 
 
-SERVING_SMALL = ["--workload", "serving:18,18,19,19,20", "--steps", "60", "--warmup", "1", "--budget-gb", "1.5"]
+SERVING_SMALL = ["--workload", "serving:18,18,19,19,20", "--steps", "60", "--warmup", "3", "--budget-gb", "1.5"]
 
 
 def serving_summary():
@@ -504,7 +504,9 @@ def serving_summary():
     return {"command": "bench.py " + " ".join(SERVING_SMALL), "workload": d["config"]["workload"],
             "updates_per_s": d["value"], "latency_ms": d["latency_ms"], "states_gb": d["config"]["states_gb"],
             "budget_gb": d["config"]["budget_gb"], "evictions": d["serving"].get("evictions"),
-            "flow_check": d["flow_check"], "gpu_launches": d["gpu_launches"], "wall_s": time.perf_counter() - t0}
+            "flow_check": d["flow_check"], "gpu_launches": d["gpu_launches"],
+            "offered_rate_per_s": d["config"]["rate_per_s"], "calibration": d["calibration"],
+            "wall_s": time.perf_counter() - t0}
 
 
 def batched_summary():
@@ -705,7 +707,13 @@ def run_serving(args):
         r.arrival = 0.0
     srv.max_per_tick = 1
     cst = srv.run(cal)
-    mean_s = cst.wall_s / len(cal)
+    # service time of a timed request: the calibration's mean per request, or its
+    # mean per update times the timed requests' mean size, whichever is longer
+    # (the calibration sample's sizes need not match the timed requests' mix)
+    per_req_s = cst.wall_s / len(cal)
+    per_upd_s = cst.wall_s / max(1, sum(r.size for r in cal))
+    mean_size = float(np.mean([r.size for r in reqs[n_cal:]])) if args.steps > 0 else 0.0
+    mean_s = max(per_req_s, per_upd_s * mean_size)
     rate = args.utilization / mean_s
     srv.max_per_tick = None
     srv.stats = SV.ServeStats()
@@ -743,7 +751,9 @@ def run_serving(args):
                        "target_utilization": args.utilization, "group_blocks": args.group_blocks,
                        "l2": "states of several GB, larger than L2"},
             "latency_ms": {"p50": sm["p50_ms"], "p99": sm["p99_ms"], "mean": sm["mean_ms"]},
-            "serving": sm, "calibration": {"requests": len(cal), "mean_wall_ms": 1e3 * mean_s},
+            "serving": sm, "calibration": {"requests": len(cal), "mean_wall_ms": 1e3 * per_req_s,
+                                           "updates": int(sum(r.size for r in cal)),
+                                           "service_ms_per_timed_request": 1e3 * mean_s},
             "flow_check": {"graph": 0, "requests": sum(1 for r in reqs if r.graph == 0), "gpu": int(got),
                            "oracle": int(want), "equal": bool(got == want)},
             "gpu_launches": launches,
