@@ -3,8 +3,9 @@
 The batched launch is replaced by a function of the knobs the tuner set on
 the solvers, so the search itself is checked: it finds the best value of
 every knob when the cost is separable, never returns a configuration worse
-than the default, stops after a pass without gain, and leaves the solvers set
-to what it returns.
+than the default, stops after a pass without gain, does not keep a
+configuration that won one trial by luck, and leaves the solvers set to what
+it returns.
 """
 from paper_2511_01235_gb300 import autotune, native
 
@@ -61,3 +62,32 @@ def test_never_worse_than_the_default_and_stops_without_gain(monkeypatch):
     others = sum(len(v) - 1 for v in (autotune.GROUP_BLOCKS, autotune.ROUNDS, autotune.CYCLES, autotune.SPLITS))
     assert len(trials) == 1 + others
     assert len(calls) == 2 * (1 + others)                 # reps launches per trial
+
+
+def test_a_lucky_trial_does_not_replace_the_default(monkeypatch):
+    """A configuration that wins its one descent trial but loses the interleaved
+    confirmation against the default is dropped: the default stays."""
+    lucky = (8, 4, 0, (0, 0, 0))          # rounds = 4
+    seen = {"lucky": 0}
+
+    def cost(gb, r, k, sp):
+        if (gb, r, k, sp) == lucky:
+            seen["lucky"] += 1
+            return 4.0 if seen["lucky"] <= 2 else 6.0     # fast in its trial (two reps), slow afterwards
+        return 5.0 if (gb, r, k, sp) == (8, 0, 0, (0, 0, 0)) else 7.0
+
+    _install(monkeypatch, cost)
+    S = [FakeSolver()]
+    best, best_ms, trials = autotune.tune(S, passes=2, reps=2, confirm_reps=3)
+    assert any(cfg["rounds"] == 4 and ms == 4.0 for cfg, ms in trials)    # it did win its trial
+    assert best == autotune.DEFAULT and best_ms == 5.0
+    assert (S[0].rounds, S[0].cycles, S[0].split) == (0, 0, (0, 0, 0))
+
+
+def test_a_win_within_the_margin_is_not_taken(monkeypatch):
+    """A trial 1 % faster than the best so far (inside MARGIN) does not replace it."""
+    _install(monkeypatch, lambda gb, r, k, sp: 4.95 if (gb, r, k, sp) == (8, 4, 0, (0, 0, 0))
+             else (5.0 if (gb, r, k, sp) == (8, 0, 0, (0, 0, 0)) else 7.0))
+    S = [FakeSolver()]
+    best, best_ms, _ = autotune.tune(S, passes=2, reps=1)
+    assert best == autotune.DEFAULT and best_ms == 5.0
