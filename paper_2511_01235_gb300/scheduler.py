@@ -104,10 +104,12 @@ def family(name: str, seed: int):
 # traces
 # ---------------------------------------------------------------------------
 
-def collect(solver: native.Solver, batches, actions=None, log=None):
+def collect(solver: native.Solver, batches, actions=None, log=None, reps=1):
     """Features and per-action device time (ms) of every batch, each action on a
-    clone.  The state then advances by the batch's fastest action: the states a
-    good schedule meets are those it makes itself, and a static re-solve or a
+    clone (the fastest of `reps` runs, each on a fresh clone: single runs vary
+    by several percent, and a noisy target teaches the network noise).  The
+    state then advances by the batch's fastest action: the states a good
+    schedule meets are those it makes itself, and a static re-solve or a
     many-round update leaves a different preflow than the default would."""
     if actions is None:
         actions = list(range(len(native.maxflow_sched_actions())))
@@ -118,11 +120,14 @@ def collect(solver: native.Solver, batches, actions=None, log=None):
     for i, b in enumerate(batches):
         X[i] = solver.features(b.u, b.v, b.cap)
         for a in actions:
-            C = solver.clone()
-            C.run_action(b.u, b.v, b.cap, a)
-            T[i, a] = C.stats()["ms_update"]
+            t = float("inf")
+            for _ in range(max(1, reps)):
+                C = solver.clone()
+                C.run_action(b.u, b.v, b.cap, a)
+                t = min(t, C.stats()["ms_update"])
+                C.close()
+            T[i, a] = t
             M[i, a] = 1.0
-            C.close()
         solver.run_action(b.u, b.v, b.cap, int(np.argmin(np.where(M[i] > 0, T[i], np.inf))))
         if log:
             log(f"  batch {i} B={b.size} best action {int(np.argmin(np.where(M[i] > 0, T[i], np.inf)))} "
@@ -130,11 +135,11 @@ def collect(solver: native.Solver, batches, actions=None, log=None):
     return X, T, M
 
 
-def collect_family(name, seed, k, log=None):
+def collect_family(name, seed, k, log=None, reps=1):
     g, make = family(name, seed)
     S = native.Solver(g.n, g.src, g.dst, g.cap, g.s, g.t)
     batches = make(k)
-    X, T, M = collect(S, batches, log=log)
+    X, T, M = collect(S, batches, log=log, reps=reps)
     S.close()
     return X, T, M
 
@@ -194,6 +199,7 @@ def main():
     ap.add_argument("--out", default=DEFAULT_WEIGHTS)
     ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--traces", default=None, help="save traces (npz) here")
+    ap.add_argument("--reps", type=int, default=2, help="runs per action and batch (the fastest counts)")
     args = ap.parse_args()
     import torch
     torch.cuda.set_device(0)
@@ -202,11 +208,11 @@ def main():
     parts = []
     for name, seed, k in TRAIN_PLAN:
         print(f"collect {name} seed {seed} x{k}", flush=True)
-        parts.append(collect_family(name, seed, k, log=print))
+        parts.append(collect_family(name, seed, k, log=print, reps=args.reps))
     X = np.concatenate([p[0] for p in parts])
     T = np.concatenate([p[1] for p in parts])
     M = np.concatenate([p[2] for p in parts])
-    held = [collect_family(name, seed, k) for name, seed, k in HELDOUT_PLAN]
+    held = [collect_family(name, seed, k, reps=args.reps) for name, seed, k in HELDOUT_PLAN]
     Xh = np.concatenate([p[0] for p in held])
     Th = np.concatenate([p[1] for p in held])
     Mh = np.concatenate([p[2] for p in held])
@@ -216,7 +222,7 @@ def main():
     ev_train = evaluate(mlp, X, T, M)
     ev_held = evaluate(mlp, Xh, Th, Mh)
     meta = {"train_rows": int(len(X)), "train_loss": loss, "train_eval": ev_train, "heldout_eval": ev_held,
-            "collect_s": time.time() - t0, "plan": TRAIN_PLAN}
+            "collect_s": time.time() - t0, "plan": TRAIN_PLAN, "reps": args.reps}
     save(mlp, args.out, meta)
     print(json.dumps(meta), flush=True)
 
