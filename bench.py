@@ -670,6 +670,21 @@ def _serving_worker(job):
     return g, SV.graph_batches(g, sizes, bseed)
 
 
+def service_time(cal_wall_s: float, cal_sizes, timed_sizes):
+    """(calibration mean per request, expected service time of a timed request), in seconds.
+
+    The calibration serves its requests one at a time in cal_wall_s.  A timed
+    request is taken to cost the longer of the calibration's mean per request
+    and its mean per update times the timed requests' mean size: the
+    calibration sample's sizes need not match the timed mix, and the per-request
+    mean of a sample of small requests would offer more load than the server
+    sustains."""
+    per_req = cal_wall_s / max(1, len(cal_sizes))
+    per_upd = cal_wall_s / max(1, int(sum(cal_sizes)))
+    mean_size = float(np.mean(timed_sizes)) if len(timed_sizes) else 0.0
+    return per_req, max(per_req, per_upd * mean_size)
+
+
 def run_serving(args):
     """Serving: 16 R-MAT graphs (scales 18x4, 19x3, 20x3, 21x3, 22x3) under a device-memory
     budget, Poisson arrivals of mixed batches (sizes log-uniform in [10, 100K]), continuous
@@ -707,13 +722,7 @@ def run_serving(args):
         r.arrival = 0.0
     srv.max_per_tick = 1
     cst = srv.run(cal)
-    # service time of a timed request: the calibration's mean per request, or its
-    # mean per update times the timed requests' mean size, whichever is longer
-    # (the calibration sample's sizes need not match the timed requests' mix)
-    per_req_s = cst.wall_s / len(cal)
-    per_upd_s = cst.wall_s / max(1, sum(r.size for r in cal))
-    mean_size = float(np.mean([r.size for r in reqs[n_cal:]])) if args.steps > 0 else 0.0
-    mean_s = max(per_req_s, per_upd_s * mean_size)
+    per_req_s, mean_s = service_time(cst.wall_s, [r.size for r in cal], [r.size for r in reqs[n_cal:]])
     rate = args.utilization / mean_s
     srv.max_per_tick = None
     srv.stats = SV.ServeStats()

@@ -49,3 +49,15 @@ def test_cpu_baseline_sample_is_bounded_by_its_budget():
     assert len(bench.cpu_baseline_sample(g, batches, budget_s=0.0)) == 1       # stops after the first batch
     times = bench.cpu_baseline_sample(g, batches, budget_s=60.0)
     assert len(times) == 4 and all(t > 0 for t in times)
+
+
+def test_serving_service_time_follows_the_timed_sizes():
+    """The offered load of the serving run: a calibration of small requests
+    scales up to the timed requests' mean size; a calibration of large ones
+    keeps its own per-request mean."""
+    import bench
+    per_req, svc = bench.service_time(0.1, [1000] * 10, [5000, 15000])      # 10 ms per 1 K updates
+    assert abs(per_req - 0.01) < 1e-12 and abs(svc - 0.1) < 1e-12          # 10 K mean size -> 100 ms
+    per_req, svc = bench.service_time(1.0, [50000] * 10, [10, 30])
+    assert abs(per_req - 0.1) < 1e-12 and abs(svc - 0.1) < 1e-12           # never below the per-request mean
+    assert bench.service_time(0.5, [100], [])[1] == 0.5
