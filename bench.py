@@ -670,6 +670,29 @@ def _serving_worker(job):
     return g, SV.graph_batches(g, sizes, bseed)
 
 
+def step_records(lat_ms, kernel_ms, detail, barriers, alg_bytes, batch: int):
+    """One record per timed batch: latency (CUDA events around the call), the
+    kernel's own time, updates/s, the solve's counters and the algorithmic
+    bytes with their rate.  detail rows: kernel ms, iterations, BFS levels,
+    pushes, relabels."""
+    out = []
+    for k, lt in enumerate(lat_ms):
+        row = detail[k]
+        km = float(kernel_ms[k])
+        out.append({"step": k, "batch": int(batch), "latency_ms": float(lt), "kernel_ms": km,
+                    "updates_per_s": batch / (float(lt) / 1e3) if lt > 0 else None,
+                    "iterations": int(row[1]), "bfs_levels": int(row[2]), "pushes": int(row[3]),
+                    "relabels": int(row[4]), "barriers": int(barriers[k]), "alg_bytes": float(alg_bytes[k]),
+                    "alg_gbs": float(alg_bytes[k]) / (km * 1e6) if km > 0 else None})
+    return out
+
+
+def write_jsonl(path: str, records):
+    with open(path, "w") as f:
+        for r in records:
+            f.write(json.dumps(r) + "\n")
+
+
 def service_time(cal_wall_s: float, cal_sizes, timed_sizes):
     """(calibration mean per request, expected service time of a timed request), in seconds.
 
@@ -792,6 +815,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-configs", action="store_true", help="headline workload only (no configs block)")
+    ap.add_argument("--log-jsonl", default=None,
+                    help="write one JSON record per timed batch (latency, kernel time, iterations, bytes, GB/s)")
     ap.add_argument("--static-reps", type=int, default=3)
     ap.add_argument("--quick", action="store_true", help="timed steps only (for profiling runs)")
     ap.add_argument("--sched-steps", type=int, default=30, help="held-out batches for the learned-vs-fixed schedule comparison")
@@ -872,6 +897,8 @@ def main():
     launches = native.kernel_launches() - l0
     clocks = clk.stop()
     lat = np.array([a.elapsed_time(b) for a, b in evs])
+    if args.log_jsonl and rank == 0:
+        write_jsonl(args.log_jsonl, step_records(lat, kms, detail, barriers, kbytes, args.batch))
     tot_ms = float(lat.sum())
     value, tot_ms, _ = aggregate_over_ranks(tot_ms, args.batch * args.steps, device="cuda" if ws > 1 else None)
     final_value = S.query()[0]

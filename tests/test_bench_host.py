@@ -61,3 +61,20 @@ def test_serving_service_time_follows_the_timed_sizes():
     per_req, svc = bench.service_time(1.0, [50000] * 10, [10, 30])
     assert abs(per_req - 0.1) < 1e-12 and abs(svc - 0.1) < 1e-12           # never below the per-request mean
     assert bench.service_time(0.5, [100], [])[1] == 0.5
+
+
+def test_per_batch_jsonl_records(tmp_path):
+    """--log-jsonl: one record per timed batch, its rate and GB/s from its own
+    latency, kernel time and algorithmic bytes."""
+    import json
+    import bench
+    recs = bench.step_records([2.0, 1.0], [1.5, 0.5], [[1.5, 2, 11, 100, 7], [0.5, 1, 5, 40, 3]], [26, 19],
+                              [3.0e8, 1.0e8], 10000)
+    assert [r["step"] for r in recs] == [0, 1]
+    assert recs[0]["updates_per_s"] == 10000 / 2e-3 and recs[1]["updates_per_s"] == 10000 / 1e-3
+    assert abs(recs[0]["alg_gbs"] - 3.0e8 / 1.5e6) < 1e-9 and recs[1]["iterations"] == 1
+    assert recs[0]["barriers"] == 26 and recs[1]["relabels"] == 3
+    path = tmp_path / "steps.jsonl"
+    bench.write_jsonl(str(path), recs)
+    back = [json.loads(line) for line in path.read_text().splitlines()]
+    assert back == recs
