@@ -108,11 +108,12 @@ def test_learned_schedule_beats_the_fixed_schedules_on_heldout_batches():
     counts (CUDA events around the call on the clone's stream, the learned
     path's features and forward pass included); the stream's solver then takes
     the batch with the default schedule.  The learned schedule's total is below
-    the paper's fixed schedule by a wide margin and no worse than the library's
-    own default schedule (measured this way the two are within about 2 % on
-    these families: the network mostly picks the default here, and its gain
-    over the default comes from large R-MAT batches, where a static re-solve
-    is faster); the flow value is the same whatever the schedule."""
+    the paper's fixed schedule by a wide margin and no more than 2 % above the
+    library's own default schedule.  That bound is loose on purpose: the
+    committed weights measure 0.86-0.90 of the default here, but weights trained
+    on single-run timings measured 0.92-0.98, and a bound tighter than the
+    run-to-run spread would test the noise.  The flow value is the same
+    whatever the schedule."""
     import torch
     mlp = SCH.load()
     totals = {"learned": 0.0, "paper": 0.0, "default": 0.0}
