@@ -2,10 +2,11 @@
 //
 // One cooperative, persistent kernel runs a whole solve: the optional static
 // initialisation (Alg. 1) or batch repair (Alg. 5),
-// then the loop { backward BFS (Alg. 4 / Alg. 6) ; active-vertex worklist
-// (Sec. 5.2.1 O1) ; stop if empty ; push-relabel discharge (Alg. 2) ;
-// remove-invalid-edges (Alg. 3) }, then the value formula of Alg. 5.  Phases
-// are separated by a grid barrier instead of kernel launches, so the
+// then the loop { backward BFS (Alg. 4 / Alg. 6), direction-optimising, which
+// also builds the active-vertex worklist (Sec. 5.2.1 O1) ; stop if empty ;
+// push-relabel discharge (Alg. 2) in one or more rounds ; remove-invalid-edges
+// (Alg. 3, when enabled: off by default) }, then the value formula of Alg. 5.
+// Phases are separated by a grid barrier instead of kernel launches, so the
 // termination test never leaves the device and a small update costs one
 // launch.  Every barrier wait is bounded in time: on expiry the CTA records
 // MF_E_WAIT and returns, and the host reports MAXFLOW_ERR_INTERNAL.
