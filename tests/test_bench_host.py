@@ -78,3 +78,29 @@ def test_per_batch_jsonl_records(tmp_path):
     bench.write_jsonl(str(path), recs)
     back = [json.loads(line) for line in path.read_text().splitlines()]
     assert back == recs
+
+
+def test_phase_roofline_arithmetic():
+    """Per-phase rate: algorithmic bytes over the phase's device time, and its
+    fraction of the peak; a phase that took no time reports 0."""
+    import bench
+
+    class FakeStats:
+        def __init__(self, rows):
+            self.rows = iter(rows)
+
+        def stats(self):
+            return next(self.rows)
+
+    calls = [{"bytes_bfs": 3.0e8, "ms_bfs": 0.5, "bytes_discharge": 1.0e8, "ms_discharge": 0.25,
+              "bytes_fix": 0, "ms_fix": 0.0, "bytes_apply": 1.0e6, "ms_apply": 0.1}] * 2
+    S = FakeStats(calls)
+    totals = {}
+    bench._phase_rates(S, totals)
+    bench._phase_rates(S, totals)
+    assert totals["bfs"] == [6.0e8, 1.0] and totals["discharge"] == [2.0e8, 0.5]
+    out = bench.phase_roofline(totals, hbm=6000.0)
+    assert abs(out["bfs"]["gbs"] - 600.0) < 1e-9 and abs(out["bfs"]["frac"] - 0.1) < 1e-12
+    assert abs(out["discharge"]["gbs"] - 400.0) < 1e-9
+    assert out["fix"]["gbs"] == 0.0 and out["fix"]["frac"] == 0.0
+    assert abs(out["apply"]["gbs"] - 10.0) < 1e-9
