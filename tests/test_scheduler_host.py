@@ -1,4 +1,4 @@
-"""The scheduler's offline evaluation and targets, on the CPU with a stand-in network."""
+"""The scheduler's offline evaluation, targets and trace collection, on the CPU with stand-ins."""
 import numpy as np
 
 from paper_2511_01235_gb300 import scheduler as SCH
@@ -35,3 +35,56 @@ def test_targets_are_log_times_clamped_below():
     t = SCH.targets(T)
     assert t.dtype == np.float32
     assert np.allclose(t, [[0.0, 1.0, np.log(1e-3), np.log(1e-3)]], atol=1e-6)
+
+
+class _Clone:
+    def __init__(self, parent):
+        self.parent = parent
+        self.t = None
+
+    def run_action(self, u, v, c, a):
+        self.t = self.parent.script(a)
+
+    def stats(self):
+        return {"ms_update": self.t}
+
+    def close(self):
+        pass
+
+
+class _Solver:
+    """Stands in for native.Solver: each clone's run of action a takes the next
+    scripted time of a; the solver records the actions it runs itself."""
+
+    def __init__(self, times):
+        self.times = {a: list(ts) for a, ts in times.items()}
+        self.ran = []
+
+    def script(self, a):
+        return self.times[a].pop(0)
+
+    def features(self, u, v, c):
+        return np.zeros(16, np.float32)
+
+    def clone(self):
+        return _Clone(self)
+
+    def run_action(self, u, v, c, a):
+        self.ran.append(a)
+
+
+class _Batch:
+    u = v = cap = np.zeros(1, np.int32)
+
+
+def test_collect_keeps_the_fastest_run_and_advances_by_the_best_action():
+    """Traces take the fastest of `reps` runs of every action (each on a fresh
+    clone), and the stream then advances by the batch's fastest action."""
+    acts = [0, 1, 2]
+    times = {0: [5.0, 4.0], 1: [2.5, 6.0], 2: [3.0, 2.0]}      # fastest runs: 4.0, 2.5, 2.0
+    S = _Solver(times)
+    X, T, M = SCH.collect(S, [_Batch()], actions=acts, reps=2)
+    assert list(T[0, :3]) == [4.0, 2.5, 2.0] and list(M[0, :3]) == [1.0, 1.0, 1.0]
+    assert M[0, 3:].sum() == 0                                  # actions not run stay masked
+    assert S.ran == [2]
+    assert all(len(v) == 0 for v in S.times.values())           # two runs of every action
